@@ -1,0 +1,143 @@
+/*
+ * Exact all-pairs Jaccard oracle: TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the smoke check and the CPU-baseline leg of the benchmark
+ * may load this library.  The product path never calls it and shares no code
+ * with it: no headers, no helpers, no constants.
+ *
+ * What it computes is the plain definition of the quantities (Sec. II-A and
+ * Sec. III-A of "Communication-Efficient Jaccard Similarity for
+ * High-Performance Distributed Genome Comparisons", arXiv 1911.04200):
+ *
+ *   |X_i|                 number of distinct values of sample i
+ *   b_ij = |X_i ∩ X_j|    counted by a two-pointer merge of the two sorted
+ *                         value lists (the intersection matrix, Sec. III-A;
+ *                         called C in this library's interface)
+ *   c_ij = |X_i| + |X_j| - b_ij           (union by inclusion-exclusion)
+ *   s_ij = b_ij / c_ij    in IEEE binary64, round-to-nearest (Eq. 2);
+ *                         s_ij = 1 when both sets are empty (Sec. II-A)
+ *
+ * Inputs are sample value lists sorted ascending (the paper's samples are
+ * sorted numeric files, Sec. IV); equal adjacent values are one set element.
+ * There is no blocking, no packing and no reordering: every pair is merged.
+ */
+#include <stdint.h>
+#include <stddef.h>
+
+/* Number of distinct values in a sorted list (|X|, Sec. II-A). */
+uint64_t oracle_distinct(const uint64_t* a, uint64_t na)
+{
+    uint64_t k = 0;
+    for (uint64_t i = 0; i < na; ++i)
+        if (i == 0 || a[i] != a[i - 1]) ++k;
+    return k;
+}
+
+/* |X ∩ Y| for two sorted lists, by a two-pointer merge (Sec. II-A). */
+uint64_t oracle_intersect(const uint64_t* a, uint64_t na,
+                          const uint64_t* b, uint64_t nb)
+{
+    uint64_t i = 0, j = 0, k = 0;
+    while (i < na && j < nb) {
+        if (a[i] < b[j]) {
+            ++i;
+        } else if (b[j] < a[i]) {
+            ++j;
+        } else {
+            uint64_t v = a[i];
+            ++k;
+            while (i < na && a[i] == v) ++i;
+            while (j < nb && b[j] == v) ++j;
+        }
+    }
+    return k;
+}
+
+/* s = b / (|X|+|Y|-b) in binary64; 1 for two empty sets (Sec. II-A, Eq. 2). */
+double oracle_jaccard(uint64_t inter, uint64_t size_x, uint64_t size_y)
+{
+    uint64_t uni = size_x + size_y - inter;
+    if (uni == 0) return 1.0;
+    return (double)inter / (double)uni;
+}
+
+/*
+ * All pairs of one collection.  offsets has n+1 entries; sample i is
+ * ids[offsets[i] .. offsets[i+1]).  C and J are n*n row-major (either may be
+ * NULL), sizes has n entries (may be NULL).
+ */
+void oracle_all_pairs(uint64_t n, const uint64_t* offsets, const uint64_t* ids,
+                      uint64_t* C, uint64_t* sizes, double* J, int threads)
+{
+    uint64_t* sz = sizes;
+    /* sizes are needed for J; compute them first */
+    #pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1)
+    for (int64_t i = 0; i < (int64_t)n; ++i) {
+        uint64_t d = oracle_distinct(ids + offsets[i], offsets[i + 1] - offsets[i]);
+        if (sz) sz[i] = d;
+    }
+    #pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1)
+    for (int64_t i = 0; i < (int64_t)n; ++i) {
+        const uint64_t* a = ids + offsets[i];
+        uint64_t na = offsets[i + 1] - offsets[i];
+        uint64_t si = sz ? sz[i] : oracle_distinct(a, na);
+        for (uint64_t j = (uint64_t)i; j < n; ++j) {
+            const uint64_t* b = ids + offsets[j];
+            uint64_t nb = offsets[j + 1] - offsets[j];
+            uint64_t inter = oracle_intersect(a, na, b, nb);
+            if (C) { C[(uint64_t)i * n + j] = inter; C[j * n + (uint64_t)i] = inter; }
+            if (J) {
+                uint64_t sj = sz ? sz[j] : oracle_distinct(b, nb);
+                double s = oracle_jaccard(inter, si, sj);
+                J[(uint64_t)i * n + j] = s;
+                J[j * n + (uint64_t)i] = s;
+            }
+        }
+    }
+}
+
+/*
+ * A sample of pairs (pi[t], pj[t]) of one collection, each merged on its own.
+ * Used where the whole matrix is too large for this oracle.
+ */
+void oracle_pairs(uint64_t n, const uint64_t* offsets, const uint64_t* ids,
+                  uint64_t npairs, const uint64_t* pi, const uint64_t* pj,
+                  uint64_t* C_out, double* J_out, int threads)
+{
+    (void)n;
+    #pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1)
+    for (int64_t t = 0; t < (int64_t)npairs; ++t) {
+        const uint64_t* a = ids + offsets[pi[t]];
+        uint64_t na = offsets[pi[t] + 1] - offsets[pi[t]];
+        const uint64_t* b = ids + offsets[pj[t]];
+        uint64_t nb = offsets[pj[t] + 1] - offsets[pj[t]];
+        uint64_t inter = oracle_intersect(a, na, b, nb);
+        if (C_out) C_out[t] = inter;
+        if (J_out) J_out[t] = oracle_jaccard(inter, oracle_distinct(a, na), oracle_distinct(b, nb));
+    }
+}
+
+/*
+ * Query collection against reference collection: C[q][r] = |Q_q ∩ R_r|,
+ * J likewise (the same definitions with X from one collection and Y from the
+ * other).  C and J are nq*nr row-major; qsizes has nq entries.
+ */
+void oracle_cross(uint64_t nq, const uint64_t* qoff, const uint64_t* qids,
+                  uint64_t nr, const uint64_t* roff, const uint64_t* rids,
+                  uint64_t* C, uint64_t* qsizes, double* J, int threads)
+{
+    #pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1)
+    for (int64_t q = 0; q < (int64_t)nq; ++q) {
+        const uint64_t* a = qids + qoff[q];
+        uint64_t na = qoff[q + 1] - qoff[q];
+        uint64_t sq = oracle_distinct(a, na);
+        if (qsizes) qsizes[q] = sq;
+        for (uint64_t r = 0; r < nr; ++r) {
+            const uint64_t* b = rids + roff[r];
+            uint64_t nb = roff[r + 1] - roff[r];
+            uint64_t inter = oracle_intersect(a, na, b, nb);
+            if (C) C[(uint64_t)q * nr + r] = inter;
+            if (J) J[(uint64_t)q * nr + r] = oracle_jaccard(inter, sq, oracle_distinct(b, nb));
+        }
+    }
+}
