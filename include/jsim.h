@@ -1,0 +1,202 @@
+/*
+ * jsim: exact all-pairs Jaccard similarity on one GB300 GPU (sm_103a).
+ *
+ * Method: "Communication-Efficient Jaccard Similarity for High-Performance
+ * Distributed Genome Comparisons" (arXiv 1911.04200).  Each sample i is a
+ * set X_i of unsigned 64-bit values (k-mer IDs in genomics).  The samples are
+ * the columns of a boolean indicator matrix A (a_ki = 1 iff k in X_i,
+ * Sec. III-A).  The library computes, for every pair of samples,
+ *
+ *   C[i][j] = |X_i ∩ X_j|            the intersection matrix A^T A (the paper
+ *                                    calls it B, Sec. III-A)
+ *   sizes[i] = |X_i|                 column sums of A (the paper's a-hat)
+ *   J[i][j] = C / (|X_i|+|X_j|-C)    in IEEE binary64, round-to-nearest;
+ *                                    1.0 when both sets are empty (Sec. II-A)
+ *
+ * by the paper's method (Sec. III-B): rows of A are cut into batches of
+ * `batch_rows` consecutive values (Eq. 3); in each batch the all-zero rows are
+ * dropped through a filter vector and its prefix sum (Eq. 5, Eq. 6); every 64
+ * consecutive surviving rows of a sample become one bitmask word (b = 64);
+ * and C accumulates sum_w popcount(word_wi AND word_wj) over all batches
+ * (Eq. 7, Eq. 4).  All of it runs in this library's CUDA kernels.
+ *
+ * Results are exact: C and sizes are integers, and J is the correctly rounded
+ * binary64 quotient of two integers below 2^53.
+ *
+ * Conventions for every call:
+ *  - Return value: JSIM_OK (0) or one of the JSIM_ERR_* codes below;
+ *    jsim_strerror() gives a message.  On an error no output buffer is
+ *    written, except where a call says otherwise.
+ *  - Ownership: the caller owns every buffer it passes.  The library reads
+ *    inputs during the call only, never keeps or frees caller pointers, and
+ *    frees whatever it allocated before it returns (handles excepted, which
+ *    their destroy calls free).
+ *  - Pointers are host or device pointers as the `mem` field or argument says.
+ *    Device pointers must be on the context's device.  Host pointers may be
+ *    pageable; pinned host memory makes the copies faster.
+ *  - Calls on one context are not thread-safe; use one context per thread.
+ *  - All device work is ordered on the context's stream; every call returns
+ *    after its work has finished (it synchronises that stream).
+ */
+#ifndef JSIM_H
+#define JSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define JSIM_API __attribute__((visibility("default")))
+#else
+#define JSIM_API
+#endif
+
+/* ---- error codes --------------------------------------------------------- */
+#define JSIM_OK               0
+#define JSIM_ERR_ARG          1  /* invalid argument (NULL pointer, bad size or option) */
+#define JSIM_ERR_UNSORTED     2  /* a sample's values are not in ascending order */
+#define JSIM_ERR_OVERFLOW     3  /* a set size does not fit count_bits */
+#define JSIM_ERR_ID_RANGE     4  /* a value is >= 2^id_bits */
+#define JSIM_ERR_OOM          5  /* the allocator returned NULL */
+#define JSIM_ERR_CUDA         6  /* a CUDA runtime call failed (see jsim_last_cuda_error) */
+#define JSIM_ERR_TIMEOUT      7  /* a bounded device wait ran out */
+#define JSIM_ERR_CANCELLED    8  /* a request was cancelled */
+#define JSIM_ERR_UNSUPPORTED  9  /* the requested variant or mode is not available */
+
+/* ---- memory kinds ---------------------------------------------------------- */
+#define JSIM_MEM_HOST   0
+#define JSIM_MEM_DEVICE 1
+
+/* ---- product variants (the semiring product of Eq. 7) --------------------- */
+#define JSIM_VARIANT_AUTO 0  /* choose by size and density (measured table) */
+#define JSIM_VARIANT_POPC 1  /* CUDA cores: AND + population count, register tiles */
+#define JSIM_VARIANT_B1   2  /* legacy tensor mma.sync .b1 with .and.popc */
+#define JSIM_VARIANT_I8   3  /* legacy tensor mma.sync .s8, bits unpacked to 0/1 bytes, s32 accumulate */
+#define JSIM_VARIANT_F8   4  /* legacy tensor mma.sync .e4m3, bits unpacked to 0/1.0, f32 accumulate in exact ranges */
+#define JSIM_VARIANT_TC   5  /* tcgen05.mma kind::f8f6f4 with TMEM accumulators, 0/1.0 e4m3 operands */
+#define JSIM_VARIANT_COUNT 6
+
+/*
+ * A collection of n samples in compressed-row form: sample i is
+ * ids[offsets[i] .. offsets[i+1]), sorted ascending.  Equal adjacent values
+ * are one set element (set semantics).  offsets has n+1 entries and
+ * offsets[0] must be 0.  n = 0 is allowed.  ids may be NULL when
+ * offsets[n] = 0.  mem says where offsets and ids live.
+ */
+typedef struct {
+    uint64_t n;
+    const uint64_t* offsets;
+    const uint64_t* ids;
+    int mem;
+} jsim_sets;
+
+/* Device memory hooks.  alloc returns a device pointer of at least `bytes`
+ * bytes, usable in stream order on `stream`, or NULL; free releases it. */
+typedef void* (*jsim_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*jsim_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+typedef struct {
+    uint64_t batch_rows;  /* m~ of Eq. 3: values per row batch, a multiple of 64;
+                             0 = automatic (largest batch whose filter state stays
+                             in L2 and whose packed block fits memory) */
+    int word_bits;        /* b of the bitmask words: 64 (default) or 32 */
+    int variant;          /* JSIM_VARIANT_* for the product */
+    int count_bits;       /* width of C: 32 (default) or 64 */
+    int id_bits;          /* values must be < 2^id_bits; 1..64 (default 64) */
+    jsim_alloc_fn alloc;  /* NULL: cudaMallocAsync on the stream */
+    jsim_free_fn free;    /* NULL: cudaFreeAsync on the stream */
+    void* alloc_user;     /* passed to alloc/free */
+    void* stream;         /* cudaStream_t; NULL = a stream the context creates */
+    int device;           /* CUDA device ordinal */
+    int timeout_ms;       /* bound on device-side waits (persistent kernels, serving) */
+    int profile;          /* 1: record per-stage CUDA-event times into jsim_stats */
+} jsim_options;
+
+typedef struct jsim_ctx jsim_ctx;
+
+/* Statistics of the last jsim_all_pairs / jsim_product call on a context. */
+typedef struct {
+    uint64_t batches;          /* row batches processed (non-empty ones) */
+    uint64_t rows_nonzero;     /* sum over batches of R_l = |f^(l)| (Eq. 5) */
+    uint64_t words;            /* sum over batches of W_l = ceil(R_l / 64) */
+    uint64_t batch_rows;       /* m~ actually used */
+    int variant;               /* product variant actually used */
+    int product_launches;      /* product kernel launches */
+    int launches;              /* all kernel launches of the call */
+    double ms_total;           /* wall time of the call's device work (profile=1) */
+    double ms_h2d, ms_validate, ms_filter, ms_scan, ms_pack, ms_product, ms_epilogue, ms_d2h;
+    double bitops_dense;       /* 64 * sum_l W_l * n(n+1)/2: dense AND+popcount bit-operations */
+} jsim_stats;
+
+/* Fill *opt with the defaults described above. */
+JSIM_API void jsim_default_options(jsim_options* opt);
+
+/* Create a context on opt->device.  Returns JSIM_ERR_ARG for bad options. */
+JSIM_API int jsim_create(jsim_ctx** out, const jsim_options* opt);
+
+/* Destroy a context (waits for its stream).  NULL is ignored. */
+JSIM_API void jsim_destroy(jsim_ctx* ctx);
+
+/*
+ * All-pairs similarity of one collection (Sec. III, Listing 1): C, sizes and
+ * J as defined at the top of this file.
+ *   C     n*n row-major, uint32 (count_bits 32) or uint64 (count_bits 64), or NULL
+ *   sizes n entries, or NULL
+ *   J     n*n row-major binary64, or NULL
+ *   out_mem: JSIM_MEM_HOST or JSIM_MEM_DEVICE for all three outputs.
+ * Errors: JSIM_ERR_ARG, JSIM_ERR_UNSORTED, JSIM_ERR_ID_RANGE, JSIM_ERR_OVERFLOW
+ * (a size >= 2^count_bits), JSIM_ERR_OOM, JSIM_ERR_CUDA, JSIM_ERR_UNSUPPORTED.
+ */
+JSIM_API int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets,
+                   void* C, uint64_t* sizes, double* J, int out_mem);
+
+/*
+ * One row batch of the method, for inspection and step-level testing
+ * (Eq. 5, Eq. 6 and the bitmask compression before Eq. 7): the values of
+ * each sample in [lo, lo + width) become packed words.
+ *   width     a multiple of 64, > 0
+ *   filter    width/64 uint64 words of f^(l) (bit k of word w = row 64w+k), or NULL
+ *   words     n rows of `stride` uint64 words, word r/64 bit r%64 set iff the
+ *             sample holds the value of rank r (rank = p^(l), LSB first);
+ *             words beyond W = ceil(R/64) in a row are zero.  Or NULL.
+ *   stride    row stride of `words` in uint64 units, >= ceil(width/64) or >= W
+ *   R_out     number of nonzero rows R_l (may be NULL)
+ *   sizes     per-sample count of distinct values in the batch (Eq. 4's a-hat^(l)), or NULL
+ * If stride < W, returns JSIM_ERR_ARG with *R_out set, so a caller may ask for
+ * R first with words = NULL.
+ */
+JSIM_API int jsim_pack(jsim_ctx* ctx, const jsim_sets* sets, uint64_t lo, uint64_t width,
+              uint64_t* filter, uint64_t* words, uint64_t stride, uint64_t* R_out,
+              uint64_t* sizes, int out_mem);
+
+/*
+ * The semiring product alone (Eq. 7) on packed words already in device
+ * memory: C[i][j] = sum_{w<W} popcount(words[i][w] AND words[j][w]) for all
+ * i, j (computed on the upper triangle and mirrored).
+ *   words   device, n rows of `stride` uint64 words (stride >= W)
+ *   C       device, n*n uint32 (count_bits 32) or uint64, overwritten
+ *   variant JSIM_VARIANT_*
+ * Errors: JSIM_ERR_ARG, JSIM_ERR_UNSUPPORTED, JSIM_ERR_OOM, JSIM_ERR_CUDA.
+ */
+JSIM_API int jsim_product(jsim_ctx* ctx, const uint64_t* words, uint64_t n, uint64_t W, uint64_t stride,
+                 void* C, int variant);
+
+/* Statistics of the last call on the context. */
+JSIM_API int jsim_get_stats(const jsim_ctx* ctx, jsim_stats* out);
+
+/* Message for an error code. */
+JSIM_API const char* jsim_strerror(int code);
+
+/* The CUDA error string behind the last JSIM_ERR_CUDA on this context. */
+JSIM_API const char* jsim_last_cuda_error(const jsim_ctx* ctx);
+
+/* Library version, e.g. "jsim 0.1". */
+JSIM_API const char* jsim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JSIM_H */

@@ -70,12 +70,23 @@ def bitmask_words(members, lo: int, p, R: int, b: int = 64):
     return words
 
 
+_POP8 = np.array([bin(v).count("1") for v in range(256)], dtype=np.uint8)
+
+
+def popcount(x):
+    """Number of set bits of every element of an unsigned integer array."""
+    x = np.ascontiguousarray(x)
+    if hasattr(np, "bitwise_count"):
+        return np.bitwise_count(x)
+    return _POP8[x.view(np.uint8)].reshape(x.shape + (x.itemsize,)).sum(axis=-1)
+
+
 def popcount_product(words):
     """s^(l)_ij = sum_w popcount(ahat_wi AND ahat_wj) for all pairs (Eq. 7)."""
     n = words.shape[0]
     s = np.zeros((n, n), dtype=np.uint64)
     for i in range(n):
-        s[i, :] = np.bitwise_count(words[i][None, :] & words).sum(axis=1, dtype=np.uint64)
+        s[i, :] = popcount(words[i][None, :] & words).sum(axis=1, dtype=np.uint64)
     return s
 
 

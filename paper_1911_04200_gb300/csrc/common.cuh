@@ -1,0 +1,74 @@
+// Shared declarations of the jsim CUDA library (internal; not installed).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "jsim.h"
+
+namespace jsim {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// Values of one sample per chunk of the ingest kernels (filter, validate, pack).
+constexpr u64 kChunk = 4096;
+// Bitmap words covered by one directory block of the rank scan.
+constexpr u64 kScanBlockWords = 4096;
+// Row granularity of the packed matrix; every product tile is a multiple of it.
+constexpr u64 kRowPad = 128;
+// Word granularity of a packed row (K padding of every product variant).
+constexpr u64 kWordPad = 64;
+
+// Error flags raised by device kernels.
+constexpr u32 kFlagUnsorted = 1u;
+constexpr u32 kFlagIdRange = 2u;
+
+// Per-batch plan of which values of each sample fall in [lo, hi).
+struct Plan {
+    u64* beg;    // [n]   first position of the sample's batch values
+    u64* len;    // [n]   number of them
+    u64* cofs;   // [n+1] exclusive prefix of chunk counts
+    u64* totals; // [4]   total values, total chunks, first value after the batch, whether one exists
+};
+
+// ---- ingest.cu -------------------------------------------------------------
+cudaError_t launch_plan(const u64* offsets, const u64* ids, u64 n, u64 lo, u64 hi, bool full,
+                        Plan plan, cudaStream_t st);
+cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan, u64 max_chunks,
+                            int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, int sms,
+                            cudaStream_t st);
+cudaError_t launch_filter(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
+                          u32* bitmap, int sms, cudaStream_t st);
+cudaError_t launch_scan(const u64* bitmap, u64 nwords, u32* dir, u64* bsum, u64* boff, u64* R,
+                        cudaStream_t st);
+cudaError_t launch_zero_rows(u64* X, u64 rows, u64 stride, u64 words, int sms, cudaStream_t st);
+cudaError_t launch_pack(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
+                        const u64* bitmap, const u32* dir, const u64* boff, u64* X, u64 stride,
+                        u64* batch_sizes, int sms, cudaStream_t st);
+
+// ---- product kernels ---------------------------------------------------------
+// C (n x n, CT = u32 or u64, row-major with row stride ldc) += X X^T on the
+// upper-triangle tiles (both halves of diagonal tiles).  X has rows of
+// `stride` words; words at or beyond W, and rows at or beyond n, read as 0.
+struct ProductArgs {
+    const u64* X;
+    u64 stride;
+    u64 n;
+    u64 W;
+    void* C;
+    u64 ldc;
+    int count_bits;
+    int word_bits;
+    int sms;
+    int launches;   // out: kernel launches made
+};
+cudaError_t product_popc(ProductArgs& a, cudaStream_t st);
+cudaError_t product_mma(ProductArgs& a, int variant, cudaStream_t st);
+cudaError_t product_tc(ProductArgs& a, cudaStream_t st);
+bool product_tc_supported(int device);
+
+// ---- epilogue.cu ---------------------------------------------------------------
+// Cout[i][j] = Cacc[min(i,j)][max(i,j)], J = C / (s_i + s_j - C) (binary64), 1 if 0.
+cudaError_t launch_epilogue(const void* Cacc, u64 n, int count_bits, const u64* sizes,
+                            void* Cout, double* J, cudaStream_t st);
+
+}  // namespace jsim

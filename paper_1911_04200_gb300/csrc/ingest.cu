@@ -1,0 +1,380 @@
+// Ingest kernels: per-batch plan, input validation, the zero-row filter
+// f^(l) (Eq. 5), its prefix sum p^(l) as a rank directory (Eq. 6), and the
+// bitmask compression of the surviving rows into 64-bit words (Sec. III-B).
+#include "common.cuh"
+
+namespace jsim {
+
+namespace {
+
+constexpr int kPlanThreads = 1024;
+constexpr int kIngestThreads = 256;
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = (int)(kScanBlockWords / kScanThreads);  // 16
+
+__device__ __forceinline__ u64 lower_bound_u64(const u64* a, u64 lo, u64 hi, u64 v)
+{
+    while (lo < hi) {
+        u64 mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Block-wide exclusive scan of one u64 per thread; returns the block total.
+template <int NT>
+__device__ __forceinline__ u64 block_exclusive_scan(u64 v, u64& excl, u64* smem /* NT/32 */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u64 x = v;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        u64 y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        u64 w = lane < NT / 32 ? smem[lane] : 0;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            u64 y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NT / 32) smem[lane] = w;
+    }
+    __syncthreads();
+    u64 warp_base = warp ? smem[warp - 1] : 0;
+    u64 total = smem[NT / 32 - 1];
+    excl = warp_base + x - v;
+    __syncthreads();
+    return total;
+}
+
+// One CTA: per-sample [beg, beg+len) of values in [lo, hi) and chunk prefix.
+__global__ void __launch_bounds__(kPlanThreads)
+k_plan(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, u64 lo, u64 hi,
+       int full, Plan plan)
+{
+    __shared__ u64 sm[kPlanThreads / 32];
+    __shared__ u64 s_next;
+    __shared__ int s_has_next;
+    if (threadIdx.x == 0) { s_next = ~0ull; s_has_next = 0; }
+    __syncthreads();
+    u64 carry = 0, total_len = 0;
+    for (u64 base = 0; base < n; base += kPlanThreads) {
+        u64 i = base + threadIdx.x;
+        u64 b = 0, l = 0, nch = 0;
+        if (i < n) {
+            u64 s = offsets[i], e = offsets[i + 1];
+            if (!full) {
+                const u64 se = e;
+                u64 bb = lower_bound_u64(ids, s, e, lo);
+                u64 ee = hi == 0 ? e : lower_bound_u64(ids, bb, e, hi);  // hi==0: unbounded
+                s = bb; e = ee;
+                if (ee < se) {  // first value of this sample after the batch
+                    atomicMin(&s_next, ids[ee]);
+                    s_has_next = 1;
+                }
+            }
+            b = s; l = e - s; nch = (l + kChunk - 1) / kChunk;
+            plan.beg[i] = b;
+            plan.len[i] = l;
+        }
+        u64 ex;
+        u64 tot = block_exclusive_scan<kPlanThreads>(nch, ex, sm);
+        if (i < n) plan.cofs[i] = carry + ex;
+        carry += tot;
+        u64 ex2;
+        total_len += block_exclusive_scan<kPlanThreads>(l, ex2, sm);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        plan.cofs[n] = carry;
+        plan.totals[0] = total_len;
+        plan.totals[1] = carry;
+        plan.totals[2] = s_next;
+        plan.totals[3] = (u64)s_has_next;
+    }
+}
+
+// Chunk c -> sample index (largest i with cofs[i] <= c, among samples with chunks).
+__device__ __forceinline__ u64 chunk_sample(const u64* cofs, u64 n, u64 c)
+{
+    u64 lo = 0, hi = n;  // find last i in [0,n) with cofs[i] <= c
+    while (lo < hi) {
+        u64 mid = lo + ((hi - lo + 1) >> 1);
+        if (cofs[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kIngestThreads)
+k_validate(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, Plan plan,
+           int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid)
+{
+    __shared__ u64 s_i, s_p0, s_p1;
+    __shared__ u32 s_cnt[kIngestThreads / 32];
+    const u64 nch = plan.totals[1];
+    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+        if (threadIdx.x == 0) {
+            u64 i = chunk_sample(plan.cofs, n, c);
+            u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+            u64 p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+            s_i = i; s_p0 = p0; s_p1 = p1;
+        }
+        __syncthreads();
+        const u64 i = s_i, p0 = s_p0, p1 = s_p1;
+        const u64 sb = offsets[i], se = offsets[i + 1];
+        u32 cnt = 0, flags = 0;
+        for (u64 pos = p0 + threadIdx.x; pos < p1; pos += kIngestThreads) {
+            u64 x = ids[pos];
+            if (pos > sb) {
+                u64 prev = ids[pos - 1];
+                if (x < prev) flags |= kFlagUnsorted;
+                cnt += (x != prev);
+            } else {
+                cnt += 1;
+                atomicMin(minid, x);
+            }
+            if (id_bits < 64 && (x >> id_bits) != 0) flags |= kFlagIdRange;
+            if (pos + 1 == se) atomicMax(maxid, x);
+        }
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_cnt[threadIdx.x >> 5] = cnt;
+            if (flags) atomicOr(err, flags);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u32 t = 0;
+            for (int w = 0; w < kIngestThreads / 32; ++w) t += s_cnt[w];
+            atomicAdd(sizes + i, (u64)t);
+        }
+        __syncthreads();
+    }
+}
+
+// Inclusive OR over the lanes that share key q, accumulated toward the
+// segment's first lane (q is non-decreasing across lanes).  Returns true on
+// the lane that must publish the segment's value.
+template <typename T>
+__device__ __forceinline__ bool segmented_or(u64 q, T& v)
+{
+    const int lane = threadIdx.x & 31;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T w = __shfl_down_sync(0xffffffffu, v, o);
+        u64 qq = __shfl_down_sync(0xffffffffu, q, o);
+        if (lane + o < 32 && qq == q) v |= w;
+    }
+    u64 qprev = __shfl_up_sync(0xffffffffu, q, 1);
+    return lane == 0 || qprev != q;
+}
+
+// f^(l): set bit (x - lo) for every value x of the batch (Eq. 5).
+__global__ void __launch_bounds__(kIngestThreads)
+k_filter(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, u32* bitmap)
+{
+    __shared__ u64 s_p0, s_p1;
+    const u64 nch = plan.totals[1];
+    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+        if (threadIdx.x == 0) {
+            u64 i = chunk_sample(plan.cofs, n, c);
+            u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+            s_p0 = p0;
+            s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+        }
+        __syncthreads();
+        const u64 p0 = s_p0, p1 = s_p1;
+        // every warp walks whole 32-position groups so shuffles see full warps
+        for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
+            u64 pos = base + (threadIdx.x & 31);
+            u64 q = ~0ull;
+            u32 bit = 0;
+            if (pos < p1) {
+                u64 d = ids[pos] - lo;
+                if (d < width) { q = d >> 5; bit = 1u << (d & 31); }
+            }
+            bool lead = segmented_or<u32>(q, bit);
+            if (lead && bit) atomicOr(bitmap + q, bit);
+        }
+        __syncthreads();
+    }
+}
+
+// Directory pass 1: per 4096-word block, block-relative exclusive popcounts.
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_blocks(const u64* __restrict__ bitmap, u64 nwords, u32* __restrict__ dir, u64* __restrict__ bsum)
+{
+    __shared__ u64 sm[kScanThreads / 32];
+    const u64 w0 = (u64)blockIdx.x * kScanBlockWords + (u64)threadIdx.x * kScanPerThread;
+    u32 pc[kScanPerThread];
+    u32 mine = 0;
+    #pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) {
+        u64 w = w0 + k;
+        pc[k] = w < nwords ? __popcll(bitmap[w]) : 0u;
+        mine += pc[k];
+    }
+    u64 ex;
+    u64 tot = block_exclusive_scan<kScanThreads>((u64)mine, ex, sm);
+    u32 run = (u32)ex;
+    #pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) {
+        u64 w = w0 + k;
+        if (w < nwords) dir[w] = run;
+        run += pc[k];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// Directory pass 2 (one CTA): exclusive prefix of block sums; R = total.
+__global__ void __launch_bounds__(1024)
+k_scan_top(const u64* __restrict__ bsum, u64 nb, u64* __restrict__ boff, u64* R)
+{
+    __shared__ u64 sm[32];
+    u64 carry = 0;
+    for (u64 base = 0; base < nb; base += 1024) {
+        u64 b = base + threadIdx.x;
+        u64 v = b < nb ? bsum[b] : 0, ex;
+        u64 tot = block_exclusive_scan<1024>(v, ex, sm);
+        if (b < nb) boff[b] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *R = carry;
+}
+
+__global__ void k_zero_rows(u64* X, u64 rows, u64 stride, u64 words)
+{
+    const u64 per_row = words;
+    const u64 total = rows * per_row;
+    for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (u64)gridDim.x * blockDim.x) {
+        u64 r = t / per_row, w = t - r * per_row;
+        X[r * stride + w] = 0ull;
+    }
+}
+
+// Bitmask compression: value x of sample i -> rank r = p^(l)_{x-lo}; word
+// r/64, bit r%64 of row i (Eq. 6 and the b-bit masks before Eq. 7).
+__global__ void __launch_bounds__(kIngestThreads)
+k_pack(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
+       const u64* __restrict__ bitmap, const u32* __restrict__ dir, const u64* __restrict__ boff,
+       u64* X, u64 stride, u64* batch_sizes)
+{
+    __shared__ u64 s_i, s_p0, s_p1, s_b;
+    __shared__ u32 s_cnt[kIngestThreads / 32];
+    const u64 nch = plan.totals[1];
+    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+        if (threadIdx.x == 0) {
+            u64 i = chunk_sample(plan.cofs, n, c);
+            u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+            s_i = i; s_p0 = p0; s_b = plan.beg[i];
+            s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+        }
+        __syncthreads();
+        const u64 i = s_i, p0 = s_p0, p1 = s_p1, bb = s_b;
+        u64* row = X + i * stride;
+        u32 cnt = 0;
+        for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
+            u64 pos = base + (threadIdx.x & 31);
+            u64 q = ~0ull, bit = 0;
+            if (pos < p1) {
+                u64 x = ids[pos];
+                u64 d = x - lo;
+                if (d < width) {
+                    u64 w = d >> 6;
+                    u64 below = bitmap[w] & ((1ull << (d & 63)) - 1ull);
+                    u64 r = boff[w / kScanBlockWords] + (u64)dir[w] + (u64)__popcll(below);
+                    q = r >> 6;
+                    bit = 1ull << (r & 63);
+                }
+                if (batch_sizes) cnt += (pos == bb) || (ids[pos - 1] != x);
+            }
+            bool lead = segmented_or<u64>(q, bit);
+            if (lead && bit) atomicOr(row + q, bit);
+        }
+        if (batch_sizes) {
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = cnt;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                u32 t = 0;
+                for (int w = 0; w < kIngestThreads / 32; ++w) t += s_cnt[w];
+                atomicAdd(batch_sizes + i, (u64)t);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+inline unsigned grid_for_chunks(u64 max_chunks, int sms)
+{
+    u64 g = (u64)sms * 8;
+    if (max_chunks < g) g = max_chunks;
+    return (unsigned)(g ? g : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_plan(const u64* offsets, const u64* ids, u64 n, u64 lo, u64 hi, bool full,
+                        Plan plan, cudaStream_t st)
+{
+    k_plan<<<1, kPlanThreads, 0, st>>>(offsets, ids, n, lo, hi, full ? 1 : 0, plan);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan, u64 max_chunks,
+                            int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, int sms,
+                            cudaStream_t st)
+{
+    k_validate<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(offsets, ids, n, plan, id_bits,
+                                                                            sizes, err, maxid, minid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
+                          u32* bitmap, int sms, cudaStream_t st)
+{
+    k_filter<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, width, bitmap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const u64* bitmap, u64 nwords, u32* dir, u64* bsum, u64* boff, u64* R,
+                        cudaStream_t st)
+{
+    u64 nb = (nwords + kScanBlockWords - 1) / kScanBlockWords;
+    if (nb == 0) nb = 1;
+    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(bitmap, nwords, dir, bsum);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_scan_top<<<1, 1024, 0, st>>>(bsum, nb, boff, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_rows(u64* X, u64 rows, u64 stride, u64 words, int sms, cudaStream_t st)
+{
+    if (rows == 0 || words == 0) return cudaSuccess;
+    u64 total = rows * words;
+    u64 g = (total + 255) / 256;
+    u64 cap = (u64)sms * 16;
+    if (g > cap) g = cap;
+    k_zero_rows<<<(unsigned)g, 256, 0, st>>>(X, rows, stride, words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
+                        const u64* bitmap, const u32* dir, const u64* boff, u64* X, u64 stride,
+                        u64* batch_sizes, int sms, cudaStream_t st)
+{
+    k_pack<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, width, bitmap, dir,
+                                                                        boff, X, stride, batch_sizes);
+    return cudaGetLastError();
+}
+
+}  // namespace jsim

@@ -1,0 +1,284 @@
+"""Thin ctypes binding of the jsim C-ABI (include/jsim.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch supplies device memory (its caching allocator, through the
+library's allocator hooks) and the CUDA stream.  There is no CPU fallback:
+if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build_native
+
+JSIM_OK = 0
+ERRORS = {1: "JSIM_ERR_ARG", 2: "JSIM_ERR_UNSORTED", 3: "JSIM_ERR_OVERFLOW", 4: "JSIM_ERR_ID_RANGE",
+          5: "JSIM_ERR_OOM", 6: "JSIM_ERR_CUDA", 7: "JSIM_ERR_TIMEOUT", 8: "JSIM_ERR_CANCELLED",
+          9: "JSIM_ERR_UNSUPPORTED"}
+MEM_HOST, MEM_DEVICE = 0, 1
+VARIANTS = {"auto": 0, "popc": 1, "b1": 2, "i8": 3, "f8": 4, "tc": 5}
+VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class JsimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+        self.name = ERRORS.get(code, "?")
+
+
+class Sets(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("offsets", ctypes.c_void_p), ("ids", ctypes.c_void_p),
+                ("mem", ctypes.c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("batch_rows", ctypes.c_uint64), ("word_bits", ctypes.c_int), ("variant", ctypes.c_int),
+                ("count_bits", ctypes.c_int), ("id_bits", ctypes.c_int), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+                ("device", ctypes.c_int), ("timeout_ms", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_uint64), ("rows_nonzero", ctypes.c_uint64), ("words", ctypes.c_uint64),
+                ("batch_rows", ctypes.c_uint64), ("variant", ctypes.c_int), ("product_launches", ctypes.c_int),
+                ("launches", ctypes.c_int), ("ms_total", ctypes.c_double), ("ms_h2d", ctypes.c_double),
+                ("ms_validate", ctypes.c_double), ("ms_filter", ctypes.c_double), ("ms_scan", ctypes.c_double),
+                ("ms_pack", ctypes.c_double), ("ms_product", ctypes.c_double), ("ms_epilogue", ctypes.c_double),
+                ("ms_d2h", ctypes.c_double), ("bitops_dense", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["variant"] = VARIANT_NAMES.get(d["variant"], d["variant"])
+        return d
+
+
+# Every C-ABI entry point declared in include/jsim.h, with its ctypes signature.
+SIGNATURES = {
+    "jsim_default_options": (None, [ctypes.POINTER(Options)]),
+    "jsim_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Options)]),
+    "jsim_destroy": (None, [ctypes.c_void_p]),
+    "jsim_all_pairs": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int]),
+    "jsim_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_uint64, ctypes.c_uint64,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, _u64p, ctypes.c_void_p,
+                                 ctypes.c_int]),
+    "jsim_product": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                    ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]),
+    "jsim_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
+    "jsim_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "jsim_last_cuda_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "jsim_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return build_native.LIB
+
+
+def load(build: bool = True):
+    """Load libjsim.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build_native.build() if build else build_native.LIB
+            if not os.path.exists(path):
+                raise RuntimeError("libjsim.so is not built: %s" % path)
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, ctx_ptr=None):
+    if rc != JSIM_OK:
+        lib = load()
+        msg = lib.jsim_strerror(rc).decode()
+        if rc == 6 and ctx_ptr:
+            msg += ": " + lib.jsim_last_cuda_error(ctx_ptr).decode()
+        raise JsimError(rc, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """A jsim context on one CUDA device.
+
+    Device memory comes from PyTorch's caching allocator and work runs on the
+    given torch stream (default: the device's current stream).
+    """
+
+    def __init__(self, device: int = 0, variant: str | int = "auto", batch_rows: int = 0, word_bits: int = 64,
+                 count_bits: int = 32, id_bits: int = 64, profile: bool = False, stream=None,
+                 use_torch_allocator: bool = True, timeout_ms: int = 2000):
+        torch = _torch()
+        self._lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        o = Options()
+        self._lib.jsim_default_options(ctypes.byref(o))
+        o.batch_rows = batch_rows
+        o.word_bits = word_bits
+        o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        o.count_bits = count_bits
+        o.id_bits = id_bits
+        o.device = device
+        o.profile = 1 if profile else 0
+        o.timeout_ms = timeout_ms
+        o.stream = ctypes.c_void_p(stream.cuda_stream)
+        self._keep = []
+        if use_torch_allocator:
+            dev = device
+
+            def _alloc(nbytes, st, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(st or 0))
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, st, user):
+                if ptr:
+                    torch.cuda.caching_allocator_delete(int(ptr))
+
+            a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+            self._keep += [a, f]
+            o.alloc, o.free = a, f
+        self.count_bits = count_bits
+        self._opts = o
+        h = ctypes.c_void_p()
+        _check(self._lib.jsim_create(ctypes.byref(h), ctypes.byref(o)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.jsim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers -----------------------------------------------------------------
+    @staticmethod
+    def _ptr(x):
+        if x is None:
+            return None
+        if isinstance(x, np.ndarray):
+            return x.ctypes.data
+        return x.data_ptr()
+
+    def _sets(self, offsets, ids):
+        torch = _torch()
+        is_dev = isinstance(offsets, torch.Tensor) and offsets.is_cuda
+        if is_dev:
+            assert offsets.dtype == torch.uint64 or offsets.dtype == torch.int64
+            assert offsets.is_contiguous() and ids.is_contiguous()
+            n = offsets.numel() - 1
+        else:
+            offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+            ids = np.ascontiguousarray(ids, dtype=np.uint64)
+            n = offsets.size - 1
+        s = Sets()
+        s.n = n
+        s.offsets = self._ptr(offsets)
+        s.ids = self._ptr(ids) if (ids is not None and (ids.numel() if is_dev else ids.size)) else None
+        s.mem = MEM_DEVICE if is_dev else MEM_HOST
+        return s, (offsets, ids), is_dev
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(self._lib.jsim_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    # -- entry points --------------------------------------------------------------
+    def all_pairs(self, offsets, ids, want_C=True, want_J=True, want_sizes=True, out_device=None, out=None):
+        """C (n x n), sizes (n), J (n x n) of one collection.
+
+        Host inputs (numpy) give numpy outputs unless out_device=True; CUDA
+        tensors give CUDA tensor outputs.  ``out`` may pass preallocated
+        (C, sizes, J) buffers of the right kind.
+        """
+        torch = _torch()
+        s, keep, is_dev = self._sets(offsets, ids)
+        n = s.n
+        dev_out = is_dev if out_device is None else out_device
+        cdt_np = np.uint64 if self.count_bits == 64 else np.uint32
+        cdt_t = torch.uint64 if self.count_bits == 64 else torch.uint32
+        if out is not None:
+            C, sizes, J = out
+        elif dev_out:
+            d = torch.device("cuda", self.device)
+            C = torch.empty((n, n), dtype=cdt_t, device=d) if want_C else None
+            sizes = torch.empty(n, dtype=torch.uint64, device=d) if want_sizes else None
+            J = torch.empty((n, n), dtype=torch.float64, device=d) if want_J else None
+        else:
+            C = np.empty((n, n), dtype=cdt_np) if want_C else None
+            sizes = np.empty(n, dtype=np.uint64) if want_sizes else None
+            J = np.empty((n, n), dtype=np.float64) if want_J else None
+        rc = self._lib.jsim_all_pairs(self._h, ctypes.byref(s), self._ptr(C), self._ptr(sizes), self._ptr(J),
+                                      MEM_DEVICE if dev_out else MEM_HOST)
+        _check(rc, self._h)
+        return C, sizes, J
+
+    def pack(self, offsets, ids, lo: int, width: int, want_filter=True, want_words=True, want_sizes=True,
+             stride: int | None = None):
+        """One row batch: (filter words, packed words [n, stride], R, per-batch sizes) on the host."""
+        s, keep, is_dev = self._sets(offsets, ids)
+        n = s.n
+        R = ctypes.c_uint64(0)
+        # ask for R first
+        rc = self._lib.jsim_pack(self._h, ctypes.byref(s), lo, width, None, None, 0, ctypes.byref(R), None,
+                                 MEM_HOST)
+        _check(rc, self._h)
+        W = (R.value + 63) // 64
+        if stride is None:
+            stride = max(W, 1)
+        filt = np.empty(width // 64, dtype=np.uint64) if want_filter else None
+        words = np.empty((n, stride), dtype=np.uint64) if want_words else None
+        sz = np.empty(n, dtype=np.uint64) if want_sizes else None
+        rc = self._lib.jsim_pack(self._h, ctypes.byref(s), lo, width, self._ptr(filt), self._ptr(words), stride,
+                                 ctypes.byref(R), self._ptr(sz), MEM_HOST)
+        _check(rc, self._h)
+        return filt, words, R.value, sz
+
+    def product(self, words, n: int, W: int, stride: int, C=None, variant: str | int = "auto"):
+        """C = X X^T over (AND, popcount, +) of device-resident packed words."""
+        torch = _torch()
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        if C is None:
+            C = torch.empty((n, n), dtype=torch.uint64 if self.count_bits == 64 else torch.uint32,
+                            device=torch.device("cuda", self.device))
+        rc = self._lib.jsim_product(self._h, self._ptr(words), n, W, stride, self._ptr(C), v)
+        _check(rc, self._h)
+        return C
+
+
+def version() -> str:
+    return load().jsim_version().decode()

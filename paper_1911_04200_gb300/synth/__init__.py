@@ -67,6 +67,8 @@ def _load():
             lib.synth_fill.restype = None
             lib.synth_compact.argtypes = [ctypes.c_uint64, u64p, u64p, u64p, u64p]
             lib.synth_compact.restype = ctypes.c_uint64
+            lib.synth_range_distinct.argtypes = [ctypes.c_uint64, u64p, ctypes.c_int, ctypes.c_uint64, u64p]
+            lib.synth_range_distinct.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -174,3 +176,15 @@ def serving_queries(first: int, count: int, seed: int = SEED_BASE + 5, n_ref: in
     return generate("clade", n=count, id_bits=32, seed=seed, sample_base=n_ref + first, n_clades=64,
                     core=0.3, u_max=0.4, median=median, sigma=SIGMA_DECADE,
                     lo=median / 10, hi=median * 10)
+
+
+def range_distinct(ids, range_bits: int, nranges: int):
+    """Distinct values of a whole collection per aligned range of 2^range_bits
+    values (a workload statistic: with batches of that size, batch r has
+    counts[r] nonzero rows and ceil(counts[r] / 64) packed words per sample)."""
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    counts = np.zeros(nranges, dtype=np.uint64)
+    rc = _load().synth_range_distinct(ids.size, _ptr(ids), range_bits, nranges, _ptr(counts))
+    if rc != 0:
+        raise ValueError("range_distinct failed (%d)" % rc)
+    return counts

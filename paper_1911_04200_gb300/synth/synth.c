@@ -30,6 +30,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static inline uint64_t mix64(uint64_t z)
 {
@@ -251,4 +254,46 @@ uint64_t synth_compact(uint64_t n, const uint64_t* slot, const uint64_t* distinc
     }
     offsets[n] = o;
     return o;
+}
+
+/*
+ * Workload statistics (not part of any result): number of distinct values of
+ * the whole collection inside each aligned range [r * 2^range_bits,
+ * (r+1) * 2^range_bits) for r < nranges, written to counts[r].  Used only to
+ * state how much dense packed work a batch plan implies.  Values must be
+ * below nranges * 2^range_bits.  One bit per value of the domain is set in a
+ * scratch bitmap (domain_bits <= 36), partitioned by range across threads.
+ */
+int synth_range_distinct(uint64_t n_values, const uint64_t* ids, int range_bits, uint64_t nranges,
+                         uint64_t* counts)
+{
+    uint64_t domain = nranges << range_bits;
+    if (range_bits < 6 || domain == 0 || domain > (1ull << 36)) return -1;
+    uint64_t nw = domain / 64;
+    uint64_t* bm = (uint64_t*)calloc(nw, sizeof(uint64_t));
+    if (!bm) return -2;
+    int bad = 0;
+    #pragma omp parallel
+    {
+        /* every thread owns a contiguous stripe of the bitmap words */
+        int nt = 1, t = 0;
+#ifdef _OPENMP
+        nt = omp_get_num_threads(); t = omp_get_thread_num();
+#endif
+        uint64_t w0 = nw * (uint64_t)t / (uint64_t)nt, w1 = nw * (uint64_t)(t + 1) / (uint64_t)nt;
+        for (uint64_t k = 0; k < n_values; ++k) {
+            uint64_t x = ids[k];
+            if (x >= domain) { bad = 1; continue; }
+            uint64_t w = x >> 6;
+            if (w >= w0 && w < w1) bm[w] |= 1ull << (x & 63);
+        }
+    }
+    uint64_t per = (1ull << range_bits) / 64;
+    for (uint64_t r = 0; r < nranges; ++r) {
+        uint64_t c = 0;
+        for (uint64_t w = r * per; w < (r + 1) * per; ++w) c += (uint64_t)__builtin_popcountll(bm[w]);
+        counts[r] = c;
+    }
+    free(bm);
+    return bad ? -3 : 0;
 }

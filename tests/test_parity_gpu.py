@@ -1,0 +1,175 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracles.
+
+C, |X_i| and the filter/rank/packed words are integers and must match
+bit for bit; J is the correctly rounded binary64 quotient of the same
+integers, so it must match bit for bit as well (tolerance 0).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import packed
+from paper_1911_04200_gb300 import jsim, synth
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["popc"]
+
+
+def collection(segs):
+    offsets = np.zeros(len(segs) + 1, dtype=np.uint64)
+    offsets[1:] = np.cumsum([len(s) for s in segs])
+    ids = np.concatenate([np.asarray(s, dtype=np.uint64) for s in segs]) if segs else np.zeros(0, np.uint64)
+    return offsets, ids.astype(np.uint64)
+
+
+def to_np(t):
+    """torch CUDA/CPU tensor or ndarray -> ndarray (unsigned views kept)."""
+    import torch
+    if isinstance(t, np.ndarray):
+        return t
+    m = {torch.uint64: (torch.int64, np.uint64), torch.uint32: (torch.int32, np.uint32)}
+    if t.dtype in m:
+        sdt, ndt = m[t.dtype]
+        return t.view(sdt).cpu().numpy().view(ndt)
+    return t.cpu().numpy()
+
+
+def assert_same(res, ref):
+    C, sizes, J = res
+    Co, so, Jo = ref
+    np.testing.assert_array_equal(np.asarray(sizes, dtype=np.uint64), so)
+    np.testing.assert_array_equal(np.asarray(C).astype(np.uint64), Co)
+    # bit-exact binary64
+    np.testing.assert_array_equal(np.asarray(J).view(np.uint64), Jo.view(np.uint64))
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return synth.ancestral64()
+
+
+@pytest.fixture(scope="module")
+def c1_ref(c1):
+    return oracle.all_pairs(*c1)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_ancestral64_host_io(gpu, c1, c1_ref, variant):
+    with jsim.Context(variant=variant) as ctx:
+        assert_same(ctx.all_pairs(*c1), c1_ref)
+        assert ctx.stats()["variant"] == variant
+
+
+@pytest.mark.parametrize("batch_rows", [1 << 12, 1 << 16, 3 << 14, 1 << 20, 1 << 26])
+def test_ancestral64_batch_invariance(gpu, c1, c1_ref, batch_rows):
+    """Eq. 4: any row-batch size gives the same C (several batches, a ragged last one)."""
+    with jsim.Context(batch_rows=batch_rows) as ctx:
+        assert_same(ctx.all_pairs(*c1), c1_ref)
+        st = ctx.stats()
+        assert st["batch_rows"] == batch_rows
+        assert (st["batches"] > 1) == (batch_rows < 2**20)
+
+
+@pytest.mark.parametrize("count_bits,word_bits", [(64, 64), (32, 32), (64, 32)])
+def test_ancestral64_widths(gpu, c1, c1_ref, count_bits, word_bits):
+    with jsim.Context(count_bits=count_bits, word_bits=word_bits) as ctx:
+        assert_same(ctx.all_pairs(*c1), c1_ref)
+
+
+def test_ancestral64_device_io(gpu, c1, c1_ref):
+    import torch
+    off = torch.from_numpy(c1[0].view(np.int64)).cuda()
+    ids = torch.from_numpy(c1[1].view(np.int64)).cuda()
+    with jsim.Context() as ctx:
+        C, s, J = ctx.all_pairs(off, ids)
+        torch.cuda.synchronize()
+        res = (to_np(C), to_np(s), to_np(J))
+    assert_same(res, c1_ref)
+
+
+@pytest.mark.parametrize("n,median", [(130, 2e4), (1, 5e4), (257, 3e3)])
+def test_clade_recipe_scaled(gpu, n, median):
+    """The 1024-sample clade recipe at sizes the oracle finishes in seconds
+    (ragged n spans several tiles and a partial one)."""
+    off, ids = synth.clade1024(n=n, median=median)
+    ref = oracle.all_pairs(off, ids)
+    for v in VARIANTS:
+        with jsim.Context(variant=v) as ctx:
+            assert_same(ctx.all_pairs(off, ids), ref)
+
+
+def test_edge_cases(gpu):
+    segs = [[], [], [0], [0, 2**64 - 1], [5, 5, 5, 7], list(range(1000, 1300)), [2**63, 2**63 + 1],
+            [2**64 - 1]]
+    off, ids = collection(segs)
+    ref = oracle.all_pairs(off, ids)
+    with jsim.Context() as ctx:
+        assert_same(ctx.all_pairs(off, ids), ref)
+    # all empty
+    off, ids = collection([[], [], []])
+    with jsim.Context() as ctx:
+        C, s, J = ctx.all_pairs(off, ids)
+    assert np.all(C == 0) and np.all(s == 0) and np.all(J == 1.0)
+    # n = 0
+    with jsim.Context() as ctx:
+        C, s, J = ctx.all_pairs(np.zeros(1, np.uint64), np.zeros(0, np.uint64))
+    assert C.shape == (0, 0)
+
+
+def test_errors(gpu):
+    with jsim.Context() as ctx:
+        off, ids = collection([[1, 2, 3], [4, 3]])
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs(off, ids)
+        assert e.value.name == "JSIM_ERR_UNSORTED"
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs(np.array([1, 3], np.uint64), np.array([1, 2, 3], np.uint64))
+        assert e.value.name == "JSIM_ERR_ARG"
+    with jsim.Context(id_bits=20) as ctx:
+        off, ids = collection([[1, 2**20], [4]])
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs(off, ids)
+        assert e.value.name == "JSIM_ERR_ID_RANGE"
+        # the context is still usable after an error
+        off, ids = collection([[1, 2], [2, 3]])
+        C, s, J = ctx.all_pairs(off, ids)
+        assert C[0, 1] == 1 and J[0, 1] == 1 / 3
+
+
+@pytest.mark.parametrize("lo,width", [(0, 1 << 20), (1 << 18, 1 << 16), (123 * 64, 64 * 1000)])
+def test_pack_matches_packed_oracle(gpu, c1, lo, width):
+    """Filter (Eq. 5), ranks (Eq. 6) and bitmask words against the step-by-step model."""
+    off, ids = c1
+    sub_off = off[:9]
+    sub_ids = ids[:int(off[8])]
+    ref = packed.run_batch(sub_off, sub_ids, lo, width, 64)
+    with jsim.Context() as ctx:
+        filt, words, R, sz = ctx.pack(sub_off, sub_ids, lo, width)
+    assert R == ref["R"]
+    fbits = np.unpackbits(filt.view(np.uint8), bitorder="little").astype(bool)
+    np.testing.assert_array_equal(fbits, ref["f"])
+    np.testing.assert_array_equal(words[:, :ref["words"].shape[1]], ref["words"])
+    np.testing.assert_array_equal(sz, ref["ahat"])
+
+
+def popcount_product_ref(X, W):
+    return packed.popcount_product(np.ascontiguousarray(X[:, :W]))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n,W,density", [(1, 1, 0.5), (64, 64, 0.5), (65, 70, 0.05), (130, 300, 1.0),
+                                         (300, 129, 0.3), (200, 1000, 0.01), (128, 4096, 1.0)])
+def test_product_random_bits(gpu, variant, n, W, density):
+    """The semiring product alone (Eq. 7) on random packed words, all-ones included."""
+    import torch
+    rng = np.random.default_rng(n * 1000 + W)
+    stride = W + 3
+    bits = rng.random((n, stride * 64)) < density
+    X = np.packbits(bits, axis=1, bitorder="little").view(np.uint64).copy()
+    ref = popcount_product_ref(X, W)
+    with jsim.Context(count_bits=64) as ctx:
+        Xd = torch.from_numpy(X.view(np.int64)).cuda()
+        C = ctx.product(Xd, n, W, stride, variant=variant)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(to_np(C), ref)
