@@ -132,7 +132,7 @@ class Context:
         self._lib = load()
         self.device = device
         if stream is None:
-            stream = torch.cuda.current_stream(device)
+            stream = torch.cuda.Stream(device)
         self.stream = stream
         o = Options()
         self._lib.jsim_default_options(ctypes.byref(o))
@@ -212,6 +212,13 @@ class Context:
         s.mem = MEM_DEVICE if is_dev else MEM_HOST
         return s, (offsets, ids), is_dev
 
+    def _order(self):
+        """The library's stream waits for work already queued on torch's current stream."""
+        torch = _torch()
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+
     def stats(self) -> dict:
         st = Stats()
         _check(self._lib.jsim_get_stats(self._h, ctypes.byref(st)))
@@ -242,6 +249,7 @@ class Context:
             C = np.empty((n, n), dtype=cdt_np) if want_C else None
             sizes = np.empty(n, dtype=np.uint64) if want_sizes else None
             J = np.empty((n, n), dtype=np.float64) if want_J else None
+        self._order()
         rc = self._lib.jsim_all_pairs(self._h, ctypes.byref(s), self._ptr(C), self._ptr(sizes), self._ptr(J),
                                       MEM_DEVICE if dev_out else MEM_HOST)
         _check(rc, self._h)
@@ -254,6 +262,7 @@ class Context:
         n = s.n
         R = ctypes.c_uint64(0)
         # ask for R first
+        self._order()
         rc = self._lib.jsim_pack(self._h, ctypes.byref(s), lo, width, None, None, 0, ctypes.byref(R), None,
                                  MEM_HOST)
         _check(rc, self._h)
@@ -275,6 +284,7 @@ class Context:
         if C is None:
             C = torch.empty((n, n), dtype=torch.uint64 if self.count_bits == 64 else torch.uint32,
                             device=torch.device("cuda", self.device))
+        self._order()
         rc = self._lib.jsim_product(self._h, self._ptr(words), n, W, stride, self._ptr(C), v)
         _check(rc, self._h)
         return C
