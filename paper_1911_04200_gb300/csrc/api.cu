@@ -291,6 +291,9 @@ int run_product(jsim_ctx* ctx, int variant, const u64* X, u64 stride, u64 n, u64
     cudaError_t e = cudaSuccess;
     switch (variant) {
     case JSIM_VARIANT_POPC: e = product_popc(a, ctx->stream); break;
+    case JSIM_VARIANT_B1:
+    case JSIM_VARIANT_I8:
+    case JSIM_VARIANT_F8: e = product_mma(a, variant, ctx->stream); break;
     default: return JSIM_ERR_UNSUPPORTED;
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "product");

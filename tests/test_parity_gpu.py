@@ -13,7 +13,7 @@ from paper_1911_04200_gb300 import jsim, synth
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ["popc"]
+VARIANTS = ["popc", "b1", "i8", "f8"]
 
 
 def collection(segs):
@@ -173,3 +173,28 @@ def test_product_random_bits(gpu, variant, n, W, density):
         C = ctx.product(Xd, n, W, stride, variant=variant)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(to_np(C), ref)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_product_all_ones_long(gpu, variant):
+    """Adversarial exactness: all-ones rows over 2^23 bit-rows (every count is
+    8388608; f32 accumulation must stay exact, so slices are capped)."""
+    import torch
+    n, W = 130, 1 << 17
+    Xd = torch.full((n, W), -1, dtype=torch.int64, device="cuda")
+    with jsim.Context(count_bits=64) as ctx:
+        C = ctx.product(Xd, n, W, W, variant=variant)
+        torch.cuda.synchronize()
+    assert np.all(to_np(C) == W * 64)
+
+
+@pytest.mark.parametrize("variant", VARIANTS[1:])
+def test_variants_agree_on_clade_batches(gpu, variant):
+    """All product variants give byte-identical C, sizes and J on the clade recipe."""
+    off, ids = synth.clade1024(n=200, median=5e4)
+    with jsim.Context(variant="popc", batch_rows=1 << 28) as ctx:
+        ref = ctx.all_pairs(off, ids)
+    with jsim.Context(variant=variant, batch_rows=1 << 28) as ctx:
+        out = ctx.all_pairs(off, ids)
+    for a, b in zip(out, ref):
+        np.testing.assert_array_equal(a.view(np.uint8), b.view(np.uint8))
