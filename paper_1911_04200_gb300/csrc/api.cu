@@ -21,6 +21,8 @@ struct jsim_ctx {
     char cuda_err[256];
     // small pinned host scratch for device -> host scalars
     unsigned long long* h_scalars;
+    // device error word of kernels with bounded waits
+    unsigned int* d_err;
     // stage timing (profile = 1): events recorded on the stream, resolved at
     // the end of each call, so timing adds no host synchronisation
     std::vector<cudaEvent_t> events;
@@ -288,8 +290,14 @@ int run_product(jsim_ctx* ctx, int variant, const u64* X, u64 stride, u64 n, u64
     ProductArgs a{};
     a.X = X; a.stride = stride; a.n = n; a.W = W; a.C = C; a.ldc = n;
     a.count_bits = ctx->opt.count_bits; a.word_bits = ctx->opt.word_bits; a.sms = ctx->sms;
+    a.timeout_ms = ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000;
+    a.err = ctx->d_err;
     cudaError_t e = cudaSuccess;
     switch (variant) {
+    case JSIM_VARIANT_TC:
+        if (!product_tc_supported(ctx->opt.device)) return JSIM_ERR_UNSUPPORTED;
+        e = product_tc(a, ctx->stream);
+        break;
     case JSIM_VARIANT_POPC: e = product_popc(a, ctx->stream); break;
     case JSIM_VARIANT_B1:
     case JSIM_VARIANT_I8:
@@ -404,6 +412,12 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
         }
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_scalars, 64 * sizeof(u64));
+    if (e == cudaSuccess) {
+        c->d_err = (unsigned int*)o.alloc(256, (void*)c->stream, o.alloc_user);
+        if (!c->d_err) e = cudaErrorMemoryAllocation;
+        else e = cudaMemsetAsync(c->d_err, 0, 256, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -417,6 +431,8 @@ void jsim_destroy(jsim_ctx* ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->opt.device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->d_err) ctx->opt.free(ctx->d_err, 256, (void*)ctx->stream, ctx->opt.alloc_user);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);

@@ -59,7 +59,9 @@ struct ProductArgs {
     int count_bits;
     int word_bits;
     int sms;
-    int launches;   // out: kernel launches made
+    int timeout_ms;  // bound on device-side waits
+    u32* err;        // device error word (bit 4: a bounded wait timed out)
+    int launches;    // out: kernel launches made
 };
 cudaError_t product_popc(ProductArgs& a, cudaStream_t st);
 cudaError_t product_mma(ProductArgs& a, int variant, cudaStream_t st);
