@@ -35,11 +35,15 @@ constexpr int kN = 256;                 // B-side rows per tile
 constexpr int kStageBits = 256;         // bit-rows per stage
 constexpr int kStageWords = kStageBits / 64;
 constexpr int kBlkBytes = 128;          // one swizzle atom row
-constexpr int kABytes = kM * kStageBits / 8;   // 32 KiB (two 16 KiB column blocks)
-constexpr int kBBytes = kN * kStageBits / 8;   // 64 KiB (two 32 KiB column blocks)
+// one byte per bit-row after unpacking
+constexpr int kABytes = kM * kStageBits;       // 32 KiB (two 16 KiB column blocks)
+constexpr int kBBytes = kN * kStageBits;       // 64 KiB (two 32 KiB column blocks)
 constexpr int kStageBytes = kABytes + kBBytes; // 96 KiB
+static_assert(kABytes == (kStageBits / 128) * kM * kBlkBytes, "A stage = column blocks x rows x 128 B");
+static_assert(kBBytes == (kStageBits / 128) * kN * kBlkBytes, "B stage = column blocks x rows x 128 B");
 constexpr int kStages = 2;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
+static_assert(kSmemBytes <= 232448, "fits the per-CTA shared-memory limit");
 constexpr int kTmemCols = 256;
 constexpr u64 kMaxSliceBits = 1ull << 22;
 constexpr u32 kErrTimeout = 4u;
@@ -139,7 +143,7 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u32 kspli
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                     :: "r"(smem_u32(&tmem_slot)), "r"(kTmemCols));
+                     :: "r"(smem_u32(&tmem_slot)), "r"(kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
