@@ -12,7 +12,7 @@
 // A CTA owns a 128 x 256 tile of C (128 rows of the A side, 256 of the B
 // side, both taken from X) that touches the upper triangle, and a slice of the
 // word range.  One stage covers 256 bit-rows: the packed words are loaded
-// with plain 8-byte loads (prefetched one stage ahead in registers), expanded
+// with plain 8-byte loads (prefetched two stages ahead in registers), expanded
 // to bytes by all 256 threads and stored into shared memory in the canonical
 // K-major 128-byte-swizzle layout (8-row x 128-byte atoms, 16-byte chunk c of
 // row r at c ^ (r % 8)), two 128-byte column blocks per operand.  After a
@@ -155,8 +155,9 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u32 kspli
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const u32 tmem = tmem_slot;
 
-    // this thread's three (row, 128-bit block) items of every stage
-    u64 cur[3][2], nxt[3][2];
+    // this thread's three (row, 128-bit block) items of every stage, loaded
+    // two stages ahead
+    u64 cur[3][2], nxt[3][2], nxt2[3][2];
     auto load = [&](u64 s, u64 (&v)[3][2]) {
         const u64 k0 = s * kStageWords;
         #pragma unroll
@@ -197,9 +198,10 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u32 kspli
 
     bool ok = true;
     load(s_begin, cur);
+    if (s_begin + 1 < s_end) load(s_begin + 1, nxt);
     for (u64 s = s_begin; s < s_end; ++s) {
         const int b = (int)((s - s_begin) & 1);
-        if (s + 1 < s_end) load(s + 1, nxt);
+        if (s + 2 < s_end) load(s + 2, nxt2);
         // buffer b was last read by the MMAs of stage s - 2
         if (s - s_begin >= 2) {
             u32 parity = (u32)(((s - s_begin) / 2 - 1) & 1);
@@ -226,7 +228,10 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u32 kspli
                          :: "r"(smem_u32(&bars[b])) : "memory");
         }
         #pragma unroll
-        for (int e = 0; e < 3; ++e) { cur[e][0] = nxt[e][0]; cur[e][1] = nxt[e][1]; }
+        for (int e = 0; e < 3; ++e) {
+            cur[e][0] = nxt[e][0]; cur[e][1] = nxt[e][1];
+            nxt[e][0] = nxt2[e][0]; nxt[e][1] = nxt2[e][1];
+        }
     }
 
     // wait for every committed stage (the last commit on each buffer)
