@@ -4,24 +4,36 @@
 //
 // Every bit of a packed word becomes one e4m3 byte, 0x00 (0.0) or 0x38
 // (1.0); a product of two such values is 0 or 1, and the tensor core sums
-// them into FP32 accumulators held in tensor memory (TMEM).  A CTA's slice of
-// the word range is capped at 2^22 bit-rows, so every accumulator is an
-// integer below 2^24 and FP32 holds it exactly.  The epilogue converts to
-// integers and adds them into C.
+// them into FP32 accumulators held in tensor memory (TMEM).  A segment of
+// work accumulates at most 2^22 bit-rows, so every accumulator is an integer
+// below 2^24, which FP32 holds exactly; the epilogue converts to integers and
+// adds them into C.
 //
-// A CTA owns a 128 x 256 tile of C (128 rows of the A side, 256 of the B
-// side, both taken from X) that touches the upper triangle, and a slice of the
-// word range.  One stage covers 256 bit-rows: the packed words are loaded
-// with plain 8-byte loads (prefetched two stages ahead in registers), expanded
-// to bytes by all 256 threads and stored into shared memory in the canonical
-// K-major 128-byte-swizzle layout (8-row x 128-byte atoms, 16-byte chunk c of
-// row r at c ^ (r % 8)), two 128-byte column blocks per operand.  After a
-// proxy fence and a CTA barrier one thread issues 8 tcgen05.mma
-// (M=128, N=256, K=32 each) and commits them to the stage buffer's mbarrier;
-// the buffer is refilled once that barrier reports the tensor core done with
-// it.  Two stage buffers of 96 KiB alternate.  Every mbarrier wait is bounded
-// (clock64 budget); on time-out the CTA raises an error flag, waits (bounded)
-// for its committed MMAs, frees its TMEM and leaves.
+// Work: the tiles of C are 128 x 256 (128 rows on the A side, 256 on the B
+// side, both read from X) that touch the upper triangle; each tile's word
+// range is cut into stages of 128 bit-rows.  The (tile, stage) units are laid
+// out tile-major and one persistent CTA per SM takes an equal contiguous
+// share, split into segments at tile boundaries and at the exactness cap.
+//
+// Roles inside a CTA (17 warps):
+//   warps 0-11  unpack: thread p owns row p of every stage (rows 0-127 A,
+//               128-383 B); it keeps its packed words four stages ahead in
+//               registers, waits until the tensor core has released the
+//               stage buffer, writes its 128-byte row in the canonical
+//               K-major 128-byte-swizzle layout (16-byte chunk c of row r at
+//               c ^ (r % 8)), fences the generic-to-async proxy and arrives
+//               on the buffer's `full` barrier;
+//   warp 12     one lane issues 4 tcgen05.mma (M=128, N=256, K=32) per stage
+//               into one of two TMEM accumulators and commits them to the
+//               buffer's `empty` barrier, and each finished segment to the
+//               accumulator's `acc_full` barrier;
+//   warps 13-16 epilogue: wait for `acc_full`, read the accumulator with
+//               tcgen05.ld (each warp its 32 TMEM lanes), add it into C and
+//               release it through `acc_empty`.
+// Four 48 KiB stage buffers; two 256-column accumulators, so the epilogue of
+// one segment overlaps the MMAs of the next.  Every wait is bounded (clock64
+// budget, plus a CTA-wide abort flag); on time-out the CTA raises the error
+// word, waits (bounded) for its issued MMAs, frees its TMEM and leaves.
 #include <algorithm>
 #include "common.cuh"
 
@@ -29,23 +41,27 @@ namespace jsim {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kM = 128;                 // A-side rows per tile
-constexpr int kN = 256;                 // B-side rows per tile
-constexpr int kStageBits = 256;         // bit-rows per stage
+constexpr int kProducerWarps = 12;
+constexpr int kMmaWarp = 12;
+constexpr int kEpiWarp0 = 13;
+constexpr int kWarps = 17;
+constexpr int kThreads = kWarps * 32;          // 544
+constexpr int kM = 128;                        // A-side rows per tile
+constexpr int kN = 256;                        // B-side rows per tile
+constexpr int kRows = kM + kN;                 // rows unpacked per stage (one per producer thread)
+static_assert(kRows == kProducerWarps * 32, "one row per producer thread");
+static_assert(kEpiWarp0 % 4 == 1, "epilogue warp e reads TMEM lanes of warp rank (kEpiWarp0 + e) % 4");
+constexpr int kStageBits = 128;                // bit-rows per stage = one 128-byte swizzle atom row
 constexpr int kStageWords = kStageBits / 64;
-constexpr int kBlkBytes = 128;          // one swizzle atom row
-// one byte per bit-row after unpacking
-constexpr int kABytes = kM * kStageBits;       // 32 KiB (two 16 KiB column blocks)
-constexpr int kBBytes = kN * kStageBits;       // 64 KiB (two 32 KiB column blocks)
-constexpr int kStageBytes = kABytes + kBBytes; // 96 KiB
-static_assert(kABytes == (kStageBits / 128) * kM * kBlkBytes, "A stage = column blocks x rows x 128 B");
-static_assert(kBBytes == (kStageBits / 128) * kN * kBlkBytes, "B stage = column blocks x rows x 128 B");
-constexpr int kStages = 2;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
+constexpr int kBlkBytes = 128;
+constexpr int kABytes = kM * kBlkBytes;        // 16 KiB
+constexpr int kStageBytes = kRows * kBlkBytes; // 48 KiB
+constexpr int kBufs = 4;
+constexpr int kAhead = 4;                      // stages of packed words held in registers
+constexpr int kSmemBytes = kBufs * kStageBytes + 1024;  // + alignment slack
 static_assert(kSmemBytes <= 232448, "fits the per-CTA shared-memory limit");
-constexpr int kTmemCols = 256;
-constexpr u64 kMaxSliceBits = 1ull << 22;
+constexpr int kTmemCols = 512;                 // two 256-column FP32 accumulators
+constexpr u64 kMaxSegStages = (1ull << 22) / kStageBits;
 constexpr u32 kErrTimeout = 4u;
 
 // instruction descriptor: kind::f8f6f4, D = F32, A = B = E4M3, both K-major,
@@ -65,7 +81,13 @@ __device__ __forceinline__ u64 sw128_desc(u32 saddr)
 
 __device__ __forceinline__ void mbar_init(u64* bar, u32 count)
 {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(bar)), "r"(count));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(u64* bar)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" :: "r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity)
@@ -76,12 +98,17 @@ __device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity)
     return ok != 0;
 }
 
-// bounded wait: true when the phase completed, false on time-out
-__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity, long long budget)
+// Bounded wait for the phase of `parity`; false on time-out or when another
+// role has already aborted the CTA.
+__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity, long long budget, volatile int* abort_flag)
 {
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > budget) return false;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > budget) {
+            *abort_flag = 1;
+            return false;
+        }
     }
     return true;
 }
@@ -104,9 +131,9 @@ __device__ __forceinline__ void tmem_ld32(u32 taddr, u32 (&r)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-// tile t -> (ti, tj) over 128 x 256 tiles with rows [128 ti, +128) and
-// columns [256 tj, +256) that hold at least one pair i <= j (ti <= 2 tj + 1)
-__device__ __forceinline__ void tc_tile(u64 t, u64 TM, u64& ti, u64& tj)
+// tile t -> first row and column over 128 x 256 tiles with rows [128 ti, +128)
+// and columns [256 tj, +256) that hold at least one pair i <= j (ti <= 2 tj + 1)
+__device__ __forceinline__ void tc_tile(u64 t, u64 TM, u64& r0, u64& c0)
 {
     u64 j = 0;
     for (;;) {
@@ -115,28 +142,42 @@ __device__ __forceinline__ void tc_tile(u64 t, u64 TM, u64& ti, u64& tj)
         t -= cnt;
         ++j;
     }
-    ti = t;
-    tj = j;
+    r0 = t * kM;
+    c0 = j * kN;
+}
+
+// The CTA's work: units [w0, w1) of the tile-major (tile, stage) order.
+struct Work {
+    u64 w0, w1, nst;
+};
+
+// segment starting at unit w: its tile, first stage and stage count
+__device__ __forceinline__ void next_segment(const Work& wk, u64 w, u64& tile, u64& kst, u64& len)
+{
+    tile = w / wk.nst;
+    kst = w - tile * wk.nst;
+    u64 end = min(wk.w1, (tile + 1) * wk.nst);
+    len = min(end - w, kMaxSegStages);
 }
 
 template <typename CT>
 __global__ void __launch_bounds__(kThreads, 1)
-k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u32 ksplit, CT* __restrict__ C, u64 ldc,
+k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total, CT* __restrict__ C, u64 ldc,
           u32* err, long long budget)
 {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) u64 bars[kStages];
+    __shared__ __align__(8) u64 full_bar[kBufs], empty_bar[kBufs], accf_bar[2], acce_bar[2], done_bar;
     __shared__ u32 tmem_slot;
+    __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    u64 ti, tj;
-    tc_tile(blockIdx.x, TM, ti, tj);
-    const u64 r0 = ti * kM, c0 = tj * kN;
     const u64 nst = (W + kStageWords - 1) / kStageWords;
-    const u64 s_begin = nst * blockIdx.y / ksplit, s_end = nst * (blockIdx.y + 1) / ksplit;
-    if (s_begin >= s_end) return;  // uniform per CTA, before any TMEM or barrier use
+    Work wk;
+    wk.nst = nst;
+    wk.w0 = total * blockIdx.x / gridDim.x;
+    wk.w1 = total * (blockIdx.x + 1) / gridDim.x;
+    if (wk.w0 >= wk.w1) return;  // uniform per CTA, before any TMEM or barrier use
 
-    // 1024-aligned operand area
     const u32 raw = smem_u32(smem_raw);
     const u32 base = (raw + 1023u) & ~1023u;
     unsigned char* sm = smem_raw + (base - raw);
@@ -144,48 +185,61 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u32 kspli
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
                      :: "r"(smem_u32(&tmem_slot)), "r"(kTmemCols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    if (tid == 0) {
-        for (int b = 0; b < kStages; ++b) mbar_init(&bars[b], 1);
+    if (tid == 32) {
+        for (int b = 0; b < kBufs; ++b) {
+            mbar_init(&full_bar[b], kRows);
+            mbar_init(&empty_bar[b], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf_bar[a], 1);
+            mbar_init(&acce_bar[a], 4 * 32);
+        }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const u32 tmem = tmem_slot;
+    volatile int* abort_v = &abort_flag;
 
-    // this thread's three (row, 128-bit block) items of every stage, loaded
-    // two stages ahead
-    u64 cur[3][2], nxt[3][2], nxt2[3][2];
-    auto load = [&](u64 s, u64 (&v)[3][2]) {
-        const u64 k0 = s * kStageWords;
+    if (warp < kProducerWarps) {
+        // ---------------- unpack producers ----------------
+        const int p = tid;  // row of every stage this thread writes
+        const bool is_a = p < kM;
+        const int row = is_a ? p : p - kM;
+        const u32 row_off = (u32)((is_a ? 0 : kABytes) + row * kBlkBytes);
+        u64 ring[kAhead][2];
+        u64 lt = ~0ull, lr0 = 0, lc0 = 0;  // tile of the last lookup
+        // packed words of unit t of this CTA for this thread's row (0 outside)
+        auto fetch = [&](u64 t, u64 (&v)[2]) {
+            v[0] = v[1] = 0ull;
+            u64 w = wk.w0 + t;
+            if (w >= wk.w1) return;
+            u64 tile = w / nst, kst = w - tile * nst;
+            if (tile != lt) { tc_tile(tile, TM, lr0, lc0); lt = tile; }
+            u64 grow = is_a ? lr0 + row : lc0 + row;
+            if (grow >= n) return;
+            u64 gk = kst * kStageWords;
+            const u64* src = X + grow * stride + gk;
+            if (gk < W) v[0] = __ldg(src);
+            if (gk + 1 < W) v[1] = __ldg(src + 1);
+        };
         #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            int idx = tid + kThreads * e;
-            int ra = idx >> 1, blk = idx & 1;
-            u64 grow = ra < kM ? r0 + ra : c0 + (ra - kM);
-            u64 gk = k0 + 2 * blk;
-            const u64* p = X + grow * stride + gk;
-            bool rowok = grow < n;
-            v[e][0] = (rowok && gk < W) ? __ldg(p) : 0ull;
-            v[e][1] = (rowok && gk + 1 < W) ? __ldg(p + 1) : 0ull;
-        }
-    };
-    auto unpack = [&](int b, const u64 (&v)[3][2]) {
-        unsigned char* sbuf = sm + b * kStageBytes;
-        #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            int idx = tid + kThreads * e;
-            int ra = idx >> 1, blk = idx & 1;
-            unsigned char* opbase;
-            int row;
-            if (ra < kM) { opbase = sbuf + blk * (kM * kBlkBytes); row = ra; }
-            else { opbase = sbuf + kABytes + blk * (kN * kBlkBytes); row = ra - kM; }
-            unsigned char* rowp = opbase + row * kBlkBytes;
+        for (int a = 0; a < kAhead; ++a) fetch((u64)a, ring[a]);
+        const u64 T = wk.w1 - wk.w0;
+        for (u64 t = 0; t < T; ++t) {
+            const int b = (int)(t % kBufs);
+            if (t >= kBufs) {
+                if (!mbar_wait(&empty_bar[b], (u32)((t / kBufs - 1) & 1), budget, abort_v)) break;
+            }
+            unsigned char* rowp = sm + b * kStageBytes + row_off;
             #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                u32 h = (u32)(v[e][c >> 2] >> (16 * (c & 3)));
+                u32 h = (u32)(ring[0][c >> 2] >> (16 * (c & 3)));
                 uint4 o;
                 o.x = expand4(h & 15u);
                 o.y = expand4((h >> 4) & 15u);
@@ -193,84 +247,105 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u32 kspli
                 o.w = expand4((h >> 12) & 15u);
                 *(uint4*)(rowp + ((c ^ (row & 7)) << 4)) = o;
             }
-        }
-    };
-
-    bool ok = true;
-    load(s_begin, cur);
-    if (s_begin + 1 < s_end) load(s_begin + 1, nxt);
-    for (u64 s = s_begin; s < s_end; ++s) {
-        const int b = (int)((s - s_begin) & 1);
-        if (s + 2 < s_end) load(s + 2, nxt2);
-        // buffer b was last read by the MMAs of stage s - 2
-        if (s - s_begin >= 2) {
-            u32 parity = (u32)(((s - s_begin) / 2 - 1) & 1);
-            if (!mbar_wait(&bars[b], parity, budget)) ok = false;
-        }
-        if (__syncthreads_and(ok) == 0) { ok = false; break; }
-        unpack(b, cur);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const u32 abase = base + b * kStageBytes, bbase = abase + kABytes;
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_arrive(&full_bar[b]);
             #pragma unroll
-            for (int k = 0; k < kStageBits / 32; ++k) {
-                const int blk = k >> 2, off = (k & 3) * 32;
-                u64 da = sw128_desc(abase + blk * (kM * kBlkBytes) + off);
-                u64 db = sw128_desc(bbase + blk * (kN * kBlkBytes) + off);
-                u32 acc = (s > s_begin || k > 0) ? 1u : 0u;
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
-                             :: "r"(tmem), "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+            for (int a = 0; a + 1 < kAhead; ++a) { ring[a][0] = ring[a + 1][0]; ring[a][1] = ring[a + 1][1]; }
+            fetch(t + kAhead, ring[kAhead - 1]);
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            u64 t = 0, g = 0;
+            bool ok = true;
+            for (u64 w = wk.w0; w < wk.w1 && ok; ++g) {
+                u64 tile, kst, len;
+                next_segment(wk, w, tile, kst, len);
+                const u32 acc = (u32)(g & 1);
+                if (g >= 2 && !mbar_wait(&acce_bar[acc], (u32)((g / 2 - 1) & 1), budget, abort_v)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const u32 dt = tmem + acc * 256u;
+                for (u64 q = 0; q < len; ++q, ++t) {
+                    const int b = (int)(t % kBufs);
+                    if (!mbar_wait(&full_bar[b], (u32)((t / kBufs) & 1), budget, abort_v)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const u32 abase = base + b * kStageBytes, bbase = abase + kABytes;
+                    #pragma unroll
+                    for (int k = 0; k < kStageBits / 32; ++k) {
+                        u64 da = sw128_desc(abase + k * 32);
+                        u64 db = sw128_desc(bbase + k * 32);
+                        u32 accum = (q > 0 || k > 0) ? 1u : 0u;
+                        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+                                     :: "r"(dt), "l"(da), "l"(db), "r"(kIdesc), "r"(accum) : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                                 :: "r"(smem_u32(&empty_bar[b])) : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                             :: "r"(smem_u32(&accf_bar[acc])) : "memory");
+                w += len;
             }
+            // every MMA this thread issued completes before this arrival
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                         :: "r"(smem_u32(&bars[b])) : "memory");
+                         :: "r"(smem_u32(&done_bar)) : "memory");
         }
-        #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            cur[e][0] = nxt[e][0]; cur[e][1] = nxt[e][1];
-            nxt[e][0] = nxt2[e][0]; nxt[e][1] = nxt2[e][1];
-        }
-    }
-
-    // wait for every committed stage (the last commit on each buffer)
-    const u64 ns = s_end - s_begin;
-    for (int b = 0; b < kStages; ++b) {
-        if ((u64)b >= ns) continue;
-        // the last stage that used buffer b is its (last / 2)-th commit; the
-        // barrier has completed either last / 2 or last / 2 + 1 phases, so
-        // the parity of that phase tells which
-        u64 last = ((ns - 1 - b) / 2) * 2 + b;
-        u32 parity = (u32)((last / 2) & 1);
-        if (!mbar_wait(&bars[b], parity, budget)) ok = false;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const bool all_ok = __syncthreads_and(ok) != 0;
-
-    if (all_ok && warp < 4) {
-        // TMEM lane = tile row, column = tile column
-        const u64 i = r0 + warp * 32 + lane;
-        #pragma unroll 1
-        for (int cb = 0; cb < kN / 32; ++cb) {
-            u32 r[32];
-            tmem_ld32(tmem + ((u32)(warp * 32) << 16) + (u32)(cb * 32), r);
-            if (i < n) {
-                #pragma unroll
-                for (int x = 0; x < 32; ++x) {
-                    u64 j = c0 + cb * 32 + x;
-                    u32 v = (u32)__uint_as_float(r[x]);
-                    if (j < n && i <= j && v) atomicAdd(C + i * ldc + j, (CT)v);
+        __syncwarp();
+    } else {
+        // ---------------- epilogue ----------------
+        const int e = (warp - kEpiWarp0 + 1) & 3;  // TMEM lane quarter of this warp (warp % 4)
+        u64 g = 0;
+        for (u64 w = wk.w0; w < wk.w1; ++g) {
+            u64 tile, kst, len;
+            next_segment(wk, w, tile, kst, len);
+            const u32 acc = (u32)(g & 1);
+            // one lane waits and the warp follows its verdict, so the
+            // warp-collective tcgen05.ld below never runs diverged
+            int got = 0;
+            if (lane == 0) got = mbar_wait(&accf_bar[acc], (u32)((g / 2) & 1), budget, abort_v) ? 1 : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            u64 r0, c0;
+            tc_tile(tile, TM, r0, c0);
+            const u64 i = r0 + (u64)(e * 32 + lane);
+            #pragma unroll 1
+            for (int cb = 0; cb < kN / 32; ++cb) {
+                u32 r[32];
+                tmem_ld32(tmem + ((u32)(e * 32) << 16) + acc * 256u + (u32)(cb * 32), r);
+                if (i < n) {
+                    #pragma unroll
+                    for (int x = 0; x < 32; ++x) {
+                        u64 j = c0 + cb * 32 + x;
+                        u32 v = (u32)__uint_as_float(r[x]);
+                        if (j < n && i <= j && v) atomicAdd(C + i * ldc + j, (CT)v);
+                    }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(&acce_bar[acc]);
+            w += len;
         }
     }
-    if (!all_ok && tid == 0) atomicOr(err, kErrTimeout);
+
+    // wait (bounded) until every issued MMA has completed, then free TMEM
+    if (warp == 0) {
+        long long t0 = clock64();
+        while (!mbar_try_wait(&done_bar, 0u)) {
+            if (clock64() - t0 > budget) { *abort_v = 1; break; }
+        }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
+    if (tid == 0 && *abort_v) atomicOr(err, kErrTimeout);
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(kTmemCols)
+                     : "memory");
     }
 }
 
@@ -281,23 +356,16 @@ cudaError_t run(ProductArgs& a, cudaStream_t st)
     u64 tiles = 0;
     for (u64 j = 0; j < TN; ++j) tiles += std::min<u64>(TM, 2 * j + 2);
     const u64 nst = (a.W + kStageWords - 1) / kStageWords;
-    if (tiles == 0 || nst == 0) return cudaSuccess;
-    u64 want = (u64)a.sms;  // one wave of one CTA per SM
-    u64 ks = (want + tiles - 1) / tiles;
-    u64 min_ks = (nst * (u64)kStageBits + kMaxSliceBits - 1) / kMaxSliceBits;
-    if (ks < min_ks) ks = min_ks;
-    u64 maxks = (nst + 3) / 4;  // at least 4 stages per CTA
-    if (ks > maxks && maxks >= min_ks) ks = maxks;
-    if (ks < 1) ks = 1;
-    if (ks > 65535 || tiles > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+    const u64 total = tiles * nst;
+    if (total == 0) return cudaSuccess;
+    const u64 grid = std::min<u64>((u64)a.sms, total);
     cudaError_t e = cudaFuncSetAttribute(k_prod_tc<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     int clk_khz = 0;
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, 0);
     long long budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * (long long)a.timeout_ms / 1000LL;
-    dim3 grid((unsigned)tiles, (unsigned)ks);
-    k_prod_tc<CT><<<grid, kThreads, kSmemBytes, st>>>(a.X, a.stride, a.n, a.W, TM, (u32)ks, (CT*)a.C, a.ldc,
-                                                      a.err, budget);
+    k_prod_tc<CT><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(a.X, a.stride, a.n, a.W, TM, total, (CT*)a.C, a.ldc,
+                                                                a.err, budget);
     a.launches += 1;
     return cudaGetLastError();
 }
