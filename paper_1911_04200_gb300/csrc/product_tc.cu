@@ -213,45 +213,59 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
         const int row = is_a ? p : p - kM;
         const u32 row_off = (u32)((is_a ? 0 : kABytes) + row * kBlkBytes);
         u64 ring[kAhead][2];
-        u64 lt = ~0ull, lr0 = 0, lc0 = 0;  // tile of the last lookup
-        // packed words of unit t of this CTA for this thread's row (0 outside)
-        auto fetch = [&](u64 t, u64 (&v)[2]) {
+        // position of the next fetch: tile, stage within the tile, and the
+        // tile's first row and column (advanced without division)
+        u64 f_tile = wk.w0 / nst, f_kst = wk.w0 - (wk.w0 / nst) * nst, f_r0, f_c0, f_left = wk.w1 - wk.w0;
+        tc_tile(f_tile, TM, f_r0, f_c0);
+        // packed words of this thread's row at the next fetch position (0 outside)
+        auto fetch = [&](u64 (&v)[2]) {
             v[0] = v[1] = 0ull;
-            u64 w = wk.w0 + t;
-            if (w >= wk.w1) return;
-            u64 tile = w / nst, kst = w - tile * nst;
-            if (tile != lt) { tc_tile(tile, TM, lr0, lc0); lt = tile; }
-            u64 grow = is_a ? lr0 + row : lc0 + row;
-            if (grow >= n) return;
-            u64 gk = kst * kStageWords;
-            const u64* src = X + grow * stride + gk;
-            if (gk < W) v[0] = __ldg(src);
-            if (gk + 1 < W) v[1] = __ldg(src + 1);
+            if (f_left == 0) return;
+            u64 grow = is_a ? f_r0 + row : f_c0 + row;
+            u64 gk = f_kst * kStageWords;
+            if (grow < n) {
+                const u64* src = X + grow * stride + gk;
+                if (gk < W) v[0] = __ldg(src);
+                if (gk + 1 < W) v[1] = __ldg(src + 1);
+            }
+            --f_left;
+            if (++f_kst == nst) {
+                f_kst = 0;
+                ++f_tile;
+                if (f_left) tc_tile(f_tile, TM, f_r0, f_c0);
+            }
         };
         #pragma unroll
-        for (int a = 0; a < kAhead; ++a) fetch((u64)a, ring[a]);
+        for (int a = 0; a < kAhead; ++a) fetch(ring[a]);
         const u64 T = wk.w1 - wk.w0;
-        for (u64 t = 0; t < T; ++t) {
-            const int b = (int)(t % kBufs);
-            if (t >= kBufs) {
-                if (!mbar_wait(&empty_bar[b], (u32)((t / kBufs - 1) & 1), budget, abort_v)) break;
-            }
-            unsigned char* rowp = sm + b * kStageBytes + row_off;
+        bool ok = true;
+        for (u64 t0 = 0; t0 < T && ok; t0 += kAhead) {
+            // ring slot a holds stage t0 + a; static indices keep the
+            // prefetched words in registers without moves
             #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                u32 h = (u32)(ring[0][c >> 2] >> (16 * (c & 3)));
-                uint4 o;
-                o.x = expand4(h & 15u);
-                o.y = expand4((h >> 4) & 15u);
-                o.z = expand4((h >> 8) & 15u);
-                o.w = expand4((h >> 12) & 15u);
-                *(uint4*)(rowp + ((c ^ (row & 7)) << 4)) = o;
+            for (int a = 0; a < kAhead; ++a) {
+                const u64 t = t0 + a;
+                if (t >= T || !ok) break;
+                const int b = (int)(t % kBufs);
+                if (t >= kBufs && !mbar_wait(&empty_bar[b], (u32)((t / kBufs - 1) & 1), budget, abort_v)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* rowp = sm + b * kStageBytes + row_off;
+                #pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    u32 h = (u32)(ring[a][c >> 2] >> (16 * (c & 3)));
+                    uint4 o;
+                    o.x = expand4(h & 15u);
+                    o.y = expand4((h >> 4) & 15u);
+                    o.z = expand4((h >> 8) & 15u);
+                    o.w = expand4((h >> 12) & 15u);
+                    *(uint4*)(rowp + ((c ^ (row & 7)) << 4)) = o;
+                }
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(&full_bar[b]);
+                fetch(ring[a]);
             }
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            mbar_arrive(&full_bar[b]);
-            #pragma unroll
-            for (int a = 0; a + 1 < kAhead; ++a) { ring[a][0] = ring[a + 1][0]; ring[a][1] = ring[a + 1][1]; }
-            fetch(t + kAhead, ring[kAhead - 1]);
         }
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------
