@@ -21,8 +21,8 @@
 //               registers, waits until the tensor core has released the
 //               stage buffer, writes its 128-byte row in the canonical
 //               K-major 128-byte-swizzle layout (16-byte chunk c of row r at
-//               c ^ (r % 8)), fences the generic-to-async proxy and arrives
-//               on the buffer's `full` barrier;
+//               c ^ (r % 8)), fences the generic-to-async proxy; one lane per
+//               warp then arrives on the buffer's `full` barrier;
 //   warp 12     one lane issues 4 tcgen05.mma (M=128, N=256, K=32) per stage
 //               into one of two TMEM accumulators and commits them to the
 //               buffer's `empty` barrier, and each finished segment to the
@@ -189,7 +189,7 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
     }
     if (tid == 32) {
         for (int b = 0; b < kBufs; ++b) {
-            mbar_init(&full_bar[b], kRows);
+            mbar_init(&full_bar[b], kProducerWarps);
             mbar_init(&empty_bar[b], 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -262,8 +262,11 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
                     o.w = expand4((h >> 12) & 15u);
                     *(uint4*)(rowp + ((c ^ (row & 7)) << 4)) = o;
                 }
+                // every writer fences its generic-proxy stores for the async
+                // proxy; the warp converges, and one lane arrives for it
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                mbar_arrive(&full_bar[b]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full_bar[b]);
                 fetch(ring[a]);
             }
         }
