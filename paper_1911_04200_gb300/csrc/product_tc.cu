@@ -2,12 +2,13 @@
 // C += X X^T over (AND, popcount, +) (Eq. 7), computed exactly as an FP8
 // matrix product of 0/1 values.
 //
-// Every bit of a packed word becomes one e4m3 byte, 0x00 (0.0) or 0x38
-// (1.0); a product of two such values is 0 or 1, and the tensor core sums
-// them into FP32 accumulators held in tensor memory (TMEM).  A segment of
-// work accumulates at most 2^22 bit-rows, so every accumulator is an integer
-// below 2^24, which FP32 holds exactly; the epilogue converts to integers and
-// adds them into C.
+// Every bit of a packed word becomes one e4m3 byte, 0x00 (0.0) or 0x08
+// (2^-6, the smallest normal); a product of two such values is 0 or 2^-12,
+// and the tensor core sums them into FP32 accumulators held in tensor memory
+// (TMEM).  A segment of work accumulates at most 2^22 bit-rows, so every
+// accumulator is count * 2^-12 with count < 2^24 - a value FP32 holds
+// exactly, as it holds every partial sum on the way; the epilogue scales by
+// 2^12, converts to integers and adds them into C.
 //
 // Work: the tiles of C are 128 x 256 (128 rows on the A side, 256 on the B
 // side, both read from X) that touch the upper triangle; each tile's word
@@ -113,9 +114,12 @@ __device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity, long long budget
     return true;
 }
 
+// 4 bits -> 4 e4m3 bytes: bit i -> byte i = 0x08 (2^-6) or 0x00.  The
+// multiplier's terms place bit i at 3 + i + 7j; only j = i lands on a byte's
+// bit 3 (3 + 8i), and no two terms share a position, so nothing carries.
 __device__ __forceinline__ u32 expand4(u32 nib)
 {
-    return ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
+    return (nib * 0x01020408u) & 0x08080808u;
 }
 
 __device__ __forceinline__ void tmem_ld32(u32 taddr, u32 (&r)[32])
@@ -146,24 +150,79 @@ __device__ __forceinline__ void tc_tile(u64 t, u64 TM, u64& r0, u64& c0)
     c0 = j * kN;
 }
 
-// The CTA's work: units [w0, w1) of the tile-major (tile, stage) order.
-struct Work {
-    u64 w0, w1, nst;
+// The CTA's work.  The stage range of every tile is cut into chunks of L
+// stages; chunk k's units (tile, stage) are laid out tile-major and CTA c
+// takes the c-th of G equal contiguous shares.  Every CTA therefore walks the
+// chunks in the same order and at the same pace, so at any time all CTAs
+// read the same window of L stages of every row (it stays in L2), and a CTA
+// meets the same one or two tiles in every chunk, so their accumulators
+// persist across chunks.
+struct WorkIter {
+    u64 tiles, nst, L, G, c, KC;
+    u64 k, Lk, u, uend;
+    __device__ __forceinline__ void init(u64 tiles_, u64 nst_, u64 L_, u64 G_, u64 c_)
+    {
+        tiles = tiles_; nst = nst_; L = L_; G = G_; c = c_;
+        KC = (nst + L - 1) / L;
+        k = ~0ull; u = uend = Lk = 0;
+    }
+    // next segment (a run of stages of one tile); false at the end
+    __device__ __forceinline__ bool next(u64& tile, u64& kst, u64& len)
+    {
+        while (u >= uend) {
+            k = (k == ~0ull) ? 0 : k + 1;
+            if (k >= KC) return false;
+            Lk = min(L, nst - k * L);
+            const u64 Uk = tiles * Lk;
+            u = c * Uk / G;
+            uend = (c + 1) * Uk / G;
+        }
+        tile = u / Lk;
+        const u64 s_in = u - tile * Lk;
+        const u64 e = min(uend, (tile + 1) * Lk);
+        len = e - u;
+        kst = k * L + s_in;
+        u = e;
+        return true;
+    }
 };
 
-// segment starting at unit w: its tile, first stage and stage count
-__device__ __forceinline__ void next_segment(const Work& wk, u64 w, u64& tile, u64& kst, u64& len)
-{
-    tile = w / wk.nst;
-    kst = w - tile * wk.nst;
-    u64 end = min(wk.w1, (tile + 1) * wk.nst);
-    len = min(end - w, kMaxSegStages);
-}
+// Accumulator bookkeeping shared (replayed identically) by the MMA warp and
+// the epilogue warps: two TMEM slots tagged with a tile; a segment of a tile
+// already in a slot accumulates there, otherwise a free slot or the less
+// recently used one is taken (flushing it first).  A slot is also flushed
+// before its accumulated stages would pass the exactness cap.
+struct Slots {
+    u64 tile[2];
+    u64 fill[2];
+    u32 flushes[2];
+    int last;
+    __device__ __forceinline__ void init()
+    {
+        tile[0] = tile[1] = ~0ull;
+        fill[0] = fill[1] = 0;
+        flushes[0] = flushes[1] = 0;
+        last = 1;
+    }
+    __device__ __forceinline__ int pick(u64 t) const
+    {
+        if (tile[0] == t) return 0;
+        if (tile[1] == t) return 1;
+        if (tile[0] == ~0ull) return 0;
+        if (tile[1] == ~0ull) return 1;
+        return 1 - last;
+    }
+    // does slot s have to be flushed before a segment of tile t, len stages?
+    __device__ __forceinline__ bool needs_flush(int s, u64 t, u64 len) const
+    {
+        return tile[s] != ~0ull && (tile[s] != t || fill[s] + len > kMaxSegStages);
+    }
+};
 
 template <typename CT>
 __global__ void __launch_bounds__(kThreads, 1)
-k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total, CT* __restrict__ C, u64 ldc,
-          u32* err, long long budget)
+k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 tiles, u64 L, CT* __restrict__ C,
+          u64 ldc, u32* err, long long budget)
 {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) u64 full_bar[kBufs], empty_bar[kBufs], accf_bar[2], acce_bar[2], done_bar;
@@ -172,11 +231,16 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const u64 nst = (W + kStageWords - 1) / kStageWords;
-    Work wk;
-    wk.nst = nst;
-    wk.w0 = total * blockIdx.x / gridDim.x;
-    wk.w1 = total * (blockIdx.x + 1) / gridDim.x;
-    if (wk.w0 >= wk.w1) return;  // uniform per CTA, before any TMEM or barrier use
+    // stages of this CTA (sum of its shares over all chunks)
+    u64 T = 0;
+    {
+        const u64 KC = (nst + L - 1) / L;
+        for (u64 k = 0; k < KC; ++k) {
+            const u64 Uk = tiles * min(L, nst - k * L);
+            T += (blockIdx.x + 1) * Uk / gridDim.x - blockIdx.x * Uk / gridDim.x;
+        }
+    }
+    if (T == 0) return;  // uniform per CTA, before any TMEM or barrier use
 
     const u32 raw = smem_u32(smem_raw);
     const u32 base = (raw + 1023u) & ~1023u;
@@ -213,14 +277,19 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
         const int row = is_a ? p : p - kM;
         const u32 row_off = (u32)((is_a ? 0 : kABytes) + row * kBlkBytes);
         u64 ring[kAhead][2];
-        // position of the next fetch: tile, stage within the tile, and the
-        // tile's first row and column (advanced without division)
-        u64 f_tile = wk.w0 / nst, f_kst = wk.w0 - (wk.w0 / nst) * nst, f_r0, f_c0, f_left = wk.w1 - wk.w0;
-        tc_tile(f_tile, TM, f_r0, f_c0);
-        // packed words of this thread's row at the next fetch position (0 outside)
+        // position of the next fetch: the current segment's tile (first row
+        // and column), stage, and stages left in it
+        WorkIter fit;
+        fit.init(tiles, nst, L, gridDim.x, blockIdx.x);
+        u64 f_tile = ~0ull, f_kst = 0, f_left = 0, f_r0 = 0, f_c0 = 0;
+        // packed words of this thread's row at the next fetch position (0 past the end)
         auto fetch = [&](u64 (&v)[2]) {
             v[0] = v[1] = 0ull;
-            if (f_left == 0) return;
+            if (f_left == 0) {
+                u64 tile;
+                if (!fit.next(tile, f_kst, f_left)) return;
+                if (tile != f_tile) { tc_tile(tile, TM, f_r0, f_c0); f_tile = tile; }
+            }
             u64 grow = is_a ? f_r0 + row : f_c0 + row;
             u64 gk = f_kst * kStageWords;
             if (grow < n) {
@@ -229,15 +298,10 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
                 if (gk + 1 < W) v[1] = __ldg(src + 1);
             }
             --f_left;
-            if (++f_kst == nst) {
-                f_kst = 0;
-                ++f_tile;
-                if (f_left) tc_tile(f_tile, TM, f_r0, f_c0);
-            }
+            ++f_kst;
         };
         #pragma unroll
         for (int a = 0; a < kAhead; ++a) fetch(ring[a]);
-        const u64 T = wk.w1 - wk.w0;
         bool ok = true;
         for (u64 t0 = 0; t0 < T && ok; t0 += kAhead) {
             // ring slot a holds stage t0 + a; static indices keep the
@@ -254,12 +318,14 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
                 unsigned char* rowp = sm + b * kStageBytes + row_off;
                 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    u32 h = (u32)(ring[a][c >> 2] >> (16 * (c & 3)));
+                    // bits 16c .. 16c+15 of the stage row -> 16 bytes
+                    const u32 half = (c & 2) ? (u32)(ring[a][c >> 2] >> 32) : (u32)ring[a][c >> 2];
+                    const int sh = (c & 1) * 16;
                     uint4 o;
-                    o.x = expand4(h & 15u);
-                    o.y = expand4((h >> 4) & 15u);
-                    o.z = expand4((h >> 8) & 15u);
-                    o.w = expand4((h >> 12) & 15u);
+                    o.x = expand4((half >> sh) & 15u);
+                    o.y = expand4((half >> (sh + 4)) & 15u);
+                    o.z = expand4((half >> (sh + 8)) & 15u);
+                    o.w = expand4((half >> (sh + 12)) & 15u);
                     *(uint4*)(rowp + ((c ^ (row & 7)) << 4)) = o;
                 }
                 // every writer fences its generic-proxy stores for the async
@@ -273,18 +339,34 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            u64 t = 0, g = 0;
+            WorkIter it;
+            it.init(tiles, nst, L, gridDim.x, blockIdx.x);
+            Slots sl;
+            sl.init();
+            u64 t = 0, tile, kst, len;
             bool ok = true;
-            for (u64 w = wk.w0; w < wk.w1 && ok; ++g) {
-                u64 tile, kst, len;
-                next_segment(wk, w, tile, kst, len);
-                const u32 acc = (u32)(g & 1);
-                if (g >= 2 && !mbar_wait(&acce_bar[acc], (u32)((g / 2 - 1) & 1), budget, abort_v)) {
-                    ok = false;
-                    break;
+            while (ok && it.next(tile, kst, len)) {
+                const int sidx = sl.pick(tile);
+                if (sl.needs_flush(sidx, tile, len)) {
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                                 :: "r"(smem_u32(&accf_bar[sidx])) : "memory");
+                    sl.flushes[sidx] += 1;
+                    sl.tile[sidx] = ~0ull;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const u32 dt = tmem + acc * 256u;
+                bool fresh = false;
+                if (sl.tile[sidx] == ~0ull) {
+                    // reuse of a flushed slot waits until the epilogue has read it
+                    if (sl.flushes[sidx] > 0 &&
+                        !mbar_wait(&acce_bar[sidx], (sl.flushes[sidx] - 1) & 1u, budget, abort_v)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    sl.tile[sidx] = tile;
+                    sl.fill[sidx] = 0;
+                    fresh = true;
+                }
+                const u32 dt = tmem + (u32)sidx * 256u;
                 for (u64 q = 0; q < len; ++q, ++t) {
                     const int b = (int)(t % kBufs);
                     if (!mbar_wait(&full_bar[b], (u32)((t / kBufs) & 1), budget, abort_v)) { ok = false; break; }
@@ -294,7 +376,7 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
                     for (int k = 0; k < kStageBits / 32; ++k) {
                         u64 da = sw128_desc(abase + k * 32);
                         u64 db = sw128_desc(bbase + k * 32);
-                        u32 accum = (q > 0 || k > 0) ? 1u : 0u;
+                        u32 accum = (fresh && q == 0 && k == 0) ? 0u : 1u;
                         asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
                                      :: "r"(dt), "l"(da), "l"(db), "r"(kIdesc), "r"(accum) : "memory");
@@ -302,10 +384,15 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                                  :: "r"(smem_u32(&empty_bar[b])) : "memory");
                 }
-                if (!ok) break;
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                             :: "r"(smem_u32(&accf_bar[acc])) : "memory");
-                w += len;
+                sl.fill[sidx] += len;
+                sl.last = sidx;
+            }
+            if (ok) {
+                for (int sidx = 0; sidx < 2; ++sidx) {
+                    if (sl.tile[sidx] == ~0ull) continue;
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                                 :: "r"(smem_u32(&accf_bar[sidx])) : "memory");
+                }
             }
             // every MMA this thread issued completes before this arrival
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
@@ -315,17 +402,12 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
     } else {
         // ---------------- epilogue ----------------
         const int e = (warp - kEpiWarp0 + 1) & 3;  // TMEM lane quarter of this warp (warp % 4)
-        u64 g = 0;
-        for (u64 w = wk.w0; w < wk.w1; ++g) {
-            u64 tile, kst, len;
-            next_segment(wk, w, tile, kst, len);
-            const u32 acc = (u32)(g & 1);
-            // one lane waits and the warp follows its verdict, so the
-            // warp-collective tcgen05.ld below never runs diverged
+        // drain slot sidx holding `tile` (its n-th flush); false on abort
+        auto drain = [&](int sidx, u64 tile, u32 nth) -> bool {
             int got = 0;
-            if (lane == 0) got = mbar_wait(&accf_bar[acc], (u32)((g / 2) & 1), budget, abort_v) ? 1 : 0;
-            got = __shfl_sync(0xffffffffu, got, 0);
-            if (!got) break;
+            if (lane == 0) got = mbar_wait(&accf_bar[sidx], nth & 1u, budget, abort_v) ? 1 : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);  // the warp follows one verdict
+            if (!got) return false;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             u64 r0, c0;
             tc_tile(tile, TM, r0, c0);
@@ -333,19 +415,45 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 total
             #pragma unroll 1
             for (int cb = 0; cb < kN / 32; ++cb) {
                 u32 r[32];
-                tmem_ld32(tmem + ((u32)(e * 32) << 16) + acc * 256u + (u32)(cb * 32), r);
+                tmem_ld32(tmem + ((u32)(e * 32) << 16) + (u32)sidx * 256u + (u32)(cb * 32), r);
                 if (i < n) {
                     #pragma unroll
                     for (int x = 0; x < 32; ++x) {
                         u64 j = c0 + cb * 32 + x;
-                        u32 v = (u32)__uint_as_float(r[x]);
+                        // accumulator = count * 2^-12 (operands 2^-6), exact below 2^24 * 2^-12
+                        u32 v = (u32)(__uint_as_float(r[x]) * 4096.0f);
                         if (j < n && i <= j && v) atomicAdd(C + i * ldc + j, (CT)v);
                     }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            mbar_arrive(&acce_bar[acc]);
-            w += len;
+            mbar_arrive(&acce_bar[sidx]);
+            return true;
+        };
+        WorkIter it;
+        it.init(tiles, nst, L, gridDim.x, blockIdx.x);
+        Slots sl;
+        sl.init();
+        u64 tile, kst, len;
+        bool ok = true;
+        while (ok && it.next(tile, kst, len)) {
+            const int sidx = sl.pick(tile);
+            if (sl.needs_flush(sidx, tile, len)) {
+                ok = drain(sidx, sl.tile[sidx], sl.flushes[sidx]);
+                sl.flushes[sidx] += 1;
+                sl.tile[sidx] = ~0ull;
+            }
+            if (sl.tile[sidx] == ~0ull) {
+                sl.tile[sidx] = tile;
+                sl.fill[sidx] = 0;
+            }
+            sl.fill[sidx] += len;
+            sl.last = sidx;
+        }
+        for (int sidx = 0; ok && sidx < 2; ++sidx) {
+            if (sl.tile[sidx] == ~0ull) continue;
+            ok = drain(sidx, sl.tile[sidx], sl.flushes[sidx]);
+            sl.flushes[sidx] += 1;
         }
     }
 
@@ -376,13 +484,17 @@ cudaError_t run(ProductArgs& a, cudaStream_t st)
     const u64 total = tiles * nst;
     if (total == 0) return cudaSuccess;
     const u64 grid = std::min<u64>((u64)a.sms, total);
+    // chunk length: the window of L stages of all n rows (16 bytes per row
+    // per stage) is about 48 MiB, so it stays in L2 while every CTA reads it
+    u64 L = (48ull << 20) / (16ull * std::max<u64>(a.n, 1));
+    L = std::max<u64>(64, std::min<u64>(L, kMaxSegStages));
     cudaError_t e = cudaFuncSetAttribute(k_prod_tc<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     int clk_khz = 0;
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, 0);
     long long budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * (long long)a.timeout_ms / 1000LL;
-    k_prod_tc<CT><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(a.X, a.stride, a.n, a.W, TM, total, (CT*)a.C, a.ldc,
-                                                                a.err, budget);
+    k_prod_tc<CT><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(a.X, a.stride, a.n, a.W, TM, tiles, L, (CT*)a.C,
+                                                                a.ldc, a.err, budget);
     a.launches += 1;
     return cudaGetLastError();
 }
