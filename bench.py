@@ -197,19 +197,17 @@ def cpu_baseline(off, ids, n, bitops_total, seconds):
     threads = oracle.default_threads()
     rng = np.random.default_rng(12345)
     total_pairs = n * (n + 1) // 2
-    # calibrate on a few pairs, then size the sample to about `seconds`
-    k = max(threads, 16)
-    pi = rng.integers(0, n, k).astype(np.uint64)
-    pj = rng.integers(0, n, k).astype(np.uint64)
-    t0 = time.perf_counter()
-    oracle.pairs(off, ids, pi, pj, threads)
-    dt = time.perf_counter() - t0
-    k2 = int(min(total_pairs, max(k, seconds / max(dt / k, 1e-9))))
-    pi = rng.integers(0, n, k2).astype(np.uint64)
-    pj = rng.integers(0, n, k2).astype(np.uint64)
-    t0 = time.perf_counter()
-    oracle.pairs(off, ids, pi, pj, threads)
-    dt = time.perf_counter() - t0
+    # merge random pairs in growing rounds until about `seconds` of work
+    k2, dt, k = 0, 0.0, max(threads, 16)
+    while dt < seconds and k2 < total_pairs:
+        k = int(min(k, total_pairs - k2))
+        pi = rng.integers(0, n, k).astype(np.uint64)
+        pj = rng.integers(0, n, k).astype(np.uint64)
+        t0 = time.perf_counter()
+        oracle.pairs(off, ids, pi, pj, threads)
+        dt += time.perf_counter() - t0
+        k2 += k
+        k *= 2
     value = bitops_total * (k2 / total_pairs) / dt / 1e12
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d random pairs of the %d-sample workload merged in %.1f s; scaled by pairs to the "

@@ -279,14 +279,15 @@ u64 auto_batch_rows(u64 domain)
     return m;
 }
 
-// Variant choice (measured on GB300, 1024 samples: CUDA-core AND+popcount
-// ~128 Tbit-ops/s, legacy mma.sync e4m3/s8/b1 at or below that, tcgen05 FP8
-// ~750): the tensor-core kernel whenever the device has tcgen05; otherwise
-// the CUDA-core kernel.
+// Variant choice (measured on GB300: for 1024 samples the CUDA-core
+// AND+popcount kernel runs ~128 Tbit-ops/s, the legacy mma.sync e4m3/s8/b1
+// kernels at or below that, the tcgen05 FP8 kernel ~700; for 64 samples the
+// CUDA-core kernel wins, 0.33 ms against 0.88 ms per all-pairs call, because
+// one 128 x 256 tensor tile is mostly idle).
 int choose_variant(jsim_ctx* ctx, u64 n, u64 W)
 {
-    (void)n; (void)W;
-    if (product_tc_supported(ctx->opt.device)) return JSIM_VARIANT_TC;
+    (void)W;
+    if (n >= 256 && product_tc_supported(ctx->opt.device)) return JSIM_VARIANT_TC;
     return JSIM_VARIANT_POPC;
 }
 
