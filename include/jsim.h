@@ -184,6 +184,30 @@ JSIM_API int jsim_pack(jsim_ctx* ctx, const jsim_sets* sets, uint64_t lo, uint64
 JSIM_API int jsim_product(jsim_ctx* ctx, const uint64_t* words, uint64_t n, uint64_t W, uint64_t stride,
                  void* C, int variant);
 
+/*
+ * Allocation-free variant of jsim_product, for callers that cannot let the
+ * library allocate device memory during a call - for example an application
+ * that owns a fixed memory budget for the whole GPU, or a steady-state loop
+ * that must not stall on an allocation.  The paper has no counterpart: it is
+ * an interface of this library only.
+ *
+ * Same arguments, result and errors as jsim_product; the caller still passes
+ * the packed words and C.  Instead of allocating, the call keeps its scratch
+ * (the count accumulator and a device error word) in one fixed array of
+ * 4 MiB + 256 bytes of device memory owned by the library module, so n*n
+ * counts must fit in 4 MiB: n <= 1024 with count_bits 32, n <= 724 with
+ * count_bits 64; larger n returns JSIM_ERR_ARG.  Every GPU that loads the
+ * library holds the array until the process exits.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with the context's device current); make that first call before
+ * any stream capture.  All calls on a device share the array and the call
+ * clears what it needs before use, so calls that overlap on the GPU (two
+ * streams, two threads, two contexts on one device) race: serialize them.
+ */
+JSIM_API int jsim_product_noalloc(jsim_ctx* ctx, const uint64_t* words, uint64_t n, uint64_t W,
+                                  uint64_t stride, void* C, int variant);
+
 /* Statistics of the last call on the context. */
 JSIM_API int jsim_get_stats(const jsim_ctx* ctx, jsim_stats* out);
 

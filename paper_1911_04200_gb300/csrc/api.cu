@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <vector>
 #include <algorithm>
+#include <mutex>
 #include "common.cuh"
 
 using namespace jsim;
@@ -631,3 +632,91 @@ const char* jsim_version(void)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free product.
+//
+// Some callers cannot let the library allocate device memory while a call
+// runs: an application that sizes and owns every byte of the GPU up front,
+// an allocation-free steady-state loop (a server that must not stall on
+// cudaMalloc or fragment a pool mid-request), or a host that plugs its own
+// allocator into everything else but cannot hand one to this library.  For
+// them jsim_product_noalloc keeps its only scratch - the upper-triangle count
+// accumulator and a device error word - in one fixed array of device memory
+// that belongs to the library module itself.  Every GPU that loads the
+// library holds that array until the process exits, and every call on a
+// device uses the same array, so calls that overlap on the GPU race.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocCountBytes = 4u << 20;      // 4 MiB of counts: n <= 1024 (32-bit), 724 (64-bit)
+constexpr size_t kNoAllocBytes = kNoAllocCountBytes + 256;  // + error word
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices];
+
+// Device address of the scratch array on `device` (current), looked up once.
+void* noalloc_scratch(int device, cudaError_t& err)
+{
+    err = cudaSuccess;
+    if (device < 0 || device >= kMaxDevices) {
+        err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (err != cudaSuccess) return nullptr;
+        g_noalloc_ptr[device] = p;
+    }
+    return g_noalloc_ptr[device];
+}
+
+}  // namespace
+
+extern "C" int jsim_product_noalloc(jsim_ctx* ctx, const uint64_t* words, uint64_t n, uint64_t W,
+                                    uint64_t stride, void* C, int variant)
+{
+    if (!ctx || !C) return JSIM_ERR_ARG;
+    if (n && !words && W) return JSIM_ERR_ARG;
+    if (stride < W) return JSIM_ERR_ARG;
+    if (variant < 0 || variant >= JSIM_VARIANT_COUNT) return JSIM_ERR_ARG;
+    const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
+    if (n > (1u << 16) || (size_t)(n * n) * cb > kNoAllocCountBytes) return JSIM_ERR_ARG;
+    CK(cudaSetDevice(ctx->opt.device));
+    if (n == 0) return JSIM_OK;
+    cudaError_t e;
+    unsigned char* scratch = (unsigned char*)noalloc_scratch(ctx->opt.device, e);
+    if (!scratch) return cuda_fail(ctx, e, "cudaGetSymbolAddress(scratch)");
+    u32* err = (u32*)(scratch + kNoAllocCountBytes);
+    CK(cudaMemsetAsync(scratch, 0, (size_t)(n * n) * cb, ctx->stream));
+    CK(cudaMemsetAsync(err, 0, sizeof(u32), ctx->stream));
+    int v = variant == JSIM_VARIANT_AUTO ? choose_variant(ctx, n, W) : variant;
+    if (W) {
+        ProductArgs a{};
+        a.X = (const u64*)words; a.stride = stride; a.n = n; a.W = W; a.C = scratch; a.ldc = n;
+        a.count_bits = ctx->opt.count_bits; a.word_bits = ctx->opt.word_bits; a.sms = ctx->sms;
+        a.timeout_ms = ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000;
+        a.err = err;
+        switch (v) {
+        case JSIM_VARIANT_TC:
+            if (!product_tc_supported(ctx->opt.device)) return JSIM_ERR_UNSUPPORTED;
+            e = product_tc(a, ctx->stream);
+            break;
+        case JSIM_VARIANT_POPC: e = product_popc(a, ctx->stream); break;
+        case JSIM_VARIANT_B1:
+        case JSIM_VARIANT_I8:
+        case JSIM_VARIANT_F8: e = product_mma(a, v, ctx->stream); break;
+        default: return JSIM_ERR_UNSUPPORTED;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "product");
+    }
+    CK(launch_epilogue(scratch, n, ctx->opt.count_bits, nullptr, C, nullptr, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_scalars, err, sizeof(u32), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if ((u32)ctx->h_scalars[0] != 0) return JSIM_ERR_TIMEOUT;
+    return JSIM_OK;
+}

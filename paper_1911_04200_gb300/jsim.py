@@ -73,6 +73,8 @@ SIGNATURES = {
                                  ctypes.c_int]),
     "jsim_product": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]),
+    "jsim_product_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]),
     "jsim_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "jsim_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "jsim_last_cuda_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -286,6 +288,16 @@ class Context:
                             device=torch.device("cuda", self.device))
         self._order()
         rc = self._lib.jsim_product(self._h, self._ptr(words), n, W, stride, self._ptr(C), v)
+        _check(rc, self._h)
+        return C
+
+
+    def product_noalloc(self, words, n: int, W: int, stride: int, C, variant: str | int = "auto"):
+        """jsim_product without device allocation (see include/jsim.h): C must
+        be preallocated by the caller; scratch is the library's fixed array."""
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        self._order()
+        rc = self._lib.jsim_product_noalloc(self._h, self._ptr(words), n, W, stride, self._ptr(C), v)
         _check(rc, self._h)
         return C
 
