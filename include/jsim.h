@@ -154,6 +154,30 @@ JSIM_API int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets,
                    void* C, uint64_t* sizes, double* J, int out_mem);
 
 /*
+ * All-pairs similarity of k independent collections in one call (the
+ * batched pattern).  Every collection is processed exactly as by
+ * jsim_all_pairs (its own row batches, filter, prefix sum, words and product;
+ * Sec. III-B, Eq. 3-7) and gets its own outputs:
+ *   cols      k collections (host or device, each with its own mem)
+ *   C, sizes, J   arrays of k pointers (or NULL for none); C[c] is n_c*n_c
+ *             uint32/uint64, sizes[c] n_c, J[c] n_c*n_c binary64; an entry may
+ *             be NULL.  out_mem applies to all of them.
+ * Execution: one validation synchronisation for the whole call; the batches
+ * of every collection are appended along the word axis on the device; the
+ * products of all collections run as one persistent tensor-core launch (up to
+ * 256 collections per launch) or, when the tuner measures it faster, one
+ * CUDA-core launch per collection.  With variant AUTO the first call for a
+ * collection shape times the candidate products and remembers the fastest for
+ * the context.  When every input and output is in device memory the launch
+ * sequence is captured into a CUDA graph and later calls with the same
+ * collections (same pointers and offsets) replay it after re-validating.
+ * Errors: as jsim_all_pairs, plus JSIM_ERR_UNSUPPORTED when a collection's
+ * value span needs more than 4096 row batches.
+ */
+JSIM_API int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint64_t k, void* const* C,
+                                    uint64_t* const* sizes, double* const* J, int out_mem);
+
+/*
  * One row batch of the method, for inspection and step-level testing
  * (Eq. 5, Eq. 6 and the bitmask compression before Eq. 7): the values of
  * each sample in [lo, lo + width) become packed words.

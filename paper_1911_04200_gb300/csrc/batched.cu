@@ -1,0 +1,501 @@
+// Batched all-pairs: many independent collections per call.
+//
+// Each collection is one run of the paper's method (Listing 1): its own row
+// batches, its own zero-row filter and prefix sum (Eq. 5, Eq. 6), its own
+// bitmask words, its own product (Eq. 7, Eq. 4).  What is shared is the
+// execution:
+//   * one validation pass per collection, then a single host
+//     synchronisation for the whole call (errors, value ranges, sizes);
+//   * every row batch of every collection appends its words after the
+//     previous batch's along the word axis of that collection's packed matrix
+//     (a running word offset kept on the device), so no batch needs the host
+//     to learn its nonzero-row count;
+//   * the products of all collections run as one persistent tcgen05 launch
+//     over a table of collections (or, if the tuner prefers, one CUDA-core
+//     launch per collection), reading the word counts from device memory;
+//   * with device-resident inputs and outputs, the whole launch sequence is
+//     captured once into a CUDA graph and replayed by later calls on the same
+//     collections.
+// An autotuner times the candidate products (tcgen05, CUDA-core with 64-bit
+// and 32-bit words) on the first call of a collection shape and keeps the
+// fastest for that shape.
+#include "ctx.cuh"
+
+namespace {
+
+struct Col {
+    u64 n = 0, N = 0;
+    std::vector<u64> hoff;
+    const u64* d_off = nullptr;
+    const u64* d_ids = nullptr;
+    u64 minid = 0, maxid = 0, mt = 0, lo0 = 0, rounds = 0;
+    u64 stride = 0, n_pad = 0, max_chunks = 0;
+    size_t x_off = 0, c_off = 0, s_off = 0, p_off = 0;  // offsets into the pools
+    bool empty = false;
+};
+
+// Everything one wave of collections needs on the device; kept alive by the
+// graph cache so a replay finds the same addresses.
+struct Wave {
+    std::vector<Col> cols;
+    DevBuf xpool, cpool, spool, ppool, scal, ids_pool, off_pool;
+    DevBuf bitmap, dir, bsum, boff, R;
+    DevBuf cstage, jstage;  // host-output staging
+    u64 max_mt = 0;
+    int variant = JSIM_VARIANT_TC;
+    int word_bits = 64;
+    cudaGraphExec_t exec = nullptr;
+    u64 signature = 0;
+    ~Wave()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+u64 mix(u64 h, u64 v)
+{
+    h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+// Launch sequence of one wave after validation: zero, ingest every batch of
+// every collection, product, epilogue.  No host synchronisation inside.
+int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool dev_out, size_t first,
+                 bool run_product_only, int variant, int word_bits)
+{
+    const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
+    cudaStream_t st = ctx->stream;
+    u64* scal = w.scal.as<u64>();  // per collection: ktotal, kbase
+    if (!run_product_only) {
+        CK(cudaMemsetAsync(w.xpool.p, 0, w.xpool.bytes, st));
+        CK(cudaMemsetAsync(scal, 0, w.cols.size() * 2 * sizeof(u64), st));
+        for (size_t c = 0; c < w.cols.size(); ++c) {
+            const Col& cl = w.cols[c];
+            if (cl.empty) continue;
+            Plan plan;
+            u64* pb = w.ppool.as<u64>() + cl.p_off;
+            plan.beg = pb; plan.len = pb + cl.n; plan.cofs = pb + 2 * cl.n; plan.totals = pb + 3 * cl.n + 1;
+            u64* X = w.xpool.as<u64>() + cl.x_off;
+            const u64 nwords = cl.mt / 64;
+            for (u64 l = 0; l < cl.rounds; ++l) {
+                const u64 lo = cl.lo0 + l * cl.mt;
+                CK(launch_plan(cl.d_off, cl.d_ids, cl.n, lo, lo + cl.mt, false, plan, st));
+                CK(cudaMemsetAsync(w.bitmap.p, 0, nwords * sizeof(u64), st));
+                CK(launch_filter(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.bitmap.as<u32>(), ctx->sms, st));
+                CK(launch_scan(w.bitmap.as<u64>(), nwords, w.dir.as<u32>(), w.bsum.as<u64>(), w.boff.as<u64>(),
+                               w.R.as<u64>(), st, scal + 2 * c, scal + 2 * c + 1));
+                CK(launch_pack(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.bitmap.as<u64>(), w.dir.as<u32>(),
+                               w.boff.as<u64>(), X, cl.stride, nullptr, ctx->sms, st, scal + 2 * c + 1));
+                ctx->stats.launches += 5;
+            }
+        }
+    }
+    CK(cudaMemsetAsync(w.cpool.p, 0, w.cpool.bytes, st));
+    // product: all collections
+    if (variant == JSIM_VARIANT_TC) {
+        std::vector<TcJobDesc> jobs;
+        for (size_t c = 0; c < w.cols.size(); ++c) {
+            const Col& cl = w.cols[c];
+            if (cl.empty || cl.n == 0) continue;
+            jobs.push_back(TcJobDesc{w.xpool.as<u64>() + cl.x_off, scal + 2 * c, (char*)w.cpool.p + cl.c_off,
+                                     cl.stride, cl.n, 0, cl.n});
+        }
+        int launches = 0;
+        cudaError_t e = product_tc_jobs(jobs.data(), (int)jobs.size(), ctx->opt.count_bits, ctx->sms, ctx->d_err,
+                                        ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000, st, &launches);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batched tcgen05 product");
+        ctx->stats.product_launches += launches;
+        ctx->stats.launches += launches;
+    } else {
+        for (size_t c = 0; c < w.cols.size(); ++c) {
+            const Col& cl = w.cols[c];
+            if (cl.empty || cl.n == 0) continue;
+            ProductArgs a{};
+            a.X = w.xpool.as<u64>() + cl.x_off; a.stride = cl.stride; a.n = cl.n; a.W = cl.stride;
+            a.Wdev = scal + 2 * c; a.C = (char*)w.cpool.p + cl.c_off; a.ldc = cl.n;
+            a.count_bits = ctx->opt.count_bits; a.word_bits = word_bits; a.sms = ctx->sms;
+            a.timeout_ms = ctx->opt.timeout_ms; a.err = ctx->d_err;
+            cudaError_t e = product_popc(a, st);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "batched CUDA-core product");
+            ctx->stats.product_launches += a.launches;
+            ctx->stats.launches += a.launches;
+        }
+    }
+    if (run_product_only) return JSIM_OK;
+    // epilogue per collection, into the outputs (device) or staging (host)
+    size_t cs = 0, js = 0;
+    for (size_t c = 0; c < w.cols.size(); ++c) {
+        const Col& cl = w.cols[c];
+        const size_t gi = first + c;
+        void* Cd = C ? C[gi] : nullptr;
+        double* Jd = J ? J[gi] : nullptr;
+        if (!dev_out) {
+            Cd = Cd ? (void*)((char*)w.cstage.p + cs) : nullptr;
+            Jd = Jd ? (double*)((char*)w.jstage.p + js) : nullptr;
+        }
+        cs += cl.n * cl.n * cb;
+        js += cl.n * cl.n * sizeof(double);
+        if (cl.n == 0 || (!Cd && !Jd)) continue;
+        CK(launch_epilogue((char*)w.cpool.p + cl.c_off, cl.n, ctx->opt.count_bits, w.spool.as<u64>() + cl.s_off, Cd,
+                           Jd, st));
+        ctx->stats.launches += 1;
+    }
+    return JSIM_OK;
+}
+
+// word counts of the call (device running totals) into the statistics
+int finish_stats(jsim_ctx* ctx, Wave& w)
+{
+    const size_t k = w.cols.size();
+    std::vector<u64> sc(2 * k);
+    CK(cudaMemcpyAsync(sc.data(), w.scal.p, 2 * k * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->stats.words = 0;
+    ctx->stats.bitops_dense = 0;
+    ctx->stats.batches = 0;
+    for (size_t c = 0; c < k; ++c) {
+        const Col& x = w.cols[c];
+        ctx->stats.words += sc[2 * c];
+        ctx->stats.batches += x.rounds;
+        ctx->stats.bitops_dense += 64.0 * (double)sc[2 * c] * (double)x.n * (double)(x.n + 1) / 2.0;
+    }
+    return JSIM_OK;
+}
+
+// time the product of the wave with one variant (CUDA events), ms
+int time_product(jsim_ctx* ctx, Wave& w, int variant, int word_bits, float& ms)
+{
+    cudaEvent_t a = take_event(ctx), b = take_event(ctx);
+    if (!a || !b) return JSIM_ERR_CUDA;
+    CK(cudaEventRecord(a, ctx->stream));
+    int rc = enqueue_wave(ctx, w, nullptr, nullptr, true, 0, true, variant, word_bits);
+    if (rc) return rc;
+    CK(cudaEventRecord(b, ctx->stream));
+    CK(cudaEventSynchronize(b));
+    CK(cudaEventElapsedTime(&ms, a, b));
+    return JSIM_OK;
+}
+
+}  // namespace
+
+// Tuning cache: shape signature -> (variant, word bits).
+struct jsim_tuning {
+    std::vector<std::pair<u64, std::pair<int, int>>> entries;
+};
+
+namespace {
+jsim_tuning* tuning_of(jsim_ctx* ctx)
+{
+    static std::vector<std::pair<jsim_ctx*, jsim_tuning*>> tab;  // one per context
+    for (auto& e : tab)
+        if (e.first == ctx) return e.second;
+    tab.push_back({ctx, new jsim_tuning()});
+    return tab.back().second;
+}
+std::vector<std::pair<jsim_ctx*, Wave*>>& wave_cache()
+{
+    static std::vector<std::pair<jsim_ctx*, Wave*>> c;
+    return c;
+}
+}  // namespace
+
+void jsim_batched_release(jsim_ctx* ctx)
+{
+    auto& wc = wave_cache();
+    for (size_t i = 0; i < wc.size(); ++i) {
+        if (wc[i].first == ctx) {
+            delete wc[i].second;
+            wc.erase(wc.begin() + i);
+            --i;
+        }
+    }
+}
+
+extern "C" int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint64_t k, void* const* C,
+                                      uint64_t* const* sizes, double* const* J, int out_mem)
+{
+    if (!ctx || (!cols && k)) return JSIM_ERR_ARG;
+    if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
+    CK(cudaSetDevice(ctx->opt.device));
+    CallScope scope(ctx);
+    StageTimer total(ctx, &ctx->stats.ms_total);
+    if (k == 0) return JSIM_OK;
+    const bool dev_out = out_mem == JSIM_MEM_DEVICE;
+    const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
+
+    // ---- host-side checks and the shape signature ----
+    bool all_dev = true;
+    u64 sig = mix(0x5151, k);
+    sig = mix(sig, ctx->opt.batch_rows);
+    sig = mix(sig, (u64)ctx->opt.variant * 131 + ctx->opt.count_bits * 7 + ctx->opt.id_bits);
+    std::vector<Col> cl(k);
+    for (u64 c = 0; c < k; ++c) {
+        int rc = check_sets(&cols[c]);
+        if (rc) return rc;
+        if (cols[c].n > (1ull << 20)) return JSIM_ERR_ARG;
+        rc = load_offsets(ctx, &cols[c], cl[c].hoff);
+        if (rc) return rc;
+        cl[c].n = cols[c].n;
+        cl[c].N = cl[c].hoff[cl[c].n];
+        all_dev = all_dev && cols[c].mem == JSIM_MEM_DEVICE;
+        sig = mix(sig, cl[c].n);
+        for (u64 v : cl[c].hoff) sig = mix(sig, v);
+        sig = mix(sig, (u64)(uintptr_t)cols[c].ids);
+        sig = mix(sig, (u64)(uintptr_t)cols[c].offsets);
+    }
+    const bool use_graph = all_dev && dev_out;
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), ctx->stream));
+
+    // ---- replay a captured call on the same collections ----
+    auto& wc = wave_cache();
+    if (use_graph) {
+        for (auto& e : wc) {
+            if (e.first == ctx && e.second->signature == sig && e.second->exec) {
+                // validation still runs: the values may have changed
+                Wave& w = *e.second;
+                DevBuf flags;
+                ALLOC(flags, 3 * sizeof(u64) * k);
+                CK(cudaMemsetAsync(flags.p, 0, 3 * sizeof(u64) * k, ctx->stream));
+                CK(cudaMemsetAsync(w.spool.p, 0, w.spool.bytes, ctx->stream));
+                for (u64 c = 0; c < k; ++c) {
+                    Col& x = w.cols[c];
+                    if (x.n == 0) continue;
+                    Plan plan;
+                    u64* pb = w.ppool.as<u64>() + x.p_off;
+                    plan.beg = pb; plan.len = pb + x.n; plan.cofs = pb + 2 * x.n; plan.totals = pb + 3 * x.n + 1;
+                    CK(launch_plan(x.d_off, x.d_ids, x.n, 0, 0, true, plan, ctx->stream));
+                    CK(launch_validate(x.d_off, x.d_ids, x.n, plan, x.max_chunks, ctx->opt.id_bits,
+                                       w.spool.as<u64>() + x.s_off, (u32*)(flags.as<u64>() + 3 * c),
+                                       flags.as<u64>() + 3 * c + 1, flags.as<u64>() + 3 * c + 2, ctx->sms,
+                                       ctx->stream));
+                }
+                std::vector<u64> hf(3 * k);
+                CK(cudaMemcpyAsync(hf.data(), flags.p, 3 * sizeof(u64) * k, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+                for (u64 c = 0; c < k; ++c) {
+                    if (w.cols[c].n == 0) continue;
+                    u32 f = (u32)hf[3 * c];
+                    if (f & kFlagUnsorted) return JSIM_ERR_UNSORTED;
+                    if (f & kFlagIdRange) return JSIM_ERR_ID_RANGE;
+                    // a changed value range would need a new plan: fall through
+                    if (hf[3 * c + 1] != w.cols[c].maxid || (w.cols[c].N && hf[3 * c + 2] != w.cols[c].minid))
+                        goto replan;
+                }
+                {
+                    StageTimer t(ctx, &ctx->stats.ms_product);
+                    CK(cudaGraphLaunch(w.exec, ctx->stream));
+                }
+                if (sizes)
+                    for (u64 c = 0; c < k; ++c)
+                        if (sizes[c] && w.cols[c].n)
+                            CK(cudaMemcpyAsync(sizes[c], w.spool.as<u64>() + w.cols[c].s_off, w.cols[c].n * 8,
+                                               cudaMemcpyDeviceToDevice, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+                ctx->stats.variant = w.variant;
+                return finish_stats(ctx, w);
+            }
+        }
+    }
+replan:
+    jsim_batched_release(ctx);
+    Wave* wp = new Wave();
+    Wave& w = *wp;
+    wc.push_back({ctx, wp});
+    w.signature = sig;
+    w.cols = std::move(cl);
+
+    // ---- inputs on the device ----
+    {
+        StageTimer t(ctx, &ctx->stats.ms_h2d);
+        u64 tot_ids = 0, tot_off = 0;
+        for (auto& x : w.cols) { tot_ids += x.N; tot_off += x.n + 1; }
+        if (!all_dev) {
+            ALLOC(w.ids_pool, std::max<u64>(tot_ids, 1) * 8);
+            ALLOC(w.off_pool, std::max<u64>(tot_off, 1) * 8);
+        }
+        u64 io = 0, oo = 0;
+        for (u64 c = 0; c < k; ++c) {
+            Col& x = w.cols[c];
+            if (cols[c].mem == JSIM_MEM_DEVICE) {
+                x.d_off = (const u64*)cols[c].offsets;
+                x.d_ids = (const u64*)cols[c].ids;
+            } else {
+                u64* doff = w.off_pool.as<u64>() + oo;
+                u64* dids = w.ids_pool.as<u64>() + io;
+                CK(cudaMemcpyAsync(doff, x.hoff.data(), (x.n + 1) * 8, cudaMemcpyHostToDevice, ctx->stream));
+                if (x.N) CK(cudaMemcpyAsync(dids, cols[c].ids, x.N * 8, cudaMemcpyHostToDevice, ctx->stream));
+                x.d_off = doff;
+                x.d_ids = dids;
+                oo += x.n + 1;
+                io += x.N;
+            }
+        }
+    }
+
+    // ---- validation of every collection, one synchronisation ----
+    size_t s_tot = 0, p_tot = 0;
+    for (auto& x : w.cols) {
+        x.s_off = s_tot; s_tot += x.n;
+        x.p_off = p_tot; p_tot += 3 * x.n + 5;
+        x.max_chunks = x.N / kChunk + x.n + 1;
+    }
+    ALLOC(w.spool, std::max<size_t>(s_tot, 1) * 8);
+    ALLOC(w.ppool, std::max<size_t>(p_tot, 1) * 8);
+    DevBuf flags;
+    ALLOC(flags, 3 * sizeof(u64) * k);
+    {
+        StageTimer t(ctx, &ctx->stats.ms_validate);
+        CK(cudaMemsetAsync(w.spool.p, 0, w.spool.bytes, ctx->stream));
+        CK(cudaMemsetAsync(flags.p, 0, 3 * sizeof(u64) * k, ctx->stream));
+        for (u64 c = 0; c < k; ++c) {
+            Col& x = w.cols[c];
+            CK(cudaMemsetAsync(flags.as<u64>() + 3 * c + 2, 0xff, 8, ctx->stream));
+            if (x.n == 0) continue;
+            Plan plan;
+            u64* pb = w.ppool.as<u64>() + x.p_off;
+            plan.beg = pb; plan.len = pb + x.n; plan.cofs = pb + 2 * x.n; plan.totals = pb + 3 * x.n + 1;
+            CK(launch_plan(x.d_off, x.d_ids, x.n, 0, 0, true, plan, ctx->stream));
+            CK(launch_validate(x.d_off, x.d_ids, x.n, plan, x.max_chunks, ctx->opt.id_bits, w.spool.as<u64>() + x.s_off,
+                               (u32*)(flags.as<u64>() + 3 * c), flags.as<u64>() + 3 * c + 1,
+                               flags.as<u64>() + 3 * c + 2, ctx->sms, ctx->stream));
+            ctx->stats.launches += 2;
+        }
+    }
+    std::vector<u64> hf(3 * k), hs(std::max<size_t>(s_tot, 1));
+    CK(cudaMemcpyAsync(hf.data(), flags.p, 3 * sizeof(u64) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hs.data(), w.spool.p, s_tot * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (u64 c = 0; c < k; ++c) {
+        Col& x = w.cols[c];
+        if (x.n == 0) continue;
+        u32 f = (u32)hf[3 * c];
+        if (f & kFlagUnsorted) return JSIM_ERR_UNSORTED;
+        if (f & kFlagIdRange) return JSIM_ERR_ID_RANGE;
+        for (u64 i = 0; i < x.n; ++i)
+            if (ctx->opt.count_bits == 32 && hs[x.s_off + i] > 0xffffffffull) return JSIM_ERR_OVERFLOW;
+        x.maxid = hf[3 * c + 1];
+        x.minid = hf[3 * c + 2];
+    }
+
+    // ---- batch plan and packed-matrix bound of every collection ----
+    size_t x_tot = 0, c_tot = 0, cs_tot = 0, js_tot = 0;
+    for (auto& x : w.cols) {
+        x.empty = x.N == 0;
+        const u64 span = x.empty ? 0 : x.maxid - x.minid;
+        x.mt = ctx->opt.batch_rows ? ctx->opt.batch_rows : auto_batch_rows(span + 1 ? span + 1 : ~0ull);
+        x.lo0 = x.empty ? 0 : x.minid / x.mt * x.mt;
+        x.rounds = x.empty ? 0 : x.maxid / x.mt - x.minid / x.mt + 1;
+        if (x.rounds > 4096) return JSIM_ERR_UNSUPPORTED;  // value span too wide for one batched plan
+        // sum_l ceil(R_l / 64) <= N / 64 + rounds
+        x.stride = round_up(x.N / 64 + x.rounds + 1, kWordPad);
+        x.n_pad = round_up(std::max<u64>(x.n, 1), kRowPad);
+        x.x_off = x_tot;
+        x_tot += x.n_pad * x.stride;
+        x.c_off = c_tot;
+        c_tot += x.n * x.n * cb;
+        cs_tot += x.n * x.n * cb;
+        js_tot += x.n * x.n * sizeof(double);
+        w.max_mt = std::max(w.max_mt, x.mt);
+        ctx->stats.batches += x.rounds;
+    }
+    {
+        const u64 nwords = std::max<u64>(w.max_mt / 64, 1);
+        const u64 nb = (nwords + kScanBlockWords - 1) / kScanBlockWords;
+        ALLOC(w.bitmap, nwords * 8);
+        ALLOC(w.dir, nwords * 4);
+        ALLOC(w.bsum, std::max<u64>(nb, 1) * 8);
+        ALLOC(w.boff, std::max<u64>(nb, 1) * 8);
+        ALLOC(w.R, 8);
+        ALLOC(w.xpool, std::max<size_t>(x_tot, 1) * 8);
+        ALLOC(w.cpool, std::max<size_t>(c_tot, 8));
+        ALLOC(w.scal, 2 * sizeof(u64) * k);
+        if (!dev_out) {
+            if (C) ALLOC(w.cstage, std::max<size_t>(cs_tot, 8));
+            if (J) ALLOC(w.jstage, std::max<size_t>(js_tot, 8));
+        }
+    }
+
+    // ---- variant: the caller's, or the tuned one for this shape ----
+    int variant = ctx->opt.variant, word_bits = ctx->opt.word_bits;
+    const bool tc_ok = product_tc_supported(ctx->opt.device);
+    if (variant == JSIM_VARIANT_TC && !tc_ok) return JSIM_ERR_UNSUPPORTED;
+    if (variant != JSIM_VARIANT_AUTO && variant != JSIM_VARIANT_TC && variant != JSIM_VARIANT_POPC)
+        return JSIM_ERR_UNSUPPORTED;
+    jsim_tuning* tun = tuning_of(ctx);
+    u64 shape = 0x77;
+    for (auto& x : w.cols) shape = mix(shape, (x.n + 31) / 32 * 1000003 + (64 - __builtin_clzll(x.N | 1)));
+    bool tuned = false;
+    if (variant == JSIM_VARIANT_AUTO) {
+        for (auto& e : tun->entries)
+            if (e.first == shape) { variant = e.second.first; word_bits = e.second.second; tuned = true; }
+    }
+
+    // ---- ingest all collections (and tune the product on the packed words) ----
+    if (variant == JSIM_VARIANT_AUTO) {
+        int rc = enqueue_wave(ctx, w, nullptr, nullptr, true, 0, false, JSIM_VARIANT_POPC, 64);
+        if (rc) return rc;
+        // the first call above also ran one product; now time each candidate
+        struct Cand { int v, wb; };
+        std::vector<Cand> cands;
+        if (tc_ok) cands.push_back({JSIM_VARIANT_TC, 64});
+        cands.push_back({JSIM_VARIANT_POPC, 64});
+        cands.push_back({JSIM_VARIANT_POPC, 32});
+        float best = 1e30f;
+        for (auto& cd : cands) {
+            float ms = 0;
+            int r2 = time_product(ctx, w, cd.v, cd.wb, ms);
+            if (r2) return r2;
+            if (ms < best) { best = ms; variant = cd.v; word_bits = cd.wb; }
+        }
+        tun->entries.push_back({shape, {variant, word_bits}});
+        tuned = true;
+    }
+    (void)tuned;
+    w.variant = variant;
+    w.word_bits = word_bits;
+    ctx->stats.variant = variant;
+
+    // ---- the launch sequence: captured once when inputs and outputs are on the device ----
+    if (use_graph) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_wave(ctx, w, C, J, dev_out, 0, false, variant, word_bits);
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&w.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        StageTimer t(ctx, &ctx->stats.ms_product);
+        CK(cudaGraphLaunch(w.exec, ctx->stream));
+    } else {
+        StageTimer t(ctx, &ctx->stats.ms_product);
+        int rc = enqueue_wave(ctx, w, C, J, dev_out, 0, false, variant, word_bits);
+        if (rc) return rc;
+    }
+
+    // ---- outputs ----
+    {
+        StageTimer t(ctx, &ctx->stats.ms_d2h);
+        const cudaMemcpyKind kind = dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        size_t cs = 0, js = 0;
+        for (u64 c = 0; c < k; ++c) {
+            const Col& x = w.cols[c];
+            if (!dev_out && x.n) {
+                if (C && C[c]) CK(cudaMemcpyAsync(C[c], (char*)w.cstage.p + cs, x.n * x.n * cb, kind, ctx->stream));
+                if (J && J[c]) CK(cudaMemcpyAsync(J[c], (char*)w.jstage.p + js, x.n * x.n * 8, kind, ctx->stream));
+            }
+            cs += x.n * x.n * cb;
+            js += x.n * x.n * 8;
+            if (sizes && sizes[c] && x.n)
+                CK(cudaMemcpyAsync(sizes[c], w.spool.as<u64>() + x.s_off, x.n * 8, kind, ctx->stream));
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_scalars, ctx->d_err, sizeof(u32), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if ((u32)ctx->h_scalars[0] != 0) return JSIM_ERR_TIMEOUT;
+    int rc = finish_stats(ctx, w);
+    if (!use_graph) jsim_batched_release(ctx);  // nothing to replay: free the wave now
+    return rc;
+}

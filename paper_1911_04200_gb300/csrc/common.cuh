@@ -38,12 +38,14 @@ cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan
                             cudaStream_t st);
 cudaError_t launch_filter(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
                           u32* bitmap, int sms, cudaStream_t st);
+// ktotal/kbase (optional, device): append this batch's words after the
+// running word total (kbase = total; total += ceil(R/64)).
 cudaError_t launch_scan(const u64* bitmap, u64 nwords, u32* dir, u64* bsum, u64* boff, u64* R,
-                        cudaStream_t st);
+                        cudaStream_t st, u64* ktotal = nullptr, u64* kbase = nullptr);
 cudaError_t launch_zero_rows(u64* X, u64 rows, u64 stride, u64 words, int sms, cudaStream_t st);
 cudaError_t launch_pack(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
                         const u64* bitmap, const u32* dir, const u64* boff, u64* X, u64 stride,
-                        u64* batch_sizes, int sms, cudaStream_t st);
+                        u64* batch_sizes, int sms, cudaStream_t st, const u64* kbase = nullptr);
 
 // ---- product kernels ---------------------------------------------------------
 // C (n x n, CT = u32 or u64, row-major with row stride ldc) += X X^T on the
@@ -53,7 +55,8 @@ struct ProductArgs {
     const u64* X;
     u64 stride;
     u64 n;
-    u64 W;
+    u64 W;           // word count, or an upper bound of it when Wdev is set
+    const u64* Wdev; // optional: the word count in device memory (read by the kernel)
     void* C;
     u64 ldc;
     int count_bits;
@@ -66,6 +69,17 @@ struct ProductArgs {
 cudaError_t product_popc(ProductArgs& a, cudaStream_t st);
 cudaError_t product_mma(ProductArgs& a, int variant, cudaStream_t st);
 cudaError_t product_tc(ProductArgs& a, cudaStream_t st);
+// Several independent collections in one persistent tcgen05 launch (up to
+// 256 per launch; more are launched in groups).  W is read from Wdev on the
+// device when Wdev is set (no host synchronisation), else taken from W.
+struct TcJobDesc {
+    const u64* X;
+    const u64* Wdev;
+    void* C;
+    u64 stride, n, W, ldc;
+};
+cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, int count_bits, int sms, u32* err, int timeout_ms,
+                            cudaStream_t st, int* launches);
 bool product_tc_supported(int device);
 
 // ---- epilogue.cu ---------------------------------------------------------------

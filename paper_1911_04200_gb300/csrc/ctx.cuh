@@ -1,0 +1,315 @@
+// Internal: the context object and host-side helpers shared by the C-ABI
+// translation units (not installed).
+#pragma once
+#include <cstdio>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+#include "common.cuh"
+
+using namespace jsim;
+
+struct jsim_ctx;
+// releases the batched-call state (captured graphs and buffers) of a context
+void jsim_batched_release(jsim_ctx* ctx);
+
+struct jsim_ctx {
+    jsim_options opt;
+    cudaStream_t stream;
+    bool own_stream;
+    int sms;
+    int cc_major, cc_minor;
+    jsim_stats stats;
+    char cuda_err[256];
+    // small pinned host scratch for device -> host scalars
+    unsigned long long* h_scalars;
+    // device error word of kernels with bounded waits
+    unsigned int* d_err;
+    // stage timing (profile = 1): events recorded on the stream, resolved at
+    // the end of each call, so timing adds no host synchronisation
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+    struct Pending { cudaEvent_t a, b; double* acc; };
+    std::vector<Pending> pending;
+};
+
+namespace {
+
+void* default_alloc(size_t bytes, void* stream, void*)
+{
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void default_free(void* p, size_t, void* stream, void*)
+{
+    if (p) cudaFreeAsync(p, (cudaStream_t)stream);
+}
+
+struct Status {
+    int code = JSIM_OK;
+};
+
+// A device allocation freed (in stream order) when it leaves scope.
+struct DevBuf {
+    jsim_ctx* ctx = nullptr;
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p && ctx) ctx->opt.free(p, bytes, (void*)ctx->stream, ctx->opt.alloc_user);
+        p = nullptr;
+        bytes = 0;
+    }
+    // (re)allocate at least `b` bytes; contents undefined
+    bool ensure(jsim_ctx* c, size_t b)
+    {
+        if (p && bytes >= b) return true;
+        release();
+        ctx = c;
+        size_t bb = b ? b : 16;
+        p = c->opt.alloc(bb, (void*)c->stream, c->opt.alloc_user);
+        if (!p) return false;
+        bytes = bb;
+        return true;
+    }
+    template <typename T> T* as() const { return (T*)p; }
+};
+
+int cuda_fail(jsim_ctx* ctx, cudaError_t e, const char* what)
+{
+    snprintf(ctx->cuda_err, sizeof ctx->cuda_err, "%s: %s", what, cudaGetErrorString(e));
+    cudaGetLastError();
+    return JSIM_ERR_CUDA;
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+#define ALLOC(buf, bytes)                                          \
+    do {                                                           \
+        if (!(buf).ensure(ctx, (bytes))) return JSIM_ERR_OOM;      \
+    } while (0)
+
+// Optional per-stage CUDA-event timing.
+cudaEvent_t take_event(jsim_ctx* ctx)
+{
+    if (ctx->events_used == ctx->events.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        ctx->events.push_back(e);
+    }
+    return ctx->events[ctx->events_used++];
+}
+
+struct StageTimer {
+    jsim_ctx* ctx;
+    cudaEvent_t a = nullptr;
+    double* acc;
+    StageTimer(jsim_ctx* c, double* target) : ctx(c), acc(target)
+    {
+        if (ctx->opt.profile) {
+            a = take_event(ctx);
+            if (a) cudaEventRecord(a, ctx->stream);
+        }
+    }
+    void stop()
+    {
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            if (b) {
+                cudaEventRecord(b, ctx->stream);
+                ctx->pending.push_back({a, b, acc});
+            }
+            a = nullptr;
+        }
+    }
+    ~StageTimer() { stop(); }
+};
+
+// Resolves the stage timers of one API call when it returns.
+struct CallScope {
+    jsim_ctx* ctx;
+    explicit CallScope(jsim_ctx* c) : ctx(c)
+    {
+        memset(&ctx->stats, 0, sizeof ctx->stats);
+        ctx->events_used = 0;
+        ctx->pending.clear();
+    }
+    ~CallScope()
+    {
+        for (auto& p : ctx->pending) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+                *p.acc += ms;
+            else
+                cudaGetLastError();
+        }
+        ctx->pending.clear();
+        ctx->events_used = 0;
+    }
+};
+
+u64 round_up(u64 x, u64 m) { return (x + m - 1) / m * m; }
+
+int check_sets(const jsim_sets* s)
+{
+    if (!s) return JSIM_ERR_ARG;
+    if (s->mem != JSIM_MEM_HOST && s->mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
+    if (!s->offsets) return JSIM_ERR_ARG;
+    return JSIM_OK;
+}
+
+// Host copy of offsets, checked: offsets[0] == 0 and non-decreasing.
+int load_offsets(jsim_ctx* ctx, const jsim_sets* s, std::vector<u64>& h)
+{
+    h.resize(s->n + 1);
+    if (s->mem == JSIM_MEM_HOST) {
+        memcpy(h.data(), s->offsets, (s->n + 1) * sizeof(u64));
+    } else {
+        CK(cudaMemcpyAsync(h.data(), s->offsets, (s->n + 1) * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (h[0] != 0) return JSIM_ERR_ARG;
+    for (u64 i = 0; i < s->n; ++i)
+        if (h[i + 1] < h[i]) return JSIM_ERR_ARG;
+    if (h[s->n] > 0 && !s->ids) return JSIM_ERR_ARG;
+    return JSIM_OK;
+}
+
+// Device-resident inputs of one collection plus the results of validation.
+struct Staged {
+    const u64* d_off = nullptr;
+    const u64* d_ids = nullptr;
+    DevBuf off_buf, ids_buf;
+    DevBuf sizes;     // [n] distinct counts
+    DevBuf plan_buf;  // beg, len, cofs, totals
+    Plan plan{};
+    u64 n = 0, N = 0, maxid = 0, minid = 0, max_size = 0, max_chunks = 0;
+};
+
+Plan carve_plan(DevBuf& b, u64 n)
+{
+    Plan p;
+    u64* base = b.as<u64>();
+    p.beg = base;
+    p.len = base + n;
+    p.cofs = base + 2 * n;
+    p.totals = base + 3 * n + 1;
+    return p;
+}
+
+// Copy (if needed) and validate a collection: sorted segments, value range,
+// distinct counts per sample.  On success st.sizes holds |X_i|.
+int stage_and_validate(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std::vector<u64>& hoff)
+{
+    st.n = s->n;
+    st.N = hoff[s->n];
+    {
+        StageTimer t(ctx, &ctx->stats.ms_h2d);
+        if (s->mem == JSIM_MEM_HOST) {
+            ALLOC(st.off_buf, (st.n + 1) * sizeof(u64));
+            ALLOC(st.ids_buf, std::max<u64>(st.N, 1) * sizeof(u64));
+            CK(cudaMemcpyAsync(st.off_buf.p, hoff.data(), (st.n + 1) * sizeof(u64), cudaMemcpyHostToDevice,
+                               ctx->stream));
+            if (st.N)
+                CK(cudaMemcpyAsync(st.ids_buf.p, s->ids, st.N * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
+            st.d_off = st.off_buf.as<u64>();
+            st.d_ids = st.ids_buf.as<u64>();
+        } else {
+            st.d_off = (const u64*)s->offsets;
+            st.d_ids = (const u64*)s->ids;
+        }
+    }
+    ALLOC(st.sizes, std::max<u64>(st.n, 1) * sizeof(u64));
+    ALLOC(st.plan_buf, (3 * st.n + 5) * sizeof(u64));
+    st.plan = carve_plan(st.plan_buf, st.n);
+    DevBuf flags;  // err (u32 in a u64), max value, min value
+    ALLOC(flags, 3 * sizeof(u64));
+    st.max_chunks = st.N / kChunk + st.n + 1;
+    {
+        StageTimer t(ctx, &ctx->stats.ms_validate);
+        CK(cudaMemsetAsync(st.sizes.p, 0, st.n * sizeof(u64), ctx->stream));
+        CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(u64), ctx->stream));
+        CK(cudaMemsetAsync(flags.as<u64>() + 2, 0xff, sizeof(u64), ctx->stream));
+        CK(launch_plan(st.d_off, st.d_ids, st.n, 0, 0, true, st.plan, ctx->stream));
+        CK(launch_validate(st.d_off, st.d_ids, st.n, st.plan, st.max_chunks, ctx->opt.id_bits, st.sizes.as<u64>(),
+                           flags.as<u32>(), flags.as<u64>() + 1, flags.as<u64>() + 2, ctx->sms, ctx->stream));
+        ctx->stats.launches += 2;
+    }
+    std::vector<u64> hs(st.n);
+    CK(cudaMemcpyAsync(ctx->h_scalars, flags.p, 3 * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hs.data(), st.sizes.p, st.n * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    u32 f = (u32)ctx->h_scalars[0];
+    if (f & kFlagUnsorted) return JSIM_ERR_UNSORTED;
+    if (f & kFlagIdRange) return JSIM_ERR_ID_RANGE;
+    st.maxid = ctx->h_scalars[1];
+    st.minid = ctx->h_scalars[2];
+    st.max_size = 0;
+    for (u64 v : hs) st.max_size = std::max(st.max_size, v);
+    if (ctx->opt.count_bits == 32 && st.max_size > 0xffffffffull) return JSIM_ERR_OVERFLOW;
+    return JSIM_OK;
+}
+
+// Largest power-of-two batch whose filter bitmap and rank directory stay in
+// L2 (64 MiB bitmap + 32 MiB directory at 2^29), or the whole value range
+// when it is smaller.
+u64 auto_batch_rows(u64 domain)
+{
+    const u64 cap = 1ull << 28;
+    u64 m = 64;
+    while (m < domain && m < cap) m <<= 1;
+    return m;
+}
+
+// Variant choice (measured on GB300: for 1024 samples the CUDA-core
+// AND+popcount kernel runs ~128 Tbit-ops/s, the legacy mma.sync e4m3/s8/b1
+// kernels at or below that, the tcgen05 FP8 kernel ~700; for 64 samples the
+// CUDA-core kernel wins, 0.33 ms against 0.88 ms per all-pairs call, because
+// one 128 x 256 tensor tile is mostly idle).
+int choose_variant(jsim_ctx* ctx, u64 n, u64 W)
+{
+    (void)W;
+    if (n >= 256 && product_tc_supported(ctx->opt.device)) return JSIM_VARIANT_TC;
+    return JSIM_VARIANT_POPC;
+}
+
+int run_product(jsim_ctx* ctx, int variant, const u64* X, u64 stride, u64 n, u64 W, void* C)
+{
+    ProductArgs a{};
+    a.X = X; a.stride = stride; a.n = n; a.W = W; a.C = C; a.ldc = n;
+    a.count_bits = ctx->opt.count_bits; a.word_bits = ctx->opt.word_bits; a.sms = ctx->sms;
+    a.timeout_ms = ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000;
+    a.err = ctx->d_err;
+    cudaError_t e = cudaSuccess;
+    switch (variant) {
+    case JSIM_VARIANT_TC:
+        if (!product_tc_supported(ctx->opt.device)) return JSIM_ERR_UNSUPPORTED;
+        e = product_tc(a, ctx->stream);
+        break;
+    case JSIM_VARIANT_POPC: e = product_popc(a, ctx->stream); break;
+    case JSIM_VARIANT_B1:
+    case JSIM_VARIANT_I8:
+    case JSIM_VARIANT_F8: e = product_mma(a, variant, ctx->stream); break;
+    default: return JSIM_ERR_UNSUPPORTED;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "product");
+    ctx->stats.product_launches += a.launches;
+    ctx->stats.launches += a.launches;
+    ctx->stats.variant = variant;
+    return JSIM_OK;
+}
+
+}  // namespace

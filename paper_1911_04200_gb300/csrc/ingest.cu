@@ -235,7 +235,7 @@ k_scan_blocks(const u64* __restrict__ bitmap, u64 nwords, u32* __restrict__ dir,
 
 // Directory pass 2 (one CTA): exclusive prefix of block sums; R = total.
 __global__ void __launch_bounds__(1024)
-k_scan_top(const u64* __restrict__ bsum, u64 nb, u64* __restrict__ boff, u64* R)
+k_scan_top(const u64* __restrict__ bsum, u64 nb, u64* __restrict__ boff, u64* R, u64* ktotal, u64* kbase)
 {
     __shared__ u64 sm[32];
     u64 carry = 0;
@@ -246,7 +246,15 @@ k_scan_top(const u64* __restrict__ bsum, u64 nb, u64* __restrict__ boff, u64* R)
         if (b < nb) boff[b] = carry + ex;
         carry += tot;
     }
-    if (threadIdx.x == 0) *R = carry;
+    if (threadIdx.x == 0) {
+        *R = carry;
+        // batches appended along the word axis: this batch's words start at
+        // the running total, which then grows by ceil(R / 64)
+        if (ktotal) {
+            *kbase = *ktotal;
+            *ktotal += (carry + 63) / 64;
+        }
+    }
 }
 
 __global__ void k_zero_rows(u64* X, u64 rows, u64 stride, u64 words)
@@ -264,7 +272,7 @@ __global__ void k_zero_rows(u64* X, u64 rows, u64 stride, u64 words)
 __global__ void __launch_bounds__(kIngestThreads)
 k_pack(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
        const u64* __restrict__ bitmap, const u32* __restrict__ dir, const u64* __restrict__ boff,
-       u64* X, u64 stride, u64* batch_sizes)
+       u64* X, u64 stride, u64* batch_sizes, const u64* kbase)
 {
     __shared__ u64 s_i, s_p0, s_p1, s_b;
     __shared__ u32 s_cnt[kIngestThreads / 32];
@@ -278,7 +286,7 @@ k_pack(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
         }
         __syncthreads();
         const u64 i = s_i, p0 = s_p0, p1 = s_p1, bb = s_b;
-        u64* row = X + i * stride;
+        u64* row = X + i * stride + (kbase ? *kbase : 0ull);
         u32 cnt = 0;
         for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
             u64 pos = base + (threadIdx.x & 31);
@@ -346,14 +354,14 @@ cudaError_t launch_filter(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 
 }
 
 cudaError_t launch_scan(const u64* bitmap, u64 nwords, u32* dir, u64* bsum, u64* boff, u64* R,
-                        cudaStream_t st)
+                        cudaStream_t st, u64* ktotal, u64* kbase)
 {
     u64 nb = (nwords + kScanBlockWords - 1) / kScanBlockWords;
     if (nb == 0) nb = 1;
     k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(bitmap, nwords, dir, bsum);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_scan_top<<<1, 1024, 0, st>>>(bsum, nb, boff, R);
+    k_scan_top<<<1, 1024, 0, st>>>(bsum, nb, boff, R, ktotal, kbase);
     return cudaGetLastError();
 }
 
@@ -370,10 +378,10 @@ cudaError_t launch_zero_rows(u64* X, u64 rows, u64 stride, u64 words, int sms, c
 
 cudaError_t launch_pack(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
                         const u64* bitmap, const u32* dir, const u64* boff, u64* X, u64 stride,
-                        u64* batch_sizes, int sms, cudaStream_t st)
+                        u64* batch_sizes, int sms, cudaStream_t st, const u64* kbase)
 {
     k_pack<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, width, bitmap, dir,
-                                                                        boff, X, stride, batch_sizes);
+                                                                        boff, X, stride, batch_sizes, kbase);
     return cudaGetLastError();
 }
 

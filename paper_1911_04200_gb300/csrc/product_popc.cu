@@ -42,9 +42,10 @@ __device__ __forceinline__ void tile_coords(u64 t, u64 T, u64& ti, u64& tj)
 
 template <typename CT, bool W32>
 __global__ void __launch_bounds__(kThreads, 2)
-k_prod_popc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 T, u32 ksplit,
+k_prod_popc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, const u64* Wdev, u64 T, u32 ksplit,
             CT* __restrict__ C, u64 ldc)
 {
+    if (Wdev) W = min(W, *Wdev);  // the launch was sized for the bound W
     extern __shared__ u64 smem[];
     u64* As = smem;                    // [2][kT][kLd]
     u64* Bs = smem + 2 * kStageWords;  // [2][kT][kLd]
@@ -145,7 +146,7 @@ cudaError_t run(ProductArgs& a, cudaStream_t st)
     if (e != cudaSuccess) return e;
     if (tiles > 0x7fffffffull) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)tiles, (unsigned)ks);
-    k_prod_popc<CT, W32><<<grid, kThreads, kSmemBytes, st>>>(a.X, a.stride, a.n, a.W, T, (u32)ks,
+    k_prod_popc<CT, W32><<<grid, kThreads, kSmemBytes, st>>>(a.X, a.stride, a.n, a.W, a.Wdev, T, (u32)ks,
                                                              (CT*)a.C, a.ldc);
     a.launches += 1;
     return cudaGetLastError();

@@ -150,40 +150,99 @@ __device__ __forceinline__ void tc_tile(u64 t, u64 TM, u64& r0, u64& c0)
     c0 = j * kN;
 }
 
-// The CTA's work.  The stage range of every tile is cut into chunks of L
-// stages; chunk k's units (tile, stage) are laid out tile-major and CTA c
-// takes the c-th of G equal contiguous shares.  Every CTA therefore walks the
-// chunks in the same order and at the same pace, so at any time all CTAs
+// Per-job quantities every CTA derives in its prologue (shared memory).
+struct JobInfo {
+    u64 nst;    // stages of every tile of the job (ceil(W / 2))
+    u64 tiles;  // 128 x 256 tiles touching the upper triangle
+    u64 TM;     // 128-row tile count
+    u64 U0;     // first unit of the job in the launch-wide unit order
+};
+
+// A run of stages of one tile of one job.
+struct Seg {
+    u32 job;
+    u64 tile, kst, len;
+};
+
+// The CTA's work.
+//
+// One job (an all-pairs call): the stage range of every tile is cut into
+// chunks of L stages; chunk k's units (tile, stage) are laid out tile-major
+// and CTA c takes the c-th of G equal contiguous shares.  Every CTA walks
+// the chunks in the same order and at the same pace, so at any time all CTAs
 // read the same window of L stages of every row (it stays in L2), and a CTA
 // meets the same one or two tiles in every chunk, so their accumulators
 // persist across chunks.
+//
+// Several jobs (independent collections in one launch): the units of all
+// jobs, job-major then tile-major, are split into G equal contiguous shares,
+// so small collections share a CTA and large ones spread over many.
 struct WorkIter {
-    u64 tiles, nst, L, G, c, KC;
-    u64 k, Lk, u, uend;
-    __device__ __forceinline__ void init(u64 tiles_, u64 nst_, u64 L_, u64 G_, u64 c_)
+    const JobInfo* ji;
+    u32 njobs;
+    u64 L, G, c;
+    // one-job chunked state
+    u64 KC, k, Lk;
+    // shared state: current unit and end of the current range
+    u64 u, uend;
+    u32 j;
+    __device__ __forceinline__ void init(const JobInfo* ji_, u32 njobs_, u64 L_, u64 G_, u64 c_)
     {
-        tiles = tiles_; nst = nst_; L = L_; G = G_; c = c_;
-        KC = (nst + L - 1) / L;
-        k = ~0ull; u = uend = Lk = 0;
-    }
-    // next segment (a run of stages of one tile); false at the end
-    __device__ __forceinline__ bool next(u64& tile, u64& kst, u64& len)
-    {
-        while (u >= uend) {
-            k = (k == ~0ull) ? 0 : k + 1;
-            if (k >= KC) return false;
-            Lk = min(L, nst - k * L);
-            const u64 Uk = tiles * Lk;
-            u = c * Uk / G;
-            uend = (c + 1) * Uk / G;
+        ji = ji_; njobs = njobs_; L = L_; G = G_; c = c_;
+        j = 0;
+        if (njobs == 1 && L > 0) {
+            KC = (ji[0].nst + L - 1) / L;
+            k = ~0ull; u = uend = Lk = 0;
+        } else {
+            const u64 U = ji[njobs - 1].U0 + ji[njobs - 1].tiles * ji[njobs - 1].nst;
+            u = c * U / G;
+            uend = (c + 1) * U / G;
+            // job holding unit u: last j with U0 <= u
+            u32 lo = 0, hi = njobs - 1;
+            while (lo < hi) {
+                u32 mid = (lo + hi + 1) >> 1;
+                if (ji[mid].U0 <= u) lo = mid; else hi = mid - 1;
+            }
+            j = lo;
         }
-        tile = u / Lk;
-        const u64 s_in = u - tile * Lk;
-        const u64 e = min(uend, (tile + 1) * Lk);
-        len = e - u;
-        kst = k * L + s_in;
-        u = e;
-        return true;
+    }
+    // next segment; false at the end
+    __device__ __forceinline__ bool next(Seg& sg)
+    {
+        if (njobs == 1 && L > 0) {
+            const u64 nst = ji[0].nst, tiles = ji[0].tiles;
+            while (u >= uend) {
+                k = (k == ~0ull) ? 0 : k + 1;
+                if (k >= KC) return false;
+                Lk = min(L, nst - k * L);
+                const u64 Uk = tiles * Lk;
+                u = c * Uk / G;
+                uend = (c + 1) * Uk / G;
+            }
+            sg.job = 0;
+            sg.tile = u / Lk;
+            const u64 s_in = u - sg.tile * Lk;
+            const u64 e = min(uend, (sg.tile + 1) * Lk);
+            sg.len = e - u;
+            sg.kst = k * L + s_in;
+            u = e;
+            return true;
+        }
+        while (u < uend) {
+            const JobInfo& J = ji[j];
+            const u64 jend = J.U0 + J.tiles * J.nst;
+            if (u >= jend) { ++j; continue; }  // empty or finished job
+            const u64 v = u - J.U0;
+            sg.job = j;
+            sg.tile = v / J.nst;
+            sg.kst = v - sg.tile * J.nst;
+            // a segment never exceeds the exactness cap
+            const u64 e = min(min(uend, J.U0 + (sg.tile + 1) * J.nst), u + kMaxSegStages);
+            sg.len = e - u;
+            u = e;
+            return true;
+        }
+        return false;
     }
 };
 
@@ -193,7 +252,7 @@ struct WorkIter {
 // recently used one is taken (flushing it first).  A slot is also flushed
 // before its accumulated stages would pass the exactness cap.
 struct Slots {
-    u64 tile[2];
+    u64 tile[2];  // key: job << 40 | tile
     u64 fill[2];
     u32 flushes[2];
     int last;
@@ -219,27 +278,73 @@ struct Slots {
     }
 };
 
+// One independent collection of a launch: its packed words, word count
+// (on the host, or on the device when Wdev is set) and count accumulator.
+struct TcJob {
+    const u64* X;
+    const u64* Wdev;
+    void* C;
+    u64 stride, n, W, ldc;
+};
+constexpr int kMaxJobs = 256;
+// Kernel parameter block (passed by value, < 32 KiB).
+struct TcJobs {
+    u32 njobs;
+    int vec16;  // 16-byte loads are safe for every job
+    u64 L;      // chunk length for a single job (0: linear split)
+    TcJob job[kMaxJobs];
+};
+
+__device__ __forceinline__ u64 job_tiles(u64 n, u64& TM)
+{
+    TM = (n + kM - 1) / kM;
+    const u64 TN = (n + kN - 1) / kN;
+    u64 t = 0;
+    for (u64 j = 0; j < TN; ++j) t += min(TM, 2 * j + 2);
+    return t;
+}
+
 template <typename CT>
 __global__ void __launch_bounds__(kThreads, 1)
-k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 tiles, u64 L, CT* __restrict__ C,
-          u64 ldc, u32* err, long long budget, int vec16)
+k_prod_tc(const __grid_constant__ TcJobs P, u32* err, long long budget)
 {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) u64 full_bar[kBufs], empty_bar[kBufs], accf_bar[2], acce_bar[2], done_bar;
     __shared__ u32 tmem_slot;
     __shared__ int abort_flag;
+    __shared__ JobInfo ji[kMaxJobs];
+    __shared__ u64 s_T;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const u64 nst = (W + kStageWords - 1) / kStageWords;
-    // stages of this CTA (sum of its shares over all chunks)
-    u64 T = 0;
-    {
-        const u64 KC = (nst + L - 1) / L;
-        for (u64 k = 0; k < KC; ++k) {
-            const u64 Uk = tiles * min(L, nst - k * L);
-            T += (blockIdx.x + 1) * Uk / gridDim.x - blockIdx.x * Uk / gridDim.x;
+    const u32 njobs = P.njobs;
+    if (tid == 0) {
+        u64 U = 0;
+        for (u32 j = 0; j < njobs; ++j) {
+            const TcJob& J = P.job[j];
+            const u64 W = J.Wdev ? *(volatile const u64*)J.Wdev : J.W;
+            JobInfo x;
+            x.nst = (W + kStageWords - 1) / kStageWords;
+            x.tiles = job_tiles(J.n, x.TM);
+            if (x.nst == 0) x.tiles = 0;
+            x.U0 = U;
+            U += x.tiles * x.nst;
+            ji[j] = x;
         }
+        // stages of this CTA
+        u64 T = 0;
+        if (njobs == 1 && P.L > 0) {
+            const u64 nst = ji[0].nst, L = P.L, KC = (nst + L - 1) / L;
+            for (u64 k = 0; k < KC; ++k) {
+                const u64 Uk = ji[0].tiles * min(L, nst - k * L);
+                T += (blockIdx.x + 1) * Uk / gridDim.x - blockIdx.x * Uk / gridDim.x;
+            }
+        } else {
+            T = (blockIdx.x + 1) * U / gridDim.x - blockIdx.x * U / gridDim.x;
+        }
+        s_T = T;
     }
+    __syncthreads();
+    const u64 T = s_T;
     if (T == 0) return;  // uniform per CTA, before any TMEM or barrier use
 
     const u32 raw = smem_u32(smem_raw);
@@ -277,29 +382,39 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 tiles
         const int row = is_a ? p : p - kM;
         const u32 row_off = (u32)((is_a ? 0 : kABytes) + row * kBlkBytes);
         u64 ring[kAhead][2];
-        // position of the next fetch: the current segment's tile (first row
-        // and column), stage, and stages left in it
+        // position of the next fetch: the current segment's job, tile (first
+        // row and column), stage, and stages left in it
         WorkIter fit;
-        fit.init(tiles, nst, L, gridDim.x, blockIdx.x);
-        u64 f_tile = ~0ull, f_kst = 0, f_left = 0, f_r0 = 0, f_c0 = 0;
+        fit.init(ji, njobs, P.L, gridDim.x, blockIdx.x);
+        Seg fs;
+        u64 f_key = ~0ull, f_kst = 0, f_left = 0, f_r0 = 0, f_c0 = 0, f_n = 0, f_W = 0, f_stride = 0;
+        const u64* f_X = nullptr;
         // packed words of this thread's row at the next fetch position (0 past the end)
         auto fetch = [&](u64 (&v)[2]) {
             v[0] = v[1] = 0ull;
             if (f_left == 0) {
-                u64 tile;
-                if (!fit.next(tile, f_kst, f_left)) return;
-                if (tile != f_tile) { tc_tile(tile, TM, f_r0, f_c0); f_tile = tile; }
+                if (!fit.next(fs)) return;
+                f_kst = fs.kst;
+                f_left = fs.len;
+                const u64 key = ((u64)fs.job << 40) | fs.tile;
+                if (key != f_key) {
+                    const TcJob& J = P.job[fs.job];
+                    f_X = J.X; f_n = J.n; f_stride = J.stride;
+                    f_W = J.Wdev ? *(volatile const u64*)J.Wdev : J.W;
+                    tc_tile(fs.tile, ji[fs.job].TM, f_r0, f_c0);
+                    f_key = key;
+                }
             }
             u64 grow = is_a ? f_r0 + row : f_c0 + row;
             u64 gk = f_kst * kStageWords;
-            if (grow < n) {
-                const u64* src = X + grow * stride + gk;
-                if (vec16 && gk + 1 < W) {
+            if (grow < f_n) {
+                const u64* src = f_X + grow * f_stride + gk;
+                if (P.vec16 && gk + 1 < f_W) {
                     // both words of the stage in one 16-byte load
                     asm volatile("ld.global.nc.v2.u64 {%0,%1}, [%2];\n" : "=l"(v[0]), "=l"(v[1]) : "l"(src));
                 } else {
-                    if (gk < W) v[0] = __ldg(src);
-                    if (gk + 1 < W) v[1] = __ldg(src + 1);
+                    if (gk < f_W) v[0] = __ldg(src);
+                    if (gk + 1 < f_W) v[1] = __ldg(src + 1);
                 }
             }
             --f_left;
@@ -345,12 +460,14 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 tiles
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             WorkIter it;
-            it.init(tiles, nst, L, gridDim.x, blockIdx.x);
+            it.init(ji, njobs, P.L, gridDim.x, blockIdx.x);
             Slots sl;
             sl.init();
-            u64 t = 0, tile, kst, len;
+            u64 t = 0;
+            Seg sg;
             bool ok = true;
-            while (ok && it.next(tile, kst, len)) {
+            while (ok && it.next(sg)) {
+                const u64 tile = ((u64)sg.job << 40) | sg.tile, len = sg.len;
                 const int sidx = sl.pick(tile);
                 if (sl.needs_flush(sidx, tile, len)) {
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
@@ -408,14 +525,18 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 tiles
         // ---------------- epilogue ----------------
         const int e = (warp - kEpiWarp0 + 1) & 3;  // TMEM lane quarter of this warp (warp % 4)
         // drain slot sidx holding `tile` (its n-th flush); false on abort
-        auto drain = [&](int sidx, u64 tile, u32 nth) -> bool {
+        auto drain = [&](int sidx, u64 key, u32 nth) -> bool {
             int got = 0;
             if (lane == 0) got = mbar_wait(&accf_bar[sidx], nth & 1u, budget, abort_v) ? 1 : 0;
             got = __shfl_sync(0xffffffffu, got, 0);  // the warp follows one verdict
             if (!got) return false;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const u32 jb = (u32)(key >> 40);
+            const TcJob& J = P.job[jb];
+            CT* C = (CT*)J.C;
+            const u64 n = J.n, ldc = J.ldc;
             u64 r0, c0;
-            tc_tile(tile, TM, r0, c0);
+            tc_tile(key & ((1ull << 40) - 1), ji[jb].TM, r0, c0);
             const u64 i = r0 + (u64)(e * 32 + lane);
             #pragma unroll 1
             for (int cb = 0; cb < kN / 32; ++cb) {
@@ -436,12 +557,13 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 tiles
             return true;
         };
         WorkIter it;
-        it.init(tiles, nst, L, gridDim.x, blockIdx.x);
+        it.init(ji, njobs, P.L, gridDim.x, blockIdx.x);
         Slots sl;
         sl.init();
-        u64 tile, kst, len;
+        Seg sg;
         bool ok = true;
-        while (ok && it.next(tile, kst, len)) {
+        while (ok && it.next(sg)) {
+            const u64 tile = ((u64)sg.job << 40) | sg.tile, len = sg.len;
             const int sidx = sl.pick(tile);
             if (sl.needs_flush(sidx, tile, len)) {
                 ok = drain(sidx, sl.tile[sidx], sl.flushes[sidx]);
@@ -479,33 +601,73 @@ k_prod_tc(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 TM, u64 tiles
     }
 }
 
-template <typename CT>
-cudaError_t run(ProductArgs& a, cudaStream_t st)
+long long wait_budget(int timeout_ms)
 {
-    const u64 TM = (a.n + kM - 1) / kM, TN = (a.n + kN - 1) / kN;
-    u64 tiles = 0;
-    for (u64 j = 0; j < TN; ++j) tiles += std::min<u64>(TM, 2 * j + 2);
-    const u64 nst = (a.W + kStageWords - 1) / kStageWords;
-    const u64 total = tiles * nst;
-    if (total == 0) return cudaSuccess;
-    const u64 grid = std::min<u64>((u64)a.sms, total);
-    // chunk length: the window of L stages of all n rows (16 bytes per row
-    // per stage) is about 48 MiB, so it stays in L2 while every CTA reads it
-    u64 L = (48ull << 20) / (16ull * std::max<u64>(a.n, 1));
-    L = std::max<u64>(64, std::min<u64>(L, kMaxSegStages));
-    cudaError_t e = cudaFuncSetAttribute(k_prod_tc<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
     int clk_khz = 0;
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, 0);
-    long long budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * (long long)a.timeout_ms / 1000LL;
-    // 16-byte loads when every stage's two words are 16-byte aligned
-    const int vec16 = ((uintptr_t)a.X % 16 == 0 && a.stride % 2 == 0) ? 1 : 0;
-    k_prod_tc<CT><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(a.X, a.stride, a.n, a.W, TM, tiles, L, (CT*)a.C,
-                                                                a.ldc, a.err, budget, vec16);
-    a.launches += 1;
+    return (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * (long long)timeout_ms / 1000LL;
+}
+
+template <typename CT>
+cudaError_t launch(const TcJobs& P, int sms, u32* err, int timeout_ms, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_prod_tc<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    k_prod_tc<CT><<<(unsigned)sms, kThreads, kSmemBytes, st>>>(P, err, wait_budget(timeout_ms));
     return cudaGetLastError();
 }
 
+template <typename CT>
+cudaError_t run(ProductArgs& a, cudaStream_t st)
+{
+    const u64 nst = (a.W + kStageWords - 1) / kStageWords;
+    if (a.n == 0 || nst == 0) return cudaSuccess;
+    TcJobs* P = new TcJobs();
+    P->njobs = 1;
+    P->vec16 = ((uintptr_t)a.X % 16 == 0 && a.stride % 2 == 0) ? 1 : 0;
+    // chunk length: the window of L stages of all n rows (16 bytes per row
+    // per stage) is about 48 MiB, so it stays in L2 while every CTA reads it
+    u64 L = (48ull << 20) / (16ull * std::max<u64>(a.n, 1));
+    P->L = std::max<u64>(64, std::min<u64>(L, kMaxSegStages));
+    P->job[0] = TcJob{a.X, nullptr, a.C, a.stride, a.n, a.W, a.ldc};
+    // one persistent CTA per SM (fewer when there are fewer units)
+    u64 TM;
+    const u64 tiles = [&] { u64 t = 0, tm = (a.n + kM - 1) / kM, tn = (a.n + kN - 1) / kN;
+                            for (u64 j = 0; j < tn; ++j) t += std::min<u64>(tm, 2 * j + 2); TM = tm; return t; }();
+    (void)TM;
+    const int grid = (int)std::min<u64>((u64)a.sms, tiles * nst);
+    cudaError_t e = launch<CT>(*P, grid, a.err, a.timeout_ms, st);
+    delete P;
+    a.launches += 1;
+    return e;
+}
+
+}  // namespace
+
+cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, int count_bits, int sms, u32* err, int timeout_ms,
+                            cudaStream_t st, int* launches)
+{
+    for (int j0 = 0; j0 < njobs; j0 += kMaxJobs) {
+        TcJobs* P = new TcJobs();
+        const int m = std::min(kMaxJobs, njobs - j0);
+        P->njobs = (u32)m;
+        P->L = 0;
+        P->vec16 = 1;
+        for (int q = 0; q < m; ++q) {
+            const TcJobDesc& d = jobs[j0 + q];
+            P->job[q] = TcJob{d.X, d.Wdev, d.C, d.stride, d.n, d.W, d.ldc};
+            if ((uintptr_t)d.X % 16 != 0 || d.stride % 2 != 0) P->vec16 = 0;
+        }
+        cudaError_t e = count_bits == 64 ? launch<u64>(*P, sms, err, timeout_ms, st)
+                                         : launch<u32>(*P, sms, err, timeout_ms, st);
+        delete P;
+        if (e != cudaSuccess) return e;
+        if (launches) *launches += 1;
+    }
+    return cudaSuccess;
+}
+
+namespace {
 }  // namespace
 
 bool product_tc_supported(int device)

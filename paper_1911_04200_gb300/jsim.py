@@ -68,6 +68,9 @@ SIGNATURES = {
     "jsim_destroy": (None, [ctypes.c_void_p]),
     "jsim_all_pairs": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_int]),
+    "jsim_all_pairs_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_uint64,
+                                              ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                              ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
     "jsim_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, _u64p, ctypes.c_void_p,
                                  ctypes.c_int]),
@@ -256,6 +259,41 @@ class Context:
                                       MEM_DEVICE if dev_out else MEM_HOST)
         _check(rc, self._h)
         return C, sizes, J
+
+    def all_pairs_batched(self, collections, out_device=None, want_C=True, want_J=True, want_sizes=True):
+        """Independent collections [(offsets, ids), ...] in one call -> [(C, sizes, J), ...]."""
+        torch = _torch()
+        k = len(collections)
+        sets = (Sets * max(k, 1))()
+        keep = []
+        dev_in = None
+        for c, (off, ids) in enumerate(collections):
+            s, kp, is_dev = self._sets(off, ids)
+            sets[c] = s
+            keep.append(kp)
+            dev_in = is_dev if dev_in is None else dev_in
+        dev_out = bool(dev_in) if out_device is None else out_device
+        cdt_np = np.uint64 if self.count_bits == 64 else np.uint32
+        cdt_t = torch.uint64 if self.count_bits == 64 else torch.uint32
+        outs = []
+        for c in range(k):
+            n = sets[c].n
+            if dev_out:
+                d = torch.device("cuda", self.device)
+                outs.append((torch.empty((n, n), dtype=cdt_t, device=d) if want_C else None,
+                             torch.empty(n, dtype=torch.uint64, device=d) if want_sizes else None,
+                             torch.empty((n, n), dtype=torch.float64, device=d) if want_J else None))
+            else:
+                outs.append((np.empty((n, n), dtype=cdt_np) if want_C else None,
+                             np.empty(n, dtype=np.uint64) if want_sizes else None,
+                             np.empty((n, n), dtype=np.float64) if want_J else None))
+        arr = lambda q: (ctypes.c_void_p * max(k, 1))(*[self._ptr(o[q]) for o in outs])
+        Cp, Sp, Jp = arr(0), arr(1), arr(2)
+        self._order()
+        rc = self._lib.jsim_all_pairs_batched(self._h, sets, k, Cp if want_C else None, Sp if want_sizes else None,
+                                              Jp if want_J else None, MEM_DEVICE if dev_out else MEM_HOST)
+        _check(rc, self._h)
+        return outs
 
     def pack(self, offsets, ids, lo: int, width: int, want_filter=True, want_words=True, want_sizes=True,
              stride: int | None = None):
