@@ -242,6 +242,9 @@ extern "C" int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint
         for (u64 v : cl[c].hoff) sig = mix(sig, v);
         sig = mix(sig, (u64)(uintptr_t)cols[c].ids);
         sig = mix(sig, (u64)(uintptr_t)cols[c].offsets);
+        // a captured graph writes C and J through the pointers it saw
+        sig = mix(sig, (u64)(uintptr_t)(C ? C[c] : nullptr));
+        sig = mix(sig, (u64)(uintptr_t)(J ? J[c] : nullptr));
     }
     const bool use_graph = all_dev && dev_out;
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), ctx->stream));
@@ -259,6 +262,7 @@ extern "C" int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint
                 CK(cudaMemsetAsync(w.spool.p, 0, w.spool.bytes, ctx->stream));
                 for (u64 c = 0; c < k; ++c) {
                     Col& x = w.cols[c];
+                    CK(cudaMemsetAsync(flags.as<u64>() + 3 * c + 2, 0xff, 8, ctx->stream));
                     if (x.n == 0) continue;
                     Plan plan;
                     u64* pb = w.ppool.as<u64>() + x.p_off;

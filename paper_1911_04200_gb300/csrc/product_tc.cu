@@ -12,9 +12,10 @@
 //
 // Work: the tiles of C are 128 x 256 (128 rows on the A side, 256 on the B
 // side, both read from X) that touch the upper triangle; each tile's word
-// range is cut into stages of 128 bit-rows.  The (tile, stage) units are laid
-// out tile-major and one persistent CTA per SM takes an equal contiguous
-// share, split into segments at tile boundaries and at the exactness cap.
+// range is cut into stages of 128 bit-rows.  The (job, tile, stage) units of
+// all collections of a launch are laid out job-major, then tile-major, and
+// one persistent CTA per SM takes an equal contiguous share, split into
+// segments at tile boundaries and at the exactness cap.
 //
 // Roles inside a CTA (17 warps):
 //   warps 0-11  unpack: thread p owns row p of every stage (rows 0-127 A,
@@ -164,70 +165,32 @@ struct Seg {
     u64 tile, kst, len;
 };
 
-// The CTA's work.
-//
-// One job (an all-pairs call): the stage range of every tile is cut into
-// chunks of L stages; chunk k's units (tile, stage) are laid out tile-major
-// and CTA c takes the c-th of G equal contiguous shares.  Every CTA walks
-// the chunks in the same order and at the same pace, so at any time all CTAs
-// read the same window of L stages of every row (it stays in L2), and a CTA
-// meets the same one or two tiles in every chunk, so their accumulators
-// persist across chunks.
-//
-// Several jobs (independent collections in one launch): the units of all
-// jobs, job-major then tile-major, are split into G equal contiguous shares,
-// so small collections share a CTA and large ones spread over many.
+// The CTA's work: the units (job, tile, stage) of all jobs of the launch,
+// job-major then tile-major, are split into G equal contiguous shares, one
+// per persistent CTA; small collections share a CTA and large ones spread
+// over many.  A segment never exceeds the exactness cap.
 struct WorkIter {
     const JobInfo* ji;
     u32 njobs;
-    u64 L, G, c;
-    // one-job chunked state
-    u64 KC, k, Lk;
-    // shared state: current unit and end of the current range
     u64 u, uend;
     u32 j;
-    __device__ __forceinline__ void init(const JobInfo* ji_, u32 njobs_, u64 L_, u64 G_, u64 c_)
+    __device__ __forceinline__ void init(const JobInfo* ji_, u32 njobs_, u64 G, u64 c)
     {
-        ji = ji_; njobs = njobs_; L = L_; G = G_; c = c_;
-        j = 0;
-        if (njobs == 1 && L > 0) {
-            KC = (ji[0].nst + L - 1) / L;
-            k = ~0ull; u = uend = Lk = 0;
-        } else {
-            const u64 U = ji[njobs - 1].U0 + ji[njobs - 1].tiles * ji[njobs - 1].nst;
-            u = c * U / G;
-            uend = (c + 1) * U / G;
-            // job holding unit u: last j with U0 <= u
-            u32 lo = 0, hi = njobs - 1;
-            while (lo < hi) {
-                u32 mid = (lo + hi + 1) >> 1;
-                if (ji[mid].U0 <= u) lo = mid; else hi = mid - 1;
-            }
-            j = lo;
+        ji = ji_; njobs = njobs_;
+        const u64 U = ji[njobs - 1].U0 + ji[njobs - 1].tiles * ji[njobs - 1].nst;
+        u = c * U / G;
+        uend = (c + 1) * U / G;
+        // job holding unit u: last j with U0 <= u
+        u32 lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            u32 mid = (lo + hi + 1) >> 1;
+            if (ji[mid].U0 <= u) lo = mid; else hi = mid - 1;
         }
+        j = lo;
     }
     // next segment; false at the end
     __device__ __forceinline__ bool next(Seg& sg)
     {
-        if (njobs == 1 && L > 0) {
-            const u64 nst = ji[0].nst, tiles = ji[0].tiles;
-            while (u >= uend) {
-                k = (k == ~0ull) ? 0 : k + 1;
-                if (k >= KC) return false;
-                Lk = min(L, nst - k * L);
-                const u64 Uk = tiles * Lk;
-                u = c * Uk / G;
-                uend = (c + 1) * Uk / G;
-            }
-            sg.job = 0;
-            sg.tile = u / Lk;
-            const u64 s_in = u - sg.tile * Lk;
-            const u64 e = min(uend, (sg.tile + 1) * Lk);
-            sg.len = e - u;
-            sg.kst = k * L + s_in;
-            u = e;
-            return true;
-        }
         while (u < uend) {
             const JobInfo& J = ji[j];
             const u64 jend = J.U0 + J.tiles * J.nst;
@@ -236,7 +199,6 @@ struct WorkIter {
             sg.job = j;
             sg.tile = v / J.nst;
             sg.kst = v - sg.tile * J.nst;
-            // a segment never exceeds the exactness cap
             const u64 e = min(min(uend, J.U0 + (sg.tile + 1) * J.nst), u + kMaxSegStages);
             sg.len = e - u;
             u = e;
@@ -291,7 +253,6 @@ constexpr int kMaxJobs = 256;
 struct TcJobs {
     u32 njobs;
     int vec16;  // 16-byte loads are safe for every job
-    u64 L;      // chunk length for a single job (0: linear split)
     TcJob job[kMaxJobs];
 };
 
@@ -331,17 +292,7 @@ k_prod_tc(const __grid_constant__ TcJobs P, u32* err, long long budget)
             ji[j] = x;
         }
         // stages of this CTA
-        u64 T = 0;
-        if (njobs == 1 && P.L > 0) {
-            const u64 nst = ji[0].nst, L = P.L, KC = (nst + L - 1) / L;
-            for (u64 k = 0; k < KC; ++k) {
-                const u64 Uk = ji[0].tiles * min(L, nst - k * L);
-                T += (blockIdx.x + 1) * Uk / gridDim.x - blockIdx.x * Uk / gridDim.x;
-            }
-        } else {
-            T = (blockIdx.x + 1) * U / gridDim.x - blockIdx.x * U / gridDim.x;
-        }
-        s_T = T;
+        s_T = (blockIdx.x + 1) * U / gridDim.x - blockIdx.x * U / gridDim.x;
     }
     __syncthreads();
     const u64 T = s_T;
@@ -385,7 +336,7 @@ k_prod_tc(const __grid_constant__ TcJobs P, u32* err, long long budget)
         // position of the next fetch: the current segment's job, tile (first
         // row and column), stage, and stages left in it
         WorkIter fit;
-        fit.init(ji, njobs, P.L, gridDim.x, blockIdx.x);
+        fit.init(ji, njobs, gridDim.x, blockIdx.x);
         Seg fs;
         u64 f_key = ~0ull, f_kst = 0, f_left = 0, f_r0 = 0, f_c0 = 0, f_n = 0, f_W = 0, f_stride = 0;
         const u64* f_X = nullptr;
@@ -460,7 +411,7 @@ k_prod_tc(const __grid_constant__ TcJobs P, u32* err, long long budget)
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             WorkIter it;
-            it.init(ji, njobs, P.L, gridDim.x, blockIdx.x);
+            it.init(ji, njobs, gridDim.x, blockIdx.x);
             Slots sl;
             sl.init();
             u64 t = 0;
@@ -557,7 +508,7 @@ k_prod_tc(const __grid_constant__ TcJobs P, u32* err, long long budget)
             return true;
         };
         WorkIter it;
-        it.init(ji, njobs, P.L, gridDim.x, blockIdx.x);
+        it.init(ji, njobs, gridDim.x, blockIdx.x);
         Slots sl;
         sl.init();
         Seg sg;
@@ -617,31 +568,6 @@ cudaError_t launch(const TcJobs& P, int sms, u32* err, int timeout_ms, cudaStrea
     return cudaGetLastError();
 }
 
-template <typename CT>
-cudaError_t run(ProductArgs& a, cudaStream_t st)
-{
-    const u64 nst = (a.W + kStageWords - 1) / kStageWords;
-    if (a.n == 0 || nst == 0) return cudaSuccess;
-    TcJobs* P = new TcJobs();
-    P->njobs = 1;
-    P->vec16 = ((uintptr_t)a.X % 16 == 0 && a.stride % 2 == 0) ? 1 : 0;
-    // chunk length: the window of L stages of all n rows (16 bytes per row
-    // per stage) is about 48 MiB, so it stays in L2 while every CTA reads it
-    u64 L = (48ull << 20) / (16ull * std::max<u64>(a.n, 1));
-    P->L = std::max<u64>(64, std::min<u64>(L, kMaxSegStages));
-    P->job[0] = TcJob{a.X, nullptr, a.C, a.stride, a.n, a.W, a.ldc};
-    // one persistent CTA per SM (fewer when there are fewer units)
-    u64 TM;
-    const u64 tiles = [&] { u64 t = 0, tm = (a.n + kM - 1) / kM, tn = (a.n + kN - 1) / kN;
-                            for (u64 j = 0; j < tn; ++j) t += std::min<u64>(tm, 2 * j + 2); TM = tm; return t; }();
-    (void)TM;
-    const int grid = (int)std::min<u64>((u64)a.sms, tiles * nst);
-    cudaError_t e = launch<CT>(*P, grid, a.err, a.timeout_ms, st);
-    delete P;
-    a.launches += 1;
-    return e;
-}
-
 }  // namespace
 
 cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, int count_bits, int sms, u32* err, int timeout_ms,
@@ -651,7 +577,6 @@ cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, int count_bits, in
         TcJobs* P = new TcJobs();
         const int m = std::min(kMaxJobs, njobs - j0);
         P->njobs = (u32)m;
-        P->L = 0;
         P->vec16 = 1;
         for (int q = 0; q < m; ++q) {
             const TcJobDesc& d = jobs[j0 + q];
@@ -680,7 +605,10 @@ bool product_tc_supported(int device)
 
 cudaError_t product_tc(ProductArgs& a, cudaStream_t st)
 {
-    return a.count_bits == 64 ? run<u64>(a, st) : run<u32>(a, st);
+    if (a.n == 0 || a.W == 0) return cudaSuccess;
+    TcJobDesc d{a.X, a.Wdev, a.C, a.stride, a.n, a.W, a.ldc};
+    return product_tc_jobs(&d, 1, a.count_bits, a.sms, a.err, a.timeout_ms > 0 ? a.timeout_ms : 2000, st,
+                           &a.launches);
 }
 
 }  // namespace jsim
