@@ -69,6 +69,7 @@ struct ProductArgs {
 cudaError_t product_popc(ProductArgs& a, cudaStream_t st);
 cudaError_t product_mma(ProductArgs& a, int variant, cudaStream_t st);
 cudaError_t product_tc(ProductArgs& a, cudaStream_t st);
+cudaError_t product_tc_single(ProductArgs& a, cudaStream_t st);
 // Several independent collections in one persistent tcgen05 launch (up to
 // 256 per launch; more are launched in groups).  W is read from Wdev on the
 // device when Wdev is set (no host synchronisation), else taken from W.

@@ -605,10 +605,7 @@ bool product_tc_supported(int device)
 
 cudaError_t product_tc(ProductArgs& a, cudaStream_t st)
 {
-    if (a.n == 0 || a.W == 0) return cudaSuccess;
-    TcJobDesc d{a.X, a.Wdev, a.C, a.stride, a.n, a.W, a.ldc};
-    return product_tc_jobs(&d, 1, a.count_bits, a.sms, a.err, a.timeout_ms > 0 ? a.timeout_ms : 2000, st,
-                           &a.launches);
+    return product_tc_single(a, st);
 }
 
 }  // namespace jsim
