@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jsim", choices=["jsim", "reference"])
-    ap.add_argument("--workload", default="clade1024", choices=["clade1024", "ancestral64"])
+    ap.add_argument("--workload", default="clade1024", choices=["clade1024", "ancestral64", "batched200"])
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--batch-rows", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -242,6 +242,86 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args):
+    """200 independent collections (n ~ U{8..512}, log-normal sizes, clade
+    model): one jsim_all_pairs_batched call per step (persistent multi-
+    collection launch, CUDA-graph replay) against one jsim_all_pairs call per
+    collection, same device-resident inputs and outputs."""
+    import torch
+    from paper_1911_04200_gb300 import jsim, synth
+    dev = torch.device("cuda", 0)
+    median = float(os.environ.get("JSIM_BATCHED_MEDIAN", "2e4"))
+    cols = synth.batched_collections(median=median, lo=1e4, hi=5e6)
+    dcols = [(torch.from_numpy(o.view(np.int64)).to(dev), torch.from_numpy(i.view(np.int64)).to(dev)) for o, i in cols]
+    N = sum(int(o[-1]) for o, _ in cols)
+    ctx = jsim.Context(device=0, id_bits=32, profile=False)
+    outs = None
+
+    def batched_step():
+        nonlocal outs
+        return ctx.all_pairs_batched(dcols) if outs is None else ctx.all_pairs_batched(dcols)
+
+    # preallocated outputs so the captured graph is replayed every step
+    import ctypes
+    k = len(dcols)
+    Cs = [torch.empty((len(o) - 1, len(o) - 1), dtype=torch.uint32, device=dev) for o, _ in cols]
+    Ss = [torch.empty(len(o) - 1, dtype=torch.uint64, device=dev) for o, _ in cols]
+    Js = [torch.empty((len(o) - 1, len(o) - 1), dtype=torch.float64, device=dev) for o, _ in cols]
+    sets = (jsim.Sets * k)()
+    for c, (o, i) in enumerate(dcols):
+        sets[c] = jsim.Sets(len(cols[c][0]) - 1, o.data_ptr(), i.data_ptr() if i.numel() else None, jsim.MEM_DEVICE)
+    arr = lambda L: (ctypes.c_void_p * k)(*[t.data_ptr() for t in L])
+    Cp, Sp, Jp = arr(Cs), arr(Ss), arr(Js)
+    lib = jsim.load()
+
+    def call():
+        ctx._order()
+        rc = lib.jsim_all_pairs_batched(ctx._h, sets, k, Cp, Sp, Jp, jsim.MEM_DEVICE)
+        jsim._check(rc, ctx._h)
+        return ctx.stats()
+
+    for _ in range(args.warmup):
+        st = call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    bo = 0.0
+    for _ in range(args.steps):
+        st = call()
+        bo += st["bitops_dense"]
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / args.steps
+    variant = st["variant"]
+    # plain: one all-pairs call per collection
+    pctx = jsim.Context(device=0, id_bits=32)
+    plain_out = [(Cs[c], Ss[c], Js[c]) for c in range(k)]
+    for _ in range(1):
+        for c, (o, i) in enumerate(dcols):
+            pctx.all_pairs(o, i, out=plain_out[c])
+    torch.cuda.synchronize()
+    e0.record(pctx.stream)
+    for _ in range(args.steps):
+        for c, (o, i) in enumerate(dcols):
+            pctx.all_pairs(o, i, out=plain_out[c])
+    e1.record(pctx.stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1) / args.steps
+    bitops = bo / args.steps
+    line = {"metric": METRIC, "value": bitops / (ms_b * 1e-3) / 1e12, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
+            "config": {"workload": "batched200: 200 collections, n ~ U{8..512}, log-normal sizes median %.0e, "
+                                   "values in [0,2^32), ceil(n/32) clades" % median,
+                       "collections": k, "samples": sum(len(o) - 1 for o, _ in cols), "values": N,
+                       "variant": variant, "bitops_dense_per_step": bitops},
+            "plain": {"value": bitops / (ms_p * 1e-3) / 1e12, "ms_per_step": ms_p,
+                      "how": "one jsim_all_pairs call per collection (AUTO variant), same inputs/outputs"},
+            "speedup_vs_plain": ms_p / ms_b}
+    print(json.dumps(line))
+    return 0
+
+
 def run_jsim(args):
     import torch
     import torch.distributed as dist
@@ -361,6 +441,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched200":
+        return run_batched(args)
     return run_jsim(args)
 
 

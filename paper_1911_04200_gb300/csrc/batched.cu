@@ -40,6 +40,7 @@ struct Wave {
     std::vector<Col> cols;
     DevBuf xpool, cpool, spool, ppool, scal, ids_pool, off_pool;
     DevBuf bitmap, dir, bsum, boff, R;
+    DevBuf jobtab;          // tensor-core job table
     DevBuf cstage, jstage;  // host-output staging
     u64 max_mt = 0;
     int variant = JSIM_VARIANT_TC;
@@ -58,8 +59,23 @@ u64 mix(u64 h, u64 v)
     return h;
 }
 
+// the tensor-core job table of the wave (one entry per nonempty collection)
+std::vector<TcJobDesc> wave_jobs(Wave& w)
+{
+    std::vector<TcJobDesc> jobs;
+    u64* scal = w.scal.as<u64>();
+    for (size_t c = 0; c < w.cols.size(); ++c) {
+        const Col& cl = w.cols[c];
+        if (cl.empty || cl.n == 0) continue;
+        jobs.push_back(TcJobDesc{w.xpool.as<u64>() + cl.x_off, scal + 2 * c, (char*)w.cpool.p + cl.c_off,
+                                 cl.stride, cl.n, 0, cl.n});
+    }
+    return jobs;
+}
+
 // Launch sequence of one wave after validation: zero, ingest every batch of
-// every collection, product, epilogue.  No host synchronisation inside.
+// every collection, product, epilogue.  No host synchronisation inside; the
+// job table must already be in device memory.
 int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool dev_out, size_t first,
                  bool run_product_only, int variant, int word_bits)
 {
@@ -93,16 +109,11 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
     CK(cudaMemsetAsync(w.cpool.p, 0, w.cpool.bytes, st));
     // product: all collections
     if (variant == JSIM_VARIANT_TC) {
-        std::vector<TcJobDesc> jobs;
-        for (size_t c = 0; c < w.cols.size(); ++c) {
-            const Col& cl = w.cols[c];
-            if (cl.empty || cl.n == 0) continue;
-            jobs.push_back(TcJobDesc{w.xpool.as<u64>() + cl.x_off, scal + 2 * c, (char*)w.cpool.p + cl.c_off,
-                                     cl.stride, cl.n, 0, cl.n});
-        }
+        std::vector<TcJobDesc> jobs = wave_jobs(w);
         int launches = 0;
-        cudaError_t e = product_tc_jobs(jobs.data(), (int)jobs.size(), ctx->opt.count_bits, ctx->sms, ctx->d_err,
-                                        ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000, st, &launches);
+        cudaError_t e = product_tc_jobs(jobs.data(), (int)jobs.size(), w.jobtab.p, false, ctx->opt.count_bits,
+                                        ctx->sms, ctx->d_err, ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000,
+                                        st, &launches);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batched tcgen05 product");
         ctx->stats.product_launches += launches;
         ctx->stats.launches += launches;
@@ -413,6 +424,12 @@ replan:
         ALLOC(w.xpool, std::max<size_t>(x_tot, 1) * 8);
         ALLOC(w.cpool, std::max<size_t>(c_tot, 8));
         ALLOC(w.scal, 2 * sizeof(u64) * k);
+        ALLOC(w.jobtab, sizeof(TcJobDesc) * std::max<u64>(k, 1));
+        std::vector<TcJobDesc> jobs = wave_jobs(w);
+        if (!jobs.empty())
+            CK(cudaMemcpyAsync(w.jobtab.p, jobs.data(), sizeof(TcJobDesc) * jobs.size(), cudaMemcpyHostToDevice,
+                               ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
         if (!dev_out) {
             if (C) ALLOC(w.cstage, std::max<size_t>(cs_tot, 8));
             if (J) ALLOC(w.jstage, std::max<size_t>(js_tot, 8));
@@ -428,10 +445,9 @@ replan:
     jsim_tuning* tun = tuning_of(ctx);
     u64 shape = 0x77;
     for (auto& x : w.cols) shape = mix(shape, (x.n + 31) / 32 * 1000003 + (64 - __builtin_clzll(x.N | 1)));
-    bool tuned = false;
     if (variant == JSIM_VARIANT_AUTO) {
         for (auto& e : tun->entries)
-            if (e.first == shape) { variant = e.second.first; word_bits = e.second.second; tuned = true; }
+            if (e.first == shape) { variant = e.second.first; word_bits = e.second.second; }
     }
 
     // ---- ingest all collections (and tune the product on the packed words) ----
@@ -452,9 +468,7 @@ replan:
             if (ms < best) { best = ms; variant = cd.v; word_bits = cd.wb; }
         }
         tun->entries.push_back({shape, {variant, word_bits}});
-        tuned = true;
     }
-    (void)tuned;
     w.variant = variant;
     w.word_bits = word_bits;
     ctx->stats.variant = variant;

@@ -79,8 +79,11 @@ struct TcJobDesc {
     void* C;
     u64 stride, n, W, ldc;
 };
-cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, int count_bits, int sms, u32* err, int timeout_ms,
-                            cudaStream_t st, int* launches);
+// dev_table: device memory for njobs table entries (sizeof(TcJobDesc) each),
+// read by the kernels; with upload it is first written from `jobs`
+// (stream-ordered; not allowed while the stream is being captured).
+cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, void* dev_table, bool upload, int count_bits, int sms,
+                            u32* err, int timeout_ms, cudaStream_t st, int* launches);
 bool product_tc_supported(int device);
 
 // ---- epilogue.cu ---------------------------------------------------------------

@@ -37,6 +37,7 @@
 // budget, plus a CTA-wide abort flag); on time-out the CTA raises the error
 // word, waits (bounded) for its issued MMAs, frees its TMEM and leaves.
 #include <algorithm>
+#include <vector>
 #include "common.cuh"
 
 namespace jsim {
@@ -249,11 +250,11 @@ struct TcJob {
     u64 stride, n, W, ldc;
 };
 constexpr int kMaxJobs = 256;
-// Kernel parameter block (passed by value, < 32 KiB).
+// Kernel parameters: the job table lives in device memory.
 struct TcJobs {
+    const TcJob* job;
     u32 njobs;
     int vec16;  // 16-byte loads are safe for every job
-    TcJob job[kMaxJobs];
 };
 
 __device__ __forceinline__ u64 job_tiles(u64 n, u64& TM)
@@ -267,7 +268,7 @@ __device__ __forceinline__ u64 job_tiles(u64 n, u64& TM)
 
 template <typename CT>
 __global__ void __launch_bounds__(kThreads, 1)
-k_prod_tc(const __grid_constant__ TcJobs P, u32* err, long long budget)
+k_prod_tc(const TcJobs P, u32* err, long long budget)
 {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) u64 full_bar[kBufs], empty_bar[kBufs], accf_bar[2], acce_bar[2], done_bar;
@@ -570,22 +571,31 @@ cudaError_t launch(const TcJobs& P, int sms, u32* err, int timeout_ms, cudaStrea
 
 }  // namespace
 
-cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, int count_bits, int sms, u32* err, int timeout_ms,
-                            cudaStream_t st, int* launches)
+cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, void* dev_table, bool upload, int count_bits, int sms,
+                            u32* err, int timeout_ms, cudaStream_t st, int* launches)
 {
+    // the table of every job, copied once to device memory (dev_table holds
+    // njobs entries of TcJob); one launch per group of kMaxJobs jobs
+    static_assert(sizeof(TcJob) == sizeof(TcJobDesc), "table entry layout");
+    std::vector<TcJob> host((size_t)njobs);
+    int vec16 = 1;
+    for (int q = 0; q < njobs; ++q) {
+        const TcJobDesc& d = jobs[q];
+        host[q] = TcJob{d.X, d.Wdev, d.C, d.stride, d.n, d.W, d.ldc};
+        if ((uintptr_t)d.X % 16 != 0 || d.stride % 2 != 0) vec16 = 0;
+    }
+    if (njobs == 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (upload) {
+        e = cudaMemcpyAsync(dev_table, host.data(), sizeof(TcJob) * (size_t)njobs, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
     for (int j0 = 0; j0 < njobs; j0 += kMaxJobs) {
-        TcJobs* P = new TcJobs();
-        const int m = std::min(kMaxJobs, njobs - j0);
-        P->njobs = (u32)m;
-        P->vec16 = 1;
-        for (int q = 0; q < m; ++q) {
-            const TcJobDesc& d = jobs[j0 + q];
-            P->job[q] = TcJob{d.X, d.Wdev, d.C, d.stride, d.n, d.W, d.ldc};
-            if ((uintptr_t)d.X % 16 != 0 || d.stride % 2 != 0) P->vec16 = 0;
-        }
-        cudaError_t e = count_bits == 64 ? launch<u64>(*P, sms, err, timeout_ms, st)
-                                         : launch<u32>(*P, sms, err, timeout_ms, st);
-        delete P;
+        TcJobs P;
+        P.job = (const TcJob*)dev_table + j0;
+        P.njobs = (u32)std::min(kMaxJobs, njobs - j0);
+        P.vec16 = vec16;
+        e = count_bits == 64 ? launch<u64>(P, sms, err, timeout_ms, st) : launch<u32>(P, sms, err, timeout_ms, st);
         if (e != cudaSuccess) return e;
         if (launches) *launches += 1;
     }
