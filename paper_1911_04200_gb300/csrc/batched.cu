@@ -397,7 +397,14 @@ replan:
     for (auto& x : w.cols) {
         x.empty = x.N == 0;
         const u64 span = x.empty ? 0 : x.maxid - x.minid;
-        x.mt = ctx->opt.batch_rows ? ctx->opt.batch_rows : auto_batch_rows(span + 1 ? span + 1 : ~0ull);
+        // one row batch per collection when its filter bitmap fits in 512 MiB:
+        // a batched call is dominated by per-batch launches of small
+        // collections, not by the bitmap's L2 residency
+        u64 one = 64;
+        while (one < span + 1 && one < (1ull << 32)) one <<= 1;
+        const bool fits = span < (1ull << 32);
+        x.mt = ctx->opt.batch_rows ? ctx->opt.batch_rows
+                                   : (fits ? one : auto_batch_rows(span + 1 ? span + 1 : ~0ull));
         x.lo0 = x.empty ? 0 : x.minid / x.mt * x.mt;
         x.rounds = x.empty ? 0 : x.maxid / x.mt - x.minid / x.mt + 1;
         if (x.rounds > 4096) return JSIM_ERR_UNSUPPORTED;  // value span too wide for one batched plan
