@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jsim", choices=["jsim", "reference"])
-    ap.add_argument("--workload", default="clade1024", choices=["clade1024", "ancestral64", "batched200"])
+    ap.add_argument("--workload", default="clade1024",
+                    choices=["clade1024", "ancestral64", "batched200", "stream4096"])
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--batch-rows", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -255,12 +256,6 @@ def run_batched(args):
     dcols = [(torch.from_numpy(o.view(np.int64)).to(dev), torch.from_numpy(i.view(np.int64)).to(dev)) for o, i in cols]
     N = sum(int(o[-1]) for o, _ in cols)
     ctx = jsim.Context(device=0, id_bits=32, profile=False)
-    outs = None
-
-    def batched_step():
-        nonlocal outs
-        return ctx.all_pairs_batched(dcols) if outs is None else ctx.all_pairs_batched(dcols)
-
     # preallocated outputs so the captured graph is replayed every step
     import ctypes
     k = len(dcols)
@@ -319,6 +314,79 @@ def run_batched(args):
                       "how": "one jsim_all_pairs call per collection (AUTO variant), same inputs/outputs"},
             "speedup_vs_plain": ms_p / ms_b}
     print(json.dumps(line))
+    return 0
+
+
+def run_streamed(args):
+    """The 4096-sample clade recipe over [0, 2^40) in (pageable) host memory,
+    64-bit counts, row batches of 2^26 values: one jsim_all_pairs_streamed
+    call per step (super-batches gathered into two pinned staging buffers,
+    copies on a second stream overlapping the product) against one plain
+    jsim_all_pairs call on the same host input (one copy of all values, then
+    the batch loop).  Both write C, sizes and J to host memory; both are
+    timed on the wall clock around the call, which returns after its last
+    copy."""
+    import torch
+    from paper_1911_04200_gb300 import jsim, synth
+    median = float(os.environ.get("JSIM_STREAM_MEDIAN", "2e5"))
+    staging = int(os.environ.get("JSIM_STREAM_STAGING", str(1 << 30)))
+    br = args.batch_rows or (1 << 26)
+    off, ids = synth.clade4096(median=median)
+    n = len(off) - 1
+    N = int(off[-1])
+    hC = torch.empty((n, n), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    hS = torch.empty(n, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    hJ = torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy()
+    ctx = jsim.Context(device=0, variant=args.variant, batch_rows=br, count_bits=64, id_bits=40, profile=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        agg = {"ms_product": 0.0, "product_launches": 0, "launches": 0, "bitops": 0.0}
+        for _ in range(args.steps):
+            fn()
+            st = ctx.stats()
+            agg["ms_product"] += st["ms_product"]
+            agg["product_launches"] += st["product_launches"]
+            agg["launches"] += st["launches"]
+            agg["bitops"] += st["bitops_dense"]
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / args.steps, st, agg
+
+    with Clocks(0) as clk:
+        dt_s, st_s, agg = timed(lambda: ctx.all_pairs_streamed(off, ids, staging_bytes=staging, out=(hC, hS, hJ)))
+    J_s = hJ.copy()
+    dt_p, st_p, _ = timed(lambda: ctx.all_pairs(off, ids, out=(hC, hS, hJ)))
+    assert np.array_equal(J_s.view(np.uint64), hJ.view(np.uint64)), "streamed and plain results differ"
+    bitops = st_s["bitops_dense"]
+    variant = st_s["variant"]
+    roof = roofline_for(variant, agg["bitops"] / max(1, agg["product_launches"]),
+                        agg["ms_product"] / max(1, agg["product_launches"]), measured_peaks(),
+                        traffic_from_profiles(variant, "stream4096"))
+    stages = ("ms_h2d", "ms_validate", "ms_filter", "ms_scan", "ms_pack", "ms_product", "ms_epilogue", "ms_d2h")
+    line = {"metric": METRIC, "value": bitops / dt_s / 1e12, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64 ids, u64 counts, f64 J", "data": "synthetic",
+            "config": {"workload": "stream4096: n=4096, values in [0,2^40), log-normal sizes median %.0e "
+                                   "(x/10-10x), 64 clades, 30%% core, 0-40%% substitution" % median,
+                       "values": N, "host_bytes": N * 8, "staging_bytes": staging, "batch_rows": br,
+                       "batches": st_s["batches"], "words": st_s["words"], "rows_nonzero": st_s["rows_nonzero"],
+                       "variant": variant, "bitops_dense_per_step": bitops,
+                       "product_launches": st_s["product_launches"],
+                       "h2d_gbs_effective": N * 8 / dt_s / 1e9,
+                       "stage_ms": {k: round(st_s[k], 3) for k in stages},
+                       "l2": "inputs (%.1f GB) larger than L2 (129 MB); no flush" % (N * 8 / 1e9)},
+            "clocks": clk.summary(), "gpu_launches": agg["launches"], "roofline": roof,
+            "e2e": {"value": bitops / dt_s / 1e12, "unit": UNIT, "h2d_bytes_per_step": int(N * 8 + (n + 1) * 8),
+                    "d2h_bytes_per_step": int(n * n * 16 + n * 8)},
+            "plain": {"value": bitops / dt_p / 1e12, "ms_per_step": dt_p * 1e3, "batches": st_p["batches"],
+                      "how": "one jsim_all_pairs call on the same pageable host input and host outputs",
+                      "stage_ms": {k: round(st_p[k], 3) for k in stages}},
+            "speedup_vs_plain": dt_p / dt_s}
+    print(json.dumps(line))
+    ctx.close()
     return 0
 
 
@@ -443,6 +511,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched200":
         return run_batched(args)
+    if args.workload == "stream4096":
+        return run_streamed(args)
     return run_jsim(args)
 
 

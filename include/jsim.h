@@ -178,6 +178,32 @@ JSIM_API int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint64
                                     uint64_t* const* sizes, double* const* J, int out_mem);
 
 /*
+ * All-pairs similarity of one collection held in host memory, streamed to
+ * the device in pieces (the batch loop of Sec. III-B, Eq. 3 and Eq. 4, for
+ * inputs that do not fit in device memory).  Results are those of
+ * jsim_all_pairs, bit for bit.
+ *   sets          host memory only (JSIM_ERR_ARG otherwise); caller-owned,
+ *                 read (never written) during the call
+ *   C, sizes, J, out_mem   as jsim_all_pairs
+ *   staging_bytes size of each of two pinned host staging buffers (>= 1 MiB);
+ *                 the device holds two value buffers of at most this size,
+ *                 filter bitmaps of at most twice it, and the packed matrix
+ *                 of one super-batch
+ * Execution: the value range is cut into super-batches of whole row batches
+ * (m~ = batch_rows, or the automatic choice) whose values fit the staging;
+ * each super-batch is filtered, ranked and packed as one batch (C is additive
+ * over any partition of the rows, Eq. 4), so m~ only sets where super-batches
+ * may begin and end.  While the device multiplies super-batch g, the host
+ * gathers super-batch g+1 into the other pinned buffer and a second stream
+ * copies it, so host->device traffic overlaps the product.  The pinned
+ * buffers are kept by the context for later calls (freed by jsim_destroy).
+ * Errors: as jsim_all_pairs, plus JSIM_ERR_OOM when a single row batch holds
+ * more values than the staging (lower batch_rows or raise staging_bytes).
+ */
+JSIM_API int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes, double* J,
+                                     int out_mem, uint64_t staging_bytes);
+
+/*
  * One row batch of the method, for inspection and step-level testing
  * (Eq. 5, Eq. 6 and the bitmask compression before Eq. 7): the values of
  * each sample in [lo, lo + width) become packed words.

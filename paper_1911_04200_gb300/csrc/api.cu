@@ -145,6 +145,7 @@ void jsim_destroy(jsim_ctx* ctx)
     cudaSetDevice(ctx->opt.device);
     cudaStreamSynchronize(ctx->stream);
     jsim_batched_release(ctx);
+    jsim_streamed_release(ctx);
     if (ctx->d_err) ctx->opt.free(ctx->d_err, 256, (void*)ctx->stream, ctx->opt.alloc_user);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);

@@ -12,6 +12,9 @@ using namespace jsim;
 struct jsim_ctx;
 // releases the batched-call state (captured graphs and buffers) of a context
 void jsim_batched_release(jsim_ctx* ctx);
+// releases the streamed-call state (pinned staging, copy stream) of a context
+void jsim_streamed_release(jsim_ctx* ctx);
+struct StreamState;
 
 struct jsim_ctx {
     jsim_options opt;
@@ -31,6 +34,8 @@ struct jsim_ctx {
     size_t events_used = 0;
     struct Pending { cudaEvent_t a, b; double* acc; };
     std::vector<Pending> pending;
+    // streamed calls: pinned staging buffers kept between calls
+    StreamState* streamed = nullptr;
 };
 
 namespace {

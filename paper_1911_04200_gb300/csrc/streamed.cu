@@ -1,0 +1,413 @@
+// Streamed all-pairs for inputs held in host memory that are too large to
+// copy to the device at once (the batch loop of Sec. III-B, Eq. 3 and Eq. 4,
+// with each batch's values brought over from host memory as it is needed).
+//
+// The value range is cut into super-batches: runs of consecutive row batches
+// (aligned to m~) whose values fit one pinned staging buffer and whose filter
+// bitmaps fit a device budget.  Two staging buffers and two device buffers
+// alternate:
+//   host:    gather super-batch g+1's values (one contiguous slice of each
+//            sample, found by binary search) into pinned staging, with
+//            several host threads, while the device multiplies g;
+//   copy:    on a second stream, staging -> device buffer, once the device
+//            has finished reading that buffer (two super-batches back);
+//   compute: validate the slice (distinct counts accumulate: equal values
+//            never straddle a boundary); filter and rank-scan the whole
+//            super-batch as one batch of the method (Eq. 5, Eq. 6); one
+//            synchronisation learns its row count; pack it; one product
+//            launch adds its AND+popcount counts into C (Eq. 7, Eq. 4).
+// C is accumulated over all super-batches; the epilogue runs once.
+//
+// Sortedness is checked in two places: on the device inside every slice,
+// and on the host across slices (every sample's slices must tile it).  Both
+// together imply that every sample is sorted, because a binary search that
+// cuts a sample at position q has seen a[q-1] < boundary <= a[q].
+#include <thread>
+#include "ctx.cuh"
+
+struct StreamState {
+    int device = -1;
+    cudaStream_t xs = nullptr;  // copy stream
+    u64* pin[2] = {nullptr, nullptr};
+    size_t pin_words = 0;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, released[2] = {nullptr, nullptr};
+};
+
+void jsim_streamed_release(jsim_ctx* ctx)
+{
+    StreamState* s = ctx->streamed;
+    if (!s) return;
+    if (s->xs) cudaStreamSynchronize(s->xs);
+    for (int k = 0; k < 2; ++k) {
+        if (s->pin[k]) cudaFreeHost(s->pin[k]);
+        if (s->copied[k]) cudaEventDestroy(s->copied[k]);
+        if (s->released[k]) cudaEventDestroy(s->released[k]);
+    }
+    if (s->xs) cudaStreamDestroy(s->xs);
+    cudaGetLastError();
+    delete s;
+    ctx->streamed = nullptr;
+}
+
+namespace {
+
+// pinned staging of at least `words` u64 each, a copy stream and events
+int stream_state(jsim_ctx* ctx, size_t words, StreamState*& out)
+{
+    if (!ctx->streamed) {
+        StreamState* s = new StreamState;
+        s->device = ctx->opt.device;
+        ctx->streamed = s;
+        CK(cudaStreamCreateWithFlags(&s->xs, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            CK(cudaEventCreateWithFlags(&s->copied[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&s->released[k], cudaEventDisableTiming));
+        }
+    }
+    StreamState* s = ctx->streamed;
+    if (s->pin_words < words) {
+        CK(cudaStreamSynchronize(s->xs));
+        for (int k = 0; k < 2; ++k) {
+            if (s->pin[k]) cudaFreeHost(s->pin[k]);
+            s->pin[k] = nullptr;
+        }
+        s->pin_words = 0;
+        for (int k = 0; k < 2; ++k) CK(cudaMallocHost((void**)&s->pin[k], words * sizeof(u64)));
+        s->pin_words = words;
+    }
+    out = s;
+    return JSIM_OK;
+}
+
+// first position in [lo, hi) of a sorted array with value >= v
+u64 lower_bound_host(const uint64_t* a, u64 lo, u64 hi, u64 v)
+{
+    while (lo < hi) {
+        u64 mid = lo + (hi - lo) / 2;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+struct Super {
+    u64 b0 = 0, b1 = 0;  // row batches [b0, b1)
+    u64 count = 0;       // values in the super-batch
+    std::vector<u64> beg, len, off;  // per sample: slice start, length, staging offset
+};
+
+// Per-sample slices of the values in [lo, hi) (hi == 0: unbounded above).
+void slice(const std::vector<u64>& hoff, const uint64_t* ids, u64 n, u64 lo, u64 hi, Super& s)
+{
+    s.beg.resize(n);
+    s.len.resize(n);
+    s.off.resize(n + 1);
+    u64 acc = 0;
+    for (u64 i = 0; i < n; ++i) {
+        const u64 a = hoff[i], b = hoff[i + 1];
+        const u64 p = lower_bound_host(ids, a, b, lo);
+        const u64 q = hi == 0 ? b : lower_bound_host(ids, p, b, hi);
+        s.beg[i] = p;
+        s.len[i] = q - p;
+        s.off[i] = acc;
+        acc += q - p;
+    }
+    s.off[n] = acc;
+    s.count = acc;
+}
+
+// Cut [min value, max value] into super-batches of at most `cap_vals` values
+// and `rb_cap` row batches of `mt` rows each; ranges without values are
+// skipped.  Returns JSIM_ERR_UNSORTED when the slices do not tile every
+// sample (the input is not sorted), JSIM_ERR_OOM when one row batch alone
+// holds more values than the staging.
+int plan_supers(const std::vector<u64>& hoff, const uint64_t* ids, u64 n, u64 mt, u64 cap_vals, u64 rb_cap,
+                std::vector<Super>& out)
+{
+    u64 minid = ~0ull, maxid = 0;
+    for (u64 i = 0; i < n; ++i) {
+        const u64 a = hoff[i], b = hoff[i + 1];
+        if (b == a) continue;
+        if (ids[a] > ids[b - 1]) return JSIM_ERR_UNSORTED;
+        minid = std::min<u64>(minid, ids[a]);
+        maxid = std::max<u64>(maxid, ids[b - 1]);
+    }
+    const u64 N = hoff[n];
+    if (N == 0) return JSIM_OK;
+    const u64 first = minid / mt, last = maxid / mt;
+    // row batches per super-batch from the average density, 25 % headroom
+    const double per_d = (double)cap_vals / ((double)N / (double)(last - first + 1)) / 1.25;
+    const u64 per0 = per_d >= (double)rb_cap ? rb_cap : std::max<u64>(1, (u64)per_d);
+    std::vector<u64> pos(hoff.begin(), hoff.end() - 1);
+    u64 b = first, per = per0;
+    for (;;) {
+        const u64 e = std::min(last + 1, b + per);
+        Super s;
+        s.b0 = b;
+        s.b1 = e;
+        slice(hoff, ids, n, b * mt, e * mt, s);  // e * mt wraps to 0 only at the top of the range
+        if (s.count > cap_vals) {
+            if (e - b == 1) return JSIM_ERR_OOM;
+            per = (e - b) / 2;
+            continue;
+        }
+        u64 maxv = 0;
+        for (u64 i = 0; i < n; ++i) {
+            if (s.beg[i] != pos[i]) return JSIM_ERR_UNSORTED;
+            pos[i] += s.len[i];
+            if (s.len[i]) maxv = std::max<u64>(maxv, ids[s.beg[i] + s.len[i] - 1]);
+        }
+        if (s.count) s.b1 = std::max(b + 1, std::min(e, maxv / mt + 1));  // drop empty trailing row batches
+        // first value at or above the range, to skip empty row batches
+        u64 nv = ~0ull;
+        bool more = false;
+        if (e <= last)
+            for (u64 i = 0; i < n; ++i) {
+                const u64 q = s.beg[i] + s.len[i];
+                if (q < hoff[i + 1]) { more = true; nv = std::min<u64>(nv, ids[q]); }
+            }
+        if (s.count) out.push_back(std::move(s));
+        if (!more) break;
+        b = std::max(e, nv / mt);
+        per = per0;
+    }
+    for (u64 i = 0; i < n; ++i)
+        if (pos[i] != hoff[i + 1]) return JSIM_ERR_UNSORTED;
+    return JSIM_OK;
+}
+
+// gather a super-batch's slices into `dst` (pinned) with several host threads
+void gather(const uint64_t* ids, const Super& s, u64* dst)
+{
+    const u64 n = s.beg.size();
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (s.count < (1u << 20)) nt = 1;
+    auto work = [&](unsigned t) {
+        for (u64 i = t; i < n; i += nt)
+            if (s.len[i]) memcpy(dst + s.off[i], ids + s.beg[i], s.len[i] * sizeof(u64));
+    };
+    if (nt == 1) { work(0); return; }
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+}
+
+// waits for the copy stream before device buffers that its copies may still
+// write are released (declared after them, so destroyed first)
+struct CopyFence {
+    cudaStream_t xs;
+    ~CopyFence()
+    {
+        if (xs) cudaStreamSynchronize(xs);
+    }
+};
+
+}  // namespace
+
+extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes, double* J,
+                                       int out_mem, uint64_t staging_bytes)
+{
+    if (!ctx) return JSIM_ERR_ARG;
+    int rc = check_sets(sets);
+    if (rc) return rc;
+    if (sets->mem != JSIM_MEM_HOST) return JSIM_ERR_ARG;  // streaming reads host memory
+    if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
+    if (staging_bytes < (1u << 20)) return JSIM_ERR_ARG;
+    CK(cudaSetDevice(ctx->opt.device));
+    CallScope scope(ctx);
+    StageTimer total(ctx, &ctx->stats.ms_total);
+    const u64 n = sets->n;
+    if (n == 0) return JSIM_OK;
+    if (n > (1ull << 20)) return JSIM_ERR_ARG;
+    std::vector<u64> hoff;
+    rc = load_offsets(ctx, sets, hoff);
+    if (rc) return rc;
+    const u64 N = hoff[n];
+    const uint64_t* ids = sets->ids;
+    const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
+    const u64 cap_vals = staging_bytes / sizeof(u64);
+    const u64 head = round_up(n + 1, 32);  // staging: offsets, then values at a 256-byte boundary
+
+    // value range of the call (samples sorted: first and last values)
+    u64 minid = ~0ull, maxid = 0;
+    for (u64 i = 0; i < n; ++i)
+        if (hoff[i + 1] > hoff[i]) {
+            minid = std::min<u64>(minid, ids[hoff[i]]);
+            maxid = std::max<u64>(maxid, ids[hoff[i + 1] - 1]);
+        }
+    const u64 span = N && maxid >= minid ? maxid - minid : 0;
+    u64 mt = ctx->opt.batch_rows;
+    if (!mt) {
+        // the automatic batch, halved until a row batch of average density
+        // fills at most a quarter of the staging
+        mt = auto_batch_rows(span + 1 ? span + 1 : ~0ull);
+        const double dens = (double)N / ((double)span + 1.0);
+        while (mt > 64 && dens * (double)mt > (double)cap_vals / 4) mt >>= 1;
+    }
+    ctx->stats.batch_rows = mt;
+    // per row batch of the super-batch: bitmap (m~/8 B), rank directory
+    // (m~/16 B) and block offsets; at most twice the staging in total
+    const u64 nwords = mt / 64;
+    const u64 rb_bytes = nwords * 12 + (nwords + kScanBlockWords - 1) / kScanBlockWords * 16;
+    const u64 rb_cap = std::max<u64>(1, std::min<u64>(2 * staging_bytes / rb_bytes, 1u << 16));
+    std::vector<Super> sup;
+    rc = plan_supers(hoff, ids, n, mt, cap_vals, rb_cap, sup);
+    if (rc) return rc;
+
+    // ---- buffers ----
+    StreamState* ss = nullptr;
+    rc = stream_state(ctx, head + cap_vals, ss);
+    if (rc) return rc;
+    cudaStream_t cs = ctx->stream, xs = ss->xs;
+    u64 rb_max = 1, count_max = 0;
+    for (auto& s : sup) {
+        rb_max = std::max<u64>(rb_max, s.b1 - s.b0);
+        count_max = std::max<u64>(count_max, s.count);
+    }
+    const u64 nw_max = rb_max * nwords;  // bitmap words of the widest super-batch
+    const u64 nbk_max = std::max<u64>((nw_max + kScanBlockWords - 1) / kScanBlockWords, 1);
+    DevBuf dbuf[2], Cacc, sizes_d, flags, plan_buf, X, bm, dir, bsum, boff, Rd, Cst, Jst;
+    ALLOC(dbuf[0], (head + count_max) * sizeof(u64));
+    ALLOC(dbuf[1], (head + count_max) * sizeof(u64));
+    CopyFence fence{xs};
+    ALLOC(Cacc, n * n * cb);
+    ALLOC(sizes_d, n * sizeof(u64));
+    ALLOC(flags, 3 * sizeof(u64));
+    ALLOC(plan_buf, (3 * n + 5) * sizeof(u64));
+    ALLOC(bm, nw_max * sizeof(u64));
+    ALLOC(dir, nw_max * sizeof(u32));
+    ALLOC(bsum, nbk_max * sizeof(u64));
+    ALLOC(boff, nbk_max * sizeof(u64));
+    ALLOC(Rd, sizeof(u64));
+    CK(cudaMemsetAsync(Cacc.p, 0, n * n * cb, cs));
+    CK(cudaMemsetAsync(sizes_d.p, 0, n * sizeof(u64), cs));
+    CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(u64), cs));
+    CK(cudaMemsetAsync(flags.as<u64>() + 2, 0xff, sizeof(u64), cs));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), cs));
+    const Plan plan = carve_plan(plan_buf, n);
+    const u64 n_pad = round_up(n, kRowPad);
+
+    // copy super-batch g into device buffer g & 1 once the device has read
+    // what that buffer held two super-batches earlier
+    auto stage = [&](size_t g) -> int {
+        const int k = (int)(g & 1);
+        const Super& s = sup[g];
+        memcpy(ss->pin[k], s.off.data(), (n + 1) * sizeof(u64));
+        gather(ids, s, ss->pin[k] + head);
+        CK(cudaStreamWaitEvent(xs, ss->released[k], 0));
+        cudaEvent_t a = nullptr;
+        if (ctx->opt.profile && (a = take_event(ctx))) cudaEventRecord(a, xs);
+        CK(cudaMemcpyAsync(dbuf[k].p, ss->pin[k], (head + s.count) * sizeof(u64), cudaMemcpyHostToDevice, xs));
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            if (b) {
+                cudaEventRecord(b, xs);
+                ctx->pending.push_back({a, b, &ctx->stats.ms_h2d});
+            }
+        }
+        CK(cudaEventRecord(ss->copied[k], xs));
+        return JSIM_OK;
+    };
+    for (int k = 0; k < 2; ++k) CK(cudaEventRecord(ss->released[k], cs));
+    if (!sup.empty()) {
+        rc = stage(0);
+        if (rc) return rc;
+    }
+    // Every super-batch is one batch of the method (Eq. 3) spanning its row
+    // batches: one filter, one rank scan and one pack over [lo, lo + width).
+    // C is additive over any partition of the rows (Eq. 4), so grouping row
+    // batches changes no count; it only packs fewer, longer rows.
+    for (size_t g = 0; g < sup.size(); ++g) {
+        const int k = (int)(g & 1);
+        const Super& s = sup[g];
+        const u64* d_off = dbuf[k].as<u64>();
+        const u64* d_ids = dbuf[k].as<u64>() + head;
+        const u64 max_chunks = s.count / kChunk + n + 1;
+        const u64 lo = s.b0 * mt, width = (s.b1 - s.b0) * mt, nw = width / 64;
+        CK(cudaStreamWaitEvent(cs, ss->copied[k], 0));
+        {
+            // the plan covers every value of the slice, all inside [lo, lo + width)
+            StageTimer t(ctx, &ctx->stats.ms_validate);
+            CK(launch_plan(d_off, d_ids, n, 0, 0, true, plan, cs));
+            CK(launch_validate(d_off, d_ids, n, plan, max_chunks, ctx->opt.id_bits, sizes_d.as<u64>(),
+                               flags.as<u32>(), flags.as<u64>() + 1, flags.as<u64>() + 2, ctx->sms, cs));
+            ctx->stats.launches += 2;
+        }
+        {
+            StageTimer t(ctx, &ctx->stats.ms_filter);
+            CK(cudaMemsetAsync(bm.p, 0, nw * sizeof(u64), cs));
+            CK(launch_filter(d_ids, n, plan, max_chunks, lo, width, bm.as<u32>(), ctx->sms, cs));
+            ctx->stats.launches += 1;
+        }
+        {
+            StageTimer t(ctx, &ctx->stats.ms_scan);
+            CK(launch_scan(bm.as<u64>(), nw, dir.as<u32>(), bsum.as<u64>(), boff.as<u64>(), Rd.as<u64>(), cs));
+            ctx->stats.launches += 2;
+        }
+        CK(cudaMemcpyAsync(ctx->h_scalars, Rd.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
+        CK(cudaStreamSynchronize(cs));
+        const u64 R = ctx->h_scalars[0], W = (R + 63) / 64;
+        ctx->stats.rows_nonzero += R;
+        ctx->stats.batches += R != 0;
+        const u64 stride = round_up(W, kWordPad);
+        if (W) {
+            ALLOC(X, n_pad * stride * sizeof(u64));
+            StageTimer t(ctx, &ctx->stats.ms_pack);
+            CK(launch_zero_rows(X.as<u64>(), n_pad, stride, stride, ctx->sms, cs));
+            CK(launch_pack(d_ids, n, plan, max_chunks, lo, width, bm.as<u64>(), dir.as<u32>(), boff.as<u64>(),
+                           X.as<u64>(), stride, nullptr, ctx->sms, cs));
+            ctx->stats.launches += 2;
+        }
+        CK(cudaEventRecord(ss->released[k], cs));  // the slice's values are no longer read
+        if (W) {
+            const int v = ctx->opt.variant == JSIM_VARIANT_AUTO ? choose_variant(ctx, n, W) : ctx->opt.variant;
+            StageTimer t(ctx, &ctx->stats.ms_product);
+            rc = run_product(ctx, v, X.as<u64>(), stride, n, W, Cacc.p);
+            if (rc) return rc;
+            ctx->stats.words += W;
+            ctx->stats.bitops_dense += 64.0 * (double)W * (double)n * (double)(n + 1) / 2.0;
+        }
+        // the next super-batch is gathered and copied while this one multiplies
+        if (g + 1 < sup.size()) {
+            rc = stage(g + 1);
+            if (rc) return rc;
+        }
+    }
+
+    // ---- input errors, epilogue ----
+    CK(cudaMemcpyAsync(ctx->h_scalars, flags.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
+    std::vector<u64> hs(n);
+    CK(cudaMemcpyAsync(hs.data(), sizes_d.p, n * sizeof(u64), cudaMemcpyDeviceToHost, cs));
+    CK(cudaStreamSynchronize(cs));
+    const u32 f = (u32)ctx->h_scalars[0];
+    if (f & kFlagUnsorted) return JSIM_ERR_UNSORTED;
+    if (f & kFlagIdRange) return JSIM_ERR_ID_RANGE;
+    if (ctx->opt.count_bits == 32)
+        for (u64 v : hs)
+            if (v > 0xffffffffull) return JSIM_ERR_OVERFLOW;
+    void* Cdst = C;
+    double* Jdst = J;
+    if (out_mem == JSIM_MEM_HOST) {
+        if (C) { ALLOC(Cst, n * n * cb); Cdst = Cst.p; }
+        if (J) { ALLOC(Jst, n * n * sizeof(double)); Jdst = Jst.as<double>(); }
+    }
+    {
+        StageTimer t(ctx, &ctx->stats.ms_epilogue);
+        if (Cdst || Jdst) {
+            CK(launch_epilogue(Cacc.p, n, ctx->opt.count_bits, sizes_d.as<u64>(), Cdst, Jdst, cs));
+            ctx->stats.launches += 1;
+        }
+    }
+    {
+        StageTimer t(ctx, &ctx->stats.ms_d2h);
+        const cudaMemcpyKind kind = out_mem == JSIM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        if (out_mem == JSIM_MEM_HOST) {
+            if (C) CK(cudaMemcpyAsync(C, Cst.p, n * n * cb, kind, cs));
+            if (J) CK(cudaMemcpyAsync(J, Jst.p, n * n * sizeof(double), kind, cs));
+        }
+        if (sizes) CK(cudaMemcpyAsync(sizes, sizes_d.p, n * sizeof(u64), kind, cs));
+    }
+    CK(cudaMemcpyAsync(ctx->h_scalars, ctx->d_err, sizeof(u32), cudaMemcpyDeviceToHost, cs));
+    CK(cudaStreamSynchronize(cs));
+    if ((u32)ctx->h_scalars[0] != 0) return JSIM_ERR_TIMEOUT;
+    return JSIM_OK;
+}

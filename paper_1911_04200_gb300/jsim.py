@@ -71,6 +71,8 @@ SIGNATURES = {
     "jsim_all_pairs_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_uint64,
                                               ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                               ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
+    "jsim_all_pairs_streamed": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64]),
     "jsim_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, _u64p, ctypes.c_void_p,
                                  ctypes.c_int]),
@@ -237,26 +239,41 @@ class Context:
         tensors give CUDA tensor outputs.  ``out`` may pass preallocated
         (C, sizes, J) buffers of the right kind.
         """
-        torch = _torch()
         s, keep, is_dev = self._sets(offsets, ids)
-        n = s.n
         dev_out = is_dev if out_device is None else out_device
-        cdt_np = np.uint64 if self.count_bits == 64 else np.uint32
-        cdt_t = torch.uint64 if self.count_bits == 64 else torch.uint32
-        if out is not None:
-            C, sizes, J = out
-        elif dev_out:
-            d = torch.device("cuda", self.device)
-            C = torch.empty((n, n), dtype=cdt_t, device=d) if want_C else None
-            sizes = torch.empty(n, dtype=torch.uint64, device=d) if want_sizes else None
-            J = torch.empty((n, n), dtype=torch.float64, device=d) if want_J else None
-        else:
-            C = np.empty((n, n), dtype=cdt_np) if want_C else None
-            sizes = np.empty(n, dtype=np.uint64) if want_sizes else None
-            J = np.empty((n, n), dtype=np.float64) if want_J else None
+        C, sizes, J = out if out is not None else self._outputs(s.n, dev_out, want_C, want_sizes, want_J)
         self._order()
         rc = self._lib.jsim_all_pairs(self._h, ctypes.byref(s), self._ptr(C), self._ptr(sizes), self._ptr(J),
                                       MEM_DEVICE if dev_out else MEM_HOST)
+        _check(rc, self._h)
+        return C, sizes, J
+
+    def _outputs(self, n, dev_out, want_C, want_sizes, want_J):
+        torch = _torch()
+        if dev_out:
+            d = torch.device("cuda", self.device)
+            cdt = torch.uint64 if self.count_bits == 64 else torch.uint32
+            return (torch.empty((n, n), dtype=cdt, device=d) if want_C else None,
+                    torch.empty(n, dtype=torch.uint64, device=d) if want_sizes else None,
+                    torch.empty((n, n), dtype=torch.float64, device=d) if want_J else None)
+        cdt = np.uint64 if self.count_bits == 64 else np.uint32
+        return (np.empty((n, n), dtype=cdt) if want_C else None,
+                np.empty(n, dtype=np.uint64) if want_sizes else None,
+                np.empty((n, n), dtype=np.float64) if want_J else None)
+
+    def all_pairs_streamed(self, offsets, ids, staging_bytes: int = 1 << 30, want_C=True, want_J=True,
+                           want_sizes=True, out_device=False, out=None):
+        """As all_pairs for a collection in host memory, streamed through two
+        pinned staging buffers of ``staging_bytes`` each (host->device copies
+        overlap the device's work)."""
+        s, keep, is_dev = self._sets(offsets, ids)
+        if is_dev:
+            raise ValueError("all_pairs_streamed reads its input from host memory")
+        C, sizes, J = out if out is not None else self._outputs(s.n, out_device, want_C, want_sizes, want_J)
+        self._order()
+        rc = self._lib.jsim_all_pairs_streamed(self._h, ctypes.byref(s), self._ptr(C), self._ptr(sizes),
+                                               self._ptr(J), MEM_DEVICE if out_device else MEM_HOST,
+                                               int(staging_bytes))
         _check(rc, self._h)
         return C, sizes, J
 

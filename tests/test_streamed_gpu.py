@@ -1,0 +1,128 @@
+"""GPU parity of the streamed all-pairs call (host input copied to the device
+in super-batches through pinned double-buffered staging) against the oracle
+and against the one-shot call.  All results are integers or correctly
+rounded binary64 quotients of integers, so the tolerance is zero."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_04200_gb300 import jsim, synth
+
+pytestmark = pytest.mark.gpu
+
+MIB = 1 << 20
+
+
+def collection(segs):
+    offsets = np.zeros(len(segs) + 1, dtype=np.uint64)
+    offsets[1:] = np.cumsum([len(s) for s in segs])
+    ids = np.concatenate([np.asarray(s, dtype=np.uint64) for s in segs]) if segs else np.zeros(0, np.uint64)
+    return offsets, ids.astype(np.uint64)
+
+
+def assert_same(res, ref):
+    C, sizes, J = res
+    Co, so, Jo = ref
+    np.testing.assert_array_equal(np.asarray(sizes, dtype=np.uint64), so)
+    np.testing.assert_array_equal(np.asarray(C).astype(np.uint64), Co)
+    np.testing.assert_array_equal(np.asarray(J).view(np.uint64), Jo.view(np.uint64))
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return synth.ancestral64()
+
+
+@pytest.fixture(scope="module")
+def c1_ref(c1):
+    return oracle.all_pairs(*c1)
+
+
+@pytest.mark.parametrize("batch_rows,staging", [(1 << 14, MIB), (3 << 12, MIB), (1 << 16, 4 * MIB), (0, 64 * MIB)])
+@pytest.mark.parametrize("variant", ["auto", "popc", "tc"])
+def test_ancestral64_streamed(gpu, c1, c1_ref, batch_rows, staging, variant):
+    """Several super-batches (1 MiB staging = 131,072 values of 3.1e6), each
+    several row batches with a ragged last one, give the oracle's results."""
+    with jsim.Context(batch_rows=batch_rows, variant=variant) as ctx:
+        assert_same(ctx.all_pairs_streamed(*c1, staging_bytes=staging), c1_ref)
+        st = ctx.stats()
+        if batch_rows:
+            assert st["batch_rows"] == batch_rows
+        # a second call on the same context reuses its pinned staging
+        assert_same(ctx.all_pairs_streamed(*c1, staging_bytes=staging), c1_ref)
+
+
+def test_ancestral64_streamed_device_out(gpu, c1, c1_ref):
+    import torch
+    with jsim.Context(batch_rows=1 << 15) as ctx:
+        C, s, J = ctx.all_pairs_streamed(*c1, staging_bytes=2 * MIB, out_device=True)
+        torch.cuda.synchronize()
+        C = C.view(torch.int32).cpu().numpy().view(np.uint32)
+        s = s.view(torch.int64).cpu().numpy().view(np.uint64)
+        assert_same((C, s, J.cpu().numpy()), c1_ref)
+
+
+@pytest.mark.parametrize("n,median", [(130, 3e4), (257, 1e4)])
+def test_clade40_streamed_matches_oracle_and_one_shot(gpu, n, median):
+    """The 4096-sample 40-bit clade recipe at sizes the oracle finishes in
+    seconds, 64-bit counts, streamed through 4 MiB staging."""
+    off, ids = synth.clade4096(n=n, median=median)
+    ref = oracle.all_pairs(off, ids)
+    with jsim.Context(count_bits=64, id_bits=40) as ctx:
+        assert_same(ctx.all_pairs_streamed(off, ids, staging_bytes=4 * MIB), ref)
+        st = ctx.stats()
+        assert st["batches"] > 1
+        assert_same(ctx.all_pairs(off, ids), ref)
+
+
+def test_streamed_edge_cases(gpu):
+    segs = [[], [], [0], [0, 2**64 - 1], [5, 5, 5, 7], list(range(1000, 1300)), [2**63, 2**63 + 1],
+            [2**64 - 1], [2**40 + k * 977 for k in range(3000)]]
+    off, ids = collection(segs)
+    ref = oracle.all_pairs(off, ids)
+    for batch_rows in (0, 64, 1 << 20):
+        with jsim.Context(batch_rows=batch_rows) as ctx:
+            assert_same(ctx.all_pairs_streamed(off, ids, staging_bytes=MIB), ref)
+    with jsim.Context() as ctx:
+        C, s, J = ctx.all_pairs_streamed(*collection([[], [], []]), staging_bytes=MIB)
+        assert np.all(C == 0) and np.all(s == 0) and np.all(J == 1.0)
+        C, s, J = ctx.all_pairs_streamed(np.zeros(1, np.uint64), np.zeros(0, np.uint64))
+        assert C.shape == (0, 0)
+
+
+def test_streamed_errors(gpu):
+    import torch
+    with jsim.Context(batch_rows=64) as ctx:
+        # a descent inside one slice (seen on the device)
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*collection([[1, 2, 3], [5, 3, 9]]), staging_bytes=MIB)
+        assert e.value.name == "JSIM_ERR_UNSORTED"
+        # a descent between slices (seen on the host)
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*collection([[1, 2, 10**6], [100, 5 * 10**6, 200]]), staging_bytes=MIB)
+        assert e.value.name == "JSIM_ERR_UNSORTED"
+        # first value above the last
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*collection([[1, 2], [9, 3]]), staging_bytes=MIB)
+        assert e.value.name == "JSIM_ERR_UNSORTED"
+        # staging below 1 MiB
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*collection([[1, 2]]), staging_bytes=1000)
+        assert e.value.name == "JSIM_ERR_ARG"
+        # device input is not streamed
+        off, ids = collection([[1, 2]])
+        with pytest.raises(ValueError):
+            ctx.all_pairs_streamed(torch.from_numpy(off.view(np.int64)).cuda(),
+                                   torch.from_numpy(ids.view(np.int64)).cuda())
+        # still usable after errors
+        C, s, J = ctx.all_pairs_streamed(*collection([[1, 2], [2, 3]]), staging_bytes=MIB)
+        assert C[0, 1] == 1 and J[0, 1] == 1 / 3
+    # one row batch with more values than the staging holds
+    with jsim.Context(batch_rows=1 << 20) as ctx:
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*collection([list(range(200_000))]), staging_bytes=MIB)
+        assert e.value.name == "JSIM_ERR_OOM"
+    with jsim.Context(id_bits=20) as ctx:
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*collection([[1, 2**20], [4]]), staging_bytes=MIB)
+        assert e.value.name == "JSIM_ERR_ID_RANGE"
