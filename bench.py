@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jsim", choices=["jsim", "reference"])
     ap.add_argument("--workload", default="clade1024",
-                    choices=["clade1024", "ancestral64", "batched200", "stream4096"])
+                    choices=["clade1024", "ancestral64", "batched200", "stream4096", "serve2048"])
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--batch-rows", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -390,6 +390,125 @@ def run_streamed(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: a resident index of a 2048-sample reference (values in
+    [0, 2^32), log-normal sizes, 64 clades) and requests of U{1..64} query
+    samples from the same clades.  Capacity = requests/s of a closed burst;
+    then Poisson arrivals at 0.5, 0.8 and 0.95 x capacity with p50/p99
+    request latency (submit to results ready, host clock).  The plain form
+    answers a request with one jsim_all_pairs call on reference + query
+    samples (the only way to get query x reference counts without an index)."""
+    import threading
+    import torch
+    from paper_1911_04200_gb300 import jsim, synth
+    median = float(os.environ.get("JSIM_SERVE_MEDIAN", "1e5"))
+    n_req = int(os.environ.get("JSIM_SERVE_REQUESTS", "400"))
+    pool = 512
+    roff, rids = synth.serving_reference(median=median)
+    qoff, qids = synth.serving_queries(0, pool, median=median)
+    n_ref = len(roff) - 1
+    rng = np.random.default_rng(11)
+
+    def request():
+        q = int(rng.integers(1, 65))
+        a = int(rng.integers(0, pool - q + 1))
+        return (qoff[a:a + q + 1] - qoff[a]).astype(np.uint64), qids[int(qoff[a]):int(qoff[a + q])]
+
+    sizes = np.diff(qoff.astype(np.int64))
+    max_vals = int(np.sort(sizes)[-64:].sum())
+    ctx = jsim.Context(device=0, id_bits=32)
+    t0 = time.perf_counter()
+    ix = jsim.Index(ctx, roff, rids, max_batch_samples=64, max_batch_values=max_vals, slots=2)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    for _ in range(max(args.warmup, 1)):
+        ix.submit(*request()).wait()
+
+    def run(reqs, gaps=None):
+        st0 = ix.stats()
+        handles = []
+        t_begin = time.perf_counter()
+        if gaps is None:
+            handles = [ix.submit(*r) for r in reqs]
+        else:
+            t_next = t_begin
+            for r, g in zip(reqs, gaps):
+                t_next += g
+                d = t_next - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                handles.append(ix.submit(*r))
+        for h in handles:
+            h.wait()
+        elapsed = time.perf_counter() - t_begin
+        lat = np.array([h.latency()[1] for h in handles])
+        st1 = ix.stats()
+        for h in handles:
+            h.free()
+        d = {k: st1[k] - st0[k] for k in ("batches", "samples_done", "values_done", "ms_device", "ms_product",
+                                          "index_bytes_read", "touched_words")}
+        return elapsed, lat, d
+
+    reqs = [request() for _ in range(n_req)]
+    with Clocks(0) as clk:
+        elapsed, lat, d = run(reqs)
+    capacity = n_req / elapsed
+    samples = sum(len(o) - 1 for o, _ in reqs)
+    levels = {}
+    for f in (0.5, 0.8, 0.95):
+        lam = f * capacity
+        rq = [request() for _ in range(n_req)]
+        gaps = rng.exponential(1.0 / lam, n_req)
+        el, lt, _ = run(rq, gaps)
+        levels["%.2f" % f] = {"rate_rps": round(lam, 2), "achieved_rps": round(n_req / el, 2),
+                              "p50_ms": round(float(np.percentile(lt, 50)), 3),
+                              "p99_ms": round(float(np.percentile(lt, 99)), 3),
+                              "mean_ms": round(float(lt.mean()), 3)}
+    # plain: one all-pairs call on reference + query samples per request
+    plain_ms = []
+    pctx = jsim.Context(device=0, id_bits=32)
+    for k in range(2):
+        o, v = reqs[k]
+        off = np.concatenate([roff, roff[-1] + o[1:]]).astype(np.uint64)
+        ids = np.concatenate([rids, v])
+        t0 = time.perf_counter()
+        C, S, J = pctx.all_pairs(off, ids, want_J=True)
+        plain_ms.append((time.perf_counter() - t0) * 1e3)
+        h = ix.submit(o, v)
+        Cs, Ss, Js = h.wait()
+        h.free()
+        assert np.array_equal(Cs, C[n_ref:, :n_ref]) and np.array_equal(Js.view(np.uint64),
+                                                                         J[n_ref:, :n_ref].view(np.uint64))
+    pk, src = measured_peaks()
+    achieved = d["index_bytes_read"] / (d["ms_product"] * 1e-3) / 1e9 if d["ms_product"] else 0.0
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic_from_profiles("qprod", "serve2048"),
+            "kernel": "k_qprod", "peak_source": "%s HBM copy bandwidth" % src}
+    line = {"metric": METRIC, "value": capacity, "unit": "requests/s", "n_gpus": 1, "steps": n_req,
+            "warmup": args.warmup, "ms_per_step": elapsed / n_req * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
+            "config": {"workload": "serve2048: reference n=2048, values in [0,2^32), log-normal sizes median "
+                                   "%.0e (x/10-10x), 64 clades; requests of U{1..64} query samples of the same "
+                                   "recipe" % median,
+                       "index_words": ix.words, "index_bytes": ix.words * ((n_ref + 511) // 512 * 512) * 8,
+                       "build_ms": round(build_ms, 1), "requests": n_req, "query_samples": samples,
+                       "samples_per_s": samples / elapsed, "batches": d["batches"],
+                       "samples_per_batch": d["samples_done"] / max(1, d["batches"]),
+                       "device_ms_per_batch": d["ms_device"] / max(1, d["batches"]),
+                       "qprod_ms_per_batch": d["ms_product"] / max(1, d["batches"]),
+                       "touched_words_per_batch": d["touched_words"] / max(1, d["batches"]),
+                       "l2": "index (%.1f GB) larger than L2; no flush" % (ix.words * n_ref * 8 / 1e9)},
+            "latency": levels, "clocks": clk.summary(), "gpu_launches": int(10 * d["batches"]), "roofline": roof,
+            "e2e": {"value": capacity, "unit": "requests/s",
+                    "h2d_bytes_per_step": int(d["values_done"] * 8 / n_req),
+                    "d2h_bytes_per_step": int(samples * n_ref * 12 / n_req)},
+            "plain": {"ms_per_request": float(np.mean(plain_ms)), "value": 1e3 / float(np.mean(plain_ms)),
+                      "how": "one jsim_all_pairs call on reference + the request's samples (host in/out)"},
+            "speedup_vs_plain": capacity * float(np.mean(plain_ms)) / 1e3}
+    print(json.dumps(line))
+    ix.close()
+    return 0
+
+
 def run_jsim(args):
     import torch
     import torch.distributed as dist
@@ -513,6 +632,8 @@ def main():
         return run_batched(args)
     if args.workload == "stream4096":
         return run_streamed(args)
+    if args.workload == "serve2048":
+        return run_serve(args)
     return run_jsim(args)
 
 

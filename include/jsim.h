@@ -258,6 +258,94 @@ JSIM_API int jsim_product(jsim_ctx* ctx, const uint64_t* words, uint64_t n, uint
 JSIM_API int jsim_product_noalloc(jsim_ctx* ctx, const uint64_t* words, uint64_t n, uint64_t W,
                                   uint64_t stride, void* C, int variant);
 
+/* ---- Serving: a resident reference index and continuous query batching ----
+ *
+ * The reference collection is packed once, as one batch of the method over
+ * its whole value range (Sec. III-B: filter f, Eq. 5; rank directory, Eq. 6;
+ * packed words), and stays in device memory.  A query sample Q is compared
+ * with every reference sample S_j: C[q][j] = |Q cap S_j|, J as above, and
+ * |Q| counts every distinct value of Q, also those the reference lacks.
+ * Query values are ranked against the resident filter (a value absent from
+ * f meets no reference sample), so a query reads only the index words its
+ * values fall in (Eq. 7 restricted to them).
+ */
+typedef struct jsim_index jsim_index;
+typedef struct jsim_request jsim_request;
+
+typedef struct {
+    uint64_t max_batch_samples; /* query samples per device batch, 1..64 (default 64) */
+    uint64_t max_batch_values;  /* query values per device batch, < 2^32 (default 2^27) */
+    int slots;                  /* device batches in flight, 1..8 (default 2) */
+} jsim_serve_options;
+
+typedef struct {
+    uint64_t requests_submitted, requests_done, samples_done, values_done;
+    uint64_t batches;           /* device batches retired */
+    uint64_t queued;            /* requests waiting for a slot now */
+    uint64_t touched_words;     /* index rows read, summed over batches */
+    double ms_device;           /* device time of the batches (copy in to copy out), summed */
+    double ms_product;          /* device time of the query x index product kernels, summed */
+    double index_bytes_read;    /* touched rows x row bytes, summed */
+    double bitops_dense;        /* 64 x touched words x batch samples x n_ref, summed */
+} jsim_serve_stats;
+
+JSIM_API void jsim_serve_default_options(jsim_serve_options* opt);
+
+/*
+ * Build the index of `ref` (host or device memory, n >= 1) on the context's
+ * device and start its server thread.  The index allocates everything it will
+ * use here (index, filter, per-slot buffers, pinned staging) through the
+ * context's allocator; serving allocates nothing.  The context must outlive
+ * the index and must not be used by another thread during this call.
+ * Device memory: W x round_up(n, 512) x 8 bytes of index (W = ceil(R / 64),
+ * R the reference's distinct values), width/8 + width/16 bytes of filter and
+ * directory, and per slot about max_batch_values x 8 + min(W,
+ * max_batch_values) x max_batch_samples x 8 bytes.
+ * Errors: JSIM_ERR_ARG, JSIM_ERR_UNSORTED, JSIM_ERR_ID_RANGE, JSIM_ERR_OOM,
+ * JSIM_ERR_CUDA, JSIM_ERR_UNSUPPORTED (reference value span >= 2^36).
+ */
+JSIM_API int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_serve_options* opt,
+                              jsim_index** out);
+
+/* Stop the server (queued requests end with JSIM_ERR_CANCELLED, running
+ * batches finish) and free the index.  Free every request first or after;
+ * a request that was cancelled here stays valid until jsim_request_free. */
+JSIM_API void jsim_index_destroy(jsim_index* ix);
+
+/* n_ref, index words W, and the reference sizes |S_j| (host, n_ref entries);
+ * any pointer may be NULL. */
+JSIM_API int jsim_index_info(const jsim_index* ix, uint64_t* n_ref, uint64_t* words, uint64_t* ref_sizes);
+
+/* Server counters since the index was built. */
+JSIM_API int jsim_index_stats(jsim_index* ix, jsim_serve_stats* out);
+
+/*
+ * Queue a request of q->n query samples (host memory only).  Thread-safe.
+ * The offsets are copied; the values are read by the server until the
+ * request is done, so they must stay valid and unchanged until
+ * jsim_request_wait has returned for it (or jsim_request_free).
+ * Errors: JSIM_ERR_ARG (bad offsets, device memory, or more samples or values
+ * than one batch holds), JSIM_ERR_CANCELLED (the index is stopping).
+ */
+JSIM_API int jsim_query_submit(jsim_index* ix, const jsim_sets* q, jsim_request** out);
+
+/*
+ * Wait up to timeout_ms (< 0: no limit) for a request and copy its results
+ * (host memory; any may be NULL): C q x n_ref (uint32 or uint64 as the
+ * context's count_bits), qsizes q, J q x n_ref binary64.
+ * Errors: JSIM_ERR_TIMEOUT (not done yet; wait again), JSIM_ERR_UNSORTED or
+ * JSIM_ERR_ID_RANGE (this request's input), JSIM_ERR_OVERFLOW,
+ * JSIM_ERR_CANCELLED, JSIM_ERR_CUDA.
+ */
+JSIM_API int jsim_request_wait(jsim_request* r, void* C, uint64_t* qsizes, double* J, int timeout_ms);
+
+/* Host-clock times of a finished request: submit to admission into a device
+ * batch, and submit to results ready.  JSIM_ERR_TIMEOUT while not done. */
+JSIM_API int jsim_request_latency(const jsim_request* r, double* queued_ms, double* total_ms);
+
+/* Release a request: a queued one is withdrawn, a running one is waited for. */
+JSIM_API void jsim_request_free(jsim_request* r);
+
 /* Statistics of the last call on the context. */
 JSIM_API int jsim_get_stats(const jsim_ctx* ctx, jsim_stats* out);
 

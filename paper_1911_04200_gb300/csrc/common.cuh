@@ -33,9 +33,10 @@ struct Plan {
 // ---- ingest.cu -------------------------------------------------------------
 cudaError_t launch_plan(const u64* offsets, const u64* ids, u64 n, u64 lo, u64 hi, bool full,
                         Plan plan, cudaStream_t st);
+// err_stride 0: one error word for all samples; 1: err[i] per sample
 cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan, u64 max_chunks,
                             int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, int sms,
-                            cudaStream_t st);
+                            cudaStream_t st, u64 err_stride = 0);
 cudaError_t launch_filter(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
                           u32* bitmap, int sms, cudaStream_t st);
 // ktotal/kbase (optional, device): append this batch's words after the
@@ -43,9 +44,12 @@ cudaError_t launch_filter(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 
 cudaError_t launch_scan(const u64* bitmap, u64 nwords, u32* dir, u64* bsum, u64* boff, u64* R,
                         cudaStream_t st, u64* ktotal = nullptr, u64* kbase = nullptr);
 cudaError_t launch_zero_rows(u64* X, u64 rows, u64 stride, u64 words, int sms, cudaStream_t st);
+// Sample i's word q goes to X[i * stride + (kbase + q) * wstride]: row-major
+// packed rows with wstride 1, word-major (one row per word) with stride 1.
 cudaError_t launch_pack(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
                         const u64* bitmap, const u32* dir, const u64* boff, u64* X, u64 stride,
-                        u64* batch_sizes, int sms, cudaStream_t st, const u64* kbase = nullptr);
+                        u64* batch_sizes, int sms, cudaStream_t st, const u64* kbase = nullptr,
+                        u64 wstride = 1);
 
 // ---- product kernels ---------------------------------------------------------
 // C (n x n, CT = u32 or u64, row-major with row stride ldc) += X X^T on the
@@ -85,6 +89,31 @@ struct TcJobDesc {
 cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, void* dev_table, bool upload, int count_bits, int sms,
                             u32* err, int timeout_ms, cudaStream_t st, int* launches);
 bool product_tc_supported(int device);
+
+// ---- query.cu (serving) ---------------------------------------------------------
+// A resident reference index: the reference as one batch over [lo, lo+width)
+// with filter bitmap, rank directory and word-major packed words (row w holds
+// word w of all n_ref samples; row stride ns, a multiple of 512).
+struct QueryIndex {
+    const u64* index;
+    const u64* bm;
+    const u32* dir;
+    const u64* boff;
+    u64 lo, width, W, n_ref, ns;
+};
+cudaError_t launch_qtouch(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix, u32* touched,
+                          int sms, cudaStream_t st);
+// zeroes Qc[0 .. min(*Udev, Umax) * S) and fills it
+cudaError_t launch_qpack(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix,
+                         const u64* touched, const u32* dir_t, const u64* boff_t, const u64* Udev, u64 Umax,
+                         u64* Qc, int sms, cudaStream_t st);
+cudaError_t launch_qemit(const u64* touched, u64 nwt, const u32* dir_t, const u64* boff_t, u64* wlist, int sms,
+                         cudaStream_t st);
+// Cacc (S x n_ref u32, zeroed by the caller) += query x index counts; S <= 64
+cudaError_t launch_qprod(const QueryIndex& ix, const u64* wlist, const u64* Udev, u64 Umax, const u64* Qc, int S,
+                         u32* Cacc, int sms, cudaStream_t st);
+cudaError_t launch_qepi(const u32* Cacc, u64 S, u64 n_ref, const u64* sq, const u64* sr, int count_bits, void* Cout,
+                        double* J, int sms, cudaStream_t st);
 
 // ---- epilogue.cu ---------------------------------------------------------------
 // Cout[i][j] = Cacc[min(i,j)][max(i,j)], J = C / (s_i + s_j - C) (binary64), 1 if 0.

@@ -1,55 +1,11 @@
 // Ingest kernels: per-batch plan, input validation, the zero-row filter
 // f^(l) (Eq. 5), its prefix sum p^(l) as a rank directory (Eq. 6), and the
 // bitmask compression of the surviving rows into 64-bit words (Sec. III-B).
-#include "common.cuh"
+#include "ingest_dev.cuh"
 
 namespace jsim {
 
 namespace {
-
-constexpr int kPlanThreads = 1024;
-constexpr int kIngestThreads = 256;
-constexpr int kScanThreads = 256;
-constexpr int kScanPerThread = (int)(kScanBlockWords / kScanThreads);  // 16
-
-__device__ __forceinline__ u64 lower_bound_u64(const u64* a, u64 lo, u64 hi, u64 v)
-{
-    while (lo < hi) {
-        u64 mid = lo + ((hi - lo) >> 1);
-        if (a[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// Block-wide exclusive scan of one u64 per thread; returns the block total.
-template <int NT>
-__device__ __forceinline__ u64 block_exclusive_scan(u64 v, u64& excl, u64* smem /* NT/32 */)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    u64 x = v;
-    #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        u64 y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) smem[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        u64 w = lane < NT / 32 ? smem[lane] : 0;
-        #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            u64 y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < NT / 32) smem[lane] = w;
-    }
-    __syncthreads();
-    u64 warp_base = warp ? smem[warp - 1] : 0;
-    u64 total = smem[NT / 32 - 1];
-    excl = warp_base + x - v;
-    __syncthreads();
-    return total;
-}
 
 // One CTA: per-sample [beg, beg+len) of values in [lo, hi) and chunk prefix.
 __global__ void __launch_bounds__(kPlanThreads)
@@ -98,20 +54,9 @@ k_plan(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, u64 
     }
 }
 
-// Chunk c -> sample index (largest i with cofs[i] <= c, among samples with chunks).
-__device__ __forceinline__ u64 chunk_sample(const u64* cofs, u64 n, u64 c)
-{
-    u64 lo = 0, hi = n;  // find last i in [0,n) with cofs[i] <= c
-    while (lo < hi) {
-        u64 mid = lo + ((hi - lo + 1) >> 1);
-        if (cofs[mid] <= c) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 __global__ void __launch_bounds__(kIngestThreads)
 k_validate(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, Plan plan,
-           int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid)
+           int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, u64 err_stride)
 {
     __shared__ u64 s_i, s_p0, s_p1;
     __shared__ u32 s_cnt[kIngestThreads / 32];
@@ -147,7 +92,7 @@ k_validate(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, 
         }
         if ((threadIdx.x & 31) == 0) {
             s_cnt[threadIdx.x >> 5] = cnt;
-            if (flags) atomicOr(err, flags);
+            if (flags) atomicOr(err + i * err_stride, flags);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -157,23 +102,6 @@ k_validate(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, 
         }
         __syncthreads();
     }
-}
-
-// Inclusive OR over the lanes that share key q, accumulated toward the
-// segment's first lane (q is non-decreasing across lanes).  Returns true on
-// the lane that must publish the segment's value.
-template <typename T>
-__device__ __forceinline__ bool segmented_or(u64 q, T& v)
-{
-    const int lane = threadIdx.x & 31;
-    #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T w = __shfl_down_sync(0xffffffffu, v, o);
-        u64 qq = __shfl_down_sync(0xffffffffu, q, o);
-        if (lane + o < 32 && qq == q) v |= w;
-    }
-    u64 qprev = __shfl_up_sync(0xffffffffu, q, 1);
-    return lane == 0 || qprev != q;
 }
 
 // f^(l): set bit (x - lo) for every value x of the batch (Eq. 5).
@@ -272,7 +200,7 @@ __global__ void k_zero_rows(u64* X, u64 rows, u64 stride, u64 words)
 __global__ void __launch_bounds__(kIngestThreads)
 k_pack(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
        const u64* __restrict__ bitmap, const u32* __restrict__ dir, const u64* __restrict__ boff,
-       u64* X, u64 stride, u64* batch_sizes, const u64* kbase)
+       u64* X, u64 stride, u64* batch_sizes, const u64* kbase, u64 wstride)
 {
     __shared__ u64 s_i, s_p0, s_p1, s_b;
     __shared__ u32 s_cnt[kIngestThreads / 32];
@@ -286,7 +214,7 @@ k_pack(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
         }
         __syncthreads();
         const u64 i = s_i, p0 = s_p0, p1 = s_p1, bb = s_b;
-        u64* row = X + i * stride + (kbase ? *kbase : 0ull);
+        u64* row = X + i * stride + (kbase ? *kbase : 0ull) * wstride;
         u32 cnt = 0;
         for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
             u64 pos = base + (threadIdx.x & 31);
@@ -304,7 +232,7 @@ k_pack(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
                 if (batch_sizes) cnt += (pos == bb) || (ids[pos - 1] != x);
             }
             bool lead = segmented_or<u64>(q, bit);
-            if (lead && bit) atomicOr(row + q, bit);
+            if (lead && bit) atomicOr(row + q * wstride, bit);
         }
         if (batch_sizes) {
             #pragma unroll
@@ -339,10 +267,10 @@ cudaError_t launch_plan(const u64* offsets, const u64* ids, u64 n, u64 lo, u64 h
 
 cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan, u64 max_chunks,
                             int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, int sms,
-                            cudaStream_t st)
+                            cudaStream_t st, u64 err_stride)
 {
     k_validate<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(offsets, ids, n, plan, id_bits,
-                                                                            sizes, err, maxid, minid);
+                                                                            sizes, err, maxid, minid, err_stride);
     return cudaGetLastError();
 }
 
@@ -378,10 +306,11 @@ cudaError_t launch_zero_rows(u64* X, u64 rows, u64 stride, u64 words, int sms, c
 
 cudaError_t launch_pack(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
                         const u64* bitmap, const u32* dir, const u64* boff, u64* X, u64 stride,
-                        u64* batch_sizes, int sms, cudaStream_t st, const u64* kbase)
+                        u64* batch_sizes, int sms, cudaStream_t st, const u64* kbase, u64 wstride)
 {
     k_pack<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, width, bitmap, dir,
-                                                                        boff, X, stride, batch_sizes, kbase);
+                                                                        boff, X, stride, batch_sizes, kbase,
+                                                                        wstride);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,83 @@
+// Device helpers shared by the ingest and query kernels (internal).
+#pragma once
+#include "common.cuh"
+
+namespace jsim {
+
+namespace {
+
+constexpr int kPlanThreads = 1024;
+constexpr int kIngestThreads = 256;
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = (int)(kScanBlockWords / kScanThreads);  // 16
+
+__device__ __forceinline__ u64 lower_bound_u64(const u64* a, u64 lo, u64 hi, u64 v)
+{
+    while (lo < hi) {
+        u64 mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Block-wide exclusive scan of one u64 per thread; returns the block total.
+template <int NT>
+__device__ __forceinline__ u64 block_exclusive_scan(u64 v, u64& excl, u64* smem /* NT/32 */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u64 x = v;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        u64 y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        u64 w = lane < NT / 32 ? smem[lane] : 0;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            u64 y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NT / 32) smem[lane] = w;
+    }
+    __syncthreads();
+    u64 warp_base = warp ? smem[warp - 1] : 0;
+    u64 total = smem[NT / 32 - 1];
+    excl = warp_base + x - v;
+    __syncthreads();
+    return total;
+}
+
+// Chunk c -> sample index (largest i with cofs[i] <= c, among samples with chunks).
+__device__ __forceinline__ u64 chunk_sample(const u64* cofs, u64 n, u64 c)
+{
+    u64 lo = 0, hi = n;  // find last i in [0,n) with cofs[i] <= c
+    while (lo < hi) {
+        u64 mid = lo + ((hi - lo + 1) >> 1);
+        if (cofs[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Inclusive OR over the lanes that share key q, accumulated toward the
+// segment's first lane (q is non-decreasing across lanes).  Returns true on
+// the lane that must publish the segment's value.
+template <typename T>
+__device__ __forceinline__ bool segmented_or(u64 q, T& v)
+{
+    const int lane = threadIdx.x & 31;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T w = __shfl_down_sync(0xffffffffu, v, o);
+        u64 qq = __shfl_down_sync(0xffffffffu, q, o);
+        if (lane + o < 32 && qq == q) v |= w;
+    }
+    u64 qprev = __shfl_up_sync(0xffffffffu, q, 1);
+    return lane == 0 || qprev != q;
+}
+
+}  // namespace
+
+}  // namespace jsim

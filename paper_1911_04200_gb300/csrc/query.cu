@@ -1,0 +1,289 @@
+// Query kernels of the serving pattern: query samples against a resident
+// reference index.
+//
+// The index holds the reference as one batch of the method (Sec. III-B):
+// its filter f over [lo, lo + width) (Eq. 5), the rank directory of f
+// (Eq. 6) and the packed words, word-major (row w = word w of every
+// reference sample, so one query word reads one contiguous row).  A query
+// value x can meet a reference sample only if f has row x; its rank r there
+// names index word r/64, bit r%64.  Values absent from f count in |Q| only.
+//
+// For a batch of S query samples:
+//   k_qtouch  marks the index words any query value falls in (bitmap over W);
+//   rank scan of that bitmap numbers the U touched words;
+//   k_qpack   builds Qc[u][s], the query's mask on touched word u;
+//   k_qemit   lists the index word of every touched word;
+//   k_qprod   C[s][j] = sum_u popcount(Qc[u][s] & index[w_u][j]) (Eq. 7
+//             restricted to the words a query touches), reading each touched
+//             index row once for the whole batch;
+//   k_qepi    J = C / (|Q_s| + |S_j| - C) in binary64 (Sec. II-A).
+#include <algorithm>
+#include "ingest_dev.cuh"
+
+namespace jsim {
+
+namespace {
+
+constexpr int kQThreads = 256;
+constexpr int kQCols = 2 * kQThreads;  // reference columns per CTA (two per thread)
+constexpr int kQTile = 16;             // index rows in flight per thread
+
+// rank of x in the reference filter, if f has row x
+__device__ __forceinline__ bool ref_rank(u64 x, u64 lo, u64 width, const u64* __restrict__ bm,
+                                         const u32* __restrict__ dir, const u64* __restrict__ boff, u64& r)
+{
+    const u64 d = x - lo;
+    if (d >= width) return false;
+    const u64 w = d >> 6;
+    const u64 word = bm[w];
+    const u64 bit = 1ull << (d & 63);
+    if (!(word & bit)) return false;
+    r = boff[w / kScanBlockWords] + (u64)dir[w] + (u64)__popcll(word & (bit - 1ull));
+    return true;
+}
+
+__global__ void __launch_bounds__(kIngestThreads)
+k_qtouch(const u64* __restrict__ ids, u64 S, Plan plan, u64 lo, u64 width, const u64* __restrict__ bm,
+         const u32* __restrict__ dir, const u64* __restrict__ boff, u32* touched)
+{
+    __shared__ u64 s_p0, s_p1;
+    const u64 nch = plan.totals[1];
+    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const u64 i = chunk_sample(plan.cofs, S, c);
+            const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+            s_p0 = p0;
+            s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+        }
+        __syncthreads();
+        const u64 p0 = s_p0, p1 = s_p1;
+        for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
+            const u64 pos = base + (threadIdx.x & 31);
+            u64 q = ~0ull, r;
+            u32 bit = 0;
+            if (pos < p1 && ref_rank(ids[pos], lo, width, bm, dir, boff, r)) {
+                const u64 w = r >> 6;
+                q = w >> 5;
+                bit = 1u << (w & 31);
+            }
+            const bool lead = segmented_or<u32>(q, bit);
+            if (lead && bit) atomicOr(touched + q, bit);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_zero_dyn(u64* X, const u64* __restrict__ count, u64 per, u64 cap)
+{
+    const u64 total = min(*count, cap) * per;
+    for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (u64)gridDim.x * blockDim.x)
+        X[t] = 0ull;
+}
+
+__global__ void __launch_bounds__(kIngestThreads)
+k_qpack(const u64* __restrict__ ids, u64 S, Plan plan, u64 lo, u64 width, const u64* __restrict__ bm,
+        const u32* __restrict__ dir, const u64* __restrict__ boff, const u64* __restrict__ touched,
+        const u32* __restrict__ dir_t, const u64* __restrict__ boff_t, u64* Qc)
+{
+    __shared__ u64 s_i, s_p0, s_p1;
+    const u64 nch = plan.totals[1];
+    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const u64 i = chunk_sample(plan.cofs, S, c);
+            const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+            s_i = i;
+            s_p0 = p0;
+            s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+        }
+        __syncthreads();
+        const u64 s = s_i, p0 = s_p0, p1 = s_p1;
+        for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
+            const u64 pos = base + (threadIdx.x & 31);
+            u64 key = ~0ull, bit = 0, r;
+            if (pos < p1 && ref_rank(ids[pos], lo, width, bm, dir, boff, r)) {
+                const u64 w = r >> 6, tw = w >> 6;
+                const u64 u = boff_t[tw / kScanBlockWords] + (u64)dir_t[tw] +
+                              (u64)__popcll(touched[tw] & ((1ull << (w & 63)) - 1ull));
+                key = u * S + s;
+                bit = 1ull << (r & 63);
+            }
+            const bool lead = segmented_or<u64>(key, bit);
+            if (lead && bit) atomicOr(Qc + key, bit);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_qemit(const u64* __restrict__ touched, u64 nwt, const u32* __restrict__ dir_t,
+                        const u64* __restrict__ boff_t, u64* wlist)
+{
+    for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < nwt; t += (u64)gridDim.x * blockDim.x) {
+        u64 x = touched[t];
+        u64 u = boff_t[t / kScanBlockWords] + (u64)dir_t[t];
+        while (x) {
+            wlist[u++] = t * 64 + (u64)(__ffsll((long long)x) - 1);
+            x &= x - 1;
+        }
+    }
+}
+
+// One CTA: reference columns [blockIdx.x * 512, +512) and touched words
+// [U * y / Y, U * (y + 1) / Y).  Counts per (query sample, column) live in
+// shared memory; each thread owns two columns, so no two threads share a
+// counter.  Per tile of kQTile touched words the CTA stages their masks
+// (kQTile x S) and which samples are nonzero, issues all index-row loads,
+// then adds popcounts for the nonzero masks only.
+__global__ void __launch_bounds__(kQThreads)
+k_qprod(const u64* __restrict__ index, u64 ns, u64 n_ref, const u64* __restrict__ wlist,
+        const u64* __restrict__ Udev, const u64* __restrict__ Qc, int S, u32* Cacc)
+{
+    extern __shared__ __align__(16) u64 q_smem[];
+    uint2* cnt = (uint2*)q_smem;                   // [S][kQThreads] pairs of counters
+    u64* qs = q_smem + (size_t)S * kQThreads;      // [kQTile][S]
+    u64* wl = qs + kQTile * S;                     // [kQTile]
+    u64* nz = wl + kQTile;                         // [kQTile]
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const u64 col = (u64)blockIdx.x * kQCols + 2 * (u64)t;
+    const u64 U = *Udev;
+    const u64 u0 = U * blockIdx.y / gridDim.y, u1 = U * (blockIdx.y + 1) / gridDim.y;
+    for (int e = t; e < S * kQThreads; e += kQThreads) cnt[e] = make_uint2(0u, 0u);
+    __syncthreads();
+    for (u64 base = u0; base < u1; base += kQTile) {
+        const int nt = (int)min((u64)kQTile, u1 - base);
+        for (int e = t; e < nt * S; e += kQThreads) qs[e] = Qc[base * (u64)S + e];
+        if (t < nt) wl[t] = wlist[base + t];
+        __syncthreads();
+        for (int j = warp; j < nt; j += kQThreads / 32) {
+            const u64 a = lane < S ? qs[j * S + lane] : 0ull;
+            const u64 b = lane + 32 < S ? qs[j * S + lane + 32] : 0ull;
+            const u32 lo = __ballot_sync(0xffffffffu, a != 0ull), hi = __ballot_sync(0xffffffffu, b != 0ull);
+            if (lane == 0) nz[j] = (u64)lo | ((u64)hi << 32);
+        }
+        ulonglong2 r[kQTile];
+        #pragma unroll
+        for (int j = 0; j < kQTile; ++j)
+            if (j < nt) r[j] = __ldg((const ulonglong2*)(index + wl[j] * ns + col));
+        __syncthreads();
+        #pragma unroll
+        for (int j = 0; j < kQTile; ++j) {
+            if (j < nt) {
+                u64 m = nz[j];
+                while (m) {
+                    const int s = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    const u64 q = qs[j * S + s];
+                    uint2 c = cnt[s * kQThreads + t];
+                    c.x += (u32)__popcll(q & r[j].x);
+                    c.y += (u32)__popcll(q & r[j].y);
+                    cnt[s * kQThreads + t] = c;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (u0 >= u1) return;
+    for (int s = 0; s < S; ++s) {
+        const uint2 c = cnt[s * kQThreads + t];
+        if (c.x && col < n_ref) atomicAdd(Cacc + (u64)s * n_ref + col, c.x);
+        if (c.y && col + 1 < n_ref) atomicAdd(Cacc + (u64)s * n_ref + col + 1, c.y);
+    }
+}
+
+template <typename CT>
+__global__ void k_qepi(const u32* __restrict__ Cacc, u64 S, u64 n_ref, const u64* __restrict__ sq,
+                       const u64* __restrict__ sr, CT* Cout, double* J)
+{
+    const u64 total = S * n_ref;
+    for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (u64)gridDim.x * blockDim.x) {
+        const u64 s = e / n_ref, j = e - s * n_ref;
+        const u64 c = Cacc[e];
+        const u64 u = sq[s] + sr[j] - c;
+        if (Cout) Cout[e] = (CT)c;
+        if (J) J[e] = u ? __ddiv_rn(__ull2double_rn(c), __ull2double_rn(u)) : 1.0;
+    }
+}
+
+inline unsigned grid_chunks(u64 max_chunks, int sms)
+{
+    u64 g = (u64)sms * 8;
+    if (max_chunks < g) g = max_chunks;
+    return (unsigned)(g ? g : 1);
+}
+
+inline unsigned grid_flat(u64 total, int sms, int threads)
+{
+    u64 g = (total + threads - 1) / threads;
+    const u64 cap = (u64)sms * 8;
+    if (g > cap) g = cap;
+    return (unsigned)(g ? g : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_qtouch(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix, u32* touched,
+                          int sms, cudaStream_t st)
+{
+    k_qtouch<<<grid_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, S, plan, ix.lo, ix.width, ix.bm, ix.dir,
+                                                                      ix.boff, touched);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qpack(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix,
+                         const u64* touched, const u32* dir_t, const u64* boff_t, const u64* Udev, u64 Umax,
+                         u64* Qc, int sms, cudaStream_t st)
+{
+    k_zero_dyn<<<grid_flat(Umax * S, sms, 256), 256, 0, st>>>(Qc, Udev, S, Umax);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_qpack<<<grid_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, S, plan, ix.lo, ix.width, ix.bm, ix.dir,
+                                                                     ix.boff, touched, dir_t, boff_t, Qc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qemit(const u64* touched, u64 nwt, const u32* dir_t, const u64* boff_t, u64* wlist, int sms,
+                         cudaStream_t st)
+{
+    if (nwt == 0) return cudaSuccess;
+    k_qemit<<<grid_flat(nwt, sms, 256), 256, 0, st>>>(touched, nwt, dir_t, boff_t, wlist);
+    return cudaGetLastError();
+}
+
+size_t qprod_smem(int S)
+{
+    return ((size_t)S * kQThreads + (size_t)kQTile * S + 2 * kQTile) * sizeof(u64);
+}
+
+cudaError_t launch_qprod(const QueryIndex& ix, const u64* wlist, const u64* Udev, u64 Umax, const u64* Qc, int S,
+                         u32* Cacc, int sms, cudaStream_t st)
+{
+    if (S < 1 || S > 64) return cudaErrorInvalidValue;
+    if (ix.W == 0 || Umax == 0) return cudaSuccess;
+    const size_t smem = qprod_smem(S);
+    cudaError_t e = cudaFuncSetAttribute(k_qprod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qprod, kQThreads, smem);
+    if (e != cudaSuccess) return e;
+    const u64 gx = ix.ns / kQCols;
+    u64 gy = ((u64)sms * (u64)std::max(per_sm, 1) + gx - 1) / gx;
+    const u64 tiles = (Umax + kQTile - 1) / kQTile;
+    if (gy > tiles) gy = tiles;
+    if (gy > 65535) gy = 65535;
+    if (gy == 0) gy = 1;
+    k_qprod<<<dim3((unsigned)gx, (unsigned)gy), kQThreads, smem, st>>>(ix.index, ix.ns, ix.n_ref, wlist, Udev, Qc, S,
+                                                                      Cacc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qepi(const u32* Cacc, u64 S, u64 n_ref, const u64* sq, const u64* sr, int count_bits, void* Cout,
+                        double* J, int sms, cudaStream_t st)
+{
+    const unsigned g = grid_flat(S * n_ref, sms, 256);
+    if (count_bits == 64)
+        k_qepi<u64><<<g, 256, 0, st>>>(Cacc, S, n_ref, sq, sr, (u64*)Cout, J);
+    else
+        k_qepi<u32><<<g, 256, 0, st>>>(Cacc, S, n_ref, sq, sr, (u32*)Cout, J);
+    return cudaGetLastError();
+}
+
+}  // namespace jsim

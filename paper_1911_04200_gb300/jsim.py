@@ -61,6 +61,23 @@ class Stats(ctypes.Structure):
         return d
 
 
+class ServeOptions(ctypes.Structure):
+    _fields_ = [("max_batch_samples", ctypes.c_uint64), ("max_batch_values", ctypes.c_uint64),
+                ("slots", ctypes.c_int)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("requests_submitted", ctypes.c_uint64), ("requests_done", ctypes.c_uint64),
+                ("samples_done", ctypes.c_uint64), ("values_done", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("touched_words", ctypes.c_uint64),
+                ("ms_device", ctypes.c_double), ("ms_product", ctypes.c_double),
+                ("index_bytes_read", ctypes.c_double),
+                ("bitops_dense", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # Every C-ABI entry point declared in include/jsim.h, with its ctypes signature.
 SIGNATURES = {
     "jsim_default_options": (None, [ctypes.POINTER(Options)]),
@@ -80,6 +97,18 @@ SIGNATURES = {
                                     ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]),
     "jsim_product_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                             ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]),
+    "jsim_serve_default_options": (None, [ctypes.POINTER(ServeOptions)]),
+    "jsim_index_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.POINTER(ServeOptions),
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "jsim_index_destroy": (None, [ctypes.c_void_p]),
+    "jsim_index_info": (ctypes.c_int, [ctypes.c_void_p, _u64p, _u64p, ctypes.c_void_p]),
+    "jsim_index_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServeStats)]),
+    "jsim_query_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.POINTER(ctypes.c_void_p)]),
+    "jsim_request_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int]),
+    "jsim_request_latency": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "jsim_request_free": (None, [ctypes.c_void_p]),
     "jsim_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "jsim_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "jsim_last_cuda_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -355,6 +384,110 @@ class Context:
         rc = self._lib.jsim_product_noalloc(self._h, self._ptr(words), n, W, stride, self._ptr(C), v)
         _check(rc, self._h)
         return C
+
+
+class Index:
+    """A resident reference index with its query server (jsim_index_build).
+
+    ``submit`` queues query samples (host arrays) and returns a Request; the
+    arrays are kept referenced by the Request until it is freed, because the
+    server reads them until the request is done.
+    """
+
+    def __init__(self, ctx: Context, offsets, ids, max_batch_samples: int = 64, max_batch_values: int = 1 << 27,
+                 slots: int = 2):
+        self._lib = ctx._lib
+        self.ctx = ctx
+        self.count_bits = ctx.count_bits
+        s, self._ref_keep, _ = ctx._sets(offsets, ids)
+        opt = ServeOptions(max_batch_samples, max_batch_values, slots)
+        h = ctypes.c_void_p()
+        ctx._order()
+        _check(self._lib.jsim_index_build(ctx._h, ctypes.byref(s), ctypes.byref(opt), ctypes.byref(h)), ctx._h)
+        self._h = h
+        self._ref_keep = None  # the index holds its own copy
+        n_ref, words = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._lib.jsim_index_info(self._h, ctypes.byref(n_ref), ctypes.byref(words), None))
+        self.n_ref, self.words = n_ref.value, words.value
+
+    def ref_sizes(self):
+        out = np.empty(self.n_ref, dtype=np.uint64)
+        _check(self._lib.jsim_index_info(self._h, None, None, out.ctypes.data))
+        return out
+
+    def submit(self, offsets, ids) -> "Request":
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        s = Sets()
+        s.n = offsets.size - 1
+        s.offsets = offsets.ctypes.data
+        s.ids = ids.ctypes.data if ids.size else None
+        s.mem = MEM_HOST
+        h = ctypes.c_void_p()
+        _check(self._lib.jsim_query_submit(self._h, ctypes.byref(s), ctypes.byref(h)))
+        return Request(self, h, s.n, (offsets, ids))
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(self._lib.jsim_index_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self._h is not None:
+            self._lib.jsim_index_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Request:
+    """One submitted query request (jsim_query_submit)."""
+
+    def __init__(self, index: Index, h, q: int, keep):
+        self._lib = index._lib
+        self._index = index  # the index outlives its requests
+        self._h = h
+        self.q = q
+        self.n_ref = index.n_ref
+        self.count_bits = index.count_bits
+        self._keep = keep
+
+    def wait(self, timeout_ms: int = -1):
+        """(C q x n_ref, sizes q, J q x n_ref) as numpy arrays."""
+        C = np.empty((self.q, self.n_ref), dtype=np.uint64 if self.count_bits == 64 else np.uint32)
+        sizes = np.empty(self.q, dtype=np.uint64)
+        J = np.empty((self.q, self.n_ref), dtype=np.float64)
+        _check(self._lib.jsim_request_wait(self._h, C.ctypes.data, sizes.ctypes.data, J.ctypes.data,
+                                           int(timeout_ms)))
+        return C, sizes, J
+
+    def latency(self):
+        """(submit -> admitted, submit -> done) in ms, host clock."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.jsim_request_latency(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def free(self):
+        if self._h is not None:
+            self._lib.jsim_request_free(self._h)
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def version() -> str:
