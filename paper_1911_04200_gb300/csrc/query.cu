@@ -24,9 +24,14 @@ namespace jsim {
 
 namespace {
 
+// Build-time tuning of the query product: index rows per tile (measured on
+// GB300: 16 beats 8 and 32).
+#ifndef JSIM_QTILE
+#define JSIM_QTILE 16
+#endif
 constexpr int kQThreads = 256;
 constexpr int kQCols = 2 * kQThreads;  // reference columns per CTA (two per thread)
-constexpr int kQTile = 16;             // index rows in flight per thread
+constexpr int kQTile = JSIM_QTILE;     // index rows in flight per thread
 
 // rank of x in the reference filter, if f has row x
 __device__ __forceinline__ bool ref_rank(u64 x, u64 lo, u64 width, const u64* __restrict__ bm,
@@ -130,52 +135,77 @@ __global__ void k_qemit(const u64* __restrict__ touched, u64 nwt, const u32* __r
 // One CTA: reference columns [blockIdx.x * 512, +512) and touched words
 // [U * y / Y, U * (y + 1) / Y).  Counts per (query sample, column) live in
 // shared memory; each thread owns two columns, so no two threads share a
-// counter.  Per tile of kQTile touched words the CTA stages their masks
-// (kQTile x S) and which samples are nonzero, issues all index-row loads,
-// then adds popcounts for the nonzero masks only.
+// counter.  Per tile of kQTile touched words the CTA compacts each word's
+// nonzero query masks into a list of (mask, sample) entries (a warp per
+// word: ballot + prefix popcount), issues all index-row loads, then adds
+// popcounts two entries at a time (a word's entries have distinct samples,
+// so the two counter updates are independent).
 __global__ void __launch_bounds__(kQThreads)
 k_qprod(const u64* __restrict__ index, u64 ns, u64 n_ref, const u64* __restrict__ wlist,
         const u64* __restrict__ Udev, const u64* __restrict__ Qc, int S, u32* Cacc)
 {
     extern __shared__ __align__(16) u64 q_smem[];
     uint2* cnt = (uint2*)q_smem;                   // [S][kQThreads] pairs of counters
-    u64* qs = q_smem + (size_t)S * kQThreads;      // [kQTile][S]
-    u64* wl = qs + kQTile * S;                     // [kQTile]
-    u64* nz = wl + kQTile;                         // [kQTile]
+    u64* eq = q_smem + (size_t)S * kQThreads;      // [kQTile][64] nonzero masks
+    u32* es = (u32*)(eq + kQTile * 64);            // [kQTile][64] their samples
+    u64* wl = (u64*)(es + kQTile * 64);            // [kQTile]
+    int* ne = (int*)(wl + kQTile);                 // [kQTile] entries per word
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const u64 col = (u64)blockIdx.x * kQCols + 2 * (u64)t;
     const u64 U = *Udev;
     const u64 u0 = U * blockIdx.y / gridDim.y, u1 = U * (blockIdx.y + 1) / gridDim.y;
+    const u32 lt = (1u << lane) - 1u;
     for (int e = t; e < S * kQThreads; e += kQThreads) cnt[e] = make_uint2(0u, 0u);
-    __syncthreads();
     for (u64 base = u0; base < u1; base += kQTile) {
         const int nt = (int)min((u64)kQTile, u1 - base);
-        for (int e = t; e < nt * S; e += kQThreads) qs[e] = Qc[base * (u64)S + e];
         if (t < nt) wl[t] = wlist[base + t];
-        __syncthreads();
         for (int j = warp; j < nt; j += kQThreads / 32) {
-            const u64 a = lane < S ? qs[j * S + lane] : 0ull;
-            const u64 b = lane + 32 < S ? qs[j * S + lane + 32] : 0ull;
-            const u32 lo = __ballot_sync(0xffffffffu, a != 0ull), hi = __ballot_sync(0xffffffffu, b != 0ull);
-            if (lane == 0) nz[j] = (u64)lo | ((u64)hi << 32);
+            const u64* row = Qc + (base + j) * (u64)S;
+            const u64 a = lane < S ? row[lane] : 0ull;
+            const u64 b = lane + 32 < S ? row[lane + 32] : 0ull;
+            const u32 ba = __ballot_sync(0xffffffffu, a != 0ull), bb = __ballot_sync(0xffffffffu, b != 0ull);
+            const int na = __popc(ba);
+            if (a) {
+                const int k = __popc(ba & lt);
+                eq[j * 64 + k] = a;
+                es[j * 64 + k] = (u32)lane;
+            }
+            if (b) {
+                const int k = na + __popc(bb & lt);
+                eq[j * 64 + k] = b;
+                es[j * 64 + k] = (u32)lane + 32u;
+            }
+            if (lane == 0) ne[j] = na + __popc(bb);
         }
+        __syncthreads();
         ulonglong2 r[kQTile];
         #pragma unroll
         for (int j = 0; j < kQTile; ++j)
             if (j < nt) r[j] = __ldg((const ulonglong2*)(index + wl[j] * ns + col));
-        __syncthreads();
         #pragma unroll
         for (int j = 0; j < kQTile; ++j) {
             if (j < nt) {
-                u64 m = nz[j];
-                while (m) {
-                    const int s = __ffsll((long long)m) - 1;
-                    m &= m - 1;
-                    const u64 q = qs[j * S + s];
-                    uint2 c = cnt[s * kQThreads + t];
-                    c.x += (u32)__popcll(q & r[j].x);
-                    c.y += (u32)__popcll(q & r[j].y);
-                    cnt[s * kQThreads + t] = c;
+                const int m = ne[j];
+                const u64* q = eq + j * 64;
+                const u32* sj = es + j * 64;
+                int k = 0;
+                for (; k + 1 < m; k += 2) {
+                    const u64 q0 = q[k], q1 = q[k + 1];
+                    const u32 s0 = sj[k] * kQThreads + t, s1 = sj[k + 1] * kQThreads + t;
+                    uint2 c0 = cnt[s0], c1 = cnt[s1];
+                    c0.x += (u32)(__popcll(q0 & r[j].x));
+                    c0.y += (u32)(__popcll(q0 & r[j].y));
+                    c1.x += (u32)(__popcll(q1 & r[j].x));
+                    c1.y += (u32)(__popcll(q1 & r[j].y));
+                    cnt[s0] = c0;
+                    cnt[s1] = c1;
+                }
+                if (k < m) {
+                    const u32 s0 = sj[k] * kQThreads + t;
+                    uint2 c0 = cnt[s0];
+                    c0.x += (u32)(__popcll(q[k] & r[j].x));
+                    c0.y += (u32)(__popcll(q[k] & r[j].y));
+                    cnt[s0] = c0;
                 }
             }
         }
@@ -250,7 +280,8 @@ cudaError_t launch_qemit(const u64* touched, u64 nwt, const u32* dir_t, const u6
 
 size_t qprod_smem(int S)
 {
-    return ((size_t)S * kQThreads + (size_t)kQTile * S + 2 * kQTile) * sizeof(u64);
+    return (size_t)S * kQThreads * sizeof(uint2) + (size_t)kQTile * 64 * (sizeof(u64) + sizeof(u32)) +
+           kQTile * (sizeof(u64) + sizeof(int));
 }
 
 cudaError_t launch_qprod(const QueryIndex& ix, const u64* wlist, const u64* Udev, u64 Umax, const u64* Qc, int S,
