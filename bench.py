@@ -69,6 +69,22 @@ def dist_env():
     return world, rank, local
 
 
+def aggregate_over_ranks(ms, work, device=None):
+    """Whole-job timing over ranks: the slowest rank's time and the summed
+    work (units every rank processed), one all-reduce each; identity on one
+    process.  `device` is where the reduction tensors live (the rank's GPU
+    under NCCL, the CPU under gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(work)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(w[0])
+
+
 def make_workload(name, rank, alloc=None):
     from paper_1911_04200_gb300 import synth
     if name == "ancestral64":
@@ -561,15 +577,7 @@ def run_jsim(args):
             agg["bitops"] += st["bitops_dense"]
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
-    ms_max = ms
-    bitops_all = agg["bitops"]
-    if world > 1:
-        t = torch.tensor([ms, bitops_all], dtype=torch.float64, device=dev)
-        tm = t.clone()
-        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms_max, bitops_all = float(tm[0]), float(t[1])
+    ms_max, bitops_all = aggregate_over_ranks(e0.elapsed_time(e1), agg["bitops"], dev)
     value = bitops_all / (ms_max * 1e-3) / 1e12
     last = st
 
@@ -587,13 +595,7 @@ def run_jsim(args):
             ctx.all_pairs(off, ids, out=(hC, hS, hJ))
             bo += ctx.stats()["bitops_dense"]
         barrier()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt, bo], dtype=torch.float64, device=dev)
-            tm = t.clone()
-            dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-            dt, bo = float(tm[0]), float(t[1])
+        dt, bo = aggregate_over_ranks(time.perf_counter() - t0, bo, dev)
         e2e = {"value": bo / dt / 1e12, "unit": UNIT, "h2d_bytes_per_step": int((n + 1) * 8 + N * 8),
                "d2h_bytes_per_step": int(n * n * 4 + n * 8 + n * n * 8), "ms_per_step": dt / args.steps * 1e3}
         # parity spot check of the e2e outputs against the device-resident run
