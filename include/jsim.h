@@ -77,7 +77,8 @@ extern "C" {
 #define JSIM_VARIANT_I8   3  /* legacy tensor mma.sync .s8, bits unpacked to 0/1 bytes, s32 accumulate */
 #define JSIM_VARIANT_F8   4  /* legacy tensor mma.sync .e4m3, bits unpacked to 0/1.0, f32 accumulate in exact ranges */
 #define JSIM_VARIANT_TC   5  /* tcgen05.mma kind::f8f6f4 with TMEM accumulators, 0/1.0 e4m3 operands */
-#define JSIM_VARIANT_COUNT 6
+#define JSIM_VARIANT_TC2  6  /* as TC, on pairs of SMs (cta_group::2, 256 x 256 tiles) */
+#define JSIM_VARIANT_COUNT 7
 
 /*
  * A collection of n samples in compressed-row form: sample i is

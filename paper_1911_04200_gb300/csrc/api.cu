@@ -419,6 +419,10 @@ extern "C" int jsim_product_noalloc(jsim_ctx* ctx, const uint64_t* words, uint64
             if (!product_tc_supported(ctx->opt.device)) return JSIM_ERR_UNSUPPORTED;
             e = product_tc(a, ctx->stream);
             break;
+        case JSIM_VARIANT_TC2:
+            if (!product_tc_supported(ctx->opt.device)) return JSIM_ERR_UNSUPPORTED;
+            e = product_tc_pair(a, ctx->stream);
+            break;
         case JSIM_VARIANT_POPC: e = product_popc(a, ctx->stream); break;
         case JSIM_VARIANT_B1:
         case JSIM_VARIANT_I8:

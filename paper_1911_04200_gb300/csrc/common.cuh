@@ -74,6 +74,8 @@ cudaError_t product_popc(ProductArgs& a, cudaStream_t st);
 cudaError_t product_mma(ProductArgs& a, int variant, cudaStream_t st);
 cudaError_t product_tc(ProductArgs& a, cudaStream_t st);
 cudaError_t product_tc_single(ProductArgs& a, cudaStream_t st);
+// the same product on clusters of two CTAs (tcgen05 cta_group::2)
+cudaError_t product_tc_pair(ProductArgs& a, cudaStream_t st);
 // Several independent collections in one persistent tcgen05 launch (up to
 // 256 per launch; more are launched in groups).  W is read from Wdev on the
 // device when Wdev is set (no host synchronisation), else taken from W.

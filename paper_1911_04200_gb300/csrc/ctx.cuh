@@ -304,6 +304,10 @@ int run_product(jsim_ctx* ctx, int variant, const u64* X, u64 stride, u64 n, u64
         if (!product_tc_supported(ctx->opt.device)) return JSIM_ERR_UNSUPPORTED;
         e = product_tc(a, ctx->stream);
         break;
+    case JSIM_VARIANT_TC2:
+        if (!product_tc_supported(ctx->opt.device)) return JSIM_ERR_UNSUPPORTED;
+        e = product_tc_pair(a, ctx->stream);
+        break;
     case JSIM_VARIANT_POPC: e = product_popc(a, ctx->stream); break;
     case JSIM_VARIANT_B1:
     case JSIM_VARIANT_I8:

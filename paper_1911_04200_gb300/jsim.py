@@ -20,7 +20,7 @@ ERRORS = {1: "JSIM_ERR_ARG", 2: "JSIM_ERR_UNSORTED", 3: "JSIM_ERR_OVERFLOW", 4: 
           5: "JSIM_ERR_OOM", 6: "JSIM_ERR_CUDA", 7: "JSIM_ERR_TIMEOUT", 8: "JSIM_ERR_CANCELLED",
           9: "JSIM_ERR_UNSUPPORTED"}
 MEM_HOST, MEM_DEVICE = 0, 1
-VARIANTS = {"auto": 0, "popc": 1, "b1": 2, "i8": 3, "f8": 4, "tc": 5}
+VARIANTS = {"auto": 0, "popc": 1, "b1": 2, "i8": 3, "f8": 4, "tc": 5, "tc2": 6}
 VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)

@@ -13,7 +13,7 @@ from paper_1911_04200_gb300 import jsim, synth
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ["popc", "b1", "i8", "f8", "tc"]
+VARIANTS = ["popc", "b1", "i8", "f8", "tc", "tc2"]
 
 
 def collection(segs):
