@@ -56,6 +56,8 @@ def parse():
                     choices=["clade1024", "ancestral64", "batched200", "stream4096", "serve2048"])
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--batch-rows", type=int, default=0)
+    ap.add_argument("--filter-min", type=int, default=1, choices=[1, 2],
+                    help="2: the filter keeps rows two or more samples hold (same C and J, fewer words)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -545,7 +547,7 @@ def run_jsim(args):
     d_off = torch.from_numpy(off.view(np.int64)).to(dev)
     d_ids = torch.from_numpy(ids.view(np.int64)).to(dev)
     ctx = jsim.Context(device=local, variant=args.variant, batch_rows=args.batch_rows,
-                       id_bits=cfg["id_bits"], profile=True)
+                       id_bits=cfg["id_bits"], profile=True, filter_min=args.filter_min)
     C = torch.empty((n, n), dtype=torch.uint32, device=dev)
     S = torch.empty(n, dtype=torch.uint64, device=dev)
     J = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -605,8 +607,9 @@ def run_jsim(args):
     per_launch_bitops = agg["bitops"] / max(1, agg["product_launches"])
     ms_per_launch = agg["ms_product"] / max(1, agg["product_launches"])
     roof = roofline_for(variant, per_launch_bitops, ms_per_launch, measured_peaks(),
-                        traffic_from_profiles(variant, args.workload))
+                        traffic_from_profiles(variant, args.workload) if args.filter_min == 1 else None)
     cfg.update({"batch_rows": last["batch_rows"], "batches": last["batches"], "variant": variant,
+                "filter_min": args.filter_min,
                 "rows_nonzero": last["rows_nonzero"], "words": last["words"], "values": N,
                 "bitops_dense_per_step": last["bitops_dense"], "parallelism": "dp%d (independent problems)" % world,
                 "l2": "inputs (%.1f GB of values) larger than L2 (129 MB); no flush" % (N * 8 / 1e9),

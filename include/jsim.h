@@ -114,6 +114,11 @@ typedef struct {
     int device;           /* CUDA device ordinal */
     int timeout_ms;       /* bound on device-side waits (persistent kernels, serving) */
     int profile;          /* 1: record per-stage CUDA-event times into jsim_stats */
+    int filter_min;       /* rows kept by the filter of a batch: 1 (default) keeps every
+                             row some sample holds (Eq. 5); 2 keeps rows held by two or
+                             more samples - a row only sample i holds adds 1 to C_ii alone,
+                             and C_ii = |X_i| is known, so C and J are unchanged while the
+                             product runs over fewer words.  Serving ignores it. */
 } jsim_options;
 
 typedef struct jsim_ctx jsim_ctx;
@@ -121,7 +126,8 @@ typedef struct jsim_ctx jsim_ctx;
 /* Statistics of the last jsim_all_pairs / jsim_product call on a context. */
 typedef struct {
     uint64_t batches;          /* row batches processed (non-empty ones) */
-    uint64_t rows_nonzero;     /* sum over batches of R_l = |f^(l)| (Eq. 5) */
+    uint64_t rows_nonzero;     /* sum over batches of R_l = |f^(l)| (Eq. 5; rows of two or more
+                                  samples with filter_min 2) */
     uint64_t words;            /* sum over batches of W_l = ceil(R_l / 64) */
     uint64_t batch_rows;       /* m~ actually used */
     int variant;               /* product variant actually used */

@@ -39,13 +39,16 @@ def batch_members(offsets, ids, lo: int, hi: int):
     return out
 
 
-def filter_vector(members, lo: int, mt: int):
-    """f^(l) as a boolean array of length mt (Eq. 5)."""
-    f = np.zeros(mt, dtype=bool)
+def filter_vector(members, lo: int, mt: int, min_count: int = 1):
+    """f^(l) as a boolean array of length mt (Eq. 5): rows held by at least
+    min_count samples.  min_count 1 is the paper's filter; min_count 2 keeps
+    the rows two or more samples hold (the library's filter_min 2 option: a
+    row held by sample i alone adds 1 to b_ii and nothing else)."""
+    cnt = np.zeros(mt, dtype=np.int64)
     for seg in members:
         if seg.size:
-            f[(seg - np.uint64(lo)).astype(np.int64)] = True
-    return f
+            np.add.at(cnt, (np.unique(seg) - np.uint64(lo)).astype(np.int64), 1)
+    return cnt >= min_count
 
 
 def prefix_sum(f):
@@ -54,13 +57,16 @@ def prefix_sum(f):
     return c - f.astype(np.int64)
 
 
-def bitmask_words(members, lo: int, p, R: int, b: int = 64):
-    """ahat^(l): sample-major words[n, ceil(R/b)] of b bits (uint32 or uint64)."""
+def bitmask_words(members, lo: int, p, R: int, b: int = 64, f=None):
+    """ahat^(l): sample-major words[n, ceil(R/b)] of b bits (uint32 or uint64);
+    with f, only the values whose row f keeps."""
     assert b in (32, 64)
     dt = np.uint64 if b == 64 else np.uint32
     W = (R + b - 1) // b
     words = np.zeros((len(members), W), dtype=dt)
     for i, seg in enumerate(members):
+        if f is not None and seg.size:
+            seg = seg[f[(seg - np.uint64(lo)).astype(np.int64)]]
         if seg.size == 0:
             continue
         r = p[(seg - np.uint64(lo)).astype(np.int64)]
@@ -95,13 +101,13 @@ def column_sums(members):
     return np.array([np.unique(seg).size for seg in members], dtype=np.uint64)
 
 
-def run_batch(offsets, ids, lo: int, mt: int, b: int = 64):
+def run_batch(offsets, ids, lo: int, mt: int, b: int = 64, min_count: int = 1):
     """All intermediate values of one batch, as a dict."""
     members = batch_members(offsets, ids, lo, lo + mt)
-    f = filter_vector(members, lo, mt)
+    f = filter_vector(members, lo, mt, min_count)
     p = prefix_sum(f)
     R = int(f.sum())
-    words = bitmask_words(members, lo, p, R, b)
+    words = bitmask_words(members, lo, p, R, b, f if min_count > 1 else None)
     return {"members": members, "f": f, "p": p, "R": R, "words": words,
             "s": popcount_product(words), "ahat": column_sums(members)}
 

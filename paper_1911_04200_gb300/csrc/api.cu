@@ -18,7 +18,7 @@ namespace {
 
 // Working buffers of the batch loop.
 struct BatchBufs {
-    DevBuf bitmap, dir, bsum, boff, R, X, plan_buf, bsizes;
+    DevBuf bitmap, seen, dir, bsum, boff, R, X, plan_buf, bsizes;  // bitmap: the rows kept
     Plan plan{};
     u64 X_bytes = 0;
 };
@@ -43,8 +43,16 @@ int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 widt
         StageTimer t(ctx, &ctx->stats.ms_filter);
         CK(launch_plan(st.d_off, st.d_ids, n, lo, hi, false, bb.plan, ctx->stream));
         CK(cudaMemsetAsync(bb.bitmap.p, 0, nwords * sizeof(u64), ctx->stream));
-        CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u32>(), ctx->sms,
-                         ctx->stream));
+        if (ctx->opt.filter_min == 2) {
+            // f of every row (seen) and the kept rows of two or more samples
+            ALLOC(bb.seen, nwords * sizeof(u64));
+            CK(cudaMemsetAsync(bb.seen.p, 0, nwords * sizeof(u64), ctx->stream));
+            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.seen.as<u32>(), ctx->sms,
+                             ctx->stream, bb.bitmap.as<u32>()));
+        } else {
+            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u32>(), ctx->sms,
+                             ctx->stream));
+        }
         ctx->stats.launches += 2;
     }
     {
@@ -91,6 +99,7 @@ void jsim_default_options(jsim_options* opt)
     opt->id_bits = 64;
     opt->device = 0;
     opt->timeout_ms = 2000;
+    opt->filter_min = 1;
 }
 
 int jsim_create(jsim_ctx** out, const jsim_options* opt)
@@ -104,6 +113,7 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
     if (o.id_bits < 1 || o.id_bits > 64) return JSIM_ERR_ARG;
     if (o.variant < 0 || o.variant >= JSIM_VARIANT_COUNT) return JSIM_ERR_ARG;
     if (o.batch_rows % 64 != 0) return JSIM_ERR_ARG;
+    if (o.filter_min != 1 && o.filter_min != 2) return JSIM_ERR_ARG;
     if ((o.alloc == nullptr) != (o.free == nullptr)) return JSIM_ERR_ARG;
     if (!o.alloc) { o.alloc = default_alloc; o.free = default_free; }
     jsim_ctx* c = new jsim_ctx();
@@ -221,7 +231,8 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
     {
         StageTimer t(ctx, &ctx->stats.ms_epilogue);
         if (Cdst || Jdst) {
-            CK(launch_epilogue(Cacc.p, n, ctx->opt.count_bits, st.sizes.as<u64>(), Cdst, Jdst, ctx->stream));
+            CK(launch_epilogue(Cacc.p, n, ctx->opt.count_bits, st.sizes.as<u64>(), Cdst, Jdst, ctx->stream,
+                               ctx->opt.filter_min == 2));
             ctx->stats.launches += 1;
         }
     }

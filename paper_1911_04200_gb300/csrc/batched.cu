@@ -39,7 +39,7 @@ struct Col {
 struct Wave {
     std::vector<Col> cols;
     DevBuf xpool, cpool, spool, ppool, scal, ids_pool, off_pool;
-    DevBuf bitmap, dir, bsum, boff, R;
+    DevBuf bitmap, seen, dir, bsum, boff, R;  // bitmap: the rows kept; seen: every row (filter_min 2)
     DevBuf jobtab;          // tensor-core job table
     DevBuf cstage, jstage;  // host-output staging
     u64 max_mt = 0;
@@ -97,7 +97,14 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
                 const u64 lo = cl.lo0 + l * cl.mt;
                 CK(launch_plan(cl.d_off, cl.d_ids, cl.n, lo, lo + cl.mt, false, plan, st));
                 CK(cudaMemsetAsync(w.bitmap.p, 0, nwords * sizeof(u64), st));
-                CK(launch_filter(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.bitmap.as<u32>(), ctx->sms, st));
+                if (ctx->opt.filter_min == 2) {
+                    CK(cudaMemsetAsync(w.seen.p, 0, nwords * sizeof(u64), st));
+                    CK(launch_filter(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.seen.as<u32>(), ctx->sms, st,
+                                     w.bitmap.as<u32>()));
+                } else {
+                    CK(launch_filter(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.bitmap.as<u32>(), ctx->sms,
+                                     st));
+                }
                 CK(launch_scan(w.bitmap.as<u64>(), nwords, w.dir.as<u32>(), w.bsum.as<u64>(), w.boff.as<u64>(),
                                w.R.as<u64>(), st, scal + 2 * c, scal + 2 * c + 1));
                 CK(launch_pack(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.bitmap.as<u64>(), w.dir.as<u32>(),
@@ -148,7 +155,7 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
         js += cl.n * cl.n * sizeof(double);
         if (cl.n == 0 || (!Cd && !Jd)) continue;
         CK(launch_epilogue((char*)w.cpool.p + cl.c_off, cl.n, ctx->opt.count_bits, w.spool.as<u64>() + cl.s_off, Cd,
-                           Jd, st));
+                           Jd, st, ctx->opt.filter_min == 2));
         ctx->stats.launches += 1;
     }
     return JSIM_OK;
@@ -239,6 +246,7 @@ extern "C" int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint
     u64 sig = mix(0x5151, k);
     sig = mix(sig, ctx->opt.batch_rows);
     sig = mix(sig, (u64)ctx->opt.variant * 131 + ctx->opt.count_bits * 7 + ctx->opt.id_bits);
+    sig = mix(sig, (u64)ctx->opt.filter_min);
     std::vector<Col> cl(k);
     for (u64 c = 0; c < k; ++c) {
         int rc = check_sets(&cols[c]);
@@ -424,6 +432,7 @@ replan:
         const u64 nwords = std::max<u64>(w.max_mt / 64, 1);
         const u64 nb = (nwords + kScanBlockWords - 1) / kScanBlockWords;
         ALLOC(w.bitmap, nwords * 8);
+        if (ctx->opt.filter_min == 2) ALLOC(w.seen, nwords * 8);
         ALLOC(w.dir, nwords * 4);
         ALLOC(w.bsum, std::max<u64>(nb, 1) * 8);
         ALLOC(w.boff, std::max<u64>(nb, 1) * 8);

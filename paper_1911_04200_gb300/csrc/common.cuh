@@ -37,8 +37,9 @@ cudaError_t launch_plan(const u64* offsets, const u64* ids, u64 n, u64 lo, u64 h
 cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan, u64 max_chunks,
                             int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, int sms,
                             cudaStream_t st, u64 err_stride = 0);
+// twice (optional): also the bitmap of rows held by two or more samples
 cudaError_t launch_filter(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
-                          u32* bitmap, int sms, cudaStream_t st);
+                          u32* bitmap, int sms, cudaStream_t st, u32* twice = nullptr);
 // ktotal/kbase (optional, device): append this batch's words after the
 // running word total (kbase = total; total += ceil(R/64)).
 cudaError_t launch_scan(const u64* bitmap, u64 nwords, u32* dir, u64* bsum, u64* boff, u64* R,
@@ -119,7 +120,9 @@ cudaError_t launch_qepi(const u32* Cacc, u64 S, u64 n_ref, const u64* sq, const 
 
 // ---- epilogue.cu ---------------------------------------------------------------
 // Cout[i][j] = Cacc[min(i,j)][max(i,j)], J = C / (s_i + s_j - C) (binary64), 1 if 0.
+// diag_sizes: C_ii = s_i (the product ran over rows held by two or more
+// samples, so its diagonal lacks the rows only sample i holds).
 cudaError_t launch_epilogue(const void* Cacc, u64 n, int count_bits, const u64* sizes,
-                            void* Cout, double* J, cudaStream_t st);
+                            void* Cout, double* J, cudaStream_t st, int diag_sizes = 0);
 
 }  // namespace jsim

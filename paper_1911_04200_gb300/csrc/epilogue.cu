@@ -18,7 +18,7 @@ constexpr int kE = 32;
 template <typename CT>
 __global__ void __launch_bounds__(kE * 8)
 k_epilogue(const CT* __restrict__ Cacc, u64 n, const u64* __restrict__ sizes,
-           CT* __restrict__ Cout, double* __restrict__ J)
+           CT* __restrict__ Cout, double* __restrict__ J, int diag_sizes)
 {
     __shared__ CT tile[kE][kE + 1];
     const u64 bi = blockIdx.y, bj = blockIdx.x;
@@ -44,6 +44,7 @@ k_epilogue(const CT* __restrict__ Cacc, u64 n, const u64* __restrict__ sizes,
         if (lower) c = tile[threadIdx.x][r];
         else if (bi == bj && i > j) c = tile[threadIdx.x][r];
         else c = tile[r][threadIdx.x];
+        if (diag_sizes && i == j) c = (CT)sizes[i];
         if (Cout) Cout[i * n + j] = c;
         if (J) {
             u64 u = sizes[i] + sizes[j] - (u64)c;
@@ -55,16 +56,16 @@ k_epilogue(const CT* __restrict__ Cacc, u64 n, const u64* __restrict__ sizes,
 }  // namespace
 
 cudaError_t launch_epilogue(const void* Cacc, u64 n, int count_bits, const u64* sizes,
-                            void* Cout, double* J, cudaStream_t st)
+                            void* Cout, double* J, cudaStream_t st, int diag_sizes)
 {
     if (n == 0) return cudaSuccess;
     u64 nb = (n + kE - 1) / kE;
     if (nb > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)nb, (unsigned)nb), block(kE, 8);
     if (count_bits == 64)
-        k_epilogue<u64><<<grid, block, 0, st>>>((const u64*)Cacc, n, sizes, (u64*)Cout, J);
+        k_epilogue<u64><<<grid, block, 0, st>>>((const u64*)Cacc, n, sizes, (u64*)Cout, J, diag_sizes);
     else
-        k_epilogue<u32><<<grid, block, 0, st>>>((const u32*)Cacc, n, sizes, (u32*)Cout, J);
+        k_epilogue<u32><<<grid, block, 0, st>>>((const u32*)Cacc, n, sizes, (u32*)Cout, J, diag_sizes);
     return cudaGetLastError();
 }
 

@@ -104,32 +104,40 @@ k_validate(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, 
     }
 }
 
-// f^(l): set bit (x - lo) for every value x of the batch (Eq. 5).
+// f^(l): set bit (x - lo) for every value x of the batch (Eq. 5).  With
+// `twice`, also set it there for rows held by two or more samples: the
+// atomic OR returns the bits other samples had already set.  A sample's
+// repeated value is skipped for `twice` (a set holds it once).
 __global__ void __launch_bounds__(kIngestThreads)
-k_filter(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, u32* bitmap)
+k_filter(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, u32* bitmap, u32* twice)
 {
-    __shared__ u64 s_p0, s_p1;
+    __shared__ u64 s_p0, s_p1, s_b;
     const u64 nch = plan.totals[1];
     for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
         if (threadIdx.x == 0) {
             u64 i = chunk_sample(plan.cofs, n, c);
             u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
             s_p0 = p0;
+            s_b = plan.beg[i];
             s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
         }
         __syncthreads();
-        const u64 p0 = s_p0, p1 = s_p1;
+        const u64 p0 = s_p0, p1 = s_p1, bb = s_b;
         // every warp walks whole 32-position groups so shuffles see full warps
         for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
             u64 pos = base + (threadIdx.x & 31);
             u64 q = ~0ull;
             u32 bit = 0;
             if (pos < p1) {
-                u64 d = ids[pos] - lo;
-                if (d < width) { q = d >> 5; bit = 1u << (d & 31); }
+                const u64 x = ids[pos];
+                u64 d = x - lo;
+                if (d < width && !(twice && pos > bb && ids[pos - 1] == x)) { q = d >> 5; bit = 1u << (d & 31); }
             }
             bool lead = segmented_or<u32>(q, bit);
-            if (lead && bit) atomicOr(bitmap + q, bit);
+            if (lead && bit) {
+                const u32 old = atomicOr(bitmap + q, bit);
+                if (twice && (old & bit)) atomicOr(twice + q, old & bit);
+            }
         }
         __syncthreads();
     }
@@ -223,11 +231,15 @@ k_pack(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
                 u64 x = ids[pos];
                 u64 d = x - lo;
                 if (d < width) {
-                    u64 w = d >> 6;
-                    u64 below = bitmap[w] & ((1ull << (d & 63)) - 1ull);
-                    u64 r = boff[w / kScanBlockWords] + (u64)dir[w] + (u64)__popcll(below);
-                    q = r >> 6;
-                    bit = 1ull << (r & 63);
+                    const u64 w = d >> 6, word = bitmap[w];
+                    // rows the bitmap leaves out (held by one sample, when it
+                    // is the two-or-more filter) are not packed
+                    if ((word >> (d & 63)) & 1ull) {
+                        u64 r = boff[w / kScanBlockWords] + (u64)dir[w] +
+                                (u64)__popcll(word & ((1ull << (d & 63)) - 1ull));
+                        q = r >> 6;
+                        bit = 1ull << (r & 63);
+                    }
                 }
                 if (batch_sizes) cnt += (pos == bb) || (ids[pos - 1] != x);
             }
@@ -275,9 +287,9 @@ cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan
 }
 
 cudaError_t launch_filter(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
-                          u32* bitmap, int sms, cudaStream_t st)
+                          u32* bitmap, int sms, cudaStream_t st, u32* twice)
 {
-    k_filter<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, width, bitmap);
+    k_filter<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, width, bitmap, twice);
     return cudaGetLastError();
 }
 

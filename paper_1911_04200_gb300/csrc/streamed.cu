@@ -247,7 +247,8 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
     // per row batch of the super-batch: bitmap (m~/8 B), rank directory
     // (m~/16 B) and block offsets; at most twice the staging in total
     const u64 nwords = mt / 64;
-    const u64 rb_bytes = nwords * 12 + (nwords + kScanBlockWords - 1) / kScanBlockWords * 16;
+    const u64 rb_bytes = nwords * (ctx->opt.filter_min == 2 ? 20 : 12) +
+                         (nwords + kScanBlockWords - 1) / kScanBlockWords * 16;
     const u64 rb_cap = std::max<u64>(1, std::min<u64>(2 * staging_bytes / rb_bytes, 1u << 16));
     std::vector<Super> sup;
     rc = plan_supers(hoff, ids, n, mt, cap_vals, rb_cap, sup);
@@ -265,7 +266,7 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
     }
     const u64 nw_max = rb_max * nwords;  // bitmap words of the widest super-batch
     const u64 nbk_max = std::max<u64>((nw_max + kScanBlockWords - 1) / kScanBlockWords, 1);
-    DevBuf dbuf[2], Cacc, sizes_d, flags, plan_buf, X, bm, dir, bsum, boff, Rd, Cst, Jst;
+    DevBuf dbuf[2], Cacc, sizes_d, flags, plan_buf, X, bm, seen, dir, bsum, boff, Rd, Cst, Jst;
     ALLOC(dbuf[0], (head + count_max) * sizeof(u64));
     ALLOC(dbuf[1], (head + count_max) * sizeof(u64));
     CopyFence fence{xs};
@@ -273,7 +274,9 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
     ALLOC(sizes_d, n * sizeof(u64));
     ALLOC(flags, 3 * sizeof(u64));
     ALLOC(plan_buf, (3 * n + 5) * sizeof(u64));
-    ALLOC(bm, nw_max * sizeof(u64));
+    ALLOC(bm, nw_max * sizeof(u64));  // the rows kept
+    const bool twice = ctx->opt.filter_min == 2;
+    if (twice) ALLOC(seen, nw_max * sizeof(u64));
     ALLOC(dir, nw_max * sizeof(u32));
     ALLOC(bsum, nbk_max * sizeof(u64));
     ALLOC(boff, nbk_max * sizeof(u64));
@@ -335,7 +338,12 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
         {
             StageTimer t(ctx, &ctx->stats.ms_filter);
             CK(cudaMemsetAsync(bm.p, 0, nw * sizeof(u64), cs));
-            CK(launch_filter(d_ids, n, plan, max_chunks, lo, width, bm.as<u32>(), ctx->sms, cs));
+            if (twice) {
+                CK(cudaMemsetAsync(seen.p, 0, nw * sizeof(u64), cs));
+                CK(launch_filter(d_ids, n, plan, max_chunks, lo, width, seen.as<u32>(), ctx->sms, cs, bm.as<u32>()));
+            } else {
+                CK(launch_filter(d_ids, n, plan, max_chunks, lo, width, bm.as<u32>(), ctx->sms, cs));
+            }
             ctx->stats.launches += 1;
         }
         {
@@ -393,7 +401,7 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
     {
         StageTimer t(ctx, &ctx->stats.ms_epilogue);
         if (Cdst || Jdst) {
-            CK(launch_epilogue(Cacc.p, n, ctx->opt.count_bits, sizes_d.as<u64>(), Cdst, Jdst, cs));
+            CK(launch_epilogue(Cacc.p, n, ctx->opt.count_bits, sizes_d.as<u64>(), Cdst, Jdst, cs, twice));
             ctx->stats.launches += 1;
         }
     }

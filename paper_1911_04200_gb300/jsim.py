@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
     _fields_ = [("batch_rows", ctypes.c_uint64), ("word_bits", ctypes.c_int), ("variant", ctypes.c_int),
                 ("count_bits", ctypes.c_int), ("id_bits", ctypes.c_int), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("stream", ctypes.c_void_p),
-                ("device", ctypes.c_int), ("timeout_ms", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("device", ctypes.c_int), ("timeout_ms", ctypes.c_int), ("profile", ctypes.c_int),
+                ("filter_min", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -163,7 +164,7 @@ class Context:
 
     def __init__(self, device: int = 0, variant: str | int = "auto", batch_rows: int = 0, word_bits: int = 64,
                  count_bits: int = 32, id_bits: int = 64, profile: bool = False, stream=None,
-                 use_torch_allocator: bool = True, timeout_ms: int = 2000):
+                 use_torch_allocator: bool = True, timeout_ms: int = 2000, filter_min: int = 1):
         torch = _torch()
         self._lib = load()
         self.device = device
@@ -180,6 +181,7 @@ class Context:
         o.device = device
         o.profile = 1 if profile else 0
         o.timeout_ms = timeout_ms
+        o.filter_min = filter_min
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         self._keep = []
         if use_torch_allocator:

@@ -93,3 +93,11 @@ def test_batched_errors(gpu):
         assert e.value.name == "JSIM_ERR_UNSORTED"
         outs = ctx.all_pairs_batched([good])
         assert outs[0][2][0, 0] == 1.0
+
+
+@pytest.mark.parametrize("variant", ["auto", "tc", "popc"])
+def test_batched_two_or_more_filter(gpu, cols, refs, variant):
+    with jsim.Context(variant=variant, id_bits=32, filter_min=2) as ctx:
+        outs = ctx.all_pairs_batched(cols)
+    for (C, s, J), ref in zip(outs, refs):
+        assert_same((C, s, J), ref)

@@ -231,6 +231,33 @@ def test_filter_invariance_and_word_layout():
     np.testing.assert_array_equal(out["p"][nz], np.arange(nz.size))
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_two_or_more_filter_keeps_every_off_diagonal_count(seed):
+    """Rows held by a single sample (the library's filter_min 2 drops them)
+    add only to that sample's diagonal entry: packing the rows held by two or
+    more samples gives A^T A off the diagonal, and the column sums restore the
+    diagonal.  Pinned against the dense 0/1 product, duplicates included."""
+    rng = np.random.default_rng(300 + seed)
+    n, m = 9, 2000
+    offsets, ids, A = random_collection(rng, n, m, [0.002, 0.03, 0.3, 0.8][seed], dup_prob=0.2)
+    Ai = A.astype(np.int64)
+    AtA = Ai.T @ Ai
+    for mt in (64, 512, 2048):
+        B = np.zeros((n, n), dtype=np.int64)
+        for lo in range(0, m, mt):
+            width = min(mt, m - lo)
+            out = packed.run_batch(offsets, ids, lo, width, 64, min_count=2)
+            B += out["s"].astype(np.int64)
+            counts = A[lo:lo + width].sum(axis=1)
+            np.testing.assert_array_equal(out["f"], counts >= 2)
+            assert out["R"] == int((counts >= 2).sum())
+        off = ~np.eye(n, dtype=bool)
+        np.testing.assert_array_equal(B[off], AtA[off])
+        assert np.all(np.diag(B) <= np.diag(AtA))
+        B[np.diag_indices(n)] = Ai.sum(axis=0)
+        np.testing.assert_array_equal(B, AtA)
+
+
 def test_pins_catch_planted_mistakes():
     """A union without the -C term, or an off-by-one in the merge, fails the
     brute-force pin (mistakes planted in copies of the oracle's formulas)."""

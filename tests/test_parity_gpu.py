@@ -198,3 +198,59 @@ def test_variants_agree_on_clade_batches(gpu, variant):
         out = ctx.all_pairs(off, ids)
     for a, b in zip(out, ref):
         np.testing.assert_array_equal(a.view(np.uint8), b.view(np.uint8))
+
+
+# ---- filter_min 2: the product over rows two or more samples hold ------------------
+
+@pytest.mark.parametrize("variant", ["popc", "tc", "tc2", "f8"])
+@pytest.mark.parametrize("batch_rows", [0, 1 << 14])
+def test_two_or_more_filter_ancestral64(gpu, c1, c1_ref, variant, batch_rows):
+    """Dropping rows only one sample holds leaves C, sizes and J unchanged."""
+    with jsim.Context(variant=variant, batch_rows=batch_rows, filter_min=2) as ctx:
+        assert_same(ctx.all_pairs(*c1), c1_ref)
+        st2 = ctx.stats()
+    with jsim.Context(variant=variant, batch_rows=batch_rows) as ctx:
+        ctx.all_pairs(*c1)
+        st1 = ctx.stats()
+    assert st2["rows_nonzero"] < st1["rows_nonzero"]
+
+
+@pytest.mark.parametrize("n,median", [(130, 2e4), (257, 5e3)])
+def test_two_or_more_filter_clade(gpu, n, median):
+    off, ids = synth.clade1024(n=n, median=median)
+    ref = oracle.all_pairs(off, ids)
+    for count_bits in (32, 64):
+        with jsim.Context(filter_min=2, count_bits=count_bits) as ctx:
+            assert_same(ctx.all_pairs(off, ids), ref)
+
+
+def test_two_or_more_filter_edge_cases(gpu):
+    segs = [[], [0], [0, 0, 0], [5, 5, 9], [9], list(range(100, 400)), list(range(100, 400)), [2**64 - 1],
+            [2**64 - 1, 2**64 - 1], [7, 8, 9, 10], []]
+    off, ids = collection(segs)
+    ref = oracle.all_pairs(off, ids)
+    for br in (0, 64, 1 << 20):
+        with jsim.Context(filter_min=2, batch_rows=br) as ctx:
+            assert_same(ctx.all_pairs(off, ids), ref)
+    # every row held by one sample: nothing to multiply, the diagonal is |X_i|
+    off, ids = collection([[1, 2, 3], [4, 5], [], [6]])
+    with jsim.Context(filter_min=2) as ctx:
+        assert_same(ctx.all_pairs(off, ids), oracle.all_pairs(off, ids))
+        assert ctx.stats()["words"] == 0
+    with pytest.raises(jsim.JsimError):
+        jsim.Context(filter_min=3)
+
+
+@pytest.mark.parametrize("lo,width", [(0, 1 << 20), (123 * 64, 64 * 1000)])
+def test_pack_two_or_more_matches_packed_oracle(gpu, c1, lo, width):
+    off, ids = c1
+    sub_off = off[:9]
+    sub_ids = ids[:int(off[8])]
+    ref = packed.run_batch(sub_off, sub_ids, lo, width, 64, min_count=2)
+    with jsim.Context(filter_min=2) as ctx:
+        filt, words, R, sz = ctx.pack(sub_off, sub_ids, lo, width)
+    assert R == ref["R"]
+    fbits = np.unpackbits(filt.view(np.uint8), bitorder="little").astype(bool)
+    np.testing.assert_array_equal(fbits, ref["f"])
+    np.testing.assert_array_equal(words[:, :ref["words"].shape[1]], ref["words"])
+    np.testing.assert_array_equal(sz, ref["ahat"])

@@ -126,3 +126,8 @@ def test_streamed_errors(gpu):
         with pytest.raises(jsim.JsimError) as e:
             ctx.all_pairs_streamed(*collection([[1, 2**20], [4]]), staging_bytes=MIB)
         assert e.value.name == "JSIM_ERR_ID_RANGE"
+
+
+def test_streamed_two_or_more_filter(gpu, c1, c1_ref):
+    with jsim.Context(batch_rows=1 << 14, filter_min=2) as ctx:
+        assert_same(ctx.all_pairs_streamed(*c1, staging_bytes=MIB), c1_ref)
