@@ -281,13 +281,14 @@ u64 auto_batch_rows(u64 domain)
 
 // Variant choice (measured on GB300: for 1024 samples the CUDA-core
 // AND+popcount kernel runs ~128 Tbit-ops/s, the legacy mma.sync e4m3/s8/b1
-// kernels at or below that, the tcgen05 FP8 kernel ~700; for 64 samples the
-// CUDA-core kernel wins, 0.33 ms against 0.88 ms per all-pairs call, because
-// one 128 x 256 tensor tile is mostly idle).
+// kernels at or below that, the one-SM tcgen05 FP8 kernel ~680 and the SM-pair
+// kernel ~840 (~1130 at 4096 samples); for 64 samples the CUDA-core kernel
+// wins, 0.33 ms against 0.88 ms per all-pairs call, because one tensor tile is
+// mostly idle).
 int choose_variant(jsim_ctx* ctx, u64 n, u64 W)
 {
     (void)W;
-    if (n >= 256 && product_tc_supported(ctx->opt.device)) return JSIM_VARIANT_TC;
+    if (n >= 256 && product_tc_supported(ctx->opt.device)) return JSIM_VARIANT_TC2;
     return JSIM_VARIANT_POPC;
 }
 

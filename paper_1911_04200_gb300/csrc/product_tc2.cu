@@ -16,23 +16,26 @@
 // above the diagonal (tile rows [256 ti, +256), columns [256 tj, +256),
 // ti <= tj).  Per stage of 128 bit-rows, CTA r unpacks A rows
 // 256 ti + 128 r + [0, 128) and B rows 256 tj + 128 r + [0, 128) into its
-// own stage buffer (same offsets in both CTAs).  Roles (21 warps per CTA):
-//   warps 0-15  unpack, in two groups of 8 warps taking alternate stages
-//               (thread p of a group: row p, A for p < 128, else B), four of
-//               its stages of packed words ahead in registers; after writing a stage
+// own stage buffer (same offsets in both CTAs).  Roles (kGroups = 1: 13
+// warps per CTA):
+//   warps 0-7   unpack (with kGroups = 2, two groups of 8 warps taking
+//               alternate stages; thread p of a group: row p, A for p < 128,
+//               else B), four of its stages of packed words ahead in
+//               registers; after writing a stage
 //               and fencing for the async proxy, one lane per warp arrives on
 //               `full` (rank 0) or on the local `ready` (rank 1), whose
 //               completion the rank-1 signal thread forwards to the rank-0
 //               `full` (one cluster-scope release per stage, 9 arrivals);
-//   warp 16     rank 1: the signal thread; rank 0: one lane issues 4 tcgen05.mma
+//   warp 8      rank 1: the signal thread; rank 0: one lane issues 8 tcgen05.mma
 //               (cta_group::2, M = 256, N = 256, K = 32) per stage into one of
 //               two TMEM accumulators and commits them, multicast to both
 //               CTAs, to `empty` (stage reusable) and, per finished segment,
 //               to `acc_full`;
-//   warps 17-20 epilogue in both CTAs: read this CTA's 128 accumulator rows
+//   warps 9-12  epilogue in both CTAs: read this CTA's 128 accumulator rows
 //               with tcgen05.ld, add them into C, and arrive (a lane per
 //               warp) on the rank-0 CTA's `acc_empty` (8 arrivals).
-// Six 32 KiB stage buffers per CTA.  Every wait is bounded (clock64 budget,
+// Three 64 KiB stage buffers per CTA (256 bit-rows: two atom columns).
+// Every wait is bounded (clock64 budget,
 // plus a CTA-wide abort flag); on time-out the CTA raises the error word,
 // waits (bounded) for the MMAs already issued, and both CTAs meet at a
 // cluster barrier before TMEM is freed and the CTAs exit.
@@ -43,15 +46,22 @@ namespace jsim {
 
 namespace {
 
-// Build-time tuning (JSIM_TC2_GROUPS, JSIM_TC2_BUFS, JSIM_TC2_AHEAD).
+// Build-time tuning (JSIM_TC2_GROUPS, JSIM_TC2_BUFS, JSIM_TC2_AHEAD,
+// JSIM_TC2_KBITS).  Measured on GB300 (n = 1024 .. 4096): 256 bit-rows per
+// stage in three 64 KiB buffers is fastest - 1.46x the 128-bit stages, whose
+// per-stage barrier round trips and proxy fences bound the kernel; 384-bit
+// stages (two buffers) and a second producer group change little.
 #ifndef JSIM_TC2_GROUPS
 #define JSIM_TC2_GROUPS 1
 #endif
 #ifndef JSIM_TC2_BUFS
-#define JSIM_TC2_BUFS 6
+#define JSIM_TC2_BUFS 3
 #endif
 #ifndef JSIM_TC2_AHEAD
 #define JSIM_TC2_AHEAD 4
+#endif
+#ifndef JSIM_TC2_KBITS
+#define JSIM_TC2_KBITS 256
 #endif
 constexpr int kGroups = JSIM_TC2_GROUPS;          // producer groups, taking alternate stages
 constexpr int kGroupWarps = 8;                    // warps per group: one row per thread
@@ -65,11 +75,14 @@ constexpr int kTile = 256;                        // tile side (rows and columns
 static_assert(2 * kHalf == kGroupWarps * 32, "one row per producer thread");
 
 static_assert(kEpiWarp0 % 4 == 1, "epilogue warp e reads TMEM lanes of warp rank (kEpiWarp0 + e) % 4");
-constexpr int kStageBits = 128;                   // bit-rows per stage = one 128-byte swizzle atom row
+constexpr int kStageBits = JSIM_TC2_KBITS;        // bit-rows per stage: kAtoms 128-byte swizzle atom columns
+constexpr int kAtoms = kStageBits / 128;
+static_assert(kAtoms >= 1 && kAtoms <= 4 && kStageBits % 128 == 0, "whole atom columns per stage");
 constexpr int kStageWords = kStageBits / 64;
 constexpr int kBlkBytes = 128;
-constexpr int kABytes = kHalf * kBlkBytes;        // 16 KiB
-constexpr int kStageBytes = 2 * kHalf * kBlkBytes;  // 32 KiB
+constexpr int kAtom = kHalf * kBlkBytes;          // one atom column of a half (A or B): 16 KiB
+constexpr int kABytes = kAtoms * kAtom;
+constexpr int kStageBytes = 2 * kAtoms * kAtom;   // 32 KiB per atom column
 constexpr int kBufs = JSIM_TC2_BUFS;
 constexpr int kAhead = JSIM_TC2_AHEAD;
 static_assert(kBufs % kGroups == 0, "stage buffers split evenly over the groups");
@@ -312,14 +325,15 @@ k_prod_tc2(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 tiles, u64 L
         const bool is_a = p < kHalf;
         const int row = is_a ? p : p - kHalf;
         const u32 row_off = (u32)((is_a ? 0 : kABytes) + row * kBlkBytes);
-        u64 ring[kAhead][2];
+        u64 ring[kAhead][kStageWords];
         WorkIter fit;
         fit.init(tiles, nst, L, G, c);
         u64 f_tile = ~0ull, f_kst = 0, f_left = 0, f_r0 = 0, f_c0 = 0;
         // advance the fetch position by one stage; load this thread's words
         // of it when `load` (0 past the end)
-        auto fetch = [&](u64 (&v)[2], bool load) {
-            v[0] = v[1] = 0ull;
+        auto fetch = [&](u64 (&v)[kStageWords], bool load) {
+            #pragma unroll
+            for (int q = 0; q < kStageWords; ++q) v[q] = 0ull;
             if (f_left == 0) {
                 u64 tile;
                 if (!fit.next(tile, f_kst, f_left)) return;
@@ -329,25 +343,29 @@ k_prod_tc2(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 tiles, u64 L
             const u64 gk = f_kst * kStageWords;
             if (load && grow < n) {
                 const u64* src = X + grow * stride + gk;
-                if (vec16 && gk + 1 < W) {
-                    asm volatile("ld.global.nc.v2.u64 {%0,%1}, [%2];\n" : "=l"(v[0]), "=l"(v[1]) : "l"(src));
-                } else {
-                    if (gk < W) v[0] = __ldg(src);
-                    if (gk + 1 < W) v[1] = __ldg(src + 1);
+                #pragma unroll
+                for (int q = 0; q < kStageWords; q += 2) {
+                    if (vec16 && gk + q + 1 < W) {
+                        asm volatile("ld.global.nc.v2.u64 {%0,%1}, [%2];\n"
+                                     : "=l"(v[q]), "=l"(v[q + 1]) : "l"(src + q));
+                    } else {
+                        if (gk + q < W) v[q] = __ldg(src + q);
+                        if (gk + q + 1 < W) v[q + 1] = __ldg(src + q + 1);
+                    }
                 }
             }
             --f_left;
             ++f_kst;
         };
         // this group's next stage: load it, then skip the other groups' stages
-        auto fetch_own = [&](u64 (&v)[2]) {
+        auto fetch_own = [&](u64 (&v)[kStageWords]) {
             fetch(v, true);
-            u64 skip[2];
+            u64 skip[kStageWords];
             #pragma unroll
             for (int q = 1; q < kGroups; ++q) fetch(skip, false);
         };
         {
-            u64 skip[2];
+            u64 skip[kStageWords];
             for (int q = 0; q < g; ++q) fetch(skip, false);
         }
         #pragma unroll
@@ -363,17 +381,21 @@ k_prod_tc2(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 tiles, u64 L
                     ok = false;
                     break;
                 }
-                unsigned char* rowp = sm + b * kStageBytes + row_off;
                 #pragma unroll
-                for (int cc = 0; cc < 8; ++cc) {
-                    const u32 half = (cc & 2) ? (u32)(ring[a][cc >> 2] >> 32) : (u32)ring[a][cc >> 2];
-                    const int sh = (cc & 1) * 16;
-                    uint4 o;
-                    o.x = expand4((half >> sh) & 15u);
-                    o.y = expand4((half >> (sh + 4)) & 15u);
-                    o.z = expand4((half >> (sh + 8)) & 15u);
-                    o.w = expand4((half >> (sh + 12)) & 15u);
-                    *(uint4*)(rowp + ((cc ^ (row & 7)) << 4)) = o;
+                for (int at = 0; at < kAtoms; ++at) {
+                    unsigned char* rowp = sm + b * kStageBytes + row_off + at * kAtom;
+                    #pragma unroll
+                    for (int cc = 0; cc < 8; ++cc) {
+                        const u64 wv = ring[a][2 * at + (cc >> 2)];
+                        const u32 half = (cc & 2) ? (u32)(wv >> 32) : (u32)wv;
+                        const int sh = (cc & 1) * 16;
+                        uint4 o;
+                        o.x = expand4((half >> sh) & 15u);
+                        o.y = expand4((half >> (sh + 4)) & 15u);
+                        o.z = expand4((half >> (sh + 8)) & 15u);
+                        o.w = expand4((half >> (sh + 12)) & 15u);
+                        *(uint4*)(rowp + ((cc ^ (row & 7)) << 4)) = o;
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 __syncwarp();
@@ -420,8 +442,8 @@ k_prod_tc2(const u64* __restrict__ X, u64 stride, u64 n, u64 W, u64 tiles, u64 L
                     const u32 abase = base + b * kStageBytes, bbase = abase + kABytes;
                     #pragma unroll
                     for (int k = 0; k < kStageBits / 32; ++k) {
-                        const u64 da = sw128_desc(abase + k * 32);
-                        const u64 db = sw128_desc(bbase + k * 32);
+                        const u64 da = sw128_desc(abase + (k >> 2) * kAtom + (k & 3) * 32);
+                        const u64 db = sw128_desc(bbase + (k >> 2) * kAtom + (k & 3) * 32);
                         const u32 accum = (fresh && q == 0 && k == 0) ? 0u : 1u;
                         asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                      " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
@@ -534,7 +556,7 @@ cudaError_t run(ProductArgs& a, cudaStream_t st)
     const u64 nst = (a.W + kStageWords - 1) / kStageWords;
     const u64 total = tiles * nst;
     if (total == 0) return cudaSuccess;
-    u64 L = (48ull << 20) / (16ull * std::max<u64>(a.n, 1));
+    u64 L = (48ull << 20) / ((u64)kStageWords * 8ull * std::max<u64>(a.n, 1));
     L = std::max<u64>(64, std::min<u64>(L, kMaxSegStages));
     cudaError_t e = cudaFuncSetAttribute(k_prod_tc2<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;

@@ -39,7 +39,7 @@ def c1_ref(c1):
 
 
 @pytest.mark.parametrize("batch_rows,staging", [(1 << 14, MIB), (3 << 12, MIB), (1 << 16, 4 * MIB), (0, 64 * MIB)])
-@pytest.mark.parametrize("variant", ["auto", "popc", "tc"])
+@pytest.mark.parametrize("variant", ["auto", "popc", "tc", "tc2"])
 def test_ancestral64_streamed(gpu, c1, c1_ref, batch_rows, staging, variant):
     """Several super-batches (1 MiB staging = 131,072 values of 3.1e6), each
     several row batches with a ragged last one, give the oracle's results."""

@@ -28,6 +28,7 @@ def to_np(t):
 @pytest.mark.parametrize("n,W,density,count_bits,variant", [
     (300, 777, 0.3, 32, "auto"),
     (1024, 2048, 0.05, 32, "tc"),
+    (600, 1500, 0.2, 64, "tc2"),
     (700, 500, 0.5, 64, "popc"),
     (130, 64, 1.0, 64, "f8"),
 ])
