@@ -107,8 +107,8 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
                 }
                 CK(launch_scan(w.bitmap.as<u64>(), nwords, w.dir.as<u32>(), w.bsum.as<u64>(), w.boff.as<u64>(),
                                w.R.as<u64>(), st, scal + 2 * c, scal + 2 * c + 1));
-                CK(launch_pack(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.bitmap.as<u64>(), w.dir.as<u32>(),
-                               w.boff.as<u64>(), X, cl.stride, nullptr, ctx->sms, st, scal + 2 * c + 1));
+                CK(launch_pack_full(cl.d_ids, cl.n, plan, cl.max_chunks, lo, w.bitmap.as<u64>(), w.dir.as<u32>(),
+                                    w.boff.as<u64>(), X, cl.stride, w.R.as<u64>(), ctx->sms, st, scal + 2 * c + 1));
                 ctx->stats.launches += 5;
             }
         }

@@ -261,6 +261,106 @@ k_pack(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
     }
 }
 
+// Packing with plain stores instead of atomic read-modify-writes: every
+// nonzero word of a batch's rows is written once, complete, into the zeroed
+// packed matrix.  Rank r' (the number of kept rows below a value) is
+// non-decreasing along a sample's sorted values, and so is its word q = r'/64
+// (a value whose row is not kept still has an insertion word).  A sample's
+// values in a chunk are cut into warp segments of kPackSeg values; segment k
+// owns the words (q of the last value before it, q of its last value]: it
+// writes their completed masks, finishing its last word by reading ahead
+// into the next segment's values while their word is the same.
+constexpr int kPackSeg = 512;
+static_assert(kChunk % kPackSeg == 0 && kPackSeg * (kIngestThreads / 32) == kChunk,
+              "a chunk is one segment per warp");
+
+__device__ __forceinline__ long long insertion_word(u64 x, u64 lo, const u64* __restrict__ bitmap,
+                                                    const u32* __restrict__ dir, const u64* __restrict__ boff,
+                                                    u64& bit)
+{
+    const u64 d = x - lo, w = d >> 6, word = bitmap[w];
+    const u64 below = word & ((1ull << (d & 63)) - 1ull);
+    const u64 r = boff[w / kScanBlockWords] + (u64)dir[w] + (u64)__popcll(below);
+    bit = ((word >> (d & 63)) & 1ull) ? (1ull << (r & 63)) : 0ull;
+    return (long long)(r >> 6);
+}
+
+__global__ void __launch_bounds__(kIngestThreads)
+k_pack_full(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, const u64* __restrict__ bitmap,
+            const u32* __restrict__ dir, const u64* __restrict__ boff, u64* X, u64 stride,
+            const u64* kbase, const u64* __restrict__ Rdev)
+{
+    __shared__ u64 s_i, s_p0, s_p1, s_b, s_e;
+    const u64 nch = plan.totals[1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long Wl = (long long)((*Rdev + 63) / 64);
+    const long long kBig = 0x7fffffffffffffffll;
+    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const u64 i = chunk_sample(plan.cofs, n, c);
+            const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+            s_i = i; s_p0 = p0; s_b = plan.beg[i];
+            s_e = plan.beg[i] + plan.len[i];
+            s_p1 = min(p0 + kChunk, s_e);
+        }
+        __syncthreads();
+        const u64 i = s_i, bb = s_b, be = s_e;
+        const u64 sbeg = s_p0 + (u64)warp * kPackSeg, send = min(sbeg + kPackSeg, s_p1);
+        __syncthreads();  // the shared chunk fields are read; the next chunk may overwrite them
+        if (sbeg >= send) continue;
+        u64* row = X + i * stride + (kbase ? *kbase : 0ull);
+        u64 tmp;
+        const long long seg_prev = sbeg > bb ? insertion_word(ids[sbeg - 1], lo, bitmap, dir, boff, tmp) : -1ll;
+        long long open_key = seg_prev;
+        u64 open_mask = 0ull;
+        for (u64 base = sbeg; base < send; base += 32) {
+            const u64 pos = base + lane;
+            long long key = kBig;
+            u64 bit = 0ull;
+            if (pos < send) key = insertion_word(ids[pos], lo, bitmap, dir, boff, bit);
+            const bool lead = segmented_or<u64>((u64)key, bit);
+            const bool real = lead && key != kBig;
+            const unsigned leads = __ballot_sync(0xffffffffu, real);
+            const int last_lead = 31 - __clz((int)leads);  // leads != 0: lane 0 holds a value
+            long long nkey = open_key;
+            u64 nmask = open_mask;
+            if (real) {
+                u64 mask = bit;
+                if (lane == 0) {
+                    if (key == open_key) {
+                        mask |= open_mask;  // the open word continues
+                    } else if (open_key > seg_prev && open_key < Wl && open_mask) {
+                        row[open_key] = open_mask;  // the open word is complete
+                    }
+                }
+                if (lane != last_lead) {
+                    if (key > seg_prev && key < Wl && mask) row[key] = mask;
+                } else {
+                    nkey = key;
+                    nmask = mask;
+                }
+            }
+            open_key = __shfl_sync(0xffffffffu, nkey, last_lead);
+            open_mask = __shfl_sync(0xffffffffu, nmask, last_lead);
+        }
+        if (open_key > seg_prev) {
+            // finish the last word with the next segment's values of the same word
+            for (u64 base = send; base < be; base += 32) {
+                const u64 pos = base + lane;
+                long long key = kBig;
+                u64 bit = 0ull;
+                if (pos < be) key = insertion_word(ids[pos], lo, bitmap, dir, boff, bit);
+                u64 m = key == open_key ? bit : 0ull;
+                #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+                open_mask |= m;
+                if (__any_sync(0xffffffffu, key != open_key)) break;
+            }
+            if (lane == 0 && open_key < Wl && open_mask) row[open_key] = open_mask;
+        }
+    }
+}
+
 inline unsigned grid_for_chunks(u64 max_chunks, int sms)
 {
     u64 g = (u64)sms * 8;
@@ -302,6 +402,15 @@ cudaError_t launch_scan(const u64* bitmap, u64 nwords, u32* dir, u64* bsum, u64*
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_scan_top<<<1, 1024, 0, st>>>(bsum, nb, boff, R, ktotal, kbase);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_full(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, const u64* bitmap,
+                             const u32* dir, const u64* boff, u64* X, u64 stride, const u64* Rdev, int sms,
+                             cudaStream_t st, const u64* kbase)
+{
+    k_pack_full<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, bitmap, dir, boff, X,
+                                                                            stride, kbase, Rdev);
     return cudaGetLastError();
 }
 

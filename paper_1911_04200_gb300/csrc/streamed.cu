@@ -361,8 +361,8 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
             ALLOC(X, n_pad * stride * sizeof(u64));
             StageTimer t(ctx, &ctx->stats.ms_pack);
             CK(launch_zero_rows(X.as<u64>(), n_pad, stride, stride, ctx->sms, cs));
-            CK(launch_pack(d_ids, n, plan, max_chunks, lo, width, bm.as<u64>(), dir.as<u32>(), boff.as<u64>(),
-                           X.as<u64>(), stride, nullptr, ctx->sms, cs));
+            CK(launch_pack_full(d_ids, n, plan, max_chunks, lo, bm.as<u64>(), dir.as<u32>(), boff.as<u64>(),
+                                X.as<u64>(), stride, Rd.as<u64>(), ctx->sms, cs));
             ctx->stats.launches += 2;
         }
         CK(cudaEventRecord(ss->released[k], cs));  // the slice's values are no longer read
