@@ -54,12 +54,15 @@ constexpr int kN = 256;                        // B-side rows per tile
 constexpr int kRows = kM + kN;                 // rows unpacked per stage (one per producer thread)
 static_assert(kRows == kProducerWarps * 32, "one row per producer thread");
 static_assert(kEpiWarp0 % 4 == 1, "epilogue warp e reads TMEM lanes of warp rank (kEpiWarp0 + e) % 4");
-constexpr int kStageBits = 128;                // bit-rows per stage = one 128-byte swizzle atom row
+constexpr int kStageBits = 256;                // bit-rows per stage: two 128-byte swizzle atom columns
+constexpr int kAtoms = kStageBits / 128;
 constexpr int kStageWords = kStageBits / 64;
 constexpr int kBlkBytes = 128;
-constexpr int kABytes = kM * kBlkBytes;        // 16 KiB
-constexpr int kStageBytes = kRows * kBlkBytes; // 48 KiB
-constexpr int kBufs = 4;
+constexpr int kAtomA = kM * kBlkBytes;         // one atom column of A: 16 KiB
+constexpr int kAtomB = kN * kBlkBytes;         // one atom column of B: 32 KiB
+constexpr int kABytes = kAtoms * kAtomA;
+constexpr int kStageBytes = kAtoms * kRows * kBlkBytes;  // 96 KiB
+constexpr int kBufs = 2;
 constexpr int kAhead = 4;                      // stages of packed words held in registers
 constexpr int kSmemBytes = kBufs * kStageBytes + 1024;  // + alignment slack
 static_assert(kSmemBytes <= 232448, "fits the per-CTA shared-memory limit");
@@ -333,7 +336,8 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         const bool is_a = p < kM;
         const int row = is_a ? p : p - kM;
         const u32 row_off = (u32)((is_a ? 0 : kABytes) + row * kBlkBytes);
-        u64 ring[kAhead][2];
+        const u32 atom_step = (u32)(is_a ? kAtomA : kAtomB);
+        u64 ring[kAhead][kStageWords];
         // position of the next fetch: the current segment's job, tile (first
         // row and column), stage, and stages left in it
         WorkIter fit;
@@ -342,8 +346,9 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         u64 f_key = ~0ull, f_kst = 0, f_left = 0, f_r0 = 0, f_c0 = 0, f_n = 0, f_W = 0, f_stride = 0;
         const u64* f_X = nullptr;
         // packed words of this thread's row at the next fetch position (0 past the end)
-        auto fetch = [&](u64 (&v)[2]) {
-            v[0] = v[1] = 0ull;
+        auto fetch = [&](u64 (&v)[kStageWords]) {
+            #pragma unroll
+            for (int q = 0; q < kStageWords; ++q) v[q] = 0ull;
             if (f_left == 0) {
                 if (!fit.next(fs)) return;
                 f_kst = fs.kst;
@@ -361,12 +366,16 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
             u64 gk = f_kst * kStageWords;
             if (grow < f_n) {
                 const u64* src = f_X + grow * f_stride + gk;
-                if (P.vec16 && gk + 1 < f_W) {
-                    // both words of the stage in one 16-byte load
-                    asm volatile("ld.global.nc.v2.u64 {%0,%1}, [%2];\n" : "=l"(v[0]), "=l"(v[1]) : "l"(src));
-                } else {
-                    if (gk < f_W) v[0] = __ldg(src);
-                    if (gk + 1 < f_W) v[1] = __ldg(src + 1);
+                #pragma unroll
+                for (int q = 0; q < kStageWords; q += 2) {
+                    if (P.vec16 && gk + q + 1 < f_W) {
+                        // two words of the stage in one 16-byte load
+                        asm volatile("ld.global.nc.v2.u64 {%0,%1}, [%2];\n"
+                                     : "=l"(v[q]), "=l"(v[q + 1]) : "l"(src + q));
+                    } else {
+                        if (gk + q < f_W) v[q] = __ldg(src + q);
+                        if (gk + q + 1 < f_W) v[q + 1] = __ldg(src + q + 1);
+                    }
                 }
             }
             --f_left;
@@ -387,18 +396,22 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                     ok = false;
                     break;
                 }
-                unsigned char* rowp = sm + b * kStageBytes + row_off;
                 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    // bits 16c .. 16c+15 of the stage row -> 16 bytes
-                    const u32 half = (c & 2) ? (u32)(ring[a][c >> 2] >> 32) : (u32)ring[a][c >> 2];
-                    const int sh = (c & 1) * 16;
-                    uint4 o;
-                    o.x = expand4((half >> sh) & 15u);
-                    o.y = expand4((half >> (sh + 4)) & 15u);
-                    o.z = expand4((half >> (sh + 8)) & 15u);
-                    o.w = expand4((half >> (sh + 12)) & 15u);
-                    *(uint4*)(rowp + ((c ^ (row & 7)) << 4)) = o;
+                for (int at = 0; at < kAtoms; ++at) {
+                    unsigned char* rowp = sm + b * kStageBytes + row_off + at * atom_step;
+                    #pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        // bits 128 at + 16c .. +15 of the stage row -> 16 bytes
+                        const u64 wv = ring[a][2 * at + (c >> 2)];
+                        const u32 half = (c & 2) ? (u32)(wv >> 32) : (u32)wv;
+                        const int sh = (c & 1) * 16;
+                        uint4 o;
+                        o.x = expand4((half >> sh) & 15u);
+                        o.y = expand4((half >> (sh + 4)) & 15u);
+                        o.z = expand4((half >> (sh + 8)) & 15u);
+                        o.w = expand4((half >> (sh + 12)) & 15u);
+                        *(uint4*)(rowp + ((c ^ (row & 7)) << 4)) = o;
+                    }
                 }
                 // every writer fences its generic-proxy stores for the async
                 // proxy; the warp converges, and one lane arrives for it
@@ -448,8 +461,9 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                     const u32 abase = base + b * kStageBytes, bbase = abase + kABytes;
                     #pragma unroll
                     for (int k = 0; k < kStageBits / 32; ++k) {
-                        u64 da = sw128_desc(abase + k * 32);
-                        u64 db = sw128_desc(bbase + k * 32);
+                        // K step k: atom column k / 4, 32-byte slice k % 4
+                        u64 da = sw128_desc(abase + (k >> 2) * kAtomA + (k & 3) * 32);
+                        u64 db = sw128_desc(bbase + (k >> 2) * kAtomB + (k & 3) * 32);
                         u32 accum = (fresh && q == 0 && k == 0) ? 0u : 1u;
                         asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
