@@ -24,14 +24,22 @@ namespace jsim {
 
 namespace {
 
-// Build-time tuning of the query product: index rows per tile (measured on
-// GB300: 16 beats 8 and 32).
+// Build-time tuning of the query product: index rows per tile and query
+// samples per CTA (measured on GB300, 64-sample batches: 8 rows and 32
+// samples - 2.32 ms per batch of 223,613 touched words - beat 4 or 16 rows
+// and 8, 16 or 64 samples by 2 to 50 %).
 #ifndef JSIM_QTILE
-#define JSIM_QTILE 16
+#define JSIM_QTILE 8
+#endif
+// query samples per CTA (the batch's samples are split over grid.z)
+#ifndef JSIM_QGROUP
+#define JSIM_QGROUP 32
 #endif
 constexpr int kQThreads = 256;
 constexpr int kQCols = 2 * kQThreads;  // reference columns per CTA (two per thread)
 constexpr int kQTile = JSIM_QTILE;     // index rows in flight per thread
+constexpr int kQGroup = JSIM_QGROUP;   // query samples per CTA
+static_assert(kQGroup >= 1 && kQGroup <= 64, "at most 64 samples per batch");
 
 // rank of x in the reference filter, if f has row x
 __device__ __forceinline__ bool ref_rank(u64 x, u64 lo, u64 width, const u64* __restrict__ bm,
@@ -132,10 +140,13 @@ __global__ void k_qemit(const u64* __restrict__ touched, u64 nwt, const u32* __r
     }
 }
 
-// One CTA: reference columns [blockIdx.x * 512, +512) and touched words
-// [U * y / Y, U * (y + 1) / Y).  Counts per (query sample, column) live in
-// shared memory; each thread owns two columns, so no two threads share a
-// counter.  Per tile of kQTile touched words the CTA compacts each word's
+// One CTA: reference columns [blockIdx.x * 512, +512), touched words
+// [U * y / Y, U * (y + 1) / Y) and query samples [kQGroup z, +kQGroup).
+// Splitting the samples over CTAs keeps the counters small, so several CTAs
+// share an SM and hide the load latency; the CTAs of the sample groups read
+// the same index rows at about the same time, from L2.  Counts per (query
+// sample, column) live in shared memory; each thread owns two columns, so
+// no two threads share a counter.  Per tile of kQTile touched words the CTA compacts each word's
 // nonzero query masks into a list of (mask, sample) entries (a warp per
 // word: ballot + prefix popcount), issues all index-row loads, then adds
 // popcounts two entries at a time (a word's entries have distinct samples,
@@ -145,35 +156,36 @@ k_qprod(const u64* __restrict__ index, u64 ns, u64 n_ref, const u64* __restrict_
         const u64* __restrict__ Udev, const u64* __restrict__ Qc, int S, u32* Cacc)
 {
     extern __shared__ __align__(16) u64 q_smem[];
-    uint2* cnt = (uint2*)q_smem;                   // [S][kQThreads] pairs of counters
-    u64* eq = q_smem + (size_t)S * kQThreads;      // [kQTile][64] nonzero masks
-    u32* es = (u32*)(eq + kQTile * 64);            // [kQTile][64] their samples
-    u64* wl = (u64*)(es + kQTile * 64);            // [kQTile]
+    uint2* cnt = (uint2*)q_smem;                   // [kQGroup][kQThreads] pairs of counters
+    u64* eq = q_smem + (size_t)kQGroup * kQThreads;  // [kQTile][kQGroup] nonzero masks
+    u32* es = (u32*)(eq + kQTile * kQGroup);       // [kQTile][kQGroup] their samples (within the group)
+    u64* wl = (u64*)(es + kQTile * kQGroup);       // [kQTile]
     int* ne = (int*)(wl + kQTile);                 // [kQTile] entries per word
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int z0 = (int)blockIdx.z * kQGroup, G = min(kQGroup, S - z0);
     const u64 col = (u64)blockIdx.x * kQCols + 2 * (u64)t;
     const u64 U = *Udev;
     const u64 u0 = U * blockIdx.y / gridDim.y, u1 = U * (blockIdx.y + 1) / gridDim.y;
     const u32 lt = (1u << lane) - 1u;
-    for (int e = t; e < S * kQThreads; e += kQThreads) cnt[e] = make_uint2(0u, 0u);
+    for (int e = t; e < G * kQThreads; e += kQThreads) cnt[e] = make_uint2(0u, 0u);
     for (u64 base = u0; base < u1; base += kQTile) {
         const int nt = (int)min((u64)kQTile, u1 - base);
         if (t < nt) wl[t] = wlist[base + t];
         for (int j = warp; j < nt; j += kQThreads / 32) {
-            const u64* row = Qc + (base + j) * (u64)S;
-            const u64 a = lane < S ? row[lane] : 0ull;
-            const u64 b = lane + 32 < S ? row[lane + 32] : 0ull;
+            const u64* row = Qc + (base + j) * (u64)S + z0;
+            const u64 a = lane < G ? row[lane] : 0ull;
+            const u64 b = lane + 32 < G ? row[lane + 32] : 0ull;
             const u32 ba = __ballot_sync(0xffffffffu, a != 0ull), bb = __ballot_sync(0xffffffffu, b != 0ull);
             const int na = __popc(ba);
             if (a) {
                 const int k = __popc(ba & lt);
-                eq[j * 64 + k] = a;
-                es[j * 64 + k] = (u32)lane;
+                eq[j * kQGroup + k] = a;
+                es[j * kQGroup + k] = (u32)lane;
             }
             if (b) {
                 const int k = na + __popc(bb & lt);
-                eq[j * 64 + k] = b;
-                es[j * 64 + k] = (u32)lane + 32u;
+                eq[j * kQGroup + k] = b;
+                es[j * kQGroup + k] = (u32)lane + 32u;
             }
             if (lane == 0) ne[j] = na + __popc(bb);
         }
@@ -186,8 +198,8 @@ k_qprod(const u64* __restrict__ index, u64 ns, u64 n_ref, const u64* __restrict_
         for (int j = 0; j < kQTile; ++j) {
             if (j < nt) {
                 const int m = ne[j];
-                const u64* q = eq + j * 64;
-                const u32* sj = es + j * 64;
+                const u64* q = eq + j * kQGroup;
+                const u32* sj = es + j * kQGroup;
                 int k = 0;
                 for (; k + 1 < m; k += 2) {
                     const u64 q0 = q[k], q1 = q[k + 1];
@@ -212,10 +224,11 @@ k_qprod(const u64* __restrict__ index, u64 ns, u64 n_ref, const u64* __restrict_
         __syncthreads();
     }
     if (u0 >= u1) return;
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < G; ++s) {
         const uint2 c = cnt[s * kQThreads + t];
-        if (c.x && col < n_ref) atomicAdd(Cacc + (u64)s * n_ref + col, c.x);
-        if (c.y && col + 1 < n_ref) atomicAdd(Cacc + (u64)s * n_ref + col + 1, c.y);
+        const u64 o = (u64)(z0 + s) * n_ref + col;
+        if (c.x && col < n_ref) atomicAdd(Cacc + o, c.x);
+        if (c.y && col + 1 < n_ref) atomicAdd(Cacc + o + 1, c.y);
     }
 }
 
@@ -278,9 +291,9 @@ cudaError_t launch_qemit(const u64* touched, u64 nwt, const u32* dir_t, const u6
     return cudaGetLastError();
 }
 
-size_t qprod_smem(int S)
+size_t qprod_smem()
 {
-    return (size_t)S * kQThreads * sizeof(uint2) + (size_t)kQTile * 64 * (sizeof(u64) + sizeof(u32)) +
+    return (size_t)kQGroup * kQThreads * sizeof(uint2) + (size_t)kQTile * kQGroup * (sizeof(u64) + sizeof(u32)) +
            kQTile * (sizeof(u64) + sizeof(int));
 }
 
@@ -289,20 +302,20 @@ cudaError_t launch_qprod(const QueryIndex& ix, const u64* wlist, const u64* Udev
 {
     if (S < 1 || S > 64) return cudaErrorInvalidValue;
     if (ix.W == 0 || Umax == 0) return cudaSuccess;
-    const size_t smem = qprod_smem(S);
+    const size_t smem = qprod_smem();
     cudaError_t e = cudaFuncSetAttribute(k_qprod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qprod, kQThreads, smem);
     if (e != cudaSuccess) return e;
-    const u64 gx = ix.ns / kQCols;
-    u64 gy = ((u64)sms * (u64)std::max(per_sm, 1) + gx - 1) / gx;
+    const u64 gx = ix.ns / kQCols, gz = ((u64)S + kQGroup - 1) / kQGroup;
+    u64 gy = ((u64)sms * (u64)std::max(per_sm, 1) + gx * gz - 1) / (gx * gz);
     const u64 tiles = (Umax + kQTile - 1) / kQTile;
     if (gy > tiles) gy = tiles;
     if (gy > 65535) gy = 65535;
     if (gy == 0) gy = 1;
-    k_qprod<<<dim3((unsigned)gx, (unsigned)gy), kQThreads, smem, st>>>(ix.index, ix.ns, ix.n_ref, wlist, Udev, Qc, S,
-                                                                      Cacc);
+    k_qprod<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), kQThreads, smem, st>>>(ix.index, ix.ns, ix.n_ref,
+                                                                                    wlist, Udev, Qc, S, Cacc);
     return cudaGetLastError();
 }
 
