@@ -463,7 +463,7 @@ def run_serve(args):
         for h in handles:
             h.free()
         d = {k: st1[k] - st0[k] for k in ("batches", "samples_done", "values_done", "ms_device", "ms_product",
-                                          "index_bytes_read", "touched_words")}
+                                          "index_bytes_read", "rows_read")}
         return elapsed, lat, d
 
     reqs = [request() for _ in range(n_req)]
@@ -499,22 +499,23 @@ def run_serve(args):
     pk, src = measured_peaks()
     achieved = d["index_bytes_read"] / (d["ms_product"] * 1e-3) / 1e9 if d["ms_product"] else 0.0
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic_from_profiles("qprod", "serve2048"),
-            "kernel": "k_qprod", "peak_source": "%s HBM copy bandwidth" % src}
+            "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic_from_profiles("qrows", "serve2048"),
+            "kernel": "k_qrows", "peak_source": "%s HBM copy bandwidth" % src,
+            "unit_bytes": "index rows read (ceil(n_ref/64) x 8 B per query value the filter holds)"}
     line = {"metric": METRIC, "value": capacity, "unit": "requests/s", "n_gpus": 1, "steps": n_req,
             "warmup": args.warmup, "ms_per_step": elapsed / n_req * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
             "config": {"workload": "serve2048: reference n=2048, values in [0,2^32), log-normal sizes median "
                                    "%.0e (x/10-10x), 64 clades; requests of U{1..64} query samples of the same "
                                    "recipe" % median,
-                       "index_words": ix.words, "index_bytes": ix.words * ((n_ref + 511) // 512 * 512) * 8,
+                       "index_rows": ix.rows, "index_bytes": ix.rows * ((n_ref + 63) // 64) * 8,
                        "build_ms": round(build_ms, 1), "requests": n_req, "query_samples": samples,
                        "samples_per_s": samples / elapsed, "batches": d["batches"],
                        "samples_per_batch": d["samples_done"] / max(1, d["batches"]),
                        "device_ms_per_batch": d["ms_device"] / max(1, d["batches"]),
                        "qprod_ms_per_batch": d["ms_product"] / max(1, d["batches"]),
-                       "touched_words_per_batch": d["touched_words"] / max(1, d["batches"]),
-                       "l2": "index (%.1f GB) larger than L2; no flush" % (ix.words * n_ref * 8 / 1e9)},
+                       "rows_read_per_batch": d["rows_read"] / max(1, d["batches"]),
+                       "l2": "index (%.1f GB) larger than L2; no flush" % (ix.rows * n_ref / 8 / 1e9)},
             "latency": levels, "clocks": clk.summary(), "gpu_launches": int(10 * d["batches"]), "roofline": roof,
             "e2e": {"value": capacity, "unit": "requests/s",
                     "h2d_bytes_per_step": int(d["values_done"] * 8 / n_req),

@@ -269,12 +269,13 @@ JSIM_API int jsim_product_noalloc(jsim_ctx* ctx, const uint64_t* words, uint64_t
  *
  * The reference collection is packed once, as one batch of the method over
  * its whole value range (Sec. III-B: filter f, Eq. 5; rank directory, Eq. 6;
- * packed words), and stays in device memory.  A query sample Q is compared
+ * the kept rows of Abar, each an n_ref-bit vector of the reference samples
+ * holding it), and stays in device memory.  A query sample Q is compared
  * with every reference sample S_j: C[q][j] = |Q cap S_j|, J as above, and
  * |Q| counts every distinct value of Q, also those the reference lacks.
  * Query values are ranked against the resident filter (a value absent from
- * f meets no reference sample), so a query reads only the index words its
- * values fall in (Eq. 7 restricted to them).
+ * f meets no reference sample), and C[q] is the sum of the rows of Q's
+ * values (Eq. 7 with the query's 0/1 column): one row read per value.
  */
 typedef struct jsim_index jsim_index;
 typedef struct jsim_request jsim_request;
@@ -289,11 +290,11 @@ typedef struct {
     uint64_t requests_submitted, requests_done, samples_done, values_done;
     uint64_t batches;           /* device batches retired */
     uint64_t queued;            /* requests waiting for a slot now */
-    uint64_t touched_words;     /* index rows read, summed over batches */
+    uint64_t rows_read;         /* index rows read (query values the reference filter holds), summed */
     double ms_device;           /* device time of the batches (copy in to copy out), summed */
-    double ms_product;          /* device time of the query x index product kernels, summed */
-    double index_bytes_read;    /* touched rows x row bytes, summed */
-    double bitops_dense;        /* 64 x touched words x batch samples x n_ref, summed */
+    double ms_product;          /* device time of the query x index kernels, summed */
+    double index_bytes_read;    /* rows read x row bytes (ceil(n_ref / 64) x 8), summed */
+    double bitops_dense;        /* rows read x n_ref (one AND+popcount bit per row and reference), summed */
 } jsim_serve_stats;
 
 JSIM_API void jsim_serve_default_options(jsim_serve_options* opt);
@@ -304,12 +305,12 @@ JSIM_API void jsim_serve_default_options(jsim_serve_options* opt);
  * use here (index, filter, per-slot buffers, pinned staging) through the
  * context's allocator; serving allocates nothing.  The context must outlive
  * the index and must not be used by another thread during this call.
- * Device memory: W x round_up(n, 512) x 8 bytes of index (W = ceil(R / 64),
- * R the reference's distinct values), width/8 + width/16 bytes of filter and
- * directory, and per slot about max_batch_values x 8 + min(W,
- * max_batch_values) x max_batch_samples x 8 bytes.
+ * Device memory: R x ceil(n / 64) x 8 bytes of index (R the reference's
+ * distinct values), width/8 + width/16 bytes of filter and directory, and
+ * per slot about max_batch_values x 8 + max_batch_samples x n x 16 bytes.
  * Errors: JSIM_ERR_ARG, JSIM_ERR_UNSORTED, JSIM_ERR_ID_RANGE, JSIM_ERR_OOM,
- * JSIM_ERR_CUDA, JSIM_ERR_UNSUPPORTED (reference value span >= 2^36).
+ * JSIM_ERR_CUDA, JSIM_ERR_UNSUPPORTED (reference value span >= 2^36, or
+ * more than 8192 reference samples).
  */
 JSIM_API int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_serve_options* opt,
                               jsim_index** out);
@@ -319,8 +320,8 @@ JSIM_API int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_se
  * a request that was cancelled here stays valid until jsim_request_free. */
 JSIM_API void jsim_index_destroy(jsim_index* ix);
 
-/* n_ref, index words W, and the reference sizes |S_j| (host, n_ref entries);
- * any pointer may be NULL. */
+/* n_ref, the index's rows R (the reference's distinct values), and the
+ * reference sizes |S_j| (host, n_ref entries); any pointer may be NULL. */
 JSIM_API int jsim_index_info(const jsim_index* ix, uint64_t* n_ref, uint64_t* words, uint64_t* ref_sizes);
 
 /* Server counters since the index was built. */

@@ -102,26 +102,24 @@ bool product_tc_supported(int device);
 
 // ---- query.cu (serving) ---------------------------------------------------------
 // A resident reference index: the reference as one batch over [lo, lo+width)
-// with filter bitmap, rank directory and word-major packed words (row w holds
-// word w of all n_ref samples; row stride ns, a multiple of 512).
+// with filter bitmap, rank directory and the R kept rows of Abar_ref,
+// rank-major (row r: ns64 = ceil(n_ref / 64) words, bit j = reference sample
+// j holds row r).
 struct QueryIndex {
     const u64* index;
     const u64* bm;
     const u32* dir;
     const u64* boff;
-    u64 lo, width, W, n_ref, ns;
+    u64 lo, width, R, n_ref, ns64;
 };
-cudaError_t launch_qtouch(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix, u32* touched,
-                          int sms, cudaStream_t st);
-// zeroes Qc[0 .. min(*Udev, Umax) * S) and fills it
-cudaError_t launch_qpack(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix,
-                         const u64* touched, const u32* dir_t, const u64* boff_t, const u64* Udev, u64 Umax,
-                         u64* Qc, int sms, cudaStream_t st);
-cudaError_t launch_qemit(const u64* touched, u64 nwt, const u32* dir_t, const u64* boff_t, u64* wlist, int sms,
-                         cudaStream_t st);
-// Cacc (S x n_ref u32, zeroed by the caller) += query x index counts; S <= 64
-cudaError_t launch_qprod(const QueryIndex& ix, const u64* wlist, const u64* Udev, u64 Umax, const u64* Qc, int S,
-                         u32* Cacc, int sms, cudaStream_t st);
+// build: Xt (R x ns64, zeroed by the caller) gets bit i of row rank(x) for
+// every value x of reference sample i
+cudaError_t launch_pack_rows(const u64* ids, u64 n, Plan plan, u64 max_chunks, const QueryIndex& ix, u64* Xt,
+                             int sms, cudaStream_t st);
+// Cacc (S x n_ref u32, zeroed by the caller) += query x reference counts;
+// *rows_read += query values found in the filter; ns64 <= 128 (n_ref <= 8192)
+cudaError_t launch_qrows(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix, u32* Cacc,
+                         u64* rows_read, int sms, cudaStream_t st);
 cudaError_t launch_qepi(const u32* Cacc, u64 S, u64 n_ref, const u64* sq, const u64* sr, int count_bits, void* Cout,
                         double* J, int sms, cudaStream_t st);
 

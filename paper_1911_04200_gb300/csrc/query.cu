@@ -3,20 +3,23 @@
 //
 // The index holds the reference as one batch of the method (Sec. III-B):
 // its filter f over [lo, lo + width) (Eq. 5), the rank directory of f
-// (Eq. 6) and the packed words, word-major (row w = word w of every
-// reference sample, so one query word reads one contiguous row).  A query
-// value x can meet a reference sample only if f has row x; its rank r there
-// names index word r/64, bit r%64.  Values absent from f count in |Q| only.
+// (Eq. 6), and the rows of Abar_ref (Eq. 6): row r, the r-th kept row, is an
+// n_ref-bit vector of the reference samples that hold it, stored as
+// ns64 = ceil(n_ref / 64) words (rank-major).  A query value x meets a
+// reference sample only if f has row x, and then exactly the samples of row
+// rank(x); values absent from f count in |Q| only.  So for a query sample s
+//   C[s][j] = sum over x in Q_s with f(x) of Abar_ref[rank(x)][j]
+// (Eq. 7 with the query's 0/1 column), read as one row of ns64 words per
+// query value.
 //
-// For a batch of S query samples:
-//   k_qtouch  marks the index words any query value falls in (bitmap over W);
-//   rank scan of that bitmap numbers the U touched words;
-//   k_qpack   builds Qc[u][s], the query's mask on touched word u;
-//   k_qemit   lists the index word of every touched word;
-//   k_qprod   C[s][j] = sum_u popcount(Qc[u][s] & index[w_u][j]) (Eq. 7
-//             restricted to the words a query touches), reading each touched
-//             index row once for the whole batch;
-//   k_qepi    J = C / (|Q_s| + |S_j| - C) in binary64 (Sec. II-A).
+//   k_pack_rows  (build) sets bit j of row rank(x) for every value x of
+//                reference sample j;
+//   k_qrows      a warp per chunk of one query sample's values: lanes rank
+//                32 values at a time, then every lane adds its words of the
+//                ranked rows into bit-sliced counters held in registers
+//                (plane k = bit k of 64 column counts); at the end of the
+//                chunk the counts go into C with atomic adds;
+//   k_qepi       J = C / (|Q_s| + |S_j| - C) in binary64 (Sec. II-A).
 #include <algorithm>
 #include "ingest_dev.cuh"
 
@@ -24,22 +27,11 @@ namespace jsim {
 
 namespace {
 
-// Build-time tuning of the query product: index rows per tile and query
-// samples per CTA (measured on GB300, 64-sample batches: 8 rows and 32
-// samples - 2.32 ms per batch of 223,613 touched words - beat 4 or 16 rows
-// and 8, 16 or 64 samples by 2 to 50 %).
-#ifndef JSIM_QTILE
-#define JSIM_QTILE 8
-#endif
-// query samples per CTA (the batch's samples are split over grid.z)
-#ifndef JSIM_QGROUP
-#define JSIM_QGROUP 32
-#endif
 constexpr int kQThreads = 256;
-constexpr int kQCols = 2 * kQThreads;  // reference columns per CTA (two per thread)
-constexpr int kQTile = JSIM_QTILE;     // index rows in flight per thread
-constexpr int kQGroup = JSIM_QGROUP;   // query samples per CTA
-static_assert(kQGroup >= 1 && kQGroup <= 64, "at most 64 samples per batch");
+constexpr int kQWarps = kQThreads / 32;
+constexpr int kPlanes = 13;   // counts of one chunk (<= kChunk = 4096 values) fit 13 bits
+static_assert((1ull << (kPlanes - 1)) >= kChunk, "bit planes hold a chunk's counts");
+constexpr int kQBatch = 8;    // rows in flight per lane
 
 // rank of x in the reference filter, if f has row x
 __device__ __forceinline__ bool ref_rank(u64 x, u64 lo, u64 width, const u64* __restrict__ bm,
@@ -56,179 +48,114 @@ __device__ __forceinline__ bool ref_rank(u64 x, u64 lo, u64 width, const u64* __
 }
 
 __global__ void __launch_bounds__(kIngestThreads)
-k_qtouch(const u64* __restrict__ ids, u64 S, Plan plan, u64 lo, u64 width, const u64* __restrict__ bm,
-         const u32* __restrict__ dir, const u64* __restrict__ boff, u32* touched)
-{
-    __shared__ u64 s_p0, s_p1;
-    const u64 nch = plan.totals[1];
-    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
-        if (threadIdx.x == 0) {
-            const u64 i = chunk_sample(plan.cofs, S, c);
-            const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
-            s_p0 = p0;
-            s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
-        }
-        __syncthreads();
-        const u64 p0 = s_p0, p1 = s_p1;
-        for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
-            const u64 pos = base + (threadIdx.x & 31);
-            u64 q = ~0ull, r;
-            u32 bit = 0;
-            if (pos < p1 && ref_rank(ids[pos], lo, width, bm, dir, boff, r)) {
-                const u64 w = r >> 6;
-                q = w >> 5;
-                bit = 1u << (w & 31);
-            }
-            const bool lead = segmented_or<u32>(q, bit);
-            if (lead && bit) atomicOr(touched + q, bit);
-        }
-        __syncthreads();
-    }
-}
-
-__global__ void k_zero_dyn(u64* X, const u64* __restrict__ count, u64 per, u64 cap)
-{
-    const u64 total = min(*count, cap) * per;
-    for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (u64)gridDim.x * blockDim.x)
-        X[t] = 0ull;
-}
-
-__global__ void __launch_bounds__(kIngestThreads)
-k_qpack(const u64* __restrict__ ids, u64 S, Plan plan, u64 lo, u64 width, const u64* __restrict__ bm,
-        const u32* __restrict__ dir, const u64* __restrict__ boff, const u64* __restrict__ touched,
-        const u32* __restrict__ dir_t, const u64* __restrict__ boff_t, u64* Qc)
+k_pack_rows(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, const u64* __restrict__ bm,
+            const u32* __restrict__ dir, const u64* __restrict__ boff, u64* Xt, u64 ns64)
 {
     __shared__ u64 s_i, s_p0, s_p1;
     const u64 nch = plan.totals[1];
     for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
         if (threadIdx.x == 0) {
-            const u64 i = chunk_sample(plan.cofs, S, c);
+            const u64 i = chunk_sample(plan.cofs, n, c);
             const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
             s_i = i;
             s_p0 = p0;
             s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
         }
         __syncthreads();
-        const u64 s = s_i, p0 = s_p0, p1 = s_p1;
-        for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
-            const u64 pos = base + (threadIdx.x & 31);
-            u64 key = ~0ull, bit = 0, r;
-            if (pos < p1 && ref_rank(ids[pos], lo, width, bm, dir, boff, r)) {
-                const u64 w = r >> 6, tw = w >> 6;
-                const u64 u = boff_t[tw / kScanBlockWords] + (u64)dir_t[tw] +
-                              (u64)__popcll(touched[tw] & ((1ull << (w & 63)) - 1ull));
-                key = u * S + s;
-                bit = 1ull << (r & 63);
-            }
-            const bool lead = segmented_or<u64>(key, bit);
-            if (lead && bit) atomicOr(Qc + key, bit);
+        const u64 i = s_i, p0 = s_p0, p1 = s_p1;
+        for (u64 pos = p0 + threadIdx.x; pos < p1; pos += kIngestThreads) {
+            u64 r;
+            if (ref_rank(ids[pos], lo, width, bm, dir, boff, r))
+                atomicOr(Xt + r * ns64 + (i >> 6), 1ull << (i & 63));
         }
         __syncthreads();
     }
 }
 
-__global__ void k_qemit(const u64* __restrict__ touched, u64 nwt, const u32* __restrict__ dir_t,
-                        const u64* __restrict__ boff_t, u64* wlist)
+// add the bits of v into the bit-sliced counters p (carry ripple)
+__device__ __forceinline__ void bs_add(u64 (&p)[kPlanes], u64 v)
 {
-    for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < nwt; t += (u64)gridDim.x * blockDim.x) {
-        u64 x = touched[t];
-        u64 u = boff_t[t / kScanBlockWords] + (u64)dir_t[t];
-        while (x) {
-            wlist[u++] = t * 64 + (u64)(__ffsll((long long)x) - 1);
-            x &= x - 1;
-        }
+    #pragma unroll
+    for (int k = 0; k < kPlanes; ++k) {
+        if (!v) break;
+        const u64 t = p[k] & v;
+        p[k] ^= v;
+        v = t;
     }
 }
 
-// One CTA: reference columns [blockIdx.x * 512, +512), touched words
-// [U * y / Y, U * (y + 1) / Y) and query samples [kQGroup z, +kQGroup).
-// Splitting the samples over CTAs keeps the counters small, so several CTAs
-// share an SM and hide the load latency; the CTAs of the sample groups read
-// the same index rows at about the same time, from L2.  Counts per (query
-// sample, column) live in shared memory; each thread owns two columns, so
-// no two threads share a counter.  Per tile of kQTile touched words the CTA compacts each word's
-// nonzero query masks into a list of (mask, sample) entries (a warp per
-// word: ballot + prefix popcount), issues all index-row loads, then adds
-// popcounts two entries at a time (a word's entries have distinct samples,
-// so the two counter updates are independent).
+template <int KW>
 __global__ void __launch_bounds__(kQThreads)
-k_qprod(const u64* __restrict__ index, u64 ns, u64 n_ref, const u64* __restrict__ wlist,
-        const u64* __restrict__ Udev, const u64* __restrict__ Qc, int S, u32* Cacc)
+k_qrows(const u64* __restrict__ ids, u64 S, Plan plan, u64 lo, u64 width, const u64* __restrict__ bm,
+        const u32* __restrict__ dir, const u64* __restrict__ boff, const u64* __restrict__ Xt, u64 ns64, u64 n_ref,
+        u32* Cacc, u64* rows_read)
 {
-    extern __shared__ __align__(16) u64 q_smem[];
-    uint2* cnt = (uint2*)q_smem;                   // [kQGroup][kQThreads] pairs of counters
-    u64* eq = q_smem + (size_t)kQGroup * kQThreads;  // [kQTile][kQGroup] nonzero masks
-    u32* es = (u32*)(eq + kQTile * kQGroup);       // [kQTile][kQGroup] their samples (within the group)
-    u64* wl = (u64*)(es + kQTile * kQGroup);       // [kQTile]
-    int* ne = (int*)(wl + kQTile);                 // [kQTile] entries per word
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int z0 = (int)blockIdx.z * kQGroup, G = min(kQGroup, S - z0);
-    const u64 col = (u64)blockIdx.x * kQCols + 2 * (u64)t;
-    const u64 U = *Udev;
-    const u64 u0 = U * blockIdx.y / gridDim.y, u1 = U * (blockIdx.y + 1) / gridDim.y;
-    const u32 lt = (1u << lane) - 1u;
-    for (int e = t; e < G * kQThreads; e += kQThreads) cnt[e] = make_uint2(0u, 0u);
-    for (u64 base = u0; base < u1; base += kQTile) {
-        const int nt = (int)min((u64)kQTile, u1 - base);
-        if (t < nt) wl[t] = wlist[base + t];
-        for (int j = warp; j < nt; j += kQThreads / 32) {
-            const u64* row = Qc + (base + j) * (u64)S + z0;
-            const u64 a = lane < G ? row[lane] : 0ull;
-            const u64 b = lane + 32 < G ? row[lane + 32] : 0ull;
-            const u32 ba = __ballot_sync(0xffffffffu, a != 0ull), bb = __ballot_sync(0xffffffffu, b != 0ull);
-            const int na = __popc(ba);
-            if (a) {
-                const int k = __popc(ba & lt);
-                eq[j * kQGroup + k] = a;
-                es[j * kQGroup + k] = (u32)lane;
-            }
-            if (b) {
-                const int k = na + __popc(bb & lt);
-                eq[j * kQGroup + k] = b;
-                es[j * kQGroup + k] = (u32)lane + 32u;
-            }
-            if (lane == 0) ne[j] = na + __popc(bb);
-        }
-        __syncthreads();
-        ulonglong2 r[kQTile];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const u64 nch = plan.totals[1];
+    for (u64 c = (u64)blockIdx.x * kQWarps + warp; c < nch; c += (u64)gridDim.x * kQWarps) {
+        const u64 s = chunk_sample(plan.cofs, S, c);
+        const u64 sb = plan.beg[s];
+        const u64 p0 = sb + (c - plan.cofs[s]) * kChunk;
+        const u64 p1 = min(p0 + kChunk, plan.beg[s] + plan.len[s]);
+        u64 pl[KW][kPlanes];
         #pragma unroll
-        for (int j = 0; j < kQTile; ++j)
-            if (j < nt) r[j] = __ldg((const ulonglong2*)(index + wl[j] * ns + col));
-        #pragma unroll
-        for (int j = 0; j < kQTile; ++j) {
-            if (j < nt) {
-                const int m = ne[j];
-                const u64* q = eq + j * kQGroup;
-                const u32* sj = es + j * kQGroup;
-                int k = 0;
-                for (; k + 1 < m; k += 2) {
-                    const u64 q0 = q[k], q1 = q[k + 1];
-                    const u32 s0 = sj[k] * kQThreads + t, s1 = sj[k + 1] * kQThreads + t;
-                    uint2 c0 = cnt[s0], c1 = cnt[s1];
-                    c0.x += (u32)(__popcll(q0 & r[j].x));
-                    c0.y += (u32)(__popcll(q0 & r[j].y));
-                    c1.x += (u32)(__popcll(q1 & r[j].x));
-                    c1.y += (u32)(__popcll(q1 & r[j].y));
-                    cnt[s0] = c0;
-                    cnt[s1] = c1;
+        for (int k = 0; k < KW; ++k)
+            #pragma unroll
+            for (int q = 0; q < kPlanes; ++q) pl[k][q] = 0ull;
+        u32 found = 0;
+        for (u64 base = p0; base < p1; base += 32) {
+            const u64 pos = base + lane;
+            u64 r = 0;
+            bool ok = false;
+            if (pos < p1) {
+                const u64 x = ids[pos];
+                // a repeated value of the sample is one element of the set
+                ok = !(pos > sb && ids[pos - 1] == x) && ref_rank(x, lo, width, bm, dir, boff, r);
+            }
+            unsigned vm = __ballot_sync(0xffffffffu, ok);
+            found += (u32)__popc(vm);
+            while (vm) {
+                u64 rr[kQBatch];
+                int cnt = 0;
+                #pragma unroll
+                for (int g = 0; g < kQBatch; ++g) {
+                    const int src = vm ? __ffs((int)vm) - 1 : 0;
+                    rr[g] = __shfl_sync(0xffffffffu, r, src);
+                    if (vm) { vm &= vm - 1; ++cnt; }
                 }
-                if (k < m) {
-                    const u32 s0 = sj[k] * kQThreads + t;
-                    uint2 c0 = cnt[s0];
-                    c0.x += (u32)(__popcll(q[k] & r[j].x));
-                    c0.y += (u32)(__popcll(q[k] & r[j].y));
-                    cnt[s0] = c0;
-                }
+                u64 v[kQBatch][KW];
+                #pragma unroll
+                for (int g = 0; g < kQBatch; ++g)
+                    #pragma unroll
+                    for (int k = 0; k < KW; ++k) {
+                        const u64 w = (u64)lane + 32ull * k;
+                        v[g][k] = (g < cnt && w < ns64) ? __ldg(Xt + rr[g] * ns64 + w) : 0ull;
+                    }
+                #pragma unroll
+                for (int g = 0; g < kQBatch; ++g)
+                    #pragma unroll
+                    for (int k = 0; k < KW; ++k) bs_add(pl[k], v[g][k]);
             }
         }
-        __syncthreads();
-    }
-    if (u0 >= u1) return;
-    for (int s = 0; s < G; ++s) {
-        const uint2 c = cnt[s * kQThreads + t];
-        const u64 o = (u64)(z0 + s) * n_ref + col;
-        if (c.x && col < n_ref) atomicAdd(Cacc + o, c.x);
-        if (c.y && col + 1 < n_ref) atomicAdd(Cacc + o + 1, c.y);
+        // counts of this chunk into C
+        #pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            const u64 w = (u64)lane + 32ull * k;
+            if (w >= ns64) continue;
+            u64 any = 0ull;
+            #pragma unroll
+            for (int q = 0; q < kPlanes; ++q) any |= pl[k][q];
+            while (any) {
+                const int b = __ffsll((long long)any) - 1;
+                any &= any - 1;
+                u32 cntb = 0;
+                #pragma unroll
+                for (int q = 0; q < kPlanes; ++q) cntb |= (u32)((pl[k][q] >> b) & 1ull) << q;
+                const u64 col = w * 64 + (u64)b;
+                if (col < n_ref) atomicAdd(Cacc + s * n_ref + col, cntb);
+            }
+        }
+        if (lane == 0 && found) atomicAdd(rows_read, (u64)found);
     }
 }
 
@@ -263,59 +190,30 @@ inline unsigned grid_flat(u64 total, int sms, int threads)
 
 }  // namespace
 
-cudaError_t launch_qtouch(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix, u32* touched,
-                          int sms, cudaStream_t st)
+cudaError_t launch_pack_rows(const u64* ids, u64 n, Plan plan, u64 max_chunks, const QueryIndex& ix, u64* Xt,
+                             int sms, cudaStream_t st)
 {
-    k_qtouch<<<grid_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, S, plan, ix.lo, ix.width, ix.bm, ix.dir,
-                                                                      ix.boff, touched);
+    k_pack_rows<<<grid_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, ix.lo, ix.width, ix.bm, ix.dir,
+                                                                         ix.boff, Xt, ix.ns64);
     return cudaGetLastError();
 }
 
-cudaError_t launch_qpack(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix,
-                         const u64* touched, const u32* dir_t, const u64* boff_t, const u64* Udev, u64 Umax,
-                         u64* Qc, int sms, cudaStream_t st)
+cudaError_t launch_qrows(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix, u32* Cacc,
+                         u64* rows_read, int sms, cudaStream_t st)
 {
-    k_zero_dyn<<<grid_flat(Umax * S, sms, 256), 256, 0, st>>>(Qc, Udev, S, Umax);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_qpack<<<grid_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, S, plan, ix.lo, ix.width, ix.bm, ix.dir,
-                                                                     ix.boff, touched, dir_t, boff_t, Qc);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_qemit(const u64* touched, u64 nwt, const u32* dir_t, const u64* boff_t, u64* wlist, int sms,
-                         cudaStream_t st)
-{
-    if (nwt == 0) return cudaSuccess;
-    k_qemit<<<grid_flat(nwt, sms, 256), 256, 0, st>>>(touched, nwt, dir_t, boff_t, wlist);
-    return cudaGetLastError();
-}
-
-size_t qprod_smem()
-{
-    return (size_t)kQGroup * kQThreads * sizeof(uint2) + (size_t)kQTile * kQGroup * (sizeof(u64) + sizeof(u32)) +
-           kQTile * (sizeof(u64) + sizeof(int));
-}
-
-cudaError_t launch_qprod(const QueryIndex& ix, const u64* wlist, const u64* Udev, u64 Umax, const u64* Qc, int S,
-                         u32* Cacc, int sms, cudaStream_t st)
-{
-    if (S < 1 || S > 64) return cudaErrorInvalidValue;
-    if (ix.W == 0 || Umax == 0) return cudaSuccess;
-    const size_t smem = qprod_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_qprod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qprod, kQThreads, smem);
-    if (e != cudaSuccess) return e;
-    const u64 gx = ix.ns / kQCols, gz = ((u64)S + kQGroup - 1) / kQGroup;
-    u64 gy = ((u64)sms * (u64)std::max(per_sm, 1) + gx * gz - 1) / (gx * gz);
-    const u64 tiles = (Umax + kQTile - 1) / kQTile;
-    if (gy > tiles) gy = tiles;
-    if (gy > 65535) gy = 65535;
-    if (gy == 0) gy = 1;
-    k_qprod<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), kQThreads, smem, st>>>(ix.index, ix.ns, ix.n_ref,
-                                                                                    wlist, Udev, Qc, S, Cacc);
+    if (ix.R == 0) return cudaSuccess;
+    const u64 blocks = std::max<u64>(1, std::min<u64>((max_chunks + kQWarps - 1) / kQWarps, (u64)sms * 8));
+    if (ix.ns64 <= 32)
+        k_qrows<1><<<(unsigned)blocks, kQThreads, 0, st>>>(ids, S, plan, ix.lo, ix.width, ix.bm, ix.dir, ix.boff,
+                                                           ix.index, ix.ns64, ix.n_ref, Cacc, rows_read);
+    else if (ix.ns64 <= 64)
+        k_qrows<2><<<(unsigned)blocks, kQThreads, 0, st>>>(ids, S, plan, ix.lo, ix.width, ix.bm, ix.dir, ix.boff,
+                                                           ix.index, ix.ns64, ix.n_ref, Cacc, rows_read);
+    else if (ix.ns64 <= 128)
+        k_qrows<4><<<(unsigned)blocks, kQThreads, 0, st>>>(ids, S, plan, ix.lo, ix.width, ix.bm, ix.dir, ix.boff,
+                                                           ix.index, ix.ns64, ix.n_ref, Cacc, rows_read);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -3,10 +3,10 @@
 //
 // jsim_index_build packs the reference once, as one batch of the method
 // (Sec. III-B): filter over its whole value range (Eq. 5), rank directory
-// (Eq. 6), packed words laid out word-major.  Queries against it need no
-// pass over the reference: each query value is ranked against the resident
-// filter (values the reference lacks count in |Q| only) and only the index
-// rows its words touch are read.
+// (Eq. 6), and the kept rows of Abar_ref rank-major (row r: which reference
+// samples hold it).  Queries against it need no pass over the reference:
+// each query value is ranked against the resident filter (values the
+// reference lacks count in |Q| only) and reads one row.
 //
 // Requests are submitted from any thread.  The worker owns `slots` device
 // batches; whenever a slot is free it admits queued requests in arrival
@@ -58,7 +58,7 @@ struct Slot {
     u64* pin_in = nullptr;     // [offsets S+1][pad][values]
     unsigned char* pin_out = nullptr;
     size_t out_bytes = 0;
-    DevBuf din, plan_buf, sq, qerr, mm, touched, dir_t, bsum_t, boff_t, Ud, Qc, wlist, Cacc, Cout, Jd;
+    DevBuf din, plan_buf, sq, qerr, mm, Ud, Cacc, Cout, Jd;
     std::vector<jsim_request*> reqs;
     u64 S = 0;
     bool busy = false;
@@ -69,7 +69,7 @@ struct Slot {
 struct jsim_index {
     jsim_ctx* ctx = nullptr;
     jsim_serve_options opt{};
-    u64 n_ref = 0, ns = 0, lo = 0, width = 0, W = 0, nwt = 0, nbk_t = 0, Umax = 0;
+    u64 n_ref = 0, ns64 = 0, lo = 0, width = 0, R = 0;
     DevBuf X, bm, dir, boff, sizes_ref;
     std::vector<u64> h_sizes_ref;
     std::vector<std::unique_ptr<Slot>> slots;
@@ -94,9 +94,9 @@ QueryIndex view(const jsim_index* ix)
     q.boff = ix->boff.as<u64>();
     q.lo = ix->lo;
     q.width = ix->width;
-    q.W = ix->W;
+    q.R = ix->R;
     q.n_ref = ix->n_ref;
-    q.ns = ix->ns;
+    q.ns64 = ix->ns64;
     return q;
 }
 
@@ -178,21 +178,8 @@ int launch_batch(jsim_index* ix, Slot& sl)
                        sl.mm.as<u64>(), sl.mm.as<u64>() + 1, ix->sms, st, 1));
     CK(cudaMemsetAsync(sl.Cacc.p, 0, S * ix->n_ref * sizeof(u32), st));
     CK(cudaMemsetAsync(sl.Ud.p, 0, sizeof(u64), st));
-    if (ix->W) {
-        CK(cudaMemsetAsync(sl.touched.p, 0, ix->nwt * sizeof(u64), st));
-        CK(launch_qtouch(d_ids, S, plan, max_chunks, qi, sl.touched.as<u32>(), ix->sms, st));
-        CK(launch_scan(sl.touched.as<u64>(), ix->nwt, sl.dir_t.as<u32>(), sl.bsum_t.as<u64>(), sl.boff_t.as<u64>(),
-                       sl.Ud.as<u64>(), st));
-        CK(launch_qpack(d_ids, S, plan, max_chunks, qi, sl.touched.as<u64>(), sl.dir_t.as<u32>(),
-                        sl.boff_t.as<u64>(), sl.Ud.as<u64>(), ix->Umax, sl.Qc.as<u64>(), ix->sms, st));
-        CK(launch_qemit(sl.touched.as<u64>(), ix->nwt, sl.dir_t.as<u32>(), sl.boff_t.as<u64>(), sl.wlist.as<u64>(),
-                        ix->sms, st));
-        CK(cudaEventRecord(sl.evp0, st));
-        CK(launch_qprod(qi, sl.wlist.as<u64>(), sl.Ud.as<u64>(), ix->Umax, sl.Qc.as<u64>(), (int)S, sl.Cacc.as<u32>(),
-                        ix->sms, st));
-    } else {
-        CK(cudaEventRecord(sl.evp0, st));
-    }
+    CK(cudaEventRecord(sl.evp0, st));
+    CK(launch_qrows(d_ids, S, plan, max_chunks, qi, sl.Cacc.as<u32>(), sl.Ud.as<u64>(), ix->sms, st));
     CK(cudaEventRecord(sl.evp1, st));
     CK(launch_qepi(sl.Cacc.as<u32>(), S, ix->n_ref, sl.sq.as<u64>(), ix->sizes_ref.as<u64>(), ix->count_bits,
                    sl.Cout.p, sl.Jd.as<double>(), ix->sms, st));
@@ -242,7 +229,7 @@ void retire(jsim_index* ix, Slot& sl, cudaError_t done)
         }
         s0 += r->q;
     }
-    const u64 U = done == cudaSuccess ? *(const u64*)(po + ol.u) : 0;
+    const u64 rows = done == cudaSuccess ? *(const u64*)(po + ol.u) : 0;
     std::lock_guard<std::mutex> lk(ix->mu);
     const double t = now_ms();
     for (auto* r : sl.reqs) {
@@ -255,9 +242,9 @@ void retire(jsim_index* ix, Slot& sl, cudaError_t done)
     ix->stats.batches += 1;
     ix->stats.ms_device += ms;
     ix->stats.ms_product += msp;
-    ix->stats.touched_words += U;
-    ix->stats.index_bytes_read += (double)U * (double)ix->ns * 8.0;
-    ix->stats.bitops_dense += 64.0 * (double)U * (double)sl.S * (double)n_ref;
+    ix->stats.rows_read += rows;
+    ix->stats.index_bytes_read += (double)rows * (double)ix->ns64 * 8.0;
+    ix->stats.bitops_dense += (double)rows * (double)n_ref;
     sl.reqs.clear();
     sl.busy = false;
     ix->cv_done.notify_all();
@@ -331,8 +318,7 @@ void free_slots(jsim_index* ix)
     for (auto& sp : ix->slots) {
         Slot& sl = *sp;
         if (sl.st) cudaStreamSynchronize(sl.st);
-        for (DevBuf* b : {&sl.din, &sl.plan_buf, &sl.sq, &sl.qerr, &sl.mm, &sl.touched, &sl.dir_t, &sl.bsum_t,
-                          &sl.boff_t, &sl.Ud, &sl.Qc, &sl.wlist, &sl.Cacc, &sl.Cout, &sl.Jd})
+        for (DevBuf* b : {&sl.din, &sl.plan_buf, &sl.sq, &sl.qerr, &sl.mm, &sl.Ud, &sl.Cacc, &sl.Cout, &sl.Jd})
             b->release();
         if (sl.pin_in) cudaFreeHost(sl.pin_in);
         if (sl.pin_out) cudaFreeHost(sl.pin_out);
@@ -388,7 +374,8 @@ int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_serve_optio
     ix->count_bits = ctx->opt.count_bits;
     const u64 n = ref->n;
     ix->n_ref = n;
-    ix->ns = round_up(n, 512);
+    ix->ns64 = (n + 63) / 64;
+    if (ix->ns64 > 128) return JSIM_ERR_UNSUPPORTED;  // rows of more than 8192 reference samples
     cudaStream_t cs = ctx->stream;
     // the reference as one batch over its value range
     if (st.N) {
@@ -409,11 +396,10 @@ int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_serve_optio
         CK(launch_scan(ix->bm.as<u64>(), nw, ix->dir.as<u32>(), bsum.as<u64>(), ix->boff.as<u64>(), R.as<u64>(), cs));
         CK(cudaMemcpyAsync(ctx->h_scalars, R.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
         CK(cudaStreamSynchronize(cs));
-        ix->W = (ctx->h_scalars[0] + 63) / 64;
-        ALLOC(ix->X, std::max<u64>(ix->W, 1) * ix->ns * sizeof(u64));
-        CK(cudaMemsetAsync(ix->X.p, 0, ix->W * ix->ns * sizeof(u64), cs));
-        CK(launch_pack(st.d_ids, n, st.plan, st.max_chunks, ix->lo, ix->width, ix->bm.as<u64>(), ix->dir.as<u32>(),
-                       ix->boff.as<u64>(), ix->X.as<u64>(), 1, nullptr, ctx->sms, cs, nullptr, ix->ns));
+        ix->R = ctx->h_scalars[0];
+        ALLOC(ix->X, std::max<u64>(ix->R, 1) * ix->ns64 * sizeof(u64));
+        CK(cudaMemsetAsync(ix->X.p, 0, ix->R * ix->ns64 * sizeof(u64), cs));
+        CK(launch_pack_rows(st.d_ids, n, st.plan, st.max_chunks, view(ix), ix->X.as<u64>(), ctx->sms, cs));
     }
     ALLOC(ix->sizes_ref, n * sizeof(u64));
     CK(cudaMemcpyAsync(ix->sizes_ref.p, st.sizes.p, n * sizeof(u64), cudaMemcpyDeviceToDevice, cs));
@@ -422,9 +408,6 @@ int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_serve_optio
     // slots
     const u64 S = o.max_batch_samples, V = o.max_batch_values;
     const size_t cb = ix->count_bits == 64 ? 8 : 4;
-    ix->nwt = (ix->W + 63) / 64;
-    ix->nbk_t = std::max<u64>((ix->nwt + kScanBlockWords - 1) / kScanBlockWords, 1);
-    ix->Umax = std::min<u64>(ix->W, V);
     const u64 head = round_up(S + 1, 32);
     for (int k = 0; k < o.slots; ++k) ix->slots.emplace_back(new Slot);
     for (auto& sp : ix->slots) {
@@ -442,13 +425,7 @@ int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_serve_optio
         ALLOC(sl.sq, S * sizeof(u64));
         ALLOC(sl.qerr, S * sizeof(u32));
         ALLOC(sl.mm, 2 * sizeof(u64));
-        ALLOC(sl.touched, std::max<u64>(ix->nwt, 1) * sizeof(u64));
-        ALLOC(sl.dir_t, std::max<u64>(ix->nwt, 1) * sizeof(u32));
-        ALLOC(sl.bsum_t, ix->nbk_t * sizeof(u64));
-        ALLOC(sl.boff_t, ix->nbk_t * sizeof(u64));
         ALLOC(sl.Ud, sizeof(u64));
-        ALLOC(sl.Qc, std::max<u64>(ix->Umax, 1) * S * sizeof(u64));
-        ALLOC(sl.wlist, std::max<u64>(ix->Umax, 1) * sizeof(u64));
         ALLOC(sl.Cacc, S * n * sizeof(u32));
         ALLOC(sl.Cout, S * n * cb);
         ALLOC(sl.Jd, S * n * sizeof(double));
@@ -488,7 +465,7 @@ int jsim_index_info(const jsim_index* ix, uint64_t* n_ref, uint64_t* words, uint
 {
     if (!ix) return JSIM_ERR_ARG;
     if (n_ref) *n_ref = ix->n_ref;
-    if (words) *words = ix->W;
+    if (words) *words = ix->R;
     if (ref_sizes) memcpy(ref_sizes, ix->h_sizes_ref.data(), ix->n_ref * sizeof(u64));
     return JSIM_OK;
 }

@@ -70,7 +70,7 @@ class ServeOptions(ctypes.Structure):
 class ServeStats(ctypes.Structure):
     _fields_ = [("requests_submitted", ctypes.c_uint64), ("requests_done", ctypes.c_uint64),
                 ("samples_done", ctypes.c_uint64), ("values_done", ctypes.c_uint64),
-                ("batches", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("touched_words", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("rows_read", ctypes.c_uint64),
                 ("ms_device", ctypes.c_double), ("ms_product", ctypes.c_double),
                 ("index_bytes_read", ctypes.c_double),
                 ("bitops_dense", ctypes.c_double)]
@@ -408,9 +408,9 @@ class Index:
         _check(self._lib.jsim_index_build(ctx._h, ctypes.byref(s), ctypes.byref(opt), ctypes.byref(h)), ctx._h)
         self._h = h
         self._ref_keep = None  # the index holds its own copy
-        n_ref, words = ctypes.c_uint64(), ctypes.c_uint64()
-        _check(self._lib.jsim_index_info(self._h, ctypes.byref(n_ref), ctypes.byref(words), None))
-        self.n_ref, self.words = n_ref.value, words.value
+        n_ref, rows = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._lib.jsim_index_info(self._h, ctypes.byref(n_ref), ctypes.byref(rows), None))
+        self.n_ref, self.rows = n_ref.value, rows.value
 
     def ref_sizes(self):
         out = np.empty(self.n_ref, dtype=np.uint64)

@@ -26,9 +26,9 @@ def serve(a):
         dt = time.perf_counter() - t0
     st = ix.stats()
     b = max(1, st["batches"])
-    print("serve: index words=%d (%.2f GB), %d batches of 64 samples, touched %.0f words/batch, qprod %.3f ms/batch "
+    print("serve: index rows=%d (%.2f GB), %d batches of 64 samples, %.0f rows read/batch, query kernel %.3f ms/batch "
           "-> %.1f GB/s of index rows; last request %.1f ms" % (
-              ix.words, ix.words * 2048 * 8 / 1e9, st["batches"], st["touched_words"] / b, st["ms_product"] / b,
+              ix.rows, ix.rows * 2048 / 8 / 1e9, st["batches"], st["rows_read"] / b, st["ms_product"] / b,
               st["index_bytes_read"] / (st["ms_product"] * 1e-3) / 1e9, dt * 1e3))
     ix.close()
 

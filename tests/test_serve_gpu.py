@@ -63,7 +63,7 @@ def test_requests_match_oracle(gpu, ref, queries, count_bits, slots, max_samples
                 assert 0 <= qms <= tms
             st = ix.stats()
             assert st["requests_done"] == len(reqs) and st["samples_done"] == 48
-            assert st["batches"] >= 1 and st["touched_words"] > 0
+            assert st["batches"] >= 1 and st["rows_read"] > 0
 
 
 def test_alone_and_in_the_mix_are_identical(gpu, ref, queries):
@@ -117,7 +117,7 @@ def test_serve_edge_cases(gpu):
     with jsim.Context() as ctx:
         eoff, eids = collection([[], []])
         with jsim.Index(ctx, eoff, eids) as ix:
-            assert ix.words == 0
+            assert ix.rows == 0
             C, s, J = ix.submit(*collection([[1, 2], []])).wait()
             assert np.all(C == 0) and list(s) == [2, 0]
             assert list(J[0]) == [0.0, 0.0] and list(J[1]) == [1.0, 1.0]
