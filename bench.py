@@ -376,8 +376,10 @@ def run_streamed(args):
     with Clocks(0) as clk:
         dt_s, st_s, agg = timed(lambda: ctx.all_pairs_streamed(off, ids, staging_bytes=staging, out=(hC, hS, hJ)))
     J_s = hJ.copy()
-    dt_p, st_p, _ = timed(lambda: ctx.all_pairs(off, ids, out=(hC, hS, hJ)))
-    assert np.array_equal(J_s.view(np.uint64), hJ.view(np.uint64)), "streamed and plain results differ"
+    plain = os.environ.get("JSIM_STREAM_PLAIN", "1") != "0"
+    if plain:
+        dt_p, st_p, _ = timed(lambda: ctx.all_pairs(off, ids, out=(hC, hS, hJ)))
+        assert np.array_equal(J_s.view(np.uint64), hJ.view(np.uint64)), "streamed and plain results differ"
     bitops = st_s["bitops_dense"]
     variant = st_s["variant"]
     roof = roofline_for(variant, agg["bitops"] / max(1, agg["product_launches"]),
@@ -401,8 +403,8 @@ def run_streamed(args):
                     "d2h_bytes_per_step": int(n * n * 16 + n * 8)},
             "plain": {"value": bitops / dt_p / 1e12, "ms_per_step": dt_p * 1e3, "batches": st_p["batches"],
                       "how": "one jsim_all_pairs call on the same pageable host input and host outputs",
-                      "stage_ms": {k: round(st_p[k], 3) for k in stages}},
-            "speedup_vs_plain": dt_p / dt_s}
+                      "stage_ms": {k: round(st_p[k], 3) for k in stages}} if plain else None,
+            "speedup_vs_plain": dt_p / dt_s if plain else None}
     print(json.dumps(line))
     ctx.close()
     return 0
