@@ -31,7 +31,11 @@ constexpr int kQThreads = 256;
 constexpr int kQWarps = kQThreads / 32;
 constexpr int kPlanes = 13;   // counts of one chunk (<= kChunk = 4096 values) fit 13 bits
 static_assert((1ull << (kPlanes - 1)) >= kChunk, "bit planes hold a chunk's counts");
-constexpr int kQBatch = 8;    // rows in flight per lane
+// Build-time tuning: rows in flight per lane (JSIM_QBATCH).
+#ifndef JSIM_QBATCH
+#define JSIM_QBATCH 8
+#endif
+constexpr int kQBatch = JSIM_QBATCH;
 
 // rank of x in the reference filter, if f has row x
 __device__ __forceinline__ bool ref_rank(u64 x, u64 lo, u64 width, const u64* __restrict__ bm,
@@ -88,15 +92,20 @@ template <int KW>
 __global__ void __launch_bounds__(kQThreads)
 k_qrows(const u64* __restrict__ ids, u64 S, Plan plan, u64 lo, u64 width, const u64* __restrict__ bm,
         const u32* __restrict__ dir, const u64* __restrict__ boff, const u64* __restrict__ Xt, u64 ns64, u64 n_ref,
-        u32* Cacc, u64* rows_read)
+        u32* Cacc, u64* rows_read, u32 nsub)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const u64 nch = plan.totals[1];
-    for (u64 c = (u64)blockIdx.x * kQWarps + warp; c < nch; c += (u64)gridDim.x * kQWarps) {
+    // work item: part `part` (of nsub) of plan chunk c, so that small
+    // batches still spread over every SM
+    const u64 items = plan.totals[1] * nsub;
+    const u64 sub = kChunk / nsub;
+    for (u64 it = (u64)blockIdx.x * kQWarps + warp; it < items; it += (u64)gridDim.x * kQWarps) {
+        const u64 c = it / nsub, part = it - c * nsub;
         const u64 s = chunk_sample(plan.cofs, S, c);
-        const u64 sb = plan.beg[s];
-        const u64 p0 = sb + (c - plan.cofs[s]) * kChunk;
-        const u64 p1 = min(p0 + kChunk, plan.beg[s] + plan.len[s]);
+        const u64 sb = plan.beg[s], se = sb + plan.len[s];
+        const u64 p0 = sb + (c - plan.cofs[s]) * kChunk + part * sub;
+        if (p0 >= se) continue;
+        const u64 p1 = min(p0 + sub, se);
         u64 pl[KW][kPlanes];
         #pragma unroll
         for (int k = 0; k < KW; ++k)
@@ -202,16 +211,21 @@ cudaError_t launch_qrows(const u64* ids, u64 S, Plan plan, u64 max_chunks, const
                          u64* rows_read, int sms, cudaStream_t st)
 {
     if (ix.R == 0) return cudaSuccess;
-    const u64 blocks = std::max<u64>(1, std::min<u64>((max_chunks + kQWarps - 1) / kQWarps, (u64)sms * 8));
+    // split chunks into up to 8 parts while the batch gives fewer than about
+    // 32 warps per SM
+    u32 nsub = 1;
+    while (nsub < 8 && max_chunks * nsub < (u64)sms * 32) nsub <<= 1;
+    const u64 items = max_chunks * nsub;
+    const u64 blocks = std::max<u64>(1, std::min<u64>((items + kQWarps - 1) / kQWarps, (u64)sms * 8));
     if (ix.ns64 <= 32)
         k_qrows<1><<<(unsigned)blocks, kQThreads, 0, st>>>(ids, S, plan, ix.lo, ix.width, ix.bm, ix.dir, ix.boff,
-                                                           ix.index, ix.ns64, ix.n_ref, Cacc, rows_read);
+                                                           ix.index, ix.ns64, ix.n_ref, Cacc, rows_read, nsub);
     else if (ix.ns64 <= 64)
         k_qrows<2><<<(unsigned)blocks, kQThreads, 0, st>>>(ids, S, plan, ix.lo, ix.width, ix.bm, ix.dir, ix.boff,
-                                                           ix.index, ix.ns64, ix.n_ref, Cacc, rows_read);
+                                                           ix.index, ix.ns64, ix.n_ref, Cacc, rows_read, nsub);
     else if (ix.ns64 <= 128)
         k_qrows<4><<<(unsigned)blocks, kQThreads, 0, st>>>(ids, S, plan, ix.lo, ix.width, ix.bm, ix.dir, ix.boff,
-                                                           ix.index, ix.ns64, ix.n_ref, Cacc, rows_read);
+                                                           ix.index, ix.ns64, ix.n_ref, Cacc, rows_read, nsub);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
