@@ -164,6 +164,9 @@ void jsim_destroy(jsim_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     jsim_batched_release(ctx);
     jsim_streamed_release(ctx);
+    for (cudaStream_t s : ctx->lanes) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    for (cudaEvent_t e : ctx->lane_join) cudaEventDestroy(e);
+    if (ctx->lane_fork) cudaEventDestroy(ctx->lane_fork);
     if (ctx->d_err) ctx->opt.free(ctx->d_err, 256, (void*)ctx->stream, ctx->opt.alloc_user);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);

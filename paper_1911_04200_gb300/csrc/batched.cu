@@ -34,12 +34,19 @@ struct Col {
     bool empty = false;
 };
 
+// Independent collections are ingested, multiplied (CUDA-core product) and
+// finished on kLanes side streams at once: their kernels are small, and one
+// stream would run them one after another.
+constexpr int kLanes = 4;
+
 // Everything one wave of collections needs on the device; kept alive by the
 // graph cache so a replay finds the same addresses.
 struct Wave {
     std::vector<Col> cols;
     DevBuf xpool, cpool, spool, ppool, scal, ids_pool, off_pool;
-    DevBuf bitmap, seen, dir, bsum, boff, R;  // bitmap: the rows kept; seen: every row (filter_min 2)
+    // per lane: bitmap (the rows kept), seen (every row, filter_min 2), rank
+    // directory and row count of the collection the lane is packing
+    DevBuf bitmap[kLanes], seen[kLanes], dir[kLanes], bsum[kLanes], boff[kLanes], R[kLanes];
     DevBuf jobtab;          // tensor-core job table
     DevBuf cstage, jstage;  // host-output staging
     u64 max_mt = 0;
@@ -85,9 +92,13 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
     if (!run_product_only) {
         CK(cudaMemsetAsync(w.xpool.p, 0, w.xpool.bytes, st));
         CK(cudaMemsetAsync(scal, 0, w.cols.size() * 2 * sizeof(u64), st));
+        int rc = lanes_fork(ctx, kLanes);
+        if (rc) return rc;
         for (size_t c = 0; c < w.cols.size(); ++c) {
             const Col& cl = w.cols[c];
             if (cl.empty) continue;
+            const int ln = (int)(c % kLanes);
+            cudaStream_t ls = ctx->lanes[ln];
             Plan plan;
             u64* pb = w.ppool.as<u64>() + cl.p_off;
             plan.beg = pb; plan.len = pb + cl.n; plan.cofs = pb + 2 * cl.n; plan.totals = pb + 3 * cl.n + 1;
@@ -95,23 +106,26 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
             const u64 nwords = cl.mt / 64;
             for (u64 l = 0; l < cl.rounds; ++l) {
                 const u64 lo = cl.lo0 + l * cl.mt;
-                CK(launch_plan(cl.d_off, cl.d_ids, cl.n, lo, lo + cl.mt, false, plan, st));
-                CK(cudaMemsetAsync(w.bitmap.p, 0, nwords * sizeof(u64), st));
+                CK(launch_plan(cl.d_off, cl.d_ids, cl.n, lo, lo + cl.mt, false, plan, ls));
+                CK(cudaMemsetAsync(w.bitmap[ln].p, 0, nwords * sizeof(u64), ls));
                 if (ctx->opt.filter_min == 2) {
-                    CK(cudaMemsetAsync(w.seen.p, 0, nwords * sizeof(u64), st));
-                    CK(launch_filter(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.seen.as<u32>(), ctx->sms, st,
-                                     w.bitmap.as<u32>()));
+                    CK(cudaMemsetAsync(w.seen[ln].p, 0, nwords * sizeof(u64), ls));
+                    CK(launch_filter(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.seen[ln].as<u32>(), ctx->sms,
+                                     ls, w.bitmap[ln].as<u32>()));
                 } else {
-                    CK(launch_filter(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.bitmap.as<u32>(), ctx->sms,
-                                     st));
+                    CK(launch_filter(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.bitmap[ln].as<u32>(),
+                                     ctx->sms, ls));
                 }
-                CK(launch_scan(w.bitmap.as<u64>(), nwords, w.dir.as<u32>(), w.bsum.as<u64>(), w.boff.as<u64>(),
-                               w.R.as<u64>(), st, scal + 2 * c, scal + 2 * c + 1));
-                CK(launch_pack_full(cl.d_ids, cl.n, plan, cl.max_chunks, lo, w.bitmap.as<u64>(), w.dir.as<u32>(),
-                                    w.boff.as<u64>(), X, cl.stride, w.R.as<u64>(), ctx->sms, st, scal + 2 * c + 1));
+                CK(launch_scan(w.bitmap[ln].as<u64>(), nwords, w.dir[ln].as<u32>(), w.bsum[ln].as<u64>(),
+                               w.boff[ln].as<u64>(), w.R[ln].as<u64>(), ls, scal + 2 * c, scal + 2 * c + 1));
+                CK(launch_pack_full(cl.d_ids, cl.n, plan, cl.max_chunks, lo, w.bitmap[ln].as<u64>(),
+                                    w.dir[ln].as<u32>(), w.boff[ln].as<u64>(), X, cl.stride, w.R[ln].as<u64>(),
+                                    ctx->sms, ls, scal + 2 * c + 1));
                 ctx->stats.launches += 5;
             }
         }
+        rc = lanes_join(ctx, kLanes);
+        if (rc) return rc;
     }
     CK(cudaMemsetAsync(w.cpool.p, 0, w.cpool.bytes, st));
     // product: all collections
@@ -125,23 +139,30 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
         ctx->stats.product_launches += launches;
         ctx->stats.launches += launches;
     } else {
+        int rc = lanes_fork(ctx, kLanes);
+        if (rc) return rc;
         for (size_t c = 0; c < w.cols.size(); ++c) {
             const Col& cl = w.cols[c];
             if (cl.empty || cl.n == 0) continue;
+            cudaStream_t ls = ctx->lanes[c % kLanes];
             ProductArgs a{};
             a.X = w.xpool.as<u64>() + cl.x_off; a.stride = cl.stride; a.n = cl.n; a.W = cl.stride;
             a.Wdev = scal + 2 * c; a.C = (char*)w.cpool.p + cl.c_off; a.ldc = cl.n;
             a.count_bits = ctx->opt.count_bits; a.word_bits = word_bits; a.sms = ctx->sms;
             a.timeout_ms = ctx->opt.timeout_ms; a.err = ctx->d_err;
-            cudaError_t e = product_popc(a, st);
+            cudaError_t e = product_popc(a, ls);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "batched CUDA-core product");
             ctx->stats.product_launches += a.launches;
             ctx->stats.launches += a.launches;
         }
+        rc = lanes_join(ctx, kLanes);
+        if (rc) return rc;
     }
     if (run_product_only) return JSIM_OK;
     // epilogue per collection, into the outputs (device) or staging (host)
     size_t cs = 0, js = 0;
+    int rce = lanes_fork(ctx, kLanes);
+    if (rce) return rce;
     for (size_t c = 0; c < w.cols.size(); ++c) {
         const Col& cl = w.cols[c];
         const size_t gi = first + c;
@@ -155,10 +176,10 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
         js += cl.n * cl.n * sizeof(double);
         if (cl.n == 0 || (!Cd && !Jd)) continue;
         CK(launch_epilogue((char*)w.cpool.p + cl.c_off, cl.n, ctx->opt.count_bits, w.spool.as<u64>() + cl.s_off, Cd,
-                           Jd, st, ctx->opt.filter_min == 2));
+                           Jd, ctx->lanes[c % kLanes], ctx->opt.filter_min == 2));
         ctx->stats.launches += 1;
     }
-    return JSIM_OK;
+    return lanes_join(ctx, kLanes);
 }
 
 // word counts of the call (device running totals) into the statistics
@@ -370,19 +391,26 @@ replan:
         StageTimer t(ctx, &ctx->stats.ms_validate);
         CK(cudaMemsetAsync(w.spool.p, 0, w.spool.bytes, ctx->stream));
         CK(cudaMemsetAsync(flags.p, 0, 3 * sizeof(u64) * k, ctx->stream));
+        for (u64 c = 0; c < k; ++c) CK(cudaMemsetAsync(flags.as<u64>() + 3 * c + 2, 0xff, 8, ctx->stream));
+        int rc = lanes_ensure(ctx, kLanes);
+        if (rc) return rc;
+        rc = lanes_fork(ctx, kLanes);
+        if (rc) return rc;
         for (u64 c = 0; c < k; ++c) {
             Col& x = w.cols[c];
-            CK(cudaMemsetAsync(flags.as<u64>() + 3 * c + 2, 0xff, 8, ctx->stream));
             if (x.n == 0) continue;
+            cudaStream_t ls = ctx->lanes[c % kLanes];
             Plan plan;
             u64* pb = w.ppool.as<u64>() + x.p_off;
             plan.beg = pb; plan.len = pb + x.n; plan.cofs = pb + 2 * x.n; plan.totals = pb + 3 * x.n + 1;
-            CK(launch_plan(x.d_off, x.d_ids, x.n, 0, 0, true, plan, ctx->stream));
+            CK(launch_plan(x.d_off, x.d_ids, x.n, 0, 0, true, plan, ls));
             CK(launch_validate(x.d_off, x.d_ids, x.n, plan, x.max_chunks, ctx->opt.id_bits, w.spool.as<u64>() + x.s_off,
                                (u32*)(flags.as<u64>() + 3 * c), flags.as<u64>() + 3 * c + 1,
-                               flags.as<u64>() + 3 * c + 2, ctx->sms, ctx->stream));
+                               flags.as<u64>() + 3 * c + 2, ctx->sms, ls));
             ctx->stats.launches += 2;
         }
+        rc = lanes_join(ctx, kLanes);
+        if (rc) return rc;
     }
     std::vector<u64> hf(3 * k), hs(std::max<size_t>(s_tot, 1));
     CK(cudaMemcpyAsync(hf.data(), flags.p, 3 * sizeof(u64) * k, cudaMemcpyDeviceToHost, ctx->stream));
@@ -431,12 +459,14 @@ replan:
     {
         const u64 nwords = std::max<u64>(w.max_mt / 64, 1);
         const u64 nb = (nwords + kScanBlockWords - 1) / kScanBlockWords;
-        ALLOC(w.bitmap, nwords * 8);
-        if (ctx->opt.filter_min == 2) ALLOC(w.seen, nwords * 8);
-        ALLOC(w.dir, nwords * 4);
-        ALLOC(w.bsum, std::max<u64>(nb, 1) * 8);
-        ALLOC(w.boff, std::max<u64>(nb, 1) * 8);
-        ALLOC(w.R, 8);
+        for (int l = 0; l < kLanes; ++l) {
+            ALLOC(w.bitmap[l], nwords * 8);
+            if (ctx->opt.filter_min == 2) ALLOC(w.seen[l], nwords * 8);
+            ALLOC(w.dir[l], nwords * 4);
+            ALLOC(w.bsum[l], std::max<u64>(nb, 1) * 8);
+            ALLOC(w.boff[l], std::max<u64>(nb, 1) * 8);
+            ALLOC(w.R[l], 8);
+        }
         ALLOC(w.xpool, std::max<size_t>(x_tot, 1) * 8);
         ALLOC(w.cpool, std::max<size_t>(c_tot, 8));
         ALLOC(w.scal, 2 * sizeof(u64) * k);

@@ -36,6 +36,11 @@ struct jsim_ctx {
     std::vector<Pending> pending;
     // streamed calls: pinned staging buffers kept between calls
     StreamState* streamed = nullptr;
+    // side streams for independent per-collection work (batched calls), with
+    // a fork event on the context's stream and one join event per lane
+    std::vector<cudaStream_t> lanes;
+    cudaEvent_t lane_fork = nullptr;
+    std::vector<cudaEvent_t> lane_join;
 };
 
 namespace {
@@ -167,6 +172,40 @@ struct CallScope {
 };
 
 u64 round_up(u64 x, u64 m) { return (x + m - 1) / m * m; }
+
+// Side streams: work on lane l is ordered after everything queued on the
+// context's stream before lanes_fork, and everything queued on it after
+// lanes_join waits for all lanes.  Under stream capture the lanes become
+// parallel branches of the graph.
+int lanes_ensure(jsim_ctx* ctx, int k)
+{
+    if (!ctx->lane_fork) CK(cudaEventCreateWithFlags(&ctx->lane_fork, cudaEventDisableTiming));
+    while ((int)ctx->lanes.size() < k) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        ctx->lanes.push_back(s);
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->lane_join.push_back(e);
+    }
+    return JSIM_OK;
+}
+
+int lanes_fork(jsim_ctx* ctx, int k)
+{
+    CK(cudaEventRecord(ctx->lane_fork, ctx->stream));
+    for (int l = 0; l < k; ++l) CK(cudaStreamWaitEvent(ctx->lanes[l], ctx->lane_fork, 0));
+    return JSIM_OK;
+}
+
+int lanes_join(jsim_ctx* ctx, int k)
+{
+    for (int l = 0; l < k; ++l) {
+        CK(cudaEventRecord(ctx->lane_join[l], ctx->lanes[l]));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->lane_join[l], 0));
+    }
+    return JSIM_OK;
+}
 
 int check_sets(const jsim_sets* s)
 {

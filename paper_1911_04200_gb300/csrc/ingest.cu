@@ -144,29 +144,56 @@ k_filter(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, u32* 
 }
 
 // Directory pass 1: per 4096-word block, block-relative exclusive popcounts.
+// Rounds of 512 consecutive words, two per thread, so every load and store
+// of a warp is one contiguous 256-byte (load) or 128-byte (store) run.
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_blocks(const u64* __restrict__ bitmap, u64 nwords, u32* __restrict__ dir, u64* __restrict__ bsum)
 {
-    __shared__ u64 sm[kScanThreads / 32];
-    const u64 w0 = (u64)blockIdx.x * kScanBlockWords + (u64)threadIdx.x * kScanPerThread;
-    u32 pc[kScanPerThread];
-    u32 mine = 0;
-    #pragma unroll
-    for (int k = 0; k < kScanPerThread; ++k) {
-        u64 w = w0 + k;
-        pc[k] = w < nwords ? __popcll(bitmap[w]) : 0u;
-        mine += pc[k];
+    constexpr int kRound = 2 * kScanThreads;
+    static_assert(kScanBlockWords % kRound == 0, "whole rounds per block");
+    __shared__ u32 wsum[kScanThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const bool vec = ((uintptr_t)bitmap & 15u) == 0 && ((uintptr_t)dir & 7u) == 0;
+    const u64 b0 = (u64)blockIdx.x * kScanBlockWords;
+    u32 run = 0;
+    for (int it = 0; it < (int)(kScanBlockWords / kRound); ++it) {
+        const u64 w = b0 + (u64)it * kRound + 2 * (u64)t;
+        u64 a = 0, b = 0;
+        if (vec && w + 1 < nwords) {
+            const ulonglong2 v = __ldg((const ulonglong2*)(bitmap + w));
+            a = v.x;
+            b = v.y;
+        } else {
+            if (w < nwords) a = bitmap[w];
+            if (w + 1 < nwords) b = bitmap[w + 1];
+        }
+        const u32 pa = (u32)__popcll(a), pc = pa + (u32)__popcll(b);
+        u32 x = pc;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        u32 woff = 0, tot = 0;
+        #pragma unroll
+        for (int k = 0; k < kScanThreads / 32; ++k) {
+            const u32 v = wsum[k];
+            if (k < warp) woff += v;
+            tot += v;
+        }
+        const u32 ex = run + woff + x - pc;
+        if (vec && w + 1 < nwords) {
+            *(uint2*)(dir + w) = make_uint2(ex, ex + pa);
+        } else {
+            if (w < nwords) dir[w] = ex;
+            if (w + 1 < nwords) dir[w + 1] = ex + pa;
+        }
+        run += tot;
+        __syncthreads();  // wsum is rewritten next round
     }
-    u64 ex;
-    u64 tot = block_exclusive_scan<kScanThreads>((u64)mine, ex, sm);
-    u32 run = (u32)ex;
-    #pragma unroll
-    for (int k = 0; k < kScanPerThread; ++k) {
-        u64 w = w0 + k;
-        if (w < nwords) dir[w] = run;
-        run += pc[k];
-    }
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+    if (t == 0) bsum[blockIdx.x] = run;
 }
 
 // Directory pass 2 (one CTA): exclusive prefix of block sums; R = total.

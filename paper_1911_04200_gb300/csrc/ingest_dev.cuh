@@ -9,7 +9,6 @@ namespace {
 constexpr int kPlanThreads = 1024;
 constexpr int kIngestThreads = 256;
 constexpr int kScanThreads = 256;
-constexpr int kScanPerThread = (int)(kScanBlockWords / kScanThreads);  // 16
 
 __device__ __forceinline__ u64 lower_bound_u64(const u64* a, u64 lo, u64 hi, u64 v)
 {
