@@ -500,8 +500,11 @@ def run_serve(args):
                                                                          J[n_ref:, :n_ref].view(np.uint64))
     pk, src = measured_peaks()
     achieved = d["index_bytes_read"] / (d["ms_product"] * 1e-3) / 1e9 if d["ms_product"] else 0.0
+    tq = traffic_from_profiles("qrows", "serve2048")
+    traffic = (round(tq["bytes_per_row"] * d["rows_read"] / max(1, d["batches"]))
+               if isinstance(tq, dict) and "bytes_per_row" in tq else None)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic_from_profiles("qrows", "serve2048"),
+            "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
             "kernel": "k_qrows", "peak_source": "%s HBM copy bandwidth" % src,
             "unit_bytes": "index rows read (ceil(n_ref/64) x 8 B per query value the filter holds)"}
     line = {"metric": METRIC, "value": capacity, "unit": "requests/s", "n_gpus": 1, "steps": n_req,
