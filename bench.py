@@ -499,14 +499,18 @@ def run_serve(args):
         assert np.array_equal(Cs, C[n_ref:, :n_ref]) and np.array_equal(Js.view(np.uint64),
                                                                          J[n_ref:, :n_ref].view(np.uint64))
     pk, src = measured_peaks()
-    achieved = d["index_bytes_read"] / (d["ms_product"] * 1e-3) / 1e9 if d["ms_product"] else 0.0
+    # algorithmic bytes of the query kernel: per row read, the row plus the
+    # value's 8 bytes, its filter word and its directory entry
+    alg = d["index_bytes_read"] + 20.0 * d["rows_read"]
+    achieved = alg / (d["ms_product"] * 1e-3) / 1e9 if d["ms_product"] else 0.0
     tq = traffic_from_profiles("qrows", "serve2048")
     traffic = (round(tq["bytes_per_row"] * d["rows_read"] / max(1, d["batches"]))
                if isinstance(tq, dict) and "bytes_per_row" in tq else None)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
             "kernel": "k_qrows", "peak_source": "%s HBM copy bandwidth" % src,
-            "unit_bytes": "index rows read (ceil(n_ref/64) x 8 B per query value the filter holds)"}
+            "unit_bytes": "per query value the filter holds: its row (ceil(n_ref/64) x 8 B) + 8 B value + "
+                          "8 B filter word + 4 B directory entry"}
     line = {"metric": METRIC, "value": capacity, "unit": "requests/s", "n_gpus": 1, "steps": n_req,
             "warmup": args.warmup, "ms_per_step": elapsed / n_req * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
