@@ -318,17 +318,18 @@ u64 auto_batch_rows(u64 domain)
     return m;
 }
 
-// Variant choice (measured on GB300: for 1024 samples the CUDA-core
-// AND+popcount kernel runs ~128 Tbit-ops/s, the legacy mma.sync e4m3/s8/b1
-// kernels at or below that, the one-SM tcgen05 FP8 kernel ~680 and the SM-pair
-// kernel ~840 (~1130 at 4096 samples); for 64 samples the CUDA-core kernel
-// wins, 0.33 ms against 0.88 ms per all-pairs call, because one tensor tile is
-// mostly idle).
+// Variant choice, from a sweep on GB300 (random packed words, Tbit-ops/s):
+//   n      64    128   192   256   512   1024  2048
+//   POPC   71    92    104   111   123   130   142
+//   TC     32    124   193   333   491   654   831
+//   TC2    24    95    211   377   601   848   1069
+// (the legacy mma.sync kernels stay at or below POPC).  Tensor tiles of 128
+// or 256 samples are mostly idle for small n.
 int choose_variant(jsim_ctx* ctx, u64 n, u64 W)
 {
     (void)W;
-    if (n >= 256 && product_tc_supported(ctx->opt.device)) return JSIM_VARIANT_TC2;
-    return JSIM_VARIANT_POPC;
+    if (n <= 96 || !product_tc_supported(ctx->opt.device)) return JSIM_VARIANT_POPC;
+    return n <= 160 ? JSIM_VARIANT_TC : JSIM_VARIANT_TC2;
 }
 
 int run_product(jsim_ctx* ctx, int variant, const u64* X, u64 stride, u64 n, u64 W, void* C)
