@@ -354,6 +354,20 @@ JSIM_API int jsim_request_latency(const jsim_request* r, double* queued_ms, doub
 /* Release a request: a queued one is withdrawn, a running one is waited for. */
 JSIM_API void jsim_request_free(jsim_request* r);
 
+/*
+ * Nearest neighbours: for every sample i, the k samples j != i with the
+ * largest J[i][j], best first; ties in J go to the smaller j, so the result is
+ * unique.  The sparsified output for collections too large to keep n x n
+ * (the paper's all-pairs matrix, Sec. II-A, feeds exactly such queries).
+ *   J     n*n row-major binary64 as jsim_all_pairs writes it (values in [0, 1])
+ *   k     1..64 and < n
+ *   idx   n*k uint64 neighbour indices; val n*k binary64 of their J, or NULL
+ *   mem   JSIM_MEM_HOST or JSIM_MEM_DEVICE for J, idx and val
+ * Errors: JSIM_ERR_ARG, JSIM_ERR_OOM, JSIM_ERR_CUDA.
+ */
+JSIM_API int jsim_topk(jsim_ctx* ctx, const double* J, uint64_t n, uint32_t k, uint64_t* idx, double* val,
+                       int mem);
+
 /* Statistics of the last call on the context. */
 JSIM_API int jsim_get_stats(const jsim_ctx* ctx, jsim_stats* out);
 

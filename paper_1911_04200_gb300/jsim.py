@@ -110,6 +110,8 @@ SIGNATURES = {
     "jsim_request_latency": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]),
     "jsim_request_free": (None, [ctypes.c_void_p]),
+    "jsim_topk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_int]),
     "jsim_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "jsim_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "jsim_last_cuda_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -364,6 +366,24 @@ class Context:
                                  ctypes.byref(R), self._ptr(sz), MEM_HOST)
         _check(rc, self._h)
         return filt, words, R.value, sz
+
+    def topk(self, J, k: int, want_val: bool = True):
+        """(idx n x k uint64, val n x k binary64 or None): the k samples with the
+        largest J of every sample (itself excluded), ties to the smaller index."""
+        torch = _torch()
+        is_dev = isinstance(J, torch.Tensor) and J.is_cuda
+        n = J.shape[0]
+        if is_dev:
+            idx = torch.empty((n, k), dtype=torch.uint64, device=J.device)
+            val = torch.empty((n, k), dtype=torch.float64, device=J.device) if want_val else None
+        else:
+            J = np.ascontiguousarray(J, dtype=np.float64)
+            idx = np.empty((n, k), dtype=np.uint64)
+            val = np.empty((n, k), dtype=np.float64) if want_val else None
+        self._order()
+        _check(self._lib.jsim_topk(self._h, self._ptr(J), n, k, self._ptr(idx), self._ptr(val),
+                                   MEM_DEVICE if is_dev else MEM_HOST), self._h)
+        return idx, val
 
     def product(self, words, n: int, W: int, stride: int, C=None, variant: str | int = "auto"):
         """C = X X^T over (AND, popcount, +) of device-resident packed words."""
