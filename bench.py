@@ -500,8 +500,8 @@ def run_serve(args):
                                                                          J[n_ref:, :n_ref].view(np.uint64))
     pk, src = measured_peaks()
     # algorithmic bytes of the query kernel: per row read, the row plus the
-    # value's 8 bytes, its filter word and its directory entry
-    alg = d["index_bytes_read"] + 20.0 * d["rows_read"]
+    # value's 8 bytes and its 16-byte filter entry (word, rank of its first bit)
+    alg = d["index_bytes_read"] + 24.0 * d["rows_read"]
     achieved = alg / (d["ms_product"] * 1e-3) / 1e9 if d["ms_product"] else 0.0
     tq = traffic_from_profiles("qrows", "serve2048")
     traffic = (round(tq["bytes_per_row"] * d["rows_read"] / max(1, d["batches"]))
@@ -510,7 +510,7 @@ def run_serve(args):
             "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
             "kernel": "k_qrows", "peak_source": "%s HBM copy bandwidth" % src,
             "unit_bytes": "per query value the filter holds: its row (ceil(n_ref/64) x 8 B) + 8 B value + "
-                          "8 B filter word + 4 B directory entry"}
+                          "16 B filter entry (word, rank of its first bit)"}
     line = {"metric": METRIC, "value": capacity, "unit": "requests/s", "n_gpus": 1, "steps": n_req,
             "warmup": args.warmup, "ms_per_step": elapsed / n_req * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",

@@ -107,18 +107,23 @@ bool product_tc_supported(int device);
 // j holds row r).
 struct QueryIndex {
     const u64* index;
-    const u64* bm;
+    const u64* bm;           // filter words, rank directory and block offsets (build)
     const u32* dir;
     const u64* boff;
+    const ulonglong2* fr;    // (filter word, rank of its first bit) per word (queries)
     u64 lo, width, R, n_ref, ns64;
 };
 // build: Xt (R x ns64, zeroed by the caller) gets bit i of row rank(x) for
 // every value x of reference sample i
 cudaError_t launch_pack_rows(const u64* ids, u64 n, Plan plan, u64 max_chunks, const QueryIndex& ix, u64* Xt,
                              int sms, cudaStream_t st);
+// fr[w] = (bm[w], boff[w / kScanBlockWords] + dir[w]) for the width / 64 words
+cudaError_t launch_rank_words(const QueryIndex& ix, ulonglong2* fr, int sms, cudaStream_t st);
 // Cacc (S x n_ref u32, zeroed by the caller) += query x reference counts;
-// *rows_read += query values found in the filter; ns64 <= 128 (n_ref <= 8192)
-cudaError_t launch_qrows(const u64* ids, u64 S, Plan plan, u64 max_chunks, const QueryIndex& ix, u32* Cacc,
+// *rows_read += query values found in the filter; ns64 <= 128 (n_ref <= 8192).
+// The S samples lie back to back in ids (plan of offsets, full); values =
+// their total (host copy).
+cudaError_t launch_qrows(const u64* ids, u64 S, Plan plan, u64 values, const QueryIndex& ix, u32* Cacc,
                          u64* rows_read, int sms, cudaStream_t st);
 cudaError_t launch_qepi(const u32* Cacc, u64 S, u64 n_ref, const u64* sq, const u64* sr, int count_bits, void* Cout,
                         double* J, int sms, cudaStream_t st);

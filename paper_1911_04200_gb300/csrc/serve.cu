@@ -70,7 +70,7 @@ struct jsim_index {
     jsim_ctx* ctx = nullptr;
     jsim_serve_options opt{};
     u64 n_ref = 0, ns64 = 0, lo = 0, width = 0, R = 0;
-    DevBuf X, bm, dir, boff, sizes_ref;
+    DevBuf X, bm, dir, boff, fr, sizes_ref;
     std::vector<u64> h_sizes_ref;
     std::vector<std::unique_ptr<Slot>> slots;
     std::thread worker;
@@ -92,6 +92,7 @@ QueryIndex view(const jsim_index* ix)
     q.bm = ix->bm.as<u64>();
     q.dir = ix->dir.as<u32>();
     q.boff = ix->boff.as<u64>();
+    q.fr = ix->fr.as<ulonglong2>();
     q.lo = ix->lo;
     q.width = ix->width;
     q.R = ix->R;
@@ -179,7 +180,7 @@ int launch_batch(jsim_index* ix, Slot& sl)
     CK(cudaMemsetAsync(sl.Cacc.p, 0, S * ix->n_ref * sizeof(u32), st));
     CK(cudaMemsetAsync(sl.Ud.p, 0, sizeof(u64), st));
     CK(cudaEventRecord(sl.evp0, st));
-    CK(launch_qrows(d_ids, S, plan, max_chunks, qi, sl.Cacc.as<u32>(), sl.Ud.as<u64>(), ix->sms, st));
+    CK(launch_qrows(d_ids, S, plan, V, qi, sl.Cacc.as<u32>(), sl.Ud.as<u64>(), ix->sms, st));
     CK(cudaEventRecord(sl.evp1, st));
     CK(launch_qepi(sl.Cacc.as<u32>(), S, ix->n_ref, sl.sq.as<u64>(), ix->sizes_ref.as<u64>(), ix->count_bits,
                    sl.Cout.p, sl.Jd.as<double>(), ix->sms, st));
@@ -400,6 +401,14 @@ int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_serve_optio
         ALLOC(ix->X, std::max<u64>(ix->R, 1) * ix->ns64 * sizeof(u64));
         CK(cudaMemsetAsync(ix->X.p, 0, ix->R * ix->ns64 * sizeof(u64), cs));
         CK(launch_pack_rows(st.d_ids, n, st.plan, st.max_chunks, view(ix), ix->X.as<u64>(), ctx->sms, cs));
+        // queries rank through one 16-byte entry per filter word; the
+        // separate bitmap, directory and block offsets are build-only
+        ALLOC(ix->fr, nw * sizeof(ulonglong2));
+        CK(launch_rank_words(view(ix), ix->fr.as<ulonglong2>(), ctx->sms, cs));
+        CK(cudaStreamSynchronize(cs));
+        ix->bm.release();
+        ix->dir.release();
+        ix->boff.release();
     }
     ALLOC(ix->sizes_ref, n * sizeof(u64));
     CK(cudaMemcpyAsync(ix->sizes_ref.p, st.sizes.p, n * sizeof(u64), cudaMemcpyDeviceToDevice, cs));
