@@ -12,7 +12,8 @@ Two oracles live here, both written from arXiv 1911.04200:
 * ``oracle.c`` (loaded through ``ctypes`` below) is the plain definition:
   distinct-value counts, pairwise intersections by a two-pointer merge of
   sorted lists, union by inclusion-exclusion and the binary64 quotient
-  (Sec. II-A, Sec. III-A, Eq. 2).
+  (Sec. II-A, Sec. III-A, Eq. 2), and the Jaccard distance 1 - J as the
+  quotient (union - intersection) / union (Sec. II-A).
 * ``packed.py`` follows the paper's batched method step by step in numpy:
   row batches (Eq. 3), the zero-row filter (Eq. 5), its prefix sum and the
   compacted rows (Eq. 6), b-bit bitmask words and the AND+popcount product
@@ -69,6 +70,10 @@ def _load():
             lib.oracle_intersect.argtypes = [_u64p, ctypes.c_uint64, _u64p, ctypes.c_uint64]
             lib.oracle_jaccard.restype = ctypes.c_double
             lib.oracle_jaccard.argtypes = [ctypes.c_uint64] * 3
+            lib.oracle_distance.restype = ctypes.c_double
+            lib.oracle_distance.argtypes = [ctypes.c_uint64] * 3
+            lib.oracle_distance_matrix.restype = None
+            lib.oracle_distance_matrix.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p, _u64p, _f64p]
             lib.oracle_all_pairs.restype = None
             lib.oracle_all_pairs.argtypes = [ctypes.c_uint64, _u64p, _u64p, _u64p, _u64p, _f64p, ctypes.c_int]
             lib.oracle_pairs.restype = None
@@ -112,6 +117,23 @@ def intersect(a, b) -> int:
 def jaccard(inter: int, size_x: int, size_y: int) -> float:
     """b / (|X|+|Y|-b) in binary64, 1.0 for two empty sets."""
     return float(_load().oracle_jaccard(inter, size_x, size_y))
+
+
+def distance(inter: int, size_x: int, size_y: int) -> float:
+    """Jaccard distance (|X|+|Y|-2b) / (|X|+|Y|-b) in binary64, 0.0 for two
+    empty sets (Sec. II-A: 1 - J, as one quotient of integers)."""
+    return float(_load().oracle_distance(inter, size_x, size_y))
+
+
+def distance_matrix(C, srow, scol):
+    """Distances of a count matrix C (rows x cols) with the row and column
+    samples' sizes."""
+    C, srow, scol = _u64(C), _u64(srow), _u64(scol)
+    nr, nc = C.shape
+    D = np.zeros((nr, nc), dtype=np.float64)
+    if nr and nc:
+        _load().oracle_distance_matrix(nr, nc, _p64(C), _p64(srow), _p64(scol), _pf(D))
+    return D
 
 
 def all_pairs(offsets, ids, threads: int | None = None):

@@ -62,6 +62,26 @@ double oracle_jaccard(uint64_t inter, uint64_t size_x, uint64_t size_y)
 }
 
 /*
+ * Jaccard distance 1 - J (Sec. II-A) as the binary64 quotient of integers:
+ * (|X u Y| - |X n Y|) / |X u Y|, the size of the symmetric difference over
+ * the union, 0 for two empty sets.
+ */
+double oracle_distance(uint64_t inter, uint64_t size_x, uint64_t size_y)
+{
+    uint64_t uni = size_x + size_y - inter;
+    if (uni == 0) return 0.0;
+    return (double)(uni - inter) / (double)uni;
+}
+
+/* D[r][c] = oracle_distance(C[r][c], srow[r], scol[c]) for an nr x nc matrix. */
+void oracle_distance_matrix(uint64_t nr, uint64_t nc, const uint64_t* C, const uint64_t* srow,
+                            const uint64_t* scol, double* D)
+{
+    for (uint64_t r = 0; r < nr; ++r)
+        for (uint64_t c = 0; c < nc; ++c) D[r * nc + c] = oracle_distance(C[r * nc + c], srow[r], scol[c]);
+}
+
+/*
  * All pairs of one collection.  offsets has n+1 entries; sample i is
  * ids[offsets[i] .. offsets[i+1]).  C and J are n*n row-major (either may be
  * NULL), sizes has n entries (may be NULL).

@@ -8,7 +8,8 @@ from here, so both sides see identical collections.
 A collection is ``(offsets, ids)``: ``offsets`` is uint64[n+1], sample i is
 ``ids[offsets[i]:offsets[i+1]]``, sorted ascending with no repeats.
 
-The recipes (``ANCESTRAL`` and ``CLADE``) are documented in ``synth.c``.  The
+The recipes (``ANCESTRAL``, ``CLADE`` and ``BERNOULLI``) are documented in
+``synth.c``.  The
 named workloads stand in for the paper's k-mer datasets (Kingsford RNASeq and
 BIGSI, Sec. V-A), which are not available here; they reproduce the stated
 shapes (sample counts, set-size distributions, value domains, clade
@@ -39,7 +40,8 @@ class _Params(ctypes.Structure):
                 ("n_anc", ctypes.c_uint64), ("anc_size", ctypes.c_uint64),
                 ("n_clades", ctypes.c_uint64), ("core", ctypes.c_double), ("u_max", ctypes.c_double),
                 ("median", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("lo", ctypes.c_double), ("hi", ctypes.c_double)]
+                ("lo", ctypes.c_double), ("hi", ctypes.c_double),
+                ("m", ctypes.c_uint64), ("p", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -81,12 +83,15 @@ def generate(kind: str, *, n: int, id_bits: int, seed: int, sample_base: int = 0
              n_anc: int = 8, anc_size: int = 50_000, u_max: float = 0.6,
              n_clades: int = 32, core: float = 0.3, median: float = 1e6,
              sigma: float | None = None, lo: float | None = None, hi: float | None = None,
-             alloc=None):
+             m: int = 0, p: float = 0.0, alloc=None):
     """Draw one collection.  ``alloc(count) -> uint64 ndarray`` may supply the
     value buffer (for example pinned host memory); it must hold ``count``
     entries and the result is a prefix view of it."""
+    prob = p
     p = _Params()
-    p.kind = 0 if kind == "ancestral" else 1
+    p.kind = {"ancestral": 0, "clade": 1, "bernoulli": 2}[kind]
+    p.m = m
+    p.p = prob
     p.id_bits = id_bits
     p.seed = seed
     p.n = n
@@ -176,6 +181,20 @@ def serving_queries(first: int, count: int, seed: int = SEED_BASE + 5, n_ref: in
     return generate("clade", n=count, id_bits=32, seed=seed, sample_base=n_ref + first, n_clades=64,
                     core=0.3, u_max=0.4, median=median, sigma=SIGMA_DECADE,
                     lo=median / 10, hi=median * 10)
+
+
+def bernoulli(n: int, m: int, p: float, seed: int = SEED_BASE + 6, alloc=None):
+    """n samples over [0, m): every value is in every sample independently
+    with probability p (the paper's synthetic indicator matrices, Sec. V-A:
+    density p)."""
+    bits = max(1, int(m - 1).bit_length())
+    return generate("bernoulli", n=n, id_bits=bits, seed=seed, m=m, p=p, alloc=alloc)
+
+
+def bernoulli10k(seed: int = SEED_BASE + 6, alloc=None):
+    """The paper's synthetic strong-scaling matrix: m = 32M (2^25) rows,
+    n = 10,000 samples, density p = 0.01 (about 3.4e9 values)."""
+    return bernoulli(10_000, 1 << 25, 0.01, seed=seed, alloc=alloc)
 
 
 def range_distinct(ids, range_bits: int, nranges: int):

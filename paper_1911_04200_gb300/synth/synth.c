@@ -26,6 +26,12 @@
  *    truncated to [lo, hi] by resampling.  Values are hash >> (64 - id_bits).
  *    Then sort + dedupe.  `sample_base` offsets the sample index so that query
  *    sets can be drawn from the same clades as a reference collection.
+ *
+ *  BERNOULLI (kind 2): every value t of [0, m) is in sample i independently
+ *    with probability p (the synthetic indicator matrices of the paper's
+ *    evaluation, Sec. V-A).  Drawn as geometric gaps: the next member after
+ *    t is t + 1 + floor(log(U) / log(1 - p)), U uniform in (0, 1].  Sorted and
+ *    distinct by construction.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -56,7 +62,7 @@ static inline uint64_t to_domain(uint64_t h, int id_bits)
 }
 
 enum { T_ANC = 1, T_U = 2, T_PERM = 3, T_NEW = 4, T_ROOT = 5, T_CORE = 6, T_CLADE = 7,
-       T_SUB = 8, T_FRESH = 9, T_SIZE = 10 };
+       T_SUB = 8, T_FRESH = 9, T_SIZE = 10, T_BERN = 11 };
 
 /* exp(x) for |x| <= 40 from +,*,/ only: x = k*ln2/64 ... computed as
  * (1 + y + y^2/2 + ... ) ^ (2^s) with y = x / 2^s, |y| < 2^-10, 12 terms.
@@ -70,6 +76,18 @@ static double det_exp(double x)
     for (int k = 1; k <= 12; ++k) { term = term * y / (double)k; sum += term; }
     for (int k = 0; k < s; ++k) sum = sum * sum;
     return sum;
+}
+
+/* log(x) for x in (0, 1] from +,*,/ only: x = f * 2^-e with f in [0.5, 1),
+ * log f = 2 atanh(z), z = (f - 1) / (f + 1) in [-1/3, 0), summed to z^41
+ * (error below 3^-41).  Deterministic; a gap draw needs no more. */
+static double det_log01(double x)
+{
+    int e = 0;
+    while (x < 0.5) { x *= 2.0; ++e; }
+    double z = (x - 1.0) / (x + 1.0), z2 = z * z, term = z, sum = 0.0;
+    for (int k = 1; k <= 41; k += 2) { sum += term / (double)k; term *= z2; }
+    return 2.0 * sum - (double)e * 0.6931471805599453;
 }
 
 /* standard normal deviate, Irwin-Hall sum of 12 uniforms minus 6 */
@@ -92,11 +110,22 @@ typedef struct {
     uint64_t n_clades;
     double core, u_max;
     double median, sigma, lo, hi;
+    /* bernoulli */
+    uint64_t m;
+    double p;
 } synth_params;
 
 static uint64_t sample_len(const synth_params* p, uint64_t i)
 {
     if (p->kind == 0) return p->anc_size;
+    if (p->kind == 2) {
+        /* slot: mean + 12 standard deviations + 64 of Binomial(m, p); the
+           draw stops at the slot's end (never reached in practice) */
+        double mu = (double)p->m * p->p, var = mu * (1.0 - p->p), sd = 1.0;
+        for (int k = 0; k < 60; ++k) sd = 0.5 * (sd + var / sd);  /* sqrt by Newton */
+        double L = mu + 12.0 * sd + 64.0;
+        return L > (double)p->m ? p->m : (uint64_t)L;
+    }
     uint64_t gi = i + p->sample_base;
     double lm = p->median;
     for (uint64_t attempt = 0; attempt < 1000; ++attempt) {
@@ -202,6 +231,25 @@ void synth_fill(const synth_params* p, const uint64_t* slot, uint64_t* ids, uint
                 cap = L;
                 tmp = (uint64_t*)malloc(sizeof(uint64_t) * cap);
                 perm = (uint64_t*)malloc(sizeof(uint64_t) * cap);
+            }
+            if (p->kind == 2) {
+                uint64_t k = 0;
+                if (p->p >= 1.0) {
+                    for (; k < L; ++k) v[k] = k;
+                } else if (p->p > 0.0) {
+                    const double lq = det_log01(1.0 - p->p);
+                    uint64_t t = 0;
+                    for (uint64_t d = 0; k < L; ++d) {
+                        const double u = 1.0 - U01(H3(p->seed, T_BERN, i + p->sample_base, d));
+                        const double g = det_log01(u) / lq;
+                        if (g >= (double)(p->m - t)) break;
+                        t += (uint64_t)g;
+                        if (t >= p->m) break;
+                        v[k++] = t++;
+                    }
+                }
+                distinct[i] = k;
+                continue;
             }
             if (p->kind == 0) {
                 const uint64_t* A = anc + (i % p->n_anc) * p->anc_size;

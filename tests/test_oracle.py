@@ -272,3 +272,67 @@ def test_pins_catch_planted_mistakes():
     segs = [ids[int(offsets[i]):int(offsets[i + 1])] for i in range(6)]
     off_by_one = np.array([[np.intersect1d(a[1:], b).size for b in segs] for a in segs])
     assert not np.array_equal(off_by_one, ref_C)
+
+
+def test_bernoulli_recipe_statistics():
+    """Statistical sanity of the synthetic Bernoulli(p) matrices (Sec. V-A):
+    sizes average m p, pairwise intersections m p^2, and J about p / (2 - p);
+    the draw is sorted, distinct, inside [0, m) and repeatable."""
+    from paper_1911_04200_gb300 import synth
+    n, m, p = 48, 1 << 16, 0.05
+    off, ids = synth.bernoulli(n, m, p)
+    off2, ids2 = synth.bernoulli(n, m, p)
+    np.testing.assert_array_equal(off, off2)
+    np.testing.assert_array_equal(ids, ids2)
+    for i in range(n):
+        a = ids[int(off[i]):int(off[i + 1])].astype(np.int64)
+        assert np.all(np.diff(a) > 0) and a[0] >= 0 and a[-1] < m
+    C, s, J = oracle.all_pairs(off, ids)
+    sd_size = np.sqrt(m * p * (1 - p))
+    assert abs(s.astype(np.float64).mean() - m * p) < 4 * sd_size / np.sqrt(n)
+    iu = np.triu_indices(n, 1)
+    c = C[iu].astype(np.float64)
+    # pairs share samples, so allow a wide band: 8 standard errors of independent pairs
+    assert abs(c.mean() - m * p * p) < 8 * np.sqrt(m * p * p) / np.sqrt(c.size)
+    assert abs(J[iu].mean() - p / (2 - p)) < 0.002
+    # the extremes: p = 1 gives every value, p = 0 none
+    o1, i1 = synth.bernoulli(3, 1000, 1.0)
+    np.testing.assert_array_equal(i1, np.tile(np.arange(1000, dtype=np.uint64), 3))
+    o0, i0 = synth.bernoulli(3, 1000, 0.0)
+    assert int(o0[-1]) == 0
+
+
+def test_distance_is_correctly_rounded_one_minus_J():
+    """D = 1 - J (Sec. II-A) as one binary64 quotient: D is the double nearest
+    the exact rational (U - C) / U (checked with fractions against both
+    neighbours), D(empty, empty) = 0, D(X, X) = 0, D of disjoint sets = 1, and
+    the distance obeys the triangle inequality on random small sets."""
+    rng = np.random.default_rng(31)
+    for _ in range(400):
+        sx, sy = (int(v) for v in rng.integers(0, 10**6, 2))
+        b = int(rng.integers(0, min(sx, sy) + 1))
+        d = oracle.distance(b, sx, sy)
+        u = sx + sy - b
+        if u == 0:
+            assert d == 0.0
+            continue
+        exact = Fraction(u - b, u)
+        err = abs(Fraction(d) - exact)
+        for nb in (np.nextafter(d, -1.0), np.nextafter(d, 2.0)):
+            assert err <= abs(Fraction(float(nb)) - exact)
+    assert oracle.distance(0, 0, 0) == 0.0
+    assert oracle.distance(7, 7, 7) == 0.0
+    assert oracle.distance(0, 3, 5) == 1.0
+    # metric: d(a, c) <= d(a, b) + d(b, c) (up to one rounding each)
+    sets = [set(rng.integers(0, 40, int(rng.integers(0, 30))).tolist()) for _ in range(12)]
+
+    def dist(p, q):
+        return oracle.distance(len(p & q), len(p), len(q))
+    for p in sets:
+        for q in sets:
+            for r in sets:
+                assert dist(p, r) <= dist(p, q) + dist(q, r) + 1e-15
+    # the matrix form matches the scalar one
+    C = np.array([[3, 1], [0, 2]], dtype=np.uint64)
+    D = oracle.distance_matrix(C, np.array([3, 4], np.uint64), np.array([5, 2], np.uint64))
+    assert D[0, 0] == oracle.distance(3, 3, 5) and D[1, 1] == oracle.distance(2, 4, 2)
