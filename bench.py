@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jsim", choices=["jsim", "reference"])
     ap.add_argument("--workload", default="clade1024",
-                    choices=["clade1024", "ancestral64", "batched200", "stream4096", "serve2048"])
+                    choices=["clade1024", "ancestral64", "batched200", "stream4096", "serve2048",
+                             "bernoulli10k", "density"])
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--batch-rows", type=int, default=0)
     ap.add_argument("--filter-min", type=int, default=1, choices=[1, 2],
@@ -93,6 +94,11 @@ def make_workload(name, rank, alloc=None):
         off, ids = synth.ancestral64(seed=synth.SEED_BASE + 1 + 1000 * rank, alloc=alloc)
         cfg = {"workload": "ancestral64: n=64, values in [0,2^20), 8 ancestors x 50k, 0-60% replaced",
                "n": 64, "id_bits": 20}
+    elif name == "bernoulli10k":
+        off, ids = synth.bernoulli10k(seed=synth.SEED_BASE + 6 + 1000 * rank, alloc=alloc)
+        cfg = {"workload": "bernoulli10k: n=10,000 samples, m=2^25 rows, every entry present with p=0.01 "
+                           "(the paper's synthetic strong-scaling matrix)",
+               "n": 10_000, "id_bits": 25}
     else:
         off, ids = synth.clade1024(seed=synth.SEED_BASE + 2 + 1000 * rank, alloc=alloc)
         cfg = {"workload": "clade1024: n=1024, values in [0,2^32), log-normal sizes median 1e6 "
@@ -639,6 +645,67 @@ def run_jsim(args):
     return 0
 
 
+def run_density(args):
+    """Density sweep (the paper's synthetic matrices, Sec. V-A): n=1024
+    samples over m=2^25 rows, entries present with probability p; every
+    product variant with both filters, one all-pairs call per step, inputs
+    resident.  The curve behind the automatic variant choice."""
+    import torch
+    from paper_1911_04200_gb300 import jsim, synth
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, m = 1024, 1 << 25
+    C = torch.empty((n, n), dtype=torch.uint32, device=dev)
+    S = torch.empty(n, dtype=torch.uint64, device=dev)
+    J = torch.empty((n, n), dtype=torch.float64, device=dev)
+    rows, best = [], None
+    with Clocks(local) as clk:
+        for p in (1e-4, 1e-3, 1e-2, 5e-2):
+            off, ids = synth.bernoulli(n, m, p)
+            d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+            d_ids = torch.from_numpy(ids.view(np.int64)).to(dev)
+            ref = None
+            for fm in (1, 2):
+                for variant in ("popc", "tc", "tc2", "auto"):
+                    ctx = jsim.Context(device=local, variant=variant, id_bits=25, profile=True, filter_min=fm)
+                    for _ in range(max(1, args.warmup)):
+                        ctx.all_pairs(d_off, d_ids, out=(C, S, J))
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(ctx.stream)
+                    for _ in range(args.steps):
+                        ctx.all_pairs(d_off, d_ids, out=(C, S, J))
+                    e1.record(ctx.stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / args.steps
+                    st = ctx.stats()
+                    ctx.close()
+                    # every variant and filter gives the same J
+                    h = J[::97, ::89].cpu().numpy().view(np.uint64)
+                    if ref is None:
+                        ref = h
+                    assert np.array_equal(h, ref)
+                    row = {"p": p, "values": int(off[-1]), "filter_min": fm, "variant": st["variant"],
+                           "words": st["words"], "ms": round(ms, 3), "ms_product": round(st["ms_product"], 3),
+                           "tbitops": round(st["bitops_dense"] / (ms * 1e-3) / 1e12, 1)}
+                    rows.append(row)
+                    if variant == "auto" and fm == 1 and p == 1e-2:
+                        best = row
+            del d_off, d_ids
+    line = {"metric": METRIC, "value": best["tbitops"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
+            "config": {"workload": "density: n=1024, m=2^25 rows, Bernoulli(p) entries, p in 1e-4..5e-2; "
+                                   "value = automatic variant at p=0.01",
+                       "sweep": rows, "l2": "inputs larger than L2 at p >= 1e-3; no flush"},
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -649,6 +716,8 @@ def main():
         return run_streamed(args)
     if args.workload == "serve2048":
         return run_serve(args)
+    if args.workload == "density":
+        return run_density(args)
     return run_jsim(args)
 
 

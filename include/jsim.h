@@ -119,6 +119,11 @@ typedef struct {
                              more samples - a row only sample i holds adds 1 to C_ii alone,
                              and C_ii = |X_i| is known, so C and J are unchanged while the
                              product runs over fewer words.  Serving ignores it. */
+    int distance;         /* 0 (default): the J output holds the similarity J = C / U (Eq. 2);
+                             1: it holds the Jaccard distance D = 1 - J (Sec. II-A), computed
+                             as the correctly rounded quotient (U - C) / U, D = 0 for two
+                             empty sets.  Applies to every call that writes J (plain,
+                             streamed, batched, serving indexes built on the context). */
 } jsim_options;
 
 typedef struct jsim_ctx jsim_ctx;
@@ -367,6 +372,23 @@ JSIM_API void jsim_request_free(jsim_request* r);
  */
 JSIM_API int jsim_topk(jsim_ctx* ctx, const double* J, uint64_t n, uint32_t k, uint64_t* idx, double* val,
                        int mem);
+
+/*
+ * Threshold output: the pairs i < j with J[i][j] >= tau (below = 0), or with
+ * J[i][j] <= tau (below = 1, for a distance matrix), in row-major order (i,
+ * then j).  The sparse form of the all-pairs matrix (Sec. II-A) for
+ * collections too large to keep n x n.
+ *   J      n*n row-major binary64 as jsim_all_pairs writes it
+ *   tau    threshold (not NaN)
+ *   cap    capacity of pi, pj and val in pairs (0: count only)
+ *   pi,pj  uint64 indices of the first min(count, cap) pairs (NULL when cap is 0)
+ *   val    their J, or NULL
+ *   count  total number of pairs that pass (also when above cap)
+ *   mem    JSIM_MEM_HOST or JSIM_MEM_DEVICE for J, pi, pj and val (count: host)
+ * Errors: JSIM_ERR_ARG, JSIM_ERR_OOM, JSIM_ERR_CUDA.
+ */
+JSIM_API int jsim_threshold(jsim_ctx* ctx, const double* J, uint64_t n, double tau, int below, uint64_t cap,
+                            uint64_t* pi, uint64_t* pj, double* val, uint64_t* count, int mem);
 
 /* Statistics of the last call on the context. */
 JSIM_API int jsim_get_stats(const jsim_ctx* ctx, jsim_stats* out);

@@ -69,7 +69,7 @@ int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 widt
     if (next) *next = ctx->h_scalars[1];
     if (has_next) *has_next = ctx->h_scalars[2] != 0;
     const u64 W = (R + 63) / 64;
-    stride = round_up(std::max<u64>(W, 1), kWordPad);
+    stride = row_stride_words(W);
     const u64 n_pad = round_up(std::max<u64>(n, 1), kRowPad);
     const u64 need = n_pad * stride * sizeof(u64);
     ALLOC(bb.X, need);
@@ -108,6 +108,7 @@ void jsim_default_options(jsim_options* opt)
     opt->device = 0;
     opt->timeout_ms = 2000;
     opt->filter_min = 1;
+    opt->distance = 0;
 }
 
 int jsim_create(jsim_ctx** out, const jsim_options* opt)
@@ -122,6 +123,7 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
     if (o.variant < 0 || o.variant >= JSIM_VARIANT_COUNT) return JSIM_ERR_ARG;
     if (o.batch_rows % 64 != 0) return JSIM_ERR_ARG;
     if (o.filter_min != 1 && o.filter_min != 2) return JSIM_ERR_ARG;
+    if (o.distance != 0 && o.distance != 1) return JSIM_ERR_ARG;
     if ((o.alloc == nullptr) != (o.free == nullptr)) return JSIM_ERR_ARG;
     if (!o.alloc) { o.alloc = default_alloc; o.free = default_free; }
     jsim_ctx* c = new jsim_ctx();
@@ -243,7 +245,7 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
         StageTimer t(ctx, &ctx->stats.ms_epilogue);
         if (Cdst || Jdst) {
             CK(launch_epilogue(Cacc.p, n, ctx->opt.count_bits, st.sizes.as<u64>(), Cdst, Jdst, ctx->stream,
-                               ctx->opt.filter_min == 2));
+                               ctx->opt.filter_min == 2, ctx->opt.distance));
             ctx->stats.launches += 1;
         }
     }

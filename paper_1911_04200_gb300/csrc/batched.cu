@@ -176,7 +176,7 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
         js += cl.n * cl.n * sizeof(double);
         if (cl.n == 0 || (!Cd && !Jd)) continue;
         CK(launch_epilogue((char*)w.cpool.p + cl.c_off, cl.n, ctx->opt.count_bits, w.spool.as<u64>() + cl.s_off, Cd,
-                           Jd, ctx->lanes[c % kLanes], ctx->opt.filter_min == 2));
+                           Jd, ctx->lanes[c % kLanes], ctx->opt.filter_min == 2, ctx->opt.distance));
         ctx->stats.launches += 1;
     }
     return lanes_join(ctx, kLanes);

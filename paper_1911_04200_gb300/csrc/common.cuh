@@ -18,6 +18,21 @@ constexpr u64 kRowPad = 128;
 // Word granularity of a packed row (K padding of every product variant).
 constexpr u64 kWordPad = 64;
 
+// Row stride of a packed matrix of W words per row: a multiple of kWordPad
+// holding W, made an odd number of granules (1024 words for rows of 2^16
+// words or more, kWordPad below) so that rows do not all start on the same
+// DRAM channel.  Measured on the SM-pair product: rows of 2^19 words (4 MiB
+// apart) ran at 935 Tbit-ops/s, 1074 with the stride one 8 KiB granule
+// longer; 2^18-word rows 974 -> 1043.
+inline u64 row_stride_words(u64 W)
+{
+    const u64 w = W ? W : 1;
+    const u64 g = w > (1ull << 16) - kWordPad ? 1024 : kWordPad;
+    u64 k = (w + g - 1) / g;
+    if (k % 2 == 0) ++k;
+    return k * g;
+}
+
 // Error flags raised by device kernels.
 constexpr u32 kFlagUnsorted = 1u;
 constexpr u32 kFlagIdRange = 2u;
@@ -125,14 +140,16 @@ cudaError_t launch_rank_words(const QueryIndex& ix, ulonglong2* fr, int sms, cud
 // their total (host copy).
 cudaError_t launch_qrows(const u64* ids, u64 S, Plan plan, u64 values, const QueryIndex& ix, u32* Cacc,
                          u64* rows_read, int sms, cudaStream_t st);
+// distance: J holds D = (U - C) / U instead (0 for two empty sets)
 cudaError_t launch_qepi(const u32* Cacc, u64 S, u64 n_ref, const u64* sq, const u64* sr, int count_bits, void* Cout,
-                        double* J, int sms, cudaStream_t st);
+                        double* J, int sms, cudaStream_t st, int distance = 0);
 
 // ---- epilogue.cu ---------------------------------------------------------------
 // Cout[i][j] = Cacc[min(i,j)][max(i,j)], J = C / (s_i + s_j - C) (binary64), 1 if 0.
 // diag_sizes: C_ii = s_i (the product ran over rows held by two or more
 // samples, so its diagonal lacks the rows only sample i holds).
+// distance: J holds D = (U - C) / U instead (0 for two empty sets).
 cudaError_t launch_epilogue(const void* Cacc, u64 n, int count_bits, const u64* sizes,
-                            void* Cout, double* J, cudaStream_t st, int diag_sizes = 0);
+                            void* Cout, double* J, cudaStream_t st, int diag_sizes = 0, int distance = 0);
 
 }  // namespace jsim

@@ -1,6 +1,8 @@
 // Epilogue: mirror the upper-triangle counts into a full C and form
 // J = C / (|X_i| + |X_j| - C) (Sec. III-A: union by inclusion-exclusion,
-// Eq. 2: s_ij = b_ij / c_ij), with J = 1 for two empty sets (Sec. II-A).
+// Eq. 2: s_ij = b_ij / c_ij), with J = 1 for two empty sets (Sec. II-A);
+// or, with `distance`, the Jaccard distance D = 1 - J (Sec. II-A) as the
+// correctly rounded quotient (U - C) / U, D = 0 for two empty sets.
 //
 // The quotient is one IEEE binary64 division, round-to-nearest (__ddiv_rn),
 // of two integers below 2^53 converted exactly, so it is correctly rounded
@@ -18,7 +20,7 @@ constexpr int kE = 32;
 template <typename CT>
 __global__ void __launch_bounds__(kE * 8)
 k_epilogue(const CT* __restrict__ Cacc, u64 n, const u64* __restrict__ sizes,
-           CT* __restrict__ Cout, double* __restrict__ J, int diag_sizes)
+           CT* __restrict__ Cout, double* __restrict__ J, int diag_sizes, int distance)
 {
     __shared__ CT tile[kE][kE + 1];
     const u64 bi = blockIdx.y, bj = blockIdx.x;
@@ -47,8 +49,9 @@ k_epilogue(const CT* __restrict__ Cacc, u64 n, const u64* __restrict__ sizes,
         if (diag_sizes && i == j) c = (CT)sizes[i];
         if (Cout) Cout[i * n + j] = c;
         if (J) {
-            u64 u = sizes[i] + sizes[j] - (u64)c;
-            J[i * n + j] = u ? __ddiv_rn(__ull2double_rn((u64)c), __ull2double_rn(u)) : 1.0;
+            const u64 u = sizes[i] + sizes[j] - (u64)c;
+            const u64 num = distance ? u - (u64)c : (u64)c;
+            J[i * n + j] = u ? __ddiv_rn(__ull2double_rn(num), __ull2double_rn(u)) : (distance ? 0.0 : 1.0);
         }
     }
 }
@@ -56,16 +59,16 @@ k_epilogue(const CT* __restrict__ Cacc, u64 n, const u64* __restrict__ sizes,
 }  // namespace
 
 cudaError_t launch_epilogue(const void* Cacc, u64 n, int count_bits, const u64* sizes,
-                            void* Cout, double* J, cudaStream_t st, int diag_sizes)
+                            void* Cout, double* J, cudaStream_t st, int diag_sizes, int distance)
 {
     if (n == 0) return cudaSuccess;
     u64 nb = (n + kE - 1) / kE;
     if (nb > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)nb, (unsigned)nb), block(kE, 8);
     if (count_bits == 64)
-        k_epilogue<u64><<<grid, block, 0, st>>>((const u64*)Cacc, n, sizes, (u64*)Cout, J, diag_sizes);
+        k_epilogue<u64><<<grid, block, 0, st>>>((const u64*)Cacc, n, sizes, (u64*)Cout, J, diag_sizes, distance);
     else
-        k_epilogue<u32><<<grid, block, 0, st>>>((const u32*)Cacc, n, sizes, (u32*)Cout, J, diag_sizes);
+        k_epilogue<u32><<<grid, block, 0, st>>>((const u32*)Cacc, n, sizes, (u32*)Cout, J, diag_sizes, distance);
     return cudaGetLastError();
 }
 

@@ -60,6 +60,14 @@ namespace {
 #ifndef JSIM_TC2_AHEAD
 #define JSIM_TC2_AHEAD 4
 #endif
+// L2 window shared by all clusters (MiB of packed words of all rows).  A
+// longer window means fewer accumulator flushes per tile; measured with
+// padded row strides (Tbit-ops/s, 48 / 96 / 128 MiB): n=1024 1060 / 1024 /
+// 1064, n=2048 1156 / 1146 / 1181, n=4096 1175 / 1247 / 1210, n=10000
+// 1077 / 1132 / 1172.
+#ifndef JSIM_TC2_WINDOW_MIB
+#define JSIM_TC2_WINDOW_MIB 128
+#endif
 #ifndef JSIM_TC2_KBITS
 #define JSIM_TC2_KBITS 256
 #endif
@@ -556,7 +564,7 @@ cudaError_t run(ProductArgs& a, cudaStream_t st)
     const u64 nst = (a.W + kStageWords - 1) / kStageWords;
     const u64 total = tiles * nst;
     if (total == 0) return cudaSuccess;
-    u64 L = (48ull << 20) / ((u64)kStageWords * 8ull * std::max<u64>(a.n, 1));
+    u64 L = ((u64)JSIM_TC2_WINDOW_MIB << 20) / ((u64)kStageWords * 8ull * std::max<u64>(a.n, 1));
     L = std::max<u64>(64, std::min<u64>(L, kMaxSegStages));
     cudaError_t e = cudaFuncSetAttribute(k_prod_tc2<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;

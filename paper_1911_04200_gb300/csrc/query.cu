@@ -25,7 +25,8 @@
 //                column counts) through a carry-save adder tree; at the end
 //                of a sample (or 4096 values) the counts go into C with
 //                atomic adds;
-//   k_qepi       J = C / (|Q_s| + |S_j| - C) in binary64 (Sec. II-A).
+//   k_qepi       J = C / (|Q_s| + |S_j| - C) in binary64 (Sec. II-A), or
+//                the distance (U - C) / U.
 #include <algorithm>
 #include "ingest_dev.cuh"
 
@@ -286,7 +287,7 @@ k_qrows(const u64* __restrict__ ids, u64 S, Plan plan, u64 lo, u64 width, const 
 
 template <typename CT>
 __global__ void k_qepi(const u32* __restrict__ Cacc, u64 S, u64 n_ref, const u64* __restrict__ sq,
-                       const u64* __restrict__ sr, CT* Cout, double* J)
+                       const u64* __restrict__ sr, CT* Cout, double* J, int distance)
 {
     const u64 total = S * n_ref;
     for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (u64)gridDim.x * blockDim.x) {
@@ -294,7 +295,10 @@ __global__ void k_qepi(const u32* __restrict__ Cacc, u64 S, u64 n_ref, const u64
         const u64 c = Cacc[e];
         const u64 u = sq[s] + sr[j] - c;
         if (Cout) Cout[e] = (CT)c;
-        if (J) J[e] = u ? __ddiv_rn(__ull2double_rn(c), __ull2double_rn(u)) : 1.0;
+        if (J) {
+            const u64 num = distance ? u - c : c;
+            J[e] = u ? __ddiv_rn(__ull2double_rn(num), __ull2double_rn(u)) : (distance ? 0.0 : 1.0);
+        }
     }
 }
 
@@ -361,13 +365,13 @@ cudaError_t launch_qrows(const u64* ids, u64 S, Plan plan, u64 values, const Que
 }
 
 cudaError_t launch_qepi(const u32* Cacc, u64 S, u64 n_ref, const u64* sq, const u64* sr, int count_bits, void* Cout,
-                        double* J, int sms, cudaStream_t st)
+                        double* J, int sms, cudaStream_t st, int distance)
 {
     const unsigned g = grid_flat(S * n_ref, sms, 256);
     if (count_bits == 64)
-        k_qepi<u64><<<g, 256, 0, st>>>(Cacc, S, n_ref, sq, sr, (u64*)Cout, J);
+        k_qepi<u64><<<g, 256, 0, st>>>(Cacc, S, n_ref, sq, sr, (u64*)Cout, J, distance);
     else
-        k_qepi<u32><<<g, 256, 0, st>>>(Cacc, S, n_ref, sq, sr, (u32*)Cout, J);
+        k_qepi<u32><<<g, 256, 0, st>>>(Cacc, S, n_ref, sq, sr, (u32*)Cout, J, distance);
     return cudaGetLastError();
 }
 

@@ -80,7 +80,7 @@ struct jsim_index {
     std::unordered_set<jsim_request*> live;  // requests not yet freed
     bool stop = false;
     jsim_serve_stats stats{};
-    int device = 0, sms = 0, count_bits = 32;
+    int device = 0, sms = 0, count_bits = 32, distance = 0;
 };
 
 namespace {
@@ -183,7 +183,7 @@ int launch_batch(jsim_index* ix, Slot& sl)
     CK(launch_qrows(d_ids, S, plan, V, qi, sl.Cacc.as<u32>(), sl.Ud.as<u64>(), ix->sms, st));
     CK(cudaEventRecord(sl.evp1, st));
     CK(launch_qepi(sl.Cacc.as<u32>(), S, ix->n_ref, sl.sq.as<u64>(), ix->sizes_ref.as<u64>(), ix->count_bits,
-                   sl.Cout.p, sl.Jd.as<double>(), ix->sms, st));
+                   sl.Cout.p, sl.Jd.as<double>(), ix->sms, st, ix->distance));
     unsigned char* po = sl.pin_out;
     CK(cudaMemcpyAsync(po + ol.c, sl.Cout.p, S * ix->n_ref * cb, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(po + ol.j, sl.Jd.p, S * ix->n_ref * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -373,6 +373,7 @@ int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_serve_optio
     ix->device = ctx->opt.device;
     ix->sms = ctx->sms;
     ix->count_bits = ctx->opt.count_bits;
+    ix->distance = ctx->opt.distance;
     const u64 n = ref->n;
     ix->n_ref = n;
     ix->ns64 = (n + 63) / 64;

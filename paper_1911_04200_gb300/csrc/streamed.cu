@@ -356,7 +356,7 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
         const u64 R = ctx->h_scalars[0], W = (R + 63) / 64;
         ctx->stats.rows_nonzero += R;
         ctx->stats.batches += R != 0;
-        const u64 stride = round_up(W, kWordPad);
+        const u64 stride = row_stride_words(W);
         if (W) {
             ALLOC(X, n_pad * stride * sizeof(u64));
             StageTimer t(ctx, &ctx->stats.ms_pack);
@@ -401,7 +401,8 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
     {
         StageTimer t(ctx, &ctx->stats.ms_epilogue);
         if (Cdst || Jdst) {
-            CK(launch_epilogue(Cacc.p, n, ctx->opt.count_bits, sizes_d.as<u64>(), Cdst, Jdst, cs, twice));
+            CK(launch_epilogue(Cacc.p, n, ctx->opt.count_bits, sizes_d.as<u64>(), Cdst, Jdst, cs, twice,
+                               ctx->opt.distance));
             ctx->stats.launches += 1;
         }
     }

@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
                 ("count_bits", ctypes.c_int), ("id_bits", ctypes.c_int), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("timeout_ms", ctypes.c_int), ("profile", ctypes.c_int),
-                ("filter_min", ctypes.c_int)]
+                ("filter_min", ctypes.c_int), ("distance", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -112,6 +112,9 @@ SIGNATURES = {
     "jsim_request_free": (None, [ctypes.c_void_p]),
     "jsim_topk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_int]),
+    "jsim_threshold": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _u64p,
+                                      ctypes.c_int]),
     "jsim_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "jsim_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "jsim_last_cuda_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -166,7 +169,8 @@ class Context:
 
     def __init__(self, device: int = 0, variant: str | int = "auto", batch_rows: int = 0, word_bits: int = 64,
                  count_bits: int = 32, id_bits: int = 64, profile: bool = False, stream=None,
-                 use_torch_allocator: bool = True, timeout_ms: int = 2000, filter_min: int = 1):
+                 use_torch_allocator: bool = True, timeout_ms: int = 2000, filter_min: int = 1,
+                 distance: bool = False):
         torch = _torch()
         self._lib = load()
         self.device = device
@@ -184,6 +188,7 @@ class Context:
         o.profile = 1 if profile else 0
         o.timeout_ms = timeout_ms
         o.filter_min = filter_min
+        o.distance = 1 if distance else 0
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         self._keep = []
         if use_torch_allocator:
@@ -384,6 +389,37 @@ class Context:
         _check(self._lib.jsim_topk(self._h, self._ptr(J), n, k, self._ptr(idx), self._ptr(val),
                                    MEM_DEVICE if is_dev else MEM_HOST), self._h)
         return idx, val
+
+    def threshold(self, J, tau: float, below: bool = False, cap: int | None = None, want_val: bool = True):
+        """Pairs i < j with J >= tau (below: J <= tau, for distances), row-major:
+        (pi uint64, pj uint64, val binary64 or None, count).  cap (default: every
+        pair that passes, found by a counting call first) bounds the pairs
+        written; count is the total that pass."""
+        torch = _torch()
+        is_dev = isinstance(J, torch.Tensor) and J.is_cuda
+        n = J.shape[0]
+        if not is_dev:
+            J = np.ascontiguousarray(J, dtype=np.float64)
+        mem = MEM_DEVICE if is_dev else MEM_HOST
+        cnt = ctypes.c_uint64(0)
+        self._order()
+        if cap is None:
+            _check(self._lib.jsim_threshold(self._h, self._ptr(J), n, float(tau), int(bool(below)), 0, None, None,
+                                            None, ctypes.byref(cnt), mem), self._h)
+            cap = cnt.value
+        if is_dev:
+            pi = torch.empty(cap, dtype=torch.uint64, device=J.device)
+            pj = torch.empty(cap, dtype=torch.uint64, device=J.device)
+            val = torch.empty(cap, dtype=torch.float64, device=J.device) if want_val else None
+        else:
+            pi = np.empty(cap, dtype=np.uint64)
+            pj = np.empty(cap, dtype=np.uint64)
+            val = np.empty(cap, dtype=np.float64) if want_val else None
+        _check(self._lib.jsim_threshold(self._h, self._ptr(J), n, float(tau), int(bool(below)), cap,
+                                        self._ptr(pi) if cap else None, self._ptr(pj) if cap else None,
+                                        self._ptr(val) if cap else None, ctypes.byref(cnt), mem), self._h)
+        w = min(cap, cnt.value)
+        return pi[:w], pj[:w], (val[:w] if val is not None else None), cnt.value
 
     def product(self, words, n: int, W: int, stride: int, C=None, variant: str | int = "auto"):
         """C = X X^T over (AND, popcount, +) of device-resident packed words."""

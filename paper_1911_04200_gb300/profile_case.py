@@ -42,6 +42,7 @@ def main():
     ap.add_argument("--words", type=int, default=32768)
     ap.add_argument("--density", type=float, default=0.25)
     ap.add_argument("--calls", type=int, default=3)
+    ap.add_argument("--pad", type=int, default=0, help="words of padding after every row (row stride)")
     a = ap.parse_args()
     if a.serve:
         return serve(a)
@@ -58,15 +59,20 @@ def main():
     else:
         w = torch.randint(-2**63, 2**63 - 1, (a.n, a.words), dtype=torch.int64, device="cuda", generator=g)
     del bits
+    stride = a.words + a.pad
+    if a.pad:
+        wp = torch.zeros((a.n, stride), dtype=torch.int64, device="cuda")
+        wp[:, :a.words] = w
+        w = wp
     ctx = jsim.Context(variant=a.variant, count_bits=32, profile=True)
     C = torch.empty((a.n, a.n), dtype=torch.uint32, device="cuda")
     for _ in range(a.calls):
-        ctx.product(w, a.n, a.words, a.words, C=C, variant=a.variant)
+        ctx.product(w, a.n, a.words, stride, C=C, variant=a.variant)
         st = ctx.stats()
     torch.cuda.synchronize()
     t = st["ms_product"]
-    print("variant=%s n=%d words=%d product %.3f ms -> %.1f Tbit-ops/s" % (
-        a.variant, a.n, a.words, t, st["bitops_dense"] / (t * 1e-3) / 1e12))
+    print("variant=%s n=%d words=%d stride=%d product %.3f ms -> %.1f Tbit-ops/s" % (
+        a.variant, a.n, a.words, stride, t, st["bitops_dense"] / (t * 1e-3) / 1e12))
 
 
 if __name__ == "__main__":

@@ -254,3 +254,22 @@ def test_pack_two_or_more_matches_packed_oracle(gpu, c1, lo, width):
     np.testing.assert_array_equal(fbits, ref["f"])
     np.testing.assert_array_equal(words[:, :ref["words"].shape[1]], ref["words"])
     np.testing.assert_array_equal(sz, ref["ahat"])
+
+
+@pytest.mark.parametrize("n,m,p", [(130, 1 << 20, 0.01), (64, 1 << 22, 1e-3), (200, 1 << 16, 0.3)])
+@pytest.mark.parametrize("variant", ["auto", "popc", "tc", "tc2"])
+def test_bernoulli_matrices(gpu, n, m, p, variant):
+    """The paper's synthetic indicator matrices (every entry present with
+    probability p) at three densities, with both filters; at low density the
+    two-or-more filter keeps far fewer rows."""
+    off, ids = synth.bernoulli(n, m, p)
+    ref = oracle.all_pairs(off, ids)
+    with jsim.Context(variant=variant, id_bits=max(20, (m - 1).bit_length())) as ctx:
+        assert_same(ctx.all_pairs(off, ids), ref)
+        w1 = ctx.stats()["words"]
+    with jsim.Context(variant=variant, filter_min=2, batch_rows=1 << 14) as ctx:
+        assert_same(ctx.all_pairs(off, ids), ref)
+    with jsim.Context(variant=variant, filter_min=2) as ctx:
+        assert_same(ctx.all_pairs(off, ids), ref)
+        w2 = ctx.stats()["words"]
+    assert w2 <= w1
