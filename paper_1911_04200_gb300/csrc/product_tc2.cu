@@ -60,13 +60,21 @@ namespace {
 #ifndef JSIM_TC2_AHEAD
 #define JSIM_TC2_AHEAD 4
 #endif
-// L2 window shared by all clusters (MiB of packed words of all rows).  A
-// longer window means fewer accumulator flushes per tile; measured with
-// padded row strides (Tbit-ops/s, 48 / 96 / 128 MiB): n=1024 1060 / 1024 /
-// 1064, n=2048 1156 / 1146 / 1181, n=4096 1175 / 1247 / 1210, n=10000
-// 1077 / 1132 / 1172.
+// L2 window shared by all clusters: JSIM_TC2_WINDOW_MIB of packed words of
+// all rows, but at least JSIM_TC2_MIN_STAGES stages per chunk.  Every tile
+// switch flushes an accumulator, so for many rows a window that fits L2 is
+// too short (157 stages at n = 10,000); for few rows a window beyond L2
+// re-reads the panels from DRAM (128 MiB at n = 1024: 2.1x the packed bytes).
+// Swept with padded strides (Tbit-ops/s; n = 1024 / 2048 / 4096 / 10,000):
+//   48 MiB, >= 512 stages   1063 / 1161 / 1182 / 1231
+//   48 MiB, >= 768 stages   1063 / 1157 / 1250 / 1257
+//   64 MiB, >= 512 stages   1065 / 1209 / 1180 / 1208
+//   48 MiB, no minimum      1060 / 1156 / 1175 / 1077
 #ifndef JSIM_TC2_WINDOW_MIB
-#define JSIM_TC2_WINDOW_MIB 128
+#define JSIM_TC2_WINDOW_MIB 64
+#endif
+#ifndef JSIM_TC2_MIN_STAGES
+#define JSIM_TC2_MIN_STAGES 768
 #endif
 #ifndef JSIM_TC2_KBITS
 #define JSIM_TC2_KBITS 256
@@ -565,7 +573,7 @@ cudaError_t run(ProductArgs& a, cudaStream_t st)
     const u64 total = tiles * nst;
     if (total == 0) return cudaSuccess;
     u64 L = ((u64)JSIM_TC2_WINDOW_MIB << 20) / ((u64)kStageWords * 8ull * std::max<u64>(a.n, 1));
-    L = std::max<u64>(64, std::min<u64>(L, kMaxSegStages));
+    L = std::max<u64>(JSIM_TC2_MIN_STAGES, std::min<u64>(L, kMaxSegStages));
     cudaError_t e = cudaFuncSetAttribute(k_prod_tc2<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     // as many clusters as can be resident at once (a GPC with an odd number
