@@ -65,6 +65,8 @@ extern "C" {
 #define JSIM_ERR_TIMEOUT      7  /* a bounded device wait ran out */
 #define JSIM_ERR_CANCELLED    8  /* a request was cancelled */
 #define JSIM_ERR_UNSUPPORTED  9  /* the requested variant or mode is not available */
+#define JSIM_ERR_INCOMPLETE  10  /* the call stopped early as asked; its checkpoint holds the progress */
+#define JSIM_ERR_CHECKPOINT  11  /* a checkpoint file is unreadable, corrupt or from another call */
 
 /* ---- memory kinds ---------------------------------------------------------- */
 #define JSIM_MEM_HOST   0
@@ -214,6 +216,34 @@ JSIM_API int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint64
  */
 JSIM_API int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes, double* J,
                                      int out_mem, uint64_t staging_bytes);
+
+/* Checkpoint/resume of a streamed call (progress is kept after whole
+ * super-batches: the counts C accumulated so far, the sizes, the input-error
+ * flags and the statistics). */
+typedef struct {
+    const char* path;     /* checkpoint file; written as path + ".tmp", then renamed */
+    uint32_t every;       /* write it after every `every` super-batches (0: only when stopping) */
+    uint32_t max_supers;  /* process at most this many super-batches in this call (0: all); if work
+                             remains, write the checkpoint and return JSIM_ERR_INCOMPLETE */
+    int resume;           /* 1: when `path` exists, continue after the super-batches it holds */
+} jsim_checkpoint;
+
+/*
+ * jsim_all_pairs_streamed with checkpoints (ck may be NULL: no checkpoint).
+ * A resumed call must be the same call: the same collection (checked by a
+ * fingerprint of the offsets, every sample's first and last value and 4096
+ * evenly spaced values), options and staging_bytes; otherwise, or when the
+ * file is corrupt (checksum), it returns JSIM_ERR_CHECKPOINT and writes
+ * nothing.  The file stays in place after a complete call.  The results of a
+ * call resumed any number of times are those of one uninterrupted call, bit
+ * for bit.  The file holds host-endian binary (header, sizes, C, checksum).
+ * Errors: as jsim_all_pairs_streamed, plus JSIM_ERR_INCOMPLETE (max_supers
+ * reached with work left) and JSIM_ERR_CHECKPOINT (file I/O, mismatch,
+ * corruption; max_supers without a path).
+ */
+JSIM_API int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes,
+                                          double* J, int out_mem, uint64_t staging_bytes,
+                                          const jsim_checkpoint* ck);
 
 /*
  * One row batch of the method, for inspection and step-level testing

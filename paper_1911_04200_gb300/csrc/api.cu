@@ -354,6 +354,8 @@ const char* jsim_strerror(int code)
     case JSIM_ERR_TIMEOUT: return "a bounded device wait timed out";
     case JSIM_ERR_CANCELLED: return "request cancelled";
     case JSIM_ERR_UNSUPPORTED: return "variant or mode not supported";
+    case JSIM_ERR_INCOMPLETE: return "stopped early as asked; the checkpoint holds the progress";
+    case JSIM_ERR_CHECKPOINT: return "checkpoint file unreadable, corrupt or from another call";
     default: return "unknown error";
     }
 }

@@ -22,6 +22,16 @@
 // and on the host across slices (every sample's slices must tile it).  Both
 // together imply that every sample is sorted, because a binary search that
 // cuts a sample at position q has seen a[q-1] < boundary <= a[q].
+//
+// Checkpoints: after whole super-batches the state of the call is C so far,
+// the sizes, the input-error flags and the statistics; a checkpoint file
+// holds them with a header that identifies the call, and a resumed call
+// starts at the first super-batch the file does not hold.  C is a sum over
+// super-batches (Eq. 4), so the order of additions, and with it every count,
+// is that of one uninterrupted call.
+#include <cstdio>
+#include <cstring>
+#include <string>
 #include <thread>
 #include "ctx.cuh"
 
@@ -191,6 +201,128 @@ void gather(const uint64_t* ids, const Super& s, u64* dst)
     for (auto& x : th) x.join();
 }
 
+// ---- checkpoint file --------------------------------------------------------
+
+// the splitmix64 finaliser (Steele, Lea and Flood, OOPSLA 2014) as a mixer
+inline u64 ck_mix(u64 z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct CkHash {
+    u64 h = 0x6A09E667F3BCC909ull;
+    void word(u64 w) { h = ck_mix(h ^ w); }
+    void bytes(const void* p, size_t len)
+    {
+        const unsigned char* b = (const unsigned char*)p;
+        size_t k = 0;
+        for (; k + 8 <= len; k += 8) {
+            u64 w;
+            memcpy(&w, b + k, 8);
+            word(w);
+        }
+        u64 t = 0;
+        if (k < len) {
+            memcpy(&t, b + k, len - k);
+            word(t ^ ((u64)(len - k) << 56));
+        }
+    }
+};
+
+// the collection's identity: offsets, every sample's first and last value
+// and 4096 evenly spaced values
+u64 ck_fingerprint(const std::vector<u64>& hoff, const uint64_t* ids, u64 n)
+{
+    CkHash h;
+    h.word(n);
+    const u64 N = hoff[n];
+    h.word(N);
+    for (u64 i = 0; i <= n; ++i) h.word(hoff[i]);
+    for (u64 i = 0; i < n; ++i)
+        if (hoff[i + 1] > hoff[i]) {
+            h.word(ids[hoff[i]]);
+            h.word(ids[hoff[i + 1] - 1]);
+        }
+    if (N)
+        for (u64 k = 0; k < 4096; ++k) h.word(ids[N * k / 4096]);
+    return h.h;
+}
+
+struct CkHeader {
+    char magic[8];
+    u64 version, n, N, mt, cap_vals, count_bits, filter_min, id_bits, distance, supers, fingerprint;
+    u64 done;  // super-batches whose counts C holds
+    u64 rows_nonzero, batches, words;
+    double bitops;
+    u64 flags[3];
+};
+constexpr char kCkMagic[8] = {'J', 'S', 'I', 'M', 'C', 'K', 'P', '1'};
+
+// same call: every identifying field equal
+bool ck_same_call(const CkHeader& a, const CkHeader& b)
+{
+    return memcmp(a.magic, b.magic, 8) == 0 && a.version == b.version && a.n == b.n && a.N == b.N &&
+           a.mt == b.mt && a.cap_vals == b.cap_vals && a.count_bits == b.count_bits &&
+           a.filter_min == b.filter_min && a.id_bits == b.id_bits && a.distance == b.distance &&
+           a.supers == b.supers && a.fingerprint == b.fingerprint;
+}
+
+// write header, sizes, C and a checksum to path.tmp, then rename it to path
+int ck_write(const char* path, const CkHeader& h, const std::vector<u64>& sizes, const std::vector<unsigned char>& C)
+{
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) return JSIM_ERR_CHECKPOINT;
+    CkHash sum;
+    sum.bytes(&h, sizeof h);
+    sum.bytes(sizes.data(), sizes.size() * sizeof(u64));
+    sum.bytes(C.data(), C.size());
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1;
+    ok = ok && (sizes.empty() || fwrite(sizes.data(), sizeof(u64), sizes.size(), f) == sizes.size());
+    ok = ok && (C.empty() || fwrite(C.data(), 1, C.size(), f) == C.size());
+    ok = ok && fwrite(&sum.h, sizeof(u64), 1, f) == 1;
+    ok = (fflush(f) == 0) && ok;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return JSIM_ERR_CHECKPOINT;
+    }
+    return JSIM_OK;
+}
+
+// read path into h, sizes and C if it exists (found = false otherwise);
+// JSIM_ERR_CHECKPOINT when it is short, corrupt or of another call
+int ck_read(const char* path, const CkHeader& want, CkHeader& h, std::vector<u64>& sizes,
+            std::vector<unsigned char>& C, bool& found)
+{
+    found = false;
+    FILE* f = fopen(path, "rb");
+    if (!f) return JSIM_OK;
+    found = true;
+    u64 stored = 0;
+    bool ok = fread(&h, sizeof h, 1, f) == 1 && ck_same_call(h, want) && h.done <= h.supers;
+    if (ok) {
+        sizes.resize(h.n);
+        C.resize(h.n * h.n * (h.count_bits == 64 ? 8 : 4));
+        ok = (sizes.empty() || fread(sizes.data(), sizeof(u64), sizes.size(), f) == sizes.size()) &&
+             (C.empty() || fread(C.data(), 1, C.size(), f) == C.size()) && fread(&stored, sizeof(u64), 1, f) == 1;
+    }
+    if (ok) {
+        char extra;
+        ok = fread(&extra, 1, 1, f) == 0;  // nothing after the checksum
+    }
+    fclose(f);
+    if (!ok) return JSIM_ERR_CHECKPOINT;
+    CkHash sum;
+    sum.bytes(&h, sizeof h);
+    sum.bytes(sizes.data(), sizes.size() * sizeof(u64));
+    sum.bytes(C.data(), C.size());
+    return sum.h == stored ? JSIM_OK : JSIM_ERR_CHECKPOINT;
+}
+
 // waits for the copy stream before device buffers that its copies may still
 // write are released (declared after them, so destroyed first)
 struct CopyFence {
@@ -206,7 +338,17 @@ struct CopyFence {
 extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes, double* J,
                                        int out_mem, uint64_t staging_bytes)
 {
+    return jsim_all_pairs_streamed_ckpt(ctx, sets, C, sizes, J, out_mem, staging_bytes, nullptr);
+}
+
+extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes,
+                                            double* J, int out_mem, uint64_t staging_bytes,
+                                            const jsim_checkpoint* ck)
+{
     if (!ctx) return JSIM_ERR_ARG;
+    const bool ck_on = ck && ck->path && ck->path[0];
+    if (ck && !ck_on && ck->max_supers) return JSIM_ERR_CHECKPOINT;  // progress would be lost
+    if (ck && ck->resume != 0 && ck->resume != 1) return JSIM_ERR_ARG;
     int rc = check_sets(sets);
     if (rc) return rc;
     if (sets->mem != JSIM_MEM_HOST) return JSIM_ERR_ARG;  // streaming reads host memory
@@ -254,6 +396,32 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
     rc = plan_supers(hoff, ids, n, mt, cap_vals, rb_cap, sup);
     if (rc) return rc;
 
+    // ---- checkpoint: the call's identity, and the state to resume from ----
+    CkHeader ckh{};
+    std::vector<u64> ck_sizes;
+    std::vector<unsigned char> ck_C;
+    bool resumed = false;
+    if (ck_on) {
+        memcpy(ckh.magic, kCkMagic, 8);
+        ckh.version = 1;
+        ckh.n = n;
+        ckh.N = N;
+        ckh.mt = mt;
+        ckh.cap_vals = cap_vals;
+        ckh.count_bits = (u64)ctx->opt.count_bits;
+        ckh.filter_min = (u64)ctx->opt.filter_min;
+        ckh.id_bits = (u64)ctx->opt.id_bits;
+        ckh.distance = (u64)ctx->opt.distance;
+        ckh.supers = sup.size();
+        ckh.fingerprint = ck_fingerprint(hoff, ids, n);
+        if (ck->resume) {
+            CkHeader got{};
+            rc = ck_read(ck->path, ckh, got, ck_sizes, ck_C, resumed);
+            if (rc) return rc;
+            if (resumed) ckh = got;
+        }
+    }
+
     // ---- buffers ----
     StreamState* ss = nullptr;
     rc = stream_state(ctx, head + cap_vals, ss);
@@ -281,10 +449,40 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
     ALLOC(bsum, nbk_max * sizeof(u64));
     ALLOC(boff, nbk_max * sizeof(u64));
     ALLOC(Rd, sizeof(u64));
-    CK(cudaMemsetAsync(Cacc.p, 0, n * n * cb, cs));
-    CK(cudaMemsetAsync(sizes_d.p, 0, n * sizeof(u64), cs));
-    CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(u64), cs));
-    CK(cudaMemsetAsync(flags.as<u64>() + 2, 0xff, sizeof(u64), cs));
+    u64 g0 = 0;  // first super-batch of this call
+    if (resumed) {
+        g0 = ckh.done;
+        CK(cudaMemcpyAsync(Cacc.p, ck_C.data(), n * n * cb, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(sizes_d.p, ck_sizes.data(), n * sizeof(u64), cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(flags.p, ckh.flags, 3 * sizeof(u64), cudaMemcpyHostToDevice, cs));
+        CK(cudaStreamSynchronize(cs));  // the host copies are pageable and are released below
+        ctx->stats.rows_nonzero = ckh.rows_nonzero;
+        ctx->stats.batches = ckh.batches;
+        ctx->stats.words = ckh.words;
+        ctx->stats.bitops_dense = ckh.bitops;
+        std::vector<unsigned char>().swap(ck_C);
+    } else {
+        CK(cudaMemsetAsync(Cacc.p, 0, n * n * cb, cs));
+        CK(cudaMemsetAsync(sizes_d.p, 0, n * sizeof(u64), cs));
+        CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(u64), cs));
+        CK(cudaMemsetAsync(flags.as<u64>() + 2, 0xff, sizeof(u64), cs));
+    }
+    // the state after super-batch g (its product enqueued) into the file
+    auto save = [&](u64 done) -> int {
+        ckh.done = done;
+        ckh.rows_nonzero = ctx->stats.rows_nonzero;
+        ckh.batches = ctx->stats.batches;
+        ckh.words = ctx->stats.words;
+        ckh.bitops = ctx->stats.bitops_dense;
+        std::vector<u64> hsz(n);
+        std::vector<unsigned char> hc(n * n * cb);
+        CK(cudaMemcpyAsync(hc.data(), Cacc.p, n * n * cb, cudaMemcpyDeviceToHost, cs));
+        CK(cudaMemcpyAsync(hsz.data(), sizes_d.p, n * sizeof(u64), cudaMemcpyDeviceToHost, cs));
+        CK(cudaMemcpyAsync(ctx->h_scalars, flags.p, 3 * sizeof(u64), cudaMemcpyDeviceToHost, cs));
+        CK(cudaStreamSynchronize(cs));
+        for (int q = 0; q < 3; ++q) ckh.flags[q] = ctx->h_scalars[q];
+        return ck_write(ck->path, ckh, hsz, hc);
+    };
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), cs));
     const Plan plan = carve_plan(plan_buf, n);
     const u64 n_pad = round_up(n, kRowPad);
@@ -311,15 +509,15 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
         return JSIM_OK;
     };
     for (int k = 0; k < 2; ++k) CK(cudaEventRecord(ss->released[k], cs));
-    if (!sup.empty()) {
-        rc = stage(0);
+    if (g0 < sup.size()) {
+        rc = stage(g0);
         if (rc) return rc;
     }
     // Every super-batch is one batch of the method (Eq. 3) spanning its row
     // batches: one filter, one rank scan and one pack over [lo, lo + width).
     // C is additive over any partition of the rows (Eq. 4), so grouping row
     // batches changes no count; it only packs fewer, longer rows.
-    for (size_t g = 0; g < sup.size(); ++g) {
+    for (size_t g = g0; g < sup.size(); ++g) {
         const int k = (int)(g & 1);
         const Super& s = sup[g];
         const u64* d_off = dbuf[k].as<u64>();
@@ -373,6 +571,14 @@ extern "C" int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, voi
             if (rc) return rc;
             ctx->stats.words += W;
             ctx->stats.bitops_dense += 64.0 * (double)W * (double)n * (double)(n + 1) / 2.0;
+        }
+        if (ck_on && g + 1 < sup.size()) {
+            const bool stop = ck->max_supers && g + 1 - g0 >= ck->max_supers;
+            if (stop || (ck->every && (g + 1) % ck->every == 0)) {
+                rc = save(g + 1);
+                if (rc) return rc;
+            }
+            if (stop) return JSIM_ERR_INCOMPLETE;
         }
         // the next super-batch is gathered and copied while this one multiplies
         if (g + 1 < sup.size()) {

@@ -18,7 +18,7 @@ from . import build_native
 JSIM_OK = 0
 ERRORS = {1: "JSIM_ERR_ARG", 2: "JSIM_ERR_UNSORTED", 3: "JSIM_ERR_OVERFLOW", 4: "JSIM_ERR_ID_RANGE",
           5: "JSIM_ERR_OOM", 6: "JSIM_ERR_CUDA", 7: "JSIM_ERR_TIMEOUT", 8: "JSIM_ERR_CANCELLED",
-          9: "JSIM_ERR_UNSUPPORTED"}
+          9: "JSIM_ERR_UNSUPPORTED", 10: "JSIM_ERR_INCOMPLETE", 11: "JSIM_ERR_CHECKPOINT"}
 MEM_HOST, MEM_DEVICE = 0, 1
 VARIANTS = {"auto": 0, "popc": 1, "b1": 2, "i8": 3, "f8": 4, "tc": 5, "tc2": 6}
 VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
@@ -38,6 +38,11 @@ class JsimError(RuntimeError):
 class Sets(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("offsets", ctypes.c_void_p), ("ids", ctypes.c_void_p),
                 ("mem", ctypes.c_int)]
+
+
+class Checkpoint(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_char_p), ("every", ctypes.c_uint32), ("max_supers", ctypes.c_uint32),
+                ("resume", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):
@@ -91,6 +96,9 @@ SIGNATURES = {
                                               ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
     "jsim_all_pairs_streamed": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64]),
+    "jsim_all_pairs_streamed_ckpt": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                                    ctypes.POINTER(Checkpoint)]),
     "jsim_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, _u64p, ctypes.c_void_p,
                                  ctypes.c_int]),
@@ -300,18 +308,31 @@ class Context:
                 np.empty((n, n), dtype=np.float64) if want_J else None)
 
     def all_pairs_streamed(self, offsets, ids, staging_bytes: int = 1 << 30, want_C=True, want_J=True,
-                           want_sizes=True, out_device=False, out=None):
+                           want_sizes=True, out_device=False, out=None, checkpoint: dict | None = None):
         """As all_pairs for a collection in host memory, streamed through two
         pinned staging buffers of ``staging_bytes`` each (host->device copies
-        overlap the device's work)."""
+        overlap the device's work).  ``checkpoint`` = {"path": ..., "every": k,
+        "max_supers": m, "resume": bool} keeps progress in a file (see
+        jsim_all_pairs_streamed_ckpt); a stop after m super-batches raises
+        JsimError JSIM_ERR_INCOMPLETE."""
         s, keep, is_dev = self._sets(offsets, ids)
         if is_dev:
             raise ValueError("all_pairs_streamed reads its input from host memory")
         C, sizes, J = out if out is not None else self._outputs(s.n, out_device, want_C, want_sizes, want_J)
         self._order()
-        rc = self._lib.jsim_all_pairs_streamed(self._h, ctypes.byref(s), self._ptr(C), self._ptr(sizes),
-                                               self._ptr(J), MEM_DEVICE if out_device else MEM_HOST,
-                                               int(staging_bytes))
+        mem = MEM_DEVICE if out_device else MEM_HOST
+        if checkpoint is None:
+            rc = self._lib.jsim_all_pairs_streamed(self._h, ctypes.byref(s), self._ptr(C), self._ptr(sizes),
+                                                   self._ptr(J), mem, int(staging_bytes))
+        else:
+            ck = Checkpoint()
+            path = checkpoint.get("path")
+            ck.path = os.fsencode(path) if path else None
+            ck.every = int(checkpoint.get("every", 0))
+            ck.max_supers = int(checkpoint.get("max_supers", 0))
+            ck.resume = 1 if checkpoint.get("resume", False) else 0
+            rc = self._lib.jsim_all_pairs_streamed_ckpt(self._h, ctypes.byref(s), self._ptr(C), self._ptr(sizes),
+                                                        self._ptr(J), mem, int(staging_bytes), ctypes.byref(ck))
         _check(rc, self._h)
         return C, sizes, J
 

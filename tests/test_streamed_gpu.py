@@ -131,3 +131,88 @@ def test_streamed_errors(gpu):
 def test_streamed_two_or_more_filter(gpu, c1, c1_ref):
     with jsim.Context(batch_rows=1 << 14, filter_min=2) as ctx:
         assert_same(ctx.all_pairs_streamed(*c1, staging_bytes=MIB), c1_ref)
+
+
+def run_to_end(ctx, c, path, staging, every=0, step=0, out_device=False):
+    """Resume a checkpointed streamed call `step` super-batches at a time
+    until it completes; returns the result and the number of calls."""
+    calls = 0
+    while True:
+        calls += 1
+        try:
+            return ctx.all_pairs_streamed(*c, staging_bytes=staging, out_device=out_device,
+                                          checkpoint={"path": path, "every": every, "max_supers": step,
+                                                      "resume": True}), calls
+        except jsim.JsimError as e:
+            if e.name != "JSIM_ERR_INCOMPLETE":
+                raise
+            assert calls < 1000
+
+
+@pytest.mark.parametrize("filter_min,count_bits", [(1, 32), (2, 64)])
+def test_checkpoint_resume_matches_one_call(gpu, c1, c1_ref, tmp_path, filter_min, count_bits):
+    """A streamed call stopped after every 3 super-batches and resumed from its
+    file gives the one-call result bit for bit (and the same statistics)."""
+    path = str(tmp_path / "ck.bin")
+    with jsim.Context(batch_rows=1 << 14, filter_min=filter_min, count_bits=count_bits) as ctx:
+        one = ctx.all_pairs_streamed(*c1, staging_bytes=MIB)
+        st_one = ctx.stats()
+        assert st_one["batches"] > 6
+        res, calls = run_to_end(ctx, c1, path, MIB, every=2, step=3)
+        assert calls > 2
+        assert_same(res, c1_ref)
+        assert_same(res, (one[0].astype(np.uint64), one[1], one[2]))
+        st = ctx.stats()
+        for k in ("rows_nonzero", "words", "batches"):
+            assert st[k] == st_one[k]
+        # the file keeps the last checkpoint before the end: resuming it again
+        # redoes only the super-batches after it
+        again = ctx.all_pairs_streamed(*c1, staging_bytes=MIB, checkpoint={"path": path, "resume": True})
+        assert_same(again, c1_ref)
+        assert 0 < ctx.stats()["product_launches"] < st_one["product_launches"]
+
+
+def test_checkpoint_mismatch_corruption_and_errors(gpu, c1, c1_ref, tmp_path):
+    path = str(tmp_path / "ck.bin")
+    with jsim.Context(batch_rows=1 << 14) as ctx:
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*c1, staging_bytes=MIB, checkpoint={"path": path, "max_supers": 2})
+        assert e.value.name == "JSIM_ERR_INCOMPLETE"
+        good = open(path, "rb").read()
+        # another staging size is another call
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*c1, staging_bytes=2 * MIB, checkpoint={"path": path, "resume": True})
+        assert e.value.name == "JSIM_ERR_CHECKPOINT"
+        # another collection is another call
+        other = synth.ancestral64(seed=synth.SEED_BASE + 77)
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*other, staging_bytes=MIB, checkpoint={"path": path, "resume": True})
+        assert e.value.name == "JSIM_ERR_CHECKPOINT"
+        # a flipped byte in C fails the checksum; a truncated file is refused
+        bad = bytearray(good)
+        bad[len(bad) // 2] ^= 0x40
+        open(path, "wb").write(bytes(bad))
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*c1, staging_bytes=MIB, checkpoint={"path": path, "resume": True})
+        assert e.value.name == "JSIM_ERR_CHECKPOINT"
+        open(path, "wb").write(good[:-9])
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*c1, staging_bytes=MIB, checkpoint={"path": path, "resume": True})
+        assert e.value.name == "JSIM_ERR_CHECKPOINT"
+        # the intact file still resumes to the right answer
+        open(path, "wb").write(good)
+        res, _ = run_to_end(ctx, c1, path, MIB, step=0)
+        assert_same(res, c1_ref)
+        # a missing file with resume starts from the beginning
+        res = ctx.all_pairs_streamed(*c1, staging_bytes=MIB,
+                                     checkpoint={"path": str(tmp_path / "none.bin"), "resume": True})
+        assert_same(res, c1_ref)
+        # stopping without a file would lose the progress
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_streamed(*c1, staging_bytes=MIB, checkpoint={"path": None, "max_supers": 1})
+        assert e.value.name == "JSIM_ERR_CHECKPOINT"
+        # an input error is reported by the resumed call that reaches it
+        bad_c = collection([[1, 2, 3], list(range(10, 300000, 3)), [5, 3, 9]])
+        with pytest.raises(jsim.JsimError) as e:
+            run_to_end(ctx, bad_c, str(tmp_path / "bad.bin"), MIB, step=1)
+        assert e.value.name == "JSIM_ERR_UNSORTED"
