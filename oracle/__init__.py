@@ -12,8 +12,8 @@ Two oracles live here, both written from arXiv 1911.04200:
 * ``oracle.c`` (loaded through ``ctypes`` below) is the plain definition:
   distinct-value counts, pairwise intersections by a two-pointer merge of
   sorted lists, union by inclusion-exclusion and the binary64 quotient
-  (Sec. II-A, Sec. III-A, Eq. 2), and the Jaccard distance 1 - J as the
-  quotient (union - intersection) / union (Sec. II-A).
+  (Sec. II-A, Sec. III-A, Eq. 2), and the Jaccard distance as the binary64
+  subtraction 1.0 - J (Sec. II-A).
 * ``packed.py`` follows the paper's batched method step by step in numpy:
   row batches (Eq. 3), the zero-row filter (Eq. 5), its prefix sum and the
   compacted rows (Eq. 6), b-bit bitmask words and the AND+popcount product
@@ -120,8 +120,8 @@ def jaccard(inter: int, size_x: int, size_y: int) -> float:
 
 
 def distance(inter: int, size_x: int, size_y: int) -> float:
-    """Jaccard distance (|X|+|Y|-2b) / (|X|+|Y|-b) in binary64, 0.0 for two
-    empty sets (Sec. II-A: 1 - J, as one quotient of integers)."""
+    """Jaccard distance 1 - J (Sec. II-A) as the binary64 subtraction 1.0 - J,
+    0.0 for two empty sets."""
     return float(_load().oracle_distance(inter, size_x, size_y))
 
 

