@@ -122,10 +122,11 @@ typedef struct {
                              and C_ii = |X_i| is known, so C and J are unchanged while the
                              product runs over fewer words.  Serving ignores it. */
     int distance;         /* 0 (default): the J output holds the similarity J = C / U (Eq. 2);
-                             1: it holds the Jaccard distance D = 1 - J (Sec. II-A), computed
-                             as the correctly rounded quotient (U - C) / U, D = 0 for two
-                             empty sets.  Applies to every call that writes J (plain,
-                             streamed, batched, serving indexes built on the context). */
+                             1: it holds the Jaccard distance D = 1 - J (Sec. II-A), the
+                             binary64 subtraction 1.0 - J of the correctly rounded J
+                             (D = 0 for two empty sets).  Applies to every call that writes
+                             J (plain, streamed, batched, serving indexes built on the
+                             context). */
 } jsim_options;
 
 typedef struct jsim_ctx jsim_ctx;

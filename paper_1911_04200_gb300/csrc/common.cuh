@@ -140,7 +140,7 @@ cudaError_t launch_rank_words(const QueryIndex& ix, ulonglong2* fr, int sms, cud
 // their total (host copy).
 cudaError_t launch_qrows(const u64* ids, u64 S, Plan plan, u64 values, const QueryIndex& ix, u32* Cacc,
                          u64* rows_read, int sms, cudaStream_t st);
-// distance: J holds D = (U - C) / U instead (0 for two empty sets)
+// distance: J holds D = 1.0 - J instead (binary64; 0 for two empty sets)
 cudaError_t launch_qepi(const u32* Cacc, u64 S, u64 n_ref, const u64* sq, const u64* sr, int count_bits, void* Cout,
                         double* J, int sms, cudaStream_t st, int distance = 0);
 
@@ -148,7 +148,7 @@ cudaError_t launch_qepi(const u32* Cacc, u64 S, u64 n_ref, const u64* sq, const 
 // Cout[i][j] = Cacc[min(i,j)][max(i,j)], J = C / (s_i + s_j - C) (binary64), 1 if 0.
 // diag_sizes: C_ii = s_i (the product ran over rows held by two or more
 // samples, so its diagonal lacks the rows only sample i holds).
-// distance: J holds D = (U - C) / U instead (0 for two empty sets).
+// distance: J holds D = 1.0 - J instead (binary64; 0 for two empty sets).
 cudaError_t launch_epilogue(const void* Cacc, u64 n, int count_bits, const u64* sizes,
                             void* Cout, double* J, cudaStream_t st, int diag_sizes = 0, int distance = 0);
 

@@ -2,7 +2,7 @@
 // J = C / (|X_i| + |X_j| - C) (Sec. III-A: union by inclusion-exclusion,
 // Eq. 2: s_ij = b_ij / c_ij), with J = 1 for two empty sets (Sec. II-A);
 // or, with `distance`, the Jaccard distance D = 1 - J (Sec. II-A) as the
-// correctly rounded quotient (U - C) / U, D = 0 for two empty sets.
+// binary64 subtraction 1.0 - J (D = 0 for two empty sets).
 //
 // The quotient is one IEEE binary64 division, round-to-nearest (__ddiv_rn),
 // of two integers below 2^53 converted exactly, so it is correctly rounded
@@ -50,8 +50,8 @@ k_epilogue(const CT* __restrict__ Cacc, u64 n, const u64* __restrict__ sizes,
         if (Cout) Cout[i * n + j] = c;
         if (J) {
             const u64 u = sizes[i] + sizes[j] - (u64)c;
-            const u64 num = distance ? u - (u64)c : (u64)c;
-            J[i * n + j] = u ? __ddiv_rn(__ull2double_rn(num), __ull2double_rn(u)) : (distance ? 0.0 : 1.0);
+            const double s = u ? __ddiv_rn(__ull2double_rn((u64)c), __ull2double_rn(u)) : 1.0;
+            J[i * n + j] = distance ? __dsub_rn(1.0, s) : s;
         }
     }
 }

@@ -26,7 +26,7 @@
 //                of a sample (or 4096 values) the counts go into C with
 //                atomic adds;
 //   k_qepi       J = C / (|Q_s| + |S_j| - C) in binary64 (Sec. II-A), or
-//                the distance (U - C) / U.
+//                the distance 1.0 - J.
 #include <algorithm>
 #include "ingest_dev.cuh"
 
@@ -296,8 +296,8 @@ __global__ void k_qepi(const u32* __restrict__ Cacc, u64 S, u64 n_ref, const u64
         const u64 u = sq[s] + sr[j] - c;
         if (Cout) Cout[e] = (CT)c;
         if (J) {
-            const u64 num = distance ? u - c : c;
-            J[e] = u ? __ddiv_rn(__ull2double_rn(num), __ull2double_rn(u)) : (distance ? 0.0 : 1.0);
+            const double s = u ? __ddiv_rn(__ull2double_rn(c), __ull2double_rn(u)) : 1.0;
+            J[e] = distance ? __dsub_rn(1.0, s) : s;
         }
     }
 }

@@ -1,8 +1,8 @@
 """Distance and threshold outputs against the oracle.
 
-The distance D = 1 - J is the correctly rounded quotient (U - C) / U of the
-same integers, so it is compared bit for bit with the oracle's; threshold
-lists are compared as exact (i, j, value) sequences in row-major order."""
+The distance D = 1 - J is the binary64 subtraction 1.0 - J of the correctly
+rounded J, so it is compared bit for bit with the oracle's; threshold lists
+are compared as exact (i, j, value) sequences in row-major order."""
 import numpy as np
 import pytest
 
@@ -53,10 +53,10 @@ def test_distance_plain_streamed_batched(gpu, filter_min):
         outs = ctx.all_pairs_batched([c1, c2, c4])
         for (C, s, D), (Co, so, Do) in zip(outs, refs[:2] + [oracle_D(*c4)]):
             same_bits(D, Do)
-    # the similarity context still gives J, and D + J == 1 up to one rounding each
+    # the similarity context still gives J, and D is exactly 1.0 - J
     with jsim.Context() as ctx:
         _, _, J = ctx.all_pairs(*c2)
-    assert np.all(np.abs(J + refs[1][2] - 1.0) <= 2.3e-16)
+    same_bits(1.0 - J, refs[1][2])
 
 
 def test_distance_serving(gpu):
