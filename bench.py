@@ -619,6 +619,16 @@ def run_jsim(args):
         # parity spot check of the e2e outputs against the device-resident run
         assert np.array_equal(hJ.view(np.uint64)[:4, :4], J[:4, :4].cpu().numpy().view(np.uint64))
 
+    # the method's useful work (pairs of nonzero packed words, the count a
+    # sparse product needs) and the compulsory bytes, from one more untimed call
+    uctx = jsim.Context(device=local, variant=args.variant, batch_rows=args.batch_rows, id_bits=cfg["id_bits"],
+                        filter_min=args.filter_min, count_useful=True)
+    uctx.all_pairs(d_off, d_ids, out=(C, S, J))
+    useful = uctx.stats()["bitops_useful"]
+    uctx.close()
+    cb = 4
+    compulsory = 8 * N + 8 * n * last["words"] + n * n * (cb + 8) + 8 * n
+
     variant = last["variant"]
     per_launch_bitops = agg["bitops"] / max(1, agg["product_launches"])
     ms_per_launch = agg["ms_product"] / max(1, agg["product_launches"])
@@ -627,7 +637,10 @@ def run_jsim(args):
     cfg.update({"batch_rows": last["batch_rows"], "batches": last["batches"], "variant": variant,
                 "filter_min": args.filter_min,
                 "rows_nonzero": last["rows_nonzero"], "words": last["words"], "values": N,
-                "bitops_dense_per_step": last["bitops_dense"], "parallelism": "dp%d (independent problems)" % world,
+                "bitops_dense_per_step": last["bitops_dense"], "bitops_useful_per_step": useful,
+                "useful_fraction": round(useful / last["bitops_dense"], 4) if last["bitops_dense"] else None,
+                "compulsory_bytes_per_step": compulsory,
+                "parallelism": "dp%d (independent problems)" % world,
                 "l2": "inputs (%.1f GB of values) larger than L2 (129 MB); no flush" % (N * 8 / 1e9),
                 "stage_ms": {k: round(last[k], 3) for k in ("ms_validate", "ms_filter", "ms_scan", "ms_pack",
                                                             "ms_product", "ms_epilogue")}})

@@ -127,6 +127,10 @@ typedef struct {
                              (D = 0 for two empty sets).  Applies to every call that writes
                              J (plain, streamed, batched, serving indexes built on the
                              context). */
+    int count_useful;     /* 1: also count the useful work of the plain and streamed calls and
+                             of jsim_product into jsim_stats.bitops_useful (one more read of
+                             every packed batch; a resumed streamed call counts the
+                             super-batches it ran); 0 (default): not counted */
 } jsim_options;
 
 typedef struct jsim_ctx jsim_ctx;
@@ -144,6 +148,10 @@ typedef struct {
     double ms_total;           /* wall time of the call's device work (profile=1) */
     double ms_h2d, ms_validate, ms_filter, ms_scan, ms_pack, ms_product, ms_epilogue, ms_d2h;
     double bitops_dense;       /* 64 * sum_l W_l * n(n+1)/2: dense AND+popcount bit-operations */
+    double bitops_useful;      /* with count_useful: 64 * sum over word columns of
+                                  nnz(nnz+1)/2, nnz the rows whose word is nonzero - the pairs of
+                                  nonzero words, the work a sparse product needs (the operation
+                                  count depends on the sparsity structure, Sec. IV); else 0 */
 } jsim_stats;
 
 /* Fill *opt with the defaults described above. */

@@ -109,6 +109,7 @@ void jsim_default_options(jsim_options* opt)
     opt->timeout_ms = 2000;
     opt->filter_min = 1;
     opt->distance = 0;
+    opt->count_useful = 0;
 }
 
 int jsim_create(jsim_ctx** out, const jsim_options* opt)
@@ -124,6 +125,7 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
     if (o.batch_rows % 64 != 0) return JSIM_ERR_ARG;
     if (o.filter_min != 1 && o.filter_min != 2) return JSIM_ERR_ARG;
     if (o.distance != 0 && o.distance != 1) return JSIM_ERR_ARG;
+    if (o.count_useful != 0 && o.count_useful != 1) return JSIM_ERR_ARG;
     if ((o.alloc == nullptr) != (o.free == nullptr)) return JSIM_ERR_ARG;
     if (!o.alloc) { o.alloc = default_alloc; o.free = default_free; }
     jsim_ctx* c = new jsim_ctx();
@@ -210,9 +212,13 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), ctx->stream));
 
     const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
-    DevBuf Cacc;
+    DevBuf Cacc, useful;
     ALLOC(Cacc, n * n * cb);
     CK(cudaMemsetAsync(Cacc.p, 0, n * n * cb, ctx->stream));
+    if (ctx->opt.count_useful) {
+        ALLOC(useful, sizeof(u64));
+        CK(cudaMemsetAsync(useful.p, 0, sizeof(u64), ctx->stream));
+    }
 
     // values lie in [minid, maxid]; batches are aligned to multiples of m~ and
     // empty stretches of the value range are skipped
@@ -234,6 +240,8 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
                 StageTimer t(ctx, &ctx->stats.ms_product);
                 rc = run_product(ctx, v, bb.X.as<u64>(), stride, n, W, Cacc.p);
                 if (rc) return rc;
+                if (ctx->opt.count_useful)
+                    CK(launch_useful(bb.X.as<u64>(), n, stride, W, useful.as<u64>(), ctx->sms, ctx->stream));
                 ctx->stats.batches += 1;
                 ctx->stats.rows_nonzero += R;
                 ctx->stats.words += W;
@@ -270,7 +278,10 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
         if (sizes) CK(cudaMemcpyAsync(sizes, st.sizes.p, n * sizeof(u64), k, ctx->stream));
     }
     CK(cudaMemcpyAsync(ctx->h_scalars, ctx->d_err, sizeof(u32), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->opt.count_useful)
+        CK(cudaMemcpyAsync(ctx->h_scalars + 1, useful.p, sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->opt.count_useful) ctx->stats.bitops_useful = 64.0 * (double)ctx->h_scalars[1];
     if ((u32)ctx->h_scalars[0] != 0) return JSIM_ERR_TIMEOUT;
     return JSIM_OK;
 }
@@ -331,10 +342,19 @@ int jsim_product(jsim_ctx* ctx, const uint64_t* words, uint64_t n, uint64_t W, u
     CK(cudaMemsetAsync(Cacc.p, 0, n * n * cb, ctx->stream));
     int v = variant == JSIM_VARIANT_AUTO ? choose_variant(ctx, n, W) : variant;
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), ctx->stream));
+    DevBuf useful;
     if (W) {
         StageTimer t(ctx, &ctx->stats.ms_product);
         int rc = run_product(ctx, v, (const u64*)words, stride, n, W, Cacc.p);
         if (rc) return rc;
+    }
+    if (W && ctx->opt.count_useful) {
+        ALLOC(useful, sizeof(u64));
+        CK(cudaMemsetAsync(useful.p, 0, sizeof(u64), ctx->stream));
+        CK(launch_useful((const u64*)words, n, stride, W, useful.as<u64>(), ctx->sms, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->h_scalars + 1, useful.p, sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->stats.bitops_useful = 64.0 * (double)ctx->h_scalars[1];
     }
     ctx->stats.words = W;
     ctx->stats.bitops_dense = 64.0 * (double)W * (double)n * (double)(n + 1) / 2.0;

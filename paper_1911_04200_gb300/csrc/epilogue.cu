@@ -9,6 +9,7 @@
 // and bit-identical to any other correctly rounded evaluation.  32 x 32
 // tiles are staged through shared memory so both the read of the mirrored
 // half and the writes stay coalesced.
+#include <algorithm>
 #include "common.cuh"
 
 namespace jsim {
@@ -56,7 +57,32 @@ k_epilogue(const CT* __restrict__ Cacc, u64 n, const u64* __restrict__ sizes,
     }
 }
 
+// Useful work of a packed batch: for every word column w, nnz_w = rows whose
+// word w is nonzero; adds sum_w nnz_w (nnz_w + 1) / 2 (the pairs i <= j of
+// nonzero words) to *acc.  Consecutive threads take consecutive columns, so
+// every row read is coalesced.
+__global__ void k_useful(const u64* __restrict__ X, u64 n, u64 stride, u64 W, unsigned long long* acc)
+{
+    u64 local = 0;
+    for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < W; w += (u64)gridDim.x * blockDim.x) {
+        u64 c = 0;
+        for (u64 i = 0; i < n; ++i) c += X[i * stride + w] != 0ull;
+        local += c * (c + 1) / 2;
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(acc, (unsigned long long)local);
+}
+
 }  // namespace
+
+cudaError_t launch_useful(const u64* X, u64 n, u64 stride, u64 W, u64* acc, int sms, cudaStream_t st)
+{
+    if (W == 0 || n == 0) return cudaSuccess;
+    const u64 blocks = std::min<u64>((W + 255) / 256, (u64)sms * 8);
+    k_useful<<<(unsigned)blocks, 256, 0, st>>>(X, n, stride, W, (unsigned long long*)acc);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_epilogue(const void* Cacc, u64 n, int count_bits, const u64* sizes,
                             void* Cout, double* J, cudaStream_t st, int diag_sizes, int distance)

@@ -434,7 +434,7 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
     }
     const u64 nw_max = rb_max * nwords;  // bitmap words of the widest super-batch
     const u64 nbk_max = std::max<u64>((nw_max + kScanBlockWords - 1) / kScanBlockWords, 1);
-    DevBuf dbuf[2], Cacc, sizes_d, flags, plan_buf, X, bm, seen, dir, bsum, boff, Rd, Cst, Jst;
+    DevBuf dbuf[2], Cacc, sizes_d, flags, plan_buf, X, bm, seen, dir, bsum, boff, Rd, Cst, Jst, useful;
     ALLOC(dbuf[0], (head + count_max) * sizeof(u64));
     ALLOC(dbuf[1], (head + count_max) * sizeof(u64));
     CopyFence fence{xs};
@@ -449,6 +449,10 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
     ALLOC(bsum, nbk_max * sizeof(u64));
     ALLOC(boff, nbk_max * sizeof(u64));
     ALLOC(Rd, sizeof(u64));
+    if (ctx->opt.count_useful) {
+        ALLOC(useful, sizeof(u64));
+        CK(cudaMemsetAsync(useful.p, 0, sizeof(u64), cs));
+    }
     u64 g0 = 0;  // first super-batch of this call
     if (resumed) {
         g0 = ckh.done;
@@ -569,6 +573,8 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
             StageTimer t(ctx, &ctx->stats.ms_product);
             rc = run_product(ctx, v, X.as<u64>(), stride, n, W, Cacc.p);
             if (rc) return rc;
+            if (ctx->opt.count_useful)
+                CK(launch_useful(X.as<u64>(), n, stride, W, useful.as<u64>(), ctx->sms, cs));
             ctx->stats.words += W;
             ctx->stats.bitops_dense += 64.0 * (double)W * (double)n * (double)(n + 1) / 2.0;
         }
@@ -622,7 +628,10 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
         if (sizes) CK(cudaMemcpyAsync(sizes, sizes_d.p, n * sizeof(u64), kind, cs));
     }
     CK(cudaMemcpyAsync(ctx->h_scalars, ctx->d_err, sizeof(u32), cudaMemcpyDeviceToHost, cs));
+    if (ctx->opt.count_useful)
+        CK(cudaMemcpyAsync(ctx->h_scalars + 1, useful.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
     CK(cudaStreamSynchronize(cs));
+    if (ctx->opt.count_useful) ctx->stats.bitops_useful = 64.0 * (double)ctx->h_scalars[1];
     if ((u32)ctx->h_scalars[0] != 0) return JSIM_ERR_TIMEOUT;
     return JSIM_OK;
 }

@@ -50,7 +50,7 @@ class Options(ctypes.Structure):
                 ("count_bits", ctypes.c_int), ("id_bits", ctypes.c_int), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("timeout_ms", ctypes.c_int), ("profile", ctypes.c_int),
-                ("filter_min", ctypes.c_int), ("distance", ctypes.c_int)]
+                ("filter_min", ctypes.c_int), ("distance", ctypes.c_int), ("count_useful", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
                 ("launches", ctypes.c_int), ("ms_total", ctypes.c_double), ("ms_h2d", ctypes.c_double),
                 ("ms_validate", ctypes.c_double), ("ms_filter", ctypes.c_double), ("ms_scan", ctypes.c_double),
                 ("ms_pack", ctypes.c_double), ("ms_product", ctypes.c_double), ("ms_epilogue", ctypes.c_double),
-                ("ms_d2h", ctypes.c_double), ("bitops_dense", ctypes.c_double)]
+                ("ms_d2h", ctypes.c_double), ("bitops_dense", ctypes.c_double),
+                ("bitops_useful", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -178,7 +179,7 @@ class Context:
     def __init__(self, device: int = 0, variant: str | int = "auto", batch_rows: int = 0, word_bits: int = 64,
                  count_bits: int = 32, id_bits: int = 64, profile: bool = False, stream=None,
                  use_torch_allocator: bool = True, timeout_ms: int = 2000, filter_min: int = 1,
-                 distance: bool = False):
+                 distance: bool = False, count_useful: bool = False):
         torch = _torch()
         self._lib = load()
         self.device = device
@@ -197,6 +198,7 @@ class Context:
         o.timeout_ms = timeout_ms
         o.filter_min = filter_min
         o.distance = 1 if distance else 0
+        o.count_useful = 1 if count_useful else 0
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         self._keep = []
         if use_torch_allocator:

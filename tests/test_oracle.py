@@ -342,3 +342,31 @@ def test_distance_is_one_minus_J_within_one_rounding():
     C = np.array([[3, 1], [0, 2]], dtype=np.uint64)
     D = oracle.distance_matrix(C, np.array([3, 4], np.uint64), np.array([5, 2], np.uint64))
     assert D[0, 0] == oracle.distance(3, 3, 5) and D[1, 1] == oracle.distance(2, 4, 2)
+
+
+def permute_rows(offsets, ids, bits=64, a=0x9E3779B97F4A7C15, b=0x632BE59BD9B4E019):
+    """Relabel every value of [0, 2^bits) by x -> a*x + b mod 2^bits (a
+    bijection of that domain: a is odd) and re-sort each sample."""
+    mask = np.uint64((1 << bits) - 1) if bits < 64 else np.uint64(2**64 - 1)
+    out = np.empty_like(ids)
+    for i in range(len(offsets) - 1):
+        s, e = int(offsets[i]), int(offsets[i + 1])
+        v = (ids[s:e].astype(np.uint64) * np.uint64(a) + np.uint64(b)) & mask
+        out[s:e] = np.sort(v)
+    return offsets.copy(), out
+
+
+def test_row_permutation_invariance():
+    """Reordering the rows of the indicator matrix (Sec. III-C permutes rows
+    for load balance) changes no count: the oracle gives the same C, sizes
+    and J for a collection and for its values relabelled by a bijection of
+    the 64-bit domain."""
+    from paper_1911_04200_gb300 import synth
+    off, ids = synth.clade1024(n=40, median=3e3)
+    poff, pids = permute_rows(off, ids)
+    assert not np.array_equal(pids, ids)
+    C0, s0, J0 = oracle.all_pairs(off, ids)
+    C1, s1, J1 = oracle.all_pairs(poff, pids)
+    np.testing.assert_array_equal(C0, C1)
+    np.testing.assert_array_equal(s0, s1)
+    np.testing.assert_array_equal(J0.view(np.uint64), J1.view(np.uint64))

@@ -273,3 +273,44 @@ def test_bernoulli_matrices(gpu, n, m, p, variant):
         assert_same(ctx.all_pairs(off, ids), ref)
         w2 = ctx.stats()["words"]
     assert w2 <= w1
+
+
+@pytest.mark.parametrize("variant", ["auto", "popc", "tc2"])
+def test_row_permutation_invariance(gpu, variant):
+    """Values relabelled by a bijection of their 32-bit domain (a reordering
+    of the indicator matrix's rows, Sec. III-C): the GPU path gives the
+    original collection's oracle results, with either filter and batch size."""
+    from test_oracle import permute_rows
+    off, ids = synth.clade1024(n=130, median=2e4)
+    ref = oracle.all_pairs(off, ids)
+    poff, pids = permute_rows(off, ids, bits=32)
+    with jsim.Context(variant=variant, id_bits=32) as ctx:
+        assert_same(ctx.all_pairs(poff, pids), ref)
+    with jsim.Context(variant=variant, filter_min=2, batch_rows=1 << 26) as ctx:
+        assert_same(ctx.all_pairs(poff, pids), ref)
+
+
+@pytest.mark.parametrize("filter_min", [1, 2])
+def test_useful_work_count(gpu, c1, filter_min):
+    """bitops_useful = 64 x the pairs (i <= j) of nonzero packed words per
+    word column, summed over batches: against the packed step oracle's words
+    for the same batches; the dense count is 64 x W x n(n+1)/2 as before."""
+    off, ids = c1
+    mt = 1 << 16
+    F = 0
+    for lo in range(0, 1 << 20, mt):
+        words = packed.run_batch(off, ids, lo, mt, min_count=filter_min)["words"]
+        nnz = (words != 0).sum(axis=0).astype(np.int64)
+        F += int((nnz * (nnz + 1) // 2).sum())
+    with jsim.Context(batch_rows=mt, filter_min=filter_min, count_useful=True) as ctx:
+        ctx.all_pairs(*c1)
+        st = ctx.stats()
+        assert st["bitops_useful"] == 64.0 * F
+        assert 0 < st["bitops_useful"] <= st["bitops_dense"]
+        # a streamed call packs super-batches of several row batches: fewer,
+        # longer word columns, so its count differs but is also positive
+        ctx.all_pairs_streamed(*c1, staging_bytes=4 << 20)
+        assert 0 < ctx.stats()["bitops_useful"] <= ctx.stats()["bitops_dense"]
+    with jsim.Context(batch_rows=mt, filter_min=filter_min) as ctx:
+        ctx.all_pairs(*c1)
+        assert ctx.stats()["bitops_useful"] == 0.0
