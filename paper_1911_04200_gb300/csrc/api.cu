@@ -84,8 +84,9 @@ int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 widt
                            bb.boff.as<u64>(), bb.X.as<u64>(), stride, batch_sizes, ctx->sms, ctx->stream));
         } else {
             CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->sms, ctx->stream));
-            CK(launch_pack_full(st.d_ids, n, bb.plan, st.max_chunks, lo, bb.bitmap.as<u64>(), bb.dir.as<u32>(),
-                                bb.boff.as<u64>(), bb.X.as<u64>(), stride, bb.R.as<u64>(), ctx->sms, ctx->stream));
+            CK(launch_pack_full(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u64>(),
+                                bb.dir.as<u32>(), bb.boff.as<u64>(), bb.X.as<u64>(), stride, bb.R.as<u64>(), ctx->sms,
+                                ctx->stream));
         }
         ctx->stats.launches += 2;
     }

@@ -118,7 +118,7 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
                 }
                 CK(launch_scan(w.bitmap[ln].as<u64>(), nwords, w.dir[ln].as<u32>(), w.bsum[ln].as<u64>(),
                                w.boff[ln].as<u64>(), w.R[ln].as<u64>(), ls, scal + 2 * c, scal + 2 * c + 1));
-                CK(launch_pack_full(cl.d_ids, cl.n, plan, cl.max_chunks, lo, w.bitmap[ln].as<u64>(),
+                CK(launch_pack_full(cl.d_ids, cl.n, plan, cl.max_chunks, lo, cl.mt, w.bitmap[ln].as<u64>(),
                                     w.dir[ln].as<u32>(), w.boff[ln].as<u64>(), X, cl.stride, w.R[ln].as<u64>(),
                                     ctx->sms, ls, scal + 2 * c + 1));
                 ctx->stats.launches += 5;

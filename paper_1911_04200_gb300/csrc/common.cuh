@@ -64,9 +64,10 @@ cudaError_t launch_zero_rows(u64* X, u64 rows, u64 stride, u64 words, int sms, c
 // 0..n-1 (W_l = ceil(*Rdev / 64), device) is written once and complete, into
 // a packed matrix the caller has zeroed.  Values whose bit the bitmap lacks
 // are not packed (the two-or-more filter).
-cudaError_t launch_pack_full(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, const u64* bitmap,
-                             const u32* dir, const u64* boff, u64* X, u64 stride, const u64* Rdev, int sms,
-                             cudaStream_t st, const u64* kbase = nullptr);
+// Values outside [lo, lo + width) are not packed.
+cudaError_t launch_pack_full(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
+                             const u64* bitmap, const u32* dir, const u64* boff, u64* X, u64 stride,
+                             const u64* Rdev, int sms, cudaStream_t st, const u64* kbase = nullptr);
 // Sample i's word q goes to X[i * stride + (kbase + q) * wstride]: row-major
 // packed rows with wstride 1, word-major (one row per word) with stride 1.
 cudaError_t launch_pack(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,

@@ -301,11 +301,18 @@ constexpr int kPackSeg = 512;
 static_assert(kChunk % kPackSeg == 0 && kPackSeg * (kIngestThreads / 32) == kChunk,
               "a chunk is one segment per warp");
 
-__device__ __forceinline__ long long insertion_word(u64 x, u64 lo, const u64* __restrict__ bitmap,
+// A value outside [lo, lo + width) (only an unsorted input can put one in a
+// slice) gets the sentinel word 2^63 - 1, which is never written.
+__device__ __forceinline__ long long insertion_word(u64 x, u64 lo, u64 width, const u64* __restrict__ bitmap,
                                                     const u32* __restrict__ dir, const u64* __restrict__ boff,
                                                     u64& bit)
 {
-    const u64 d = x - lo, w = d >> 6, word = bitmap[w];
+    const u64 d = x - lo;
+    if (d >= width) {
+        bit = 0ull;
+        return 0x7fffffffffffffffll;
+    }
+    const u64 w = d >> 6, word = bitmap[w];
     const u64 below = word & ((1ull << (d & 63)) - 1ull);
     const u64 r = boff[w / kScanBlockWords] + (u64)dir[w] + (u64)__popcll(below);
     bit = ((word >> (d & 63)) & 1ull) ? (1ull << (r & 63)) : 0ull;
@@ -313,7 +320,7 @@ __device__ __forceinline__ long long insertion_word(u64 x, u64 lo, const u64* __
 }
 
 __global__ void __launch_bounds__(kIngestThreads)
-k_pack_full(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, const u64* __restrict__ bitmap,
+k_pack_full(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, const u64* __restrict__ bitmap,
             const u32* __restrict__ dir, const u64* __restrict__ boff, u64* X, u64 stride,
             const u64* kbase, const u64* __restrict__ Rdev)
 {
@@ -337,14 +344,14 @@ k_pack_full(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, const u64* __
         if (sbeg >= send) continue;
         u64* row = X + i * stride + (kbase ? *kbase : 0ull);
         u64 tmp;
-        const long long seg_prev = sbeg > bb ? insertion_word(ids[sbeg - 1], lo, bitmap, dir, boff, tmp) : -1ll;
+        const long long seg_prev = sbeg > bb ? insertion_word(ids[sbeg - 1], lo, width, bitmap, dir, boff, tmp) : -1ll;
         long long open_key = seg_prev;
         u64 open_mask = 0ull;
         for (u64 base = sbeg; base < send; base += 32) {
             const u64 pos = base + lane;
             long long key = kBig;
             u64 bit = 0ull;
-            if (pos < send) key = insertion_word(ids[pos], lo, bitmap, dir, boff, bit);
+            if (pos < send) key = insertion_word(ids[pos], lo, width, bitmap, dir, boff, bit);
             const bool lead = segmented_or<u64>((u64)key, bit);
             const bool real = lead && key != kBig;
             const unsigned leads = __ballot_sync(0xffffffffu, real);
@@ -376,7 +383,7 @@ k_pack_full(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, const u64* __
                 const u64 pos = base + lane;
                 long long key = kBig;
                 u64 bit = 0ull;
-                if (pos < be) key = insertion_word(ids[pos], lo, bitmap, dir, boff, bit);
+                if (pos < be) key = insertion_word(ids[pos], lo, width, bitmap, dir, boff, bit);
                 u64 m = key == open_key ? bit : 0ull;
                 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
@@ -432,12 +439,12 @@ cudaError_t launch_scan(const u64* bitmap, u64 nwords, u32* dir, u64* bsum, u64*
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_full(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, const u64* bitmap,
-                             const u32* dir, const u64* boff, u64* X, u64 stride, const u64* Rdev, int sms,
-                             cudaStream_t st, const u64* kbase)
+cudaError_t launch_pack_full(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
+                             const u64* bitmap, const u32* dir, const u64* boff, u64* X, u64 stride,
+                             const u64* Rdev, int sms, cudaStream_t st, const u64* kbase)
 {
-    k_pack_full<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, bitmap, dir, boff, X,
-                                                                            stride, kbase, Rdev);
+    k_pack_full<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, width, bitmap, dir,
+                                                                            boff, X, stride, kbase, Rdev);
     return cudaGetLastError();
 }
 

@@ -554,7 +554,16 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
             ctx->stats.launches += 2;
         }
         CK(cudaMemcpyAsync(ctx->h_scalars, Rd.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
+        CK(cudaMemcpyAsync(ctx->h_scalars + 1, flags.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
         CK(cudaStreamSynchronize(cs));
+        {
+            // an input error found by this or an earlier slice's validation
+            // ends the call before the pack (an unsorted slice may hold values
+            // outside the super-batch's range)
+            const u32 f = (u32)ctx->h_scalars[1];
+            if (f & kFlagUnsorted) return JSIM_ERR_UNSORTED;
+            if (f & kFlagIdRange) return JSIM_ERR_ID_RANGE;
+        }
         const u64 R = ctx->h_scalars[0], W = (R + 63) / 64;
         ctx->stats.rows_nonzero += R;
         ctx->stats.batches += R != 0;
@@ -563,8 +572,8 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
             ALLOC(X, n_pad * stride * sizeof(u64));
             StageTimer t(ctx, &ctx->stats.ms_pack);
             CK(launch_zero_rows(X.as<u64>(), n_pad, stride, stride, ctx->sms, cs));
-            CK(launch_pack_full(d_ids, n, plan, max_chunks, lo, bm.as<u64>(), dir.as<u32>(), boff.as<u64>(),
-                                X.as<u64>(), stride, Rd.as<u64>(), ctx->sms, cs));
+            CK(launch_pack_full(d_ids, n, plan, max_chunks, lo, width, bm.as<u64>(), dir.as<u32>(),
+                                boff.as<u64>(), X.as<u64>(), stride, Rd.as<u64>(), ctx->sms, cs));
             ctx->stats.launches += 2;
         }
         CK(cudaEventRecord(ss->released[k], cs));  // the slice's values are no longer read

@@ -1,13 +1,44 @@
 """Parity at the full sizes of the workloads, in the launch configuration the
-benchmark times, on outputs the oracle can compute one by one: sampled pairs
-(merge counts and binary64 J), every size, and the invariants that hold at
-any size (symmetry, C_ii = |X_i|, C_ij <= min, J_ii = 1, 0 <= J <= 1).
-Integers and correctly rounded quotients: tolerance zero."""
+benchmark times: the whole result against digests of the oracle's result
+(computed once by tests/golden/make_full_size_hashes.py, which calls only the
+oracle), sampled pairs the oracle computes one by one (merge counts and
+binary64 J), every size, and the invariants that hold at any size (symmetry,
+C_ii = |X_i|, C_ij <= min, J_ii = 1, 0 <= J <= 1).  Integers and correctly
+rounded quotients: tolerance zero."""
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_1911_04200_gb300 import jsim, synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_size_sha256.json")
+
+
+def golden(name):
+    with open(GOLDEN) as f:
+        return json.load(f)[name]
+
+
+def sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def check_digests(name, off, ids, C, s, J):
+    """The whole result against the oracle's, by SHA-256 of C (uint32), sizes
+    (uint64) and the bit patterns of J, stored by
+    tests/golden/make_full_size_hashes.py (which calls only the oracle)."""
+    g = golden(name)
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(off, dtype="<u8").tobytes())
+    h.update(np.ascontiguousarray(ids, dtype="<u8").tobytes())
+    assert h.hexdigest() == g["input_sha256"], "the generator drew another collection"
+    assert sha(np.asarray(C).astype(np.uint32)) == g["C_u32_sha256"]
+    assert sha(np.asarray(s).astype(np.uint64)) == g["sizes_u64_sha256"]
+    assert sha(np.asarray(J).view(np.uint64)) == g["J_f64_sha256"]
 
 pytestmark = pytest.mark.gpu
 
@@ -47,11 +78,36 @@ def test_clade1024_full_size(gpu, clade1024):
         C, s, J = ctx.all_pairs(off, ids)
         assert ctx.stats()["variant"] == "tc2"
     check_sampled(off, ids, C, s, J)
+    check_digests("clade1024", off, ids, C, s, J)
     with jsim.Context(id_bits=32, filter_min=2) as ctx:
         C2, s2, J2 = ctx.all_pairs(off, ids)
     np.testing.assert_array_equal(C2, C)
     np.testing.assert_array_equal(s2, s)
     np.testing.assert_array_equal(J2.view(np.uint64), J.view(np.uint64))
+
+
+@pytest.mark.timeout(900)
+def test_clade1024_device_input_whole_result(gpu, clade1024):
+    """Device-resident input (the benchmark's timed call: plain row batches,
+    no streaming) gives the oracle's whole result, by digest."""
+    import torch
+    off, ids = clade1024
+    d_off = torch.from_numpy(off.view(np.int64)).cuda()
+    d_ids = torch.from_numpy(ids.view(np.int64)).cuda()
+    with jsim.Context(id_bits=32) as ctx:
+        C, s, J = ctx.all_pairs(d_off, d_ids)
+        torch.cuda.synchronize()
+        C = C.view(torch.int32).cpu().numpy().view(np.uint32)
+        s = s.view(torch.int64).cpu().numpy().view(np.uint64)
+        J = J.cpu().numpy()
+    check_digests("clade1024", off, ids, C, s, J)
+
+
+def test_ancestral64_whole_result_digest(gpu):
+    off, ids = synth.ancestral64()
+    with jsim.Context() as ctx:
+        C, s, J = ctx.all_pairs(off, ids)
+    check_digests("ancestral64", off, ids, C, s, J)
 
 
 @pytest.mark.timeout(900)
