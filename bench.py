@@ -444,7 +444,8 @@ def run_serve(args):
     max_vals = int(np.sort(sizes)[-64:].sum())
     ctx = jsim.Context(device=0, id_bits=32)
     t0 = time.perf_counter()
-    ix = jsim.Index(ctx, roff, rids, max_batch_samples=64, max_batch_values=max_vals, slots=2)
+    slots = int(os.environ.get("JSIM_SERVE_SLOTS", "3"))
+    ix = jsim.Index(ctx, roff, rids, max_batch_samples=64, max_batch_values=max_vals, slots=slots)
     build_ms = (time.perf_counter() - t0) * 1e3
     for _ in range(max(args.warmup, 1)):
         ix.submit(*request()).wait()

@@ -330,7 +330,7 @@ typedef struct jsim_request jsim_request;
 typedef struct {
     uint64_t max_batch_samples; /* query samples per device batch, 1..64 (default 64) */
     uint64_t max_batch_values;  /* query values per device batch, < 2^32 (default 2^27) */
-    int slots;                  /* device batches in flight, 1..8 (default 2) */
+    int slots;                  /* device batches in flight, 1..8 (default 3) */
 } jsim_serve_options;
 
 typedef struct {

@@ -476,7 +476,7 @@ class Index:
     """
 
     def __init__(self, ctx: Context, offsets, ids, max_batch_samples: int = 64, max_batch_values: int = 1 << 27,
-                 slots: int = 2):
+                 slots: int = 3):
         self._lib = ctx._lib
         self.ctx = ctx
         self.count_bits = ctx.count_bits
