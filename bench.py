@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--batch-rows", type=int, default=0)
     ap.add_argument("--filter-min", type=int, default=1, choices=[1, 2],
                     help="2: the filter keeps rows two or more samples hold (same C and J, fewer words)")
+    ap.add_argument("--split", action="store_true",
+                    help="strong scaling: every rank takes one part of the same collection's row batches "
+                         "(jsim_all_pairs_part), one all-reduce sums the counts, rank 0 forms C and J")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -544,6 +547,64 @@ def run_serve(args):
     return 0
 
 
+def run_split(args):
+    """One collection split over the ranks by row batches (C is additive over
+    batches, Eq. 4): part `rank` of `world` on every rank, one all-reduce of
+    the n x n counts (NCCL; the only exchange), J on rank 0.  Strong scaling."""
+    import torch
+    import torch.distributed as dist
+    from paper_1911_04200_gb300 import jsim
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    off, ids, cfg = make_workload(args.workload, 0)  # the same collection on every rank
+    n = cfg["n"]
+    d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+    d_ids = torch.from_numpy(ids.view(np.int64)).to(dev)
+    ctx = jsim.Context(device=local, variant=args.variant, batch_rows=args.batch_rows, id_bits=cfg["id_bits"],
+                       filter_min=args.filter_min)
+
+    def step():
+        Cp, sp = ctx.all_pairs_part(d_off, d_ids, rank, world)
+        bitops = ctx.stats()["bitops_dense"]
+        Ci = Cp.view(torch.int32)  # u32 counts; their sum fits u32, so the int32 sum has the same bits
+        if world > 1:
+            dist.all_reduce(Ci, op=dist.ReduceOp.SUM)
+        if rank == 0:
+            ctx.finish(Ci, sp)
+        return bitops
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    t0 = time.perf_counter()
+    bitops = 0.0
+    for _ in range(args.steps):
+        bitops += step()
+    barrier()
+    ms, bitops_all = aggregate_over_ranks((time.perf_counter() - t0) * 1e3, bitops, dev)
+    cfg.update({"parallelism": "split contraction over %d ranks (one all-reduce of n x n counts)" % world,
+                "filter_min": args.filter_min})
+    line = {"metric": METRIC, "value": bitops_all / (ms * 1e-3) / 1e12, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
+            "config": cfg}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_jsim(args):
     import torch
     import torch.distributed as dist
@@ -732,6 +793,8 @@ def main():
         return run_serve(args)
     if args.workload == "density":
         return run_density(args)
+    if args.split:
+        return run_split(args)
     return run_jsim(args)
 
 

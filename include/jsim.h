@@ -180,6 +180,36 @@ JSIM_API int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets,
                    void* C, uint64_t* sizes, double* J, int out_mem);
 
 /*
+ * One part of an all-pairs call split over several devices or processes
+ * (the batches of Eq. 3 are independent and C is their sum, Eq. 4; the
+ * paper's layered grid reduces the partial counts in the same way).  The
+ * nb row batches between the collection's first and last value are cut into
+ * `parts` contiguous runs; part p takes batches [nb*p/parts, nb*(p+1)/parts)
+ * (by value range, so hashed values balance).
+ *   part, parts   0 <= part < parts
+ *   C             n*n counts of this part's rows (uint32 or uint64 as
+ *                 count_bits), both triangles; required
+ *   sizes         n distinct counts |X_i| of the whole samples (every part
+ *                 gives the same), or NULL
+ * Summing C over all parts (any order; each sum fits count_bits) and calling
+ * jsim_finish gives jsim_all_pairs's C and J, bit for bit.  The input is
+ * validated whole by every part.  Errors: as jsim_all_pairs.
+ */
+JSIM_API int jsim_all_pairs_part(jsim_ctx* ctx, const jsim_sets* sets, uint32_t part, uint32_t parts, void* C,
+                                 uint64_t* sizes, int out_mem);
+
+/*
+ * C and J from summed counts: Cout = C with the diagonal set to sizes (a
+ * part's rows may miss rows only one sample holds, with filter_min 2), J as
+ * in jsim_all_pairs (or the distance, per the context's options).
+ *   n       samples; C n*n counts (count_bits), sizes n
+ *   Cout, J outputs (either may be NULL); mem: JSIM_MEM_HOST or JSIM_MEM_DEVICE for all
+ * Errors: JSIM_ERR_ARG, JSIM_ERR_OOM, JSIM_ERR_CUDA.
+ */
+JSIM_API int jsim_finish(jsim_ctx* ctx, uint64_t n, const void* C, const uint64_t* sizes, void* Cout, double* J,
+                         int mem);
+
+/*
  * All-pairs similarity of k independent collections in one call (the
  * batched pattern).  Every collection is processed exactly as by
  * jsim_all_pairs (its own row batches, filter, prefix sum, words and product;

@@ -188,15 +188,17 @@ void jsim_destroy(jsim_ctx* ctx)
 // 228 / 261 ms; the device-resident call 207 ms.
 constexpr u64 kHostStreamBytes = 1ull << 30;
 
-int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes, double* J, int out_mem)
+namespace {
+
+// The plain call over the row batches [b_first + nb * part / parts,
+// b_first + nb * (part + 1) / parts) of the nb batches between the first and
+// the last value (parts = 1: all of them).  counts_only: C gets the part's
+// counts (both triangles, the diagonal from the part's rows only) and J is
+// not formed.
+int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes, double* J, int out_mem,
+                   u64 part, u64 parts, bool counts_only)
 {
-    if (!ctx) return JSIM_ERR_ARG;
-    int rc = check_sets(sets);
-    if (rc) return rc;
-    if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
-    if (sets->mem == JSIM_MEM_HOST && sets->n > 0 && sets->offsets[sets->n] >= sets->offsets[0] &&
-        (sets->offsets[sets->n] - sets->offsets[0]) * sizeof(u64) > kHostStreamBytes)
-        return jsim_all_pairs_streamed(ctx, sets, C, sizes, J, out_mem, kHostStreamBytes);
+    int rc = 0;
     CK(cudaSetDevice(ctx->opt.device));
     CallScope scope(ctx);
     StageTimer total(ctx, &ctx->stats.ms_total);
@@ -227,9 +229,13 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
     u64 mt = ctx->opt.batch_rows ? ctx->opt.batch_rows : auto_batch_rows(span + 1 ? span + 1 : ~0ull);
     ctx->stats.batch_rows = mt;
     int variant = ctx->opt.variant;
-    if (st.N) {
+    // this part's row batches [b_beg, b_end)
+    const u64 b_first = st.minid / mt, nb = st.maxid / mt - b_first + 1;
+    const u64 b_beg = b_first + (u64)((unsigned __int128)nb * part / parts);
+    const u64 b_end = b_first + (u64)((unsigned __int128)nb * (part + 1) / parts);
+    if (st.N && b_beg < b_end) {
         BatchBufs bb;
-        u64 lo = st.minid / mt * mt;
+        u64 lo = b_beg * mt;
         for (;;) {
             u64 R = 0, stride = 0, next = 0;
             bool has_next = false;
@@ -248,7 +254,7 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
                 ctx->stats.words += W;
                 ctx->stats.bitops_dense += 64.0 * (double)W * (double)n * (double)(n + 1) / 2.0;
             }
-            if (!has_next) break;
+            if (!has_next || next / mt >= b_end) break;
             lo = next / mt * mt;
         }
     }
@@ -263,9 +269,10 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
     }
     {
         StageTimer t(ctx, &ctx->stats.ms_epilogue);
+        if (counts_only) Jdst = nullptr;
         if (Cdst || Jdst) {
             CK(launch_epilogue(Cacc.p, n, ctx->opt.count_bits, st.sizes.as<u64>(), Cdst, Jdst, ctx->stream,
-                               ctx->opt.filter_min == 2, ctx->opt.distance));
+                               !counts_only && ctx->opt.filter_min == 2, ctx->opt.distance));
             ctx->stats.launches += 1;
         }
     }
@@ -284,6 +291,71 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
     CK(cudaStreamSynchronize(ctx->stream));
     if (ctx->opt.count_useful) ctx->stats.bitops_useful = 64.0 * (double)ctx->h_scalars[1];
     if ((u32)ctx->h_scalars[0] != 0) return JSIM_ERR_TIMEOUT;
+    return JSIM_OK;
+}
+
+}  // namespace
+
+int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes, double* J, int out_mem)
+{
+    if (!ctx) return JSIM_ERR_ARG;
+    int rc = check_sets(sets);
+    if (rc) return rc;
+    if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
+    if (sets->mem == JSIM_MEM_HOST && sets->n > 0 && sets->offsets[sets->n] >= sets->offsets[0] &&
+        (sets->offsets[sets->n] - sets->offsets[0]) * sizeof(u64) > kHostStreamBytes)
+        return jsim_all_pairs_streamed(ctx, sets, C, sizes, J, out_mem, kHostStreamBytes);
+    return all_pairs_impl(ctx, sets, C, sizes, J, out_mem, 0, 1, false);
+}
+
+int jsim_all_pairs_part(jsim_ctx* ctx, const jsim_sets* sets, uint32_t part, uint32_t parts, void* C,
+                        uint64_t* sizes, int out_mem)
+{
+    if (!ctx || !C) return JSIM_ERR_ARG;
+    if (parts == 0 || part >= parts) return JSIM_ERR_ARG;
+    int rc = check_sets(sets);
+    if (rc) return rc;
+    if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
+    return all_pairs_impl(ctx, sets, C, sizes, nullptr, out_mem, part, parts, true);
+}
+
+int jsim_finish(jsim_ctx* ctx, uint64_t n, const void* C, const uint64_t* sizes, void* Cout, double* J, int mem)
+{
+    if (!ctx || !C || !sizes) return JSIM_ERR_ARG;
+    if (mem != JSIM_MEM_HOST && mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
+    if (n > (1ull << 20)) return JSIM_ERR_ARG;
+    if (n == 0 || (!Cout && !J)) return JSIM_OK;
+    CK(cudaSetDevice(ctx->opt.device));
+    CallScope scope(ctx);
+    StageTimer total(ctx, &ctx->stats.ms_total);
+    const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
+    cudaStream_t s = ctx->stream;
+    DevBuf Cd, Sd, Co, Jd;
+    const void* Cp = C;
+    const u64* Sp = (const u64*)sizes;
+    void* Cop = Cout;
+    double* Jp = J;
+    if (mem == JSIM_MEM_HOST) {
+        ALLOC(Cd, n * n * cb);
+        ALLOC(Sd, n * sizeof(u64));
+        CK(cudaMemcpyAsync(Cd.p, C, n * n * cb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(Sd.p, sizes, n * sizeof(u64), cudaMemcpyHostToDevice, s));
+        Cp = Cd.p;
+        Sp = Sd.as<u64>();
+        if (Cout) { ALLOC(Co, n * n * cb); Cop = Co.p; }
+        if (J) { ALLOC(Jd, n * n * sizeof(double)); Jp = Jd.as<double>(); }
+    }
+    {
+        StageTimer t(ctx, &ctx->stats.ms_epilogue);
+        // the diagonal is |X_i| (a part's own rows may miss some of it)
+        CK(launch_epilogue(Cp, n, ctx->opt.count_bits, Sp, Cop, Jp, s, 1, ctx->opt.distance));
+        ctx->stats.launches += 1;
+    }
+    if (mem == JSIM_MEM_HOST) {
+        if (Cout) CK(cudaMemcpyAsync(Cout, Cop, n * n * cb, cudaMemcpyDeviceToHost, s));
+        if (J) CK(cudaMemcpyAsync(J, Jp, n * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
     return JSIM_OK;
 }
 

@@ -40,6 +40,15 @@ class Sets(ctypes.Structure):
                 ("mem", ctypes.c_int)]
 
 
+def partition_batches(minid: int, maxid: int, batch_rows: int, parts: int):
+    """The row batches [begin, end) (batch index = value // batch_rows) of each
+    part of jsim_all_pairs_part: the nb batches between the first and last
+    value cut into `parts` contiguous runs."""
+    first = minid // batch_rows
+    nb = maxid // batch_rows - first + 1
+    return [(first + nb * p // parts, first + nb * (p + 1) // parts) for p in range(parts)]
+
+
 class Checkpoint(ctypes.Structure):
     _fields_ = [("path", ctypes.c_char_p), ("every", ctypes.c_uint32), ("max_supers", ctypes.c_uint32),
                 ("resume", ctypes.c_int)]
@@ -121,6 +130,10 @@ SIGNATURES = {
     "jsim_request_free": (None, [ctypes.c_void_p]),
     "jsim_topk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_int]),
+    "jsim_all_pairs_part": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Sets), ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "jsim_finish": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "jsim_threshold": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _u64p,
                                       ctypes.c_int]),
@@ -295,6 +308,36 @@ class Context:
                                       MEM_DEVICE if dev_out else MEM_HOST)
         _check(rc, self._h)
         return C, sizes, J
+
+    def all_pairs_part(self, offsets, ids, part: int, parts: int, out_device=None):
+        """(C, sizes): the counts of part `part` of `parts` of the collection's
+        row batches (see jsim_all_pairs_part); sum C over the parts and call
+        finish()."""
+        s, keep, is_dev = self._sets(offsets, ids)
+        dev_out = is_dev if out_device is None else out_device
+        C, sizes, _ = self._outputs(s.n, dev_out, True, True, False)
+        self._order()
+        rc = self._lib.jsim_all_pairs_part(self._h, ctypes.byref(s), int(part), int(parts), self._ptr(C),
+                                           self._ptr(sizes), MEM_DEVICE if dev_out else MEM_HOST)
+        _check(rc, self._h)
+        return C, sizes
+
+    def finish(self, C, sizes, want_C=True, want_J=True):
+        """(C, J) from summed part counts and the sizes (jsim_finish); device
+        tensors in, device tensors out."""
+        torch = _torch()
+        is_dev = isinstance(C, torch.Tensor) and C.is_cuda
+        n = int(C.shape[0])
+        if not is_dev:
+            cdt = np.uint64 if self.count_bits == 64 else np.uint32
+            C = np.ascontiguousarray(C, dtype=cdt)
+            sizes = np.ascontiguousarray(sizes, dtype=np.uint64)
+        Co, _, J = self._outputs(n, is_dev, want_C, False, want_J)
+        self._order()
+        rc = self._lib.jsim_finish(self._h, n, self._ptr(C), self._ptr(sizes), self._ptr(Co), self._ptr(J),
+                                   MEM_DEVICE if is_dev else MEM_HOST)
+        _check(rc, self._h)
+        return Co, J
 
     def _outputs(self, n, dev_out, want_C, want_sizes, want_J):
         torch = _torch()

@@ -314,3 +314,42 @@ def test_useful_work_count(gpu, c1, filter_min):
     with jsim.Context(batch_rows=mt, filter_min=filter_min) as ctx:
         ctx.all_pairs(*c1)
         assert ctx.stats()["bitops_useful"] == 0.0
+
+
+@pytest.mark.parametrize("filter_min", [1, 2])
+def test_split_contraction_parts_sum_to_the_whole(gpu, c1, c1_ref, filter_min):
+    """jsim_all_pairs_part over 1, 2, 3 and 5 parts (emulating that many
+    devices one after the other), summed on the host and finished, gives the
+    oracle's C and J bit for bit; a part past the last batch counts nothing."""
+    with jsim.Context(batch_rows=1 << 14, filter_min=filter_min) as ctx:
+        for parts in (1, 2, 3, 5):
+            acc = None
+            for p in range(parts):
+                Cp, sp = ctx.all_pairs_part(*c1, p, parts)
+                np.testing.assert_array_equal(sp, c1_ref[1])
+                acc = Cp.astype(np.uint64) if acc is None else acc + Cp.astype(np.uint64)
+            C, J = ctx.finish(acc.astype(np.uint32), sp)
+            assert_same((C, sp, J), c1_ref)
+        # more parts than batches (64 here): part 0 of 200 holds none
+        Cp, _ = ctx.all_pairs_part(*c1, 0, 200)
+        assert not Cp.any()
+
+
+def test_split_contraction_device(gpu):
+    import torch
+    off, ids = synth.clade1024(n=130, median=2e4)
+    ref = oracle.all_pairs(off, ids)
+    d_off = torch.from_numpy(off.view(np.int64)).cuda()
+    d_ids = torch.from_numpy(ids.view(np.int64)).cuda()
+    with jsim.Context(id_bits=32, count_bits=64) as ctx:
+        acc = None
+        for p in range(4):
+            Cp, sp = ctx.all_pairs_part(d_off, d_ids, p, 4)
+            Ci = Cp.view(torch.int64)  # the same bits; the sums stay below 2^63
+            acc = Ci.clone() if acc is None else acc + Ci
+        C, J = ctx.finish(acc, sp)
+        torch.cuda.synchronize()
+        assert_same((to_np(C), to_np(sp), J.cpu().numpy()), ref)
+    with jsim.Context() as ctx:
+        with pytest.raises(jsim.JsimError):
+            ctx.all_pairs_part(off, ids, 4, 4)
