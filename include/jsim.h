@@ -170,7 +170,7 @@ JSIM_API void jsim_destroy(jsim_ctx* ctx);
  *   sizes n entries, or NULL
  *   J     n*n row-major binary64, or NULL
  *   out_mem: JSIM_MEM_HOST or JSIM_MEM_DEVICE for all three outputs.
- * Host input of more than 1 GiB of values runs as jsim_all_pairs_streamed
+ * Host input of more than 4 GiB of values runs as jsim_all_pairs_streamed
  * with 1 GiB staging (copies overlap the device's work; same results, the
  * statistics count super-batches).
  * Errors: JSIM_ERR_ARG, JSIM_ERR_UNSORTED, JSIM_ERR_ID_RANGE, JSIM_ERR_OVERFLOW

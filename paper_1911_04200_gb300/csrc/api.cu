@@ -180,13 +180,16 @@ void jsim_destroy(jsim_ctx* ctx)
     delete ctx;
 }
 
-// Host input above this many bytes of values goes through the streamed call
-// (super-batches of this size, copies overlapping the device's work) instead
-// of one copy before the batch loop.  Measured on 1024 clade samples (10.5 GB
-// of pinned host values): one copy then the batch loop 256 ms per call;
-// streamed through 256 MiB / 512 MiB / 1 GiB / 2 GiB staging 276 / 238 /
-// 228 / 261 ms; the device-resident call 207 ms.
+// Host input above kHostStreamMin bytes of values goes through the streamed
+// call (super-batches of kHostStreamBytes, copies overlapping the device's
+// work) instead of one copy before the batch loop.  Measured on 1024 clade
+// samples (10.5 GB of pinned host values): one copy then the batch loop 256
+// ms per call; streamed through 256 MiB / 512 MiB / 1 GiB / 2 GiB staging
+// 276 / 238 / 228 / 261 ms; the device-resident call 207 ms.  For 2048
+// samples of 1.6 GB the streamed call was slower (260 against 189 ms with a
+// fresh context: the pinned staging is allocated on first use).
 constexpr u64 kHostStreamBytes = 1ull << 30;
+constexpr u64 kHostStreamMin = 4ull << 30;
 
 namespace {
 
@@ -303,7 +306,7 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
     if (rc) return rc;
     if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
     if (sets->mem == JSIM_MEM_HOST && sets->n > 0 && sets->offsets[sets->n] >= sets->offsets[0] &&
-        (sets->offsets[sets->n] - sets->offsets[0]) * sizeof(u64) > kHostStreamBytes)
+        (sets->offsets[sets->n] - sets->offsets[0]) * sizeof(u64) > kHostStreamMin)
         return jsim_all_pairs_streamed(ctx, sets, C, sizes, J, out_mem, kHostStreamBytes);
     return all_pairs_impl(ctx, sets, C, sizes, J, out_mem, 0, 1, false);
 }

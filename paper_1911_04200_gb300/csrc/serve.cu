@@ -19,6 +19,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <functional>
 #include <mutex>
 #include <memory>
 #include <thread>
@@ -66,6 +67,8 @@ struct Slot {
 
 }  // namespace
 
+struct GatherPool;
+
 struct jsim_index {
     jsim_ctx* ctx = nullptr;
     jsim_serve_options opt{};
@@ -81,6 +84,8 @@ struct jsim_index {
     bool stop = false;
     jsim_serve_stats stats{};
     int device = 0, sms = 0, count_bits = 32, distance = 0;
+    std::unique_ptr<GatherPool> gather;  // host threads that gather query values
+    ~jsim_index();
 };
 
 namespace {
@@ -118,14 +123,76 @@ OutLayout out_layout(u64 S, u64 n_ref, size_t cb)
     return o;
 }
 
-// Build-time tuning: host threads that gather a batch's query values.
-// Measured on the 2048-sample reference at full size (capacity, requests/s;
-// 2 / 3 / 4 slots): 8 threads 200 / 217 / 224, 16 threads 209 / 253 / 253.
+// Build-time tuning: host threads that gather a batch's query values (the
+// server thread and JSIM_GATHER_THREADS - 1 pool threads started with the
+// index) and the batch size below which one thread copies alone.
 #ifndef JSIM_GATHER_THREADS
 #define JSIM_GATHER_THREADS 16
 #endif
+#ifndef JSIM_GATHER_MIN_PER_THREAD
+#define JSIM_GATHER_MIN_PER_THREAD (1u << 18)
+#endif
 
-void gather_values(const std::vector<jsim_request*>& reqs, u64* dst)
+}  // namespace
+
+// Threads that copy parts of a batch's query values, started with the index
+// and idle between batches (no thread start per batch).
+struct GatherPool {
+    std::vector<std::thread> th;
+    std::mutex mu;
+    std::condition_variable cv, cv_done;
+    std::function<void(unsigned)> job;
+    unsigned parts = 0, next = 0, done = 0;
+    bool stop = false;
+    void start(unsigned n)
+    {
+        for (unsigned t = 0; t < n; ++t) th.emplace_back([this] { loop(); });
+    }
+    void loop()
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv.wait(lk, [&] { return stop || next < parts; });
+            if (stop) return;
+            const unsigned p = next++;
+            lk.unlock();
+            job(p);
+            lk.lock();
+            if (++done == parts) cv_done.notify_all();
+        }
+    }
+    // run f(0) .. f(parts - 1), part 0 on the calling thread
+    void run(unsigned nparts, const std::function<void(unsigned)>& f)
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            job = f;
+            parts = nparts;
+            next = 1;
+            done = 0;
+        }
+        cv.notify_all();
+        f(0);
+        std::unique_lock<std::mutex> lk(mu);
+        if (++done != parts) cv_done.wait(lk, [&] { return done == parts; });
+        parts = next = 0;
+    }
+    ~GatherPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        for (auto& t : th) t.join();
+    }
+};
+
+jsim_index::~jsim_index() = default;
+
+namespace {
+
+void gather_values(GatherPool& pool, const std::vector<jsim_request*>& reqs, u64* dst)
 {
     u64 total = 0;
     for (auto* r : reqs) total += r->nvals;
@@ -136,8 +203,8 @@ void gather_values(const std::vector<jsim_request*>& reqs, u64* dst)
         if (r->nvals) pieces.push_back({r->ids, dst + at, r->nvals});
         at += r->nvals;
     }
-    unsigned nt = std::max(1u, std::min((unsigned)JSIM_GATHER_THREADS, std::thread::hardware_concurrency()));
-    if (total < (1u << 20)) nt = 1;
+    const u64 want = std::max<u64>(1, total / JSIM_GATHER_MIN_PER_THREAD);
+    const unsigned nt = (unsigned)std::min<u64>(want, pool.th.size() + 1);
     // split every piece into nt parts so one large request is copied in parallel
     auto work = [&](unsigned t) {
         for (auto& p : pieces) {
@@ -145,10 +212,11 @@ void gather_values(const std::vector<jsim_request*>& reqs, u64* dst)
             if (b > a) memcpy(p.dst + a, p.src + a, (b - a) * sizeof(u64));
         }
     };
-    if (nt == 1) { work(0); return; }
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; ++t) th.emplace_back(work, t);
-    for (auto& x : th) x.join();
+    if (nt == 1) {
+        work(0);
+        return;
+    }
+    pool.run(nt, work);
 }
 
 // Launch one batch on a free slot (worker thread; the slot's pinned input is
@@ -169,7 +237,7 @@ int launch_batch(jsim_index* ix, Slot& sl)
         at += r->nvals;
     }
     off[S] = V;
-    gather_values(sl.reqs, sl.pin_in + head);
+    gather_values(*ix->gather, sl.reqs, sl.pin_in + head);
     cudaStream_t st = sl.st;
     const u64* d_off = sl.din.as<u64>();
     const u64* d_ids = sl.din.as<u64>() + head;
@@ -448,6 +516,8 @@ int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_serve_optio
         ALLOC(sl.Jd, S * n * sizeof(double));
     }
     CK(cudaStreamSynchronize(cs));
+    ix->gather.reset(new GatherPool);
+    ix->gather->start(std::max(1u, std::min((unsigned)JSIM_GATHER_THREADS, std::thread::hardware_concurrency())) - 1);
     ix->worker = std::thread(worker_main, ix);
     *out = ix;
     ix = nullptr;  // the guard keeps it
