@@ -387,7 +387,15 @@ def run_streamed(args):
     J_s = hJ.copy()
     plain = os.environ.get("JSIM_STREAM_PLAIN", "1") != "0"
     if plain:
-        dt_p, st_p, _ = timed(lambda: ctx.all_pairs(off, ids, out=(hC, hS, hJ)))
+        # the plain form: one copy of all values to the device, then the batch
+        # loop (jsim_all_pairs itself streams host input this large)
+        dev = torch.device("cuda", 0)
+
+        def plain_call():
+            d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+            d_ids = torch.from_numpy(ids.view(np.int64)).to(dev)
+            ctx.all_pairs(d_off, d_ids, out=(hC, hS, hJ), out_device=False)
+        dt_p, st_p, _ = timed(plain_call)
         assert np.array_equal(J_s.view(np.uint64), hJ.view(np.uint64)), "streamed and plain results differ"
     bitops = st_s["bitops_dense"]
     variant = st_s["variant"]
@@ -411,7 +419,8 @@ def run_streamed(args):
             "e2e": {"value": bitops / dt_s / 1e12, "unit": UNIT, "h2d_bytes_per_step": int(N * 8 + (n + 1) * 8),
                     "d2h_bytes_per_step": int(n * n * 16 + n * 8)},
             "plain": {"value": bitops / dt_p / 1e12, "ms_per_step": dt_p * 1e3, "batches": st_p["batches"],
-                      "how": "one jsim_all_pairs call on the same pageable host input and host outputs",
+                      "how": "one copy of the pageable host input to the device, then one jsim_all_pairs "
+                             "call (host outputs)",
                       "stage_ms": {k: round(st_p[k], 3) for k in stages}} if plain else None,
             "speedup_vs_plain": dt_p / dt_s if plain else None}
     print(json.dumps(line))
