@@ -323,6 +323,9 @@ int ck_read(const char* path, const CkHeader& want, CkHeader& h, std::vector<u64
     return sum.h == stored ? JSIM_OK : JSIM_ERR_CHECKPOINT;
 }
 
+// samples up to which page-locked input is copied one slice per sample
+constexpr u64 kDirectSlicesMax = 16384;
+
 // waits for the copy stream before device buffers that its copies may still
 // write are released (declared after them, so destroyed first)
 struct CopyFence {
@@ -493,15 +496,32 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
 
     // copy super-batch g into device buffer g & 1 once the device has read
     // what that buffer held two super-batches earlier
+    // Page-locked input is copied slice by slice straight from the caller's
+    // memory (DMA, no host gather); pageable input is gathered into the
+    // pinned staging by host threads first.
+    bool direct = false;
+    if (N && n <= kDirectSlicesMax) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, ids) == cudaSuccess && pa.type == cudaMemoryTypeHost) direct = true;
+        cudaGetLastError();
+    }
     auto stage = [&](size_t g) -> int {
         const int k = (int)(g & 1);
         const Super& s = sup[g];
         memcpy(ss->pin[k], s.off.data(), (n + 1) * sizeof(u64));
-        gather(ids, s, ss->pin[k] + head);
+        if (!direct) gather(ids, s, ss->pin[k] + head);
         CK(cudaStreamWaitEvent(xs, ss->released[k], 0));
         cudaEvent_t a = nullptr;
         if (ctx->opt.profile && (a = take_event(ctx))) cudaEventRecord(a, xs);
-        CK(cudaMemcpyAsync(dbuf[k].p, ss->pin[k], (head + s.count) * sizeof(u64), cudaMemcpyHostToDevice, xs));
+        if (direct) {
+            CK(cudaMemcpyAsync(dbuf[k].p, ss->pin[k], head * sizeof(u64), cudaMemcpyHostToDevice, xs));
+            for (u64 i = 0; i < n; ++i)
+                if (s.len[i])
+                    CK(cudaMemcpyAsync(dbuf[k].as<u64>() + head + s.off[i], ids + s.beg[i], s.len[i] * sizeof(u64),
+                                       cudaMemcpyHostToDevice, xs));
+        } else {
+            CK(cudaMemcpyAsync(dbuf[k].p, ss->pin[k], (head + s.count) * sizeof(u64), cudaMemcpyHostToDevice, xs));
+        }
         if (a) {
             cudaEvent_t b = take_event(ctx);
             if (b) {

@@ -216,3 +216,19 @@ def test_checkpoint_mismatch_corruption_and_errors(gpu, c1, c1_ref, tmp_path):
         with pytest.raises(jsim.JsimError) as e:
             run_to_end(ctx, bad_c, str(tmp_path / "bad.bin"), MIB, step=1)
         assert e.value.name == "JSIM_ERR_UNSORTED"
+
+
+def test_streamed_page_locked_input_copies_slices_directly(gpu, c1, c1_ref):
+    """Page-locked input takes the direct path (one copy per sample slice, no
+    host gather); results are the oracle's, with several super-batches."""
+    import torch
+    off, ids = c1
+    pin = torch.empty(len(ids), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    pin[:] = ids
+    poff = torch.empty(len(off), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    poff[:] = off
+    for batch_rows, staging in ((1 << 14, MIB), (0, 64 * MIB)):
+        with jsim.Context(batch_rows=batch_rows) as ctx:
+            assert_same(ctx.all_pairs_streamed(poff, pin, staging_bytes=staging), c1_ref)
+    with jsim.Context(batch_rows=1 << 14, filter_min=2) as ctx:
+        assert_same(ctx.all_pairs_streamed(poff, pin, staging_bytes=MIB), c1_ref)
