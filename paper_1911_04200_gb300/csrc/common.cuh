@@ -15,6 +15,8 @@ constexpr u64 kChunk = 4096;
 constexpr u64 kScanBlockWords = 4096;
 // Row granularity of the packed matrix; every product tile is a multiple of it.
 constexpr u64 kRowPad = 128;
+// Devices for which launch-shape caches are kept (higher ordinals recompute).
+constexpr int kMaxDevices = 64;
 // Word granularity of a packed row (K padding of every product variant).
 constexpr u64 kWordPad = 64;
 

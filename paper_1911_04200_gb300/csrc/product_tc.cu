@@ -570,7 +570,9 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
 long long wait_budget(int timeout_ms)
 {
     int clk_khz = 0;
-    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, 0);
+    int clk_dev = 0;
+    cudaGetDevice(&clk_dev);
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, clk_dev);
     return (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * (long long)timeout_ms / 1000LL;
 }
 

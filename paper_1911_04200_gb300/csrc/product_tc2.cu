@@ -39,6 +39,7 @@
 // plus a CTA-wide abort flag); on time-out the CTA raises the error word,
 // waits (bounded) for the MMAs already issued, and both CTAs meet at a
 // cluster barrier before TMEM is freed and the CTAs exit.
+#include <atomic>
 #include <algorithm>
 #include "common.cuh"
 
@@ -578,7 +579,10 @@ cudaError_t run(ProductArgs& a, cudaStream_t st)
     if (e != cudaSuccess) return e;
     // as many clusters as can be resident at once (a GPC with an odd number
     // of free SMs leaves one unused), so no cluster waits for another's SMs
-    static int resident = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static std::atomic<int> resident_by_dev[kMaxDevices];
+    int resident = dev < kMaxDevices ? resident_by_dev[dev].load(std::memory_order_relaxed) : 0;
     if (resident == 0) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -597,10 +601,11 @@ cudaError_t run(ProductArgs& a, cudaStream_t st)
             nc = a.sms / 2;
         }
         resident = nc;
+        if (dev < kMaxDevices) resident_by_dev[dev].store(nc, std::memory_order_relaxed);
     }
     const u64 clusters = std::min<u64>((u64)std::min(resident, a.sms / 2), total);
     int clk_khz = 0;
-    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, 0);
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
     long long budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * (long long)a.timeout_ms / 1000LL;
     const int vec16 = ((uintptr_t)a.X % 16 == 0 && a.stride % 2 == 0) ? 1 : 0;
     k_prod_tc2<CT><<<(unsigned)(2 * clusters), kThreads, kSmemBytes, st>>>(a.X, a.stride, a.n, a.W, tiles, L,

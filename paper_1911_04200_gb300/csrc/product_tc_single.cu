@@ -521,7 +521,9 @@ cudaError_t run(ProductArgs& a, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(k_prod_tc1<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     int clk_khz = 0;
-    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, 0);
+    int clk_dev = 0;
+    cudaGetDevice(&clk_dev);
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, clk_dev);
     long long budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * (long long)a.timeout_ms / 1000LL;
     // 16-byte loads when every stage's two words are 16-byte aligned
     const int vec16 = ((uintptr_t)a.X % 16 == 0 && a.stride % 2 == 0) ? 1 : 0;

@@ -28,6 +28,7 @@
 //   k_qepi       J = C / (|Q_s| + |S_j| - C) in binary64 (Sec. II-A), or
 //                the distance 1.0 - J.
 #include <algorithm>
+#include <atomic>
 #include "ingest_dev.cuh"
 
 namespace jsim {
@@ -341,11 +342,15 @@ cudaError_t launch_qrows_kw(const u64* ids, u64 S, Plan plan, u64 values, const 
 {
     // one wave of resident blocks, fewer when the batch gives a warp less
     // than two rounds of values
-    static int per_sm = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static std::atomic<int> per_sm_by_dev[kMaxDevices];
+    int per_sm = dev < kMaxDevices ? per_sm_by_dev[dev].load(std::memory_order_relaxed) : 0;
     if (!per_sm) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qrows<KW>, kQThreads, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
+        if (dev < kMaxDevices) per_sm_by_dev[dev].store(per_sm, std::memory_order_relaxed);
     }
     const u64 want = (values + 2 * kQRound * kQWarps - 1) / (2 * kQRound * kQWarps);
     const u64 blocks = std::max<u64>(1, std::min<u64>(want, (u64)sms * per_sm));
