@@ -120,3 +120,44 @@ def test_batched_recipe_full_size_subset(gpu):
         outs = ctx.all_pairs_batched(cols)
     for (off, ids), (C, s, J) in zip(cols, outs):
         check_sampled(off, ids, C, s, J, pairs=128)
+
+
+@pytest.mark.timeout(1200)
+def test_serving_full_size_sampled(gpu):
+    """The serving workload at full size (2048 reference samples of median
+    1e6 values: a 171 GB resident index): one request of 6 query samples,
+    whose counts and J against 48 sampled reference samples are merged by
+    the oracle; invariants over every reference column."""
+    roff, rids = synth.serving_reference()
+    qoff, qids = synth.serving_queries(0, 6)
+    n_ref = len(roff) - 1
+    with jsim.Context(id_bits=32) as ctx:
+        with jsim.Index(ctx, roff, rids, max_batch_samples=64, max_batch_values=int(qoff[-1])) as ix:
+            r = ix.submit(qoff, qids)
+            C, qs, J = r.wait()
+            r.free()
+            rsz = ix.ref_sizes()
+    C = C.astype(np.uint64)
+    np.testing.assert_array_equal(qs, oracle.sizes_of(qoff, qids))
+    assert np.all(C <= np.minimum(qs[:, None], np.asarray(rsz, dtype=np.uint64)[None, :]))
+    assert np.all((J >= 0.0) & (J <= 1.0))
+    cols = np.sort(np.random.default_rng(9).choice(n_ref, 48, replace=False))
+    segs = [rids[int(roff[j]):int(roff[j + 1])] for j in cols]
+    soff = np.zeros(len(segs) + 1, dtype=np.uint64)
+    soff[1:] = np.cumsum([len(s) for s in segs])
+    Co, qso, Jo = oracle.cross(qoff, qids, soff, np.concatenate(segs))
+    np.testing.assert_array_equal(C[:, cols], Co)
+    np.testing.assert_array_equal(J[:, cols].view(np.uint64), Jo.view(np.uint64))
+
+
+@pytest.mark.timeout(1800)
+def test_streamed_full_size_sampled(gpu):
+    """The out-of-HBM workload at full size (4096 samples, median 2e6 values
+    in [0, 2^40), about 1.1e10 values = 88 GB of host memory, 64-bit counts)
+    through the streamed call with the benchmark's 1 GiB staging: sampled
+    pairs against the oracle's merges, and the invariants over the whole
+    matrix."""
+    off, ids = synth.clade4096()
+    with jsim.Context(count_bits=64, id_bits=40) as ctx:
+        C, s, J = ctx.all_pairs_streamed(off, ids, staging_bytes=1 << 30)
+    check_sampled(off, ids, C, s, J, pairs=128)
