@@ -282,7 +282,7 @@ def run_batched(args):
     cols = synth.batched_collections(median=median, lo=1e4, hi=5e6)
     dcols = [(torch.from_numpy(o.view(np.int64)).to(dev), torch.from_numpy(i.view(np.int64)).to(dev)) for o, i in cols]
     N = sum(int(o[-1]) for o, _ in cols)
-    ctx = jsim.Context(device=0, id_bits=32, profile=False)
+    ctx = jsim.Context(device=0, id_bits=32, profile=False, batch_rows=args.batch_rows)
     # preallocated outputs so the captured graph is replayed every step
     import ctypes
     k = len(dcols)

@@ -433,14 +433,14 @@ replan:
     for (auto& x : w.cols) {
         x.empty = x.N == 0;
         const u64 span = x.empty ? 0 : x.maxid - x.minid;
-        // one row batch per collection when its filter bitmap fits in 512 MiB:
-        // a batched call is dominated by per-batch launches of small
-        // collections, not by the bitmap's L2 residency
+        // batches of up to 2^29 rows (a 64 MiB filter bitmap): fewer, longer
+        // batches than the plain call's 2^28, since a batched call pays per
+        // batch launches for many small collections.  Measured on 200
+        // collections spanning [0, 2^32) (ms per call, rows per batch 2^26 /
+        // 2^28 / 2^29 / 2^30 / 2^31 / 2^32): 385 / 247 / 234 / 237 / 254 / 272
         u64 one = 64;
-        while (one < span + 1 && one < (1ull << 32)) one <<= 1;
-        const bool fits = span < (1ull << 32);
-        x.mt = ctx->opt.batch_rows ? ctx->opt.batch_rows
-                                   : (fits ? one : auto_batch_rows(span + 1 ? span + 1 : ~0ull));
+        while (one < span + 1 && one < (1ull << 29)) one <<= 1;
+        x.mt = ctx->opt.batch_rows ? ctx->opt.batch_rows : one;
         x.lo0 = x.empty ? 0 : x.minid / x.mt * x.mt;
         x.rounds = x.empty ? 0 : x.maxid / x.mt - x.minid / x.mt + 1;
         if (x.rounds > 4096) return JSIM_ERR_UNSUPPORTED;  // value span too wide for one batched plan
