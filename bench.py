@@ -30,6 +30,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -129,11 +130,16 @@ class Clocks:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device)
+        # samples go to a scratch file; the JSON line carries their summary
+        # (JSIM_CLOCKS_CSV keeps them at a chosen path)
+        self.path = os.environ.get("JSIM_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), "jsim_clocks_%d_rank%d.csv" % (os.getpid(), device))
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            d = os.path.dirname(self.path)
+            if d:
+                os.makedirs(d, exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
