@@ -16,6 +16,8 @@
  *   c_ij = |X_i| + |X_j| - b_ij           (union by inclusion-exclusion)
  *   s_ij = b_ij / c_ij    in IEEE binary64, round-to-nearest (Eq. 2);
  *                         s_ij = 1 when both sets are empty (Sec. II-A)
+ *   d_ij = 1.0 - s_ij     the Jaccard distance (Sec. II-A), one binary64
+ *                         subtraction
  *
  * Inputs are sample value lists sorted ascending (the paper's samples are
  * sorted numeric files, Sec. IV); equal adjacent values are one set element.
