@@ -260,8 +260,9 @@ JSIM_API int jsim_all_pairs_streamed(jsim_ctx* ctx, const jsim_sets* sets, void*
                                      int out_mem, uint64_t staging_bytes);
 
 /* Checkpoint/resume of a streamed call (progress is kept after whole
- * super-batches: the counts C accumulated so far, the sizes, the input-error
- * flags and the statistics). */
+ * super-batches: the counts C accumulated so far - a sum over batches, Eq. 4,
+ * so the remaining super-batches can be added later - the sizes, the
+ * input-error flags and the statistics). */
 typedef struct {
     const char* path;     /* checkpoint file; written as path + ".tmp", then renamed */
     uint32_t every;       /* write it after every `every` super-batches (0: only when stopping) */
