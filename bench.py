@@ -76,6 +76,33 @@ def dist_env():
     return world, rank, local
 
 
+def bind_near_gpu(device):
+    """Restrict this process to the host CPUs next to the GPU (its NUMA
+    node, from sysfs), so that pinned host buffers, allocated after this,
+    sit in the memory closest to the GPU.  Best effort: unchanged when sysfs
+    says nothing or the sets do not meet."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(device)
+        bdf = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/local_cpulist" % bdf) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        near = cpus & os.sched_getaffinity(0)
+        if near and near != os.sched_getaffinity(0):
+            os.sched_setaffinity(0, near)
+            return sorted(near)
+    except Exception:
+        pass
+    return None
+
+
 def aggregate_over_ranks(ms, work, device=None):
     """Whole-job timing over ranks: the slowest rank's time and the summed
     work (units every rank processed), one all-reduce each; identity on one
@@ -628,6 +655,7 @@ def run_jsim(args):
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    bound = bind_near_gpu(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
@@ -719,6 +747,7 @@ def run_jsim(args):
                 "compulsory_bytes_per_step": compulsory,
                 "parallelism": "dp%d (independent problems)" % world,
                 "l2": "inputs (%.1f GB of values) larger than L2 (129 MB); no flush" % (N * 8 / 1e9),
+                "host_cpus": "bound to the GPU's NUMA node (%d CPUs)" % len(bound) if bound else "unbound",
                 "stage_ms": {k: round(last[k], 3) for k in ("ms_validate", "ms_filter", "ms_scan", "ms_pack",
                                                             "ms_product", "ms_epilogue")}})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
