@@ -58,8 +58,12 @@ namespace {
 #ifndef JSIM_TC2_BUFS
 #define JSIM_TC2_BUFS 3
 #endif
+// Stages of packed words each producer holds in registers ahead of its
+// unpacking (Tbit-ops/s at n = 1024 / 2048 / 4096 / 10,000; 4 ahead:
+// 1068 / 1206 / 1241 / 1258, 6: 1064 / 1203 / 1261 / 1287, 8: 1070 / 1203 /
+// 1272 / 1289; 2: 983 at n = 1024).
 #ifndef JSIM_TC2_AHEAD
-#define JSIM_TC2_AHEAD 4
+#define JSIM_TC2_AHEAD 8
 #endif
 // L2 window shared by all clusters: JSIM_TC2_WINDOW_MIB of packed words of
 // all rows, but at least JSIM_TC2_MIN_STAGES stages per chunk.  Every tile
