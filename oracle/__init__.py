@@ -14,6 +14,11 @@ Two oracles live here, both written from arXiv 1911.04200:
   sorted lists, union by inclusion-exclusion and the binary64 quotient
   (Sec. II-A, Sec. III-A, Eq. 2), and the Jaccard distance as the binary64
   subtraction 1.0 - J (Sec. II-A).
+* ``oracle_rows_range`` in the same file counts the intersections by the
+  other plain reading of B = A^T A (Sec. III-A): the sum over values x of
+  the outer product of x's 0/1 row, restricted to a value range.  Counts
+  over disjoint ranges add up (Eq. 4), so collections larger than memory
+  are counted range by range (``rows_range`` below).
 * ``packed.py`` follows the paper's batched method step by step in numpy:
   row batches (Eq. 3), the zero-row filter (Eq. 5), its prefix sum and the
   compacted rows (Eq. 6), b-bit bitmask words and the AND+popcount product
@@ -72,6 +77,11 @@ def _load():
             lib.oracle_jaccard.argtypes = [ctypes.c_uint64] * 3
             lib.oracle_distance.restype = ctypes.c_double
             lib.oracle_distance.argtypes = [ctypes.c_uint64] * 3
+            lib.oracle_jaccard_matrix.restype = None
+            lib.oracle_jaccard_matrix.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p, _u64p, _f64p]
+            lib.oracle_rows_range.restype = ctypes.c_int
+            lib.oracle_rows_range.argtypes = [ctypes.c_uint64, _u64p, _u64p, ctypes.c_uint64, ctypes.c_uint64,
+                                              ctypes.c_uint64, _u64p, ctypes.c_int]
             lib.oracle_distance_matrix.restype = None
             lib.oracle_distance_matrix.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p, _u64p, _f64p]
             lib.oracle_all_pairs.restype = None
@@ -185,3 +195,43 @@ def cross(qoffsets, qids, roffsets, rids, threads: int | None = None):
     _load().oracle_cross(nq, _p64(qoffsets), _p64(qids), nr, _p64(roffsets), _p64(rids),
                          _p64(C), _p64(qs), _pf(J), threads or default_threads())
     return C, qs, J
+
+
+def jaccard_matrix(C, srow, scol):
+    """J of a count matrix C (rows x cols) with the row and column samples'
+    sizes, each entry by ``jaccard``."""
+    C, srow, scol = _u64(C), _u64(srow), _u64(scol)
+    nr, nc = C.shape
+    J = np.zeros((nr, nc), dtype=np.float64)
+    if nr and nc:
+        _load().oracle_jaccard_matrix(nr, nc, _p64(C), _p64(srow), _p64(scol), _pf(J))
+    return J
+
+
+def rows_range(offsets, ids, lo: int, hi: int, C=None, pieces: int | None = None,
+               threads: int | None = None):
+    """Add to the upper triangle (i <= j) of C (uint64 n*n, created when None)
+    the number of values of [lo, hi) that samples i and j both hold, counted
+    row by row of the indicator matrix; returns C.  Calls over disjoint
+    ranges add up to the whole counts (the diagonal to the sizes)."""
+    offsets, ids = _u64(offsets), _u64(ids)
+    n = offsets.size - 1
+    if C is None:
+        C = np.zeros((n, n), dtype=np.uint64)
+    assert C.dtype == np.uint64 and C.shape == (n, n) and C.flags.c_contiguous
+    if ids.size == 0:
+        ids = np.zeros(1, dtype=np.uint64)
+    t = threads or default_threads()
+    if pieces is None:
+        pieces = max(1, min(hi - lo, 64 * t))
+    rc = _load().oracle_rows_range(n, _p64(offsets), _p64(ids), lo, hi, pieces, _p64(C), t)
+    if rc != 0:
+        raise MemoryError("oracle_rows_range: allocation failed")
+    return C
+
+
+def finish_upper(Cu, sizes):
+    """Mirror an upper-triangle count matrix and form J: (C n*n, J n*n)."""
+    Cu = _u64(Cu)
+    C = np.triu(Cu) + np.triu(Cu, 1).T
+    return C, jaccard_matrix(C, sizes, sizes)

@@ -22,9 +22,15 @@
  * Inputs are sample value lists sorted ascending (the paper's samples are
  * sorted numeric files, Sec. IV); equal adjacent values are one set element.
  * There is no blocking, no packing and no reordering: every pair is merged.
+ *
+ * For collections too large to merge pair by pair in memory, b_ij is also
+ * given by its other plain reading, B = A^T A summed over the rows of the
+ * indicator matrix (oracle_rows_range below), restricted to a value range so
+ * that disjoint ranges add up (Eq. 4).
  */
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
 
 /* Number of distinct values in a sorted list (|X|, Sec. II-A). */
 uint64_t oracle_distinct(const uint64_t* a, uint64_t na)
@@ -70,6 +76,14 @@ double oracle_jaccard(uint64_t inter, uint64_t size_x, uint64_t size_y)
 double oracle_distance(uint64_t inter, uint64_t size_x, uint64_t size_y)
 {
     return 1.0 - oracle_jaccard(inter, size_x, size_y);
+}
+
+/* J[r][c] = oracle_jaccard(C[r][c], srow[r], scol[c]) for an nr x nc matrix. */
+void oracle_jaccard_matrix(uint64_t nr, uint64_t nc, const uint64_t* C, const uint64_t* srow,
+                           const uint64_t* scol, double* J)
+{
+    for (uint64_t r = 0; r < nr; ++r)
+        for (uint64_t c = 0; c < nc; ++c) J[r * nc + c] = oracle_jaccard(C[r * nc + c], srow[r], scol[c]);
 }
 
 /* D[r][c] = oracle_distance(C[r][c], srow[r], scol[c]) for an nr x nc matrix. */
@@ -159,4 +173,120 @@ void oracle_cross(uint64_t nq, const uint64_t* qoff, const uint64_t* qids,
             if (J) J[(uint64_t)q * nr + r] = oracle_jaccard(inter, sq, oracle_distinct(b, nb));
         }
     }
+}
+
+/*
+ * Intersection counts by the rows of the indicator matrix, restricted to the
+ * values of [lo, hi): the plain definition B = A^T A of Sec. III-A read row
+ * by row, B = sum over values x of a_x a_x^T, where a_x is the 0/1 row of
+ * value x (sample i holds x).  Every value x in [lo, hi) adds 1 to C[i][j]
+ * for every pair i <= j of samples that both hold x (i = j included, so the
+ * diagonal gains |X_i restricted to the range|).  C is additive over any
+ * partition of the values into ranges (Eq. 4), so the counts of a
+ * collection too large for memory are the sum of calls over disjoint ranges.
+ *
+ * C is n*n row-major uint64; only the upper triangle (i <= j) is added to.
+ * The range is cut into `pieces` equal stretches of values, processed by
+ * threads in any order (each stretch's counts go into a thread-private
+ * matrix, added into C at the end).  For one stretch: every (value, sample)
+ * membership is listed, the list is sorted by value then sample (qsort),
+ * repeated memberships (duplicate values inside a sample) are one, and each
+ * run of equal values is one row a_x whose pairs are counted.
+ * Returns 0, or -1 when a thread-private matrix cannot be allocated.
+ */
+typedef struct { uint64_t v; uint64_t s; } oracle_member;
+
+static int oracle_member_cmp(const void* pa, const void* pb)
+{
+    const oracle_member* a = (const oracle_member*)pa;
+    const oracle_member* b = (const oracle_member*)pb;
+    if (a->v != b->v) return a->v < b->v ? -1 : 1;
+    if (a->s != b->s) return a->s < b->s ? -1 : 1;
+    return 0;
+}
+
+/* first index k of sorted a[0..na) with a[k] >= x */
+static uint64_t oracle_lower_bound(const uint64_t* a, uint64_t na, uint64_t x)
+{
+    uint64_t lo = 0, hi = na;
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+int oracle_rows_range(uint64_t n, const uint64_t* offsets, const uint64_t* ids,
+                      uint64_t lo, uint64_t hi, uint64_t pieces, uint64_t* C, int threads)
+{
+    if (hi <= lo || n == 0) return 0;
+    if (pieces == 0) pieces = 1;
+    if (pieces > hi - lo) pieces = hi - lo;
+    int nt = threads > 0 ? threads : 1;
+    int failed = 0;
+    #pragma omp parallel num_threads(nt)
+    {
+        uint64_t* Cp = (uint64_t*)calloc(n * n, sizeof(uint64_t));
+        if (!Cp) {
+            #pragma omp atomic write
+            failed = 1;
+        }
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t pc = 0; pc < (int64_t)pieces; ++pc) {
+            if (!Cp) continue;
+            /* stretch [a, b) of the values; the last one ends at hi */
+            uint64_t width = hi - lo;
+            uint64_t a = lo + (uint64_t)(((unsigned __int128)width * (uint64_t)pc) / pieces);
+            uint64_t b = lo + (uint64_t)(((unsigned __int128)width * (uint64_t)(pc + 1)) / pieces);
+            uint64_t total = 0;
+            for (uint64_t i = 0; i < n; ++i) {
+                const uint64_t* s = ids + offsets[i];
+                uint64_t ns = offsets[i + 1] - offsets[i];
+                total += oracle_lower_bound(s, ns, b) - oracle_lower_bound(s, ns, a);
+            }
+            if (total == 0) continue;
+            oracle_member* m = (oracle_member*)malloc(total * sizeof(oracle_member));
+            if (!m) {
+                #pragma omp atomic write
+                failed = 1;
+                continue;
+            }
+            uint64_t k = 0;
+            for (uint64_t i = 0; i < n; ++i) {
+                const uint64_t* s = ids + offsets[i];
+                uint64_t ns = offsets[i + 1] - offsets[i];
+                uint64_t e = oracle_lower_bound(s, ns, b);
+                for (uint64_t t = oracle_lower_bound(s, ns, a); t < e; ++t) {
+                    m[k].v = s[t];
+                    m[k].s = i;
+                    ++k;
+                }
+            }
+            qsort(m, total, sizeof(oracle_member), oracle_member_cmp);
+            /* drop repeated (value, sample) memberships: a set holds a value once */
+            uint64_t u = 0;
+            for (uint64_t t = 0; t < total; ++t)
+                if (u == 0 || m[t].v != m[u - 1].v || m[t].s != m[u - 1].s) m[u++] = m[t];
+            /* every run of equal values is one row a_x; add a_x a_x^T (i <= j) */
+            for (uint64_t r = 0; r < u;) {
+                uint64_t e = r;
+                while (e < u && m[e].v == m[r].v) ++e;
+                for (uint64_t p = r; p < e; ++p) {
+                    uint64_t* row = Cp + m[p].s * n;
+                    for (uint64_t q = p; q < e; ++q) row[m[q].s] += 1;
+                }
+                r = e;
+            }
+            free(m);
+        }
+        if (Cp) {
+            #pragma omp critical
+            {
+                for (uint64_t i = 0; i < n; ++i)
+                    for (uint64_t j = i; j < n; ++j) C[i * n + j] += Cp[i * n + j];
+            }
+            free(Cp);
+        }
+    }
+    return failed ? -1 : 0;
 }

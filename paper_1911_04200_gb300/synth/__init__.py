@@ -67,6 +67,9 @@ def _load():
             lib.synth_lengths.restype = None
             lib.synth_fill.argtypes = [ctypes.POINTER(_Params), u64p, u64p, u64p]
             lib.synth_fill.restype = None
+            lib.synth_fill_range.argtypes = [ctypes.POINTER(_Params), u64p, ctypes.c_uint64, ctypes.c_uint64,
+                                             u64p, u64p, u64p]
+            lib.synth_fill_range.restype = None
             lib.synth_compact.argtypes = [ctypes.c_uint64, u64p, u64p, u64p, u64p]
             lib.synth_compact.restype = ctypes.c_uint64
             lib.synth_range_distinct.argtypes = [ctypes.c_uint64, u64p, ctypes.c_int, ctypes.c_uint64, u64p]
@@ -79,14 +82,11 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
 
 
-def generate(kind: str, *, n: int, id_bits: int, seed: int, sample_base: int = 0,
-             n_anc: int = 8, anc_size: int = 50_000, u_max: float = 0.6,
-             n_clades: int = 32, core: float = 0.3, median: float = 1e6,
-             sigma: float | None = None, lo: float | None = None, hi: float | None = None,
-             m: int = 0, p: float = 0.0, alloc=None):
-    """Draw one collection.  ``alloc(count) -> uint64 ndarray`` may supply the
-    value buffer (for example pinned host memory); it must hold ``count``
-    entries and the result is a prefix view of it."""
+def _params(kind: str, *, n: int, id_bits: int, seed: int, sample_base: int = 0,
+            n_anc: int = 8, anc_size: int = 50_000, u_max: float = 0.6,
+            n_clades: int = 32, core: float = 0.3, median: float = 1e6,
+            sigma: float | None = None, lo: float | None = None, hi: float | None = None,
+            m: int = 0, p: float = 0.0):
     prob = p
     p = _Params()
     p.kind = {"ancestral": 0, "clade": 1, "bernoulli": 2}[kind]
@@ -105,6 +105,15 @@ def generate(kind: str, *, n: int, id_bits: int, seed: int, sample_base: int = 0
     p.sigma = sigma if sigma is not None else math.log(10.0) / 3.0
     p.lo = lo if lo is not None else median / 10.0
     p.hi = hi if hi is not None else median * 10.0
+    return p
+
+
+def generate(kind: str, *, alloc=None, **kw):
+    """Draw one collection.  ``alloc(count) -> uint64 ndarray`` may supply the
+    value buffer (for example pinned host memory); it must hold ``count``
+    entries and the result is a prefix view of it."""
+    p = _params(kind, **kw)
+    n = p.n
     lib = _load()
     lens = np.zeros(n, dtype=np.uint64)
     if n:
@@ -118,6 +127,29 @@ def generate(kind: str, *, n: int, id_bits: int, seed: int, sample_base: int = 0
     if n:
         lib.synth_fill(ctypes.byref(p), _ptr(slot), _ptr(ids), _ptr(distinct))
         lib.synth_compact(n, _ptr(slot), _ptr(distinct), _ptr(ids), _ptr(offsets))
+    return offsets, ids[:int(offsets[-1])]
+
+
+def generate_range(kind: str, value_lo: int, value_hi: int, **kw):
+    """The collection ``generate(kind, **kw)`` draws, restricted to the values
+    of [value_lo, value_hi): every sample keeps its values inside the range (possibly
+    none).  The restrictions to disjoint ranges that cover the value domain
+    are exactly the pieces of the whole collection, so a collection too large
+    for memory can be visited range by range."""
+    p = _params(kind, **kw)
+    n = p.n
+    lib = _load()
+    lens = np.zeros(n, dtype=np.uint64)
+    counts = np.zeros(n, dtype=np.uint64)
+    offsets = np.zeros(n + 1, dtype=np.uint64)
+    if n == 0:
+        return offsets, np.zeros(0, dtype=np.uint64)
+    lib.synth_lengths(ctypes.byref(p), _ptr(lens))
+    null = ctypes.POINTER(ctypes.c_uint64)()
+    lib.synth_fill_range(ctypes.byref(p), _ptr(lens), value_lo, value_hi, _ptr(counts), null, null)
+    np.cumsum(counts, out=offsets[1:])
+    ids = np.empty(max(int(offsets[-1]), 1), dtype=np.uint64)
+    lib.synth_fill_range(ctypes.byref(p), _ptr(lens), value_lo, value_hi, _ptr(counts), _ptr(offsets), _ptr(ids))
     return offsets, ids[:int(offsets[-1])]
 
 
@@ -144,28 +176,46 @@ def clade1024(seed: int = SEED_BASE + 2, n: int = 1024, median: float = 1e6, all
                     median=median, sigma=SIGMA_DECADE, lo=median / 10, hi=median * 10, alloc=alloc)
 
 
+def batched_collection(k: int, seed: int = SEED_BASE + 3, n_lo: int = 8, n_hi: int = 512,
+                       median: float = 2e5, lo: float = 1e4, hi: float = 5e6, alloc=None):
+    """Collection k of the batched recipe: n ~ U{n_lo..n_hi} samples (a
+    per-collection splitmix64 draw), sizes log-normal (median 2e5, range
+    1e4-5e6, both scaled with the median), values in [0, 2^32), ceil(n/32)
+    clades."""
+    h = (seed * 0x9E3779B97F4A7C15 + k * 0xBF58476D1CE4E5B9) & (2**64 - 1)
+    h ^= h >> 31
+    n = n_lo + (h % (n_hi - n_lo + 1))
+    scale = median / 2e5
+    return generate("clade", n=n, id_bits=32, seed=seed * 1000 + k, n_clades=(n + 31) // 32,
+                    core=0.3, u_max=0.4, median=median, sigma=SIGMA_C3,
+                    lo=lo * scale, hi=hi * scale, alloc=alloc)
+
+
 def batched_collections(seed: int = SEED_BASE + 3, count: int = 200, n_lo: int = 8, n_hi: int = 512,
-                        median: float = 2e5, lo: float = 1e4, hi: float = 5e6):
-    """`count` independent collections with n ~ U{n_lo..n_hi} samples, sizes
-    log-normal (median 2e5, range 1e4-5e6), values in [0, 2^32), ceil(n/32)
-    clades each."""
-    out = []
-    for k in range(count):
-        h = (seed * 0x9E3779B97F4A7C15 + k * 0xBF58476D1CE4E5B9) & (2**64 - 1)
-        h ^= h >> 31
-        n = n_lo + (h % (n_hi - n_lo + 1))
-        scale = median / 2e5
-        out.append(generate("clade", n=n, id_bits=32, seed=seed * 1000 + k, n_clades=(n + 31) // 32,
-                            core=0.3, u_max=0.4, median=median, sigma=SIGMA_C3,
-                            lo=lo * scale, hi=hi * scale))
-    return out
+                        median: float = 2e5, lo: float = 1e4, hi: float = 5e6, first: int = 0):
+    """Collections first .. first+count-1 of the batched recipe (200
+    independent collections with n ~ U{n_lo..n_hi} samples, sizes log-normal
+    (median 2e5, range 1e4-5e6), values in [0, 2^32), ceil(n/32) clades
+    each)."""
+    return [batched_collection(k, seed=seed, n_lo=n_lo, n_hi=n_hi, median=median, lo=lo, hi=hi)
+            for k in range(first, first + count)]
+
+
+def _clade4096_kw(seed, n, median):
+    return dict(n=n, id_bits=40, seed=seed, n_clades=64, core=0.3, u_max=0.4,
+                median=median, sigma=SIGMA_DECADE, lo=median / 10, hi=median * 10)
 
 
 def clade4096(seed: int = SEED_BASE + 4, n: int = 4096, median: float = 2e6, alloc=None):
     """n=4096 samples over [0, 2^40): sizes log-normal (median 2e6, range
     2e5-2e7), 64 clades; about 1e10 values in total."""
-    return generate("clade", n=n, id_bits=40, seed=seed, n_clades=64, core=0.3, u_max=0.4,
-                    median=median, sigma=SIGMA_DECADE, lo=median / 10, hi=median * 10, alloc=alloc)
+    return generate("clade", alloc=alloc, **_clade4096_kw(seed, n, median))
+
+
+def clade4096_range(value_lo: int, value_hi: int, seed: int = SEED_BASE + 4, n: int = 4096,
+                    median: float = 2e6):
+    """``clade4096`` restricted to the values of [value_lo, value_hi)."""
+    return generate_range("clade", value_lo, value_hi, **_clade4096_kw(seed, n, median))
 
 
 def serving_reference(seed: int = SEED_BASE + 5, n: int = 2048, median: float = 1e6, alloc=None):

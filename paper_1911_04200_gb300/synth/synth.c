@@ -203,19 +203,81 @@ static void make_ancestor(const synth_params* p, uint64_t a, uint64_t* out, uint
 }
 
 /*
+ * Draw sample i into v[0..L) (L = its pre-dedupe length from synth_lengths)
+ * and return the number of distinct values, which are then the sorted prefix
+ * of v.  tmp and perm hold L entries each; anc holds the ancestors (kind 0).
+ */
+static uint64_t draw_sample(const synth_params* p, const uint64_t* anc, uint64_t i, uint64_t L,
+                            uint64_t* v, uint64_t* tmp, uint64_t* perm)
+{
+    if (p->kind == 2) {
+        uint64_t k = 0;
+        if (p->p >= 1.0) {
+            for (; k < L; ++k) v[k] = k;
+        } else if (p->p > 0.0) {
+            const double lq = det_log01(1.0 - p->p);
+            uint64_t t = 0;
+            for (uint64_t d = 0; k < L; ++d) {
+                const double u = 1.0 - U01(H3(p->seed, T_BERN, i + p->sample_base, d));
+                const double g = det_log01(u) / lq;
+                if (g >= (double)(p->m - t)) break;
+                t += (uint64_t)g;
+                if (t >= p->m) break;
+                v[k++] = t++;
+            }
+        }
+        return k;
+    }
+    if (p->kind == 0) {
+        const uint64_t* A = anc + (i % p->n_anc) * p->anc_size;
+        memcpy(v, A, L * sizeof(uint64_t));
+        double u = p->u_max * U01(H3(p->seed, T_U, i, 0));
+        uint64_t k = (uint64_t)(u * (double)L);
+        /* partial Fisher-Yates over positions: the first k are replaced */
+        for (uint64_t t = 0; t < L; ++t) perm[t] = t;
+        for (uint64_t t = 0; t < k; ++t) {
+            uint64_t r = t + H3(p->seed, T_PERM, i, t) % (L - t);
+            uint64_t x = perm[t]; perm[t] = perm[r]; perm[r] = x;
+        }
+        for (uint64_t t = 0; t < k; ++t)
+            v[perm[t]] = to_domain(H3(p->seed, T_NEW, i, perm[t]), p->id_bits);
+    } else {
+        uint64_t gi = i + p->sample_base;
+        uint64_t c = gi % p->n_clades;
+        double u = p->u_max * U01(H3(p->seed, T_U, gi, 0));
+        for (uint64_t t = 0; t < L; ++t) {
+            uint64_t h;
+            if (U01(H3(p->seed, T_SUB, gi, t)) < u) {
+                h = H3(p->seed, T_FRESH, gi, t);
+            } else if (U01(H3(p->seed, T_CORE, c, t)) < p->core) {
+                h = H3(p->seed, T_ROOT, 0, t);
+            } else {
+                h = H3(p->seed, T_CLADE, c, t);
+            }
+            v[t] = to_domain(h, p->id_bits);
+        }
+    }
+    return sort_unique(v, L, p->id_bits, tmp);
+}
+
+static uint64_t* make_ancestors(const synth_params* p)
+{
+    if (p->kind != 0) return NULL;
+    uint64_t* anc = (uint64_t*)malloc(sizeof(uint64_t) * p->n_anc * p->anc_size + 8);
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t a = 0; a < (int64_t)p->n_anc; ++a)
+        make_ancestor(p, (uint64_t)a, anc + (uint64_t)a * p->anc_size, NULL);
+    return anc;
+}
+
+/*
  * Fill sample slots.  slot[i] .. slot[i+1] is sample i's slot of length
  * len[i] (from synth_lengths).  On return the first distinct[i] entries of
  * the slot are the sample's sorted distinct values.
  */
 void synth_fill(const synth_params* p, const uint64_t* slot, uint64_t* ids, uint64_t* distinct)
 {
-    uint64_t* anc = NULL;
-    if (p->kind == 0) {
-        anc = (uint64_t*)malloc(sizeof(uint64_t) * p->n_anc * p->anc_size + 8);
-        #pragma omp parallel for schedule(dynamic, 1)
-        for (int64_t a = 0; a < (int64_t)p->n_anc; ++a)
-            make_ancestor(p, (uint64_t)a, anc + (uint64_t)a * p->anc_size, NULL);
-    }
+    uint64_t* anc = make_ancestors(p);
     #pragma omp parallel
     {
         uint64_t cap = 0;
@@ -225,64 +287,62 @@ void synth_fill(const synth_params* p, const uint64_t* slot, uint64_t* ids, uint
         for (int64_t ii = 0; ii < (int64_t)p->n; ++ii) {
             uint64_t i = (uint64_t)ii;
             uint64_t L = slot[i + 1] - slot[i];
-            uint64_t* v = ids + slot[i];
             if (L > cap) {
                 free(tmp); free(perm);
                 cap = L;
                 tmp = (uint64_t*)malloc(sizeof(uint64_t) * cap);
                 perm = (uint64_t*)malloc(sizeof(uint64_t) * cap);
             }
-            if (p->kind == 2) {
-                uint64_t k = 0;
-                if (p->p >= 1.0) {
-                    for (; k < L; ++k) v[k] = k;
-                } else if (p->p > 0.0) {
-                    const double lq = det_log01(1.0 - p->p);
-                    uint64_t t = 0;
-                    for (uint64_t d = 0; k < L; ++d) {
-                        const double u = 1.0 - U01(H3(p->seed, T_BERN, i + p->sample_base, d));
-                        const double g = det_log01(u) / lq;
-                        if (g >= (double)(p->m - t)) break;
-                        t += (uint64_t)g;
-                        if (t >= p->m) break;
-                        v[k++] = t++;
-                    }
-                }
-                distinct[i] = k;
-                continue;
-            }
-            if (p->kind == 0) {
-                const uint64_t* A = anc + (i % p->n_anc) * p->anc_size;
-                memcpy(v, A, L * sizeof(uint64_t));
-                double u = p->u_max * U01(H3(p->seed, T_U, i, 0));
-                uint64_t k = (uint64_t)(u * (double)L);
-                /* partial Fisher-Yates over positions: the first k are replaced */
-                for (uint64_t t = 0; t < L; ++t) perm[t] = t;
-                for (uint64_t t = 0; t < k; ++t) {
-                    uint64_t r = t + H3(p->seed, T_PERM, i, t) % (L - t);
-                    uint64_t x = perm[t]; perm[t] = perm[r]; perm[r] = x;
-                }
-                for (uint64_t t = 0; t < k; ++t)
-                    v[perm[t]] = to_domain(H3(p->seed, T_NEW, i, perm[t]), p->id_bits);
-            } else {
-                uint64_t gi = i + p->sample_base;
-                uint64_t c = gi % p->n_clades;
-                double u = p->u_max * U01(H3(p->seed, T_U, gi, 0));
-                for (uint64_t t = 0; t < L; ++t) {
-                    uint64_t h;
-                    if (U01(H3(p->seed, T_SUB, gi, t)) < u) {
-                        h = H3(p->seed, T_FRESH, gi, t);
-                    } else if (U01(H3(p->seed, T_CORE, c, t)) < p->core) {
-                        h = H3(p->seed, T_ROOT, 0, t);
-                    } else {
-                        h = H3(p->seed, T_CLADE, c, t);
-                    }
-                    v[t] = to_domain(h, p->id_bits);
-                }
-            }
-            distinct[i] = sort_unique(v, L, p->id_bits, tmp);
+            distinct[i] = draw_sample(p, anc, i, L, ids + slot[i], tmp, perm);
         }
         free(tmp); free(perm);
+    }
+    free(anc);
+}
+
+static uint64_t first_at_least(const uint64_t* v, uint64_t n, uint64_t x)
+{
+    uint64_t a = 0, b = n;
+    while (a < b) { uint64_t mid = a + (b - a) / 2; if (v[mid] < x) a = mid + 1; else b = mid; }
+    return a;
+}
+
+/*
+ * The same collection restricted to the values of [lo, hi): every sample is
+ * drawn whole (as synth_fill draws it) and only its values inside the range
+ * are kept, so the restrictions of a collection to disjoint ranges are
+ * exactly the pieces of the whole.  With ids == NULL, counts[i] receives the
+ * number of sample i's values inside the range; otherwise ids receives them,
+ * sample i's at slot[i] (slot[i+1] - slot[i] = counts[i] from the first
+ * call).  len[i] is the pre-dedupe length from synth_lengths.
+ */
+void synth_fill_range(const synth_params* p, const uint64_t* len, uint64_t lo, uint64_t hi,
+                      uint64_t* counts, const uint64_t* slot, uint64_t* ids)
+{
+    uint64_t* anc = make_ancestors(p);
+    #pragma omp parallel
+    {
+        uint64_t cap = 0;
+        uint64_t* v = NULL;
+        uint64_t* tmp = NULL;
+        uint64_t* perm = NULL;
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t ii = 0; ii < (int64_t)p->n; ++ii) {
+            uint64_t i = (uint64_t)ii;
+            uint64_t L = len[i];
+            if (L > cap) {
+                free(v); free(tmp); free(perm);
+                cap = L;
+                v = (uint64_t*)malloc(sizeof(uint64_t) * cap);
+                tmp = (uint64_t*)malloc(sizeof(uint64_t) * cap);
+                perm = (uint64_t*)malloc(sizeof(uint64_t) * cap);
+            }
+            uint64_t d = draw_sample(p, anc, i, L, v, tmp, perm);
+            uint64_t a = first_at_least(v, d, lo), b = hi > lo ? first_at_least(v, d, hi) : a;
+            if (!ids) counts[i] = b - a;
+            else memcpy(ids + slot[i], v + a, (b - a) * sizeof(uint64_t));
+        }
+        free(v); free(tmp); free(perm);
     }
     free(anc);
 }

@@ -370,3 +370,82 @@ def test_row_permutation_invariance():
     np.testing.assert_array_equal(C0, C1)
     np.testing.assert_array_equal(s0, s1)
     np.testing.assert_array_equal(J0.view(np.uint64), J1.view(np.uint64))
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_rows_range_sums_to_dense_AtA(seed):
+    """The row-by-row count (B = sum over rows a_x a_x^T, Sec. III-A),
+    restricted to value ranges and added over a partition of the values
+    (Eq. 4), equals the dense A^T A by integer matrix product and the
+    pairwise merge; cuts land on values that samples hold, so a range bound
+    taken inclusive or exclusive the wrong way shows up, and duplicates
+    inside a sample count once."""
+    rng = np.random.default_rng(100 + seed)
+    n, m = int(rng.integers(1, 14)), int(rng.integers(1, 600))
+    density = [0.0, 0.02, 0.3, 0.8, 1.0][seed]
+    offsets, ids, A = random_collection(rng, n, m, density, dup_prob=0.2)
+    Ai = A.astype(np.int64)
+    AtA = Ai.T @ Ai
+    held = np.unique(ids).astype(np.int64)
+    picks = rng.choice(held, size=min(4, held.size), replace=False) if held.size else np.zeros(0, np.int64)
+    cuts = sorted(set([0, m] + [int(x) for x in picks] + [int(x) + 1 for x in picks]))
+    cuts = [c for c in cuts if 0 <= c <= m]
+    Cu = np.zeros((n, n), dtype=np.uint64)
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        oracle.rows_range(offsets, ids, lo, hi, Cu, pieces=int(rng.integers(1, 9)))
+    np.testing.assert_array_equal(Cu.astype(np.int64), np.triu(AtA))
+    C, J = oracle.finish_upper(Cu, Ai.sum(axis=0).astype(np.uint64))
+    Cm, sm, Jm = oracle.all_pairs(offsets, ids)
+    np.testing.assert_array_equal(C, Cm)
+    np.testing.assert_array_equal(J.view(np.uint64), Jm.view(np.uint64))
+    # one range alone: the rows of A inside it
+    if len(cuts) > 2:
+        lo, hi = cuts[1], cuts[2]
+        part = oracle.rows_range(offsets, ids, lo, hi)
+        Ar = Ai[lo:hi]
+        np.testing.assert_array_equal(part.astype(np.int64), np.triu(Ar.T @ Ar))
+
+
+def test_rows_range_interval_closed_form_and_empty_ranges():
+    """Interval sets [a_i, b_i): the count restricted to [lo, hi) is the
+    length of [max(a_i, a_j, lo), min(b_i, b_j, hi)), zero when negative; a
+    range nobody holds adds nothing."""
+    rng = np.random.default_rng(31)
+    n = 9
+    a = rng.integers(0, 5000, n)
+    b = a + rng.integers(0, 4000, n)
+    segs = [np.arange(a[i], b[i], dtype=np.uint64) for i in range(n)]
+    off = np.zeros(n + 1, dtype=np.uint64)
+    off[1:] = np.cumsum([s.size for s in segs])
+    ids = np.concatenate(segs)
+    for lo, hi in [(0, 10000), (1234, 5678), (7000, 9100), (20000, 30000)]:
+        Cu = oracle.rows_range(off, ids, lo, hi, pieces=7)
+        for i in range(n):
+            for j in range(i, n):
+                want = max(0, min(b[i], b[j], hi) - max(a[i], a[j], lo))
+                assert int(Cu[i, j]) == want
+                if j > i:
+                    assert int(Cu[j, i]) == 0
+
+
+def test_generated_ranges_tile_the_collection():
+    """The generator's restriction to disjoint value ranges gives exactly the
+    pieces of the whole collection, for the clade, ancestral and Bernoulli
+    recipes (so an out-of-memory collection can be visited range by range)."""
+    from paper_1911_04200_gb300 import synth
+    cases = [
+        ("clade", dict(n=40, id_bits=40, seed=77, n_clades=4, core=0.3, u_max=0.4, median=3e3,
+                       sigma=synth.SIGMA_DECADE, lo=300, hi=3e4), [0, 1 << 20, 5 << 36, 1 << 39, 1 << 40]),
+        ("ancestral", dict(n=16, id_bits=20, seed=5, n_anc=4, anc_size=3000, u_max=0.6),
+         [0, 77777, 500000, 1 << 20]),
+        ("bernoulli", dict(n=20, id_bits=16, seed=9, m=1 << 16, p=0.05), [0, 1, 30000, 1 << 16]),
+    ]
+    for kind, kw, cuts in cases:
+        off, ids = synth.generate(kind, **kw)
+        parts = [synth.generate_range(kind, lo, hi, **kw) for lo, hi in zip(cuts[:-1], cuts[1:])]
+        for i in range(len(off) - 1):
+            whole = ids[int(off[i]):int(off[i + 1])]
+            pieces = [pi[int(po[i]):int(po[i + 1])] for po, pi in parts]
+            for (lo, hi), piece in zip(zip(cuts[:-1], cuts[1:]), pieces):
+                assert piece.size == 0 or (int(piece[0]) >= lo and int(piece[-1]) < hi)
+            np.testing.assert_array_equal(whole, np.concatenate(pieces))
