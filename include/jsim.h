@@ -210,6 +210,23 @@ JSIM_API int jsim_finish(jsim_ctx* ctx, uint64_t n, const void* C, const uint64_
                          int mem);
 
 /*
+ * The partition rule of jsim_all_pairs_part, on the host (no device, no
+ * context): the row batches of Eq. 3 that part `part` of `parts` counts, for
+ * a collection whose values lie in [minid, maxid].
+ *   batch_rows       m~ (a multiple of 64), or 0 for the automatic choice
+ *                    (the one jsim_all_pairs makes for this value span)
+ *   b_begin, b_end   batches [b_begin, b_end) of this part: batch b holds the
+ *                    values [b m~, (b+1) m~); may be NULL
+ *   batch_rows_used  the m~ used; may be NULL
+ * Parts 0..parts-1 tile the batches from minid's to maxid's in order.  Lets
+ * the ranks of a split contraction agree on the split before any device
+ * work.  Errors: JSIM_ERR_ARG (parts 0, part >= parts, maxid < minid, or
+ * batch_rows not a multiple of 64).
+ */
+JSIM_API int jsim_partition_batches(uint64_t minid, uint64_t maxid, uint64_t batch_rows, uint32_t part,
+                                    uint32_t parts, uint64_t* b_begin, uint64_t* b_end, uint64_t* batch_rows_used);
+
+/*
  * All-pairs similarity of k independent collections in one call (the
  * batched pattern).  Every collection is processed exactly as by
  * jsim_all_pairs (its own row batches, filter, prefix sum, words and product;
@@ -462,6 +479,28 @@ JSIM_API int jsim_topk(jsim_ctx* ctx, const double* J, uint64_t n, uint32_t k, u
  */
 JSIM_API int jsim_threshold(jsim_ctx* ctx, const double* J, uint64_t n, double tau, int below, uint64_t cap,
                             uint64_t* pi, uint64_t* pj, double* val, uint64_t* count, int mem);
+
+/*
+ * Self-check of the work schedule of the job-table tensor-core product (the
+ * persistent launch of jsim_all_pairs_batched), on the host: no device, no
+ * context.  The paper has no counterpart; the product it schedules is Eq. 7.
+ * For a launch of `grid` persistent CTAs over `njobs` collections (job k: n[k]
+ * samples, W[k] packed words per sample, rows of stride[k] words, rows[k] >=
+ * n[k] rows allocated), it replays what every CTA does - each unpack
+ * thread's loads (row, word, 16-byte alignment), the MMA thread's segments
+ * and accumulator slots, the epilogue's TMEM columns and count writes - with
+ * the same functions the kernel runs, and checks every address against its
+ * buffer, that every (collection, tile, stage) unit is taken exactly once,
+ * that every pair i <= j lies in exactly one tile, that no accumulator holds
+ * more stages than the exact-count cap, and that every slot is drained as
+ * often as it is committed.
+ *   njobs   1..256; grid >= 1
+ *   msg     receives a description of the first failed check (cap bytes, may be NULL)
+ * Returns 0 when every check passes, JSIM_ERR_ARG for bad arguments, and a
+ * positive check number otherwise.
+ */
+JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n, const uint64_t* W, const uint64_t* stride,
+                                    const uint64_t* rows, uint32_t grid, char* msg, size_t cap);
 
 /* Statistics of the last call on the context. */
 JSIM_API int jsim_get_stats(const jsim_ctx* ctx, jsim_stats* out);

@@ -193,6 +193,20 @@ constexpr u64 kHostStreamMin = 4ull << 30;
 
 namespace {
 
+// Row batches of part `part` of `parts` (the split contraction of
+// jsim_all_pairs_part): the batch size mt (batch_rows, or the automatic size
+// for the value span [minid, maxid]), and the batches [b_beg, b_end) (batch b
+// = values [b mt, (b+1) mt)) of this part: the nb batches between the first
+// and the last value cut into `parts` contiguous runs.
+void partition_rows(u64 minid, u64 maxid, u64 batch_rows, u64 part, u64 parts, u64& b_beg, u64& b_end, u64& mt)
+{
+    const u64 span = maxid - minid;
+    mt = batch_rows ? batch_rows : auto_batch_rows(span + 1 ? span + 1 : ~0ull);
+    const u64 b_first = minid / mt, nb = maxid / mt - b_first + 1;
+    b_beg = b_first + (u64)((unsigned __int128)nb * part / parts);
+    b_end = b_first + (u64)((unsigned __int128)nb * (part + 1) / parts);
+}
+
 // The plain call over the row batches [b_first + nb * part / parts,
 // b_first + nb * (part + 1) / parts) of the nb batches between the first and
 // the last value (parts = 1: all of them).  counts_only: C gets the part's
@@ -228,14 +242,10 @@ int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
 
     // values lie in [minid, maxid]; batches are aligned to multiples of m~ and
     // empty stretches of the value range are skipped
-    const u64 span = st.N ? st.maxid - st.minid : 0;
-    u64 mt = ctx->opt.batch_rows ? ctx->opt.batch_rows : auto_batch_rows(span + 1 ? span + 1 : ~0ull);
+    u64 mt = 0, b_beg = 0, b_end = 0;
+    partition_rows(st.N ? st.minid : 0, st.N ? st.maxid : 0, ctx->opt.batch_rows, part, parts, b_beg, b_end, mt);
     ctx->stats.batch_rows = mt;
     int variant = ctx->opt.variant;
-    // this part's row batches [b_beg, b_end)
-    const u64 b_first = st.minid / mt, nb = st.maxid / mt - b_first + 1;
-    const u64 b_beg = b_first + (u64)((unsigned __int128)nb * part / parts);
-    const u64 b_end = b_first + (u64)((unsigned __int128)nb * (part + 1) / parts);
     if (st.N && b_beg < b_end) {
         BatchBufs bb;
         u64 lo = b_beg * mt;
@@ -320,6 +330,18 @@ int jsim_all_pairs_part(jsim_ctx* ctx, const jsim_sets* sets, uint32_t part, uin
     if (rc) return rc;
     if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
     return all_pairs_impl(ctx, sets, C, sizes, nullptr, out_mem, part, parts, true);
+}
+
+int jsim_partition_batches(uint64_t minid, uint64_t maxid, uint64_t batch_rows, uint32_t part, uint32_t parts,
+                           uint64_t* b_begin, uint64_t* b_end, uint64_t* batch_rows_used)
+{
+    if (parts == 0 || part >= parts || maxid < minid || (batch_rows && batch_rows % 64)) return JSIM_ERR_ARG;
+    u64 b0 = 0, b1 = 0, mt = 0;
+    partition_rows(minid, maxid, batch_rows, part, parts, b0, b1, mt);
+    if (b_begin) *b_begin = b0;
+    if (b_end) *b_end = b1;
+    if (batch_rows_used) *batch_rows_used = mt;
+    return JSIM_OK;
 }
 
 int jsim_finish(jsim_ctx* ctx, uint64_t n, const void* C, const uint64_t* sizes, void* Cout, double* J, int mem)

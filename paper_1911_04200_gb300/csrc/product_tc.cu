@@ -39,6 +39,7 @@
 #include <algorithm>
 #include <vector>
 #include "common.cuh"
+#include "product_tc_sched.cuh"
 
 namespace jsim {
 
@@ -49,14 +50,22 @@ constexpr int kMmaWarp = 12;
 constexpr int kEpiWarp0 = 13;
 constexpr int kWarps = 17;
 constexpr int kThreads = kWarps * 32;          // 544
-constexpr int kM = 128;                        // A-side rows per tile
-constexpr int kN = 256;                        // B-side rows per tile
-constexpr int kRows = kM + kN;                 // rows unpacked per stage (one per producer thread)
+using tcs::kM;
+using tcs::kN;
+using tcs::kRows;
+using tcs::kStageBits;
+using tcs::kStageWords;
+using tcs::kMaxSegStages;
+using tcs::kMaxJobs;
+using tcs::JobInfo;
+using tcs::Seg;
+using tcs::WorkIter;
+using tcs::Slots;
+using tcs::job_tiles;
+using tcs::tc_tile;
 static_assert(kRows == kProducerWarps * 32, "one row per producer thread");
 static_assert(kEpiWarp0 % 4 == 1, "epilogue warp e reads TMEM lanes of warp rank (kEpiWarp0 + e) % 4");
-constexpr int kStageBits = 256;                // bit-rows per stage: two 128-byte swizzle atom columns
 constexpr int kAtoms = kStageBits / 128;
-constexpr int kStageWords = kStageBits / 64;
 constexpr int kBlkBytes = 128;
 constexpr int kAtomA = kM * kBlkBytes;         // one atom column of A: 16 KiB
 constexpr int kAtomB = kN * kBlkBytes;         // one atom column of B: 32 KiB
@@ -67,7 +76,6 @@ constexpr int kAhead = 4;                      // stages of packed words held in
 constexpr int kSmemBytes = kBufs * kStageBytes + 1024;  // + alignment slack
 static_assert(kSmemBytes <= 232448, "fits the per-CTA shared-memory limit");
 constexpr int kTmemCols = 512;                 // two 256-column FP32 accumulators
-constexpr u64 kMaxSegStages = (1ull << 22) / kStageBits;
 constexpr u32 kErrTimeout = 4u;
 
 // instruction descriptor: kind::f8f6f4, D = F32, A = B = E4M3, both K-major,
@@ -140,110 +148,6 @@ __device__ __forceinline__ void tmem_ld32(u32 taddr, u32 (&r)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-// tile t -> first row and column over 128 x 256 tiles with rows [128 ti, +128)
-// and columns [256 tj, +256) that hold at least one pair i <= j (ti <= 2 tj + 1)
-__device__ __forceinline__ void tc_tile(u64 t, u64 TM, u64& r0, u64& c0)
-{
-    u64 j = 0;
-    for (;;) {
-        u64 cnt = min(TM, 2 * j + 2);
-        if (t < cnt) break;
-        t -= cnt;
-        ++j;
-    }
-    r0 = t * kM;
-    c0 = j * kN;
-}
-
-// Per-job quantities every CTA derives in its prologue (shared memory).
-struct JobInfo {
-    u64 nst;    // stages of every tile of the job (ceil(W / 2))
-    u64 tiles;  // 128 x 256 tiles touching the upper triangle
-    u64 TM;     // 128-row tile count
-    u64 U0;     // first unit of the job in the launch-wide unit order
-};
-
-// A run of stages of one tile of one job.
-struct Seg {
-    u32 job;
-    u64 tile, kst, len;
-};
-
-// The CTA's work: the units (job, tile, stage) of all jobs of the launch,
-// job-major then tile-major, are split into G equal contiguous shares, one
-// per persistent CTA; small collections share a CTA and large ones spread
-// over many.  A segment never exceeds the exactness cap.
-struct WorkIter {
-    const JobInfo* ji;
-    u32 njobs;
-    u64 u, uend;
-    u32 j;
-    __device__ __forceinline__ void init(const JobInfo* ji_, u32 njobs_, u64 G, u64 c)
-    {
-        ji = ji_; njobs = njobs_;
-        const u64 U = ji[njobs - 1].U0 + ji[njobs - 1].tiles * ji[njobs - 1].nst;
-        u = c * U / G;
-        uend = (c + 1) * U / G;
-        // job holding unit u: last j with U0 <= u
-        u32 lo = 0, hi = njobs - 1;
-        while (lo < hi) {
-            u32 mid = (lo + hi + 1) >> 1;
-            if (ji[mid].U0 <= u) lo = mid; else hi = mid - 1;
-        }
-        j = lo;
-    }
-    // next segment; false at the end
-    __device__ __forceinline__ bool next(Seg& sg)
-    {
-        while (u < uend) {
-            const JobInfo& J = ji[j];
-            const u64 jend = J.U0 + J.tiles * J.nst;
-            if (u >= jend) { ++j; continue; }  // empty or finished job
-            const u64 v = u - J.U0;
-            sg.job = j;
-            sg.tile = v / J.nst;
-            sg.kst = v - sg.tile * J.nst;
-            const u64 e = min(min(uend, J.U0 + (sg.tile + 1) * J.nst), u + kMaxSegStages);
-            sg.len = e - u;
-            u = e;
-            return true;
-        }
-        return false;
-    }
-};
-
-// Accumulator bookkeeping shared (replayed identically) by the MMA warp and
-// the epilogue warps: two TMEM slots tagged with a tile; a segment of a tile
-// already in a slot accumulates there, otherwise a free slot or the less
-// recently used one is taken (flushing it first).  A slot is also flushed
-// before its accumulated stages would pass the exactness cap.
-struct Slots {
-    u64 tile[2];  // key: job << 40 | tile
-    u64 fill[2];
-    u32 flushes[2];
-    int last;
-    __device__ __forceinline__ void init()
-    {
-        tile[0] = tile[1] = ~0ull;
-        fill[0] = fill[1] = 0;
-        flushes[0] = flushes[1] = 0;
-        last = 1;
-    }
-    __device__ __forceinline__ int pick(u64 t) const
-    {
-        if (tile[0] == t) return 0;
-        if (tile[1] == t) return 1;
-        if (tile[0] == ~0ull) return 0;
-        if (tile[1] == ~0ull) return 1;
-        return 1 - last;
-    }
-    // does slot s have to be flushed before a segment of tile t, len stages?
-    __device__ __forceinline__ bool needs_flush(int s, u64 t, u64 len) const
-    {
-        return tile[s] != ~0ull && (tile[s] != t || fill[s] + len > kMaxSegStages);
-    }
-};
-
 // One independent collection of a launch: its packed words, word count
 // (on the host, or on the device when Wdev is set) and count accumulator.
 struct TcJob {
@@ -252,22 +156,12 @@ struct TcJob {
     void* C;
     u64 stride, n, W, ldc;
 };
-constexpr int kMaxJobs = 256;
 // Kernel parameters: the job table lives in device memory.
 struct TcJobs {
     const TcJob* job;
     u32 njobs;
     int vec16;  // 16-byte loads are safe for every job
 };
-
-__device__ __forceinline__ u64 job_tiles(u64 n, u64& TM)
-{
-    TM = (n + kM - 1) / kM;
-    const u64 TN = (n + kN - 1) / kN;
-    u64 t = 0;
-    for (u64 j = 0; j < TN; ++j) t += min(TM, 2 * j + 2);
-    return t;
-}
 
 template <typename CT>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -287,16 +181,12 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         for (u32 j = 0; j < njobs; ++j) {
             const TcJob& J = P.job[j];
             const u64 W = J.Wdev ? *(volatile const u64*)J.Wdev : J.W;
-            JobInfo x;
-            x.nst = (W + kStageWords - 1) / kStageWords;
-            x.tiles = job_tiles(J.n, x.TM);
-            if (x.nst == 0) x.tiles = 0;
-            x.U0 = U;
+            const JobInfo x = tcs::job_info(J.n, W, U);
             U += x.tiles * x.nst;
             ji[j] = x;
         }
         // stages of this CTA
-        s_T = (blockIdx.x + 1) * U / gridDim.x - blockIdx.x * U / gridDim.x;
+        s_T = tcs::cta_stages(U, gridDim.x, blockIdx.x);
     }
     __syncthreads();
     const u64 T = s_T;
@@ -362,19 +252,21 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                     f_key = key;
                 }
             }
-            u64 grow = is_a ? f_r0 + row : f_c0 + row;
-            u64 gk = f_kst * kStageWords;
+            const u64 grow = tcs::fetch_row(p, f_r0, f_c0);
             if (grow < f_n) {
-                const u64* src = f_X + grow * f_stride + gk;
+                const u64* src = f_X + grow * f_stride;
                 #pragma unroll
                 for (int q = 0; q < kStageWords; q += 2) {
-                    if (P.vec16 && gk + q + 1 < f_W) {
+                    u64 w0, w1;
+                    const bool in0 = tcs::fetch_word(f_kst, q, f_W, w0);
+                    const bool in1 = tcs::fetch_word(f_kst, q + 1, f_W, w1);
+                    if (P.vec16 && in1) {
                         // two words of the stage in one 16-byte load
                         asm volatile("ld.global.nc.v2.u64 {%0,%1}, [%2];\n"
-                                     : "=l"(v[q]), "=l"(v[q + 1]) : "l"(src + q));
+                                     : "=l"(v[q]), "=l"(v[q + 1]) : "l"(src + w0));
                     } else {
-                        if (gk + q < f_W) v[q] = __ldg(src + q);
-                        if (gk + q + 1 < f_W) v[q + 1] = __ldg(src + q + 1);
+                        if (in0) v[q] = __ldg(src + w0);
+                        if (in1) v[q + 1] = __ldg(src + w1);
                     }
                 }
             }
@@ -635,3 +527,166 @@ cudaError_t product_tc(ProductArgs& a, cudaStream_t st)
 }
 
 }  // namespace jsim
+
+// ---------------------------------------------------------------------------
+// Host-side check of the schedule above (no GPU): replays, for every CTA of a
+// launch, the unpack threads' fetches, the MMA thread's segments and
+// accumulator slots, and the epilogue's drains and C writes, with the same
+// __host__ __device__ functions the kernel runs, and checks every address
+// against its buffer.
+// ---------------------------------------------------------------------------
+#include <cstdio>
+#include <cstring>
+
+namespace {
+
+struct CheckMsg {
+    char* buf;
+    size_t cap;
+    int fail(int code, const char* fmt, unsigned long long a, unsigned long long b, unsigned long long c)
+    {
+        if (buf && cap) snprintf(buf, cap, fmt, a, b, c);
+        return code;
+    }
+};
+
+}  // namespace
+
+extern "C" JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n, const uint64_t* W,
+                                               const uint64_t* stride, const uint64_t* rows, uint32_t grid,
+                                               char* msg, size_t cap)
+{
+    using namespace jsim;
+    using namespace jsim::tcs;
+    CheckMsg m{msg, cap};
+    if (msg && cap) msg[0] = 0;
+    if (njobs == 0 || njobs > (uint32_t)kMaxJobs || grid == 0 || !n || !W || !stride || !rows) return JSIM_ERR_ARG;
+    std::vector<JobInfo> ji(njobs);
+    u64 U = 0;
+    for (u32 j = 0; j < njobs; ++j) {
+        if (rows[j] < n[j] || (W[j] > stride[j] && n[j] > 0)) return m.fail(1, "job %llu: rows %llu or W beyond stride %llu", j, rows[j], stride[j]);
+        ji[j] = job_info(n[j], W[j], U);
+        U += ji[j].tiles * ji[j].nst;
+    }
+    // every (job, tile, stage) unit must be taken exactly once
+    std::vector<unsigned char> seen(U, 0);
+    // every pair i <= j of a job must lie in exactly one tile
+    for (u32 jb = 0; jb < njobs; ++jb) {
+        if (n[jb] == 0 || ji[jb].tiles == 0 || n[jb] > 8192) continue;
+        const u64 N = n[jb];
+        std::vector<unsigned char> cov(N * N, 0);
+        for (u64 t = 0; t < ji[jb].tiles; ++t) {
+            u64 r0, c0;
+            tc_tile(t, ji[jb].TM, r0, c0);
+            for (u64 i = r0; i < r0 + kM && i < N; ++i)
+                for (u64 j = std::max(i, c0); j < c0 + kN && j < N; ++j) {
+                    if (cov[i * N + j]) return m.fail(2, "job %llu: pair (%llu, %llu) in two tiles", jb, i, j);
+                    cov[i * N + j] = 1;
+                }
+        }
+        for (u64 i = 0; i < N; ++i)
+            for (u64 j = i; j < N; ++j)
+                if (!cov[i * N + j]) return m.fail(3, "job %llu: pair (%llu, %llu) in no tile", jb, i, j);
+    }
+    for (u64 c = 0; c < grid; ++c) {
+        const u64 T = cta_stages(U, grid, c);
+        if (T == 0) continue;
+        // unpack threads: T fetches that find a segment, then none
+        {
+            WorkIter fit;
+            fit.init(ji.data(), njobs, grid, c);
+            Seg fs{};
+            u64 left = 0, kst = 0, r0 = 0, c0 = 0;
+            u32 job = 0;
+            for (u64 t = 0; t < T + 4; ++t) {
+                if (left == 0) {
+                    if (!fit.next(fs)) {
+                        if (t < T) return m.fail(4, "cta %llu: fetch %llu of %llu found no segment", c, t, T);
+                        break;
+                    }
+                    if (t >= T) return m.fail(5, "cta %llu: fetch %llu beyond its %llu stages", c, t, T);
+                    kst = fs.kst; left = fs.len; job = fs.job;
+                    tc_tile(fs.tile, ji[job].TM, r0, c0);
+                }
+                for (int p = 0; p < kRows; ++p) {
+                    const u64 grow = fetch_row(p, r0, c0);
+                    if (grow >= n[job]) continue;
+                    for (int q = 0; q < kStageWords; ++q) {
+                        u64 w;
+                        if (!fetch_word(kst, q, W[job], w)) continue;
+                        if (grow >= rows[job] || w >= stride[job])
+                            return m.fail(6, "cta %llu: read row %llu word %llu outside the matrix", c, grow, w);
+                        if ((q & 1) == 0 && stride[job] % 2 == 0 && ((grow * stride[job] + w) & 1))
+                            return m.fail(7, "cta %llu: 16-byte load at row %llu word %llu misaligned", c, grow, w);
+                    }
+                }
+                --left;
+                ++kst;
+            }
+        }
+        // MMA thread and epilogue: the same segments and slot decisions
+        {
+            WorkIter it;
+            it.init(ji.data(), njobs, grid, c);
+            Slots sl;
+            sl.init();
+            Seg sg{};
+            u64 t = 0;
+            u32 commits[2] = {0, 0};
+            u32 drains[2] = {0, 0};
+            auto drain = [&](int sidx, u64 key) -> int {
+                const u32 jb = (u32)(key >> 40);
+                u64 r0, c0;
+                tc_tile(key & ((1ull << 40) - 1), ji[jb].TM, r0, c0);
+                for (u64 e = 0; e < 4; ++e)
+                    for (u64 lane = 0; lane < 32; ++lane) {
+                        const u64 i = r0 + e * 32 + lane;
+                        for (u64 col = 0; col < (u64)kN; ++col) {
+                            const u64 tcol = (u64)sidx * 256 + col;
+                            if (tcol >= 512) return m.fail(8, "cta %llu: TMEM column %llu of slot %llu", c, tcol, sidx);
+                            const u64 j = c0 + col;
+                            if (i < n[jb] && j < n[jb] && i <= j && i * n[jb] + j >= n[jb] * n[jb])
+                                return m.fail(9, "cta %llu: C write (%llu, %llu) outside", c, i, j);
+                        }
+                    }
+                drains[sidx] += 1;
+                return 0;
+            };
+            while (it.next(sg)) {
+                const u64 key = ((u64)sg.job << 40) | sg.tile;
+                const u64 u0 = ji[sg.job].U0 + sg.tile * ji[sg.job].nst + sg.kst;
+                for (u64 q = 0; q < sg.len; ++q) {
+                    if (u0 + q >= U || seen[u0 + q]) return m.fail(10, "cta %llu: unit %llu taken twice (of %llu)", c, u0 + q, U);
+                    seen[u0 + q] = 1;
+                }
+                const int sidx = sl.pick(key);
+                if (sl.needs_flush(sidx, key, sg.len)) {
+                    commits[sidx] += 1;
+                    if (int r = drain(sidx, sl.tile[sidx])) return r;
+                    sl.flushes[sidx] += 1;
+                    sl.tile[sidx] = ~0ull;
+                }
+                if (sl.tile[sidx] == ~0ull) {
+                    sl.tile[sidx] = key;
+                    sl.fill[sidx] = 0;
+                }
+                sl.fill[sidx] += sg.len;
+                if (sl.fill[sidx] > kMaxSegStages)
+                    return m.fail(11, "cta %llu: slot %llu holds %llu stages (beyond the exact cap)", c, sidx, sl.fill[sidx]);
+                sl.last = sidx;
+                t += sg.len;
+            }
+            for (int sidx = 0; sidx < 2; ++sidx) {
+                if (sl.tile[sidx] == ~0ull) continue;
+                commits[sidx] += 1;
+                if (int r = drain(sidx, sl.tile[sidx])) return r;
+            }
+            if (t != T) return m.fail(12, "cta %llu: MMA stages %llu, unpacked %llu", c, t, T);
+            for (int s = 0; s < 2; ++s)
+                if (commits[s] != drains[s]) return m.fail(13, "cta %llu: slot %llu commits %llu != drains", c, s, commits[s]);
+        }
+    }
+    for (u64 u = 0; u < U; ++u)
+        if (!seen[u]) return m.fail(14, "unit %llu of %llu taken by no CTA%llu", u, U, 0);
+    return 0;
+}

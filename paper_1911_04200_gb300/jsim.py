@@ -42,11 +42,30 @@ class Sets(ctypes.Structure):
 
 def partition_batches(minid: int, maxid: int, batch_rows: int, parts: int):
     """The row batches [begin, end) (batch index = value // batch_rows) of each
-    part of jsim_all_pairs_part: the nb batches between the first and last
-    value cut into `parts` contiguous runs."""
-    first = minid // batch_rows
-    nb = maxid // batch_rows - first + 1
-    return [(first + nb * p // parts, first + nb * (p + 1) // parts) for p in range(parts)]
+    part of jsim_all_pairs_part, by the library's own rule
+    (jsim_partition_batches; batch_rows 0: the automatic size)."""
+    lib = load()
+    out = []
+    for p in range(parts):
+        b0, b1, mt = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        rc = lib.jsim_partition_batches(minid, maxid, batch_rows, p, parts, ctypes.byref(b0), ctypes.byref(b1),
+                                        ctypes.byref(mt))
+        if rc:
+            raise JsimError(rc, "jsim_partition_batches")
+        out.append((b0.value, b1.value))
+    return out
+
+
+def check_tc_schedule(jobs, grid: int):
+    """Host-side check of the job-table tensor-core product's schedule for
+    jobs [(n, W, stride, rows), ...] over `grid` CTAs: (code, message), code 0
+    when every check passes (jsim_check_tc_schedule)."""
+    lib = load()
+    k = len(jobs)
+    arr = [(ctypes.c_uint64 * k)(*[int(j[f]) for j in jobs]) for f in range(4)]
+    buf = ctypes.create_string_buffer(256)
+    rc = lib.jsim_check_tc_schedule(k, arr[0], arr[1], arr[2], arr[3], grid, buf, 256)
+    return rc, buf.value.decode()
 
 
 class Checkpoint(ctypes.Structure):
@@ -96,6 +115,13 @@ class ServeStats(ctypes.Structure):
 
 # Every C-ABI entry point declared in include/jsim.h, with its ctypes signature.
 SIGNATURES = {
+    "jsim_partition_batches": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "jsim_check_tc_schedule": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                              ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint32, ctypes.c_char_p,
+                                              ctypes.c_size_t]),
     "jsim_default_options": (None, [ctypes.POINTER(Options)]),
     "jsim_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Options)]),
     "jsim_destroy": (None, [ctypes.c_void_p]),

@@ -129,3 +129,21 @@ def test_partition_rule_tiles_the_batches():
             assert all(a <= b for a, b in pb) and all(pb[k][1] == pb[k + 1][0] for k in range(parts - 1))
             sizes = [b - a for a, b in pb]
             assert max(sizes) - min(sizes) <= 1
+
+
+def test_partition_rule_is_the_library_rule_with_the_automatic_batch_size():
+    """The split is computed by the library (jsim_partition_batches), with the
+    automatic batch size of a plain call: 2^28 rows for a 2^32 span (16
+    batches), the span itself rounded up to a power of two when smaller."""
+    import ctypes
+    sys.path.insert(0, ROOT)
+    from paper_1911_04200_gb300 import jsim
+    lib = jsim.load()
+    b0, b1, mt = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    assert lib.jsim_partition_batches(0, 2**32 - 1, 0, 0, 1, ctypes.byref(b0), ctypes.byref(b1), ctypes.byref(mt)) == 0
+    assert (b0.value, b1.value, mt.value) == (0, 16, 1 << 28)
+    assert lib.jsim_partition_batches(100, 5000, 0, 1, 2, ctypes.byref(b0), ctypes.byref(b1), ctypes.byref(mt)) == 0
+    assert mt.value == 8192 and (b0.value, b1.value) == (0, 1)
+    assert jsim.partition_batches(0, 2**32 - 1, 0, 4) == [(0, 4), (4, 8), (8, 12), (12, 16)]
+    for bad in ((0, 10, 0, 2, 2), (0, 10, 0, 0, 0), (10, 0, 0, 0, 1), (0, 10, 100, 0, 1)):
+        assert lib.jsim_partition_batches(*bad, None, None, None) == 1
