@@ -147,16 +147,20 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
         }
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_scalars, 64 * sizeof(u64));
+    bool oom = false;
     if (e == cudaSuccess) {
         c->d_err = (unsigned int*)o.alloc(256, (void*)c->stream, o.alloc_user);
-        if (!c->d_err) e = cudaErrorMemoryAllocation;
+        if (!c->d_err) { e = cudaErrorMemoryAllocation; oom = true; }
         else e = cudaMemsetAsync(c->d_err, 0, 256, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (c->d_err) o.free(c->d_err, 256, (void*)c->stream, o.alloc_user);
+        if (c->h_scalars) cudaFreeHost(c->h_scalars);
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
         delete c;
-        return JSIM_ERR_CUDA;
+        return oom ? JSIM_ERR_OOM : JSIM_ERR_CUDA;
     }
     *out = c;
     return JSIM_OK;
@@ -272,6 +276,9 @@ int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
         }
     }
 
+    // nothing is written when a bounded device wait ran out
+    rc = check_device_waits(ctx, ctx->d_err);
+    if (rc) return rc;
     // epilogue into the outputs (device) or staging buffers (host)
     DevBuf Cst, Jst;
     void* Cdst = C;
@@ -456,10 +463,10 @@ int jsim_product(jsim_ctx* ctx, const uint64_t* words, uint64_t n, uint64_t W, u
     }
     ctx->stats.words = W;
     ctx->stats.bitops_dense = 64.0 * (double)W * (double)n * (double)(n + 1) / 2.0;
+    int rc = check_device_waits(ctx, ctx->d_err);
+    if (rc) return rc;
     CK(launch_epilogue(Cacc.p, n, ctx->opt.count_bits, nullptr, C, nullptr, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_scalars, ctx->d_err, sizeof(u32), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if ((u32)ctx->h_scalars[0] != 0) return JSIM_ERR_TIMEOUT;
     return JSIM_OK;
 }
 
@@ -555,6 +562,7 @@ extern "C" int jsim_product_noalloc(jsim_ctx* ctx, const uint64_t* words, uint64
     const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
     if (n > (1u << 16) || (size_t)(n * n) * cb > kNoAllocCountBytes) return JSIM_ERR_ARG;
     CK(cudaSetDevice(ctx->opt.device));
+    CallScope scope(ctx);
     if (n == 0) return JSIM_OK;
     cudaError_t e;
     unsigned char* scratch = (unsigned char*)noalloc_scratch(ctx->opt.device, e);
@@ -562,33 +570,16 @@ extern "C" int jsim_product_noalloc(jsim_ctx* ctx, const uint64_t* words, uint64
     u32* err = (u32*)(scratch + kNoAllocCountBytes);
     CK(cudaMemsetAsync(scratch, 0, (size_t)(n * n) * cb, ctx->stream));
     CK(cudaMemsetAsync(err, 0, sizeof(u32), ctx->stream));
-    int v = variant == JSIM_VARIANT_AUTO ? choose_variant(ctx, n, W) : variant;
+    const int v = variant == JSIM_VARIANT_AUTO ? choose_variant(ctx, n, W) : variant;
     if (W) {
-        ProductArgs a{};
-        a.X = (const u64*)words; a.stride = stride; a.n = n; a.W = W; a.C = scratch; a.ldc = n;
-        a.count_bits = ctx->opt.count_bits; a.word_bits = ctx->opt.word_bits; a.sms = ctx->sms;
-        a.timeout_ms = ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000;
-        a.err = err;
-        switch (v) {
-        case JSIM_VARIANT_TC:
-            if (!product_tc_supported(ctx->opt.device)) return JSIM_ERR_UNSUPPORTED;
-            e = product_tc(a, ctx->stream);
-            break;
-        case JSIM_VARIANT_TC2:
-            if (!product_tc_supported(ctx->opt.device)) return JSIM_ERR_UNSUPPORTED;
-            e = product_tc_pair(a, ctx->stream);
-            break;
-        case JSIM_VARIANT_POPC: e = product_popc(a, ctx->stream); break;
-        case JSIM_VARIANT_B1:
-        case JSIM_VARIANT_I8:
-        case JSIM_VARIANT_F8: e = product_mma(a, v, ctx->stream); break;
-        default: return JSIM_ERR_UNSUPPORTED;
-        }
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "product");
+        int rc = run_product(ctx, v, (const u64*)words, stride, n, W, scratch, err);
+        if (rc) return rc;
     }
+    ctx->stats.words = W;
+    ctx->stats.bitops_dense = 64.0 * (double)W * (double)n * (double)(n + 1) / 2.0;
+    int rc = check_device_waits(ctx, err);
+    if (rc) return rc;
     CK(launch_epilogue(scratch, n, ctx->opt.count_bits, nullptr, C, nullptr, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_scalars, err, sizeof(u32), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if ((u32)ctx->h_scalars[0] != 0) return JSIM_ERR_TIMEOUT;
     return JSIM_OK;
 }

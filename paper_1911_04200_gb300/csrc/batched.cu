@@ -176,7 +176,7 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
         js += cl.n * cl.n * sizeof(double);
         if (cl.n == 0 || (!Cd && !Jd)) continue;
         CK(launch_epilogue((char*)w.cpool.p + cl.c_off, cl.n, ctx->opt.count_bits, w.spool.as<u64>() + cl.s_off, Cd,
-                           Jd, ctx->lanes[c % kLanes], ctx->opt.filter_min == 2, ctx->opt.distance));
+                           Jd, ctx->lanes[c % kLanes], ctx->opt.filter_min == 2, ctx->opt.distance, ctx->d_err));
         ctx->stats.launches += 1;
     }
     return lanes_join(ctx, kLanes);
@@ -538,7 +538,12 @@ replan:
         if (rc) return rc;
     }
 
-    // ---- outputs ----
+    // ---- outputs (none when a bounded device wait ran out: the epilogues
+    // skipped their writes) ----
+    {
+        int rc = check_device_waits(ctx, ctx->d_err);
+        if (rc) return rc;
+    }
     {
         StageTimer t(ctx, &ctx->stats.ms_d2h);
         const cudaMemcpyKind kind = dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -556,9 +561,6 @@ replan:
         }
     }
     CK(cudaStreamSynchronize(ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_scalars, ctx->d_err, sizeof(u32), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    if ((u32)ctx->h_scalars[0] != 0) return JSIM_ERR_TIMEOUT;
     int rc = finish_stats(ctx, w);
     if (!use_graph) jsim_batched_release(ctx);  // nothing to replay: free the wave now
     return rc;

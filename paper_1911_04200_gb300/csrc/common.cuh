@@ -154,7 +154,9 @@ cudaError_t launch_qepi(const u32* Cacc, u64 S, u64 n_ref, const u64* sq, const 
 // distance: J holds D = 1.0 - J instead (binary64; 0 for two empty sets).
 // *acc (device) += sum over the W word columns of rows 0..n-1 of nnz (nnz + 1) / 2.
 cudaError_t launch_useful(const u64* X, u64 n, u64 stride, u64 W, u64* acc, int sms, cudaStream_t st);
+// skip_if (optional, device): the kernel writes nothing when *skip_if != 0
 cudaError_t launch_epilogue(const void* Cacc, u64 n, int count_bits, const u64* sizes,
-                            void* Cout, double* J, cudaStream_t st, int diag_sizes = 0, int distance = 0);
+                            void* Cout, double* J, cudaStream_t st, int diag_sizes = 0, int distance = 0,
+                            const u32* skip_if = nullptr);
 
 }  // namespace jsim

@@ -173,6 +173,17 @@ struct CallScope {
 
 u64 round_up(u64 x, u64 m) { return (x + m - 1) / m * m; }
 
+// Waits for the context's stream and reads the device error word `err` (a
+// bounded device wait ran out when it is nonzero), so that a call can return
+// JSIM_ERR_TIMEOUT before it writes any output.
+int check_device_waits(jsim_ctx* ctx, const u32* err)
+{
+    cudaError_t e = cudaMemcpyAsync(ctx->h_scalars, err, sizeof(u32), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "error word");
+    return (u32)ctx->h_scalars[0] != 0 ? JSIM_ERR_TIMEOUT : JSIM_OK;
+}
+
 // Side streams: work on lane l is ordered after everything queued on the
 // context's stream before lanes_fork, and everything queued on it after
 // lanes_join waits for all lanes.  Under stream capture the lanes become
@@ -335,13 +346,15 @@ int choose_variant(jsim_ctx* ctx, u64 n, u64 W)
     return n <= 160 ? JSIM_VARIANT_TC : JSIM_VARIANT_TC2;
 }
 
-int run_product(jsim_ctx* ctx, int variant, const u64* X, u64 stride, u64 n, u64 W, void* C)
+// The semiring product C += X X^T with the chosen variant; err is the device
+// error word the kernels raise (the context's when null).
+int run_product(jsim_ctx* ctx, int variant, const u64* X, u64 stride, u64 n, u64 W, void* C, u32* err = nullptr)
 {
     ProductArgs a{};
     a.X = X; a.stride = stride; a.n = n; a.W = W; a.C = C; a.ldc = n;
     a.count_bits = ctx->opt.count_bits; a.word_bits = ctx->opt.word_bits; a.sms = ctx->sms;
     a.timeout_ms = ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000;
-    a.err = ctx->d_err;
+    a.err = err ? err : ctx->d_err;
     cudaError_t e = cudaSuccess;
     switch (variant) {
     case JSIM_VARIANT_TC:

@@ -21,8 +21,10 @@ constexpr int kE = 32;
 template <typename CT>
 __global__ void __launch_bounds__(kE * 8)
 k_epilogue(const CT* __restrict__ Cacc, u64 n, const u64* __restrict__ sizes,
-           CT* __restrict__ Cout, double* __restrict__ J, int diag_sizes, int distance)
+           CT* __restrict__ Cout, double* __restrict__ J, int diag_sizes, int distance, const u32* skip_if)
 {
+    // a raised error word (a bounded wait of the product ran out): write nothing
+    if (skip_if && *(volatile const u32*)skip_if) return;
     __shared__ CT tile[kE][kE + 1];
     const u64 bi = blockIdx.y, bj = blockIdx.x;
     const u64 i0 = bi * kE, j0 = bj * kE;
@@ -85,16 +87,18 @@ cudaError_t launch_useful(const u64* X, u64 n, u64 stride, u64 W, u64* acc, int 
 }
 
 cudaError_t launch_epilogue(const void* Cacc, u64 n, int count_bits, const u64* sizes,
-                            void* Cout, double* J, cudaStream_t st, int diag_sizes, int distance)
+                            void* Cout, double* J, cudaStream_t st, int diag_sizes, int distance, const u32* skip_if)
 {
     if (n == 0) return cudaSuccess;
     u64 nb = (n + kE - 1) / kE;
     if (nb > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)nb, (unsigned)nb), block(kE, 8);
     if (count_bits == 64)
-        k_epilogue<u64><<<grid, block, 0, st>>>((const u64*)Cacc, n, sizes, (u64*)Cout, J, diag_sizes, distance);
+        k_epilogue<u64><<<grid, block, 0, st>>>((const u64*)Cacc, n, sizes, (u64*)Cout, J, diag_sizes, distance,
+                                                 skip_if);
     else
-        k_epilogue<u32><<<grid, block, 0, st>>>((const u32*)Cacc, n, sizes, (u32*)Cout, J, diag_sizes, distance);
+        k_epilogue<u32><<<grid, block, 0, st>>>((const u32*)Cacc, n, sizes, (u32*)Cout, J, diag_sizes, distance,
+                                                 skip_if);
     return cudaGetLastError();
 }
 

@@ -624,12 +624,15 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
 
     // ---- input errors, epilogue ----
     CK(cudaMemcpyAsync(ctx->h_scalars, flags.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(ctx->h_scalars + 2, ctx->d_err, sizeof(u32), cudaMemcpyDeviceToHost, cs));
     std::vector<u64> hs(n);
     CK(cudaMemcpyAsync(hs.data(), sizes_d.p, n * sizeof(u64), cudaMemcpyDeviceToHost, cs));
     CK(cudaStreamSynchronize(cs));
     const u32 f = (u32)ctx->h_scalars[0];
     if (f & kFlagUnsorted) return JSIM_ERR_UNSORTED;
     if (f & kFlagIdRange) return JSIM_ERR_ID_RANGE;
+    // nothing is written when a bounded device wait ran out
+    if ((u32)ctx->h_scalars[2] != 0) return JSIM_ERR_TIMEOUT;
     if (ctx->opt.count_bits == 32)
         for (u64 v : hs)
             if (v > 0xffffffffull) return JSIM_ERR_OVERFLOW;

@@ -218,7 +218,11 @@ class Context:
     def __init__(self, device: int = 0, variant: str | int = "auto", batch_rows: int = 0, word_bits: int = 64,
                  count_bits: int = 32, id_bits: int = 64, profile: bool = False, stream=None,
                  use_torch_allocator: bool = True, timeout_ms: int = 2000, filter_min: int = 1,
-                 distance: bool = False, count_useful: bool = False):
+                 distance: bool = False, count_useful: bool = False, allocator=None):
+        """``allocator`` (optional) replaces PyTorch's caching allocator as the
+        library's device allocator: an object with ``alloc(nbytes, stream) ->
+        int`` (a device pointer, or 0 when it cannot serve the request: the
+        library then returns JSIM_ERR_OOM) and ``free(ptr, nbytes, stream)``."""
         torch = _torch()
         self._lib = load()
         self.device = device
@@ -240,7 +244,21 @@ class Context:
         o.count_useful = 1 if count_useful else 0
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         self._keep = []
-        if use_torch_allocator:
+        if allocator is not None:
+            def _alloc_user(nbytes, st, user):
+                try:
+                    return int(allocator.alloc(int(nbytes), int(st or 0))) or None
+                except Exception:
+                    return None
+
+            def _free_user(ptr, nbytes, st, user):
+                if ptr:
+                    allocator.free(int(ptr), int(nbytes), int(st or 0))
+
+            a, f = ALLOC_FN(_alloc_user), FREE_FN(_free_user)
+            self._keep += [a, f]
+            o.alloc, o.free = a, f
+        elif use_torch_allocator:
             dev = device
 
             def _alloc(nbytes, st, user):
