@@ -45,6 +45,7 @@ UNIT = "Tbit-ops/s"
 POPC_PER_CLK_PER_SM = 16        # 32-bit population counts per clock per SM
 SMS = 152
 SM_MAX_MHZ = 2070.0
+LEGACY_INT_MMA_TOPS = 73.0      # mma.sync m16n8k32 s8 / m16n8k256 b1 multiply-adds per second, measured
 
 
 def parse():
@@ -55,15 +56,31 @@ def parse():
     ap.add_argument("--impl", default="jsim", choices=["jsim", "reference"])
     ap.add_argument("--workload", default="clade1024",
                     choices=["clade1024", "ancestral64", "batched200", "stream4096", "serve2048",
-                             "bernoulli10k", "density"])
+                             "bernoulli10k", "density", "product", "serve-one"],
+                    help="product: jsim_product alone on random packed words (--n, --words, --pad, --density, "
+                         "--calls; the capture case of the product kernels); serve-one: a serving index of the "
+                         "reference recipe at --median with requests submitted one at a time (the capture case "
+                         "of the query kernel)")
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--batch-rows", type=int, default=0)
     ap.add_argument("--filter-min", type=int, default=1, choices=[1, 2],
                     help="2: the filter keeps rows two or more samples hold (same C and J, fewer words)")
     ap.add_argument("--split", action="store_true",
                     help="strong scaling: every rank takes one part of the same collection's row batches "
-                         "(jsim_all_pairs_part), one all-reduce sums the counts, rank 0 forms C and J")
+                         "(jsim_all_pairs_part), one all-reduce sums the counts, rank 0 forms C and J "
+                         "(the default for the default workload on more than one rank)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="on more than one rank: every rank runs its own collection (weak scaling, no "
+                         "collective) instead of the split contraction")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="default workload: skip the serving, batched and two-or-more-filter sub-measurements")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--words", type=int, default=32768)
+    ap.add_argument("--pad", type=int, default=0, help="product: words of padding after every row")
+    ap.add_argument("--density", type=float, default=0.25, help="product: bit density of the random words")
+    ap.add_argument("--calls", type=int, default=3)
+    ap.add_argument("--median", type=float, default=2e4, help="serve-one: set-size median of the reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -230,11 +247,16 @@ def roofline_for(variant, bitops_per_launch, ms_per_launch, peaks, traffic):
     # tensor variants: one 0/1 multiply-add per bit-operation, 2 FLOP each;
     # fp8 dense peak = measured bf16 (sustained) x 2 (nominal fp8:bf16 ratio)
     pk, src = peaks
-    flops = 2.0 * achieved_t
     if variant in ("i8", "b1"):
-        peak = pk.get("bf16_tflops_sustained", 1700.0) * 2.0
-    else:
-        peak = pk.get("bf16_tflops_sustained", 1700.0) * 2.0
+        # the legacy integer/binary mma.sync pipe: one bit-operation per 0/1
+        # multiply-add (i8) or per AND+popcount bit (b1); its rate measured on
+        # this GPU with the kernels' own instruction shapes
+        peak = LEGACY_INT_MMA_TOPS
+        return {"bound": "tensor", "achieved": round(achieved_t, 3), "peak": peak, "unit": "Tbit-ops/s",
+                "frac": round(achieved_t / peak, 4), "traffic": traffic,
+                "peak_source": "measured legacy mma.sync s8/b1 issue rate (%.0f T ops/s)" % peak}
+    flops = 2.0 * achieved_t
+    peak = pk.get("bf16_tflops_sustained", 1700.0) * 2.0
     return {"bound": "tensor", "achieved": round(flops, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
             "frac": round(flops / peak, 4), "traffic": traffic,
             "peak_source": "%s bf16 sustained x 2 (fp8:bf16 nominal ratio)" % src}
@@ -303,21 +325,19 @@ def run_reference(args):
     return 0
 
 
-def run_batched(args):
-    """200 independent collections (n ~ U{8..512}, log-normal sizes, clade
-    model): one jsim_all_pairs_batched call per step (persistent multi-
-    collection launch, CUDA-graph replay) against one jsim_all_pairs call per
-    collection, same device-resident inputs and outputs."""
+def batched_measure(cols, steps, warmup, batch_rows=0):
+    """Independent collections [(offsets, ids), ...] in device memory: one
+    jsim_all_pairs_batched call per step (persistent multi-collection launch,
+    CUDA-graph replay) against one jsim_all_pairs call per collection, same
+    inputs and outputs; both checked equal.  Returns a dict of the timings."""
+    import ctypes
     import torch
-    from paper_1911_04200_gb300 import jsim, synth
+    from paper_1911_04200_gb300 import jsim
     dev = torch.device("cuda", 0)
-    median = float(os.environ.get("JSIM_BATCHED_MEDIAN", "2e4"))
-    cols = synth.batched_collections(median=median, lo=1e4, hi=5e6)
     dcols = [(torch.from_numpy(o.view(np.int64)).to(dev), torch.from_numpy(i.view(np.int64)).to(dev)) for o, i in cols]
     N = sum(int(o[-1]) for o, _ in cols)
-    ctx = jsim.Context(device=0, id_bits=32, profile=False, batch_rows=args.batch_rows)
+    ctx = jsim.Context(device=0, id_bits=32, profile=False, batch_rows=batch_rows)
     # preallocated outputs so the captured graph is replayed every step
-    import ctypes
     k = len(dcols)
     Cs = [torch.empty((len(o) - 1, len(o) - 1), dtype=torch.uint32, device=dev) for o, _ in cols]
     Ss = [torch.empty(len(o) - 1, dtype=torch.uint64, device=dev) for o, _ in cols]
@@ -335,44 +355,60 @@ def run_batched(args):
         jsim._check(rc, ctx._h)
         return ctx.stats()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         st = call()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(ctx.stream)
     bo = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         st = call()
         bo += st["bitops_dense"]
     e1.record(ctx.stream)
     torch.cuda.synchronize()
-    ms_b = e0.elapsed_time(e1) / args.steps
+    ms_b = e0.elapsed_time(e1) / steps
     variant = st["variant"]
+    batched_J = [j.clone() for j in Js]
     # plain: one all-pairs call per collection
     pctx = jsim.Context(device=0, id_bits=32)
     plain_out = [(Cs[c], Ss[c], Js[c]) for c in range(k)]
-    for _ in range(1):
-        for c, (o, i) in enumerate(dcols):
-            pctx.all_pairs(o, i, out=plain_out[c])
+    for c, (o, i) in enumerate(dcols):
+        pctx.all_pairs(o, i, out=plain_out[c])
     torch.cuda.synchronize()
     e0.record(pctx.stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for c, (o, i) in enumerate(dcols):
             pctx.all_pairs(o, i, out=plain_out[c])
     e1.record(pctx.stream)
     torch.cuda.synchronize()
-    ms_p = e0.elapsed_time(e1) / args.steps
-    bitops = bo / args.steps
-    line = {"metric": METRIC, "value": bitops / (ms_b * 1e-3) / 1e12, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+    ms_p = e0.elapsed_time(e1) / steps
+    same = all(bool(torch.equal(a.view(torch.int64), b.view(torch.int64))) for a, b in zip(batched_J, Js))
+    ctx.close()
+    pctx.close()
+    bitops = bo / steps
+    return {"ms_batched": ms_b, "ms_plain": ms_p, "speedup_vs_plain": ms_p / ms_b, "variant": variant,
+            "bitops_dense_per_step": bitops, "value": bitops / (ms_b * 1e-3) / 1e12,
+            "plain_value": bitops / (ms_p * 1e-3) / 1e12, "collections": k,
+            "samples": sum(len(o) - 1 for o, _ in cols), "values": N, "same_J_as_plain": same}
+
+
+def run_batched(args):
+    """200 independent collections (n ~ U{8..512}, log-normal sizes, clade
+    model): the batched call against one plain call per collection."""
+    from paper_1911_04200_gb300 import synth
+    median = float(os.environ.get("JSIM_BATCHED_MEDIAN", "2e4"))
+    cols = synth.batched_collections(median=median, lo=1e4, hi=5e6)
+    m = batched_measure(cols, args.steps, args.warmup, args.batch_rows)
+    line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms_batched"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
             "config": {"workload": "batched200: 200 collections, n ~ U{8..512}, log-normal sizes median %.0e, "
                                    "values in [0,2^32), ceil(n/32) clades" % median,
-                       "collections": k, "samples": sum(len(o) - 1 for o, _ in cols), "values": N,
-                       "variant": variant, "bitops_dense_per_step": bitops},
-            "plain": {"value": bitops / (ms_p * 1e-3) / 1e12, "ms_per_step": ms_p,
+                       "collections": m["collections"], "samples": m["samples"], "values": m["values"],
+                       "variant": m["variant"], "bitops_dense_per_step": m["bitops_dense_per_step"]},
+            "plain": {"value": m["plain_value"], "ms_per_step": m["ms_plain"],
                       "how": "one jsim_all_pairs call per collection (AUTO variant), same inputs/outputs"},
-            "speedup_vs_plain": ms_p / ms_b}
+            "speedup_vs_plain": m["speedup_vs_plain"], "same_J_as_plain": m["same_J_as_plain"]}
     print(json.dumps(line))
     return 0
 
@@ -461,20 +497,16 @@ def run_streamed(args):
     return 0
 
 
-def run_serve(args):
+def serve_measure(median, n_req, slots, warmup, pool=512, plain_requests=2):
     """Serving: a resident index of a 2048-sample reference (values in
-    [0, 2^32), log-normal sizes, 64 clades) and requests of U{1..64} query
-    samples from the same clades.  Capacity = requests/s of a closed burst;
-    then Poisson arrivals at 0.5, 0.8 and 0.95 x capacity with p50/p99
-    request latency (submit to results ready, host clock).  The plain form
-    answers a request with one jsim_all_pairs call on reference + query
-    samples (the only way to get query x reference counts without an index)."""
-    import threading
-    import torch
+    [0, 2^32), log-normal sizes of the given median, 64 clades) and requests
+    of U{1..64} query samples from the same clades.  Capacity = requests/s of
+    a closed burst; then Poisson arrivals at 0.5, 0.8 and 0.95 x capacity with
+    p50/p99 request latency (submit to results ready, host clock).  The plain
+    form answers a request with one jsim_all_pairs call on reference + query
+    samples (the only way to get query x reference counts without an index);
+    its results equal the index's.  Returns a dict."""
     from paper_1911_04200_gb300 import jsim, synth
-    median = float(os.environ.get("JSIM_SERVE_MEDIAN", "1e5"))
-    n_req = int(os.environ.get("JSIM_SERVE_REQUESTS", "400"))
-    pool = 512
     roff, rids = synth.serving_reference(median=median)
     qoff, qids = synth.serving_queries(0, pool, median=median)
     n_ref = len(roff) - 1
@@ -489,10 +521,9 @@ def run_serve(args):
     max_vals = int(np.sort(sizes)[-64:].sum())
     ctx = jsim.Context(device=0, id_bits=32)
     t0 = time.perf_counter()
-    slots = int(os.environ.get("JSIM_SERVE_SLOTS", "3"))
     ix = jsim.Index(ctx, roff, rids, max_batch_samples=64, max_batch_values=max_vals, slots=slots)
     build_ms = (time.perf_counter() - t0) * 1e3
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         ix.submit(*request()).wait()
 
     def run(reqs, gaps=None):
@@ -535,10 +566,9 @@ def run_serve(args):
                               "p50_ms": round(float(np.percentile(lt, 50)), 3),
                               "p99_ms": round(float(np.percentile(lt, 99)), 3),
                               "mean_ms": round(float(lt.mean()), 3)}
-    # plain: one all-pairs call on reference + query samples per request
     plain_ms = []
     pctx = jsim.Context(device=0, id_bits=32)
-    for k in range(2):
+    for k in range(plain_requests):
         o, v = reqs[k]
         off = np.concatenate([roff, roff[-1] + o[1:]]).astype(np.uint64)
         ids = np.concatenate([rids, v])
@@ -550,6 +580,7 @@ def run_serve(args):
         h.free()
         assert np.array_equal(Cs, C[n_ref:, :n_ref]) and np.array_equal(Js.view(np.uint64),
                                                                          J[n_ref:, :n_ref].view(np.uint64))
+    pctx.close()
     pk, src = measured_peaks()
     # algorithmic bytes of the query kernel: per row read, the row plus the
     # value's 8 bytes and its 16-byte filter entry (word, rank of its first bit)
@@ -563,29 +594,49 @@ def run_serve(args):
             "kernel": "k_qrows", "peak_source": "%s HBM copy bandwidth" % src,
             "unit_bytes": "per query value the filter holds: its row (ceil(n_ref/64) x 8 B) + 8 B value + "
                           "16 B filter entry (word, rank of its first bit)"}
-    line = {"metric": METRIC, "value": capacity, "unit": "requests/s", "n_gpus": 1, "steps": n_req,
-            "warmup": args.warmup, "ms_per_step": elapsed / n_req * 1e3, "higher_is_better": True,
+    out = {"capacity_rps": capacity, "elapsed_s": elapsed, "requests": n_req, "query_samples": samples,
+           "samples_per_s": samples / elapsed, "latency": levels, "clocks": clk.summary(), "roofline": roof,
+           "index_rows": ix.rows, "index_bytes": ix.rows * ((n_ref + 63) // 64) * 8, "build_ms": round(build_ms, 1),
+           "batches": d["batches"], "samples_per_batch": d["samples_done"] / max(1, d["batches"]),
+           "device_ms_per_batch": d["ms_device"] / max(1, d["batches"]),
+           "qprod_ms_per_batch": d["ms_product"] / max(1, d["batches"]),
+           "rows_read_per_batch": d["rows_read"] / max(1, d["batches"]),
+           "values_per_request": d["values_done"] / n_req, "n_ref": n_ref, "slots": slots,
+           "plain_ms_per_request": float(np.mean(plain_ms)),
+           "speedup_vs_plain": capacity * float(np.mean(plain_ms)) / 1e3}
+    ix.close()
+    ctx.close()
+    return out
+
+
+def run_serve(args):
+    """The serving workload (serve_measure) as its own JSON line."""
+    median = float(os.environ.get("JSIM_SERVE_MEDIAN", "1e5"))
+    n_req = int(os.environ.get("JSIM_SERVE_REQUESTS", "400"))
+    slots = int(os.environ.get("JSIM_SERVE_SLOTS", "3"))
+    m = serve_measure(median, n_req, slots, args.warmup)
+    n_ref = m["n_ref"]
+    line = {"metric": METRIC, "value": m["capacity_rps"], "unit": "requests/s", "n_gpus": 1, "steps": n_req,
+            "warmup": args.warmup, "ms_per_step": m["elapsed_s"] / n_req * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
             "config": {"workload": "serve2048: reference n=2048, values in [0,2^32), log-normal sizes median "
                                    "%.0e (x/10-10x), 64 clades; requests of U{1..64} query samples of the same "
                                    "recipe" % median,
-                       "index_rows": ix.rows, "index_bytes": ix.rows * ((n_ref + 63) // 64) * 8,
-                       "build_ms": round(build_ms, 1), "requests": n_req, "query_samples": samples,
-                       "samples_per_s": samples / elapsed, "batches": d["batches"],
-                       "samples_per_batch": d["samples_done"] / max(1, d["batches"]),
-                       "device_ms_per_batch": d["ms_device"] / max(1, d["batches"]),
-                       "qprod_ms_per_batch": d["ms_product"] / max(1, d["batches"]),
-                       "rows_read_per_batch": d["rows_read"] / max(1, d["batches"]),
-                       "l2": "index (%.1f GB) larger than L2; no flush" % (ix.rows * n_ref / 8 / 1e9)},
-            "latency": levels, "clocks": clk.summary(), "gpu_launches": int(10 * d["batches"]), "roofline": roof,
-            "e2e": {"value": capacity, "unit": "requests/s",
-                    "h2d_bytes_per_step": int(d["values_done"] * 8 / n_req),
-                    "d2h_bytes_per_step": int(samples * n_ref * 12 / n_req)},
-            "plain": {"ms_per_request": float(np.mean(plain_ms)), "value": 1e3 / float(np.mean(plain_ms)),
+                       "index_rows": m["index_rows"], "index_bytes": m["index_bytes"], "build_ms": m["build_ms"],
+                       "requests": n_req, "query_samples": m["query_samples"], "samples_per_s": m["samples_per_s"],
+                       "batches": m["batches"], "samples_per_batch": m["samples_per_batch"],
+                       "device_ms_per_batch": m["device_ms_per_batch"], "qprod_ms_per_batch": m["qprod_ms_per_batch"],
+                       "rows_read_per_batch": m["rows_read_per_batch"],
+                       "l2": "index (%.1f GB) larger than L2; no flush" % (m["index_bytes"] / 1e9)},
+            "latency": m["latency"], "clocks": m["clocks"], "gpu_launches": int(10 * m["batches"]),
+            "roofline": m["roofline"],
+            "e2e": {"value": m["capacity_rps"], "unit": "requests/s",
+                    "h2d_bytes_per_step": int(m["values_per_request"] * 8),
+                    "d2h_bytes_per_step": int(m["query_samples"] * n_ref * 12 / n_req)},
+            "plain": {"ms_per_request": m["plain_ms_per_request"], "value": 1e3 / m["plain_ms_per_request"],
                       "how": "one jsim_all_pairs call on reference + the request's samples (host in/out)"},
-            "speedup_vs_plain": capacity * float(np.mean(plain_ms)) / 1e3}
+            "speedup_vs_plain": m["speedup_vs_plain"]}
     print(json.dumps(line))
-    ix.close()
     return 0
 
 
@@ -645,6 +696,100 @@ def run_split(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def one_copy_gbs(ids, dev):
+    """Rate of one 1 GiB copy from the page-locked input to the device (the
+    link alone, nothing overlapping), outside any timed region."""
+    import torch
+    t = torch.from_numpy(ids.view(np.int64))
+    m = min(t.numel(), 1 << 27)
+    d = torch.empty(m, dtype=torch.int64, device=dev)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        d.copy_(t[:m], non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, m * 8 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return round(best, 1)
+
+
+def numa_of_buffer(a):
+    """The NUMA placement of a host buffer's pages as the kernel reports it
+    (the /proc/self/numa_maps line of the mapping holding it)."""
+    addr = a.ctypes.data
+    try:
+        best = None
+        with open("/proc/self/numa_maps") as f:
+            for line in f:
+                start = int(line.split()[0], 16)
+                if start <= addr:
+                    best = line
+                else:
+                    break
+        if best is None:
+            return None
+        keep = [w for w in best.split()[1:] if w.startswith(("N", "kernelpagesize", "prefer", "bind", "default"))]
+        return " ".join(keep)
+    except Exception:
+        return None
+
+
+def systems_measure(args, d_off, d_ids, J_ref, cfg):
+    """Bounded sub-measurements beside the default line: the same all-pairs
+    call with the two-or-more filter (same C and J, fewer words), the batched
+    call against one plain call per collection on a subset of the batched
+    recipe at its full set-size median, and the serving index on a reduced
+    reference (capacity, p50/p99 under Poisson arrivals, against the plain
+    form)."""
+    import torch
+    from paper_1911_04200_gb300 import jsim, synth
+    out = {}
+    n = cfg["n"]
+    dev = d_off.device
+    # two-or-more filter, same device-resident inputs
+    fctx = jsim.Context(device=dev.index, id_bits=cfg["id_bits"], filter_min=2, profile=True)
+    C2 = torch.empty((n, n), dtype=torch.uint32, device=dev)
+    S2 = torch.empty(n, dtype=torch.uint64, device=dev)
+    J2 = torch.empty((n, n), dtype=torch.float64, device=dev)
+    fctx.all_pairs(d_off, d_ids, out=(C2, S2, J2))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(fctx.stream)
+    for _ in range(args.steps):
+        fctx.all_pairs(d_off, d_ids, out=(C2, S2, J2))
+    e1.record(fctx.stream)
+    torch.cuda.synchronize()
+    st = fctx.stats()
+    out["filter_min2"] = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "words": st["words"],
+                          "rows_nonzero": st["rows_nonzero"],
+                          "same_J": bool(torch.equal(J2.view(torch.int64), J_ref.view(torch.int64))),
+                          "how": "jsim_all_pairs with filter_min 2 (rows two or more samples hold) on the "
+                                 "default workload's device-resident inputs"}
+    fctx.close()
+    del C2, S2, J2
+    # batched: a subset of the batched recipe at its full median
+    count = int(os.environ.get("JSIM_SYSTEMS_BATCHED_COUNT", "24"))
+    t0 = time.perf_counter()
+    cols = synth.batched_collections(count=count, median=2e5, lo=1e4, hi=5e6)
+    gen_s = time.perf_counter() - t0
+    m = batched_measure(cols, steps=2, warmup=1)
+    m["config"] = ("the first %d collections of the batched recipe (n ~ U{8..512}, log-normal sizes median 2e5 "
+                   "in [1e4, 5e6], values in [0,2^32), ceil(n/32) clades), device-resident" % count)
+    m["generation_s"] = round(gen_s, 1)
+    out["batched"] = m
+    del cols
+    # serving: reduced reference
+    median = float(os.environ.get("JSIM_SYSTEMS_SERVE_MEDIAN", "1e5"))
+    sm = serve_measure(median, n_req=int(os.environ.get("JSIM_SYSTEMS_SERVE_REQUESTS", "300")), slots=3, warmup=2)
+    sm["config"] = ("reference of 2048 samples, log-normal sizes median %.0e (x/10-10x, the recipe's median "
+                    "is 1e6), values in [0,2^32), 64 clades; requests of U{1..64} query samples of the same "
+                    "recipe" % median)
+    out["serving"] = sm
+    return out
 
 
 def run_jsim(args):
@@ -719,10 +864,24 @@ def run_jsim(args):
             bo += ctx.stats()["bitops_dense"]
         barrier()
         dt, bo = aggregate_over_ranks(time.perf_counter() - t0, bo, dev)
+        se = ctx.stats()  # the last end-to-end call (stage timers on)
+        e2e_ms = dt / args.steps * 1e3
         e2e = {"value": bo / dt / 1e12, "unit": UNIT, "h2d_bytes_per_step": int((n + 1) * 8 + N * 8),
-               "d2h_bytes_per_step": int(n * n * 4 + n * 8 + n * n * 8), "ms_per_step": dt / args.steps * 1e3}
-        # parity spot check of the e2e outputs against the device-resident run
-        assert np.array_equal(hJ.view(np.uint64)[:4, :4], J[:4, :4].cpu().numpy().view(np.uint64))
+               "d2h_bytes_per_step": int(n * n * 4 + n * 8 + n * n * 8), "ms_per_step": e2e_ms,
+               "exposed_ms_per_step": round(e2e_ms - ms_max / args.steps, 2),
+               "h2d_copies_per_step": int(se["h2d_copies"]),
+               "h2d_copy_stream_busy_ms": round(se["ms_h2d"], 2),
+               "h2d_gbs_while_overlapped": round(se["h2d_bytes"] / (se["ms_h2d"] * 1e-3) / 1e9, 1)
+               if se["ms_h2d"] else None,
+               "h2d_gbs_one_1gib_copy": one_copy_gbs(ids, dev),
+               "host_input_memory": numa_of_buffer(ids),
+               "path": "host input above 4 GiB: streamed through two 1 GiB pinned staging buffers, "
+                       "copies overlapping the device's work (super-batches planned one ahead)"}
+        # the whole end-to-end result equals the device-resident run's
+        assert np.array_equal(hJ.view(np.uint64), J.cpu().numpy().view(np.uint64))
+        assert np.array_equal(hC, C.view(torch.int32).cpu().numpy().view(np.uint32))
+        assert np.array_equal(hS, S.view(torch.int64).cpu().numpy().view(np.uint64))
+        e2e["parity"] = "whole C, sizes and J bit-identical to the device-resident call"
 
     # the method's useful work (pairs of nonzero packed words, the count a
     # sparse product needs) and the compulsory bytes, from one more untimed call
@@ -754,6 +913,8 @@ def run_jsim(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
             "config": cfg, "clocks": clk.summary(), "gpu_launches": agg["launches"], "roofline": roof, "e2e": e2e}
+    if world == 1 and not args.no_systems and args.workload == "clade1024":
+        line["systems"] = systems_measure(args, d_off, d_ids, J, cfg)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(off, ids, n, last["bitops_dense"], args.cpu_seconds)
     if rank == 0:
@@ -825,8 +986,80 @@ def run_density(args):
     return 0
 
 
+def run_product(args):
+    """The semiring product alone (jsim_product) on random packed words
+    already in device memory: n rows of `words` words (bit density
+    `density`; random 64-bit words above 2^23 words in all), optionally
+    padded rows, `calls` calls; prints the product time and Tbit-ops/s.  The
+    small, self-contained case the product kernels are captured on."""
+    import torch
+    from paper_1911_04200_gb300 import jsim
+    n, W = args.n, args.words
+    g = torch.Generator(device="cuda").manual_seed(7)
+    if n * W <= (1 << 23):
+        bits = torch.rand((n, W * 64), device="cuda", generator=g) < args.density
+        w = torch.zeros((n, W), dtype=torch.int64, device="cuda")
+        for k in range(64):
+            w |= bits[:, k::64].to(torch.int64) << k
+        del bits
+        dens = args.density
+    else:
+        w = torch.randint(-2**63, 2**63 - 1, (n, W), dtype=torch.int64, device="cuda", generator=g)
+        dens = 0.5
+    stride = W + args.pad
+    if args.pad:
+        wp = torch.zeros((n, stride), dtype=torch.int64, device="cuda")
+        wp[:, :W] = w
+        w = wp
+    ctx = jsim.Context(variant=args.variant, count_bits=32, profile=True)
+    C = torch.empty((n, n), dtype=torch.uint32, device="cuda")
+    for _ in range(args.calls):
+        ctx.product(w, n, W, stride, C=C, variant=args.variant)
+        st = ctx.stats()
+    torch.cuda.synchronize()
+    t = st["ms_product"]
+    v = st["bitops_dense"] / (t * 1e-3) / 1e12
+    roof = roofline_for(st["variant"], st["bitops_dense"] / max(1, st["product_launches"]),
+                        t / max(1, st["product_launches"]), measured_peaks(), None)
+    print(json.dumps({"workload": "product", "variant": st["variant"], "n": n, "words": W, "stride": stride,
+                      "bit_density": dens, "ms_product": t, "value": v, "unit": UNIT, "roofline": roof}))
+    ctx.close()
+    return 0
+
+
+def run_serve_one(args):
+    """A serving index of the 2048-sample reference recipe at a reduced set-
+    size median and `calls` requests of 64 query samples submitted one at a
+    time (one device batch each, nothing overlapping), so every query kernel
+    runs alone: the case the query kernel is captured on."""
+    from paper_1911_04200_gb300 import jsim, synth
+    roff, rids = synth.serving_reference(median=args.median)
+    qoff, qids = synth.serving_queries(0, 64, median=args.median)
+    ctx = jsim.Context(id_bits=32)
+    ix = jsim.Index(ctx, roff, rids, max_batch_samples=64, max_batch_values=int(qoff[-1]), slots=1)
+    dt = 0.0
+    for _ in range(args.calls):
+        t0 = time.perf_counter()
+        ix.submit(qoff, qids).wait()
+        dt = time.perf_counter() - t0
+    st = ix.stats()
+    b = max(1, st["batches"])
+    print(json.dumps({"workload": "serve-one", "median": args.median, "index_rows": ix.rows,
+                      "index_bytes": ix.rows * 2048 // 8, "batches": st["batches"],
+                      "rows_read_per_batch": st["rows_read"] / b, "qrows_ms_per_batch": st["ms_product"] / b,
+                      "index_row_gbs": st["index_bytes_read"] / (st["ms_product"] * 1e-3) / 1e9
+                      if st["ms_product"] else None, "last_request_ms": dt * 1e3}))
+    ix.close()
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "product":
+        return run_product(args)
+    if args.workload == "serve-one":
+        return run_serve_one(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched200":
@@ -837,7 +1070,8 @@ def main():
         return run_serve(args)
     if args.workload == "density":
         return run_density(args)
-    if args.split:
+    world = dist_env()[0]
+    if args.split or (world > 1 and not args.replicas and args.workload == "clade1024"):
         return run_split(args)
     return run_jsim(args)
 

@@ -152,6 +152,8 @@ typedef struct {
                                   nnz(nnz+1)/2, nnz the rows whose word is nonzero - the pairs of
                                   nonzero words, the work a sparse product needs (the operation
                                   count depends on the sparsity structure, Sec. IV); else 0 */
+    uint64_t h2d_copies;       /* host -> device copies the call issued for its input values */
+    uint64_t h2d_bytes;        /* bytes of those copies */
 } jsim_stats;
 
 /* Fill *opt with the defaults described above. */

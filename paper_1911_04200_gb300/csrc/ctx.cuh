@@ -280,6 +280,8 @@ int stage_and_validate(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std:
                                ctx->stream));
             if (st.N)
                 CK(cudaMemcpyAsync(st.ids_buf.p, s->ids, st.N * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
+            ctx->stats.h2d_copies += st.N ? 2 : 1;
+            ctx->stats.h2d_bytes += (st.n + 1 + st.N) * sizeof(u64);
             st.d_off = st.off_buf.as<u64>();
             st.d_ids = st.ids_buf.as<u64>();
         } else {

@@ -31,13 +31,23 @@
 // is that of one uninterrupted call.
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <string>
 #include <thread>
 #include "ctx.cuh"
 
+// Copy streams of a streamed call: page-locked input is copied slice by
+// slice, and slices spread over several streams keep several copy engines
+// busy (small copies one after another on one stream leave the link idle
+// between them).
+constexpr int kCopyStreams = 4;
+
 struct StreamState {
     int device = -1;
-    cudaStream_t xs = nullptr;  // copy stream
+    cudaStream_t xs = nullptr;  // copy stream (the first of kCopyStreams)
+    cudaStream_t xs_more[kCopyStreams - 1] = {};
+    cudaEvent_t fork[2] = {nullptr, nullptr};
+    cudaEvent_t joined[2][kCopyStreams - 1] = {};
     u64* pin[2] = {nullptr, nullptr};
     size_t pin_words = 0;
     cudaEvent_t copied[2] = {nullptr, nullptr}, released[2] = {nullptr, nullptr};
@@ -48,12 +58,19 @@ void jsim_streamed_release(jsim_ctx* ctx)
     StreamState* s = ctx->streamed;
     if (!s) return;
     if (s->xs) cudaStreamSynchronize(s->xs);
+    for (cudaStream_t x : s->xs_more)
+        if (x) cudaStreamSynchronize(x);
     for (int k = 0; k < 2; ++k) {
         if (s->pin[k]) cudaFreeHost(s->pin[k]);
         if (s->copied[k]) cudaEventDestroy(s->copied[k]);
         if (s->released[k]) cudaEventDestroy(s->released[k]);
+        if (s->fork[k]) cudaEventDestroy(s->fork[k]);
+        for (cudaEvent_t e : s->joined[k])
+            if (e) cudaEventDestroy(e);
     }
     if (s->xs) cudaStreamDestroy(s->xs);
+    for (cudaStream_t x : s->xs_more)
+        if (x) cudaStreamDestroy(x);
     cudaGetLastError();
     delete s;
     ctx->streamed = nullptr;
@@ -69,9 +86,12 @@ int stream_state(jsim_ctx* ctx, size_t words, StreamState*& out)
         s->device = ctx->opt.device;
         ctx->streamed = s;
         CK(cudaStreamCreateWithFlags(&s->xs, cudaStreamNonBlocking));
+        for (cudaStream_t& x : s->xs_more) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
         for (int k = 0; k < 2; ++k) {
             CK(cudaEventCreateWithFlags(&s->copied[k], cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&s->released[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&s->fork[k], cudaEventDisableTiming));
+            for (cudaEvent_t& e : s->joined[k]) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         }
     }
     StreamState* s = ctx->streamed;
@@ -99,91 +119,152 @@ u64 lower_bound_host(const uint64_t* a, u64 lo, u64 hi, u64 v)
     return lo;
 }
 
+// The same search started at lo, galloping (steps 1, 2, 4, ...) before
+// bisecting: the cut a super-batch boundary makes in a sample lies shortly
+// after the previous cut, so this touches a few cache lines near it instead
+// of bisecting the whole sample.  Like any bisection it leaves q with
+// a[q-1] < v (or q = lo) and a[q] >= v (or q = hi), probed.
+u64 gallop_host(const uint64_t* a, u64 lo, u64 hi, u64 v)
+{
+    u64 step = 1, base = lo;
+    while (base + step <= hi && base + step - 1 < hi && a[base + step - 1] < v) {
+        base += step;
+        step *= 2;
+    }
+    return lower_bound_host(a, base, std::min(hi, base + step - 1), v);
+}
+
 struct Super {
     u64 b0 = 0, b1 = 0;  // row batches [b0, b1)
     u64 count = 0;       // values in the super-batch
     std::vector<u64> beg, len, off;  // per sample: slice start, length, staging offset
 };
 
-// Per-sample slices of the values in [lo, hi) (hi == 0: unbounded above).
-void slice(const std::vector<u64>& hoff, const uint64_t* ids, u64 n, u64 lo, u64 hi, Super& s)
+// Per-sample slices of the values below hi (hi == 0: unbounded above), each
+// starting at pos[i], the sample's previous cut.  The searches of different
+// samples are independent and run on several host threads for large n.
+void slice(const std::vector<u64>& hoff, const uint64_t* ids, u64 n, const std::vector<u64>& pos, u64 hi, Super& s)
 {
     s.beg.resize(n);
     s.len.resize(n);
     s.off.resize(n + 1);
+    auto cut = [&](u64 i0, u64 i1) {
+        for (u64 i = i0; i < i1; ++i) {
+            const u64 p = pos[i], b = hoff[i + 1];
+            const u64 q = hi == 0 ? b : gallop_host(ids, p, b, hi);
+            s.beg[i] = p;
+            s.len[i] = q - p;
+        }
+    };
+    const unsigned nt = n >= 512 ? std::max(1u, std::min(8u, std::thread::hardware_concurrency())) : 1u;
+    if (nt == 1) {
+        cut(0, n);
+    } else {
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; ++t) th.emplace_back(cut, n * t / nt, n * (t + 1) / nt);
+        for (auto& x : th) x.join();
+    }
     u64 acc = 0;
     for (u64 i = 0; i < n; ++i) {
-        const u64 a = hoff[i], b = hoff[i + 1];
-        const u64 p = lower_bound_host(ids, a, b, lo);
-        const u64 q = hi == 0 ? b : lower_bound_host(ids, p, b, hi);
-        s.beg[i] = p;
-        s.len[i] = q - p;
         s.off[i] = acc;
-        acc += q - p;
+        acc += s.len[i];
     }
     s.off[n] = acc;
     s.count = acc;
 }
 
-// Cut [min value, max value] into super-batches of at most `cap_vals` values
-// and `rb_cap` row batches of `mt` rows each; ranges without values are
-// skipped.  Returns JSIM_ERR_UNSORTED when the slices do not tile every
-// sample (the input is not sorted), JSIM_ERR_OOM when one row batch alone
-// holds more values than the staging.
-int plan_supers(const std::vector<u64>& hoff, const uint64_t* ids, u64 n, u64 mt, u64 cap_vals, u64 rb_cap,
-                std::vector<Super>& out)
-{
-    u64 minid = ~0ull, maxid = 0;
-    for (u64 i = 0; i < n; ++i) {
-        const u64 a = hoff[i], b = hoff[i + 1];
-        if (b == a) continue;
-        if (ids[a] > ids[b - 1]) return JSIM_ERR_UNSORTED;
-        minid = std::min<u64>(minid, ids[a]);
-        maxid = std::max<u64>(maxid, ids[b - 1]);
+// Cuts [min value, max value] into super-batches of at most `cap_vals` values
+// and `rb_cap` row batches of `mt` rows each, one at a time (the next one is
+// planned on the host while the device multiplies the current one); ranges
+// without values are skipped.  Every sample is cut where its values reach a
+// boundary, searching forward from its previous cut; together with the
+// device's check that every slice is sorted, the cut property (the value
+// before a cut is below the boundary, the one at it is not) proves the whole
+// sample sorted, and values left over after the last super-batch give
+// JSIM_ERR_UNSORTED.  JSIM_ERR_OOM when one row batch alone holds more values
+// than the staging.
+struct SuperPlanner {
+    const std::vector<u64>& hoff;
+    const uint64_t* ids;
+    u64 n, mt, cap_vals, rb_cap;
+    u64 first = 0, last = 0, per0 = 1, b = 0;
+    std::vector<u64> pos;
+    bool done = false;
+
+    SuperPlanner(const std::vector<u64>& hoff_, const uint64_t* ids_, u64 n_, u64 mt_, u64 cap_vals_, u64 rb_cap_)
+        : hoff(hoff_), ids(ids_), n(n_), mt(mt_), cap_vals(cap_vals_), rb_cap(rb_cap_)
+    {
     }
-    const u64 N = hoff[n];
-    if (N == 0) return JSIM_OK;
-    const u64 first = minid / mt, last = maxid / mt;
-    // row batches per super-batch from the average density, 25 % headroom
-    const double per_d = (double)cap_vals / ((double)N / (double)(last - first + 1)) / 1.25;
-    const u64 per0 = per_d >= (double)rb_cap ? rb_cap : std::max<u64>(1, (u64)per_d);
-    std::vector<u64> pos(hoff.begin(), hoff.end() - 1);
-    u64 b = first, per = per0;
-    for (;;) {
-        const u64 e = std::min(last + 1, b + per);
-        Super s;
-        s.b0 = b;
-        s.b1 = e;
-        slice(hoff, ids, n, b * mt, e * mt, s);  // e * mt wraps to 0 only at the top of the range
-        if (s.count > cap_vals) {
-            if (e - b == 1) return JSIM_ERR_OOM;
-            per = (e - b) / 2;
-            continue;
-        }
-        u64 maxv = 0;
+
+    int init()
+    {
+        u64 minid = ~0ull, maxid = 0;
         for (u64 i = 0; i < n; ++i) {
-            if (s.beg[i] != pos[i]) return JSIM_ERR_UNSORTED;
-            pos[i] += s.len[i];
-            if (s.len[i]) maxv = std::max<u64>(maxv, ids[s.beg[i] + s.len[i] - 1]);
+            const u64 a = hoff[i], e = hoff[i + 1];
+            if (e == a) continue;
+            if (ids[a] > ids[e - 1]) return JSIM_ERR_UNSORTED;
+            minid = std::min<u64>(minid, ids[a]);
+            maxid = std::max<u64>(maxid, ids[e - 1]);
         }
-        if (s.count) s.b1 = std::max(b + 1, std::min(e, maxv / mt + 1));  // drop empty trailing row batches
-        // first value at or above the range, to skip empty row batches
-        u64 nv = ~0ull;
-        bool more = false;
-        if (e <= last)
-            for (u64 i = 0; i < n; ++i) {
-                const u64 q = s.beg[i] + s.len[i];
-                if (q < hoff[i + 1]) { more = true; nv = std::min<u64>(nv, ids[q]); }
-            }
-        if (s.count) out.push_back(std::move(s));
-        if (!more) break;
-        b = std::max(e, nv / mt);
-        per = per0;
+        const u64 N = hoff[n];
+        pos.assign(hoff.begin(), hoff.end() - 1);
+        if (N == 0) {
+            done = true;
+            return JSIM_OK;
+        }
+        first = minid / mt;
+        last = maxid / mt;
+        // row batches per super-batch from the average density, 25 % headroom
+        const double per_d = (double)cap_vals / ((double)N / (double)(last - first + 1)) / 1.25;
+        per0 = per_d >= (double)rb_cap ? rb_cap : std::max<u64>(1, (u64)per_d);
+        b = first;
+        return JSIM_OK;
     }
-    for (u64 i = 0; i < n; ++i)
-        if (pos[i] != hoff[i + 1]) return JSIM_ERR_UNSORTED;
-    return JSIM_OK;
-}
+
+    // the next non-empty super-batch into s (have = false after the last)
+    int next(Super& s, bool& have)
+    {
+        have = false;
+        u64 per = per0;
+        while (!done) {
+            const u64 e = std::min(last + 1, b + per);
+            s = Super();
+            s.b0 = b;
+            s.b1 = e;
+            slice(hoff, ids, n, pos, e * mt, s);  // e * mt wraps to 0 only at the top of the range
+            if (s.count > cap_vals) {
+                if (e - b == 1) return JSIM_ERR_OOM;
+                per = (e - b) / 2;  // the same start with half the row batches
+                continue;
+            }
+            u64 maxv = 0;
+            for (u64 i = 0; i < n; ++i) {
+                pos[i] += s.len[i];
+                if (s.len[i]) maxv = std::max<u64>(maxv, ids[s.beg[i] + s.len[i] - 1]);
+            }
+            if (s.count) s.b1 = std::max(b + 1, std::min(e, maxv / mt + 1));  // drop empty trailing row batches
+            // first value at or above the range, to skip empty row batches
+            u64 nv = ~0ull;
+            bool more = false;
+            if (e <= last)
+                for (u64 i = 0; i < n; ++i)
+                    if (pos[i] < hoff[i + 1]) { more = true; nv = std::min<u64>(nv, ids[pos[i]]); }
+            if (!more) {
+                done = true;
+                for (u64 i = 0; i < n; ++i)
+                    if (pos[i] != hoff[i + 1]) return JSIM_ERR_UNSORTED;
+            } else {
+                b = std::max(e, nv / mt);
+            }
+            if (s.count) {
+                have = true;
+                return JSIM_OK;
+            }
+            per = per0;
+        }
+        return JSIM_OK;
+    }
+};
 
 // gather a super-batch's slices into `dst` (pinned) with several host threads
 void gather(const uint64_t* ids, const Super& s, u64* dst)
@@ -329,10 +410,13 @@ constexpr u64 kDirectSlicesMax = 16384;
 // waits for the copy stream before device buffers that its copies may still
 // write are released (declared after them, so destroyed first)
 struct CopyFence {
-    cudaStream_t xs;
+    StreamState* ss;
     ~CopyFence()
     {
-        if (xs) cudaStreamSynchronize(xs);
+        if (!ss) return;
+        if (ss->xs) cudaStreamSynchronize(ss->xs);
+        for (cudaStream_t x : ss->xs_more)
+            if (x) cudaStreamSynchronize(x);
     }
 };
 
@@ -395,8 +479,23 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
     const u64 rb_bytes = nwords * (ctx->opt.filter_min == 2 ? 20 : 12) +
                          (nwords + kScanBlockWords - 1) / kScanBlockWords * 16;
     const u64 rb_cap = std::max<u64>(1, std::min<u64>(2 * staging_bytes / rb_bytes, 1u << 16));
-    std::vector<Super> sup;
-    rc = plan_supers(hoff, ids, n, mt, cap_vals, rb_cap, sup);
+    // super-batches: planned one ahead of the device (all of them first when
+    // checkpointing, whose file names their count)
+    std::deque<Super> sup;  // references stay valid while it grows
+    SuperPlanner planner(hoff, ids, n, mt, cap_vals, rb_cap);
+    rc = planner.init();
+    if (rc) return rc;
+    auto plan_upto = [&](size_t g) -> int {
+        while (sup.size() <= g && !planner.done) {
+            Super x;
+            bool have = false;
+            int r = planner.next(x, have);
+            if (r) return r;
+            if (have) sup.push_back(std::move(x));
+        }
+        return JSIM_OK;
+    };
+    rc = plan_upto(ck_on ? ~(size_t)0 : 0);
     if (rc) return rc;
 
     // ---- checkpoint: the call's identity, and the state to resume from ----
@@ -430,17 +529,14 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
     rc = stream_state(ctx, head + cap_vals, ss);
     if (rc) return rc;
     cudaStream_t cs = ctx->stream, xs = ss->xs;
-    u64 rb_max = 1, count_max = 0;
-    for (auto& s : sup) {
-        rb_max = std::max<u64>(rb_max, s.b1 - s.b0);
-        count_max = std::max<u64>(count_max, s.count);
-    }
+    // a super-batch spans at most per0 row batches and cap_vals values
+    const u64 rb_max = std::max<u64>(1, planner.per0), count_max = cap_vals;
     const u64 nw_max = rb_max * nwords;  // bitmap words of the widest super-batch
     const u64 nbk_max = std::max<u64>((nw_max + kScanBlockWords - 1) / kScanBlockWords, 1);
     DevBuf dbuf[2], Cacc, sizes_d, flags, plan_buf, X, bm, seen, dir, bsum, boff, Rd, Cst, Jst, useful;
     ALLOC(dbuf[0], (head + count_max) * sizeof(u64));
     ALLOC(dbuf[1], (head + count_max) * sizeof(u64));
-    CopyFence fence{xs};
+    CopyFence fence{ss};
     ALLOC(Cacc, n * n * cb);
     ALLOC(sizes_d, n * sizeof(u64));
     ALLOC(flags, 3 * sizeof(u64));
@@ -514,14 +610,32 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
         cudaEvent_t a = nullptr;
         if (ctx->opt.profile && (a = take_event(ctx))) cudaEventRecord(a, xs);
         if (direct) {
+            // slices in kCopyStreams contiguous groups of about equal bytes,
+            // one group per copy stream (forked from and joined back to xs)
             CK(cudaMemcpyAsync(dbuf[k].p, ss->pin[k], head * sizeof(u64), cudaMemcpyHostToDevice, xs));
-            for (u64 i = 0; i < n; ++i)
-                if (s.len[i])
-                    CK(cudaMemcpyAsync(dbuf[k].as<u64>() + head + s.off[i], ids + s.beg[i], s.len[i] * sizeof(u64),
-                                       cudaMemcpyHostToDevice, xs));
+            ctx->stats.h2d_copies += 1;
+            CK(cudaEventRecord(ss->fork[k], xs));
+            for (cudaStream_t x : ss->xs_more) CK(cudaStreamWaitEvent(x, ss->fork[k], 0));
+            u64 i = 0;
+            for (int q = 0; q < kCopyStreams; ++q) {
+                cudaStream_t x = q == 0 ? xs : ss->xs_more[q - 1];
+                const u64 upto = s.count * (u64)(q + 1) / kCopyStreams;  // this group ends at offset `upto`
+                for (; i < n && (q == kCopyStreams - 1 || s.off[i] < upto); ++i)
+                    if (s.len[i]) {
+                        CK(cudaMemcpyAsync(dbuf[k].as<u64>() + head + s.off[i], ids + s.beg[i],
+                                           s.len[i] * sizeof(u64), cudaMemcpyHostToDevice, x));
+                        ctx->stats.h2d_copies += 1;
+                    }
+            }
+            for (int q = 1; q < kCopyStreams; ++q) {
+                CK(cudaEventRecord(ss->joined[k][q - 1], ss->xs_more[q - 1]));
+                CK(cudaStreamWaitEvent(xs, ss->joined[k][q - 1], 0));
+            }
         } else {
             CK(cudaMemcpyAsync(dbuf[k].p, ss->pin[k], (head + s.count) * sizeof(u64), cudaMemcpyHostToDevice, xs));
+            ctx->stats.h2d_copies += 1;
         }
+        ctx->stats.h2d_bytes += (head + s.count) * sizeof(u64);
         if (a) {
             cudaEvent_t b = take_event(ctx);
             if (b) {
@@ -615,7 +729,10 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
             }
             if (stop) return JSIM_ERR_INCOMPLETE;
         }
-        // the next super-batch is gathered and copied while this one multiplies
+        // the next super-batch is planned, gathered and copied while this one
+        // multiplies
+        rc = plan_upto(g + 1);
+        if (rc) return rc;
         if (g + 1 < sup.size()) {
             rc = stage(g + 1);
             if (rc) return rc;

@@ -61,6 +61,22 @@ def input_digest(off, ids, h=None):
     return h
 
 
+FP_STRIDE = 4093
+
+
+def fingerprint(off, ids, h=None):
+    """A cheap identity of a collection (or of its restriction to a value
+    range): the offsets, then every FP_STRIDE-th value of every sample.
+    The GPU tests check it instead of hashing every value; the full digests
+    of the results already fail on any other input."""
+    h = h or hashlib.sha256()
+    off = np.asarray(off, dtype=np.uint64)
+    h.update(np.ascontiguousarray(off, dtype="<u8").tobytes())
+    for i in range(len(off) - 1):
+        h.update(np.ascontiguousarray(ids[int(off[i]):int(off[i + 1])][::FP_STRIDE], dtype="<u8").tobytes())
+    return h
+
+
 def whole(name):
     off, ids = getattr(synth, name)()
     t0 = time.time()
@@ -81,12 +97,13 @@ def by_rows(off, ids, lo, hi):
 
 def batched200():
     t0 = time.time()
-    hin, hC, hs, hJ = (hashlib.sha256() for _ in range(4))
+    hin, hC, hs, hJ, hfp = (hashlib.sha256() for _ in range(5))
     per, values, samples = [], 0, 0
     for k in range(N_BATCHED):
         off, ids = synth.batched_collection(k)
         C, s, J = by_rows(off, ids, 0, 1 << 32)
         input_digest(off, ids, hin)
+        fingerprint(off, ids, hfp)
         c32 = np.ascontiguousarray(C.astype("<u4"))
         hC.update(c32.tobytes())
         hs.update(np.ascontiguousarray(s, dtype="<u8").tobytes())
@@ -101,7 +118,8 @@ def batched200():
         print("  batched200 collection %d: n=%d values=%d (%.0f s)" % (k, len(off) - 1, int(off[-1]),
                                                                     time.time() - t0), flush=True)
     return {"collections": N_BATCHED, "samples": samples, "values": values,
-            "input_sha256": hin.hexdigest(), "C_u32_sha256": hC.hexdigest(), "sizes_u64_sha256": hs.hexdigest(),
+            "input_sha256": hin.hexdigest(), "input_fingerprint_sha256": hfp.hexdigest(),
+            "C_u32_sha256": hC.hexdigest(), "sizes_u64_sha256": hs.hexdigest(),
             "J_f64_sha256": hJ.hexdigest(), "per_collection_sha256_16": per,
             "oracle_seconds": round(time.time() - t0, 1), "oracle_threads": oracle.default_threads(),
             "oracle": "rows_range over [0, 2^32) per collection",
@@ -116,11 +134,13 @@ def stream4096():
     Cu = np.zeros((n, n), dtype=np.uint64)
     sizes = np.zeros(n, dtype=np.uint64)
     hin = hashlib.sha256()
+    hfp = hashlib.sha256()
     values = 0
     cuts = [top * p // PASSES for p in range(PASSES + 1)]
     for lo, hi in zip(cuts[:-1], cuts[1:]):
         off, ids = synth.clade4096_range(lo, hi)
         input_digest(off, ids, hin)
+        fingerprint(off, ids, hfp)
         oracle.rows_range(off, ids, lo, hi, Cu)
         sizes += oracle.sizes_of(off, ids)
         values += int(off[-1])
@@ -129,11 +149,14 @@ def stream4096():
         del off, ids
     C, J = oracle.finish_upper(Cu, sizes)
     return {"n": n, "values": values, "ranges": cuts, "input_sha256": hin.hexdigest(),
+            "input_fingerprint_sha256": hfp.hexdigest(),
             "C_u64_sha256": digest(C.astype(np.uint64)), "sizes_u64_sha256": digest(sizes),
             "J_f64_sha256": digest(J.view(np.uint64)), "oracle_seconds": round(time.time() - t0, 1),
             "oracle_threads": oracle.default_threads(),
             "oracle": "rows_range per value range, added up",
-            "digest_layout": "input: for each range in order, its offsets (n+1) then its values"}
+            "digest_layout": "input: for each range in order, its offsets (n+1) then its values; fingerprint: "
+                             "for each range in order, its offsets then every 4093rd value of every sample's "
+                             "piece"}
 
 
 def serve2048_q256():
@@ -146,10 +169,37 @@ def serve2048_q256():
             "query_values": int(qoff[-1]),
             "ref_input_sha256": input_digest(roff, rids).hexdigest(),
             "query_input_sha256": input_digest(qoff, qids).hexdigest(),
+            "ref_fingerprint_sha256": fingerprint(roff, rids).hexdigest(),
+            "query_fingerprint_sha256": fingerprint(qoff, qids).hexdigest(),
             "C_u32_sha256": digest(C.astype(np.uint32)), "qsizes_u64_sha256": digest(qs.astype(np.uint64)),
             "ref_sizes_u64_sha256": digest(rs), "J_f64_sha256": digest(J.view(np.uint64)),
             "oracle_seconds": round(time.time() - t0, 1), "oracle_threads": oracle.default_threads(),
             "oracle": "cross (pairwise merge of every query sample with every reference sample)"}
+
+
+def add_fingerprint(name):
+    """Add the cheap input fingerprint to an entry computed before it existed
+    (regenerates the input only; no result changes)."""
+    data = json.load(open(OUT))
+    e = data[name]
+    h = hashlib.sha256()
+    if name == "batched200":
+        for k in range(e["collections"]):
+            off, ids = synth.batched_collection(k)
+            fingerprint(off, ids, h)
+        e["input_fingerprint_sha256"] = h.hexdigest()
+    elif name == "serve2048_q256":
+        roff, rids = synth.serving_reference()
+        qoff, qids = synth.serving_queries(0, N_QUERY)
+        e["ref_fingerprint_sha256"] = fingerprint(roff, rids).hexdigest()
+        e["query_fingerprint_sha256"] = fingerprint(qoff, qids).hexdigest()
+    cur = json.load(open(OUT))
+    cur[name] = e
+    with open(OUT + ".tmp", "w") as f:
+        json.dump(cur, f, indent=1, sort_keys=True)
+        f.write("\n")
+    os.replace(OUT + ".tmp", OUT)
+    print("fingerprint", name, {k: v for k, v in e.items() if "fingerprint" in k})
 
 
 def check_rows():
@@ -168,6 +218,10 @@ def main():
     names = sys.argv[1:] or ["ancestral64", "clade1024"]
     if names == ["check-rows"]:
         sys.exit(0 if check_rows() else 1)
+    if names[0] == "fingerprint":
+        for name in names[1:]:
+            add_fingerprint(name)
+        return
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     data["_how"] = ("digests of the oracle's results on the seeded workloads at full size; C, sizes (uint64) and "
                     "the bit patterns of J (binary64), row-major little-endian; written by "

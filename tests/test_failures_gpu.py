@@ -78,12 +78,12 @@ class FailAt:
         self.torch.cuda.caching_allocator_delete(ptr)
 
 
-def run_with_failures(call, check_ok):
+def run_with_failures(call, check_ok, **ctx_kw):
     """call(ctx) once with no failure (counting the requests), then once per
     request k with the k-th refused: OOM and outputs untouched, or success;
     no block live after the context is gone."""
     base = FailAt(0)
-    with jsim.Context(allocator=base) as ctx:
+    with jsim.Context(allocator=base, **ctx_kw) as ctx:
         check_ok(call(ctx))
     assert not base.live
     total = base.calls
@@ -92,7 +92,7 @@ def run_with_failures(call, check_ok):
     for k in range(1, total + 1):
         a = FailAt(k)
         try:
-            ctx = jsim.Context(allocator=a)
+            ctx = jsim.Context(allocator=a, **ctx_kw)
         except jsim.JsimError as e:
             assert k == 1 and e.name == "JSIM_ERR_OOM"   # the context's own error word
             assert not a.live
@@ -132,7 +132,7 @@ def test_allocation_failures_plain_call(gpu):
 
 
 def test_allocation_failures_streamed_call(gpu):
-    off, ids = synth.clade1024(n=40, median=3e3)
+    off, ids = synth.clade1024(n=40, median=3e4)
     Cr, sr, Jr = oracle.all_pairs(off, ids)
     outs = []
 
@@ -141,14 +141,14 @@ def test_allocation_failures_streamed_call(gpu):
         s = np.full(40, 7, dtype=np.uint64)
         J = np.full((40, 40), -1.0)
         outs.append((C, s, J))
-        return ctx.all_pairs_streamed(off, ids, staging_bytes=1 << 16, out=(C, s, J))
+        return ctx.all_pairs_streamed(off, ids, staging_bytes=1 << 20, out=(C, s, J))
 
     def ok(res):
         C, s, J = res
         np.testing.assert_array_equal(C, Cr)
         np.testing.assert_array_equal(J.view(np.uint64), Jr.view(np.uint64))
 
-    run_with_failures(call, ok)
+    run_with_failures(call, ok, batch_rows=1 << 24)
     for C, s, J in outs[1:]:
         assert (C == 7).all() and (s == 7).all() and (J == -1.0).all()
 

@@ -5,7 +5,9 @@ oracle), sampled pairs the oracle computes one by one (merge counts and
 binary64 J), every size, and the invariants that hold at any size (symmetry,
 C_ii = |X_i|, C_ij <= min, J_ii = 1, 0 <= J <= 1).  Integers and correctly
 rounded quotients: tolerance zero."""
+import ctypes
 import hashlib
+import importlib.util
 import json
 import os
 
@@ -16,6 +18,10 @@ import oracle
 from paper_1911_04200_gb300 import jsim, synth
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_size_sha256.json")
+_spec = importlib.util.spec_from_file_location(
+    "make_full_size_hashes", os.path.join(os.path.dirname(GOLDEN), "make_full_size_hashes.py"))
+hashes = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(hashes)  # the digest script's own fingerprint of an input
 
 
 def golden(name):
@@ -110,54 +116,141 @@ def test_ancestral64_whole_result_digest(gpu):
     check_digests("ancestral64", off, ids, C, s, J)
 
 
-@pytest.mark.timeout(900)
-def test_batched_recipe_full_size_subset(gpu):
-    """The first 12 collections of the 200-collection recipe at full size
-    (n ~ U{8..512}, sizes log-normal median 2e5 in [1e4, 5e6]) through one
-    batched call."""
-    cols = synth.batched_collections(count=12)
+def batched_call_twice(ctx, dcols):
+    """jsim_all_pairs_batched on device-resident collections with the same
+    preallocated device outputs twice (capture, then replay of the CUDA
+    graph); the results of the replay, on the host."""
+    import torch
+    k = len(dcols)
+    dev = dcols[0][0].device
+    ns = [o.numel() - 1 for o, _ in dcols]
+    Cs = [torch.empty((n, n), dtype=torch.uint32, device=dev) for n in ns]
+    Ss = [torch.empty(n, dtype=torch.uint64, device=dev) for n in ns]
+    Js = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
+    sets = (jsim.Sets * k)()
+    for c, (o, i) in enumerate(dcols):
+        sets[c] = jsim.Sets(ns[c], o.data_ptr(), i.data_ptr() if i.numel() else None, jsim.MEM_DEVICE)
+    arr = lambda L: (ctypes.c_void_p * k)(*[t.data_ptr() for t in L])
+    Cp, Sp, Jp = arr(Cs), arr(Ss), arr(Js)
+    lib = jsim.load()
+    for _ in range(2):
+        ctx._order()
+        jsim._check(lib.jsim_all_pairs_batched(ctx._h, sets, k, Cp, Sp, Jp, jsim.MEM_DEVICE), ctx._h)
+    torch.cuda.synchronize()
+    return [(C.view(torch.int32).cpu().numpy().view(np.uint32), S.view(torch.int64).cpu().numpy().view(np.uint64),
+             J.cpu().numpy()) for C, S, J in zip(Cs, Ss, Js)]
+
+
+@pytest.mark.timeout(1500)
+def test_batched_recipe_full_size_whole_results(gpu):
+    """All 200 collections of the batched recipe at full size (n ~ U{8..512},
+    sizes log-normal median 2e5 in [1e4, 5e6]: 53,900 samples, 1.8e10
+    values) through batched calls on device-resident input (the graph
+    replay, as the benchmark times it), in waves of 25 collections: C, sizes
+    and J of every collection against digests of the oracle's results."""
+    import torch
+    g = golden("batched200")
+    hC, hs, hJ, hfp = (hashlib.sha256() for _ in range(4))
+    bad = []
     with jsim.Context(id_bits=32) as ctx:
-        outs = ctx.all_pairs_batched(cols)
-    for (off, ids), (C, s, J) in zip(cols, outs):
-        check_sampled(off, ids, C, s, J, pairs=128)
+        for w0 in range(0, g["collections"], 25):
+            cols = [synth.batched_collection(k) for k in range(w0, min(w0 + 25, g["collections"]))]
+            dcols = [(torch.from_numpy(o.view(np.int64)).cuda(), torch.from_numpy(i.view(np.int64)).cuda())
+                     for o, i in cols]
+            outs = batched_call_twice(ctx, dcols)
+            del dcols
+            for k, ((off, ids), (C, S, J)) in enumerate(zip(cols, outs)):
+                hashes.fingerprint(off, ids, hfp)
+                c32 = np.ascontiguousarray(C.astype("<u4"))
+                hC.update(c32.tobytes())
+                hs.update(np.ascontiguousarray(S, dtype="<u8").tobytes())
+                hJ.update(np.ascontiguousarray(J.view(np.uint64), dtype="<u8").tobytes())
+                one = hashlib.sha256()
+                one.update(c32.tobytes())
+                one.update(np.ascontiguousarray(S, dtype="<u8").tobytes())
+                one.update(np.ascontiguousarray(J.view(np.uint64), dtype="<u8").tobytes())
+                if one.hexdigest()[:16] != g["per_collection_sha256_16"][w0 + k]:
+                    bad.append(w0 + k)
+            del cols, outs
+    assert hfp.hexdigest() == g["input_fingerprint_sha256"], "the generator drew other collections"
+    assert not bad, "collections whose results differ from the oracle's: %s" % bad
+    assert hC.hexdigest() == g["C_u32_sha256"]
+    assert hs.hexdigest() == g["sizes_u64_sha256"]
+    assert hJ.hexdigest() == g["J_f64_sha256"]
 
 
-@pytest.mark.timeout(1200)
-def test_serving_full_size_sampled(gpu):
+@pytest.mark.timeout(1500)
+def test_serving_full_size_whole_results(gpu):
     """The serving workload at full size (2048 reference samples of median
-    1e6 values: a 171 GB resident index): one request of 6 query samples,
-    whose counts and J against 48 sampled reference samples are merged by
-    the oracle; invariants over every reference column."""
+    1e6 values: a 171 GB resident index): the first 256 query samples of the
+    recipe, submitted at once as requests of U{1..64} samples (so the server
+    batches them as they arrive), every result against digests of the
+    oracle's merges of every query sample with every reference sample; and a
+    sampled check of 48 reference columns for diagnosis."""
+    g = golden("serve2048_q256")
     roff, rids = synth.serving_reference()
-    qoff, qids = synth.serving_queries(0, 6)
-    n_ref = len(roff) - 1
+    qoff, qids = synth.serving_queries(0, g["queries"])
+    assert hashes.fingerprint(roff, rids).hexdigest() == g["ref_fingerprint_sha256"]
+    assert hashes.fingerprint(qoff, qids).hexdigest() == g["query_fingerprint_sha256"]
+    n_ref, nq = len(roff) - 1, len(qoff) - 1
+    rng = np.random.default_rng(21)
+    cuts = [0]
+    while cuts[-1] < nq:
+        cuts.append(min(nq, cuts[-1] + int(rng.integers(1, 65))))
+    C = np.zeros((nq, n_ref), dtype=np.uint32)
+    qs = np.zeros(nq, dtype=np.uint64)
+    J = np.zeros((nq, n_ref), dtype=np.float64)
     with jsim.Context(id_bits=32) as ctx:
-        with jsim.Index(ctx, roff, rids, max_batch_samples=64, max_batch_values=int(qoff[-1])) as ix:
-            r = ix.submit(qoff, qids)
-            C, qs, J = r.wait()
-            r.free()
+        sizes = np.diff(qoff.astype(np.int64))
+        with jsim.Index(ctx, roff, rids, max_batch_samples=64, max_batch_values=int(np.sort(sizes)[-64:].sum())) as ix:
+            reqs = []
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                o = (qoff[a:b + 1] - qoff[a]).astype(np.uint64)
+                reqs.append((a, b, ix.submit(o, qids[int(qoff[a]):int(qoff[b])])))
+            for a, b, r in reqs:
+                Cr, qr, Jr = r.wait()
+                r.free()
+                C[a:b], qs[a:b], J[a:b] = Cr, qr, Jr
             rsz = ix.ref_sizes()
-    C = C.astype(np.uint64)
-    np.testing.assert_array_equal(qs, oracle.sizes_of(qoff, qids))
-    assert np.all(C <= np.minimum(qs[:, None], np.asarray(rsz, dtype=np.uint64)[None, :]))
-    assert np.all((J >= 0.0) & (J <= 1.0))
+    assert sha(np.ascontiguousarray(rsz, dtype="<u8")) == g["ref_sizes_u64_sha256"]
     cols = np.sort(np.random.default_rng(9).choice(n_ref, 48, replace=False))
     segs = [rids[int(roff[j]):int(roff[j + 1])] for j in cols]
     soff = np.zeros(len(segs) + 1, dtype=np.uint64)
-    soff[1:] = np.cumsum([len(s) for s in segs])
-    Co, qso, Jo = oracle.cross(qoff, qids, soff, np.concatenate(segs))
-    np.testing.assert_array_equal(C[:, cols], Co)
-    np.testing.assert_array_equal(J[:, cols].view(np.uint64), Jo.view(np.uint64))
+    soff[1:] = np.cumsum([len(x) for x in segs])
+    Co, qso, Jo = oracle.cross(qoff[:7], qids[:int(qoff[6])], soff, np.concatenate(segs))
+    np.testing.assert_array_equal(C[:6][:, cols], Co)
+    np.testing.assert_array_equal(J[:6][:, cols].view(np.uint64), Jo.view(np.uint64))
+    assert sha(np.ascontiguousarray(qs, dtype="<u8")) == g["qsizes_u64_sha256"]
+    assert sha(np.ascontiguousarray(C, dtype="<u4")) == g["C_u32_sha256"]
+    assert sha(np.ascontiguousarray(J.view(np.uint64), dtype="<u8")) == g["J_f64_sha256"]
 
 
 @pytest.mark.timeout(1800)
-def test_streamed_full_size_sampled(gpu):
+def test_streamed_full_size_whole_results(gpu):
     """The out-of-HBM workload at full size (4096 samples, median 2e6 values
     in [0, 2^40), about 1.1e10 values = 88 GB of host memory, 64-bit counts)
-    through the streamed call with the benchmark's 1 GiB staging: sampled
-    pairs against the oracle's merges, and the invariants over the whole
-    matrix."""
+    through the streamed call with the benchmark's 1 GiB staging: C (uint64),
+    sizes and J against digests of the oracle's result (counted by rows of
+    the indicator matrix, range by range), sampled pairs against the
+    oracle's merges, and the invariants over the whole matrix."""
+    g = golden("stream4096")
     off, ids = synth.clade4096()
+    # the input's fingerprint, range by range as the oracle visited it
+    h = hashlib.sha256()
+    n = len(off) - 1
+    for lo, hi in zip(g["ranges"][:-1], g["ranges"][1:]):
+        a = np.array([np.searchsorted(ids[int(off[i]):int(off[i + 1])], lo) + int(off[i]) for i in range(n)])
+        b = np.array([np.searchsorted(ids[int(off[i]):int(off[i + 1])], hi) + int(off[i]) for i in range(n)])
+        po = np.zeros(n + 1, dtype=np.uint64)
+        po[1:] = np.cumsum(b - a)
+        h.update(np.ascontiguousarray(po, dtype="<u8").tobytes())
+        for i in range(n):
+            h.update(np.ascontiguousarray(ids[a[i]:b[i]][::hashes.FP_STRIDE], dtype="<u8").tobytes())
+    assert h.hexdigest() == g["input_fingerprint_sha256"], "the generator drew another collection"
     with jsim.Context(count_bits=64, id_bits=40) as ctx:
         C, s, J = ctx.all_pairs_streamed(off, ids, staging_bytes=1 << 30)
     check_sampled(off, ids, C, s, J, pairs=128)
+    # the whole result against the oracle's, counted range by range
+    assert sha(np.ascontiguousarray(s, dtype="<u8")) == g["sizes_u64_sha256"]
+    assert sha(np.ascontiguousarray(C, dtype="<u8")) == g["C_u64_sha256"]
+    assert sha(np.ascontiguousarray(J.view(np.uint64), dtype="<u8")) == g["J_f64_sha256"]
