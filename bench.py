@@ -397,13 +397,15 @@ def run_batched(args):
     model): the batched call against one plain call per collection."""
     from paper_1911_04200_gb300 import synth
     median = float(os.environ.get("JSIM_BATCHED_MEDIAN", "2e4"))
-    cols = synth.batched_collections(median=median, lo=1e4, hi=5e6)
+    count = int(os.environ.get("JSIM_BATCHED_COUNT", "200"))
+    cols = synth.batched_collections(median=median, lo=1e4, hi=5e6, count=count)
     m = batched_measure(cols, args.steps, args.warmup, args.batch_rows)
     line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": m["ms_batched"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
-            "config": {"workload": "batched200: 200 collections, n ~ U{8..512}, log-normal sizes median %.0e, "
-                                   "values in [0,2^32), ceil(n/32) clades" % median,
+            "config": {"workload": "batched200: %s%d collections, n ~ U{8..512}, log-normal sizes median %.0e, "
+                                   "values in [0,2^32), ceil(n/32) clades"
+                                   % ("the first " if count < 200 else "", count, median),
                        "collections": m["collections"], "samples": m["samples"], "values": m["values"],
                        "variant": m["variant"], "bitops_dense_per_step": m["bitops_dense_per_step"]},
             "plain": {"value": m["plain_value"], "ms_per_step": m["ms_plain"],
@@ -771,24 +773,29 @@ def systems_measure(args, d_off, d_ids, J_ref, cfg):
                                  "default workload's device-resident inputs"}
     fctx.close()
     del C2, S2, J2
-    # batched: a subset of the batched recipe at its full median
+    # batched and serving: each in a process of its own (the one-workload
+    # runs of this script), so that neither inherits this process's host
+    # memory state (the serving gather's host bandwidth did, measurably)
+    def child(workload, env, budget_s):
+        e = dict(os.environ)
+        e.update(env)
+        t0 = time.perf_counter()
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", workload, "--steps", "2",
+                            "--warmup", "2"], env=e, capture_output=True, text=True, timeout=budget_s)
+        for ln in r.stdout.splitlines():
+            if ln.startswith("{"):
+                d = json.loads(ln)
+                d["wall_s"] = round(time.perf_counter() - t0, 1)
+                return d
+        return {"error": "no result (rc %d): %s" % (r.returncode, (r.stderr or "")[-400:])}
+
     count = int(os.environ.get("JSIM_SYSTEMS_BATCHED_COUNT", "24"))
-    t0 = time.perf_counter()
-    cols = synth.batched_collections(count=count, median=2e5, lo=1e4, hi=5e6)
-    gen_s = time.perf_counter() - t0
-    m = batched_measure(cols, steps=2, warmup=1)
-    m["config"] = ("the first %d collections of the batched recipe (n ~ U{8..512}, log-normal sizes median 2e5 "
-                   "in [1e4, 5e6], values in [0,2^32), ceil(n/32) clades), device-resident" % count)
-    m["generation_s"] = round(gen_s, 1)
-    out["batched"] = m
-    del cols
-    # serving: reduced reference
-    median = float(os.environ.get("JSIM_SYSTEMS_SERVE_MEDIAN", "1e5"))
-    sm = serve_measure(median, n_req=int(os.environ.get("JSIM_SYSTEMS_SERVE_REQUESTS", "300")), slots=3, warmup=2)
-    sm["config"] = ("reference of 2048 samples, log-normal sizes median %.0e (x/10-10x, the recipe's median "
-                    "is 1e6), values in [0,2^32), 64 clades; requests of U{1..64} query samples of the same "
-                    "recipe" % median)
-    out["serving"] = sm
+    out["batched"] = child("batched200", {"JSIM_BATCHED_MEDIAN": "2e5", "JSIM_BATCHED_COUNT": str(count)}, 600)
+    median = os.environ.get("JSIM_SYSTEMS_SERVE_MEDIAN", "1e5")
+    out["serving"] = child("serve2048", {"JSIM_SERVE_MEDIAN": median,
+                                         "JSIM_SERVE_REQUESTS": os.environ.get("JSIM_SYSTEMS_SERVE_REQUESTS", "400")},
+                           600)
+    out["serving"]["note"] = "reduced reference: set-size median %s (the recipe's is 1e6)" % median
     return out
 
 

@@ -128,12 +128,26 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
     if (o.distance != 0 && o.distance != 1) return JSIM_ERR_ARG;
     if (o.count_useful != 0 && o.count_useful != 1) return JSIM_ERR_ARG;
     if ((o.alloc == nullptr) != (o.free == nullptr)) return JSIM_ERR_ARG;
-    if (!o.alloc) { o.alloc = default_alloc; o.free = default_free; }
+    const bool own_pool = !o.alloc;
     jsim_ctx* c = new jsim_ctx();
     memset(&c->stats, 0, sizeof c->stats);
-    c->opt = o;
     c->cuda_err[0] = 0;
     cudaError_t e = cudaSetDevice(o.device);
+    if (e == cudaSuccess && own_pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = o.device;
+        e = cudaMemPoolCreate(&c->pool, &props);
+        if (e == cudaSuccess) {
+            unsigned long long keep = ~0ull;  // keep freed memory for the context's later calls
+            e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        o.alloc = default_alloc;
+        o.free = default_free;
+        o.alloc_user = c->pool;
+    }
+    c->opt = o;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, o.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, o.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, o.device);
@@ -159,6 +173,7 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
         if (c->d_err) o.free(c->d_err, 256, (void*)c->stream, o.alloc_user);
         if (c->h_scalars) cudaFreeHost(c->h_scalars);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+        if (c->pool) cudaMemPoolDestroy(c->pool);
         delete c;
         return oom ? JSIM_ERR_OOM : JSIM_ERR_CUDA;
     }
@@ -181,6 +196,7 @@ void jsim_destroy(jsim_ctx* ctx)
     if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);  // released once nothing from it is outstanding
     delete ctx;
 }
 
