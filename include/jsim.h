@@ -80,7 +80,12 @@ extern "C" {
 #define JSIM_VARIANT_F8   4  /* legacy tensor mma.sync .e4m3, bits unpacked to 0/1.0, f32 accumulate in exact ranges */
 #define JSIM_VARIANT_TC   5  /* tcgen05.mma kind::f8f6f4 with TMEM accumulators, 0/1.0 e4m3 operands */
 #define JSIM_VARIANT_TC2  6  /* as TC, on pairs of SMs (cta_group::2, 256 x 256 tiles) */
-#define JSIM_VARIANT_COUNT 7
+#define JSIM_VARIANT_SPARSE 7 /* block-sparse (jsim_all_pairs only, 1..2048 samples, tensor cores):
+                                samples ordered by a sketch of their similarity into tiles of
+                                128, rows held by one tile multiplied within that tile's
+                                diagonal block only (Sec. III-B/III-C: sparsity and row/column
+                                permutations); bit-identical results */
+#define JSIM_VARIANT_COUNT 8
 
 /*
  * A collection of n samples in compressed-row form: sample i is
@@ -152,6 +157,9 @@ typedef struct {
                                   nnz(nnz+1)/2, nnz the rows whose word is nonzero - the pairs of
                                   nonzero words, the work a sparse product needs (the operation
                                   count depends on the sparsity structure, Sec. IV); else 0 */
+    double bitops_done;        /* bit-operations the product kernels carried out (64 per word pair of
+                                  the upper triangle they multiplied): bitops_dense, except for the
+                                  block-sparse variant, which skips the blocks no row reaches */
     uint64_t h2d_copies;       /* host -> device copies the call issued for its input values */
     uint64_t h2d_bytes;        /* bytes of those copies */
 } jsim_stats;

@@ -13,87 +13,7 @@
 using namespace jsim;
 
 #include "ctx.cuh"
-
-namespace {
-
-// Working buffers of the batch loop.
-struct BatchBufs {
-    DevBuf bitmap, seen, dir, bsum, boff, R, X, plan_buf, bsizes;  // bitmap: the rows kept
-    Plan plan{};
-    u64 X_bytes = 0;
-};
-
-// One row batch [lo, lo+width): plan, filter, rank directory, zero + pack.
-// On return bb.X holds n_pad rows of `stride` words and *R the nonzero rows.
-int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 width, u64& R, u64& stride,
-                u64* batch_sizes, bool* has_next = nullptr, u64* next = nullptr)
-{
-    const u64 n = st.n;
-    const u64 nwords = width / 64;
-    const u64 nb = std::max<u64>((nwords + kScanBlockWords - 1) / kScanBlockWords, 1);
-    ALLOC(bb.plan_buf, (3 * n + 5) * sizeof(u64));
-    bb.plan = carve_plan(bb.plan_buf, n);
-    ALLOC(bb.bitmap, nwords * sizeof(u64));
-    ALLOC(bb.dir, nwords * sizeof(u32));
-    ALLOC(bb.bsum, nb * sizeof(u64));
-    ALLOC(bb.boff, nb * sizeof(u64));
-    ALLOC(bb.R, sizeof(u64));
-    const u64 hi = lo + width;  // 0 on wrap-around = unbounded
-    {
-        StageTimer t(ctx, &ctx->stats.ms_filter);
-        CK(launch_plan(st.d_off, st.d_ids, n, lo, hi, false, bb.plan, ctx->stream));
-        CK(cudaMemsetAsync(bb.bitmap.p, 0, nwords * sizeof(u64), ctx->stream));
-        if (ctx->opt.filter_min == 2) {
-            // f of every row (seen) and the kept rows of two or more samples
-            ALLOC(bb.seen, nwords * sizeof(u64));
-            CK(cudaMemsetAsync(bb.seen.p, 0, nwords * sizeof(u64), ctx->stream));
-            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.seen.as<u32>(), ctx->sms,
-                             ctx->stream, bb.bitmap.as<u32>()));
-        } else {
-            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u32>(), ctx->sms,
-                             ctx->stream));
-        }
-        ctx->stats.launches += 2;
-    }
-    {
-        StageTimer t(ctx, &ctx->stats.ms_scan);
-        CK(launch_scan(bb.bitmap.as<u64>(), nwords, bb.dir.as<u32>(), bb.bsum.as<u64>(), bb.boff.as<u64>(),
-                       bb.R.as<u64>(), ctx->stream));
-        ctx->stats.launches += 2;
-    }
-    CK(cudaMemcpyAsync(ctx->h_scalars, bb.R.p, sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_scalars + 1, bb.plan.totals + 2, 2 * sizeof(u64), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    R = ctx->h_scalars[0];
-    if (next) *next = ctx->h_scalars[1];
-    if (has_next) *has_next = ctx->h_scalars[2] != 0;
-    const u64 W = (R + 63) / 64;
-    stride = row_stride_words(W);
-    const u64 n_pad = round_up(std::max<u64>(n, 1), kRowPad);
-    const u64 need = n_pad * stride * sizeof(u64);
-    ALLOC(bb.X, need);
-    {
-        StageTimer t(ctx, &ctx->stats.ms_pack);
-        if (batch_sizes) {
-            // the step-level entry point: zero-filled rows (the caller sees the
-            // padding words too) and per-sample counts of the batch
-            CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->sms, ctx->stream));
-            CK(cudaMemsetAsync(batch_sizes, 0, n * sizeof(u64), ctx->stream));
-            CK(launch_pack(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u64>(), bb.dir.as<u32>(),
-                           bb.boff.as<u64>(), bb.X.as<u64>(), stride, batch_sizes, ctx->sms, ctx->stream));
-        } else {
-            CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->sms, ctx->stream));
-            CK(launch_pack_full(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u64>(),
-                                bb.dir.as<u32>(), bb.boff.as<u64>(), bb.X.as<u64>(), stride, bb.R.as<u64>(), ctx->sms,
-                                ctx->stream));
-        }
-        ctx->stats.launches += 2;
-    }
-    return JSIM_OK;
-}
-
-}  // namespace
+#include "sparse.cuh"
 
 extern "C" {
 
@@ -251,6 +171,18 @@ int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
     if (rc) return rc;
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), ctx->stream));
 
+    // the block-sparse path: asked for, or (AUTO) where a sketch shows that
+    // ordering the samples empties enough tensor-core blocks
+    const int want = ctx->opt.variant;
+    if (want == JSIM_VARIANT_SPARSE ||
+        (want == JSIM_VARIANT_AUTO && parts == 1 && !counts_only && n >= 256 && n <= 2048 &&
+         !ctx->opt.count_useful && product_tc_supported(ctx->opt.device) &&
+         (ctx->opt.batch_rows == 0 || ctx->opt.batch_rows % (1ull << 18) == 0))) {
+        if (parts != 1 || counts_only || ctx->opt.count_useful) return JSIM_ERR_UNSUPPORTED;
+        bool declined = false;
+        rc = all_pairs_sparse(ctx, st, C, sizes, J, out_mem, want == JSIM_VARIANT_AUTO, declined);
+        if (rc || !declined) return rc;
+    }
     const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
     DevBuf Cacc, useful;
     ALLOC(Cacc, n * n * cb);
@@ -490,6 +422,7 @@ int jsim_get_stats(const jsim_ctx* ctx, jsim_stats* out)
 {
     if (!ctx || !out) return JSIM_ERR_ARG;
     *out = ctx->stats;
+    if (out->bitops_done == 0) out->bitops_done = out->bitops_dense;  // the dense products do all of it
     return JSIM_OK;
 }
 

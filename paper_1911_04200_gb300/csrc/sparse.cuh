@@ -1,0 +1,428 @@
+// Block-sparse all-pairs product (variant JSIM_VARIANT_SPARSE).
+//
+// The paper stores the bitmask matrix sparsely and notes that the product's
+// operation count depends on the sparsity structure, and that rows and
+// columns may be permuted freely (Sec. III-B, III-C; C is invariant under a
+// relabelling of the rows and permutes with the samples).  On the tensor
+// cores a block of 128 samples x 256 rows costs the same whether it holds
+// one set bit or all of them, so the work only shrinks when whole blocks are
+// empty.  This path arranges that:
+//
+//  1. Sample order.  A sketch - the product of a small range of the lowest
+//     values (about 512 per sample) - gives every pair's similarity J; the
+//     samples are ordered by a greedy chain (the next sample is the one most
+//     similar to any sample already in the current tile of 128), so that
+//     samples sharing many values land in the same tile.
+//  2. Row classes.  Per row batch, every tile of 128 samples (in that order)
+//     gets its own filter bitmap (Eq. 5 restricted to the tile's samples).
+//     A row held by two or more tiles is of class 0; a row held by tile t
+//     alone is of class 1 + t.  Every class is rank-scanned (Eq. 6), so the
+//     packed matrix of the batch splits into a class-0 matrix (all samples)
+//     and one matrix per tile holding only that tile's rows.
+//  3. Product.  Class-0 words: the dense product over all samples (Eq. 7).
+//     Class 1 + t words: a 128 x 128 product of tile t only, added to the
+//     diagonal block of tile t - the only block they can change, since no
+//     other sample holds those rows.  All tiles' blocks run in one launch of
+//     the job-table product.  C accumulates in sample-order positions; the
+//     epilogue reads it back through the order.
+//
+// Every count is the same integer as the dense product's (a sum over the
+// same rows, Eq. 4, grouped differently), so C and J are bit-identical.  With
+// AUTO the sketch's own rows are classified first; when the class structure
+// would not at least halve the product's work the call goes on dense.
+//
+// Internal header of the C-ABI translation unit (included once, after ctx.cuh).
+#pragma once
+#include <cmath>
+
+namespace {
+
+constexpr u64 kTile = 128;                // samples per tile: the rows of a one-SM tensor-core tile
+constexpr u64 kMaxTiles = 16;             // n <= 2048
+constexpr u64 kSketchPerSample = 512;     // values per sample in the sketch range, on average
+constexpr u64 kMinClassRows = 1ull << 18; // batch width granule: one scan block of every class
+constexpr u64 kTileBitmapBytes = 64ull << 20;  // all tiles' filter bitmaps of a batch together
+
+// Row classes from the tiles' bitmaps: class 0 = rows of two or more tiles,
+// class 1 + t = rows of tile t alone (with the two-or-more filter: rows tile
+// t holds twice or more and no other tile holds).  One thread per word.
+__global__ void k_classify(const u64* __restrict__ B, const u64* __restrict__ B2, u64 T, u64 nwords,
+                           u64* __restrict__ cls)
+{
+    for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < nwords; w += (u64)gridDim.x * blockDim.x) {
+        u64 b[kMaxTiles];
+        u64 ones = 0, twos = 0;
+        #pragma unroll
+        for (u64 t = 0; t < kMaxTiles; ++t) {
+            b[t] = t < T ? B[t * nwords + w] : 0ull;
+            twos |= ones & b[t];
+            ones |= b[t];
+        }
+        cls[w] = twos;
+        #pragma unroll
+        for (u64 t = 0; t < kMaxTiles; ++t)
+            if (t < T) cls[(t + 1) * nwords + w] = (B2 ? B2[t * nwords + w] : b[t]) & ~twos;
+    }
+}
+
+// Output (i, j) from counts accumulated at positions (pos[i], pos[j]) (upper
+// triangle); J as the dense epilogue forms it.  Nothing is written when
+// *skip_if is set (a bounded wait of a product ran out).
+template <typename CT>
+__global__ void k_epilogue_perm(const CT* __restrict__ Cacc, u64 n, const u32* __restrict__ pos,
+                                const u64* __restrict__ sizes, CT* __restrict__ Cout, double* __restrict__ J,
+                                int diag_sizes, int distance, const u32* skip_if)
+{
+    if (skip_if && *(volatile const u32*)skip_if) return;
+    const u64 total = n * n;
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < total; t += (u64)gridDim.x * blockDim.x) {
+        const u64 i = t / n, j = t - i * n;
+        const u64 a = pos[i], b = pos[j];
+        CT c = a <= b ? Cacc[a * n + b] : Cacc[b * n + a];
+        if (diag_sizes && i == j) c = (CT)sizes[i];
+        if (Cout) Cout[t] = c;
+        if (J) {
+            const u64 u = sizes[i] + sizes[j] - (u64)c;
+            const double s = u ? __ddiv_rn(__ull2double_rn((u64)c), __ull2double_rn(u)) : 1.0;
+            J[t] = distance ? __dsub_rn(1.0, s) : s;
+        }
+    }
+}
+
+unsigned grid_of(u64 items, int sms, unsigned threads)
+{
+    u64 g = (items + threads - 1) / threads;
+    const u64 cap = (u64)sms * 8;
+    return (unsigned)std::max<u64>(1, std::min(g, cap));
+}
+
+// Sample order from sketch counts (n x n, upper triangle and diagonal):
+// J_ij = c / (s_i + s_j - c).  A greedy chain: start at the largest sample;
+// the next sample is the unplaced one with the largest J to any sample
+// already in the current tile of kTile (a new tile starts from its
+// predecessor's similarities); ties go to the smaller index, and a sample
+// sharing nothing with the tile is taken largest first.
+std::vector<u32> sample_order(const std::vector<u64>& Cs, u64 n)
+{
+    std::vector<float> Jm(n * n, 0.f);
+    for (u64 i = 0; i < n; ++i)
+        for (u64 j = i + 1; j < n; ++j) {
+            const double c = (double)Cs[i * n + j], u = (double)Cs[i * n + i] + (double)Cs[j * n + j] - c;
+            const float v = u > 0 ? (float)(c / u) : 0.f;
+            Jm[i * n + j] = v;
+            Jm[j * n + i] = v;
+        }
+    std::vector<u32> order;
+    order.reserve(n);
+    std::vector<char> placed(n, 0);
+    std::vector<float> score(n, 0.f);
+    u64 first = 0;
+    for (u64 i = 1; i < n; ++i)
+        if (Cs[i * n + i] > Cs[first * n + first]) first = i;
+    auto place = [&](u64 k, bool fresh) {
+        order.push_back((u32)k);
+        placed[k] = 1;
+        const float* r = &Jm[k * n];
+        if (fresh)
+            for (u64 j = 0; j < n; ++j) score[j] = r[j];
+        else
+            for (u64 j = 0; j < n; ++j) score[j] = std::max(score[j], r[j]);
+    };
+    place(first, true);
+    for (u64 step = 1; step < n; ++step) {
+        if (step % kTile == 0) {
+            // a new tile: similarities of its predecessor only
+            const float* r = &Jm[(u64)order.back() * n];
+            for (u64 j = 0; j < n; ++j) score[j] = r[j];
+        }
+        u64 best = n;
+        float bs = 0.f;
+        for (u64 j = 0; j < n; ++j)
+            if (!placed[j] && score[j] > bs) { bs = score[j]; best = j; }
+        if (best == n)
+            for (u64 j = 0; j < n; ++j)
+                if (!placed[j] && (best == n || Cs[j * n + j] > Cs[best * n + best])) best = j;
+        place(best, false);
+    }
+    return order;
+}
+
+// The block-sparse path of jsim_all_pairs: JSIM_ERR_UNSUPPORTED where it does
+// not apply (more than kMaxTiles tiles, no tensor cores, a batch width that
+// is not a multiple of kMinClassRows); with may_decline, declined = true
+// when the sketch shows the product would not be halved (nothing written).
+int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, double* J, int out_mem,
+                     bool may_decline, bool& declined)
+{
+    declined = false;
+    const u64 n = st.n;
+    const u64 T = (n + kTile - 1) / kTile;
+    if (n == 0 || T > kMaxTiles || !product_tc_supported(ctx->opt.device)) return JSIM_ERR_UNSUPPORTED;
+    const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
+    const bool twice = ctx->opt.filter_min == 2;
+    cudaStream_t cs = ctx->stream;
+    const u64 n_pad = round_up(n, kRowPad);
+
+    // ---- batch width: a power of two, a whole scan block of every class, all
+    // tiles' bitmaps within kTileBitmapBytes ----
+    const u64 span = st.N ? st.maxid - st.minid : 0;
+    u64 mt = ctx->opt.batch_rows;
+    if (mt) {
+        if (mt % kMinClassRows) return JSIM_ERR_UNSUPPORTED;
+    } else {
+        mt = auto_batch_rows(span + 1 ? span + 1 : ~0ull);
+        while (mt > kMinClassRows && T * (mt / 8) > kTileBitmapBytes) mt >>= 1;
+        mt = std::max(mt, kMinClassRows);
+    }
+    ctx->stats.batch_rows = mt;
+
+    // ---- sketch: the dense product of the lowest values, about
+    // kSketchPerSample per sample ----
+    std::vector<u32> order(n), pos(n);
+    for (u64 i = 0; i < n; ++i) order[i] = (u32)i;
+    DevBuf d_pos, d_tile, d_cls_of, jobtab, B, B2, cls, dir, bsum, boff, Rd, Wc, kbase, plan_buf;
+    const u64 nw_max = mt / 64;
+    ALLOC(B, T * nw_max * sizeof(u64));
+    if (twice) ALLOC(B2, T * nw_max * sizeof(u64));
+    ALLOC(cls, (T + 1) * nw_max * sizeof(u64));
+    ALLOC(dir, (T + 1) * nw_max * sizeof(u32));
+    const u64 nb_max = (T + 1) * nw_max / kScanBlockWords;
+    ALLOC(bsum, nb_max * sizeof(u64));
+    ALLOC(boff, (nb_max + 1) * sizeof(u64));
+    ALLOC(Rd, sizeof(u64));
+    ALLOC(Wc, (T + 1) * sizeof(u64));
+    ALLOC(kbase, (T + 1) * sizeof(u64));
+    ALLOC(d_pos, n * sizeof(u32));
+    ALLOC(d_tile, n * sizeof(u32));
+    ALLOC(d_cls_of, n * sizeof(u32));
+    ALLOC(jobtab, kMaxTiles * sizeof(TcJobDesc));
+    ALLOC(plan_buf, (3 * n + 5) * sizeof(u64));
+    const Plan plan = carve_plan(plan_buf, n);
+    CK(cudaMemsetAsync(kbase.p, 0, (T + 1) * sizeof(u64), cs));
+
+    // classify the rows of [lo, lo + width) into B/cls and scan them; R_c on the host
+    std::vector<u64> Rc(T + 1, 0);
+    auto classify = [&](u64 lo, u64 width, bool& has_next, u64& next) -> int {
+        const u64 nw = width / 64;
+        const u64 hi = lo + width;  // 0 on wrap-around: unbounded
+        {
+            StageTimer t(ctx, &ctx->stats.ms_filter);
+            CK(launch_plan(st.d_off, st.d_ids, n, lo, hi, false, plan, cs));
+            CK(cudaMemsetAsync(B.p, 0, T * nw * sizeof(u64), cs));
+            if (twice) CK(cudaMemsetAsync(B2.p, 0, T * nw * sizeof(u64), cs));
+            CK(launch_filter_tiles(st.d_ids, n, plan, st.max_chunks, lo, width, B.as<u32>(),
+                                   twice ? B2.as<u32>() : nullptr, d_tile.as<u32>(), ctx->sms, cs));
+            k_classify<<<grid_of(nw, ctx->sms, 256), 256, 0, cs>>>(B.as<u64>(), twice ? B2.as<u64>() : nullptr, T, nw,
+                                                                   cls.as<u64>());
+            CK(cudaGetLastError());
+            ctx->stats.launches += 3;
+        }
+        {
+            StageTimer t(ctx, &ctx->stats.ms_scan);
+            CK(launch_scan(cls.as<u64>(), (T + 1) * nw, dir.as<u32>(), bsum.as<u64>(), boff.as<u64>(), Rd.as<u64>(),
+                           cs));
+            ctx->stats.launches += 2;
+        }
+        // every class's first block offset, the total and the plan's next value
+        const u64 nb = nw / kScanBlockWords;
+        CK(cudaMemcpy2DAsync(ctx->h_scalars, sizeof(u64), boff.as<u64>(), nb * sizeof(u64), sizeof(u64), T + 1,
+                             cudaMemcpyDeviceToHost, cs));
+        CK(cudaMemcpyAsync(ctx->h_scalars + 17, Rd.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
+        CK(cudaMemcpyAsync(ctx->h_scalars + 18, plan.totals + 2, 2 * sizeof(u64), cudaMemcpyDeviceToHost, cs));
+        CK(cudaStreamSynchronize(cs));
+        for (u64 c = 0; c <= T; ++c)
+            Rc[c] = (c < T ? ctx->h_scalars[c + 1] : ctx->h_scalars[17]) - ctx->h_scalars[c];
+        next = ctx->h_scalars[18];
+        has_next = ctx->h_scalars[19] != 0;
+        return JSIM_OK;
+    };
+
+    if (st.N) {
+        u64 ws = 1ull << 16;
+        const double want = (double)kSketchPerSample * (double)n;
+        while (ws < mt && (double)st.N * (double)ws / ((double)span + 1.0) < want) ws <<= 1;
+        const u64 lo_s = st.minid / ws * ws;
+        BatchBufs sb;
+        u64 R_s = 0, stride_s = 0;
+        int rc = build_batch(ctx, st, sb, lo_s, ws, R_s, stride_s, nullptr);
+        if (rc) return rc;
+        if (R_s) {
+            DevBuf Cs;
+            ALLOC(Cs, n * n * cb);
+            CK(cudaMemsetAsync(Cs.p, 0, n * n * cb, cs));
+            const u64 W_s = (R_s + 63) / 64;
+            rc = run_product(ctx, choose_variant(ctx, n, W_s), sb.X.as<u64>(), stride_s, n, W_s, Cs.p);
+            if (rc) return rc;
+            std::vector<u64> hc(n * n);
+            if (cb == 8) {
+                CK(cudaMemcpyAsync(hc.data(), Cs.p, n * n * 8, cudaMemcpyDeviceToHost, cs));
+                CK(cudaStreamSynchronize(cs));
+            } else {
+                std::vector<u32> h32(n * n);
+                CK(cudaMemcpyAsync(h32.data(), Cs.p, n * n * 4, cudaMemcpyDeviceToHost, cs));
+                CK(cudaStreamSynchronize(cs));
+                for (u64 k = 0; k < n * n; ++k) hc[k] = h32[k];
+            }
+            order = sample_order(hc, n);
+        }
+        for (u64 k = 0; k < n; ++k) pos[order[k]] = (u32)k;
+        std::vector<u32> tile(n), cls_of(n);
+        for (u64 i = 0; i < n; ++i) {
+            tile[i] = pos[i] / (u32)kTile;
+            cls_of[i] = 1 + tile[i];
+        }
+        CK(cudaMemcpyAsync(d_pos.p, pos.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(d_tile.p, tile.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(d_cls_of.p, cls_of.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
+        CK(cudaStreamSynchronize(cs));  // the host vectors are released at return
+
+        if (may_decline && R_s) {
+            // the sketch range's rows by class: is the product at least halved?
+            bool hn;
+            u64 nx;
+            rc = classify(lo_s, std::max(ws, kMinClassRows), hn, nx);
+            if (rc) return rc;
+            double dense = 0, sparse = 0;
+            for (u64 c = 0; c <= T; ++c) {
+                const double w = std::ceil((double)Rc[c] / 64.0);
+                dense += w;
+                if (c == 0) {
+                    sparse += w * (double)n * (double)(n + 1) / 2.0;
+                } else {
+                    const double m = (double)std::min<u64>(kTile, n - (c - 1) * kTile);
+                    sparse += w * m * (m + 1) / 2.0;
+                }
+            }
+            dense *= (double)n * (double)(n + 1) / 2.0;
+            if (sparse * 2.0 > dense) {
+                declined = true;
+                return JSIM_OK;
+            }
+        }
+    } else {
+        for (u64 k = 0; k < n; ++k) pos[k] = (u32)k;
+        CK(cudaMemcpyAsync(d_pos.p, pos.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
+        CK(cudaStreamSynchronize(cs));
+    }
+    ctx->stats.variant = JSIM_VARIANT_SPARSE;
+
+    // ---- the batch loop ----
+    DevBuf Cacc, XM, XS;
+    ALLOC(Cacc, n * n * cb);
+    CK(cudaMemsetAsync(Cacc.p, 0, n * n * cb, cs));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), cs));
+    if (st.N) {
+        u64 lo = st.minid / mt * mt;
+        for (;;) {
+            bool has_next = false;
+            u64 next = 0;
+            int rc = classify(lo, mt, has_next, next);
+            if (rc) return rc;
+            const u64 nw = mt / 64;
+            std::vector<u64> W(T + 1);
+            u64 R = 0, Wmax_s = 0;
+            for (u64 c = 0; c <= T; ++c) {
+                W[c] = (Rc[c] + 63) / 64;
+                R += Rc[c];
+                if (c) Wmax_s = std::max(Wmax_s, W[c]);
+            }
+            if (R) {
+                CK(cudaMemcpyAsync(Wc.p, W.data(), (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
+                const u64 stride_m = row_stride_words(W[0]), stride_s = row_stride_words(Wmax_s);
+                {
+                    StageTimer t(ctx, &ctx->stats.ms_pack);
+                    if (W[0]) {
+                        ALLOC(XM, n_pad * stride_m * sizeof(u64));
+                        CK(launch_zero_rows(XM.as<u64>(), n_pad, stride_m, W[0], ctx->sms, cs));
+                        CK(launch_pack_class(st.d_ids, n, plan, st.max_chunks, lo, mt, cls.as<u64>(), dir.as<u32>(),
+                                             boff.as<u64>(), nw, kbase.as<u64>(), Wc.as<u64>(), nullptr,
+                                             d_pos.as<u32>(), XM.as<u64>(), stride_m, ctx->sms, cs));
+                        ctx->stats.launches += 2;
+                    }
+                    if (Wmax_s) {
+                        ALLOC(XS, n_pad * stride_s * sizeof(u64));
+                        CK(launch_zero_rows(XS.as<u64>(), n_pad, stride_s, Wmax_s, ctx->sms, cs));
+                        CK(launch_pack_class(st.d_ids, n, plan, st.max_chunks, lo, mt, cls.as<u64>(), dir.as<u32>(),
+                                             boff.as<u64>(), nw, kbase.as<u64>(), Wc.as<u64>(), d_cls_of.as<u32>(),
+                                             d_pos.as<u32>(), XS.as<u64>(), stride_s, ctx->sms, cs));
+                        ctx->stats.launches += 2;
+                    }
+                }
+                {
+                    StageTimer t(ctx, &ctx->stats.ms_product);
+                    double done = 0;
+                    if (W[0]) {
+                        const int v = choose_variant(ctx, n, W[0]);
+                        rc = run_product(ctx, v, XM.as<u64>(), stride_m, n, W[0], Cacc.p);
+                        if (rc) return rc;
+                        done += (double)W[0] * (double)n * (double)(n + 1) / 2.0;
+                    }
+                    std::vector<TcJobDesc> jobs;
+                    for (u64 t2 = 0; t2 < T; ++t2) {
+                        if (!W[1 + t2]) continue;
+                        const u64 m = std::min<u64>(kTile, n - t2 * kTile);
+                        jobs.push_back(TcJobDesc{XS.as<u64>() + t2 * kTile * stride_s, nullptr,
+                                                 (char*)Cacc.p + (t2 * kTile * n + t2 * kTile) * cb, stride_s, m,
+                                                 W[1 + t2], n});
+                        done += (double)W[1 + t2] * (double)m * (double)(m + 1) / 2.0;
+                    }
+                    if (!jobs.empty()) {
+                        int launches = 0;
+                        CK(product_tc_jobs(jobs.data(), (int)jobs.size(), jobtab.p, true, ctx->opt.count_bits,
+                                           ctx->sms, ctx->d_err,
+                                           ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000, cs, &launches));
+                        ctx->stats.product_launches += launches;
+                        ctx->stats.launches += launches;
+                    }
+                    ctx->stats.bitops_done += 64.0 * done;
+                }
+                const u64 Wd = (R + 63) / 64;  // the words of the dense packing of the batch
+                ctx->stats.batches += 1;
+                ctx->stats.rows_nonzero += R;
+                ctx->stats.words += Wd;
+                ctx->stats.bitops_dense += 64.0 * (double)Wd * (double)n * (double)(n + 1) / 2.0;
+            }
+            if (!has_next) break;
+            lo = next / mt * mt;
+        }
+    }
+    ctx->stats.variant = JSIM_VARIANT_SPARSE;
+
+    // ---- outputs, read back through the sample order ----
+    int rc = check_device_waits(ctx, ctx->d_err);
+    if (rc) return rc;
+    DevBuf Cst, Jst;
+    void* Cdst = C;
+    double* Jdst = J;
+    if (out_mem == JSIM_MEM_HOST) {
+        if (C) { ALLOC(Cst, n * n * cb); Cdst = Cst.p; }
+        if (J) { ALLOC(Jst, n * n * sizeof(double)); Jdst = Jst.as<double>(); }
+    }
+    {
+        StageTimer t(ctx, &ctx->stats.ms_epilogue);
+        if (Cdst || Jdst) {
+            const unsigned g = grid_of(n * n, ctx->sms, 256);
+            if (cb == 8)
+                k_epilogue_perm<u64><<<g, 256, 0, cs>>>(Cacc.as<u64>(), n, d_pos.as<u32>(), st.sizes.as<u64>(),
+                                                        (u64*)Cdst, Jdst, twice, ctx->opt.distance, ctx->d_err);
+            else
+                k_epilogue_perm<u32><<<g, 256, 0, cs>>>(Cacc.as<u32>(), n, d_pos.as<u32>(), st.sizes.as<u64>(),
+                                                        (u32*)Cdst, Jdst, twice, ctx->opt.distance, ctx->d_err);
+            CK(cudaGetLastError());
+            ctx->stats.launches += 1;
+        }
+    }
+    {
+        StageTimer t(ctx, &ctx->stats.ms_d2h);
+        const cudaMemcpyKind k = out_mem == JSIM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        if (out_mem == JSIM_MEM_HOST) {
+            if (C) CK(cudaMemcpyAsync(C, Cst.p, n * n * cb, k, cs));
+            if (J) CK(cudaMemcpyAsync(J, Jst.p, n * n * sizeof(double), k, cs));
+        }
+        if (sizes) CK(cudaMemcpyAsync(sizes, st.sizes.p, n * sizeof(u64), k, cs));
+    }
+    CK(cudaStreamSynchronize(cs));
+    return JSIM_OK;
+}
+
+}  // namespace

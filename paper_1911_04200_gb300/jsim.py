@@ -20,7 +20,7 @@ ERRORS = {1: "JSIM_ERR_ARG", 2: "JSIM_ERR_UNSORTED", 3: "JSIM_ERR_OVERFLOW", 4: 
           5: "JSIM_ERR_OOM", 6: "JSIM_ERR_CUDA", 7: "JSIM_ERR_TIMEOUT", 8: "JSIM_ERR_CANCELLED",
           9: "JSIM_ERR_UNSUPPORTED", 10: "JSIM_ERR_INCOMPLETE", 11: "JSIM_ERR_CHECKPOINT"}
 MEM_HOST, MEM_DEVICE = 0, 1
-VARIANTS = {"auto": 0, "popc": 1, "b1": 2, "i8": 3, "f8": 4, "tc": 5, "tc2": 6}
+VARIANTS = {"auto": 0, "popc": 1, "b1": 2, "i8": 3, "f8": 4, "tc": 5, "tc2": 6, "sparse": 7}
 VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -88,7 +88,7 @@ class Stats(ctypes.Structure):
                 ("ms_validate", ctypes.c_double), ("ms_filter", ctypes.c_double), ("ms_scan", ctypes.c_double),
                 ("ms_pack", ctypes.c_double), ("ms_product", ctypes.c_double), ("ms_epilogue", ctypes.c_double),
                 ("ms_d2h", ctypes.c_double), ("bitops_dense", ctypes.c_double),
-                ("bitops_useful", ctypes.c_double), ("h2d_copies", ctypes.c_uint64),
+                ("bitops_useful", ctypes.c_double), ("bitops_done", ctypes.c_double), ("h2d_copies", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64)]
 
     def as_dict(self):

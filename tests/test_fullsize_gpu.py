@@ -77,19 +77,21 @@ def clade1024():
 @pytest.mark.timeout(900)
 def test_clade1024_full_size(gpu, clade1024):
     """The benchmark's workload (1024 samples, 1.3e9 values) with the automatic
-    product (SM pairs) and with the two-or-more filter: sampled parity, and the
-    two runs byte-identical."""
+    choice (the block-sparse product), the dense SM-pair product, and the
+    two-or-more filter: sampled parity, whole-result digests, and all runs
+    byte-identical."""
     off, ids = clade1024
     with jsim.Context(id_bits=32) as ctx:
         C, s, J = ctx.all_pairs(off, ids)
-        assert ctx.stats()["variant"] == "tc2"
+        assert ctx.stats()["variant"] == "sparse"
     check_sampled(off, ids, C, s, J)
     check_digests("clade1024", off, ids, C, s, J)
-    with jsim.Context(id_bits=32, filter_min=2) as ctx:
-        C2, s2, J2 = ctx.all_pairs(off, ids)
-    np.testing.assert_array_equal(C2, C)
-    np.testing.assert_array_equal(s2, s)
-    np.testing.assert_array_equal(J2.view(np.uint64), J.view(np.uint64))
+    for kw in (dict(variant="tc2"), dict(filter_min=2), dict(filter_min=2, variant="tc2")):
+        with jsim.Context(id_bits=32, **kw) as ctx:
+            C2, s2, J2 = ctx.all_pairs(off, ids)
+        np.testing.assert_array_equal(C2, C)
+        np.testing.assert_array_equal(s2, s)
+        np.testing.assert_array_equal(J2.view(np.uint64), J.view(np.uint64))
 
 
 @pytest.mark.timeout(900)
@@ -100,13 +102,14 @@ def test_clade1024_device_input_whole_result(gpu, clade1024):
     off, ids = clade1024
     d_off = torch.from_numpy(off.view(np.int64)).cuda()
     d_ids = torch.from_numpy(ids.view(np.int64)).cuda()
-    with jsim.Context(id_bits=32) as ctx:
-        C, s, J = ctx.all_pairs(d_off, d_ids)
-        torch.cuda.synchronize()
-        C = C.view(torch.int32).cpu().numpy().view(np.uint32)
-        s = s.view(torch.int64).cpu().numpy().view(np.uint64)
-        J = J.cpu().numpy()
-    check_digests("clade1024", off, ids, C, s, J)
+    for variant in ("auto", "tc2"):
+        with jsim.Context(id_bits=32, variant=variant) as ctx:
+            C, s, J = ctx.all_pairs(d_off, d_ids)
+            torch.cuda.synchronize()
+            C = C.view(torch.int32).cpu().numpy().view(np.uint32)
+            s = s.view(torch.int64).cpu().numpy().view(np.uint64)
+            J = J.cpu().numpy()
+        check_digests("clade1024", off, ids, C, s, J)
 
 
 def test_ancestral64_whole_result_digest(gpu):
