@@ -838,7 +838,8 @@ def run_jsim(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    agg = {"ms_product": 0.0, "product_launches": 0, "launches": 0, "bitops": 0.0}
+    agg = {"ms_product": 0.0, "product_launches": 0, "launches": 0, "bitops": 0.0, "bitops_done": 0.0,
+           "ms_pack": 0.0, "pack_bytes": 0, "ms_filter": 0.0}
     barrier()
     with Clocks(local) as clk:
         e0 = torch.cuda.Event(enable_timing=True)
@@ -850,6 +851,10 @@ def run_jsim(args):
             agg["product_launches"] += st["product_launches"]
             agg["launches"] += st["launches"]
             agg["bitops"] += st["bitops_dense"]
+            agg["bitops_done"] += st["bitops_done"]
+            agg["ms_pack"] += st["ms_pack"]
+            agg["pack_bytes"] += st["pack_bytes"]
+            agg["ms_filter"] += st["ms_filter"]
         e1.record(stream)
         barrier()
     ms_max, bitops_all = aggregate_over_ranks(e0.elapsed_time(e1), agg["bitops"], dev)
@@ -901,14 +906,33 @@ def run_jsim(args):
     compulsory = 8 * N + 8 * n * last["words"] + n * n * (cb + 8) + 8 * n
 
     variant = last["variant"]
-    per_launch_bitops = agg["bitops"] / max(1, agg["product_launches"])
+    # the product kernels against the tensor peak, by the bit-operations they
+    # carried out (the block-sparse variant skips the blocks no row reaches)
+    per_launch_bitops = agg["bitops_done"] / max(1, agg["product_launches"])
     ms_per_launch = agg["ms_product"] / max(1, agg["product_launches"])
-    roof = roofline_for(variant, per_launch_bitops, ms_per_launch, measured_peaks(),
-                        traffic_from_profiles(variant, args.workload) if args.filter_min == 1 else None)
+    roof_product = roofline_for(variant, per_launch_bitops, ms_per_launch, measured_peaks(),
+                                traffic_from_profiles(variant, args.workload) if args.filter_min == 1 else None)
+    roof_product["kernel"] = "product (%s)" % variant
+    # the pack against HBM, by its algorithmic bytes (values read, packed
+    # matrices filled)
+    pk, src = measured_peaks()
+    pack_gbs = agg["pack_bytes"] / (agg["ms_pack"] * 1e-3) / 1e9 if agg["ms_pack"] else 0.0
+    roof_pack = {"bound": "hbm", "achieved": round(pack_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "frac": round(pack_gbs / pk["hbm_gbs"], 4),
+                 "traffic": traffic_from_profiles("pack-" + variant, args.workload),
+                 "kernel": "pack", "peak_source": "%s HBM copy bandwidth" % src,
+                 "unit_bytes": "8 B per value packed + 8 B per word of the packed matrices filled"}
+    # the roofline line is the dominant stage's (by time)
+    if agg["ms_pack"] > agg["ms_product"]:
+        roof, roof_other = roof_pack, roof_product
+    else:
+        roof, roof_other = roof_product, roof_pack
     cfg.update({"batch_rows": last["batch_rows"], "batches": last["batches"], "variant": variant,
                 "filter_min": args.filter_min,
                 "rows_nonzero": last["rows_nonzero"], "words": last["words"], "values": N,
-                "bitops_dense_per_step": last["bitops_dense"], "bitops_useful_per_step": useful,
+                "bitops_dense_per_step": last["bitops_dense"],
+                "bitops_done_per_step": last["bitops_done"],
+                "bitops_useful_per_step": useful,
                 "useful_fraction": round(useful / last["bitops_dense"], 4) if last["bitops_dense"] else None,
                 "compulsory_bytes_per_step": compulsory,
                 "parallelism": "dp%d (independent problems)" % world,
@@ -919,7 +943,8 @@ def run_jsim(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 ids, u32 counts, f64 J", "data": "synthetic",
-            "config": cfg, "clocks": clk.summary(), "gpu_launches": agg["launches"], "roofline": roof, "e2e": e2e}
+            "config": cfg, "clocks": clk.summary(), "gpu_launches": agg["launches"], "roofline": roof,
+            "roofline_" + roof_other["kernel"].split()[0]: roof_other, "e2e": e2e}
     if world == 1 and not args.no_systems and args.workload == "clade1024":
         line["systems"] = systems_measure(args, d_off, d_ids, J, cfg)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

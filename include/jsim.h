@@ -160,6 +160,9 @@ typedef struct {
     double bitops_done;        /* bit-operations the product kernels carried out (64 per word pair of
                                   the upper triangle they multiplied): bitops_dense, except for the
                                   block-sparse variant, which skips the blocks no row reaches */
+    uint64_t pack_bytes;       /* bytes the pack kernels read and wrote by algorithm: 8 per value
+                                  packed plus 8 per word of the packed matrices they fill (zero
+                                  words included) */
     uint64_t h2d_copies;       /* host -> device copies the call issued for its input values */
     uint64_t h2d_bytes;        /* bytes of those copies */
 } jsim_stats;

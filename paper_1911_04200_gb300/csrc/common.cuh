@@ -58,14 +58,12 @@ cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan
 // width/32 u32 words each, tile-major); twice likewise (optional).
 cudaError_t launch_filter_tiles(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
                                u32* bitmaps, u32* twice, const u32* tile_of, int sms, cudaStream_t st);
-// Class-major packing (block-sparse product): sample i packs its values of
-// class cls_of[i] (class 0 when null) into row row_of[i] at word kbase[c] +
-// rank within the class / 64; cls holds nwords bitmap words per class
-// (nwords a multiple of kScanBlockWords), dir/boff the rank directory of
-// all classes scanned together; words at or beyond Wc[c] are not written.
-cudaError_t launch_pack_class(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width, const u64* cls,
-                              const u32* dir, const u64* boff, u64 nwords, const u64* kbase, const u64* Wc,
-                              const u32* cls_of, const u32* row_of, u64* X, u64 stride, int sms, cudaStream_t st);
+// Single pass into both matrices: class-0 values to XM (null: there are
+// none), class cls_of[i] values to XS, atomically OR-ed.
+cudaError_t launch_pack_classes(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width, const u64* cls,
+                                const u32* dir, const u64* boff, u64 nwords, const u64* kbase, const u32* cls_of,
+                                const u32* row_of, u64* XM, u64 stride_m, u64* XS, u64 stride_s, int sms,
+                                cudaStream_t st);
 // twice (optional): also the bitmap of rows held by two or more samples
 cudaError_t launch_filter(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
                           u32* bitmap, int sms, cudaStream_t st, u32* twice = nullptr);

@@ -436,6 +436,7 @@ int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 widt
     CK(cudaMemcpyAsync(ctx->h_scalars, bb.R.p, sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_scalars + 1, bb.plan.totals + 2, 2 * sizeof(u64), cudaMemcpyDeviceToHost,
                        ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_scalars + 3, bb.plan.totals, sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     R = ctx->h_scalars[0];
     if (next) *next = ctx->h_scalars[1];
@@ -443,6 +444,7 @@ int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 widt
     const u64 W = (R + 63) / 64;
     stride = row_stride_words(W);
     const u64 n_pad = round_up(std::max<u64>(n, 1), kRowPad);
+    ctx->stats.pack_bytes += 8 * ctx->h_scalars[3] + 8 * n_pad * W;
     const u64 need = n_pad * stride * sizeof(u64);
     ALLOC(bb.X, need);
     {

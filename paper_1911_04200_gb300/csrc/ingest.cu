@@ -400,114 +400,80 @@ k_pack_full(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, co
     }
 }
 
-// The same packing into the class-major layout of the block-sparse product.
-// The rows of a batch are split into classes, each with its own bitmap
-// (class c's words at cls + c * nwords), rank-scanned together (one
-// directory over all classes; nwords is a multiple of kScanBlockWords, so
-// class c's first block is c * nwords / kScanBlockWords and its ranks are
-// the directory's minus that block's offset).  Sample i packs its values of
-// class cls_of[i] (or of class 0 when cls_of is null) into row row_of[i] of
-// X, at word kbase[c] + (rank within the class) / 64.  Ranks within one
-// class are non-decreasing along a sample's sorted values, so the plain-store
-// ownership scheme above applies unchanged.
+// The class-major layout of the block-sparse product: the rows of a batch
+// are split into classes, each with its own bitmap (class c's words at cls +
+// c * nwords), rank-scanned together (one directory over all classes; nwords
+// is a multiple of kScanBlockWords, so class c's first block is c * nwords /
+// kScanBlockWords and its ranks are the directory's minus that block's
+// offset).
 struct ClassView {
     const u64* cls;      // class bitmaps, class-major
     const u32* dir;      // rank directory of all classes (one entry per word)
     const u64* boff;     // block offsets of all classes
     const u64* kbase;    // first word of each class in X (device)
-    const u64* Wc;       // word count of each class (device): words at or beyond it are not written
     u64 nwords;          // bitmap words per class
     const u32* cls_of;   // class of each sample, or null for class 0
     const u32* row_of;   // row of X of each sample
 };
 
-__device__ __forceinline__ long long class_word(u64 x, u64 lo, u64 width, const ClassView& v, u64 c, u64& bit)
-{
-    const u64 d = x - lo;
-    if (d >= width) {
-        bit = 0ull;
-        return 0x7fffffffffffffffll;
-    }
-    const u64 w = c * v.nwords + (d >> 6), word = v.cls[w];
-    const u64 below = word & ((1ull << (d & 63)) - 1ull);
-    const u64 r = v.boff[w / kScanBlockWords] - v.boff[c * v.nwords / kScanBlockWords] + (u64)v.dir[w] +
-                  (u64)__popcll(below);
-    bit = ((word >> (d & 63)) & 1ull) ? (1ull << (r & 63)) : 0ull;
-    return (long long)(r >> 6);
-}
-
+// Single-pass packing into both class matrices of the block-sparse product:
+// a value of sample i whose row is of class 0 goes to XM, one of class
+// cls_of[i] (the sample's tile) to XS, at word kbase[c] + (rank within the
+// class) / 64 of row row_of[i]; other rows are not packed.  Classes
+// interleave along a sample's values, so the words are OR-ed in with atomics
+// (lanes of a warp holding the same word combine first).
 __global__ void __launch_bounds__(kIngestThreads)
-k_pack_class(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, ClassView v, u64* X, u64 stride)
+k_pack_classes(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, ClassView v, u64* XM,
+               u64 stride_m, u64* XS, u64 stride_s)
 {
-    __shared__ u64 s_i, s_p0, s_p1, s_b, s_e;
+    __shared__ u64 s_i, s_p0, s_p1;
     const u64 nch = plan.totals[1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long kBig = 0x7fffffffffffffffll;
+    const u64 blk0 = 0;
     for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
         if (threadIdx.x == 0) {
             const u64 i = chunk_sample(plan.cofs, n, c);
             const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
-            s_i = i; s_p0 = p0; s_b = plan.beg[i];
-            s_e = plan.beg[i] + plan.len[i];
-            s_p1 = min(p0 + kChunk, s_e);
+            s_i = i; s_p0 = p0;
+            s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
         }
         __syncthreads();
-        const u64 i = s_i, bb = s_b, be = s_e;
-        const u64 sbeg = s_p0 + (u64)warp * kPackSeg, send = min(sbeg + kPackSeg, s_p1);
-        __syncthreads();  // the shared chunk fields are read; the next chunk may overwrite them
-        if (sbeg >= send) continue;
-        const u64 cl = v.cls_of ? (u64)v.cls_of[i] : 0ull;
-        const long long Wl = (long long)v.Wc[cl];
-        u64* row = X + (u64)v.row_of[i] * stride + v.kbase[cl];
-        u64 tmp;
-        const long long seg_prev = sbeg > bb ? class_word(ids[sbeg - 1], lo, width, v, cl, tmp) : -1ll;
-        long long open_key = seg_prev;
-        u64 open_mask = 0ull;
-        for (u64 base = sbeg; base < send; base += 32) {
-            const u64 pos = base + lane;
-            long long key = kBig;
-            u64 bit = 0ull;
-            if (pos < send) key = class_word(ids[pos], lo, width, v, cl, bit);
-            const bool lead = segmented_or<u64>((u64)key, bit);
-            const bool real = lead && key != kBig;
-            const unsigned leads = __ballot_sync(0xffffffffu, real);
-            const int last_lead = 31 - __clz((int)leads);  // leads != 0: lane 0 holds a value
-            long long nkey = open_key;
-            u64 nmask = open_mask;
-            if (real) {
-                u64 mask = bit;
-                if (lane == 0) {
-                    if (key == open_key) {
-                        mask |= open_mask;  // the open word continues
-                    } else if (open_key > seg_prev && open_key < Wl && open_mask) {
-                        row[open_key] = open_mask;  // the open word is complete
+        const u64 i = s_i, p0 = s_p0, p1 = s_p1;
+        const u64 cs = v.cls_of[i];
+        const u64 row = v.row_of[i];
+        u64* rowm = XM ? XM + row * stride_m + v.kbase[0] : nullptr;
+        u64* rows = XS + row * stride_s + v.kbase[cs];
+        const u64 bm0 = blk0, bms = cs * v.nwords / kScanBlockWords;
+        for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
+            const u64 pos = base + (threadIdx.x & 31);
+            u64 key = ~0ull, bit = 0ull;
+            if (pos < p1) {
+                const u64 d = ids[pos] - lo;
+                if (d < width) {
+                    const u64 w0 = d >> 6, sh = d & 63, low = (1ull << sh) - 1ull;
+                    const u64 m0 = v.cls[w0];
+                    if ((m0 >> sh) & 1ull) {
+                        const u64 r = v.boff[w0 / kScanBlockWords] - v.boff[bm0] + (u64)v.dir[w0] +
+                                      (u64)__popcll(m0 & low);
+                        key = r >> 6;  // class 0: keys below 2^62
+                        bit = 1ull << (r & 63);
+                    } else {
+                        const u64 ws = cs * v.nwords + w0, ms = v.cls[ws];
+                        if ((ms >> sh) & 1ull) {
+                            const u64 r = v.boff[ws / kScanBlockWords] - v.boff[bms] + (u64)v.dir[ws] +
+                                          (u64)__popcll(ms & low);
+                            key = (1ull << 62) | (r >> 6);
+                            bit = 1ull << (r & 63);
+                        }
                     }
                 }
-                if (lane != last_lead) {
-                    if (key > seg_prev && key < Wl && mask) row[key] = mask;
-                } else {
-                    nkey = key;
-                    nmask = mask;
-                }
             }
-            open_key = __shfl_sync(0xffffffffu, nkey, last_lead);
-            open_mask = __shfl_sync(0xffffffffu, nmask, last_lead);
-        }
-        if (open_key > seg_prev) {
-            // finish the last word with the next segment's values of the same word
-            for (u64 base = send; base < be; base += 32) {
-                const u64 pos = base + lane;
-                long long key = kBig;
-                u64 bit = 0ull;
-                if (pos < be) key = class_word(ids[pos], lo, width, v, cl, bit);
-                u64 m = key == open_key ? bit : 0ull;
-                #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
-                open_mask |= m;
-                if (__any_sync(0xffffffffu, key != open_key)) break;
+            const bool lead = segmented_or<u64>(key, bit);
+            if (lead && bit) {
+                if (key >> 62) atomicOr((unsigned long long*)(rows + (key & ((1ull << 62) - 1))), bit);
+                else atomicOr((unsigned long long*)(rowm + key), bit);
             }
-            if (lane == 0 && open_key < Wl && open_mask) row[open_key] = open_mask;
         }
+        __syncthreads();
     }
 }
 
@@ -573,12 +539,14 @@ cudaError_t launch_pack_full(const u64* ids, u64 n, Plan plan, u64 max_chunks, u
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_class(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width, const u64* cls,
-                              const u32* dir, const u64* boff, u64 nwords, const u64* kbase, const u64* Wc,
-                              const u32* cls_of, const u32* row_of, u64* X, u64 stride, int sms, cudaStream_t st)
+cudaError_t launch_pack_classes(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width, const u64* cls,
+                                const u32* dir, const u64* boff, u64 nwords, const u64* kbase, const u32* cls_of,
+                                const u32* row_of, u64* XM, u64 stride_m, u64* XS, u64 stride_s, int sms,
+                                cudaStream_t st)
 {
-    ClassView v{cls, dir, boff, kbase, Wc, nwords, cls_of, row_of};
-    k_pack_class<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, width, v, X, stride);
+    ClassView v{cls, dir, boff, kbase, nwords, cls_of, row_of};
+    k_pack_classes<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, width, v, XM,
+                                                                                stride_m, XS, stride_s);
     return cudaGetLastError();
 }
 

@@ -23,13 +23,19 @@
 //     Class 1 + t words: a 128 x 128 product of tile t only, added to the
 //     diagonal block of tile t - the only block they can change, since no
 //     other sample holds those rows.  All tiles' blocks run in one launch of
-//     the job-table product.  C accumulates in sample-order positions; the
-//     epilogue reads it back through the order.
+//     the job-table product.  The words of successive batches are appended
+//     (Eq. 4) and multiplied when the matrices fill and at the end.  C
+//     accumulates in sample-order positions; the epilogue reads it back
+//     through the order.
+//  The pack is one pass over the values: a value goes to the class-0 matrix
+//  or to its tile's, OR-ed in with atomics (warp lanes holding the same word
+//  combine first), since the two classes interleave along a sample.
 //
 // Every count is the same integer as the dense product's (a sum over the
 // same rows, Eq. 4, grouped differently), so C and J are bit-identical.  With
-// AUTO the sketch's own rows are classified first; when the class structure
-// would not at least halve the product's work the call goes on dense.
+// AUTO the sketch's own rows are classified first, and the call goes on dense
+// unless the estimated time of the whole call (product and ingest at rates
+// measured on GB300) is at least 5 % below the dense call's.
 //
 // Internal header of the C-ABI translation unit (included once, after ctx.cuh).
 #pragma once
@@ -42,6 +48,17 @@ constexpr u64 kMaxTiles = 16;             // n <= 2048
 constexpr u64 kSketchPerSample = 512;     // values per sample in the sketch range, on average
 constexpr u64 kMinClassRows = 1ull << 18; // batch width granule: one scan block of every class
 constexpr u64 kTileBitmapBytes = 64ull << 20;  // all tiles' filter bitmaps of a batch together
+// Rates measured on GB300 (1024 clade samples, 1.3e9 values; both filters)
+// that the automatic choice weighs: dense SM-pair product and block-sparse
+// products in bit-operations per ms; ingest (validation, filter, scan, pack)
+// per value in ms, dense and block-sparse, one filter and two-or-more.
+// Batch widths swept at 2^25..2^28 rows: the block-sparse ingest is fastest
+// where all tiles' bitmaps fit in kTileBitmapBytes (L2), 68 ms per call at
+// 2^26 (one filter) and 70 ms at 2^25 (two-or-more filter).
+constexpr double kDenseBitopsPerMs = 1.1e12;
+constexpr double kSparseBitopsPerMs = 0.65e12;
+constexpr double kIngestDenseMs[2] = {2.8e-8, 2.5e-8};
+constexpr double kIngestSparseMs[2] = {3.6e-8, 4.2e-8};
 
 // Row classes from the tiles' bitmaps: class 0 = rows of two or more tiles,
 // class 1 + t = rows of tile t alone (with the two-or-more filter: rows tile
@@ -86,6 +103,21 @@ __global__ void k_epilogue_perm(const CT* __restrict__ Cacc, u64 n, const u32* _
             const double s = u ? __ddiv_rn(__ull2double_rn((u64)c), __ull2double_rn(u)) : 1.0;
             J[t] = distance ? __dsub_rn(1.0, s) : s;
         }
+    }
+}
+
+// Zero the words [base[c], base[c] + words[c]) of the rows of every tile
+// (tile t: rows [kTile t, kTile t + kTile) of X, class c = 1 + t; c = 0:
+// all rows, class 0), before a batch packs its words there.
+__global__ void k_zero_classes(u64* X, u64 rows, u64 stride, const u64* __restrict__ base,
+                               const u64* __restrict__ words, int per_tile)
+{
+    for (u64 r = blockIdx.y; r < rows; r += gridDim.y) {
+        const u64 c = per_tile ? 1 + r / kTile : 0;
+        const u64 b = base[c], w = words[c];
+        u64* row = X + r * stride + b;
+        for (u64 k = blockIdx.x * (u64)blockDim.x + threadIdx.x; k < w; k += (u64)gridDim.x * blockDim.x)
+            row[k] = 0ull;
     }
 }
 
@@ -171,7 +203,7 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
         if (mt % kMinClassRows) return JSIM_ERR_UNSUPPORTED;
     } else {
         mt = auto_batch_rows(span + 1 ? span + 1 : ~0ull);
-        while (mt > kMinClassRows && T * (mt / 8) > kTileBitmapBytes) mt >>= 1;
+        while (mt > kMinClassRows && T * (mt / 8) * (twice ? 2 : 1) > kTileBitmapBytes) mt >>= 1;
         mt = std::max(mt, kMinClassRows);
     }
     ctx->stats.batch_rows = mt;
@@ -202,6 +234,7 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
 
     // classify the rows of [lo, lo + width) into B/cls and scan them; R_c on the host
     std::vector<u64> Rc(T + 1, 0);
+    u64 range_values = 0;  // values of the last classified range
     auto classify = [&](u64 lo, u64 width, bool& has_next, u64& next) -> int {
         const u64 nw = width / 64;
         const u64 hi = lo + width;  // 0 on wrap-around: unbounded
@@ -229,11 +262,13 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
                              cudaMemcpyDeviceToHost, cs));
         CK(cudaMemcpyAsync(ctx->h_scalars + 17, Rd.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
         CK(cudaMemcpyAsync(ctx->h_scalars + 18, plan.totals + 2, 2 * sizeof(u64), cudaMemcpyDeviceToHost, cs));
+        CK(cudaMemcpyAsync(ctx->h_scalars + 20, plan.totals, sizeof(u64), cudaMemcpyDeviceToHost, cs));
         CK(cudaStreamSynchronize(cs));
         for (u64 c = 0; c <= T; ++c)
             Rc[c] = (c < T ? ctx->h_scalars[c + 1] : ctx->h_scalars[17]) - ctx->h_scalars[c];
         next = ctx->h_scalars[18];
         has_next = ctx->h_scalars[19] != 0;
+        range_values = ctx->h_scalars[20];
         return JSIM_OK;
     };
 
@@ -282,19 +317,26 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
             u64 nx;
             rc = classify(lo_s, std::max(ws, kMinClassRows), hn, nx);
             if (rc) return rc;
-            double dense = 0, sparse = 0;
+            // the call's product work, dense and block-sparse, scaled from the
+            // sketch range's rows by values; with the ingest, the call's time
+            // either way at the measured rates
+            double rows = 0, sparse = 0;
             for (u64 c = 0; c <= T; ++c) {
-                const double w = std::ceil((double)Rc[c] / 64.0);
-                dense += w;
+                const double r = (double)Rc[c];
+                rows += r;
                 if (c == 0) {
-                    sparse += w * (double)n * (double)(n + 1) / 2.0;
+                    sparse += r * (double)n * (double)(n + 1) / 2.0;
                 } else {
                     const double m = (double)std::min<u64>(kTile, n - (c - 1) * kTile);
-                    sparse += w * m * (m + 1) / 2.0;
+                    sparse += r * m * (m + 1) / 2.0;
                 }
             }
-            dense *= (double)n * (double)(n + 1) / 2.0;
-            if (sparse * 2.0 > dense) {
+            const double scale = range_values ? (double)st.N / (double)range_values : 1.0;
+            const double dense_bitops = rows * scale * (double)n * (double)(n + 1) / 2.0;
+            const double sparse_bitops = sparse * scale;
+            const double t_dense = dense_bitops / kDenseBitopsPerMs + (double)st.N * kIngestDenseMs[twice];
+            const double t_sparse = sparse_bitops / kSparseBitopsPerMs + (double)st.N * kIngestSparseMs[twice];
+            if (t_sparse > 0.95 * t_dense) {
                 declined = true;
                 return JSIM_OK;
             }
@@ -307,10 +349,51 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
     ctx->stats.variant = JSIM_VARIANT_SPARSE;
 
     // ---- the batch loop ----
+    // The class-0 words of all samples (XM) and every tile's own words (XS,
+    // tile t in rows [kTile t, kTile t + kTile)) are appended batch after
+    // batch (C is a sum over batches, Eq. 4) and multiplied when a matrix is
+    // full and at the end: few, deep products instead of two per batch.
     DevBuf Cacc, XM, XS;
     ALLOC(Cacc, n * n * cb);
     CK(cudaMemsetAsync(Cacc.p, 0, n * n * cb, cs));
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), cs));
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 8ull << 30; }
+    const u64 budget = std::min<u64>(12ull << 30, (u64)free_b / 4);  // XM a third, XS two thirds
+    u64 capM = std::max<u64>(1ull << 12, budget / 3 / (n_pad * 8) / 64 * 64);
+    u64 capS = std::max<u64>(1ull << 12, budget * 2 / 3 / (n_pad * 8) / 64 * 64);
+    u64 stride_m = 0, stride_s = 0;
+    u64 totM = 0;
+    std::vector<u64> totS(T, 0);
+    std::vector<u64> hk(2 * (T + 1));  // kbase then Wc of a batch, uploaded together
+    auto flush = [&]() -> int {
+        StageTimer t(ctx, &ctx->stats.ms_product);
+        double done = 0;
+        if (totM) {
+            int r = run_product(ctx, choose_variant(ctx, n, totM), XM.as<u64>(), stride_m, n, totM, Cacc.p);
+            if (r) return r;
+            done += (double)totM * (double)n * (double)(n + 1) / 2.0;
+        }
+        std::vector<TcJobDesc> jobs;
+        for (u64 t2 = 0; t2 < T; ++t2) {
+            if (!totS[t2]) continue;
+            const u64 m = std::min<u64>(kTile, n - t2 * kTile);
+            jobs.push_back(TcJobDesc{XS.as<u64>() + t2 * kTile * stride_s, nullptr,
+                                     (char*)Cacc.p + (t2 * kTile * n + t2 * kTile) * cb, stride_s, m, totS[t2], n});
+            done += (double)totS[t2] * (double)m * (double)(m + 1) / 2.0;
+        }
+        if (!jobs.empty()) {
+            int launches = 0;
+            CK(product_tc_jobs(jobs.data(), (int)jobs.size(), jobtab.p, true, ctx->opt.count_bits, ctx->sms,
+                               ctx->d_err, ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000, cs, &launches));
+            ctx->stats.product_launches += launches;
+            ctx->stats.launches += launches;
+        }
+        ctx->stats.bitops_done += 64.0 * done;
+        totM = 0;
+        std::fill(totS.begin(), totS.end(), 0ull);
+        return JSIM_OK;
+    };
     if (st.N) {
         u64 lo = st.minid / mt * mt;
         for (;;) {
@@ -321,61 +404,68 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
             const u64 nw = mt / 64;
             std::vector<u64> W(T + 1);
             u64 R = 0, Wmax_s = 0;
+            bool full = false;
             for (u64 c = 0; c <= T; ++c) {
                 W[c] = (Rc[c] + 63) / 64;
                 R += Rc[c];
-                if (c) Wmax_s = std::max(Wmax_s, W[c]);
+                if (c) {
+                    Wmax_s = std::max(Wmax_s, W[c]);
+                    full = full || totS[c - 1] + W[c] > capS;
+                }
             }
+            full = full || totM + W[0] > capM;
             if (R) {
-                CK(cudaMemcpyAsync(Wc.p, W.data(), (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
-                const u64 stride_m = row_stride_words(W[0]), stride_s = row_stride_words(Wmax_s);
+                if (full) {
+                    rc = flush();
+                    if (rc) return rc;
+                }
+                // a batch alone above the capacity widens the matrix (it is empty now)
+                if (W[0] > capM) { capM = round_up(W[0], 64); stride_m = 0; }
+                if (Wmax_s > capS) { capS = round_up(Wmax_s, 64); stride_s = 0; }
+                if (!stride_m && W[0]) {
+                    stride_m = row_stride_words(capM);
+                    XM.release();
+                    ALLOC(XM, n_pad * stride_m * sizeof(u64));
+                }
+                if (!stride_s && Wmax_s) {
+                    stride_s = row_stride_words(capS);
+                    XS.release();
+                    ALLOC(XS, n_pad * stride_s * sizeof(u64));
+                }
+                hk[0] = totM;
+                hk[T + 1] = W[0];
+                for (u64 t2 = 0; t2 < T; ++t2) {
+                    hk[1 + t2] = totS[t2];
+                    hk[T + 2 + t2] = W[1 + t2];
+                }
+                CK(cudaMemcpyAsync(kbase.p, hk.data(), (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
+                CK(cudaMemcpyAsync(Wc.p, hk.data() + T + 1, (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
                 {
                     StageTimer t(ctx, &ctx->stats.ms_pack);
                     if (W[0]) {
-                        ALLOC(XM, n_pad * stride_m * sizeof(u64));
-                        CK(launch_zero_rows(XM.as<u64>(), n_pad, stride_m, W[0], ctx->sms, cs));
-                        CK(launch_pack_class(st.d_ids, n, plan, st.max_chunks, lo, mt, cls.as<u64>(), dir.as<u32>(),
-                                             boff.as<u64>(), nw, kbase.as<u64>(), Wc.as<u64>(), nullptr,
-                                             d_pos.as<u32>(), XM.as<u64>(), stride_m, ctx->sms, cs));
-                        ctx->stats.launches += 2;
+                        dim3 g(std::max<unsigned>(1, (unsigned)std::min<u64>((W[0] + 255) / 256, 64)),
+                               (unsigned)std::min<u64>(n_pad, 1024));
+                        k_zero_classes<<<g, 256, 0, cs>>>(XM.as<u64>(), n_pad, stride_m, kbase.as<u64>(), Wc.as<u64>(), 0);
+                        CK(cudaGetLastError());
                     }
                     if (Wmax_s) {
-                        ALLOC(XS, n_pad * stride_s * sizeof(u64));
-                        CK(launch_zero_rows(XS.as<u64>(), n_pad, stride_s, Wmax_s, ctx->sms, cs));
-                        CK(launch_pack_class(st.d_ids, n, plan, st.max_chunks, lo, mt, cls.as<u64>(), dir.as<u32>(),
-                                             boff.as<u64>(), nw, kbase.as<u64>(), Wc.as<u64>(), d_cls_of.as<u32>(),
-                                             d_pos.as<u32>(), XS.as<u64>(), stride_s, ctx->sms, cs));
-                        ctx->stats.launches += 2;
+                        dim3 g(std::max<unsigned>(1, (unsigned)std::min<u64>((Wmax_s + 255) / 256, 64)),
+                               (unsigned)std::min<u64>(T * kTile, 1024));
+                        k_zero_classes<<<g, 256, 0, cs>>>(XS.as<u64>(), T * kTile, stride_s, kbase.as<u64>(),
+                                                          Wc.as<u64>(), 1);
+                        CK(cudaGetLastError());
                     }
+                    CK(launch_pack_classes(st.d_ids, n, plan, st.max_chunks, lo, mt, cls.as<u64>(), dir.as<u32>(),
+                                           boff.as<u64>(), nw, kbase.as<u64>(), d_cls_of.as<u32>(), d_pos.as<u32>(),
+                                           W[0] ? XM.as<u64>() : nullptr, stride_m,
+                                           Wmax_s ? XS.as<u64>() : nullptr, stride_s, ctx->sms, cs));
+                    ctx->stats.launches += 3;
                 }
-                {
-                    StageTimer t(ctx, &ctx->stats.ms_product);
-                    double done = 0;
-                    if (W[0]) {
-                        const int v = choose_variant(ctx, n, W[0]);
-                        rc = run_product(ctx, v, XM.as<u64>(), stride_m, n, W[0], Cacc.p);
-                        if (rc) return rc;
-                        done += (double)W[0] * (double)n * (double)(n + 1) / 2.0;
-                    }
-                    std::vector<TcJobDesc> jobs;
-                    for (u64 t2 = 0; t2 < T; ++t2) {
-                        if (!W[1 + t2]) continue;
-                        const u64 m = std::min<u64>(kTile, n - t2 * kTile);
-                        jobs.push_back(TcJobDesc{XS.as<u64>() + t2 * kTile * stride_s, nullptr,
-                                                 (char*)Cacc.p + (t2 * kTile * n + t2 * kTile) * cb, stride_s, m,
-                                                 W[1 + t2], n});
-                        done += (double)W[1 + t2] * (double)m * (double)(m + 1) / 2.0;
-                    }
-                    if (!jobs.empty()) {
-                        int launches = 0;
-                        CK(product_tc_jobs(jobs.data(), (int)jobs.size(), jobtab.p, true, ctx->opt.count_bits,
-                                           ctx->sms, ctx->d_err,
-                                           ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000, cs, &launches));
-                        ctx->stats.product_launches += launches;
-                        ctx->stats.launches += launches;
-                    }
-                    ctx->stats.bitops_done += 64.0 * done;
-                }
+                totM += W[0];
+                for (u64 t2 = 0; t2 < T; ++t2) totS[t2] += W[1 + t2];
+                u64 ws_sum = 0;
+                for (u64 t2 = 0; t2 < T; ++t2) ws_sum += W[1 + t2];
+                ctx->stats.pack_bytes += 8 * range_values + 8 * (n_pad * W[0] + kTile * ws_sum);
                 const u64 Wd = (R + 63) / 64;  // the words of the dense packing of the batch
                 ctx->stats.batches += 1;
                 ctx->stats.rows_nonzero += R;
@@ -385,6 +475,8 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
             if (!has_next) break;
             lo = next / mt * mt;
         }
+        int rc = flush();
+        if (rc) return rc;
     }
     ctx->stats.variant = JSIM_VARIANT_SPARSE;
 

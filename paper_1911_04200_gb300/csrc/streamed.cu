@@ -709,6 +709,7 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
             CK(launch_pack_full(d_ids, n, plan, max_chunks, lo, width, bm.as<u64>(), dir.as<u32>(),
                                 boff.as<u64>(), X.as<u64>(), stride, Rd.as<u64>(), ctx->sms, cs));
             ctx->stats.launches += 2;
+            ctx->stats.pack_bytes += 8 * s.count + 8 * n_pad * stride;
         }
         CK(cudaEventRecord(ss->released[k], cs));  // the slice's values are no longer read
         if (W) {

@@ -88,7 +88,8 @@ class Stats(ctypes.Structure):
                 ("ms_validate", ctypes.c_double), ("ms_filter", ctypes.c_double), ("ms_scan", ctypes.c_double),
                 ("ms_pack", ctypes.c_double), ("ms_product", ctypes.c_double), ("ms_epilogue", ctypes.c_double),
                 ("ms_d2h", ctypes.c_double), ("bitops_dense", ctypes.c_double),
-                ("bitops_useful", ctypes.c_double), ("bitops_done", ctypes.c_double), ("h2d_copies", ctypes.c_uint64),
+                ("bitops_useful", ctypes.c_double), ("bitops_done", ctypes.c_double), ("pack_bytes", ctypes.c_uint64),
+                ("h2d_copies", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64)]
 
     def as_dict(self):
