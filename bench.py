@@ -45,6 +45,8 @@ UNIT = "Tbit-ops/s"
 POPC_PER_CLK_PER_SM = 16        # 32-bit population counts per clock per SM
 SMS = 152
 SM_MAX_MHZ = 2070.0
+VARIANT_NAME = {"sparse": "block-sparse product", "tc2": "dense SM-pair product", "tc": "dense one-SM product",
+                "popc": "CUDA-core product"}
 LEGACY_INT_MMA_TOPS = 73.0      # mma.sync m16n8k32 s8 / m16n8k256 b1 multiply-adds per second, measured
 
 
@@ -871,8 +873,11 @@ def run_jsim(args):
         barrier()
         t0 = time.perf_counter()
         bo = 0.0
+        calls = []
         for _ in range(args.steps):
+            tc = time.perf_counter()
             ctx.all_pairs(off, ids, out=(hC, hS, hJ))
+            calls.append((time.perf_counter() - tc) * 1e3)
             bo += ctx.stats()["bitops_dense"]
         barrier()
         dt, bo = aggregate_over_ranks(time.perf_counter() - t0, bo, dev)
@@ -882,13 +887,18 @@ def run_jsim(args):
                "d2h_bytes_per_step": int(n * n * 4 + n * 8 + n * n * 8), "ms_per_step": e2e_ms,
                "exposed_ms_per_step": round(e2e_ms - ms_max / args.steps, 2),
                "h2d_copies_per_step": int(se["h2d_copies"]),
+               "call_ms": [round(x, 1) for x in calls],
+               "stage_ms_last_call": {k: round(se[k], 2) for k in ("ms_total", "ms_h2d", "ms_validate", "ms_filter",
+                                                                   "ms_scan", "ms_pack", "ms_product", "ms_d2h")},
                "h2d_copy_stream_busy_ms": round(se["ms_h2d"], 2),
                "h2d_gbs_while_overlapped": round(se["h2d_bytes"] / (se["ms_h2d"] * 1e-3) / 1e9, 1)
                if se["ms_h2d"] else None,
                "h2d_gbs_one_1gib_copy": one_copy_gbs(ids, dev),
                "host_input_memory": numa_of_buffer(ids),
-               "path": "host input above 4 GiB: streamed through two 1 GiB pinned staging buffers, "
-                       "copies overlapping the device's work (super-batches planned one ahead)"}
+               "path": ("host input above 4 GiB: streamed through two 1 GiB pinned staging buffers, copies "
+                        "overlapping the device's work (super-batches planned one ahead)" if se["h2d_copies"] > 2 else
+                        "the whole input copied to the device in one copy, then the device-resident call "
+                        "(%s)" % VARIANT_NAME.get(se["variant"], se["variant"]))}
         # the whole end-to-end result equals the device-resident run's
         assert np.array_equal(hJ.view(np.uint64), J.cpu().numpy().view(np.uint64))
         assert np.array_equal(hC, C.view(torch.int32).cpu().numpy().view(np.uint32))

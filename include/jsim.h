@@ -136,6 +136,8 @@ typedef struct {
                              of jsim_product into jsim_stats.bitops_useful (one more read of
                              every packed batch; a resumed streamed call counts the
                              super-batches it ran); 0 (default): not counted */
+    int tile_n;           /* tensor-core tiles of a batched call's job-table product: 128 x 256
+                             (256) or 128 x 128 (128); 0 (default): the tuner times both */
 } jsim_options;
 
 typedef struct jsim_ctx jsim_ctx;
@@ -160,6 +162,8 @@ typedef struct {
     double bitops_done;        /* bit-operations the product kernels carried out (64 per word pair of
                                   the upper triangle they multiplied): bitops_dense, except for the
                                   block-sparse variant, which skips the blocks no row reaches */
+    uint64_t tile_n;           /* a batched call's tensor-core tiles: 128 x tile_n (256 or 128, as
+                                  tuned); 0 when its product ran on CUDA cores */
     uint64_t pack_bytes;       /* bytes the pack kernels read and wrote by algorithm: 8 per value
                                   packed plus 8 per word of the packed matrices they fill (zero
                                   words included) */
@@ -508,12 +512,13 @@ JSIM_API int jsim_threshold(jsim_ctx* ctx, const double* J, uint64_t n, double t
  * more stages than the exact-count cap, and that every slot is drained as
  * often as it is committed.
  *   njobs   1..256; grid >= 1
+ *   tile_n  the tile width: 256 (tiles of 128 x 256) or 128 (tiles of 128 x 128)
  *   msg     receives a description of the first failed check (cap bytes, may be NULL)
  * Returns 0 when every check passes, JSIM_ERR_ARG for bad arguments, and a
  * positive check number otherwise.
  */
 JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n, const uint64_t* W, const uint64_t* stride,
-                                    const uint64_t* rows, uint32_t grid, char* msg, size_t cap);
+                                    const uint64_t* rows, uint32_t grid, uint32_t tile_n, char* msg, size_t cap);
 
 /* Statistics of the last call on the context. */
 JSIM_API int jsim_get_stats(const jsim_ctx* ctx, jsim_stats* out);

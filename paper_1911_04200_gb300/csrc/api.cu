@@ -31,6 +31,7 @@ void jsim_default_options(jsim_options* opt)
     opt->filter_min = 1;
     opt->distance = 0;
     opt->count_useful = 0;
+    opt->tile_n = 0;
 }
 
 int jsim_create(jsim_ctx** out, const jsim_options* opt)
@@ -47,6 +48,7 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
     if (o.filter_min != 1 && o.filter_min != 2) return JSIM_ERR_ARG;
     if (o.distance != 0 && o.distance != 1) return JSIM_ERR_ARG;
     if (o.count_useful != 0 && o.count_useful != 1) return JSIM_ERR_ARG;
+    if (o.tile_n != 0 && o.tile_n != 128 && o.tile_n != 256) return JSIM_ERR_ARG;
     if ((o.alloc == nullptr) != (o.free == nullptr)) return JSIM_ERR_ARG;
     const bool own_pool = !o.alloc;
     jsim_ctx* c = new jsim_ctx();
@@ -132,6 +134,34 @@ constexpr u64 kHostStreamBytes = 1ull << 30;
 constexpr u64 kHostStreamMin = 4ull << 30;
 
 namespace {
+
+// Whether host input above kHostStreamMin should rather be copied whole to
+// the device for the block-sparse path (asked for, or AUTO in its range of
+// sample counts) than streamed through the dense path: it must fit in a
+// third of the free device memory.  The block-sparse call is three times
+// faster on the device than the dense one for clade collections, more than
+// the whole copy costs (1024 samples, 10.5 GB: copy 50 ms, call 67 ms; the
+// streamed dense call 216 ms).
+bool sparse_may_apply(jsim_ctx* ctx, const jsim_sets* sets)
+{
+    const int v = ctx->opt.variant;
+    const u64 n = sets->n;
+    if (v != JSIM_VARIANT_SPARSE &&
+        !(v == JSIM_VARIANT_AUTO && n >= 256 && n <= 2048 && !ctx->opt.count_useful &&
+          (ctx->opt.batch_rows == 0 || ctx->opt.batch_rows % (1ull << 18) == 0)))
+        return false;
+    if (cudaSetDevice(ctx->opt.device) != cudaSuccess || !product_tc_supported(ctx->opt.device)) {
+        cudaGetLastError();
+        return false;
+    }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const u64 bytes = (sets->offsets[n] - sets->offsets[0]) * sizeof(u64);
+    return bytes < (u64)free_b / 3;
+}
 
 // Row batches of part `part` of `parts` (the split contraction of
 // jsim_all_pairs_part): the batch size mt (batch_rows, or the automatic size
@@ -271,7 +301,8 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
     if (rc) return rc;
     if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
     if (sets->mem == JSIM_MEM_HOST && sets->n > 0 && sets->offsets[sets->n] >= sets->offsets[0] &&
-        (sets->offsets[sets->n] - sets->offsets[0]) * sizeof(u64) > kHostStreamMin)
+        (sets->offsets[sets->n] - sets->offsets[0]) * sizeof(u64) > kHostStreamMin &&
+        !sparse_may_apply(ctx, sets))
         return jsim_all_pairs_streamed(ctx, sets, C, sizes, J, out_mem, kHostStreamBytes);
     return all_pairs_impl(ctx, sets, C, sizes, J, out_mem, 0, 1, false);
 }

@@ -52,6 +52,7 @@ struct Wave {
     u64 max_mt = 0;
     int variant = JSIM_VARIANT_TC;
     int word_bits = 64;
+    int tile_n = 256;       // tensor-core tile width (128 x tile_n tiles)
     cudaGraphExec_t exec = nullptr;
     u64 signature = 0;
     ~Wave()
@@ -84,7 +85,7 @@ std::vector<TcJobDesc> wave_jobs(Wave& w)
 // every collection, product, epilogue.  No host synchronisation inside; the
 // job table must already be in device memory.
 int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool dev_out, size_t first,
-                 bool run_product_only, int variant, int word_bits)
+                 bool run_product_only, int variant, int word_bits, int tile_n)
 {
     const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
     cudaStream_t st = ctx->stream;
@@ -134,7 +135,7 @@ int enqueue_wave(jsim_ctx* ctx, Wave& w, void* const* C, double* const* J, bool 
         int launches = 0;
         cudaError_t e = product_tc_jobs(jobs.data(), (int)jobs.size(), w.jobtab.p, false, ctx->opt.count_bits,
                                         ctx->sms, ctx->d_err, ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000,
-                                        st, &launches);
+                                        st, &launches, tile_n);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batched tcgen05 product");
         ctx->stats.product_launches += launches;
         ctx->stats.launches += launches;
@@ -202,12 +203,12 @@ int finish_stats(jsim_ctx* ctx, Wave& w)
 }
 
 // time the product of the wave with one variant (CUDA events), ms
-int time_product(jsim_ctx* ctx, Wave& w, int variant, int word_bits, float& ms)
+int time_product(jsim_ctx* ctx, Wave& w, int variant, int word_bits, int tile_n, float& ms)
 {
     cudaEvent_t a = take_event(ctx), b = take_event(ctx);
     if (!a || !b) return JSIM_ERR_CUDA;
     CK(cudaEventRecord(a, ctx->stream));
-    int rc = enqueue_wave(ctx, w, nullptr, nullptr, true, 0, true, variant, word_bits);
+    int rc = enqueue_wave(ctx, w, nullptr, nullptr, true, 0, true, variant, word_bits, tile_n);
     if (rc) return rc;
     CK(cudaEventRecord(b, ctx->stream));
     CK(cudaEventSynchronize(b));
@@ -217,9 +218,12 @@ int time_product(jsim_ctx* ctx, Wave& w, int variant, int word_bits, float& ms)
 
 }  // namespace
 
-// Tuning cache: shape signature -> (variant, word bits).
+// Tuning cache: shape signature -> (variant, word bits, tile width).
+struct jsim_tuned {
+    int variant, word_bits, tile_n;
+};
 struct jsim_tuning {
-    std::vector<std::pair<u64, std::pair<int, int>>> entries;
+    std::vector<std::pair<u64, jsim_tuned>> entries;
 };
 
 namespace {
@@ -336,6 +340,7 @@ extern "C" int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint
                                                cudaMemcpyDeviceToDevice, ctx->stream));
                 CK(cudaStreamSynchronize(ctx->stream));
                 ctx->stats.variant = w.variant;
+                ctx->stats.tile_n = w.variant == JSIM_VARIANT_TC ? (u64)w.tile_n : 0;
                 return finish_stats(ctx, w);
             }
         }
@@ -484,6 +489,7 @@ replan:
 
     // ---- variant: the caller's, or the tuned one for this shape ----
     int variant = ctx->opt.variant, word_bits = ctx->opt.word_bits;
+    int tile_n = ctx->opt.tile_n ? ctx->opt.tile_n : 256;
     const bool tc_ok = product_tc_supported(ctx->opt.device);
     if (variant == JSIM_VARIANT_TC && !tc_ok) return JSIM_ERR_UNSUPPORTED;
     if (variant != JSIM_VARIANT_AUTO && variant != JSIM_VARIANT_TC && variant != JSIM_VARIANT_POPC)
@@ -491,39 +497,56 @@ replan:
     jsim_tuning* tun = tuning_of(ctx);
     u64 shape = 0x77;
     for (auto& x : w.cols) shape = mix(shape, (x.n + 31) / 32 * 1000003 + (64 - __builtin_clzll(x.N | 1)));
+    shape = mix(shape, (u64)ctx->opt.tile_n);
     if (variant == JSIM_VARIANT_AUTO) {
         for (auto& e : tun->entries)
-            if (e.first == shape) { variant = e.second.first; word_bits = e.second.second; }
+            if (e.first == shape) {
+                variant = e.second.variant;
+                word_bits = e.second.word_bits;
+                tile_n = e.second.tile_n;
+            }
     }
 
     // ---- ingest all collections (and tune the product on the packed words) ----
     if (variant == JSIM_VARIANT_AUTO) {
-        int rc = enqueue_wave(ctx, w, nullptr, nullptr, true, 0, false, JSIM_VARIANT_POPC, 64);
+        int rc = enqueue_wave(ctx, w, nullptr, nullptr, true, 0, false, JSIM_VARIANT_POPC, 64, 256);
         if (rc) return rc;
-        // the first call above also ran one product; now time each candidate
-        struct Cand { int v, wb; };
-        std::vector<Cand> cands;
-        if (tc_ok) cands.push_back({JSIM_VARIANT_TC, 64});
-        cands.push_back({JSIM_VARIANT_POPC, 64});
-        cands.push_back({JSIM_VARIANT_POPC, 32});
+        // the first call above also ran one product; now time each candidate:
+        // tensor-core tiles of 128 x 256 and of 128 x 128 (collections of at
+        // most 128 samples then fill whole tiles, and diagonal tiles unpack
+        // their rows once), CUDA-core products on 64- and 32-bit words
+        std::vector<jsim_tuned> cands;
+        if (tc_ok) {
+            if (ctx->opt.tile_n != 128) cands.push_back({JSIM_VARIANT_TC, 64, 256});
+            if (ctx->opt.tile_n != 256) cands.push_back({JSIM_VARIANT_TC, 64, 128});
+        }
+        cands.push_back({JSIM_VARIANT_POPC, 64, 256});
+        cands.push_back({JSIM_VARIANT_POPC, 32, 256});
         float best = 1e30f;
         for (auto& cd : cands) {
             float ms = 0;
-            int r2 = time_product(ctx, w, cd.v, cd.wb, ms);
+            int r2 = time_product(ctx, w, cd.variant, cd.word_bits, cd.tile_n, ms);
             if (r2) return r2;
-            if (ms < best) { best = ms; variant = cd.v; word_bits = cd.wb; }
+            if (ms < best) {
+                best = ms;
+                variant = cd.variant;
+                word_bits = cd.word_bits;
+                tile_n = cd.tile_n;
+            }
         }
-        tun->entries.push_back({shape, {variant, word_bits}});
+        tun->entries.push_back({shape, {variant, word_bits, tile_n}});
     }
     w.variant = variant;
     w.word_bits = word_bits;
+    w.tile_n = tile_n;
     ctx->stats.variant = variant;
+    ctx->stats.tile_n = variant == JSIM_VARIANT_TC ? (u64)tile_n : 0;
 
     // ---- the launch sequence: captured once when inputs and outputs are on the device ----
     if (use_graph) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_wave(ctx, w, C, J, dev_out, 0, false, variant, word_bits);
+        int rc = enqueue_wave(ctx, w, C, J, dev_out, 0, false, variant, word_bits, tile_n);
         cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
@@ -534,7 +557,7 @@ replan:
         CK(cudaGraphLaunch(w.exec, ctx->stream));
     } else {
         StageTimer t(ctx, &ctx->stats.ms_product);
-        int rc = enqueue_wave(ctx, w, C, J, dev_out, 0, false, variant, word_bits);
+        int rc = enqueue_wave(ctx, w, C, J, dev_out, 0, false, variant, word_bits, tile_n);
         if (rc) return rc;
     }
 

@@ -124,8 +124,10 @@ struct TcJobDesc {
 // dev_table: device memory for njobs table entries (sizeof(TcJobDesc) each),
 // read by the kernels; with upload it is first written from `jobs`
 // (stream-ordered; not allowed while the stream is being captured).
+// tile_n: tiles of 128 x 256 (256) or 128 x 128 (128; a diagonal tile then
+// unpacks its rows once for both operands).
 cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, void* dev_table, bool upload, int count_bits, int sms,
-                            u32* err, int timeout_ms, cudaStream_t st, int* launches);
+                            u32* err, int timeout_ms, cudaStream_t st, int* launches, int tile_n = 256);
 bool product_tc_supported(int device);
 
 // ---- query.cu (serving) ---------------------------------------------------------

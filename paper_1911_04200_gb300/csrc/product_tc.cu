@@ -45,14 +45,7 @@ namespace jsim {
 
 namespace {
 
-constexpr int kProducerWarps = 12;
-constexpr int kMmaWarp = 12;
-constexpr int kEpiWarp0 = 13;
-constexpr int kWarps = 17;
-constexpr int kThreads = kWarps * 32;          // 544
 using tcs::kM;
-using tcs::kN;
-using tcs::kRows;
 using tcs::kStageBits;
 using tcs::kStageWords;
 using tcs::kMaxSegStages;
@@ -63,24 +56,40 @@ using tcs::WorkIter;
 using tcs::Slots;
 using tcs::job_tiles;
 using tcs::tc_tile;
-static_assert(kRows == kProducerWarps * 32, "one row per producer thread");
-static_assert(kEpiWarp0 % 4 == 1, "epilogue warp e reads TMEM lanes of warp rank (kEpiWarp0 + e) % 4");
 constexpr int kAtoms = kStageBits / 128;
 constexpr int kBlkBytes = 128;
 constexpr int kAtomA = kM * kBlkBytes;         // one atom column of A: 16 KiB
-constexpr int kAtomB = kN * kBlkBytes;         // one atom column of B: 32 KiB
 constexpr int kABytes = kAtoms * kAtomA;
-constexpr int kStageBytes = kAtoms * kRows * kBlkBytes;  // 96 KiB
-constexpr int kBufs = 2;
 constexpr int kAhead = 4;                      // stages of packed words held in registers
-constexpr int kSmemBytes = kBufs * kStageBytes + 1024;  // + alignment slack
-static_assert(kSmemBytes <= 232448, "fits the per-CTA shared-memory limit");
-constexpr int kTmemCols = 512;                 // two 256-column FP32 accumulators
 constexpr u32 kErrTimeout = 4u;
 
-// instruction descriptor: kind::f8f6f4, D = F32, A = B = E4M3, both K-major,
-// N = 256 (bits 17..22 hold N/8), M = 128 (bits 24..28 hold M/16)
-constexpr u32 kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((u32)(kN >> 3) << 17) | ((u32)(kM >> 4) << 24);
+// The kernel's shape for tiles of 128 x TN (TN = 256 or 128).  One producer
+// thread per unpacked row (128 + TN), one MMA warp, four epilogue warps; two
+// TMEM accumulators of TN columns.  With TN = 128 a stage is two thirds the
+// size, so three stage buffers fit.
+template <int TN>
+struct Shape {
+    static constexpr int kN = TN;
+    static constexpr int kRows = kM + TN;                  // rows unpacked per stage
+    static constexpr int kProducerWarps = kRows / 32;
+    static constexpr int kMmaWarp = kProducerWarps;
+    static constexpr int kEpiWarp0 = kProducerWarps + 1;
+    static constexpr int kWarps = kEpiWarp0 + 4;
+    static constexpr int kThreads = kWarps * 32;
+    static constexpr int kAtomB = TN * kBlkBytes;          // one atom column of B
+    static constexpr int kStageBytes = kAtoms * kRows * kBlkBytes;
+    static constexpr int kBufs = TN == 128 ? 3 : 2;
+    static constexpr int kSmemBytes = kBufs * kStageBytes + 1024;  // + alignment slack
+    static constexpr int kTmemCols = 2 * TN;               // two TN-column FP32 accumulators
+    // instruction descriptor: kind::f8f6f4, D = F32, A = B = E4M3, both
+    // K-major, N = TN (bits 17..22 hold N/8), M = 128 (bits 24..28 hold M/16)
+    static constexpr u32 kIdesc =
+        (1u << 4) | (0u << 7) | (0u << 10) | ((u32)(TN >> 3) << 17) | ((u32)(kM >> 4) << 24);
+    static_assert(kRows % 32 == 0, "one row per producer thread");
+    static_assert(kEpiWarp0 % 4 == 1, "epilogue warp e reads TMEM lanes of warp rank (kEpiWarp0 + e) % 4");
+    static_assert(kSmemBytes + 9 * 1024 <= 232448, "fits the per-CTA shared-memory limit");
+    static_assert(TN == 128 || TN == 256, "tile widths");
+};
 
 __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
 
@@ -163,10 +172,15 @@ struct TcJobs {
     int vec16;  // 16-byte loads are safe for every job
 };
 
-template <typename CT>
-__global__ void __launch_bounds__(kThreads, 1)
+template <typename CT, int TN>
+__global__ void __launch_bounds__(Shape<TN>::kThreads, 1)
 k_prod_tc(const TcJobs P, u32* err, long long budget)
 {
+    using S = Shape<TN>;
+    constexpr int kBufs = S::kBufs, kStageBytes = S::kStageBytes, kAtomB = S::kAtomB;
+    constexpr int kProducerWarps = S::kProducerWarps, kMmaWarp = S::kMmaWarp, kEpiWarp0 = S::kEpiWarp0;
+    constexpr int kTmemCols = S::kTmemCols;
+    constexpr u32 kIdesc = S::kIdesc;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) u64 full_bar[kBufs], empty_bar[kBufs], accf_bar[2], acce_bar[2], done_bar;
     __shared__ u32 tmem_slot;
@@ -181,7 +195,7 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         for (u32 j = 0; j < njobs; ++j) {
             const TcJob& J = P.job[j];
             const u64 W = J.Wdev ? *(volatile const u64*)J.Wdev : J.W;
-            const JobInfo x = tcs::job_info(J.n, W, U);
+            const JobInfo x = tcs::job_info(J.n, W, U, TN);
             U += x.tiles * x.nst;
             ji[j] = x;
         }
@@ -228,6 +242,10 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         const u32 row_off = (u32)((is_a ? 0 : kABytes) + row * kBlkBytes);
         const u32 atom_step = (u32)(is_a ? kAtomA : kAtomB);
         u64 ring[kAhead][kStageWords];
+        // per ring slot: the stage's tile is diagonal (TN = 128, rows = columns):
+        // its B operand is the A operand, which the B-side threads then neither
+        // load nor write
+        bool diag[kAhead];
         // position of the next fetch: the current segment's job, tile (first
         // row and column), stage, and stages left in it
         WorkIter fit;
@@ -236,9 +254,10 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         u64 f_key = ~0ull, f_kst = 0, f_left = 0, f_r0 = 0, f_c0 = 0, f_n = 0, f_W = 0, f_stride = 0;
         const u64* f_X = nullptr;
         // packed words of this thread's row at the next fetch position (0 past the end)
-        auto fetch = [&](u64 (&v)[kStageWords]) {
+        auto fetch = [&](u64 (&v)[kStageWords], bool& dg) {
             #pragma unroll
             for (int q = 0; q < kStageWords; ++q) v[q] = 0ull;
+            dg = false;
             if (f_left == 0) {
                 if (!fit.next(fs)) return;
                 f_kst = fs.kst;
@@ -248,12 +267,13 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                     const TcJob& J = P.job[fs.job];
                     f_X = J.X; f_n = J.n; f_stride = J.stride;
                     f_W = J.Wdev ? *(volatile const u64*)J.Wdev : J.W;
-                    tc_tile(fs.tile, ji[fs.job].TM, f_r0, f_c0);
+                    tc_tile(fs.tile, ji[fs.job].TM, f_r0, f_c0, TN);
                     f_key = key;
                 }
             }
+            dg = TN == kM && f_r0 == f_c0;
             const u64 grow = tcs::fetch_row(p, f_r0, f_c0);
-            if (grow < f_n) {
+            if (grow < f_n && !(dg && !is_a)) {
                 const u64* src = f_X + grow * f_stride;
                 #pragma unroll
                 for (int q = 0; q < kStageWords; q += 2) {
@@ -274,7 +294,7 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
             ++f_kst;
         };
         #pragma unroll
-        for (int a = 0; a < kAhead; ++a) fetch(ring[a]);
+        for (int a = 0; a < kAhead; ++a) fetch(ring[a], diag[a]);
         bool ok = true;
         for (u64 t0 = 0; t0 < T && ok; t0 += kAhead) {
             // ring slot a holds stage t0 + a; static indices keep the
@@ -290,6 +310,7 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                 }
                 #pragma unroll
                 for (int at = 0; at < kAtoms; ++at) {
+                    if (diag[a] && !is_a) break;  // the MMA reads the A rows for both operands
                     unsigned char* rowp = sm + b * kStageBytes + row_off + at * atom_step;
                     #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -310,7 +331,7 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full_bar[b]);
-                fetch(ring[a]);
+                fetch(ring[a], diag[a]);
             }
         }
     } else if (warp == kMmaWarp) {
@@ -345,12 +366,16 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                     sl.fill[sidx] = 0;
                     fresh = true;
                 }
-                const u32 dt = tmem + (u32)sidx * 256u;
+                const u32 dt = tmem + (u32)sidx * (u32)TN;
+                // a diagonal tile (TN = 128, rows = columns) multiplies its A rows by themselves
+                u64 r0, c0;
+                tc_tile(sg.tile, ji[sg.job].TM, r0, c0, TN);
+                const bool dg = TN == kM && r0 == c0;
                 for (u64 q = 0; q < len; ++q, ++t) {
                     const int b = (int)(t % kBufs);
                     if (!mbar_wait(&full_bar[b], (u32)((t / kBufs) & 1), budget, abort_v)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const u32 abase = base + b * kStageBytes, bbase = abase + kABytes;
+                    const u32 abase = base + b * kStageBytes, bbase = dg ? abase : abase + kABytes;
                     #pragma unroll
                     for (int k = 0; k < kStageBits / 32; ++k) {
                         // K step k: atom column k / 4, 32-byte slice k % 4
@@ -394,12 +419,12 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
             CT* C = (CT*)J.C;
             const u64 n = J.n, ldc = J.ldc;
             u64 r0, c0;
-            tc_tile(key & ((1ull << 40) - 1), ji[jb].TM, r0, c0);
+            tc_tile(key & ((1ull << 40) - 1), ji[jb].TM, r0, c0, TN);
             const u64 i = r0 + (u64)(e * 32 + lane);
             #pragma unroll 1
-            for (int cb = 0; cb < kN / 32; ++cb) {
+            for (int cb = 0; cb < TN / 32; ++cb) {
                 u32 r[32];
-                tmem_ld32(tmem + ((u32)(e * 32) << 16) + (u32)sidx * 256u + (u32)(cb * 32), r);
+                tmem_ld32(tmem + ((u32)(e * 32) << 16) + (u32)sidx * (u32)TN + (u32)(cb * 32), r);
                 if (i < n) {
                     #pragma unroll
                     for (int x = 0; x < 32; ++x) {
@@ -468,20 +493,22 @@ long long wait_budget(int timeout_ms)
     return (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * (long long)timeout_ms / 1000LL;
 }
 
-template <typename CT>
+template <typename CT, int TN>
 cudaError_t launch(const TcJobs& P, int sms, u32* err, int timeout_ms, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_prod_tc<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    using S = Shape<TN>;
+    cudaError_t e = cudaFuncSetAttribute(k_prod_tc<CT, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes);
     if (e != cudaSuccess) return e;
-    k_prod_tc<CT><<<(unsigned)sms, kThreads, kSmemBytes, st>>>(P, err, wait_budget(timeout_ms));
+    k_prod_tc<CT, TN><<<(unsigned)sms, S::kThreads, S::kSmemBytes, st>>>(P, err, wait_budget(timeout_ms));
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, void* dev_table, bool upload, int count_bits, int sms,
-                            u32* err, int timeout_ms, cudaStream_t st, int* launches)
+                            u32* err, int timeout_ms, cudaStream_t st, int* launches, int tile_n)
 {
+    if (tile_n != 128 && tile_n != 256) return cudaErrorInvalidValue;
     // the table of every job, copied once to device memory (dev_table holds
     // njobs entries of TcJob); one launch per group of kMaxJobs jobs
     static_assert(sizeof(TcJob) == sizeof(TcJobDesc), "table entry layout");
@@ -503,7 +530,12 @@ cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, void* dev_table, b
         P.job = (const TcJob*)dev_table + j0;
         P.njobs = (u32)std::min(kMaxJobs, njobs - j0);
         P.vec16 = vec16;
-        e = count_bits == 64 ? launch<u64>(P, sms, err, timeout_ms, st) : launch<u32>(P, sms, err, timeout_ms, st);
+        if (tile_n == 128)
+            e = count_bits == 64 ? launch<u64, 128>(P, sms, err, timeout_ms, st)
+                                 : launch<u32, 128>(P, sms, err, timeout_ms, st);
+        else
+            e = count_bits == 64 ? launch<u64, 256>(P, sms, err, timeout_ms, st)
+                                 : launch<u32, 256>(P, sms, err, timeout_ms, st);
         if (e != cudaSuccess) return e;
         if (launches) *launches += 1;
     }
@@ -554,18 +586,22 @@ struct CheckMsg {
 
 extern "C" JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n, const uint64_t* W,
                                                const uint64_t* stride, const uint64_t* rows, uint32_t grid,
-                                               char* msg, size_t cap)
+                                               uint32_t tile_n, char* msg, size_t cap)
 {
     using namespace jsim;
     using namespace jsim::tcs;
     CheckMsg m{msg, cap};
     if (msg && cap) msg[0] = 0;
-    if (njobs == 0 || njobs > (uint32_t)kMaxJobs || grid == 0 || !n || !W || !stride || !rows) return JSIM_ERR_ARG;
+    if (njobs == 0 || njobs > (uint32_t)kMaxJobs || grid == 0 || !n || !W || !stride || !rows ||
+        (tile_n != 128 && tile_n != 256))
+        return JSIM_ERR_ARG;
+    const u64 kn = tile_n;
+    const int kRows = kM + (int)kn;
     std::vector<JobInfo> ji(njobs);
     u64 U = 0;
     for (u32 j = 0; j < njobs; ++j) {
         if (rows[j] < n[j] || (W[j] > stride[j] && n[j] > 0)) return m.fail(1, "job %llu: rows %llu or W beyond stride %llu", j, rows[j], stride[j]);
-        ji[j] = job_info(n[j], W[j], U);
+        ji[j] = job_info(n[j], W[j], U, kn);
         U += ji[j].tiles * ji[j].nst;
     }
     // every (job, tile, stage) unit must be taken exactly once
@@ -577,9 +613,9 @@ extern "C" JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n
         std::vector<unsigned char> cov(N * N, 0);
         for (u64 t = 0; t < ji[jb].tiles; ++t) {
             u64 r0, c0;
-            tc_tile(t, ji[jb].TM, r0, c0);
+            tc_tile(t, ji[jb].TM, r0, c0, kn);
             for (u64 i = r0; i < r0 + kM && i < N; ++i)
-                for (u64 j = std::max(i, c0); j < c0 + kN && j < N; ++j) {
+                for (u64 j = std::max(i, c0); j < c0 + kn && j < N; ++j) {
                     if (cov[i * N + j]) return m.fail(2, "job %llu: pair (%llu, %llu) in two tiles", jb, i, j);
                     cov[i * N + j] = 1;
                 }
@@ -606,7 +642,7 @@ extern "C" JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n
                     }
                     if (t >= T) return m.fail(5, "cta %llu: fetch %llu beyond its %llu stages", c, t, T);
                     kst = fs.kst; left = fs.len; job = fs.job;
-                    tc_tile(fs.tile, ji[job].TM, r0, c0);
+                    tc_tile(fs.tile, ji[job].TM, r0, c0, kn);
                 }
                 for (int p = 0; p < kRows; ++p) {
                     const u64 grow = fetch_row(p, r0, c0);
@@ -637,13 +673,13 @@ extern "C" JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n
             auto drain = [&](int sidx, u64 key) -> int {
                 const u32 jb = (u32)(key >> 40);
                 u64 r0, c0;
-                tc_tile(key & ((1ull << 40) - 1), ji[jb].TM, r0, c0);
+                tc_tile(key & ((1ull << 40) - 1), ji[jb].TM, r0, c0, kn);
                 for (u64 e = 0; e < 4; ++e)
                     for (u64 lane = 0; lane < 32; ++lane) {
                         const u64 i = r0 + e * 32 + lane;
-                        for (u64 col = 0; col < (u64)kN; ++col) {
-                            const u64 tcol = (u64)sidx * 256 + col;
-                            if (tcol >= 512) return m.fail(8, "cta %llu: TMEM column %llu of slot %llu", c, tcol, sidx);
+                        for (u64 col = 0; col < kn; ++col) {
+                            const u64 tcol = (u64)sidx * kn + col;
+                            if (tcol >= 2 * kn) return m.fail(8, "cta %llu: TMEM column %llu of slot %llu", c, tcol, sidx);
                             const u64 j = c0 + col;
                             if (i < n[jb] && j < n[jb] && i <= j && i * n[jb] + j >= n[jb] * n[jb])
                                 return m.fail(9, "cta %llu: C write (%llu, %llu) outside", c, i, j);

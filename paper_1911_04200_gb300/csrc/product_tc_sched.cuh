@@ -10,8 +10,9 @@ namespace jsim {
 namespace tcs {
 
 constexpr int kM = 128;                        // A-side rows per tile
-constexpr int kN = 256;                        // B-side rows per tile
-constexpr int kRows = kM + kN;                 // rows unpacked per stage (one per producer thread)
+// B-side rows per tile: 256 (tiles of 128 x 256) or 128 (tiles of 128 x 128,
+// whose diagonal tiles unpack their rows once for both operands); the kernel
+// and these functions take it as a parameter `kn`.
 constexpr int kStageBits = 256;                // bit-rows per stage: two 128-byte swizzle atom columns
 constexpr int kStageWords = kStageBits / 64;
 // a segment accumulates at most 2^22 bit-rows (exact FP32 counts)
@@ -20,44 +21,44 @@ constexpr int kMaxJobs = 256;
 
 __host__ __device__ __forceinline__ u64 umin(u64 a, u64 b) { return a < b ? a : b; }
 
-// 128 x 256 tiles touching the upper triangle of an n x n result: column
-// tile j (columns [256 j, +256)) pairs with row tiles ti <= 2 j + 1
-__host__ __device__ __forceinline__ u64 job_tiles(u64 n, u64& TM)
+// 128 x kn tiles touching the upper triangle of an n x n result: column
+// tile j (columns [kn j, +kn)) pairs with row tiles ti < (j + 1) kn / 128
+__host__ __device__ __forceinline__ u64 job_tiles(u64 n, u64& TM, u64 kn)
 {
     TM = (n + kM - 1) / kM;
-    const u64 TN = (n + kN - 1) / kN;
+    const u64 TN = (n + kn - 1) / kn;
     u64 t = 0;
-    for (u64 j = 0; j < TN; ++j) t += umin(TM, 2 * j + 2);
+    for (u64 j = 0; j < TN; ++j) t += umin(TM, (j + 1) * (kn / kM));
     return t;
 }
 
 // tile t -> first row r0 and column c0 (tiles column-major, as counted above)
-__host__ __device__ __forceinline__ void tc_tile(u64 t, u64 TM, u64& r0, u64& c0)
+__host__ __device__ __forceinline__ void tc_tile(u64 t, u64 TM, u64& r0, u64& c0, u64 kn)
 {
     u64 j = 0;
     for (;;) {
-        u64 cnt = umin(TM, 2 * j + 2);
+        u64 cnt = umin(TM, (j + 1) * (kn / kM));
         if (t < cnt) break;
         t -= cnt;
         ++j;
     }
     r0 = t * kM;
-    c0 = j * kN;
+    c0 = j * kn;
 }
 
 // Per-job quantities every CTA derives in its prologue.
 struct JobInfo {
     u64 nst;    // stages of every tile of the job (ceil(W / kStageWords))
-    u64 tiles;  // 128 x 256 tiles touching the upper triangle
+    u64 tiles;  // 128 x kn tiles touching the upper triangle
     u64 TM;     // 128-row tile count
     u64 U0;     // first unit of the job in the launch-wide unit order
 };
 
-__host__ __device__ __forceinline__ JobInfo job_info(u64 n, u64 W, u64 U0)
+__host__ __device__ __forceinline__ JobInfo job_info(u64 n, u64 W, u64 U0, u64 kn)
 {
     JobInfo x;
     x.nst = (W + kStageWords - 1) / kStageWords;
-    x.tiles = job_tiles(n, x.TM);
+    x.tiles = job_tiles(n, x.TM, kn);
     if (x.nst == 0) x.tiles = 0;
     x.U0 = U0;
     return x;
@@ -150,8 +151,8 @@ struct Slots {
     }
 };
 
-// Row of the packed matrix that unpack thread p (0 .. kRows-1) reads for a
-// tile at (r0, c0): threads 0..127 the A side (rows r0 + p), the others the
+// Row of the packed matrix that unpack thread p (0 .. 128 + kn - 1) reads for
+// a tile at (r0, c0): threads 0..127 the A side (rows r0 + p), the others the
 // B side (rows c0 + p - 128).
 __host__ __device__ __forceinline__ u64 fetch_row(int p, u64 r0, u64 c0)
 {

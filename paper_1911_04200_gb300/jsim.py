@@ -56,7 +56,7 @@ def partition_batches(minid: int, maxid: int, batch_rows: int, parts: int):
     return out
 
 
-def check_tc_schedule(jobs, grid: int):
+def check_tc_schedule(jobs, grid: int, tile_n: int = 256):
     """Host-side check of the job-table tensor-core product's schedule for
     jobs [(n, W, stride, rows), ...] over `grid` CTAs: (code, message), code 0
     when every check passes (jsim_check_tc_schedule)."""
@@ -64,7 +64,7 @@ def check_tc_schedule(jobs, grid: int):
     k = len(jobs)
     arr = [(ctypes.c_uint64 * k)(*[int(j[f]) for j in jobs]) for f in range(4)]
     buf = ctypes.create_string_buffer(256)
-    rc = lib.jsim_check_tc_schedule(k, arr[0], arr[1], arr[2], arr[3], grid, buf, 256)
+    rc = lib.jsim_check_tc_schedule(k, arr[0], arr[1], arr[2], arr[3], grid, tile_n, buf, 256)
     return rc, buf.value.decode()
 
 
@@ -78,7 +78,8 @@ class Options(ctypes.Structure):
                 ("count_bits", ctypes.c_int), ("id_bits", ctypes.c_int), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("timeout_ms", ctypes.c_int), ("profile", ctypes.c_int),
-                ("filter_min", ctypes.c_int), ("distance", ctypes.c_int), ("count_useful", ctypes.c_int)]
+                ("filter_min", ctypes.c_int), ("distance", ctypes.c_int), ("count_useful", ctypes.c_int),
+                ("tile_n", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -88,7 +89,8 @@ class Stats(ctypes.Structure):
                 ("ms_validate", ctypes.c_double), ("ms_filter", ctypes.c_double), ("ms_scan", ctypes.c_double),
                 ("ms_pack", ctypes.c_double), ("ms_product", ctypes.c_double), ("ms_epilogue", ctypes.c_double),
                 ("ms_d2h", ctypes.c_double), ("bitops_dense", ctypes.c_double),
-                ("bitops_useful", ctypes.c_double), ("bitops_done", ctypes.c_double), ("pack_bytes", ctypes.c_uint64),
+                ("bitops_useful", ctypes.c_double), ("bitops_done", ctypes.c_double), ("tile_n", ctypes.c_uint64),
+                ("pack_bytes", ctypes.c_uint64),
                 ("h2d_copies", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64)]
 
@@ -122,8 +124,8 @@ SIGNATURES = {
                                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "jsim_check_tc_schedule": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
                                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
-                                              ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint32, ctypes.c_char_p,
-                                              ctypes.c_size_t]),
+                                              ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint32, ctypes.c_uint32,
+                                              ctypes.c_char_p, ctypes.c_size_t]),
     "jsim_default_options": (None, [ctypes.POINTER(Options)]),
     "jsim_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Options)]),
     "jsim_destroy": (None, [ctypes.c_void_p]),
@@ -220,7 +222,7 @@ class Context:
     def __init__(self, device: int = 0, variant: str | int = "auto", batch_rows: int = 0, word_bits: int = 64,
                  count_bits: int = 32, id_bits: int = 64, profile: bool = False, stream=None,
                  use_torch_allocator: bool = True, timeout_ms: int = 2000, filter_min: int = 1,
-                 distance: bool = False, count_useful: bool = False, allocator=None):
+                 distance: bool = False, count_useful: bool = False, allocator=None, tile_n: int = 0):
         """``allocator`` (optional) replaces PyTorch's caching allocator as the
         library's device allocator: an object with ``alloc(nbytes, stream) ->
         int`` (a device pointer, or 0 when it cannot serve the request: the
@@ -244,6 +246,7 @@ class Context:
         o.filter_min = filter_min
         o.distance = 1 if distance else 0
         o.count_useful = 1 if count_useful else 0
+        o.tile_n = tile_n
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         self._keep = []
         if allocator is not None:

@@ -43,10 +43,16 @@ def refs(cols):
     return [oracle.all_pairs(o, i) for o, i in cols]
 
 
-@pytest.mark.parametrize("variant", ["auto", "tc", "popc"])
-def test_batched_host_io(gpu, cols, refs, variant):
-    with jsim.Context(variant=variant) as ctx:
+@pytest.mark.parametrize("variant,tile_n", [("auto", 0), ("tc", 256), ("tc", 128), ("auto", 128), ("popc", 0)])
+def test_batched_host_io(gpu, cols, refs, variant, tile_n):
+    """Every variant and both tensor tile shapes (128 x 256, and 128 x 128
+    whose diagonal tiles unpack their rows once for both operands) on
+    collections of 1 to 300 samples (one to three tiles, ragged)."""
+    with jsim.Context(variant=variant, tile_n=tile_n) as ctx:
         outs = ctx.all_pairs_batched(cols)
+        st = ctx.stats()
+    if variant == "tc":
+        assert st["tile_n"] == tile_n
     for res, ref in zip(outs, refs):
         assert_same(res, ref)
 

@@ -16,29 +16,49 @@ def stride_of(W):
     return max(64, -(-W // 64) * 64)
 
 
+@pytest.mark.parametrize("tile_n", [256, 128])
 @pytest.mark.parametrize("n", [1, 2, 127, 128, 129, 255, 256, 257, 300, 1024])
 @pytest.mark.parametrize("W", [1, 2, 3, 4, 5, 7, 1023])
 @pytest.mark.parametrize("grid", [1, 7, 148, 152])
-def test_single_collection_exact_rows(n, W, grid):
+def test_single_collection_exact_rows(n, W, grid, tile_n):
     """One collection whose matrix has exactly n rows (as jsim_product
-    allows): the shapes of the plain path."""
-    rc, msg = jsim.check_tc_schedule([(n, W, stride_of(W), n)], grid)
+    allows): the shapes of the plain path, for both tile widths."""
+    rc, msg = jsim.check_tc_schedule([(n, W, stride_of(W), n)], grid, tile_n)
     assert rc == 0, msg
 
 
-def test_plain_path_shapes():
+@pytest.mark.parametrize("tile_n", [256, 128])
+def test_plain_path_shapes(tile_n):
     """The shapes of the default workload's batches (1024 samples, a few
     thousand to 3.5e5 words per batch) and odd row strides."""
     for n, W, stride in [(1024, 5000, 5120), (1024, 351826, 352256), (1000, 65536, 66560), (4096, 2700, 2752)]:
-        rc, msg = jsim.check_tc_schedule([(n, W, stride, n)], 152)
+        rc, msg = jsim.check_tc_schedule([(n, W, stride, n)], 152, tile_n)
         assert rc == 0, msg
 
 
-def test_exact_count_cap_splits_segments():
+def test_block_sparse_tile_jobs():
+    """The block-sparse path's per-tile products: up to 16 jobs of one
+    diagonal 128 x 128 tile each (the last one ragged), deep word counts,
+    rows taken from one shared matrix."""
+    rng = np.random.default_rng(1)
+    for trial in range(12):
+        T = int(rng.integers(1, 17))
+        jobs = []
+        for t in range(T):
+            W = int(rng.integers(1, 700000))
+            m = 128 if t < T - 1 else int(rng.integers(1, 129))
+            jobs.append((m, W, -(-W // 1024) * 1024 + 1024, m))
+        for grid in (152, 37):
+            rc, msg = jsim.check_tc_schedule(jobs, grid, 128)
+            assert rc == 0, msg
+
+
+@pytest.mark.parametrize("tile_n", [256, 128])
+def test_exact_count_cap_splits_segments(tile_n):
     """Tiles deeper than the 2^22 bit-row cap (16384 stages): segments are cut
     and accumulators flushed before the cap, on one CTA and on many."""
     for grid in (1, 2, 152):
-        rc, msg = jsim.check_tc_schedule([(200, 70001, 70016, 200)], grid)
+        rc, msg = jsim.check_tc_schedule([(200, 70001, 70016, 200)], grid, tile_n)
         assert rc == 0, msg
 
 
@@ -56,8 +76,9 @@ def test_many_collections_like_the_batched_recipe():
         jobs.append((n, W, stride, rows))
     jobs.append((0, 0, 64, 0))
     for grid in (152, 37, 1):
-        rc, msg = jsim.check_tc_schedule(jobs, grid)
-        assert rc == 0, msg
+        for tile_n in (256, 128):
+            rc, msg = jsim.check_tc_schedule(jobs, grid, tile_n)
+            assert rc == 0, msg
 
 
 def test_check_catches_a_matrix_too_small():
