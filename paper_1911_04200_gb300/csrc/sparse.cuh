@@ -9,7 +9,8 @@
 // empty.  This path arranges that:
 //
 //  1. Sample order.  A sketch - the product of a small range of the lowest
-//     values (about 512 per sample) - gives every pair's similarity J; the
+//     values (about 512 per sample; 2048 to 32768 per sample gave the same
+//     order quality on 1024 clade samples) - gives every pair's similarity J; the
 //     samples are ordered by a greedy chain (the next sample is the one most
 //     similar to any sample already in the current tile of 128), so that
 //     samples sharing many values land in the same tile.
@@ -56,9 +57,9 @@ constexpr u64 kTileBitmapBytes = 64ull << 20;  // all tiles' filter bitmaps of a
 // where all tiles' bitmaps fit in kTileBitmapBytes (L2), 68 ms per call at
 // 2^26 (one filter) and 70 ms at 2^25 (two-or-more filter).
 constexpr double kDenseBitopsPerMs = 1.1e12;
-constexpr double kSparseBitopsPerMs = 0.65e12;
+constexpr double kSparseBitopsPerMs = 0.75e12;
 constexpr double kIngestDenseMs[2] = {2.8e-8, 2.5e-8};
-constexpr double kIngestSparseMs[2] = {3.6e-8, 4.2e-8};
+constexpr double kIngestSparseMs[2] = {3.2e-8, 3.9e-8};
 
 // Row classes from the tiles' bitmaps: class 0 = rows of two or more tiles,
 // class 1 + t = rows of tile t alone (with the two-or-more filter: rows tile
