@@ -82,7 +82,9 @@ def parse():
     ap.add_argument("--pad", type=int, default=0, help="product: words of padding after every row")
     ap.add_argument("--density", type=float, default=0.25, help="product: bit density of the random words")
     ap.add_argument("--calls", type=int, default=3)
-    ap.add_argument("--median", type=float, default=2e4, help="serve-one: set-size median of the reference")
+    ap.add_argument("--median", type=float, default=None,
+                    help="serve-one: set-size median of the reference (default 2e4); clade1024: a smaller "
+                         "set-size median than the recipe's 1e6, for profiler captures")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -138,7 +140,7 @@ def aggregate_over_ranks(ms, work, device=None):
     return float(t[0]), float(w[0])
 
 
-def make_workload(name, rank, alloc=None):
+def make_workload(name, rank, alloc=None, median=None):
     from paper_1911_04200_gb300 import synth
     if name == "ancestral64":
         off, ids = synth.ancestral64(seed=synth.SEED_BASE + 1 + 1000 * rank, alloc=alloc)
@@ -150,9 +152,10 @@ def make_workload(name, rank, alloc=None):
                            "(the paper's synthetic strong-scaling matrix)",
                "n": 10_000, "id_bits": 25}
     else:
-        off, ids = synth.clade1024(seed=synth.SEED_BASE + 2 + 1000 * rank, alloc=alloc)
-        cfg = {"workload": "clade1024: n=1024, values in [0,2^32), log-normal sizes median 1e6 "
-                           "(1e5-1e7), 32 clades, 30% core, 0-40% substitution",
+        m = median or 1e6
+        off, ids = synth.clade1024(seed=synth.SEED_BASE + 2 + 1000 * rank, alloc=alloc, median=m)
+        cfg = {"workload": "clade1024: n=1024, values in [0,2^32), log-normal sizes median %.0e "
+                           "(%.0e-%.0e), 32 clades, 30%% core, 0-40%% substitution" % (m, m / 10, m * 10),
                "n": 1024, "id_bits": 32}
     return off, ids, cfg
 
@@ -816,7 +819,7 @@ def run_jsim(args):
     def pinned(count):
         return torch.empty(count, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
 
-    off, ids, cfg = make_workload(args.workload, rank, alloc=pinned)
+    off, ids, cfg = make_workload(args.workload, rank, alloc=pinned, median=args.median)
     n = cfg["n"]
     N = int(off[-1])
     d_off = torch.from_numpy(off.view(np.int64)).to(dev)
@@ -869,7 +872,8 @@ def run_jsim(args):
         hC = torch.empty((n, n), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
         hS = torch.empty(n, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
         hJ = torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy()
-        ctx.all_pairs(off, ids, out=(hC, hS, hJ))
+        for _ in range(max(1, args.warmup)):
+            ctx.all_pairs(off, ids, out=(hC, hS, hJ))
         barrier()
         t0 = time.perf_counter()
         bo = 0.0
@@ -1075,8 +1079,9 @@ def run_serve_one(args):
     time (one device batch each, nothing overlapping), so every query kernel
     runs alone: the case the query kernel is captured on."""
     from paper_1911_04200_gb300 import jsim, synth
-    roff, rids = synth.serving_reference(median=args.median)
-    qoff, qids = synth.serving_queries(0, 64, median=args.median)
+    median = args.median or 2e4
+    roff, rids = synth.serving_reference(median=median)
+    qoff, qids = synth.serving_queries(0, 64, median=median)
     ctx = jsim.Context(id_bits=32)
     ix = jsim.Index(ctx, roff, rids, max_batch_samples=64, max_batch_values=int(qoff[-1]), slots=1)
     dt = 0.0
@@ -1086,7 +1091,7 @@ def run_serve_one(args):
         dt = time.perf_counter() - t0
     st = ix.stats()
     b = max(1, st["batches"])
-    print(json.dumps({"workload": "serve-one", "median": args.median, "index_rows": ix.rows,
+    print(json.dumps({"workload": "serve-one", "median": median, "index_rows": ix.rows,
                       "index_bytes": ix.rows * 2048 // 8, "batches": st["batches"],
                       "rows_read_per_batch": st["rows_read"] / b, "qrows_ms_per_batch": st["ms_product"] / b,
                       "index_row_gbs": st["index_bytes_read"] / (st["ms_product"] * 1e-3) / 1e9
