@@ -48,8 +48,9 @@ struct Plan {
 };
 
 // ---- ingest.cu -------------------------------------------------------------
+// perm (optional): entry i of the plan describes sample perm[i]
 cudaError_t launch_plan(const u64* offsets, const u64* ids, u64 n, u64 lo, u64 hi, bool full,
-                        Plan plan, cudaStream_t st);
+                        Plan plan, cudaStream_t st, const u32* perm = nullptr);
 // err_stride 0: one error word for all samples; 1: err[i] per sample
 cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan, u64 max_chunks,
                             int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, int sms,

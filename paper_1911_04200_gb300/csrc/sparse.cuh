@@ -48,18 +48,20 @@ constexpr u64 kTile = 128;                // samples per tile: the rows of a one
 constexpr u64 kMaxTiles = 16;             // n <= 2048
 constexpr u64 kSketchPerSample = 512;     // values per sample in the sketch range, on average
 constexpr u64 kMinClassRows = 1ull << 18; // batch width granule: one scan block of every class
-constexpr u64 kTileBitmapBytes = 64ull << 20;  // all tiles' filter bitmaps of a batch together
+constexpr u64 kTileBitmapBytes = 128ull << 20;  // all tiles' filter bitmaps of a batch together
 // Rates measured on GB300 (1024 clade samples, 1.3e9 values; both filters)
 // that the automatic choice weighs: dense SM-pair product and block-sparse
 // products in bit-operations per ms; ingest (validation, filter, scan, pack)
 // per value in ms, dense and block-sparse, one filter and two-or-more.
-// Batch widths swept at 2^25..2^28 rows: the block-sparse ingest is fastest
-// where all tiles' bitmaps fit in kTileBitmapBytes (L2), 68 ms per call at
-// 2^26 (one filter) and 70 ms at 2^25 (two-or-more filter).
+// Batch widths swept at 2^25..2^28 rows (with the samples planned in tile
+// order, so only one or two tiles' structures are in use at a time): 62.8 /
+// 58.4 / 61.4 ms per call at 2^26 / 2^27 / 2^28 rows with one filter, 69.6 /
+// 61.9 / 62.3 ms at 2^25 / 2^26 / 2^27 with the two-or-more filter - the
+// widths where all tiles' bitmaps take kTileBitmapBytes.
 constexpr double kDenseBitopsPerMs = 1.1e12;
 constexpr double kSparseBitopsPerMs = 0.75e12;
 constexpr double kIngestDenseMs[2] = {2.8e-8, 2.5e-8};
-constexpr double kIngestSparseMs[2] = {3.2e-8, 3.9e-8};
+constexpr double kIngestSparseMs[2] = {2.8e-8, 3.4e-8};
 
 // Row classes from the tiles' bitmaps: class 0 = rows of two or more tiles,
 // class 1 + t = rows of tile t alone (with the two-or-more filter: rows tile
@@ -213,7 +215,7 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
     // kSketchPerSample per sample ----
     std::vector<u32> order(n), pos(n);
     for (u64 i = 0; i < n; ++i) order[i] = (u32)i;
-    DevBuf d_pos, d_tile, d_cls_of, jobtab, B, B2, cls, dir, bsum, boff, Rd, Wc, kbase, plan_buf;
+    DevBuf d_pos, d_order, d_tile, d_cls_of, d_rowk, jobtab, B, B2, cls, dir, bsum, boff, Rd, Wc, kbase, plan_buf;
     const u64 nw_max = mt / 64;
     ALLOC(B, T * nw_max * sizeof(u64));
     if (twice) ALLOC(B2, T * nw_max * sizeof(u64));
@@ -226,6 +228,8 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
     ALLOC(Wc, (T + 1) * sizeof(u64));
     ALLOC(kbase, (T + 1) * sizeof(u64));
     ALLOC(d_pos, n * sizeof(u32));
+    ALLOC(d_order, n * sizeof(u32));
+    ALLOC(d_rowk, n * sizeof(u32));
     ALLOC(d_tile, n * sizeof(u32));
     ALLOC(d_cls_of, n * sizeof(u32));
     ALLOC(jobtab, kMaxTiles * sizeof(TcJobDesc));
@@ -241,7 +245,10 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
         const u64 hi = lo + width;  // 0 on wrap-around: unbounded
         {
             StageTimer t(ctx, &ctx->stats.ms_filter);
-            CK(launch_plan(st.d_off, st.d_ids, n, lo, hi, false, plan, cs));
+            // the plan lists the samples in their order (entry k: the sample
+            // at position k), so the chunks in flight belong to one or two
+            // tiles and their bitmaps and directories stay in L2
+            CK(launch_plan(st.d_off, st.d_ids, n, lo, hi, false, plan, cs, d_order.as<u32>()));
             CK(cudaMemsetAsync(B.p, 0, T * nw * sizeof(u64), cs));
             if (twice) CK(cudaMemsetAsync(B2.p, 0, T * nw * sizeof(u64), cs));
             CK(launch_filter_tiles(st.d_ids, n, plan, st.max_chunks, lo, width, B.as<u32>(),
@@ -302,14 +309,18 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
             order = sample_order(hc, n);
         }
         for (u64 k = 0; k < n; ++k) pos[order[k]] = (u32)k;
-        std::vector<u32> tile(n), cls_of(n);
-        for (u64 i = 0; i < n; ++i) {
-            tile[i] = pos[i] / (u32)kTile;
-            cls_of[i] = 1 + tile[i];
+        // per plan entry k (the sample at position k): its tile, class and row
+        std::vector<u32> tile(n), cls_of(n), rowk(n);
+        for (u64 k = 0; k < n; ++k) {
+            tile[k] = (u32)(k / kTile);
+            cls_of[k] = 1 + tile[k];
+            rowk[k] = (u32)k;
         }
         CK(cudaMemcpyAsync(d_pos.p, pos.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(d_order.p, order.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
         CK(cudaMemcpyAsync(d_tile.p, tile.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
         CK(cudaMemcpyAsync(d_cls_of.p, cls_of.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(d_rowk.p, rowk.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
         CK(cudaStreamSynchronize(cs));  // the host vectors are released at return
 
         if (may_decline && R_s) {
@@ -459,7 +470,7 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
                         CK(cudaGetLastError());
                     }
                     CK(launch_pack_classes(st.d_ids, n, plan, st.max_chunks, lo, mt, cls.as<u64>(), dir.as<u32>(),
-                                           boff.as<u64>(), nw, kbase.as<u64>(), d_cls_of.as<u32>(), d_pos.as<u32>(),
+                                           boff.as<u64>(), nw, kbase.as<u64>(), d_cls_of.as<u32>(), d_rowk.as<u32>(),
                                            W[0] ? XM.as<u64>() : nullptr, stride_m,
                                            Wmax_s ? XS.as<u64>() : nullptr, stride_s, ctx->sms, cs));
                     ctx->stats.launches += 3;
