@@ -369,9 +369,12 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
     ALLOC(Cacc, n * n * cb);
     CK(cudaMemsetAsync(Cacc.p, 0, n * n * cb, cs));
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), cs));
+    // a fixed share of the device (not of what is free now, which moves with
+    // other allocators' caches: sizes that change from call to call made
+    // every fourth call reallocate and take twice as long)
     size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 8ull << 30; }
-    const u64 budget = std::min<u64>(12ull << 30, (u64)free_b / 4);  // XM a third, XS two thirds
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); total_b = 64ull << 30; }
+    const u64 budget = std::min<u64>(12ull << 30, (u64)total_b / 16);  // XM a third, XS two thirds
     u64 capM = std::max<u64>(1ull << 12, budget / 3 / (n_pad * 8) / 64 * 64);
     u64 capS = std::max<u64>(1ull << 12, budget * 2 / 3 / (n_pad * 8) / 64 * 64);
     u64 stride_m = 0, stride_s = 0;
