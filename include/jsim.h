@@ -370,7 +370,9 @@ JSIM_API int jsim_product(jsim_ctx* ctx, const uint64_t* words, uint64_t n, uint
  *
  * The first call on a device looks up the array's device address (once per
  * device, with the context's device current); make that first call before
- * any stream capture.  All calls on a device share the array and the call
+ * any stream capture.  The address is kept for the life of the process: a
+ * device reset (cudaDeviceReset, or anything else that destroys the
+ * device's primary context) invalidates it, and no call may follow one.  All calls on a device share the array and the call
  * clears what it needs before use, so calls that overlap on the GPU (two
  * streams, two threads, two contexts on one device) race: serialize them.
  */

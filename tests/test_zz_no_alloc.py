@@ -55,11 +55,33 @@ def test_noalloc_matches_product_twice(gpu, n, W, density, count_bits, variant):
         np.testing.assert_array_equal(to_np(C), ref)
 
 
-def test_noalloc_rejects_sizes_beyond_its_scratch(gpu):
+@pytest.mark.parametrize("n,count_bits", [(1024, 32), (724, 64)])
+def test_noalloc_largest_sizes_its_scratch_holds(gpu, n, count_bits):
+    # n*n counts fill the 4 MiB scratch: 1024^2 x 4 B, 724^2 x 8 B
     import torch
-    with jsim.Context(count_bits=64) as ctx:
-        Xd = torch.zeros((725, 4), dtype=torch.int64, device="cuda")
-        C = torch.empty((725, 725), dtype=torch.uint64, device="cuda")
+    rng = np.random.default_rng(n)
+    W = 96
+    X = rng.integers(0, 2**63, size=(n, W), dtype=np.int64)
+    X[:, ::3] = 0
+    Xd = torch.from_numpy(X).cuda()
+    cdt = torch.uint64 if count_bits == 64 else torch.uint32
+    with jsim.Context(count_bits=count_bits) as ctx:
+        ref = to_np(ctx.product(Xd, n, W, W))
+        C = torch.empty((n, n), dtype=cdt, device="cuda")
+        ctx.product_noalloc(Xd, n, W, W, C)
+        torch.cuda.synchronize()
+    np.testing.assert_array_equal(to_np(C), ref)
+
+
+@pytest.mark.parametrize("n,count_bits", [(725, 64), (1025, 32)])
+def test_noalloc_rejects_sizes_beyond_its_scratch(gpu, n, count_bits):
+    import torch
+    cdt = torch.uint64 if count_bits == 64 else torch.uint32
+    with jsim.Context(count_bits=count_bits) as ctx:
+        Xd = torch.zeros((n, 4), dtype=torch.int64, device="cuda")
+        C = torch.full((n, n), 3, dtype=cdt, device="cuda")
         with pytest.raises(jsim.JsimError) as e:
-            ctx.product_noalloc(Xd, 725, 4, 4, C)
+            ctx.product_noalloc(Xd, n, 4, 4, C)
         assert e.value.name == "JSIM_ERR_ARG"
+        torch.cuda.synchronize()
+        assert bool((C == 3).all())
