@@ -891,15 +891,20 @@ def run_jsim(args):
                "d2h_bytes_per_step": int(n * n * 4 + n * 8 + n * n * 8), "ms_per_step": e2e_ms,
                "exposed_ms_per_step": round(e2e_ms - ms_max / args.steps, 2),
                "h2d_copies_per_step": int(se["h2d_copies"]),
+               "h2d_pieces_per_step": int(se["h2d_pieces"]),
                "call_ms": [round(x, 1) for x in calls],
                "stage_ms_last_call": {k: round(se[k], 2) for k in ("ms_total", "ms_h2d", "ms_validate", "ms_filter",
                                                                    "ms_scan", "ms_pack", "ms_product", "ms_d2h")},
-               "h2d_copy_stream_busy_ms": round(se["ms_h2d"], 2),
+               "h2d_copy_busy_ms": round(se["ms_h2d"], 2),
                "h2d_gbs_while_overlapped": round(se["h2d_bytes"] / (se["ms_h2d"] * 1e-3) / 1e9, 1)
                if se["ms_h2d"] else None,
                "h2d_gbs_one_1gib_copy": one_copy_gbs(ids, dev),
                "host_input_memory": numa_of_buffer(ids),
-               "path": ("host input above 4 GiB: streamed through two 1 GiB pinned staging buffers, copies "
+               "path": ("page-locked host input read by the device in %d value-range pieces (a copy grid of 64 "
+                        "CTAs over NVLink-C2C) while the %s batch loop runs on the pieces already there"
+                        % (se["h2d_pieces"], VARIANT_NAME.get(se["variant"], se["variant"]))
+                        if se["h2d_pieces"] else
+                        "host input above 4 GiB: streamed through two 1 GiB pinned staging buffers, copies "
                         "overlapping the device's work (super-batches planned one ahead)" if se["h2d_copies"] > 2 else
                         "the whole input copied to the device in one copy, then the device-resident call "
                         "(%s)" % VARIANT_NAME.get(se["variant"], se["variant"]))}

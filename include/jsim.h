@@ -167,8 +167,10 @@ typedef struct {
     uint64_t pack_bytes;       /* bytes the pack kernels read and wrote by algorithm: 8 per value
                                   packed plus 8 per word of the packed matrices they fill (zero
                                   words included) */
-    uint64_t h2d_copies;       /* host -> device copies the call issued for its input values */
-    uint64_t h2d_bytes;        /* bytes of those copies */
+    uint64_t h2d_copies;       /* host -> device DMA copies the call issued for its input */
+    uint64_t h2d_bytes;        /* bytes of its input brought to the device (copies and pieces) */
+    uint64_t h2d_pieces;       /* page-locked host input read by the device in this many value-range
+                                  pieces while the batch loop ran (0: not fed in pieces) */
 } jsim_stats;
 
 /* Fill *opt with the defaults described above. */

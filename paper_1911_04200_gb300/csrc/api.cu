@@ -8,11 +8,13 @@
 #include <vector>
 #include <algorithm>
 #include <mutex>
+#include <memory>
 #include "common.cuh"
 
 using namespace jsim;
 
 #include "ctx.cuh"
+#include "feed.cuh"
 #include "sparse.cuh"
 
 extern "C" {
@@ -71,6 +73,7 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
     }
     c->opt = o;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, o.device);
+    c->ingest_sms = c->sms;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, o.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, o.device);
     if (e == cudaSuccess) {
@@ -163,6 +166,33 @@ bool sparse_may_apply(jsim_ctx* ctx, const jsim_sets* sets)
     return bytes < (u64)free_b / 3;
 }
 
+// Does the plain call copy its host input piece by piece under the
+// block-sparse batch loop (feed.cuh)?  For page-locked input of at least
+// kFeedMinBytes that the device can read (hv: its device-mapped address);
+// minid and maxid from every sample's first and last value
+// (JSIM_ERR_UNSORTED later if the input is not sorted after all).
+bool feed_applies(jsim_ctx* ctx, const jsim_sets* sets, const std::vector<u64>& hoff, u64& minid, u64& maxid,
+                  const u64*& hv)
+{
+    (void)ctx;
+    const u64 n = sets->n, N = hoff[n];
+    if (sets->mem != JSIM_MEM_HOST || N * sizeof(u64) < kFeedMinBytes) return false;
+    cudaPointerAttributes pa{};
+    const bool mapped = cudaPointerGetAttributes(&pa, sets->ids) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+                        pa.devicePointer != nullptr;
+    cudaGetLastError();
+    if (!mapped) return false;
+    hv = (const u64*)pa.devicePointer;
+    minid = ~0ull;
+    maxid = 0;
+    for (u64 i = 0; i < n; ++i)
+        if (hoff[i + 1] > hoff[i]) {
+            minid = std::min<u64>(minid, sets->ids[hoff[i]]);
+            maxid = std::max<u64>(maxid, sets->ids[hoff[i + 1] - 1]);
+        }
+    return minid <= maxid;
+}
+
 // Row batches of part `part` of `parts` (the split contraction of
 // jsim_all_pairs_part): the batch size mt (batch_rows, or the automatic size
 // for the value span [minid, maxid]), and the batches [b_beg, b_end) (batch b
@@ -196,22 +226,44 @@ int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
     rc = load_offsets(ctx, sets, hoff);
     if (rc) return rc;
 
-    Staged st;
-    rc = stage_and_validate(ctx, sets, st, hoff);
-    if (rc) return rc;
-    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), ctx->stream));
-
     // the block-sparse path: asked for, or (AUTO) where a sketch shows that
     // ordering the samples empties enough tensor-core blocks
     const int want = ctx->opt.variant;
-    if (want == JSIM_VARIANT_SPARSE ||
-        (want == JSIM_VARIANT_AUTO && parts == 1 && !counts_only && n >= 256 && n <= 2048 &&
-         !ctx->opt.count_useful && product_tc_supported(ctx->opt.device) &&
-         (ctx->opt.batch_rows == 0 || ctx->opt.batch_rows % (1ull << 18) == 0))) {
-        if (parts != 1 || counts_only || ctx->opt.count_useful) return JSIM_ERR_UNSUPPORTED;
+    const bool sparse = want == JSIM_VARIANT_SPARSE ||
+                        (want == JSIM_VARIANT_AUTO && parts == 1 && !counts_only && n >= 256 && n <= 2048 &&
+                         !ctx->opt.count_useful && product_tc_supported(ctx->opt.device) &&
+                         (ctx->opt.batch_rows == 0 || ctx->opt.batch_rows % (1ull << 18) == 0));
+    if (sparse && (parts != 1 || counts_only || ctx->opt.count_useful)) return JSIM_ERR_UNSUPPORTED;
+
+    Staged st;
+    std::unique_ptr<InputFeed> feed;  // after st: its copies end before st's buffers are released
+    u64 feed_mt = 0, fminid = 0, fmaxid = 0;
+    const u64* hv = nullptr;
+    if (sparse && feed_applies(ctx, sets, hoff, fminid, fmaxid, hv) &&
+        (feed_mt = sparse_batch_rows(ctx, n, fmaxid - fminid)) != 0 && fmaxid / feed_mt - fminid / feed_mt >= 3) {
+        // page-locked host input: copied piece by piece under the batch loop
+        rc = stage_input(ctx, sets, st, hoff, false);
+        if (rc) return rc;
+        st.minid = fminid;
+        st.maxid = fmaxid;
+        feed.reset(new InputFeed());
+        rc = feed->start(ctx, st, hv, feed_mt, fminid, fmaxid);
+        if (rc) return rc;
+    } else {
+        rc = stage_and_validate(ctx, sets, st, hoff);
+        if (rc) return rc;
+    }
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), ctx->stream));
+
+    if (sparse) {
         bool declined = false;
-        rc = all_pairs_sparse(ctx, st, C, sizes, J, out_mem, want == JSIM_VARIANT_AUTO, declined);
+        rc = all_pairs_sparse(ctx, st, C, sizes, J, out_mem, want == JSIM_VARIANT_AUTO, declined, feed.get());
         if (rc || !declined) return rc;
+        if (feed) {
+            // the dense path reads the whole input: all of it in and valid
+            rc = feed->finish(st);
+            if (rc) return rc;
+        }
     }
     const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
     DevBuf Cacc, useful;

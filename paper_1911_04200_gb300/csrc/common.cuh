@@ -47,10 +47,21 @@ struct Plan {
     u64* totals; // [4]   total values, total chunks, first value after the batch, whether one exists
 };
 
+// ---- feed.cu ---------------------------------------------------------------
+// One piece of page-locked host input (hv: its device-mapped address) copied
+// to the same positions of dv: c1[i] = first position in [c0[i], off[i+1])
+// with value >= bound (off[i+1] when last), pre = exclusive prefix of the
+// slice lengths (n + 1 entries), then `grid` CTAs copy the slices.
+cudaError_t launch_feed_piece(const u64* hv, u64* dv, const u64* off, u64 n, const u64* c0, u64* c1, u64 bound,
+                              bool last, u64* pre, int grid, cudaStream_t st);
+
 // ---- ingest.cu -------------------------------------------------------------
-// perm (optional): entry i of the plan describes sample perm[i]
+// perm (optional): entry i of the plan describes sample perm[i].  ends
+// (optional): sample i's values are searched in [offsets[i], ends[i]) instead
+// of [offsets[i], offsets[i + 1]) (a slice of every sample, e.g. the part of
+// the input already copied to the device).
 cudaError_t launch_plan(const u64* offsets, const u64* ids, u64 n, u64 lo, u64 hi, bool full,
-                        Plan plan, cudaStream_t st, const u32* perm = nullptr);
+                        Plan plan, cudaStream_t st, const u32* perm = nullptr, const u64* ends = nullptr);
 // err_stride 0: one error word for all samples; 1: err[i] per sample
 cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan, u64 max_chunks,
                             int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, int sms,

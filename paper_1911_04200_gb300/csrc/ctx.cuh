@@ -21,6 +21,10 @@ struct jsim_ctx {
     cudaStream_t stream;
     bool own_stream;
     int sms;
+    // SM count the ingest kernels size their grids by: all SMs, or fewer
+    // while a small copy grid shares the GPU (feed.cuh), so that every CTA of
+    // an ingest launch is resident at once
+    int ingest_sms;
     int cc_major, cc_minor;
     jsim_stats stats;
     char cuda_err[256];
@@ -258,6 +262,7 @@ struct Staged {
     DevBuf off_buf, ids_buf;
     DevBuf sizes;     // [n] distinct counts
     DevBuf plan_buf;  // beg, len, cofs, totals
+    DevBuf flags;     // validation: error word, max value, min value
     Plan plan{};
     u64 n = 0, N = 0, maxid = 0, minid = 0, max_size = 0, max_chunks = 0;
 };
@@ -273,9 +278,10 @@ Plan carve_plan(DevBuf& b, u64 n)
     return p;
 }
 
-// Copy (if needed) and validate a collection: sorted segments, value range,
-// distinct counts per sample.  On success st.sizes holds |X_i|.
-int stage_and_validate(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std::vector<u64>& hoff)
+// Device buffers of a collection: offsets and values (copied from host
+// memory, the values only when copy_ids), sizes, a plan and the validation
+// flags.
+int stage_input(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std::vector<u64>& hoff, bool copy_ids)
 {
     st.n = s->n;
     st.N = hoff[s->n];
@@ -286,10 +292,13 @@ int stage_and_validate(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std:
             ALLOC(st.ids_buf, std::max<u64>(st.N, 1) * sizeof(u64));
             CK(cudaMemcpyAsync(st.off_buf.p, hoff.data(), (st.n + 1) * sizeof(u64), cudaMemcpyHostToDevice,
                                ctx->stream));
-            if (st.N)
+            ctx->stats.h2d_copies += 1;
+            ctx->stats.h2d_bytes += (st.n + 1) * sizeof(u64);
+            if (st.N && copy_ids) {
                 CK(cudaMemcpyAsync(st.ids_buf.p, s->ids, st.N * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
-            ctx->stats.h2d_copies += st.N ? 2 : 1;
-            ctx->stats.h2d_bytes += (st.n + 1 + st.N) * sizeof(u64);
+                ctx->stats.h2d_copies += 1;
+                ctx->stats.h2d_bytes += st.N * sizeof(u64);
+            }
             st.d_off = st.off_buf.as<u64>();
             st.d_ids = st.ids_buf.as<u64>();
         } else {
@@ -299,22 +308,33 @@ int stage_and_validate(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std:
     }
     ALLOC(st.sizes, std::max<u64>(st.n, 1) * sizeof(u64));
     ALLOC(st.plan_buf, (3 * st.n + 5) * sizeof(u64));
+    ALLOC(st.flags, 3 * sizeof(u64));  // err (u32 in a u64), max value, min value
     st.plan = carve_plan(st.plan_buf, st.n);
-    DevBuf flags;  // err (u32 in a u64), max value, min value
-    ALLOC(flags, 3 * sizeof(u64));
     st.max_chunks = st.N / kChunk + st.n + 1;
-    {
-        StageTimer t(ctx, &ctx->stats.ms_validate);
-        CK(cudaMemsetAsync(st.sizes.p, 0, st.n * sizeof(u64), ctx->stream));
-        CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(u64), ctx->stream));
-        CK(cudaMemsetAsync(flags.as<u64>() + 2, 0xff, sizeof(u64), ctx->stream));
-        CK(launch_plan(st.d_off, st.d_ids, st.n, 0, 0, true, st.plan, ctx->stream));
-        CK(launch_validate(st.d_off, st.d_ids, st.n, st.plan, st.max_chunks, ctx->opt.id_bits, st.sizes.as<u64>(),
-                           flags.as<u32>(), flags.as<u64>() + 1, flags.as<u64>() + 2, ctx->sms, ctx->stream));
-        ctx->stats.launches += 2;
-    }
+    return JSIM_OK;
+}
+
+// Validation of the staged values on stream `vs`: sorted segments, value
+// range, distinct counts per sample (into st.sizes), min and max value.
+int validate_staged(jsim_ctx* ctx, Staged& st, cudaStream_t vs)
+{
+    CK(cudaMemsetAsync(st.sizes.p, 0, st.n * sizeof(u64), vs));
+    CK(cudaMemsetAsync(st.flags.p, 0, 2 * sizeof(u64), vs));
+    CK(cudaMemsetAsync(st.flags.as<u64>() + 2, 0xff, sizeof(u64), vs));
+    CK(launch_plan(st.d_off, st.d_ids, st.n, 0, 0, true, st.plan, vs));
+    CK(launch_validate(st.d_off, st.d_ids, st.n, st.plan, st.max_chunks, ctx->opt.id_bits, st.sizes.as<u64>(),
+                       st.flags.as<u32>(), st.flags.as<u64>() + 1, st.flags.as<u64>() + 2, ctx->ingest_sms, vs));
+    ctx->stats.launches += 2;
+    return JSIM_OK;
+}
+
+// The validation's verdict (after the context's stream has waited for it):
+// JSIM_ERR_UNSORTED, JSIM_ERR_ID_RANGE, JSIM_ERR_OVERFLOW (a size that 32-bit
+// counts cannot hold), or st.minid, st.maxid and st.max_size.
+int check_staged(jsim_ctx* ctx, Staged& st)
+{
     std::vector<u64> hs(st.n);
-    CK(cudaMemcpyAsync(ctx->h_scalars, flags.p, 3 * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_scalars, st.flags.p, 3 * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(hs.data(), st.sizes.p, st.n * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     u32 f = (u32)ctx->h_scalars[0];
@@ -326,6 +346,20 @@ int stage_and_validate(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std:
     for (u64 v : hs) st.max_size = std::max(st.max_size, v);
     if (ctx->opt.count_bits == 32 && st.max_size > 0xffffffffull) return JSIM_ERR_OVERFLOW;
     return JSIM_OK;
+}
+
+// Copy (if needed) and validate a collection.  On success st.sizes holds
+// |X_i|.
+int stage_and_validate(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std::vector<u64>& hoff)
+{
+    int rc = stage_input(ctx, s, st, hoff, true);
+    if (rc) return rc;
+    {
+        StageTimer t(ctx, &ctx->stats.ms_validate);
+        rc = validate_staged(ctx, st, ctx->stream);
+        if (rc) return rc;
+    }
+    return check_staged(ctx, st);
 }
 
 // Largest power-of-two batch up to 2^28 rows (its 32 MiB filter bitmap and
@@ -388,6 +422,31 @@ int run_product(jsim_ctx* ctx, int variant, const u64* X, u64 stride, u64 n, u64
     return JSIM_OK;
 }
 
+// first position in [lo, hi) of a sorted array with value >= v
+u64 lower_bound_host(const uint64_t* a, u64 lo, u64 hi, u64 v)
+{
+    while (lo < hi) {
+        u64 mid = lo + (hi - lo) / 2;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// The same search started at lo, galloping (steps 1, 2, 4, ...) before
+// bisecting: the cut a value boundary makes in a sample lies shortly after
+// the previous boundary's cut, so this touches a few cache lines near it
+// instead of bisecting the whole sample.  Like any bisection it leaves q with
+// a[q-1] < v (or q = lo) and a[q] >= v (or q = hi), probed.
+u64 gallop_host(const uint64_t* a, u64 lo, u64 hi, u64 v)
+{
+    u64 step = 1, base = lo;
+    while (base + step <= hi && base + step - 1 < hi && a[base + step - 1] < v) {
+        base += step;
+        step *= 2;
+    }
+    return lower_bound_host(a, base, std::min(hi, base + step - 1), v);
+}
+
 // Working buffers of the batch loop.
 struct BatchBufs {
     DevBuf bitmap, seen, dir, bsum, boff, R, X, plan_buf, bsizes;  // bitmap: the rows kept
@@ -397,8 +456,11 @@ struct BatchBufs {
 
 // One row batch [lo, lo+width): plan, filter, rank directory, zero + pack.
 // On return bb.X holds n_pad rows of `stride` words and *R the nonzero rows.
+// With beg_bound/end_bound, sample i's values are searched only in
+// [beg_bound[i], end_bound[i]) (the slice of it already on the device).
 int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 width, u64& R, u64& stride,
-                u64* batch_sizes, bool* has_next = nullptr, u64* next = nullptr)
+                u64* batch_sizes, bool* has_next = nullptr, u64* next = nullptr, const u64* beg_bound = nullptr,
+                const u64* end_bound = nullptr)
 {
     const u64 n = st.n;
     const u64 nwords = width / 64;
@@ -413,16 +475,17 @@ int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 widt
     const u64 hi = lo + width;  // 0 on wrap-around = unbounded
     {
         StageTimer t(ctx, &ctx->stats.ms_filter);
-        CK(launch_plan(st.d_off, st.d_ids, n, lo, hi, false, bb.plan, ctx->stream));
+        CK(launch_plan(beg_bound ? beg_bound : st.d_off, st.d_ids, n, lo, hi, false, bb.plan, ctx->stream, nullptr,
+                       end_bound));
         CK(cudaMemsetAsync(bb.bitmap.p, 0, nwords * sizeof(u64), ctx->stream));
         if (ctx->opt.filter_min == 2) {
             // f of every row (seen) and the kept rows of two or more samples
             ALLOC(bb.seen, nwords * sizeof(u64));
             CK(cudaMemsetAsync(bb.seen.p, 0, nwords * sizeof(u64), ctx->stream));
-            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.seen.as<u32>(), ctx->sms,
+            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.seen.as<u32>(), ctx->ingest_sms,
                              ctx->stream, bb.bitmap.as<u32>()));
         } else {
-            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u32>(), ctx->sms,
+            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u32>(), ctx->ingest_sms,
                              ctx->stream));
         }
         ctx->stats.launches += 2;
@@ -452,14 +515,14 @@ int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 widt
         if (batch_sizes) {
             // the step-level entry point: zero-filled rows (the caller sees the
             // padding words too) and per-sample counts of the batch
-            CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->sms, ctx->stream));
+            CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->ingest_sms, ctx->stream));
             CK(cudaMemsetAsync(batch_sizes, 0, n * sizeof(u64), ctx->stream));
             CK(launch_pack(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u64>(), bb.dir.as<u32>(),
-                           bb.boff.as<u64>(), bb.X.as<u64>(), stride, batch_sizes, ctx->sms, ctx->stream));
+                           bb.boff.as<u64>(), bb.X.as<u64>(), stride, batch_sizes, ctx->ingest_sms, ctx->stream));
         } else {
-            CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->sms, ctx->stream));
+            CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->ingest_sms, ctx->stream));
             CK(launch_pack_full(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u64>(),
-                                bb.dir.as<u32>(), bb.boff.as<u64>(), bb.X.as<u64>(), stride, bb.R.as<u64>(), ctx->sms,
+                                bb.dir.as<u32>(), bb.boff.as<u64>(), bb.X.as<u64>(), stride, bb.R.as<u64>(), ctx->ingest_sms,
                                 ctx->stream));
         }
         ctx->stats.launches += 2;

@@ -9,10 +9,11 @@ namespace {
 
 // One CTA: per-sample [beg, beg+len) of values in [lo, hi) and chunk prefix.
 // With perm, entry i of the plan is sample perm[i] (the ingest kernels then
-// walk the samples in that order).
+// walk the samples in that order).  With ends, sample i is searched in
+// [offsets[i], ends[i]) only.
 __global__ void __launch_bounds__(kPlanThreads)
 k_plan(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, u64 lo, u64 hi,
-       int full, Plan plan, const u32* __restrict__ perm)
+       int full, Plan plan, const u32* __restrict__ perm, const u64* __restrict__ ends)
 {
     __shared__ u64 sm[kPlanThreads / 32];
     __shared__ u64 s_next;
@@ -25,7 +26,7 @@ k_plan(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, u64 
         u64 b = 0, l = 0, nch = 0;
         if (i < n) {
             const u64 si = perm ? (u64)perm[i] : i;
-            u64 s = offsets[si], e = offsets[si + 1];
+            u64 s = offsets[si], e = ends ? ends[si] : offsets[si + 1];
             if (!full) {
                 const u64 se = e;
                 u64 bb = lower_bound_u64(ids, s, e, lo);
@@ -490,9 +491,9 @@ inline unsigned grid_for_chunks(u64 max_chunks, int sms)
 }  // namespace
 
 cudaError_t launch_plan(const u64* offsets, const u64* ids, u64 n, u64 lo, u64 hi, bool full,
-                        Plan plan, cudaStream_t st, const u32* perm)
+                        Plan plan, cudaStream_t st, const u32* perm, const u64* ends)
 {
-    k_plan<<<1, kPlanThreads, 0, st>>>(offsets, ids, n, lo, hi, full ? 1 : 0, plan, perm);
+    k_plan<<<1, kPlanThreads, 0, st>>>(offsets, ids, n, lo, hi, full ? 1 : 0, plan, perm, ends);
     return cudaGetLastError();
 }
 

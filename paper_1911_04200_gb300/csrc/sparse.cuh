@@ -182,12 +182,29 @@ std::vector<u32> sample_order(const std::vector<u64>& Cs, u64 n)
     return order;
 }
 
+// Batch width of the block-sparse path for n samples over a value span: a
+// power of two, a whole scan block of every class, all tiles' bitmaps within
+// kTileBitmapBytes (0: the context's batch_rows does not divide into scan
+// blocks).
+u64 sparse_batch_rows(const jsim_ctx* ctx, u64 n, u64 span)
+{
+    const u64 T = (n + kTile - 1) / kTile;
+    u64 mt = ctx->opt.batch_rows;
+    if (mt) return mt % kMinClassRows ? 0 : mt;
+    mt = auto_batch_rows(span + 1 ? span + 1 : ~0ull);
+    while (mt > kMinClassRows && T * (mt / 8) * (ctx->opt.filter_min == 2 ? 2 : 1) > kTileBitmapBytes) mt >>= 1;
+    return std::max(mt, kMinClassRows);
+}
+
 // The block-sparse path of jsim_all_pairs: JSIM_ERR_UNSUPPORTED where it does
 // not apply (more than kMaxTiles tiles, no tensor cores, a batch width that
 // is not a multiple of kMinClassRows); with may_decline, declined = true
 // when the sketch shows the product would not be halved (nothing written).
-int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, double* J, int out_mem,
-                     bool may_decline, bool& declined)
+// With a feed, the values arrive piece by piece while the batches run (st
+// is validated when the last piece is in; until then st.minid, st.maxid and
+// the batch width are the feed's, from every sample's first and last value).
+int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double* J, int out_mem,
+                     bool may_decline, bool& declined, InputFeed* feed = nullptr)
 {
     declined = false;
     const u64 n = st.n;
@@ -198,18 +215,22 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
     cudaStream_t cs = ctx->stream;
     const u64 n_pad = round_up(n, kRowPad);
 
-    // ---- batch width: a power of two, a whole scan block of every class, all
-    // tiles' bitmaps within kTileBitmapBytes ----
     const u64 span = st.N ? st.maxid - st.minid : 0;
-    u64 mt = ctx->opt.batch_rows;
-    if (mt) {
-        if (mt % kMinClassRows) return JSIM_ERR_UNSUPPORTED;
-    } else {
-        mt = auto_batch_rows(span + 1 ? span + 1 : ~0ull);
-        while (mt > kMinClassRows && T * (mt / 8) * (twice ? 2 : 1) > kTileBitmapBytes) mt >>= 1;
-        mt = std::max(mt, kMinClassRows);
-    }
+    const u64 mt = feed ? feed->mt : sparse_batch_rows(ctx, n, span);
+    if (!mt) return JSIM_ERR_UNSUPPORTED;
     ctx->stats.batch_rows = mt;
+    // search bounds of a batch at lo: with a feed, the slices of lo's piece
+    const u64* pb = st.d_off;
+    const u64* pe = nullptr;
+    auto bounds_for = [&](u64 lo) -> int {
+        if (!feed) return JSIM_OK;
+        const int g = feed->piece_of(lo);
+        int r = feed->wait(g);
+        if (r) return r;
+        pb = feed->beg(g);
+        pe = feed->end(g);
+        return JSIM_OK;
+    };
 
     // ---- sketch: the dense product of the lowest values, about
     // kSketchPerSample per sample ----
@@ -248,12 +269,12 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
             // the plan lists the samples in their order (entry k: the sample
             // at position k), so the chunks in flight belong to one or two
             // tiles and their bitmaps and directories stay in L2
-            CK(launch_plan(st.d_off, st.d_ids, n, lo, hi, false, plan, cs, d_order.as<u32>()));
+            CK(launch_plan(pb, st.d_ids, n, lo, hi, false, plan, cs, d_order.as<u32>(), pe));
             CK(cudaMemsetAsync(B.p, 0, T * nw * sizeof(u64), cs));
             if (twice) CK(cudaMemsetAsync(B2.p, 0, T * nw * sizeof(u64), cs));
             CK(launch_filter_tiles(st.d_ids, n, plan, st.max_chunks, lo, width, B.as<u32>(),
-                                   twice ? B2.as<u32>() : nullptr, d_tile.as<u32>(), ctx->sms, cs));
-            k_classify<<<grid_of(nw, ctx->sms, 256), 256, 0, cs>>>(B.as<u64>(), twice ? B2.as<u64>() : nullptr, T, nw,
+                                   twice ? B2.as<u32>() : nullptr, d_tile.as<u32>(), ctx->ingest_sms, cs));
+            k_classify<<<grid_of(nw, ctx->ingest_sms, 256), 256, 0, cs>>>(B.as<u64>(), twice ? B2.as<u64>() : nullptr, T, nw,
                                                                    cls.as<u64>());
             CK(cudaGetLastError());
             ctx->stats.launches += 3;
@@ -287,7 +308,9 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
         const u64 lo_s = st.minid / ws * ws;
         BatchBufs sb;
         u64 R_s = 0, stride_s = 0;
-        int rc = build_batch(ctx, st, sb, lo_s, ws, R_s, stride_s, nullptr);
+        int rc = bounds_for(lo_s);
+        if (rc) return rc;
+        rc = build_batch(ctx, st, sb, lo_s, ws, R_s, stride_s, nullptr, nullptr, nullptr, pb, pe);
         if (rc) return rc;
         if (R_s) {
             DevBuf Cs;
@@ -327,7 +350,7 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
             // the sketch range's rows by class: is the product at least halved?
             bool hn;
             u64 nx;
-            rc = classify(lo_s, std::max(ws, kMinClassRows), hn, nx);
+            rc = classify(lo_s, std::max(ws, kMinClassRows), hn, nx);  // inside the first batch: same piece
             if (rc) return rc;
             // the call's product work, dense and block-sparse, scaled from the
             // sketch range's rows by values; with the ingest, the call's time
@@ -416,7 +439,9 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
         for (;;) {
             bool has_next = false;
             u64 next = 0;
-            int rc = classify(lo, mt, has_next, next);
+            int rc = bounds_for(lo);
+            if (rc) return rc;
+            rc = classify(lo, mt, has_next, next);
             if (rc) return rc;
             const u64 nw = mt / 64;
             std::vector<u64> W(T + 1);
@@ -475,7 +500,7 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
                     CK(launch_pack_classes(st.d_ids, n, plan, st.max_chunks, lo, mt, cls.as<u64>(), dir.as<u32>(),
                                            boff.as<u64>(), nw, kbase.as<u64>(), d_cls_of.as<u32>(), d_rowk.as<u32>(),
                                            W[0] ? XM.as<u64>() : nullptr, stride_m,
-                                           Wmax_s ? XS.as<u64>() : nullptr, stride_s, ctx->sms, cs));
+                                           Wmax_s ? XS.as<u64>() : nullptr, stride_s, ctx->ingest_sms, cs));
                     ctx->stats.launches += 3;
                 }
                 totM += W[0];
@@ -489,10 +514,33 @@ int all_pairs_sparse(jsim_ctx* ctx, const Staged& st, void* C, uint64_t* sizes, 
                 ctx->stats.words += Wd;
                 ctx->stats.bitops_dense += 64.0 * (double)Wd * (double)n * (double)(n + 1) / 2.0;
             }
-            if (!has_next) break;
-            lo = next / mt * mt;
+            if (!feed) {
+                if (!has_next) break;
+                lo = next / mt * mt;
+                continue;
+            }
+            // With a feed the plan saw only lo's piece: past its last value
+            // the next piece begins.  The cursor moves forward by at least a
+            // batch and stops after the last value (what the input holds is
+            // only checked when the whole of it is in).
+            const int g = feed->piece_of(lo);
+            u64 nl = has_next ? std::max(next / mt * mt, lo + mt) : g + 1 < feed->K ? feed->P[g + 1] : 0;
+            if (nl <= lo || nl > st.maxid) break;
+            // waiting for a piece still in flight: multiply what is packed
+            // so far in the meantime
+            const int gn = feed->piece_of(nl);
+            if (gn != g && !feed->arrived(gn) && (totM || std::any_of(totS.begin(), totS.end(), [](u64 w) { return w; }))) {
+                rc = flush();
+                if (rc) return rc;
+            }
+            lo = nl;
         }
         int rc = flush();
+        if (rc) return rc;
+    }
+    if (feed) {
+        // the validation's verdict (and the sizes the epilogue reads)
+        int rc = feed->finish(st);
         if (rc) return rc;
     }
     ctx->stats.variant = JSIM_VARIANT_SPARSE;

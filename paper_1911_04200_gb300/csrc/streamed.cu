@@ -109,31 +109,6 @@ int stream_state(jsim_ctx* ctx, size_t words, StreamState*& out)
     return JSIM_OK;
 }
 
-// first position in [lo, hi) of a sorted array with value >= v
-u64 lower_bound_host(const uint64_t* a, u64 lo, u64 hi, u64 v)
-{
-    while (lo < hi) {
-        u64 mid = lo + (hi - lo) / 2;
-        if (a[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// The same search started at lo, galloping (steps 1, 2, 4, ...) before
-// bisecting: the cut a super-batch boundary makes in a sample lies shortly
-// after the previous cut, so this touches a few cache lines near it instead
-// of bisecting the whole sample.  Like any bisection it leaves q with
-// a[q-1] < v (or q = lo) and a[q] >= v (or q = hi), probed.
-u64 gallop_host(const uint64_t* a, u64 lo, u64 hi, u64 v)
-{
-    u64 step = 1, base = lo;
-    while (base + step <= hi && base + step - 1 < hi && a[base + step - 1] < v) {
-        base += step;
-        step *= 2;
-    }
-    return lower_bound_host(a, base, std::min(hi, base + step - 1), v);
-}
-
 struct Super {
     u64 b0 = 0, b1 = 0;  // row batches [b0, b1)
     u64 count = 0;       // values in the super-batch

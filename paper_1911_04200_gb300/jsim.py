@@ -92,7 +92,8 @@ class Stats(ctypes.Structure):
                 ("bitops_useful", ctypes.c_double), ("bitops_done", ctypes.c_double), ("tile_n", ctypes.c_uint64),
                 ("pack_bytes", ctypes.c_uint64),
                 ("h2d_copies", ctypes.c_uint64),
-                ("h2d_bytes", ctypes.c_uint64)]
+                ("h2d_bytes", ctypes.c_uint64),
+                ("h2d_pieces", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -112,6 +112,24 @@ def test_clade1024_device_input_whole_result(gpu, clade1024):
         check_digests("clade1024", off, ids, C, s, J)
 
 
+@pytest.mark.timeout(900)
+def test_clade1024_pinned_host_input_whole_result(gpu, clade1024):
+    """Page-locked host input (the benchmark's end-to-end call): the values
+    are copied piece by piece while the block-sparse batch loop runs; the
+    oracle's whole result, by digest, with both filters."""
+    import torch
+    off, ids = clade1024
+    pin = torch.empty(len(ids), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    pin[:] = ids
+    for kw in ({}, dict(filter_min=2)):
+        with jsim.Context(id_bits=32, **kw) as ctx:
+            C, s, J = ctx.all_pairs(off, pin)
+            st = ctx.stats()
+        assert st["variant"] == "sparse"
+        assert st["h2d_pieces"] >= 3, "the input was not fed piece by piece"
+        check_digests("clade1024", off, ids, C, s, J)
+
+
 def test_ancestral64_whole_result_digest(gpu):
     off, ids = synth.ancestral64()
     with jsim.Context() as ctx:
