@@ -85,7 +85,7 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
             c->own_stream = true;
         }
     }
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_scalars, 64 * sizeof(u64));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_scalars, 256 * sizeof(u64));
     bool oom = false;
     if (e == cudaSuccess) {
         c->d_err = (unsigned int*)o.alloc(256, (void*)c->stream, o.alloc_user);

@@ -28,7 +28,7 @@ struct jsim_ctx {
     int cc_major, cc_minor;
     jsim_stats stats;
     char cuda_err[256];
-    // small pinned host scratch for device -> host scalars
+    // small pinned host scratch (256 u64) for device <-> host scalars
     unsigned long long* h_scalars;
     // device error word of kernels with bounded waits
     unsigned int* d_err;

@@ -138,7 +138,7 @@ k_filter(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, u32* 
             u64 q = ~0ull;
             u32 bit = 0;
             if (pos < p1) {
-                const u64 x = ids[pos];
+                const u64 x = __ldcs(ids + pos);  // read once: evict first
                 u64 d = x - lo;
                 if (d < width && !(twice && pos > bb && ids[pos - 1] == x)) { q = d >> 5; bit = 1u << (d & 31); }
             }
@@ -451,7 +451,7 @@ k_pack_classes(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
             const u64 pos = base + (threadIdx.x & 31);
             u64 key = ~0ull, bit = 0ull;
             if (pos < p1) {
-                const u64 d = ids[pos] - lo;
+                const u64 d = __ldcs(ids + pos) - lo;  // read once: evict first
                 if (d < width) {
                     const u64 w0 = d >> 6, sh = d & 63, low = (1ull << sh) - 1ull;
                     const u64 m0 = v.cls[w0];

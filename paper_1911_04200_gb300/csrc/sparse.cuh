@@ -236,16 +236,32 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     // kSketchPerSample per sample ----
     std::vector<u32> order(n), pos(n);
     for (u64 i = 0; i < n; ++i) order[i] = (u32)i;
-    DevBuf d_pos, d_order, d_tile, d_cls_of, d_rowk, jobtab, B, B2, cls, dir, bsum, boff, Rd, Wc, kbase, plan_buf;
+    DevBuf d_pos, d_order, d_tile, d_cls_of, d_rowk, jobtab, Wc, kbase;
     const u64 nw_max = mt / 64;
-    ALLOC(B, T * nw_max * sizeof(u64));
-    if (twice) ALLOC(B2, T * nw_max * sizeof(u64));
-    ALLOC(cls, (T + 1) * nw_max * sizeof(u64));
-    ALLOC(dir, (T + 1) * nw_max * sizeof(u32));
     const u64 nb_max = (T + 1) * nw_max / kScanBlockWords;
-    ALLOC(bsum, nb_max * sizeof(u64));
-    ALLOC(boff, (nb_max + 1) * sizeof(u64));
-    ALLOC(Rd, sizeof(u64));
+    // Two slots of batch structures: the next batch is classified while this
+    // one's class totals travel to the host and its pack is enqueued, so the
+    // device does not wait for the host between batches.  Slot s reads its
+    // totals back into pinned scalars [64 + 32 s, +21) and uploads its class
+    // bases from [128 + 64 s, +2(T + 1)).
+    struct Slot {
+        DevBuf B, B2, cls, dir, bsum, boff, Rd, plan_buf;
+        Plan plan{};
+        cudaEvent_t done = nullptr;  // totals on the host
+        ~Slot() { if (done) cudaEventDestroy(done); }
+    } slot[2];
+    for (Slot& x : slot) {
+        ALLOC(x.B, T * nw_max * sizeof(u64));
+        if (twice) ALLOC(x.B2, T * nw_max * sizeof(u64));
+        ALLOC(x.cls, (T + 1) * nw_max * sizeof(u64));
+        ALLOC(x.dir, (T + 1) * nw_max * sizeof(u32));
+        ALLOC(x.bsum, nb_max * sizeof(u64));
+        ALLOC(x.boff, (nb_max + 1) * sizeof(u64));
+        ALLOC(x.Rd, sizeof(u64));
+        ALLOC(x.plan_buf, (3 * n + 5) * sizeof(u64));
+        x.plan = carve_plan(x.plan_buf, n);
+        CK(cudaEventCreateWithFlags(&x.done, cudaEventDisableTiming));
+    }
     ALLOC(Wc, (T + 1) * sizeof(u64));
     ALLOC(kbase, (T + 1) * sizeof(u64));
     ALLOC(d_pos, n * sizeof(u32));
@@ -254,14 +270,12 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     ALLOC(d_tile, n * sizeof(u32));
     ALLOC(d_cls_of, n * sizeof(u32));
     ALLOC(jobtab, kMaxTiles * sizeof(TcJobDesc));
-    ALLOC(plan_buf, (3 * n + 5) * sizeof(u64));
-    const Plan plan = carve_plan(plan_buf, n);
     CK(cudaMemsetAsync(kbase.p, 0, (T + 1) * sizeof(u64), cs));
 
-    // classify the rows of [lo, lo + width) into B/cls and scan them; R_c on the host
-    std::vector<u64> Rc(T + 1, 0);
-    u64 range_values = 0;  // values of the last classified range
-    auto classify = [&](u64 lo, u64 width, bool& has_next, u64& next) -> int {
+    // classify the rows of [lo, lo + width) into slot s and scan them; the
+    // totals go to the host behind the slot's event
+    auto enqueue_classify = [&](int si, u64 lo, u64 width) -> int {
+        Slot& x = slot[si];
         const u64 nw = width / 64;
         const u64 hi = lo + width;  // 0 on wrap-around: unbounded
         {
@@ -269,35 +283,43 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
             // the plan lists the samples in their order (entry k: the sample
             // at position k), so the chunks in flight belong to one or two
             // tiles and their bitmaps and directories stay in L2
-            CK(launch_plan(pb, st.d_ids, n, lo, hi, false, plan, cs, d_order.as<u32>(), pe));
-            CK(cudaMemsetAsync(B.p, 0, T * nw * sizeof(u64), cs));
-            if (twice) CK(cudaMemsetAsync(B2.p, 0, T * nw * sizeof(u64), cs));
-            CK(launch_filter_tiles(st.d_ids, n, plan, st.max_chunks, lo, width, B.as<u32>(),
-                                   twice ? B2.as<u32>() : nullptr, d_tile.as<u32>(), ctx->ingest_sms, cs));
-            k_classify<<<grid_of(nw, ctx->ingest_sms, 256), 256, 0, cs>>>(B.as<u64>(), twice ? B2.as<u64>() : nullptr, T, nw,
-                                                                   cls.as<u64>());
+            CK(launch_plan(pb, st.d_ids, n, lo, hi, false, x.plan, cs, d_order.as<u32>(), pe));
+            CK(cudaMemsetAsync(x.B.p, 0, T * nw * sizeof(u64), cs));
+            if (twice) CK(cudaMemsetAsync(x.B2.p, 0, T * nw * sizeof(u64), cs));
+            CK(launch_filter_tiles(st.d_ids, n, x.plan, st.max_chunks, lo, width, x.B.as<u32>(),
+                                   twice ? x.B2.as<u32>() : nullptr, d_tile.as<u32>(), ctx->ingest_sms, cs));
+            k_classify<<<grid_of(nw, ctx->ingest_sms, 256), 256, 0, cs>>>(
+                x.B.as<u64>(), twice ? x.B2.as<u64>() : nullptr, T, nw, x.cls.as<u64>());
             CK(cudaGetLastError());
             ctx->stats.launches += 3;
         }
         {
             StageTimer t(ctx, &ctx->stats.ms_scan);
-            CK(launch_scan(cls.as<u64>(), (T + 1) * nw, dir.as<u32>(), bsum.as<u64>(), boff.as<u64>(), Rd.as<u64>(),
-                           cs));
+            CK(launch_scan(x.cls.as<u64>(), (T + 1) * nw, x.dir.as<u32>(), x.bsum.as<u64>(), x.boff.as<u64>(),
+                           x.Rd.as<u64>(), cs));
             ctx->stats.launches += 2;
         }
         // every class's first block offset, the total and the plan's next value
+        u64* hs = ctx->h_scalars + 64 + 32 * si;
         const u64 nb = nw / kScanBlockWords;
-        CK(cudaMemcpy2DAsync(ctx->h_scalars, sizeof(u64), boff.as<u64>(), nb * sizeof(u64), sizeof(u64), T + 1,
+        CK(cudaMemcpy2DAsync(hs, sizeof(u64), x.boff.as<u64>(), nb * sizeof(u64), sizeof(u64), T + 1,
                              cudaMemcpyDeviceToHost, cs));
-        CK(cudaMemcpyAsync(ctx->h_scalars + 17, Rd.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
-        CK(cudaMemcpyAsync(ctx->h_scalars + 18, plan.totals + 2, 2 * sizeof(u64), cudaMemcpyDeviceToHost, cs));
-        CK(cudaMemcpyAsync(ctx->h_scalars + 20, plan.totals, sizeof(u64), cudaMemcpyDeviceToHost, cs));
-        CK(cudaStreamSynchronize(cs));
-        for (u64 c = 0; c <= T; ++c)
-            Rc[c] = (c < T ? ctx->h_scalars[c + 1] : ctx->h_scalars[17]) - ctx->h_scalars[c];
-        next = ctx->h_scalars[18];
-        has_next = ctx->h_scalars[19] != 0;
-        range_values = ctx->h_scalars[20];
+        CK(cudaMemcpyAsync(hs + 17, x.Rd.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
+        CK(cudaMemcpyAsync(hs + 18, x.plan.totals + 2, 2 * sizeof(u64), cudaMemcpyDeviceToHost, cs));
+        CK(cudaMemcpyAsync(hs + 20, x.plan.totals, sizeof(u64), cudaMemcpyDeviceToHost, cs));
+        CK(cudaEventRecord(x.done, cs));
+        return JSIM_OK;
+    };
+    // R_c of the batch in slot s, its plan's next value and its value count
+    std::vector<u64> Rc(T + 1, 0);
+    u64 range_values = 0;
+    auto read_classify = [&](int si, bool& has_next, u64& next) -> int {
+        CK(cudaEventSynchronize(slot[si].done));
+        const u64* hs = ctx->h_scalars + 64 + 32 * si;
+        for (u64 c = 0; c <= T; ++c) Rc[c] = (c < T ? hs[c + 1] : hs[17]) - hs[c];
+        next = hs[18];
+        has_next = hs[19] != 0;
+        range_values = hs[20];
         return JSIM_OK;
     };
 
@@ -350,7 +372,9 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
             // the sketch range's rows by class: is the product at least halved?
             bool hn;
             u64 nx;
-            rc = classify(lo_s, std::max(ws, kMinClassRows), hn, nx);  // inside the first batch: same piece
+            rc = enqueue_classify(0, lo_s, std::max(ws, kMinClassRows));  // inside the first batch: same piece
+            if (rc) return rc;
+            rc = read_classify(0, hn, nx);
             if (rc) return rc;
             // the call's product work, dense and block-sparse, scaled from the
             // sketch range's rows by values; with the ingest, the call's time
@@ -403,7 +427,6 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     u64 stride_m = 0, stride_s = 0;
     u64 totM = 0;
     std::vector<u64> totS(T, 0);
-    std::vector<u64> hk(2 * (T + 1));  // kbase then Wc of a batch, uploaded together
     auto flush = [&]() -> int {
         StageTimer t(ctx, &ctx->stats.ms_product);
         double done = 0;
@@ -434,15 +457,37 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
         std::fill(totS.begin(), totS.end(), 0ull);
         return JSIM_OK;
     };
+    auto any_packed = [&]() { return totM || std::any_of(totS.begin(), totS.end(), [](u64 w) { return w; }); };
     if (st.N) {
         u64 lo = st.minid / mt * mt;
+        int si = 0;
+        int rc = bounds_for(lo);
+        if (rc) return rc;
+        rc = enqueue_classify(si, lo, mt);
+        if (rc) return rc;
+        bool dense_run = true;  // the last batch's values continued in the batch right after it
         for (;;) {
+            // While the values run on from batch to batch, the next row batch
+            // is taken to follow this one and classified before this one's
+            // totals are read (were it empty after all, that costs one
+            // classification); not when it lies in a piece of the input still
+            // in flight, where the wait is better spent multiplying.
+            const u64 lo_sp = lo + mt;
+            bool queued = false;
+            if (dense_run && lo_sp > lo && lo_sp <= st.maxid &&
+                (!feed || feed->piece_of(lo_sp) == feed->piece_of(lo) || feed->arrived(feed->piece_of(lo_sp)))) {
+                rc = bounds_for(lo_sp);
+                if (rc) return rc;
+                rc = enqueue_classify(1 - si, lo_sp, mt);
+                if (rc) return rc;
+                queued = true;
+            }
             bool has_next = false;
             u64 next = 0;
-            int rc = bounds_for(lo);
+            rc = read_classify(si, has_next, next);
             if (rc) return rc;
-            rc = classify(lo, mt, has_next, next);
-            if (rc) return rc;
+            dense_run = has_next && next / mt * mt == lo_sp;
+            const Slot& x = slot[si];
             const u64 nw = mt / 64;
             std::vector<u64> W(T + 1);
             u64 R = 0, Wmax_s = 0;
@@ -474,14 +519,18 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                     XS.release();
                     ALLOC(XS, n_pad * stride_s * sizeof(u64));
                 }
+                // the class bases and widths of the batch, from page-locked
+                // scratch of the slot (the upload that last read it precedes
+                // this batch's classification on the stream)
+                u64* hk = ctx->h_scalars + 128 + 64 * si;
                 hk[0] = totM;
                 hk[T + 1] = W[0];
                 for (u64 t2 = 0; t2 < T; ++t2) {
                     hk[1 + t2] = totS[t2];
                     hk[T + 2 + t2] = W[1 + t2];
                 }
-                CK(cudaMemcpyAsync(kbase.p, hk.data(), (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
-                CK(cudaMemcpyAsync(Wc.p, hk.data() + T + 1, (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
+                CK(cudaMemcpyAsync(kbase.p, hk, (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
+                CK(cudaMemcpyAsync(Wc.p, hk + T + 1, (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
                 {
                     StageTimer t(ctx, &ctx->stats.ms_pack);
                     if (W[0]) {
@@ -497,10 +546,10 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                                                           Wc.as<u64>(), 1);
                         CK(cudaGetLastError());
                     }
-                    CK(launch_pack_classes(st.d_ids, n, plan, st.max_chunks, lo, mt, cls.as<u64>(), dir.as<u32>(),
-                                           boff.as<u64>(), nw, kbase.as<u64>(), d_cls_of.as<u32>(), d_rowk.as<u32>(),
-                                           W[0] ? XM.as<u64>() : nullptr, stride_m,
-                                           Wmax_s ? XS.as<u64>() : nullptr, stride_s, ctx->ingest_sms, cs));
+                    CK(launch_pack_classes(st.d_ids, n, x.plan, st.max_chunks, lo, mt, x.cls.as<u64>(),
+                                           x.dir.as<u32>(), x.boff.as<u64>(), nw, kbase.as<u64>(),
+                                           d_cls_of.as<u32>(), d_rowk.as<u32>(), W[0] ? XM.as<u64>() : nullptr,
+                                           stride_m, Wmax_s ? XS.as<u64>() : nullptr, stride_s, ctx->ingest_sms, cs));
                     ctx->stats.launches += 3;
                 }
                 totM += W[0];
@@ -514,28 +563,41 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                 ctx->stats.words += Wd;
                 ctx->stats.bitops_dense += 64.0 * (double)Wd * (double)n * (double)(n + 1) / 2.0;
             }
-            if (!feed) {
-                if (!has_next) break;
-                lo = next / mt * mt;
+            if (queued) {
+                // the batch after this one is classified already: it is next
+                // (every value of this batch's successor lies at or above it)
+                si = 1 - si;
+                lo = lo_sp;
                 continue;
             }
-            // With a feed the plan saw only lo's piece: past its last value
-            // the next piece begins.  The cursor moves forward by at least a
-            // batch and stops after the last value (what the input holds is
-            // only checked when the whole of it is in).
-            const int g = feed->piece_of(lo);
-            u64 nl = has_next ? std::max(next / mt * mt, lo + mt) : g + 1 < feed->K ? feed->P[g + 1] : 0;
+            // The next batch from this one's plan: its first value above the
+            // batch; with a feed the plan saw only lo's piece, and past its
+            // last value the next piece begins.  The cursor moves forward by
+            // at least a batch and stops after the last value (what the input
+            // holds is only checked when the whole of it is in).
+            u64 nl = 0;
+            if (!feed) {
+                nl = has_next ? next / mt * mt : 0;
+            } else {
+                const int g = feed->piece_of(lo);
+                nl = has_next ? std::max(next / mt * mt, lo + mt) : g + 1 < feed->K ? feed->P[g + 1] : 0;
+            }
             if (nl <= lo || nl > st.maxid) break;
             // waiting for a piece still in flight: multiply what is packed
             // so far in the meantime
-            const int gn = feed->piece_of(nl);
-            if (gn != g && !feed->arrived(gn) && (totM || std::any_of(totS.begin(), totS.end(), [](u64 w) { return w; }))) {
+            if (feed && feed->piece_of(nl) != feed->piece_of(lo) && !feed->arrived(feed->piece_of(nl)) &&
+                any_packed()) {
                 rc = flush();
                 if (rc) return rc;
             }
+            rc = bounds_for(nl);
+            if (rc) return rc;
+            si = 1 - si;
             lo = nl;
+            rc = enqueue_classify(si, lo, mt);
+            if (rc) return rc;
         }
-        int rc = flush();
+        rc = flush();
         if (rc) return rc;
     }
     if (feed) {
