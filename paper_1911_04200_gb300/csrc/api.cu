@@ -237,6 +237,7 @@ int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
 
     Staged st;
     std::unique_ptr<InputFeed> feed;  // after st: its copies end before st's buffers are released
+    std::unique_ptr<SideValidation> sv;
     u64 feed_mt = 0, fminid = 0, fmaxid = 0;
     const u64* hv = nullptr;
     if (sparse && feed_applies(ctx, sets, hoff, fminid, fmaxid, hv) &&
@@ -249,6 +250,13 @@ int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
         feed.reset(new InputFeed());
         rc = feed->start(ctx, st, hv, feed_mt, fminid, fmaxid);
         if (rc) return rc;
+    } else if (sparse) {
+        // the input is validated beside the sketch and the batch loop
+        rc = stage_input(ctx, sets, st, hoff, true);
+        if (rc) return rc;
+        rc = first_last_values(ctx, st);
+        if (rc) return rc;
+        sv.reset(new SideValidation());  // started once the sketch is enqueued
     } else {
         rc = stage_and_validate(ctx, sets, st, hoff);
         if (rc) return rc;
@@ -257,13 +265,12 @@ int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
 
     if (sparse) {
         bool declined = false;
-        rc = all_pairs_sparse(ctx, st, C, sizes, J, out_mem, want == JSIM_VARIANT_AUTO, declined, feed.get());
+        rc = all_pairs_sparse(ctx, st, C, sizes, J, out_mem, want == JSIM_VARIANT_AUTO, declined, feed.get(),
+                              sv.get());
         if (rc || !declined) return rc;
-        if (feed) {
-            // the dense path reads the whole input: all of it in and valid
-            rc = feed->finish(st);
-            if (rc) return rc;
-        }
+        // the dense path reads the whole input: all of it in and valid
+        rc = feed ? feed->finish(st) : sv->finish(ctx, st);
+        if (rc) return rc;
     }
     const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
     DevBuf Cacc, useful;

@@ -62,6 +62,10 @@ cudaError_t launch_feed_piece(const u64* hv, u64* dv, const u64* off, u64 n, con
 // the input already copied to the device).
 cudaError_t launch_plan(const u64* offsets, const u64* ids, u64 n, u64 lo, u64 hi, bool full,
                         Plan plan, cudaStream_t st, const u32* perm = nullptr, const u64* ends = nullptr);
+// out[0] = smallest first value, out[1] = largest last value of the
+// non-empty samples (the minimum and maximum when they are sorted); out must
+// hold {~0, 0} before.
+cudaError_t launch_first_last(const u64* offsets, const u64* ids, u64 n, u64* out, cudaStream_t st);
 // err_stride 0: one error word for all samples; 1: err[i] per sample
 cudaError_t launch_validate(const u64* offsets, const u64* ids, u64 n, Plan plan, u64 max_chunks,
                             int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, int sms,

@@ -348,6 +348,70 @@ int check_staged(jsim_ctx* ctx, Staged& st)
     return JSIM_OK;
 }
 
+// Validation of a staged collection on a side stream, beside the work that
+// follows it on the context's stream: started after `after` (an event on
+// another stream) or after what the context's stream has enqueued so far;
+// finish() makes the context's stream wait for it and returns its verdict
+// (check_staged).  Until then the work on the context's stream may read
+// unvalidated values and must stay memory-safe on any input.
+struct SideValidation {
+    jsim_ctx* ctx = nullptr;
+    cudaStream_t vs = nullptr;
+    cudaEvent_t ready = nullptr, validated = nullptr;
+    bool started = false;
+    SideValidation() = default;
+    SideValidation(const SideValidation&) = delete;
+    SideValidation& operator=(const SideValidation&) = delete;
+    ~SideValidation()
+    {
+        if (vs) { cudaStreamSynchronize(vs); cudaStreamDestroy(vs); }
+        if (ready) cudaEventDestroy(ready);
+        if (validated) cudaEventDestroy(validated);
+        cudaGetLastError();
+    }
+    int start(jsim_ctx* c, Staged& st, cudaEvent_t after = nullptr)
+    {
+        ctx = c;
+        CK(cudaStreamCreateWithFlags(&vs, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&validated, cudaEventDisableTiming));
+        CK(cudaEventRecord(ready, ctx->stream));
+        CK(cudaStreamWaitEvent(vs, ready, 0));
+        if (after) CK(cudaStreamWaitEvent(vs, after, 0));
+        int rc = validate_staged(ctx, st, vs);
+        if (rc) return rc;
+        CK(cudaEventRecord(validated, vs));
+        started = true;
+        return JSIM_OK;
+    }
+    int finish(jsim_ctx* c, Staged& st)
+    {
+        if (!started) {
+            int rc = start(c, st);
+            if (rc) return rc;
+        }
+        CK(cudaStreamWaitEvent(ctx->stream, validated, 0));
+        return check_staged(ctx, st);
+    }
+};
+
+// The smallest first and largest last value of the staged samples (their
+// minimum and maximum when sorted) into st.minid and st.maxid; none: {~0, 0}.
+int first_last_values(jsim_ctx* ctx, Staged& st)
+{
+    DevBuf fl;
+    ALLOC(fl, 2 * sizeof(u64));
+    CK(cudaMemsetAsync(fl.p, 0xff, sizeof(u64), ctx->stream));
+    CK(cudaMemsetAsync(fl.as<u64>() + 1, 0, sizeof(u64), ctx->stream));
+    CK(launch_first_last(st.d_off, st.d_ids, st.n, fl.as<u64>(), ctx->stream));
+    ctx->stats.launches += 1;
+    CK(cudaMemcpyAsync(ctx->h_scalars, fl.p, 2 * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    st.minid = ctx->h_scalars[0];
+    st.maxid = ctx->h_scalars[1];
+    return JSIM_OK;
+}
+
 // Copy (if needed) and validate a collection.  On success st.sizes holds
 // |X_i|.
 int stage_and_validate(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std::vector<u64>& hoff)

@@ -45,11 +45,10 @@ struct InputFeed {
     DevBuf d_cuts;              // cut rows 1..K (row g: first position of piece g; row K: the ends)
     DevBuf d_pre;               // per piece: exclusive prefix of its slice lengths (n + 1)
     cudaStream_t xs = nullptr;  // the copy stream
-    cudaStream_t vs = nullptr;  // validation of the whole input
-    cudaEvent_t ready = nullptr, t0 = nullptr, validated = nullptr;
+    cudaEvent_t ready = nullptr, t0 = nullptr;
     std::vector<cudaEvent_t> ev;  // piece g on the device
+    SideValidation val;           // of the whole input, once the last piece is in
     int saved_ingest_sms = 0;
-    bool validation_launched = false;
 
     InputFeed() = default;
     InputFeed(const InputFeed&) = delete;
@@ -61,14 +60,13 @@ struct InputFeed {
     void shutdown()
     {
         if (xs) cudaStreamSynchronize(xs);
-        if (vs) cudaStreamSynchronize(vs);
+        if (val.vs) cudaStreamSynchronize(val.vs);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
         ev.clear();
-        for (cudaEvent_t* e : {&ready, &t0, &validated})
+        for (cudaEvent_t* e : {&ready, &t0})
             if (*e) { cudaEventDestroy(*e); *e = nullptr; }
         if (xs) { cudaStreamDestroy(xs); xs = nullptr; }
-        if (vs) { cudaStreamDestroy(vs); vs = nullptr; }
         if (ctx && saved_ingest_sms) { ctx->ingest_sms = saved_ingest_sms; saved_ingest_sms = 0; }
         cudaGetLastError();
     }
@@ -110,9 +108,7 @@ struct InputFeed {
         int lo_prio = 0, hi_prio = 0;
         CK(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
         CK(cudaStreamCreateWithPriority(&xs, cudaStreamNonBlocking, hi_prio));
-        CK(cudaStreamCreateWithFlags(&vs, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&validated, cudaEventDisableTiming));
         CK(cudaEventCreate(&t0));
         ev.assign(K, nullptr);
         for (int g = 0; g < K; ++g) CK(cudaEventCreate(&ev[g]));
@@ -130,11 +126,7 @@ struct InputFeed {
         }
         ctx->stats.launches += 2 * (u64)K;
         // the whole input validated once it is all in, beside the batch loop
-        CK(cudaStreamWaitEvent(vs, ev[K - 1], 0));
-        int rc = validate_staged(ctx, st, vs);
-        if (rc) return rc;
-        CK(cudaEventRecord(validated, vs));
-        return JSIM_OK;
+        return val.start(ctx, st, ev[K - 1]);
     }
 
     // the context's stream waits for piece g
@@ -156,8 +148,7 @@ struct InputFeed {
     // statistics, and the ingest grids back to every SM
     int finish(Staged& st)
     {
-        CK(cudaStreamWaitEvent(ctx->stream, validated, 0));
-        int rc = check_staged(ctx, st);
+        int rc = val.finish(ctx, st);
         if (saved_ingest_sms) { ctx->ingest_sms = saved_ingest_sms; saved_ingest_sms = 0; }
         if (rc) return rc;
         ctx->stats.h2d_pieces += (u64)K;

@@ -481,6 +481,32 @@ k_pack_classes(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
     }
 }
 
+// The smallest first value and the largest last value over the non-empty
+// samples (for sorted samples: the collection's minimum and maximum); out
+// must hold {~0, 0} before.  One CTA.
+__global__ void __launch_bounds__(kPlanThreads)
+k_first_last(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, u64* out)
+{
+    __shared__ unsigned long long s_min, s_max;
+    if (threadIdx.x == 0) { s_min = ~0ull; s_max = 0ull; }
+    __syncthreads();
+    unsigned long long mn = ~0ull, mx = 0ull;
+    for (u64 i = threadIdx.x; i < n; i += blockDim.x) {
+        const u64 a = offsets[i], e = offsets[i + 1];
+        if (e > a) {
+            mn = min(mn, (unsigned long long)ids[a]);
+            mx = max(mx, (unsigned long long)ids[e - 1]);
+        }
+    }
+    atomicMin(&s_min, mn);
+    atomicMax(&s_max, mx);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMin((unsigned long long*)out, s_min);
+        atomicMax((unsigned long long*)out + 1, s_max);
+    }
+}
+
 inline unsigned grid_for_chunks(u64 max_chunks, int sms)
 {
     u64 g = (u64)sms * 8;
@@ -551,6 +577,12 @@ cudaError_t launch_pack_classes(const u64* ids, u64 n, Plan plan, u64 max_chunks
     ClassView v{cls, dir, boff, kbase, nwords, cls_of, row_of};
     k_pack_classes<<<grid_for_chunks(max_chunks, sms), kIngestThreads, 0, st>>>(ids, n, plan, lo, width, v, XM,
                                                                                 stride_m, XS, stride_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_first_last(const u64* offsets, const u64* ids, u64 n, u64* out, cudaStream_t st)
+{
+    k_first_last<<<1, kPlanThreads, 0, st>>>(offsets, ids, n, out);
     return cudaGetLastError();
 }
 

@@ -10,30 +10,34 @@
 // exactly, as it holds every partial sum on the way; the epilogue scales by
 // 2^12, converts to integers and adds them into C.
 //
-// Work: the tiles of C are 128 x 256 (128 rows on the A side, 256 on the B
-// side, both read from X) that touch the upper triangle; each tile's word
-// range is cut into stages of 128 bit-rows.  The (job, tile, stage) units of
+// Work: the tiles of C are 128 x TN (TN = 256 or 128; 128 rows on the A
+// side, TN on the B side, both read from X) that touch the upper triangle;
+// each tile's word range is cut into stages of 256 bit-rows.  The (job, tile, stage) units of
 // all collections of a launch are laid out job-major, then tile-major, and
 // one persistent CTA per SM takes an equal contiguous share, split into
 // segments at tile boundaries and at the exactness cap.
 //
-// Roles inside a CTA (17 warps):
-//   warps 0-11  unpack: thread p owns row p of every stage (rows 0-127 A,
-//               128-383 B); it keeps its packed words four stages ahead in
-//               registers (one 16-byte load per stage), waits until the tensor core has released the
-//               stage buffer, writes its 128-byte row in the canonical
-//               K-major 128-byte-swizzle layout (16-byte chunk c of row r at
-//               c ^ (r % 8)), fences the generic-to-async proxy; one lane per
-//               warp then arrives on the buffer's `full` barrier;
-//   warp 12     one lane issues 4 tcgen05.mma (M=128, N=256, K=32) per stage
+// Roles inside a CTA ((128 + TN) / 32 + 5 warps):
+//   producers   unpack: thread p owns row p of every stage (rows 0-127 A,
+//               the rest B); it keeps its packed words four stages ahead in
+//               registers (16-byte loads), waits until the tensor core has
+//               released the stage buffer, writes its row's two 128-byte
+//               atom columns in the canonical K-major 128-byte-swizzle layout
+//               (16-byte chunk c of row r at c ^ (r % 8)), fences the
+//               generic-to-async proxy; one lane per warp then arrives on the
+//               buffer's `full` barrier.  On a diagonal tile (TN = 128, rows
+//               = columns) the B operand is the A operand, and the A-side and
+//               B-side threads of a row write one atom column each;
+//   MMA warp    one lane issues 8 tcgen05.mma (M=128, N=TN, K=32) per stage
 //               into one of two TMEM accumulators and commits them to the
 //               buffer's `empty` barrier, and each finished segment to the
 //               accumulator's `acc_full` barrier;
-//   warps 13-16 epilogue: wait for `acc_full`, read the accumulator with
-//               tcgen05.ld (each warp its 32 TMEM lanes), add it into C and
-//               release it through `acc_empty`.
-// Four 48 KiB stage buffers; two 256-column accumulators, so the epilogue of
-// one segment overlaps the MMAs of the next.  Every wait is bounded (clock64
+//   4 epilogue  wait for `acc_full`, read the accumulator with tcgen05.ld
+//   warps       (each warp its 32 TMEM lanes), add it into C and release it
+//               through `acc_empty`.
+// Two (TN = 256) or three (TN = 128) stage buffers; two TN-column
+// accumulators, so the epilogue of one segment overlaps the MMAs of the
+// next.  Every wait is bounded (clock64
 // budget, plus a CTA-wide abort flag); on time-out the CTA raises the error
 // word, waits (bounded) for its issued MMAs, frees its TMEM and leaves.
 #include <algorithm>
@@ -243,9 +247,11 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         const u32 atom_step = (u32)(is_a ? kAtomA : kAtomB);
         u64 ring[kAhead][kStageWords];
         // per ring slot: the stage's tile is diagonal (TN = 128, rows = columns):
-        // its B operand is the A operand, which the B-side threads then neither
-        // load nor write
+        // its B operand is the A operand, and the two threads of a row share
+        // its unpack (the A-side thread the first atom column, the B-side
+        // thread - which maps to the same row - the second)
         bool diag[kAhead];
+        static_assert(kAtoms == 2, "a diagonal row is split into two atom columns");
         // position of the next fetch: the current segment's job, tile (first
         // row and column), stage, and stages left in it
         WorkIter fit;
@@ -272,11 +278,12 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                 }
             }
             dg = TN == kM && f_r0 == f_c0;
-            const u64 grow = tcs::fetch_row(p, f_r0, f_c0);
-            if (grow < f_n && !(dg && !is_a)) {
+            const u64 grow = tcs::fetch_row(p, f_r0, f_c0);  // on a diagonal tile both sides map to row f_r0 + row
+            if (grow < f_n) {
                 const u64* src = f_X + grow * f_stride;
                 #pragma unroll
                 for (int q = 0; q < kStageWords; q += 2) {
+                    if (dg && (q >> 1) != (is_a ? 0 : 1)) continue;  // the words of this thread's atom column
                     u64 w0, w1;
                     const bool in0 = tcs::fetch_word(f_kst, q, f_W, w0);
                     const bool in1 = tcs::fetch_word(f_kst, q + 1, f_W, w1);
@@ -310,8 +317,12 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                 }
                 #pragma unroll
                 for (int at = 0; at < kAtoms; ++at) {
-                    if (diag[a] && !is_a) break;  // the MMA reads the A rows for both operands
-                    unsigned char* rowp = sm + b * kStageBytes + row_off + at * atom_step;
+                    // a diagonal tile's rows go to the A operand only (the MMA
+                    // reads them for both), atom column 0 from the A-side
+                    // thread and 1 from the B-side thread of the row
+                    if (diag[a] && at != (is_a ? 0 : 1)) continue;
+                    unsigned char* rowp = sm + b * kStageBytes +
+                                          (diag[a] ? (u32)(row * kBlkBytes + at * kAtomA) : row_off + at * atom_step);
                     #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         // bits 128 at + 16c .. +15 of the stage row -> 16 bytes

@@ -201,10 +201,12 @@ u64 sparse_batch_rows(const jsim_ctx* ctx, u64 n, u64 span)
 // is not a multiple of kMinClassRows); with may_decline, declined = true
 // when the sketch shows the product would not be halved (nothing written).
 // With a feed, the values arrive piece by piece while the batches run (st
-// is validated when the last piece is in; until then st.minid, st.maxid and
-// the batch width are the feed's, from every sample's first and last value).
+// is validated when the last piece is in); with sv, the values are there and
+// their validation runs beside the sketch and the batches.  Either way
+// st.minid and st.maxid are every sample's first and last value until the
+// verdict is read, before any output is written.
 int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double* J, int out_mem,
-                     bool may_decline, bool& declined, InputFeed* feed = nullptr)
+                     bool may_decline, bool& declined, InputFeed* feed = nullptr, SideValidation* sv = nullptr)
 {
     declined = false;
     const u64 n = st.n;
@@ -341,6 +343,11 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
             const u64 W_s = (R_s + 63) / 64;
             rc = run_product(ctx, choose_variant(ctx, n, W_s), sb.X.as<u64>(), stride_s, n, W_s, Cs.p);
             if (rc) return rc;
+            // the input's validation runs while the host orders the samples
+            if (sv && !sv->started) {
+                rc = sv->start(ctx, st);
+                if (rc) return rc;
+            }
             std::vector<u64> hc(n * n);
             if (cb == 8) {
                 CK(cudaMemcpyAsync(hc.data(), Cs.p, n * n * 8, cudaMemcpyDeviceToHost, cs));
@@ -600,9 +607,9 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
         rc = flush();
         if (rc) return rc;
     }
-    if (feed) {
+    if (feed || sv) {
         // the validation's verdict (and the sizes the epilogue reads)
-        int rc = feed->finish(st);
+        int rc = feed ? feed->finish(st) : sv->finish(ctx, st);
         if (rc) return rc;
     }
     ctx->stats.variant = JSIM_VARIANT_SPARSE;

@@ -119,3 +119,41 @@ def test_sparse_sixteen_tiles_and_its_limit(gpu):
         with pytest.raises(jsim.JsimError) as e:
             ctx.all_pairs(off2, ids2)
         assert e.value.name == "JSIM_ERR_UNSUPPORTED"
+
+
+def test_sparse_input_errors_found_beside_the_loop(gpu):
+    """On the block-sparse path the input is validated beside the sketch and
+    the batch loop: a descent or a value beyond id_bits, in host or device
+    input, is reported before any output is written, and the context keeps
+    working."""
+    import torch
+    off, ids = synth.clade1024(n=300, median=3e3)
+    n = len(off) - 1
+    i = 257
+    a, b = int(off[i]), int(off[i + 1])
+    bad_sorted = ids.copy()
+    bad_sorted[b - 3], bad_sorted[b - 2] = bad_sorted[b - 2], bad_sorted[b - 3]
+    bad_range = ids.copy()
+    bad_range[(a + b) // 2:b] = np.arange(b - (a + b) // 2, dtype=np.uint64) + (1 << 33)
+    for bad, name in ((bad_sorted, "JSIM_ERR_UNSORTED"), (bad_range, "JSIM_ERR_ID_RANGE")):
+        for dev in (False, True):
+            with jsim.Context(variant="sparse", id_bits=32) as ctx:
+                if dev:
+                    d_off = torch.from_numpy(off.view(np.int64)).cuda()
+                    d_ids = torch.from_numpy(bad.view(np.int64)).cuda()
+                    C = torch.full((n, n), 7, dtype=torch.int32, device="cuda")
+                    S = torch.full((n,), 7, dtype=torch.int64, device="cuda")
+                    J = torch.full((n, n), -1.0, dtype=torch.float64, device="cuda")
+                    with pytest.raises(jsim.JsimError) as e:
+                        ctx.all_pairs(d_off, d_ids, out=(C.view(torch.uint32), S.view(torch.uint64), J))
+                    torch.cuda.synchronize()
+                    assert bool((C == 7).all()) and bool((S == 7).all()) and bool((J == -1.0).all())
+                else:
+                    outs = (np.full((n, n), 7, dtype=np.uint32), np.full(n, 7, dtype=np.uint64),
+                            np.full((n, n), -1.0))
+                    with pytest.raises(jsim.JsimError) as e:
+                        ctx.all_pairs(off, bad, out=outs)
+                    assert (outs[0] == 7).all() and (outs[1] == 7).all() and (outs[2] == -1.0).all()
+                assert e.value.name == name
+                Cg, sg, Jg = ctx.all_pairs(off, ids)
+            check(off, ids, Cg, sg, Jg)
