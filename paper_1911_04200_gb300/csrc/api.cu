@@ -73,7 +73,6 @@ int jsim_create(jsim_ctx** out, const jsim_options* opt)
     }
     c->opt = o;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, o.device);
-    c->ingest_sms = c->sms;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, o.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, o.device);
     if (e == cudaSuccess) {
@@ -138,13 +137,14 @@ constexpr u64 kHostStreamMin = 4ull << 30;
 
 namespace {
 
-// Whether host input above kHostStreamMin should rather be copied whole to
-// the device for the block-sparse path (asked for, or AUTO in its range of
-// sample counts) than streamed through the dense path: it must fit in a
-// third of the free device memory.  The block-sparse call is three times
-// faster on the device than the dense one for clade collections, more than
-// the whole copy costs (1024 samples, 10.5 GB: copy 50 ms, call 67 ms; the
-// streamed dense call 216 ms).
+// Whether host input above kHostStreamMin should rather be brought to the
+// device whole for the block-sparse path (asked for, or AUTO in its range of
+// sample counts) than streamed through the dense path: the values, the
+// block-sparse path's class matrices (sparse_matrix_budget) and 4 GiB for
+// its other buffers must fit in the free device memory.  The block-sparse
+// call is three times faster on the device than the dense one for clade
+// collections, more than bringing the input over costs (1024 samples,
+// 10.5 GB: 71 ms end to end; the streamed dense call 216 ms).
 bool sparse_may_apply(jsim_ctx* ctx, const jsim_sets* sets)
 {
     const int v = ctx->opt.variant;
@@ -163,7 +163,7 @@ bool sparse_may_apply(jsim_ctx* ctx, const jsim_sets* sets)
         return false;
     }
     const u64 bytes = (sets->offsets[n] - sets->offsets[0]) * sizeof(u64);
-    return bytes < (u64)free_b / 3;
+    return bytes + sparse_matrix_budget(total_b) + (4ull << 30) < (u64)free_b;
 }
 
 // Does the plain call copy its host input piece by piece under the

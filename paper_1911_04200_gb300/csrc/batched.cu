@@ -385,7 +385,7 @@ replan:
     size_t s_tot = 0, p_tot = 0;
     for (auto& x : w.cols) {
         x.s_off = s_tot; s_tot += x.n;
-        x.p_off = p_tot; p_tot += 3 * x.n + 5;
+        x.p_off = p_tot; p_tot += plan_words(x.n);
         x.max_chunks = x.N / kChunk + x.n + 1;
     }
     ALLOC(w.spool, std::max<size_t>(s_tot, 1) * 8);

@@ -44,8 +44,14 @@ struct Plan {
     u64* beg;    // [n]   first position of the sample's batch values
     u64* len;    // [n]   number of them
     u64* cofs;   // [n+1] exclusive prefix of chunk counts
-    u64* totals; // [4]   total values, total chunks, first value after the batch, whether one exists
+    u64* totals; // [kPlanTotals] total values, total chunks, first value after the batch, whether one
+                 // exists; then the chunk tickets of the kernels that walk the plan (filter, pack,
+                 // validation), zeroed by the plan
 };
+constexpr u64 kPlanTotals = 8;
+constexpr int kTicketFilter = 4, kTicketPack = 5, kTicketValidate = 6;
+// u64 words of a plan over n samples: beg, len, cofs (n + 1), totals
+__host__ __device__ inline u64 plan_words(u64 n) { return 3 * n + 1 + kPlanTotals; }
 
 // ---- feed.cu ---------------------------------------------------------------
 // One piece of page-locked host input (hv: its device-mapped address) copied

@@ -21,10 +21,6 @@ struct jsim_ctx {
     cudaStream_t stream;
     bool own_stream;
     int sms;
-    // SM count the ingest kernels size their grids by: all SMs, or fewer
-    // while a small copy grid shares the GPU (feed.cuh), so that every CTA of
-    // an ingest launch is resident at once
-    int ingest_sms;
     int cc_major, cc_minor;
     jsim_stats stats;
     char cuda_err[256];
@@ -307,7 +303,7 @@ int stage_input(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std::vector
         }
     }
     ALLOC(st.sizes, std::max<u64>(st.n, 1) * sizeof(u64));
-    ALLOC(st.plan_buf, (3 * st.n + 5) * sizeof(u64));
+    ALLOC(st.plan_buf, plan_words(st.n) * sizeof(u64));
     ALLOC(st.flags, 3 * sizeof(u64));  // err (u32 in a u64), max value, min value
     st.plan = carve_plan(st.plan_buf, st.n);
     st.max_chunks = st.N / kChunk + st.n + 1;
@@ -323,7 +319,7 @@ int validate_staged(jsim_ctx* ctx, Staged& st, cudaStream_t vs)
     CK(cudaMemsetAsync(st.flags.as<u64>() + 2, 0xff, sizeof(u64), vs));
     CK(launch_plan(st.d_off, st.d_ids, st.n, 0, 0, true, st.plan, vs));
     CK(launch_validate(st.d_off, st.d_ids, st.n, st.plan, st.max_chunks, ctx->opt.id_bits, st.sizes.as<u64>(),
-                       st.flags.as<u32>(), st.flags.as<u64>() + 1, st.flags.as<u64>() + 2, ctx->ingest_sms, vs));
+                       st.flags.as<u32>(), st.flags.as<u64>() + 1, st.flags.as<u64>() + 2, ctx->sms, vs));
     ctx->stats.launches += 2;
     return JSIM_OK;
 }
@@ -529,7 +525,7 @@ int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 widt
     const u64 n = st.n;
     const u64 nwords = width / 64;
     const u64 nb = std::max<u64>((nwords + kScanBlockWords - 1) / kScanBlockWords, 1);
-    ALLOC(bb.plan_buf, (3 * n + 5) * sizeof(u64));
+    ALLOC(bb.plan_buf, plan_words(n) * sizeof(u64));
     bb.plan = carve_plan(bb.plan_buf, n);
     ALLOC(bb.bitmap, nwords * sizeof(u64));
     ALLOC(bb.dir, nwords * sizeof(u32));
@@ -546,10 +542,10 @@ int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 widt
             // f of every row (seen) and the kept rows of two or more samples
             ALLOC(bb.seen, nwords * sizeof(u64));
             CK(cudaMemsetAsync(bb.seen.p, 0, nwords * sizeof(u64), ctx->stream));
-            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.seen.as<u32>(), ctx->ingest_sms,
+            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.seen.as<u32>(), ctx->sms,
                              ctx->stream, bb.bitmap.as<u32>()));
         } else {
-            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u32>(), ctx->ingest_sms,
+            CK(launch_filter(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u32>(), ctx->sms,
                              ctx->stream));
         }
         ctx->stats.launches += 2;
@@ -579,14 +575,14 @@ int build_batch(jsim_ctx* ctx, const Staged& st, BatchBufs& bb, u64 lo, u64 widt
         if (batch_sizes) {
             // the step-level entry point: zero-filled rows (the caller sees the
             // padding words too) and per-sample counts of the batch
-            CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->ingest_sms, ctx->stream));
+            CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->sms, ctx->stream));
             CK(cudaMemsetAsync(batch_sizes, 0, n * sizeof(u64), ctx->stream));
             CK(launch_pack(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u64>(), bb.dir.as<u32>(),
-                           bb.boff.as<u64>(), bb.X.as<u64>(), stride, batch_sizes, ctx->ingest_sms, ctx->stream));
+                           bb.boff.as<u64>(), bb.X.as<u64>(), stride, batch_sizes, ctx->sms, ctx->stream));
         } else {
-            CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->ingest_sms, ctx->stream));
+            CK(launch_zero_rows(bb.X.as<u64>(), n_pad, stride, stride, ctx->sms, ctx->stream));
             CK(launch_pack_full(st.d_ids, n, bb.plan, st.max_chunks, lo, width, bb.bitmap.as<u64>(),
-                                bb.dir.as<u32>(), bb.boff.as<u64>(), bb.X.as<u64>(), stride, bb.R.as<u64>(), ctx->ingest_sms,
+                                bb.dir.as<u32>(), bb.boff.as<u64>(), bb.X.as<u64>(), stride, bb.R.as<u64>(), ctx->sms,
                                 ctx->stream));
         }
         ctx->stats.launches += 2;

@@ -50,7 +50,9 @@ k_feed_cuts(const u64* __restrict__ hv, const u64* __restrict__ off, u64 n, cons
 // batch loop running beside the copy keeps its class structures and the
 // product its shared panels in L2, which a gigabyte piece passing through
 // would otherwise evict.
-__global__ void __launch_bounds__(kGatherThreads)
+// At most 32 registers a thread (8 CTAs an SM), so a copy CTA takes no more
+// of an SM than one ingest CTA, and one fits beside a tensor-core product CTA.
+__global__ void __launch_bounds__(kGatherThreads, 8)
 k_feed_gather(const u64* __restrict__ hv, u64* __restrict__ dv, const u64* __restrict__ c0,
               const u64* __restrict__ pre, u64 n)
 {

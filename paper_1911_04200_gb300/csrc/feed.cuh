@@ -16,9 +16,8 @@
 // nothing reads values that are not there yet.  The pieces grow from one
 // batch to an eighth of the range and shrink back to one batch at the end, so
 // little of the copy is exposed at the start and little of the batch loop is
-// left when it ends.  While the copy grid runs, the ingest kernels size their
-// grids by kFeedCtas fewer CTA slots, so that all their CTAs stay resident
-// beside it.
+// left when it ends.  The ingest kernels take their chunks by ticket, so the
+// CTA slots the copy grid holds delay none of them.
 //
 // The input is validated once, whole, after the last piece has arrived (on a
 // side stream, while the batch loop goes on), and its verdict is read before
@@ -48,7 +47,6 @@ struct InputFeed {
     cudaEvent_t ready = nullptr, t0 = nullptr;
     std::vector<cudaEvent_t> ev;  // piece g on the device
     SideValidation val;           // of the whole input, once the last piece is in
-    int saved_ingest_sms = 0;
 
     InputFeed() = default;
     InputFeed(const InputFeed&) = delete;
@@ -67,7 +65,6 @@ struct InputFeed {
         for (cudaEvent_t* e : {&ready, &t0})
             if (*e) { cudaEventDestroy(*e); *e = nullptr; }
         if (xs) { cudaStreamDestroy(xs); xs = nullptr; }
-        if (ctx && saved_ingest_sms) { ctx->ingest_sms = saved_ingest_sms; saved_ingest_sms = 0; }
         cudaGetLastError();
     }
 
@@ -115,8 +112,6 @@ struct InputFeed {
         // the copies write buffers the context's stream allocated
         CK(cudaEventRecord(ready, ctx->stream));
         CK(cudaStreamWaitEvent(xs, ready, 0));
-        saved_ingest_sms = ctx->ingest_sms;
-        ctx->ingest_sms = std::max(1, ctx->sms - (kFeedCtas * 256 + 2047) / 2048);
         CK(cudaEventRecord(t0, xs));
         for (int g = 0; g < K; ++g) {
             const bool last = g + 1 == K;
@@ -144,12 +139,11 @@ struct InputFeed {
         return e == cudaSuccess;
     }
 
-    // the context's stream waits for the validation; its verdict, the copy
-    // statistics, and the ingest grids back to every SM
+    // the context's stream waits for the validation; its verdict and the
+    // copy statistics
     int finish(Staged& st)
     {
         int rc = val.finish(ctx, st);
-        if (saved_ingest_sms) { ctx->ingest_sms = saved_ingest_sms; saved_ingest_sms = 0; }
         if (rc) return rc;
         ctx->stats.h2d_pieces += (u64)K;
         ctx->stats.h2d_bytes += st.N * sizeof(u64);

@@ -55,6 +55,7 @@ k_plan(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, u64 
         plan.totals[1] = carry;
         plan.totals[2] = s_next;
         plan.totals[3] = (u64)s_has_next;
+        for (u64 k = 4; k < kPlanTotals; ++k) plan.totals[k] = 0;  // chunk tickets
     }
 }
 
@@ -62,17 +63,22 @@ __global__ void __launch_bounds__(kIngestThreads)
 k_validate(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, Plan plan,
            int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, u64 err_stride)
 {
-    __shared__ u64 s_i, s_p0, s_p1;
+    __shared__ u64 s_i, s_p0, s_p1, s_c;
     __shared__ u32 s_cnt[kIngestThreads / 32];
     const u64 nch = plan.totals[1];
-    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+    for (;;) {
         if (threadIdx.x == 0) {
-            u64 i = chunk_sample(plan.cofs, n, c);
-            u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
-            u64 p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
-            s_i = i; s_p0 = p0; s_p1 = p1;
+            const u64 c = next_chunk(plan, kTicketValidate);
+            s_c = c;
+            if (c < nch) {
+                u64 i = chunk_sample(plan.cofs, n, c);
+                u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+                u64 p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+                s_i = i; s_p0 = p0; s_p1 = p1;
+            }
         }
         __syncthreads();
+        if (s_c >= nch) break;
         const u64 i = s_i, p0 = s_p0, p1 = s_p1;
         const u64 sb = offsets[i], se = offsets[i + 1];
         u32 cnt = 0, flags = 0;
@@ -116,18 +122,23 @@ __global__ void __launch_bounds__(kIngestThreads)
 k_filter(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, u32* bitmap_all, u32* twice_all,
          const u32* __restrict__ tile_of, u64 tile_words)
 {
-    __shared__ u64 s_p0, s_p1, s_b, s_t;
+    __shared__ u64 s_p0, s_p1, s_b, s_t, s_c;
     const u64 nch = plan.totals[1];
-    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+    for (;;) {
         if (threadIdx.x == 0) {
-            u64 i = chunk_sample(plan.cofs, n, c);
-            u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
-            s_p0 = p0;
-            s_b = plan.beg[i];
-            s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
-            s_t = tile_of ? (u64)tile_of[i] * tile_words : 0ull;
+            const u64 c = next_chunk(plan, kTicketFilter);
+            s_c = c;
+            if (c < nch) {
+                u64 i = chunk_sample(plan.cofs, n, c);
+                u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+                s_p0 = p0;
+                s_b = plan.beg[i];
+                s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+                s_t = tile_of ? (u64)tile_of[i] * tile_words : 0ull;
+            }
         }
         __syncthreads();
+        if (s_c >= nch) break;
         const u64 p0 = s_p0, p1 = s_p1, bb = s_b;
         // the sample's own bitmap (one per sample tile when tile_of is given)
         u32* bitmap = bitmap_all + s_t;
@@ -246,17 +257,22 @@ k_pack(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
        const u64* __restrict__ bitmap, const u32* __restrict__ dir, const u64* __restrict__ boff,
        u64* X, u64 stride, u64* batch_sizes, const u64* kbase, u64 wstride)
 {
-    __shared__ u64 s_i, s_p0, s_p1, s_b;
+    __shared__ u64 s_i, s_p0, s_p1, s_b, s_c;
     __shared__ u32 s_cnt[kIngestThreads / 32];
     const u64 nch = plan.totals[1];
-    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+    for (;;) {
         if (threadIdx.x == 0) {
-            u64 i = chunk_sample(plan.cofs, n, c);
-            u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
-            s_i = i; s_p0 = p0; s_b = plan.beg[i];
-            s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+            const u64 c = next_chunk(plan, kTicketPack);
+            s_c = c;
+            if (c < nch) {
+                u64 i = chunk_sample(plan.cofs, n, c);
+                u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+                s_i = i; s_p0 = p0; s_b = plan.beg[i];
+                s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+            }
         }
         __syncthreads();
+        if (s_c >= nch) break;
         const u64 i = s_i, p0 = s_p0, p1 = s_p1, bb = s_b;
         u64* row = X + i * stride + (kbase ? *kbase : 0ull) * wstride;
         u32 cnt = 0;
@@ -333,20 +349,25 @@ k_pack_full(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, co
             const u32* __restrict__ dir, const u64* __restrict__ boff, u64* X, u64 stride,
             const u64* kbase, const u64* __restrict__ Rdev)
 {
-    __shared__ u64 s_i, s_p0, s_p1, s_b, s_e;
+    __shared__ u64 s_i, s_p0, s_p1, s_b, s_e, s_c;
     const u64 nch = plan.totals[1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long Wl = (long long)((*Rdev + 63) / 64);
     const long long kBig = 0x7fffffffffffffffll;
-    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+    for (;;) {
         if (threadIdx.x == 0) {
-            const u64 i = chunk_sample(plan.cofs, n, c);
-            const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
-            s_i = i; s_p0 = p0; s_b = plan.beg[i];
-            s_e = plan.beg[i] + plan.len[i];
-            s_p1 = min(p0 + kChunk, s_e);
+            const u64 c = next_chunk(plan, kTicketPack);
+            s_c = c;
+            if (c < nch) {
+                const u64 i = chunk_sample(plan.cofs, n, c);
+                const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+                s_i = i; s_p0 = p0; s_b = plan.beg[i];
+                s_e = plan.beg[i] + plan.len[i];
+                s_p1 = min(p0 + kChunk, s_e);
+            }
         }
         __syncthreads();
+        if (s_c >= nch) break;
         const u64 i = s_i, bb = s_b, be = s_e;
         const u64 sbeg = s_p0 + (u64)warp * kPackSeg, send = min(sbeg + kPackSeg, s_p1);
         __syncthreads();  // the shared chunk fields are read; the next chunk may overwrite them
@@ -430,17 +451,22 @@ __global__ void __launch_bounds__(kIngestThreads)
 k_pack_classes(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, ClassView v, u64* XM,
                u64 stride_m, u64* XS, u64 stride_s)
 {
-    __shared__ u64 s_i, s_p0, s_p1;
+    __shared__ u64 s_i, s_p0, s_p1, s_c;
     const u64 nch = plan.totals[1];
     const u64 blk0 = 0;
-    for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+    for (;;) {
         if (threadIdx.x == 0) {
-            const u64 i = chunk_sample(plan.cofs, n, c);
-            const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
-            s_i = i; s_p0 = p0;
-            s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+            const u64 c = next_chunk(plan, kTicketPack);
+            s_c = c;
+            if (c < nch) {
+                const u64 i = chunk_sample(plan.cofs, n, c);
+                const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
+                s_i = i; s_p0 = p0;
+                s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
+            }
         }
         __syncthreads();
+        if (s_c >= nch) break;
         const u64 i = s_i, p0 = s_p0, p1 = s_p1;
         const u64 cs = v.cls_of[i];
         const u64 row = v.row_of[i];

@@ -49,6 +49,15 @@ __device__ __forceinline__ u64 block_exclusive_scan(u64 v, u64& excl, u64* smem 
     return total;
 }
 
+// The next chunk of a plan for the calling CTA: a ticket from the plan's
+// counter `which` (zeroed by the plan), so the chunks go, in order, to
+// whichever CTAs are resident - a launch that shares the GPU with another
+// kernel is not held up by CTAs that start late with a fixed share of work.
+__device__ __forceinline__ u64 next_chunk(const Plan& plan, int which)
+{
+    return atomicAdd((unsigned long long*)(plan.totals + which), 1ull);
+}
+
 // Chunk c -> sample index (largest i with cofs[i] <= c, among samples with chunks).
 __device__ __forceinline__ u64 chunk_sample(const u64* cofs, u64 n, u64 c)
 {

@@ -506,7 +506,7 @@ int jsim_index_build(jsim_ctx* ctx, const jsim_sets* ref, const jsim_serve_optio
         sl.out_bytes = out_layout(S, n, cb).total;
         CK(cudaMallocHost((void**)&sl.pin_out, sl.out_bytes));
         ALLOC(sl.din, (head + V) * sizeof(u64));
-        ALLOC(sl.plan_buf, (3 * S + 5) * sizeof(u64));
+        ALLOC(sl.plan_buf, plan_words(S) * sizeof(u64));
         ALLOC(sl.sq, S * sizeof(u64));
         ALLOC(sl.qerr, S * sizeof(u32));
         ALLOC(sl.mm, 2 * sizeof(u64));

@@ -182,6 +182,11 @@ std::vector<u32> sample_order(const std::vector<u64>& Cs, u64 n)
     return order;
 }
 
+// Bytes of the class-0 and per-tile matrices the block-sparse path appends
+// its batches' words to: a fixed share of the device (12 GiB, or a sixteenth
+// of a smaller one).
+u64 sparse_matrix_budget(u64 total_bytes) { return std::min<u64>(12ull << 30, total_bytes / 16); }
+
 // Batch width of the block-sparse path for n samples over a value span: a
 // power of two, a whole scan block of every class, all tiles' bitmaps within
 // kTileBitmapBytes (0: the context's batch_rows does not divide into scan
@@ -260,7 +265,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
         ALLOC(x.bsum, nb_max * sizeof(u64));
         ALLOC(x.boff, (nb_max + 1) * sizeof(u64));
         ALLOC(x.Rd, sizeof(u64));
-        ALLOC(x.plan_buf, (3 * n + 5) * sizeof(u64));
+        ALLOC(x.plan_buf, plan_words(n) * sizeof(u64));
         x.plan = carve_plan(x.plan_buf, n);
         CK(cudaEventCreateWithFlags(&x.done, cudaEventDisableTiming));
     }
@@ -289,8 +294,9 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
             CK(cudaMemsetAsync(x.B.p, 0, T * nw * sizeof(u64), cs));
             if (twice) CK(cudaMemsetAsync(x.B2.p, 0, T * nw * sizeof(u64), cs));
             CK(launch_filter_tiles(st.d_ids, n, x.plan, st.max_chunks, lo, width, x.B.as<u32>(),
-                                   twice ? x.B2.as<u32>() : nullptr, d_tile.as<u32>(), ctx->ingest_sms, cs));
-            k_classify<<<grid_of(nw, ctx->ingest_sms, 256), 256, 0, cs>>>(
+                                   twice ? x.B2.as<u32>() : nullptr, d_tile.as<u32>(), ctx->sms, cs));
+            // one word per thread: short CTAs that any free slot can take
+            k_classify<<<(unsigned)std::max<u64>(1, (nw + 255) / 256), 256, 0, cs>>>(
                 x.B.as<u64>(), twice ? x.B2.as<u64>() : nullptr, T, nw, x.cls.as<u64>());
             CK(cudaGetLastError());
             ctx->stats.launches += 3;
@@ -428,7 +434,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     // every fourth call reallocate and take twice as long)
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); total_b = 64ull << 30; }
-    const u64 budget = std::min<u64>(12ull << 30, (u64)total_b / 16);  // XM a third, XS two thirds
+    const u64 budget = sparse_matrix_budget(total_b);  // XM a third, XS two thirds
     u64 capM = std::max<u64>(1ull << 12, budget / 3 / (n_pad * 8) / 64 * 64);
     u64 capS = std::max<u64>(1ull << 12, budget * 2 / 3 / (n_pad * 8) / 64 * 64);
     u64 stride_m = 0, stride_s = 0;
@@ -556,7 +562,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                     CK(launch_pack_classes(st.d_ids, n, x.plan, st.max_chunks, lo, mt, x.cls.as<u64>(),
                                            x.dir.as<u32>(), x.boff.as<u64>(), nw, kbase.as<u64>(),
                                            d_cls_of.as<u32>(), d_rowk.as<u32>(), W[0] ? XM.as<u64>() : nullptr,
-                                           stride_m, Wmax_s ? XS.as<u64>() : nullptr, stride_s, ctx->ingest_sms, cs));
+                                           stride_m, Wmax_s ? XS.as<u64>() : nullptr, stride_s, ctx->sms, cs));
                     ctx->stats.launches += 3;
                 }
                 totM += W[0];

@@ -515,7 +515,7 @@ extern "C" int jsim_all_pairs_streamed_ckpt(jsim_ctx* ctx, const jsim_sets* sets
     ALLOC(Cacc, n * n * cb);
     ALLOC(sizes_d, n * sizeof(u64));
     ALLOC(flags, 3 * sizeof(u64));
-    ALLOC(plan_buf, (3 * n + 5) * sizeof(u64));
+    ALLOC(plan_buf, plan_words(n) * sizeof(u64));
     ALLOC(bm, nw_max * sizeof(u64));  // the rows kept
     const bool twice = ctx->opt.filter_min == 2;
     if (twice) ALLOC(seen, nw_max * sizeof(u64));

@@ -80,6 +80,8 @@ def test_clade1024_full_size(gpu, clade1024):
     choice (the block-sparse product), the dense SM-pair product, and the
     two-or-more filter: sampled parity, whole-result digests, and all runs
     byte-identical."""
+    import torch
+    torch.cuda.empty_cache()  # host input this large takes the block-sparse route only with room on the device
     off, ids = clade1024
     with jsim.Context(id_bits=32) as ctx:
         C, s, J = ctx.all_pairs(off, ids)
@@ -118,6 +120,7 @@ def test_clade1024_pinned_host_input_whole_result(gpu, clade1024):
     are copied piece by piece while the block-sparse batch loop runs; the
     oracle's whole result, by digest, with both filters."""
     import torch
+    torch.cuda.empty_cache()  # host input this large takes the block-sparse route only with room on the device
     off, ids = clade1024
     pin = torch.empty(len(ids), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
     pin[:] = ids
