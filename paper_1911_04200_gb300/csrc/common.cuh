@@ -147,9 +147,12 @@ struct TcJobDesc {
 // read by the kernels; with upload it is first written from `jobs`
 // (stream-ordered; not allowed while the stream is being captured).
 // tile_n: tiles of 128 x 256 (256) or 128 x 128 (128; a diagonal tile then
-// unpacks its rows once for both operands).
+// unpacks its rows once for both operands).  diag_only (tile_n 128, every job
+// of at most 128 samples: one diagonal tile each): stages of the A rows only,
+// more of them in flight.
 cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, void* dev_table, bool upload, int count_bits, int sms,
-                            u32* err, int timeout_ms, cudaStream_t st, int* launches, int tile_n = 256);
+                            u32* err, int timeout_ms, cudaStream_t st, int* launches, int tile_n = 256,
+                            bool diag_only = false);
 bool product_tc_supported(int device);
 
 // ---- query.cu (serving) ---------------------------------------------------------

@@ -70,8 +70,10 @@ constexpr u32 kErrTimeout = 4u;
 // The kernel's shape for tiles of 128 x TN (TN = 256 or 128).  One producer
 // thread per unpacked row (128 + TN), one MMA warp, four epilogue warps; two
 // TMEM accumulators of TN columns.  With TN = 128 a stage is two thirds the
-// size, so three stage buffers fit.
-template <int TN>
+// size, so three stage buffers fit.  DG (TN = 128): every tile of the launch
+// is diagonal, a stage holds the A rows only, and six buffers keep more
+// stages in flight between the producers and the tensor core.
+template <int TN, bool DG = false>
 struct Shape {
     static constexpr int kN = TN;
     static constexpr int kRows = kM + TN;                  // rows unpacked per stage
@@ -81,8 +83,8 @@ struct Shape {
     static constexpr int kWarps = kEpiWarp0 + 4;
     static constexpr int kThreads = kWarps * 32;
     static constexpr int kAtomB = TN * kBlkBytes;          // one atom column of B
-    static constexpr int kStageBytes = kAtoms * kRows * kBlkBytes;
-    static constexpr int kBufs = TN == 128 ? 3 : 2;
+    static constexpr int kStageBytes = DG ? kABytes : kAtoms * kRows * kBlkBytes;
+    static constexpr int kBufs = DG ? 6 : TN == 128 ? 3 : 2;
     static constexpr int kSmemBytes = kBufs * kStageBytes + 1024;  // + alignment slack
     static constexpr int kTmemCols = 2 * TN;               // two TN-column FP32 accumulators
     // instruction descriptor: kind::f8f6f4, D = F32, A = B = E4M3, both
@@ -93,6 +95,7 @@ struct Shape {
     static_assert(kEpiWarp0 % 4 == 1, "epilogue warp e reads TMEM lanes of warp rank (kEpiWarp0 + e) % 4");
     static_assert(kSmemBytes + 9 * 1024 <= 232448, "fits the per-CTA shared-memory limit");
     static_assert(TN == 128 || TN == 256, "tile widths");
+    static_assert(!DG || TN == kM, "diagonal-only launches have square tiles");
 };
 
 __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
@@ -176,11 +179,11 @@ struct TcJobs {
     int vec16;  // 16-byte loads are safe for every job
 };
 
-template <typename CT, int TN>
-__global__ void __launch_bounds__(Shape<TN>::kThreads, 1)
+template <typename CT, int TN, bool DG>
+__global__ void __launch_bounds__(Shape<TN, DG>::kThreads, 1)
 k_prod_tc(const TcJobs P, u32* err, long long budget)
 {
-    using S = Shape<TN>;
+    using S = Shape<TN, DG>;
     constexpr int kBufs = S::kBufs, kStageBytes = S::kStageBytes, kAtomB = S::kAtomB;
     constexpr int kProducerWarps = S::kProducerWarps, kMmaWarp = S::kMmaWarp, kEpiWarp0 = S::kEpiWarp0;
     constexpr int kTmemCols = S::kTmemCols;
@@ -277,7 +280,7 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                     f_key = key;
                 }
             }
-            dg = TN == kM && f_r0 == f_c0;
+            dg = DG || (TN == kM && f_r0 == f_c0);
             const u64 grow = tcs::fetch_row(p, f_r0, f_c0);  // on a diagonal tile both sides map to row f_r0 + row
             if (grow < f_n) {
                 const u64* src = f_X + grow * f_stride;
@@ -381,7 +384,7 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                 // a diagonal tile (TN = 128, rows = columns) multiplies its A rows by themselves
                 u64 r0, c0;
                 tc_tile(sg.tile, ji[sg.job].TM, r0, c0, TN);
-                const bool dg = TN == kM && r0 == c0;
+                const bool dg = DG || (TN == kM && r0 == c0);
                 for (u64 q = 0; q < len; ++q, ++t) {
                     const int b = (int)(t % kBufs);
                     if (!mbar_wait(&full_bar[b], (u32)((t / kBufs) & 1), budget, abort_v)) { ok = false; break; }
@@ -504,22 +507,29 @@ long long wait_budget(int timeout_ms)
     return (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * (long long)timeout_ms / 1000LL;
 }
 
-template <typename CT, int TN>
+template <typename CT, int TN, bool DG = false>
 cudaError_t launch(const TcJobs& P, int sms, u32* err, int timeout_ms, cudaStream_t st)
 {
-    using S = Shape<TN>;
-    cudaError_t e = cudaFuncSetAttribute(k_prod_tc<CT, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes);
+    using S = Shape<TN, DG>;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_prod_tc<CT, TN, DG>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes);
     if (e != cudaSuccess) return e;
-    k_prod_tc<CT, TN><<<(unsigned)sms, S::kThreads, S::kSmemBytes, st>>>(P, err, wait_budget(timeout_ms));
+    k_prod_tc<CT, TN, DG><<<(unsigned)sms, S::kThreads, S::kSmemBytes, st>>>(P, err, wait_budget(timeout_ms));
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, void* dev_table, bool upload, int count_bits, int sms,
-                            u32* err, int timeout_ms, cudaStream_t st, int* launches, int tile_n)
+                            u32* err, int timeout_ms, cudaStream_t st, int* launches, int tile_n, bool diag_only)
 {
     if (tile_n != 128 && tile_n != 256) return cudaErrorInvalidValue;
+    if (diag_only) {
+        // one 128 x 128 tile per job, on the diagonal
+        if (tile_n != 128) return cudaErrorInvalidValue;
+        for (int q = 0; q < njobs; ++q)
+            if (jobs[q].n > (u64)kM) return cudaErrorInvalidValue;
+    }
     // the table of every job, copied once to device memory (dev_table holds
     // njobs entries of TcJob); one launch per group of kMaxJobs jobs
     static_assert(sizeof(TcJob) == sizeof(TcJobDesc), "table entry layout");
@@ -541,7 +551,10 @@ cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, void* dev_table, b
         P.job = (const TcJob*)dev_table + j0;
         P.njobs = (u32)std::min(kMaxJobs, njobs - j0);
         P.vec16 = vec16;
-        if (tile_n == 128)
+        if (diag_only)
+            e = count_bits == 64 ? launch<u64, 128, true>(P, sms, err, timeout_ms, st)
+                                 : launch<u32, 128, true>(P, sms, err, timeout_ms, st);
+        else if (tile_n == 128)
             e = count_bits == 64 ? launch<u64, 128>(P, sms, err, timeout_ms, st)
                                  : launch<u32, 128>(P, sms, err, timeout_ms, st);
         else

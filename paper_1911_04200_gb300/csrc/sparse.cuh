@@ -461,7 +461,8 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
             // every job is one diagonal 128 x 128 tile: its rows are unpacked
             // once for both operands
             CK(product_tc_jobs(jobs.data(), (int)jobs.size(), jobtab.p, true, ctx->opt.count_bits, ctx->sms,
-                               ctx->d_err, ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000, cs, &launches, 128));
+                               ctx->d_err, ctx->opt.timeout_ms > 0 ? ctx->opt.timeout_ms : 2000, cs, &launches, 128,
+                               true));
             ctx->stats.product_launches += launches;
             ctx->stats.launches += launches;
         }
