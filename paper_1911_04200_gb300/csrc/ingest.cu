@@ -473,17 +473,25 @@ k_pack_classes(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
         u64* rowm = XM ? XM + row * stride_m + v.kbase[0] : nullptr;
         u64* rows = XS + row * stride_s + v.kbase[cs];
         const u64 bm0 = blk0, bms = cs * v.nwords / kScanBlockWords;
-        for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
-            const u64 pos = base + (threadIdx.x & 31);
-            u64 key = ~0ull, bit = 0ull;
-            if (pos < p1) {
-                const u64 d = __ldcs(ids + pos) - lo;  // read once: evict first
-                if (d < width) {
-                    const u64 w0 = d >> 6, sh = d & 63, low = (1ull << sh) - 1ull;
-                    const u64 m0 = v.cls[w0];
-                    if ((m0 >> sh) & 1ull) {
+        // two 32-value groups per warp in flight: both groups' values and
+        // class-0 words are loaded before either is used
+        for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += 2 * kIngestThreads) {
+            const u64 posA = base + (threadIdx.x & 31), posB = posA + kIngestThreads;
+            u64 d[2] = {~0ull, ~0ull};
+            if (posA < p1) d[0] = __ldcs(ids + posA) - lo;
+            if (posB < p1) d[1] = __ldcs(ids + posB) - lo;
+            u64 m0[2] = {0ull, 0ull};
+            #pragma unroll
+            for (int g = 0; g < 2; ++g)
+                if (d[g] < width) m0[g] = v.cls[d[g] >> 6];
+            #pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                u64 key = ~0ull, bit = 0ull;
+                if (d[g] < width) {
+                    const u64 w0 = d[g] >> 6, sh = d[g] & 63, low = (1ull << sh) - 1ull;
+                    if ((m0[g] >> sh) & 1ull) {
                         const u64 r = v.boff[w0 / kScanBlockWords] - v.boff[bm0] + (u64)v.dir[w0] +
-                                      (u64)__popcll(m0 & low);
+                                      (u64)__popcll(m0[g] & low);
                         key = r >> 6;  // class 0: keys below 2^62
                         bit = 1ull << (r & 63);
                     } else {
@@ -496,11 +504,11 @@ k_pack_classes(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width,
                         }
                     }
                 }
-            }
-            const bool lead = segmented_or<u64>(key, bit);
-            if (lead && bit) {
-                if (key >> 62) atomicOr((unsigned long long*)(rows + (key & ((1ull << 62) - 1))), bit);
-                else atomicOr((unsigned long long*)(rowm + key), bit);
+                const bool lead = segmented_or<u64>(key, bit);
+                if (lead && bit) {
+                    if (key >> 62) atomicOr((unsigned long long*)(rows + (key & ((1ull << 62) - 1))), bit);
+                    else atomicOr((unsigned long long*)(rowm + key), bit);
+                }
             }
         }
         __syncthreads();
