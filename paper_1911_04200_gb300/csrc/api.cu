@@ -207,18 +207,26 @@ void partition_rows(u64 minid, u64 maxid, u64 batch_rows, u64 part, u64 parts, u
     b_end = b_first + (u64)((unsigned __int128)nb * (part + 1) / parts);
 }
 
+}  // namespace
+
 // The plain call over the row batches [b_first + nb * part / parts,
 // b_first + nb * (part + 1) / parts) of the nb batches between the first and
 // the last value (parts = 1: all of them).  counts_only: C gets the part's
 // counts (both triangles, the diagonal from the part's rows only) and J is
 // not formed.
 int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes, double* J, int out_mem,
-                   u64 part, u64 parts, bool counts_only)
+                   u64 part, u64 parts, bool counts_only, bool own_scope)
 {
     int rc = 0;
     CK(cudaSetDevice(ctx->opt.device));
-    CallScope scope(ctx);
-    StageTimer total(ctx, &ctx->stats.ms_total);
+    // a call of its own resets and resolves the statistics; one collection
+    // of a batched call adds to the batched call's
+    std::unique_ptr<CallScope> scope;
+    std::unique_ptr<StageTimer> total;
+    if (own_scope) {
+        scope.reset(new CallScope(ctx));
+        total.reset(new StageTimer(ctx, &ctx->stats.ms_total));
+    }
     const u64 n = sets->n;
     if (n == 0) return JSIM_OK;
     if (n > (1ull << 20)) return JSIM_ERR_ARG;  // n*n outputs must stay addressable
@@ -307,6 +315,7 @@ int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
                 ctx->stats.rows_nonzero += R;
                 ctx->stats.words += W;
                 ctx->stats.bitops_dense += 64.0 * (double)W * (double)n * (double)(n + 1) / 2.0;
+                ctx->stats.bitops_done += 64.0 * (double)W * (double)n * (double)(n + 1) / 2.0;
             }
             if (!has_next || next / mt >= b_end) break;
             lo = next / mt * mt;
@@ -351,7 +360,6 @@ int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
     return JSIM_OK;
 }
 
-}  // namespace
 
 int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes, double* J, int out_mem)
 {
@@ -363,7 +371,7 @@ int jsim_all_pairs(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* size
         (sets->offsets[sets->n] - sets->offsets[0]) * sizeof(u64) > kHostStreamMin &&
         !sparse_may_apply(ctx, sets))
         return jsim_all_pairs_streamed(ctx, sets, C, sizes, J, out_mem, kHostStreamBytes);
-    return all_pairs_impl(ctx, sets, C, sizes, J, out_mem, 0, 1, false);
+    return all_pairs_impl(ctx, sets, C, sizes, J, out_mem, 0, 1, false, true);
 }
 
 int jsim_all_pairs_part(jsim_ctx* ctx, const jsim_sets* sets, uint32_t part, uint32_t parts, void* C,
@@ -374,7 +382,7 @@ int jsim_all_pairs_part(jsim_ctx* ctx, const jsim_sets* sets, uint32_t part, uin
     int rc = check_sets(sets);
     if (rc) return rc;
     if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
-    return all_pairs_impl(ctx, sets, C, sizes, nullptr, out_mem, part, parts, true);
+    return all_pairs_impl(ctx, sets, C, sizes, nullptr, out_mem, part, parts, true, true);
 }
 
 int jsim_partition_batches(uint64_t minid, uint64_t maxid, uint64_t batch_rows, uint32_t part, uint32_t parts,

@@ -254,14 +254,11 @@ void jsim_batched_release(jsim_ctx* ctx)
     }
 }
 
-extern "C" int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint64_t k, void* const* C,
-                                      uint64_t* const* sizes, double* const* J, int out_mem)
+// The batched machinery over k collections (statistics into the caller's
+// scope).
+static int batched_body(jsim_ctx* ctx, const jsim_sets* cols, uint64_t k, void* const* C, uint64_t* const* sizes,
+                        double* const* J, int out_mem)
 {
-    if (!ctx || (!cols && k)) return JSIM_ERR_ARG;
-    if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
-    CK(cudaSetDevice(ctx->opt.device));
-    CallScope scope(ctx);
-    StageTimer total(ctx, &ctx->stats.ms_total);
     if (k == 0) return JSIM_OK;
     const bool dev_out = out_mem == JSIM_MEM_DEVICE;
     const size_t cb = ctx->opt.count_bits == 64 ? 8 : 4;
@@ -587,4 +584,61 @@ replan:
     int rc = finish_stats(ctx, w);
     if (!use_graph) jsim_batched_release(ctx);  // nothing to replay: free the wave now
     return rc;
+}
+
+// Collections the block-sparse product may take (variant AUTO, 256 to 2048
+// samples, tensor cores): they gain more from skipping blocks than from
+// sharing launches, and run as plain calls (which decide, by the sketch,
+// between the block-sparse and the dense product); the others share the
+// batched launches.
+extern "C" int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint64_t k, void* const* C,
+                                      uint64_t* const* sizes, double* const* J, int out_mem)
+{
+    if (!ctx || (!cols && k)) return JSIM_ERR_ARG;
+    if (out_mem != JSIM_MEM_HOST && out_mem != JSIM_MEM_DEVICE) return JSIM_ERR_ARG;
+    CK(cudaSetDevice(ctx->opt.device));
+    CallScope scope(ctx);
+    StageTimer total(ctx, &ctx->stats.ms_total);
+    if (k == 0) return JSIM_OK;
+    for (u64 c = 0; c < k; ++c) {
+        const int rc = check_sets(&cols[c]);
+        if (rc) return rc;
+    }
+    const bool split = ctx->opt.variant == JSIM_VARIANT_AUTO && !ctx->opt.count_useful &&
+                       (ctx->opt.batch_rows == 0 || ctx->opt.batch_rows % (1ull << 18) == 0) &&
+                       product_tc_supported(ctx->opt.device);
+    std::vector<u64> big, rest;
+    for (u64 c = 0; c < k; ++c)
+        (split && cols[c].n >= 256 && cols[c].n <= 2048 ? big : rest).push_back(c);
+    if (big.empty()) return batched_body(ctx, cols, k, C, sizes, J, out_mem);
+    int rc = JSIM_OK;
+    if (!rest.empty()) {
+        std::vector<jsim_sets> rc_cols;
+        std::vector<void*> rc_C;
+        std::vector<uint64_t*> rc_s;
+        std::vector<double*> rc_J;
+        for (u64 c : rest) {
+            rc_cols.push_back(cols[c]);
+            rc_C.push_back(C ? C[c] : nullptr);
+            rc_s.push_back(sizes ? sizes[c] : nullptr);
+            rc_J.push_back(J ? J[c] : nullptr);
+        }
+        rc = batched_body(ctx, rc_cols.data(), rest.size(), C ? rc_C.data() : nullptr, sizes ? rc_s.data() : nullptr,
+                          J ? rc_J.data() : nullptr, out_mem);
+        if (rc) return rc;
+    }
+    // the batched part carried out its dense work; the plain calls add theirs
+    const int wave_variant = ctx->stats.variant;
+    const u64 wave_tile = ctx->stats.tile_n;
+    if (ctx->stats.bitops_done == 0) ctx->stats.bitops_done = ctx->stats.bitops_dense;
+    for (u64 c : big) {
+        rc = all_pairs_impl(ctx, &cols[c], C ? C[c] : nullptr, sizes ? sizes[c] : nullptr, J ? J[c] : nullptr,
+                            out_mem, 0, 1, false, false);
+        if (rc) return rc;
+    }
+    if (!rest.empty()) {
+        ctx->stats.variant = wave_variant;
+        ctx->stats.tile_n = wave_tile;
+    }
+    return JSIM_OK;
 }

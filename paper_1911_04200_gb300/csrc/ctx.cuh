@@ -10,6 +10,11 @@
 using namespace jsim;
 
 struct jsim_ctx;
+// The plain all-pairs call (api.cu).  own_scope = false when it runs as one
+// collection of a batched call, whose statistics it then adds to.
+// (C linkage, as the C-ABI translation unit defines it; not exported)
+extern "C" int all_pairs_impl(jsim_ctx* ctx, const jsim_sets* sets, void* C, uint64_t* sizes, double* J,
+                              int out_mem, u64 part, u64 parts, bool counts_only, bool own_scope);
 // releases the batched-call state (captured graphs and buffers) of a context
 void jsim_batched_release(jsim_ctx* ctx);
 // releases the streamed-call state (pinned staging, copy stream) of a context

@@ -107,3 +107,29 @@ def test_batched_two_or_more_filter(gpu, cols, refs, variant):
         outs = ctx.all_pairs_batched(cols)
     for (C, s, J), ref in zip(outs, refs):
         assert_same((C, s, J), ref)
+
+
+def test_batched_mixes_block_sparse_and_shared_launches(gpu):
+    """With variant AUTO, collections of 256 to 2048 samples run as plain
+    calls (the block-sparse product where the sketch says so) and the others
+    share the batched launches: every result equals the oracle's, with host
+    and device buffers, on a first call and on a replay."""
+    import torch
+    cols = [synth.clade1024(n=300, median=3e3), synth.clade1024(n=260, median=2e3, seed=77)]
+    cols += synth.batched_collections(count=4, n_lo=5, n_hi=120, median=3e3)
+    cols.insert(2, (np.zeros(3, np.uint64), np.zeros(0, np.uint64)))
+    refs = [oracle.all_pairs(o, i) for o, i in cols]
+    with jsim.Context(id_bits=32) as ctx:
+        outs = ctx.all_pairs_batched(cols)
+        st = ctx.stats()
+    for res, ref in zip(outs, refs):
+        assert_same(res, ref)
+    assert st["bitops_done"] <= st["bitops_dense"]
+    dcols = [(torch.from_numpy(o.view(np.int64)).cuda(), torch.from_numpy(i.view(np.int64)).cuda())
+             for o, i in cols]
+    with jsim.Context(id_bits=32) as ctx:
+        for _ in range(2):
+            outs = ctx.all_pairs_batched(dcols)
+            torch.cuda.synchronize()
+            for res, ref in zip(outs, refs):
+                assert_same(res, ref)
