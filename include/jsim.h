@@ -258,7 +258,10 @@ JSIM_API int jsim_partition_batches(uint64_t minid, uint64_t maxid, uint64_t bat
  * of every collection are appended along the word axis on the device; the
  * products of all collections run as one persistent tensor-core launch (up to
  * 256 collections per launch) or, when the tuner measures it faster, one
- * CUDA-core launch per collection.  With variant AUTO the first call for a
+ * CUDA-core launch per collection.  With variant AUTO and device-resident
+ * inputs, collections of 256 to 2048 samples are instead validated first and
+ * then run as jsim_all_pairs does (the block-sparse product where it pays;
+ * their statistics add to the call's).  With variant AUTO the first call for a
  * collection shape times the candidate products and remembers the fastest for
  * the context.  When every input and output is in device memory the launch
  * sequence is captured into a CUDA graph and later calls with the same

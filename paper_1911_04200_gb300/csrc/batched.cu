@@ -19,6 +19,7 @@
 // An autotuner times the candidate products (tcgen05, CUDA-core with 64-bit
 // and 32-bit words) on the first call of a collection shape and keeps the
 // fastest for that shape.
+#include <algorithm>
 #include "ctx.cuh"
 
 namespace {
@@ -587,10 +588,11 @@ replan:
 }
 
 // Collections the block-sparse product may take (variant AUTO, 256 to 2048
-// samples, tensor cores): they gain more from skipping blocks than from
-// sharing launches, and run as plain calls (which decide, by the sketch,
-// between the block-sparse and the dense product); the others share the
-// batched launches.
+// samples, tensor cores, device-resident input): they gain more from
+// skipping blocks than from sharing launches, and run as plain calls (which
+// decide, by the sketch, between the block-sparse and the dense product);
+// the others share the batched launches.  The plain calls' inputs are
+// validated first, so an input error still leaves every output unwritten.
 extern "C" int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint64_t k, void* const* C,
                                       uint64_t* const* sizes, double* const* J, int out_mem)
 {
@@ -610,7 +612,26 @@ extern "C" int jsim_all_pairs_batched(jsim_ctx* ctx, const jsim_sets* cols, uint
     std::vector<u64> big, rest;
     for (u64 c = 0; c < k; ++c)
         (split && cols[c].n >= 256 && cols[c].n <= 2048 ? big : rest).push_back(c);
+    // device-resident inputs only, so that every collection is validated
+    // before any output is written
+    for (u64 c : big)
+        if (cols[c].mem != JSIM_MEM_DEVICE) big.clear();
     if (big.empty()) return batched_body(ctx, cols, k, C, sizes, J, out_mem);
+    for (u64 c : big) {
+        std::vector<u64> hoff;
+        int r = load_offsets(ctx, &cols[c], hoff);
+        if (r) return r;
+        Staged st;
+        r = stage_input(ctx, &cols[c], st, hoff, false);
+        if (r) return r;
+        r = validate_staged(ctx, st, ctx->stream);
+        if (r) return r;
+        r = check_staged(ctx, st);
+        if (r) return r;
+    }
+    rest.clear();
+    for (u64 c = 0; c < k; ++c)
+        if (std::find(big.begin(), big.end(), c) == big.end()) rest.push_back(c);
     int rc = JSIM_OK;
     if (!rest.empty()) {
         std::vector<jsim_sets> rc_cols;

@@ -133,3 +133,23 @@ def test_batched_mixes_block_sparse_and_shared_launches(gpu):
             torch.cuda.synchronize()
             for res, ref in zip(outs, refs):
                 assert_same(res, ref)
+
+
+def test_batched_mixed_input_error_in_a_large_collection(gpu):
+    """An unsorted large collection (a plain call inside the batched call) is
+    reported before anything runs, and the context keeps working."""
+    import torch
+    big_o, big_i = synth.clade1024(n=280, median=2e3)
+    bad_i = big_i.copy()
+    a, b = int(big_o[100]), int(big_o[101])
+    bad_i[b - 3], bad_i[b - 2] = bad_i[b - 2], bad_i[b - 3]
+    small = synth.batched_collections(count=2, n_lo=5, n_hi=60, median=2e3)
+    dev = lambda o, i: (torch.from_numpy(o.view(np.int64)).cuda(), torch.from_numpy(i.view(np.int64)).cuda())
+    with jsim.Context(id_bits=32) as ctx:
+        with pytest.raises(jsim.JsimError) as e:
+            ctx.all_pairs_batched([dev(*small[0]), dev(big_o, bad_i), dev(*small[1])])
+        assert e.value.name == "JSIM_ERR_UNSORTED"
+        outs = ctx.all_pairs_batched([dev(*small[0]), dev(big_o, big_i)])
+        torch.cuda.synchronize()
+    assert_same(outs[0], oracle.all_pairs(*small[0]))
+    assert_same(outs[1], oracle.all_pairs(big_o, big_i))
