@@ -518,14 +518,17 @@ JSIM_API int jsim_threshold(jsim_ctx* ctx, const double* J, uint64_t n, double t
  * that every pair i <= j lies in exactly one tile, that no accumulator holds
  * more stages than the exact-count cap, and that every slot is drained as
  * often as it is committed.
- *   njobs   1..256; grid >= 1
- *   tile_n  the tile width: 256 (tiles of 128 x 256) or 128 (tiles of 128 x 128)
- *   msg     receives a description of the first failed check (cap bytes, may be NULL)
+ *   njobs       1..256; grid >= 1
+ *   tile_n      the tile width: 256 (tiles of 128 x 256) or 128 (tiles of 128 x 128)
+ *   stage_bits  bit-rows per stage: 256 (or 0), or 512 with tile_n 128 (the
+ *               diagonal-only launch of the block-sparse path)
+ *   msg         receives a description of the first failed check (cap bytes, may be NULL)
  * Returns 0 when every check passes, JSIM_ERR_ARG for bad arguments, and a
  * positive check number otherwise.
  */
 JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n, const uint64_t* W, const uint64_t* stride,
-                                    const uint64_t* rows, uint32_t grid, uint32_t tile_n, char* msg, size_t cap);
+                                    const uint64_t* rows, uint32_t grid, uint32_t tile_n, uint32_t stage_bits,
+                                    char* msg, size_t cap);
 
 /* Statistics of the last call on the context. */
 JSIM_API int jsim_get_stats(const jsim_ctx* ctx, jsim_stats* out);

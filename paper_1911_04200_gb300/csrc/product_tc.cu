@@ -71,9 +71,10 @@ constexpr u32 kErrTimeout = 4u;
 // thread per unpacked row (128 + TN), one MMA warp, four epilogue warps; two
 // TMEM accumulators of TN columns.  With TN = 128 a stage is two thirds the
 // size, so three stage buffers fit.  DG (TN = 128): every tile of the launch
-// is diagonal, a stage holds the A rows only, and six buffers keep more
-// stages in flight between the producers and the tensor core.
-template <int TN, bool DG = false>
+// is diagonal and a stage holds the A rows only - of SB = 512 bit-rows (four
+// atom columns, the two producer threads of a row writing two each), so the
+// per-stage costs are paid half as often; three buffers.
+template <int TN, bool DG = false, int SB = kStageBits>
 struct Shape {
     static constexpr int kN = TN;
     static constexpr int kRows = kM + TN;                  // rows unpacked per stage
@@ -83,8 +84,11 @@ struct Shape {
     static constexpr int kWarps = kEpiWarp0 + 4;
     static constexpr int kThreads = kWarps * 32;
     static constexpr int kAtomB = TN * kBlkBytes;          // one atom column of B
-    static constexpr int kStageBytes = DG ? kABytes : kAtoms * kRows * kBlkBytes;
-    static constexpr int kBufs = DG ? 6 : TN == 128 ? 3 : 2;
+    static constexpr int kSB = SB;                         // bit-rows per stage
+    static constexpr int kSW = SB / 64;                    // packed words per stage
+    static constexpr int kAtomsS = SB / 128;               // atom columns per stage
+    static constexpr int kStageBytes = DG ? kAtomsS * kAtomA : kAtoms * kRows * kBlkBytes;
+    static constexpr int kBufs = DG ? 3 : TN == 128 ? 3 : 2;
     static constexpr int kSmemBytes = kBufs * kStageBytes + 1024;  // + alignment slack
     static constexpr int kTmemCols = 2 * TN;               // two TN-column FP32 accumulators
     // instruction descriptor: kind::f8f6f4, D = F32, A = B = E4M3, both
@@ -96,6 +100,7 @@ struct Shape {
     static_assert(kSmemBytes + 9 * 1024 <= 232448, "fits the per-CTA shared-memory limit");
     static_assert(TN == 128 || TN == 256, "tile widths");
     static_assert(!DG || TN == kM, "diagonal-only launches have square tiles");
+    static_assert(SB == kStageBits || (DG && SB == 2 * kStageBits), "512-bit stages for diagonal-only launches");
 };
 
 __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
@@ -179,11 +184,14 @@ struct TcJobs {
     int vec16;  // 16-byte loads are safe for every job
 };
 
-template <typename CT, int TN, bool DG>
-__global__ void __launch_bounds__(Shape<TN, DG>::kThreads, 1)
+template <typename CT, int TN, bool DG, int SB>
+__global__ void __launch_bounds__(Shape<TN, DG, SB>::kThreads, 1)
 k_prod_tc(const TcJobs P, u32* err, long long budget)
 {
-    using S = Shape<TN, DG>;
+    using S = Shape<TN, DG, SB>;
+    constexpr int kSW = S::kSW;                    // packed words per stage
+    constexpr u64 kSeg = (1ull << 22) / SB;        // stages per segment under the exactness cap
+    constexpr bool kWide = SB == 2 * kStageBits;   // a diagonal row split into two halves of two atom columns
     constexpr int kBufs = S::kBufs, kStageBytes = S::kStageBytes, kAtomB = S::kAtomB;
     constexpr int kProducerWarps = S::kProducerWarps, kMmaWarp = S::kMmaWarp, kEpiWarp0 = S::kEpiWarp0;
     constexpr int kTmemCols = S::kTmemCols;
@@ -202,7 +210,7 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         for (u32 j = 0; j < njobs; ++j) {
             const TcJob& J = P.job[j];
             const u64 W = J.Wdev ? *(volatile const u64*)J.Wdev : J.W;
-            const JobInfo x = tcs::job_info(J.n, W, U, TN);
+            const JobInfo x = tcs::job_info(J.n, W, U, TN, kSW);
             U += x.tiles * x.nst;
             ji[j] = x;
         }
@@ -259,6 +267,7 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         // row and column), stage, and stages left in it
         WorkIter fit;
         fit.init(ji, njobs, gridDim.x, blockIdx.x);
+        fit.max_seg = kSeg;
         Seg fs;
         u64 f_key = ~0ull, f_kst = 0, f_left = 0, f_r0 = 0, f_c0 = 0, f_n = 0, f_W = 0, f_stride = 0;
         const u64* f_X = nullptr;
@@ -286,10 +295,14 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                 const u64* src = f_X + grow * f_stride;
                 #pragma unroll
                 for (int q = 0; q < kStageWords; q += 2) {
-                    if (dg && (q >> 1) != (is_a ? 0 : 1)) continue;  // the words of this thread's atom column
+                    // the words of this thread's atom columns: with 256-bit
+                    // stages one column each on a diagonal tile, with 512-bit
+                    // stages the A side's first two and the B side's last two
+                    if (!kWide && dg && (q >> 1) != (is_a ? 0 : 1)) continue;
+                    const int qw = kWide ? q + (is_a ? 0 : kStageWords) : q;
                     u64 w0, w1;
-                    const bool in0 = tcs::fetch_word(f_kst, q, f_W, w0);
-                    const bool in1 = tcs::fetch_word(f_kst, q + 1, f_W, w1);
+                    const bool in0 = tcs::fetch_word(f_kst, qw, f_W, w0, kSW);
+                    const bool in1 = tcs::fetch_word(f_kst, qw + 1, f_W, w1, kSW);
                     if (P.vec16 && in1) {
                         // two words of the stage in one 16-byte load
                         asm volatile("ld.global.nc.v2.u64 {%0,%1}, [%2];\n"
@@ -321,11 +334,13 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                 #pragma unroll
                 for (int at = 0; at < kAtoms; ++at) {
                     // a diagonal tile's rows go to the A operand only (the MMA
-                    // reads them for both), atom column 0 from the A-side
-                    // thread and 1 from the B-side thread of the row
-                    if (diag[a] && at != (is_a ? 0 : 1)) continue;
+                    // reads them for both): with 256-bit stages atom column 0
+                    // from the A-side thread and 1 from the B-side thread of
+                    // the row; with 512-bit stages columns 0-1 and 2-3
+                    if (!kWide && diag[a] && at != (is_a ? 0 : 1)) continue;
+                    const int ga = kWide ? at + (is_a ? 0 : kAtoms) : at;
                     unsigned char* rowp = sm + b * kStageBytes +
-                                          (diag[a] ? (u32)(row * kBlkBytes + at * kAtomA) : row_off + at * atom_step);
+                                          (diag[a] ? (u32)(row * kBlkBytes + ga * kAtomA) : row_off + at * atom_step);
                     #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         // bits 128 at + 16c .. +15 of the stage row -> 16 bytes
@@ -353,8 +368,10 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         if (lane == 0) {
             WorkIter it;
             it.init(ji, njobs, gridDim.x, blockIdx.x);
+            it.max_seg = kSeg;
             Slots sl;
             sl.init();
+            sl.max_seg = kSeg;
             u64 t = 0;
             Seg sg;
             bool ok = true;
@@ -391,7 +408,7 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const u32 abase = base + b * kStageBytes, bbase = dg ? abase : abase + kABytes;
                     #pragma unroll
-                    for (int k = 0; k < kStageBits / 32; ++k) {
+                    for (int k = 0; k < SB / 32; ++k) {
                         // K step k: atom column k / 4, 32-byte slice k % 4
                         u64 da = sw128_desc(abase + (k >> 2) * kAtomA + (k & 3) * 32);
                         u64 db = sw128_desc(bbase + (k >> 2) * kAtomB + (k & 3) * 32);
@@ -455,8 +472,10 @@ k_prod_tc(const TcJobs P, u32* err, long long budget)
         };
         WorkIter it;
         it.init(ji, njobs, gridDim.x, blockIdx.x);
+        it.max_seg = kSeg;
         Slots sl;
         sl.init();
+        sl.max_seg = kSeg;
         Seg sg;
         bool ok = true;
         while (ok && it.next(sg)) {
@@ -507,14 +526,14 @@ long long wait_budget(int timeout_ms)
     return (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * (long long)timeout_ms / 1000LL;
 }
 
-template <typename CT, int TN, bool DG = false>
+template <typename CT, int TN, bool DG = false, int SB = kStageBits>
 cudaError_t launch(const TcJobs& P, int sms, u32* err, int timeout_ms, cudaStream_t st)
 {
-    using S = Shape<TN, DG>;
+    using S = Shape<TN, DG, SB>;
     cudaError_t e =
-        cudaFuncSetAttribute(k_prod_tc<CT, TN, DG>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes);
+        cudaFuncSetAttribute(k_prod_tc<CT, TN, DG, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes);
     if (e != cudaSuccess) return e;
-    k_prod_tc<CT, TN, DG><<<(unsigned)sms, S::kThreads, S::kSmemBytes, st>>>(P, err, wait_budget(timeout_ms));
+    k_prod_tc<CT, TN, DG, SB><<<(unsigned)sms, S::kThreads, S::kSmemBytes, st>>>(P, err, wait_budget(timeout_ms));
     return cudaGetLastError();
 }
 
@@ -552,8 +571,8 @@ cudaError_t product_tc_jobs(const TcJobDesc* jobs, int njobs, void* dev_table, b
         P.njobs = (u32)std::min(kMaxJobs, njobs - j0);
         P.vec16 = vec16;
         if (diag_only)
-            e = count_bits == 64 ? launch<u64, 128, true>(P, sms, err, timeout_ms, st)
-                                 : launch<u32, 128, true>(P, sms, err, timeout_ms, st);
+            e = count_bits == 64 ? launch<u64, 128, true, 2 * kStageBits>(P, sms, err, timeout_ms, st)
+                                 : launch<u32, 128, true, 2 * kStageBits>(P, sms, err, timeout_ms, st);
         else if (tile_n == 128)
             e = count_bits == 64 ? launch<u64, 128>(P, sms, err, timeout_ms, st)
                                  : launch<u32, 128>(P, sms, err, timeout_ms, st);
@@ -610,22 +629,24 @@ struct CheckMsg {
 
 extern "C" JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n, const uint64_t* W,
                                                const uint64_t* stride, const uint64_t* rows, uint32_t grid,
-                                               uint32_t tile_n, char* msg, size_t cap)
+                                               uint32_t tile_n, uint32_t stage_bits, char* msg, size_t cap)
 {
     using namespace jsim;
     using namespace jsim::tcs;
     CheckMsg m{msg, cap};
     if (msg && cap) msg[0] = 0;
+    if (stage_bits == 0) stage_bits = kStageBits;
     if (njobs == 0 || njobs > (uint32_t)kMaxJobs || grid == 0 || !n || !W || !stride || !rows ||
-        (tile_n != 128 && tile_n != 256))
+        (tile_n != 128 && tile_n != 256) || (stage_bits != kStageBits && !(stage_bits == 2 * kStageBits && tile_n == 128)))
         return JSIM_ERR_ARG;
     const u64 kn = tile_n;
+    const u64 sw = stage_bits / 64, max_seg = (1ull << 22) / stage_bits;
     const int kRows = kM + (int)kn;
     std::vector<JobInfo> ji(njobs);
     u64 U = 0;
     for (u32 j = 0; j < njobs; ++j) {
         if (rows[j] < n[j] || (W[j] > stride[j] && n[j] > 0)) return m.fail(1, "job %llu: rows %llu or W beyond stride %llu", j, rows[j], stride[j]);
-        ji[j] = job_info(n[j], W[j], U, kn);
+        ji[j] = job_info(n[j], W[j], U, kn, sw);
         U += ji[j].tiles * ji[j].nst;
     }
     // every (job, tile, stage) unit must be taken exactly once
@@ -655,6 +676,7 @@ extern "C" JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n
         {
             WorkIter fit;
             fit.init(ji.data(), njobs, grid, c);
+            fit.max_seg = max_seg;
             Seg fs{};
             u64 left = 0, kst = 0, r0 = 0, c0 = 0;
             u32 job = 0;
@@ -671,9 +693,9 @@ extern "C" JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n
                 for (int p = 0; p < kRows; ++p) {
                     const u64 grow = fetch_row(p, r0, c0);
                     if (grow >= n[job]) continue;
-                    for (int q = 0; q < kStageWords; ++q) {
+                    for (int q = 0; q < (int)sw; ++q) {
                         u64 w;
-                        if (!fetch_word(kst, q, W[job], w)) continue;
+                        if (!fetch_word(kst, q, W[job], w, sw)) continue;
                         if (grow >= rows[job] || w >= stride[job])
                             return m.fail(6, "cta %llu: read row %llu word %llu outside the matrix", c, grow, w);
                         if ((q & 1) == 0 && stride[job] % 2 == 0 && ((grow * stride[job] + w) & 1))
@@ -688,8 +710,10 @@ extern "C" JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n
         {
             WorkIter it;
             it.init(ji.data(), njobs, grid, c);
+            it.max_seg = max_seg;
             Slots sl;
             sl.init();
+            sl.max_seg = max_seg;
             Seg sg{};
             u64 t = 0;
             u32 commits[2] = {0, 0};
@@ -731,7 +755,7 @@ extern "C" JSIM_API int jsim_check_tc_schedule(uint32_t njobs, const uint64_t* n
                     sl.fill[sidx] = 0;
                 }
                 sl.fill[sidx] += sg.len;
-                if (sl.fill[sidx] > kMaxSegStages)
+                if (sl.fill[sidx] > max_seg)
                     return m.fail(11, "cta %llu: slot %llu holds %llu stages (beyond the exact cap)", c, sidx, sl.fill[sidx]);
                 sl.last = sidx;
                 t += sg.len;

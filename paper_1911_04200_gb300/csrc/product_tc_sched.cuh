@@ -14,6 +14,8 @@ constexpr int kM = 128;                        // A-side rows per tile
 // whose diagonal tiles unpack their rows once for both operands); the kernel
 // and these functions take it as a parameter `kn`.
 constexpr int kStageBits = 256;                // bit-rows per stage: two 128-byte swizzle atom columns
+                                               // (512 for diagonal-only launches: four; the functions
+                                               // below take the stage's words as a parameter)
 constexpr int kStageWords = kStageBits / 64;
 // a segment accumulates at most 2^22 bit-rows (exact FP32 counts)
 constexpr u64 kMaxSegStages = (1ull << 22) / kStageBits;
@@ -54,10 +56,10 @@ struct JobInfo {
     u64 U0;     // first unit of the job in the launch-wide unit order
 };
 
-__host__ __device__ __forceinline__ JobInfo job_info(u64 n, u64 W, u64 U0, u64 kn)
+__host__ __device__ __forceinline__ JobInfo job_info(u64 n, u64 W, u64 U0, u64 kn, u64 sw = kStageWords)
 {
     JobInfo x;
-    x.nst = (W + kStageWords - 1) / kStageWords;
+    x.nst = (W + sw - 1) / sw;  // sw words a stage
     x.tiles = job_tiles(n, x.TM, kn);
     if (x.nst == 0) x.tiles = 0;
     x.U0 = U0;
@@ -85,6 +87,7 @@ struct WorkIter {
     u32 njobs;
     u64 u, uend;
     u32 j;
+    u64 max_seg = kMaxSegStages;  // stages a segment may hold (2^22 bit-rows)
     __host__ __device__ __forceinline__ void init(const JobInfo* ji_, u32 njobs_, u64 G, u64 c)
     {
         ji = ji_; njobs = njobs_;
@@ -110,7 +113,7 @@ struct WorkIter {
             sg.job = j;
             sg.tile = v / J.nst;
             sg.kst = v - sg.tile * J.nst;
-            const u64 e = umin(umin(uend, J.U0 + (sg.tile + 1) * J.nst), u + kMaxSegStages);
+            const u64 e = umin(umin(uend, J.U0 + (sg.tile + 1) * J.nst), u + max_seg);
             sg.len = e - u;
             u = e;
             return true;
@@ -129,6 +132,7 @@ struct Slots {
     u64 fill[2];
     u32 flushes[2];
     int last;
+    u64 max_seg = kMaxSegStages;
     __host__ __device__ __forceinline__ void init()
     {
         tile[0] = tile[1] = ~0ull;
@@ -147,7 +151,7 @@ struct Slots {
     // does slot s have to be flushed before a segment of tile t, len stages?
     __host__ __device__ __forceinline__ bool needs_flush(int s, u64 t, u64 len) const
     {
-        return tile[s] != ~0ull && (tile[s] != t || fill[s] + len > kMaxSegStages);
+        return tile[s] != ~0ull && (tile[s] != t || fill[s] + len > max_seg);
     }
 };
 
@@ -162,9 +166,9 @@ __host__ __device__ __forceinline__ u64 fetch_row(int p, u64 r0, u64 c0)
 // Words q of stage kst that unpack thread p loads: word kst * kStageWords + q
 // of its row, for q with that word < W; a 16-byte load takes q and q + 1 when
 // both are < W (q even) and vec16 holds.  Rows >= n are not read.
-__host__ __device__ __forceinline__ bool fetch_word(u64 kst, int q, u64 W, u64& word)
+__host__ __device__ __forceinline__ bool fetch_word(u64 kst, int q, u64 W, u64& word, u64 sw = kStageWords)
 {
-    word = kst * kStageWords + (u64)q;
+    word = kst * sw + (u64)q;
     return word < W;
 }
 

@@ -56,15 +56,16 @@ def partition_batches(minid: int, maxid: int, batch_rows: int, parts: int):
     return out
 
 
-def check_tc_schedule(jobs, grid: int, tile_n: int = 256):
+def check_tc_schedule(jobs, grid: int, tile_n: int = 256, stage_bits: int = 256):
     """Host-side check of the job-table tensor-core product's schedule for
-    jobs [(n, W, stride, rows), ...] over `grid` CTAs: (code, message), code 0
-    when every check passes (jsim_check_tc_schedule)."""
+    jobs [(n, W, stride, rows), ...] over `grid` CTAs, with stages of
+    `stage_bits` bit-rows: (code, message), code 0 when every check passes
+    (jsim_check_tc_schedule)."""
     lib = load()
     k = len(jobs)
     arr = [(ctypes.c_uint64 * k)(*[int(j[f]) for j in jobs]) for f in range(4)]
     buf = ctypes.create_string_buffer(256)
-    rc = lib.jsim_check_tc_schedule(k, arr[0], arr[1], arr[2], arr[3], grid, tile_n, buf, 256)
+    rc = lib.jsim_check_tc_schedule(k, arr[0], arr[1], arr[2], arr[3], grid, tile_n, stage_bits, buf, 256)
     return rc, buf.value.decode()
 
 
@@ -126,7 +127,7 @@ SIGNATURES = {
     "jsim_check_tc_schedule": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
                                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                               ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint32, ctypes.c_uint32,
-                                              ctypes.c_char_p, ctypes.c_size_t]),
+                                              ctypes.c_uint32, ctypes.c_char_p, ctypes.c_size_t]),
     "jsim_default_options": (None, [ctypes.POINTER(Options)]),
     "jsim_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Options)]),
     "jsim_destroy": (None, [ctypes.c_void_p]),

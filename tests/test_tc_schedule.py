@@ -36,10 +36,12 @@ def test_plain_path_shapes(tile_n):
         assert rc == 0, msg
 
 
-def test_block_sparse_tile_jobs():
+@pytest.mark.parametrize("stage_bits", [256, 512])
+def test_block_sparse_tile_jobs(stage_bits):
     """The block-sparse path's per-tile products: up to 16 jobs of one
     diagonal 128 x 128 tile each (the last one ragged), deep word counts,
-    rows taken from one shared matrix."""
+    rows taken from one shared matrix; the diagonal-only launch's 512-bit
+    stages too (segments cut at 8192 stages)."""
     rng = np.random.default_rng(1)
     for trial in range(12):
         T = int(rng.integers(1, 17))
@@ -48,9 +50,17 @@ def test_block_sparse_tile_jobs():
             W = int(rng.integers(1, 700000))
             m = 128 if t < T - 1 else int(rng.integers(1, 129))
             jobs.append((m, W, -(-W // 1024) * 1024 + 1024, m))
-        for grid in (152, 37):
-            rc, msg = jsim.check_tc_schedule(jobs, grid, 128)
+        for grid in (152, 37, 1):
+            rc, msg = jsim.check_tc_schedule(jobs, grid, 128, stage_bits)
             assert rc == 0, msg
+
+
+def test_512_bit_stages_only_for_128_wide_tiles():
+    rc, _ = jsim.check_tc_schedule([(128, 100, 128, 128)], 4, 256, 512)
+    assert jsim.ERRORS.get(rc) == "JSIM_ERR_ARG"
+    for W in (1, 7, 8, 9, 8191 * 8, 8192 * 8 + 3, 3 * 8192 * 8):
+        rc, msg = jsim.check_tc_schedule([(100, W, -(-W // 64) * 64, 128)], 3, 128, 512)
+        assert rc == 0, msg
 
 
 @pytest.mark.parametrize("tile_n", [256, 128])
