@@ -171,6 +171,8 @@ typedef struct {
     uint64_t h2d_bytes;        /* bytes of its input brought to the device (copies and pieces) */
     uint64_t h2d_pieces;       /* page-locked host input read by the device in this many value-range
                                   pieces while the batch loop ran (0: not fed in pieces) */
+    uint64_t windows;          /* row windows the block-sparse variant's windowed ingest classified and
+                                  packed (0: its per-value ingest ran, or another variant) */
 } jsim_stats;
 
 /* Fill *opt with the defaults described above. */

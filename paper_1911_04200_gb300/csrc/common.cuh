@@ -46,10 +46,11 @@ struct Plan {
     u64* cofs;   // [n+1] exclusive prefix of chunk counts
     u64* totals; // [kPlanTotals] total values, total chunks, first value after the batch, whether one
                  // exists; then the chunk tickets of the kernels that walk the plan (filter, pack,
-                 // validation), zeroed by the plan
+                 // validation) and the windowed ingest's count of class rows, zeroed by the plan
 };
 constexpr u64 kPlanTotals = 8;
 constexpr int kTicketFilter = 4, kTicketPack = 5, kTicketValidate = 6;
+constexpr int kPlanRowsTotal = 7;
 // u64 words of a plan over n samples: beg, len, cofs (n + 1), totals
 __host__ __device__ inline u64 plan_words(u64 n) { return 3 * n + 1 + kPlanTotals; }
 
@@ -60,6 +61,41 @@ __host__ __device__ inline u64 plan_words(u64 n) { return 3 * n + 1 + kPlanTotal
 // slice lengths (n + 1 entries), then `grid` CTAs copy the slices.
 cudaError_t launch_feed_piece(const u64* hv, u64* dv, const u64* off, u64 n, const u64* c0, u64* c1, u64 bound,
                               bool last, u64* pre, int grid, cudaStream_t st);
+
+// ---- windows.cu ------------------------------------------------------------
+// Windowed ingest of the block-sparse path: the batch [lo, lo + nwin 2^wl)
+// of a plan over n samples in tile order (tiles of 128) is cut into nwin
+// windows of 2^wl rows, and the windows into G ranges of wpc (the last one
+// possibly shorter); both passes run one CTA per (range, tile).
+// A range holds at most kWinRangeWords words (of 64 rows) per class: pass 2
+// keeps two classes' words of a range in shared memory.
+constexpr u64 kMaxWinPerRange = 16;
+constexpr u64 kWinRangeWords = 4096;
+struct WinGeom {
+    u64 n, T, lo;
+    u64 nwin, wpc, G;
+    u64 nw;     // words per class bitmap: nwin 2^wl / 64
+    int wl;     // log2 of the rows of a window, 12..16
+};
+// Pass 1: B (B2 with the two-or-more filter; T x nw words, tile-major) = the
+// tiles' filter bitmaps, cls ((T + 1) x nw, class-major) = the class
+// bitmaps, cnt ((T + 1) x nwin) = every window's rows per class, agg
+// ((T + 1) x G) = every range's rows per class rounded up to 64, curs
+// ((G + 1) x n) = every sample's position at each range start and at the
+// batch end; plan.totals[kPlanRowsTotal] += the rows of all classes (zeroed
+// by the plan).
+size_t win_tiles_smem(const WinGeom& g, bool twice);
+cudaError_t launch_win_classes(const u64* ids, Plan plan, const WinGeom& g, bool twice, u64* B, u64* B2, u64* cls,
+                               u32* cnt, u64* agg, u64* curs, cudaStream_t st);
+// Pass 2: with boff the exclusive prefix of agg (class c's range r at
+// boff[c G + r] - boff[c G]), every word of the batch's class-0 part of XM
+// (words [kbase[0], kbase[0] + W_0) of rows 0..n-1; null: no class-0 rows)
+// and of tile t's part of XS (words [kbase[1 + t], ...) of rows 128t..) is
+// stored once, with plain stores.
+size_t win_pack_smem(const WinGeom& g);
+cudaError_t launch_win_pack(const u64* ids, const WinGeom& g, const u64* cls, const u32* cnt, const u64* boff,
+                            const u64* curs, const u64* kbase, u64* XM, u64 stride_m, u64* XS, u64 stride_s,
+                            cudaStream_t st);
 
 // ---- ingest.cu -------------------------------------------------------------
 // perm (optional): entry i of the plan describes sample perm[i].  ends
@@ -93,6 +129,8 @@ cudaError_t launch_filter(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 
 // running word total (kbase = total; total += ceil(R/64)).
 cudaError_t launch_scan(const u64* bitmap, u64 nwords, u32* dir, u64* bsum, u64* boff, u64* R,
                         cudaStream_t st, u64* ktotal = nullptr, u64* kbase = nullptr);
+// boff = exclusive prefix of the nb counts bsum, *R = their total (one CTA)
+cudaError_t launch_scan_top(const u64* bsum, u64 nb, u64* boff, u64* R, cudaStream_t st);
 cudaError_t launch_zero_rows(u64* X, u64 rows, u64 stride, u64 words, int sms, cudaStream_t st);
 // Packing with plain stores: every nonzero word [kbase, kbase + W_l) of rows
 // 0..n-1 (W_l = ceil(*Rdev / 64), device) is written once and complete, into

@@ -594,6 +594,12 @@ cudaError_t launch_scan(const u64* bitmap, u64 nwords, u32* dir, u64* bsum, u64*
     return cudaGetLastError();
 }
 
+cudaError_t launch_scan_top(const u64* bsum, u64 nb, u64* boff, u64* R, cudaStream_t st)
+{
+    k_scan_top<<<1, 1024, 0, st>>>(bsum, nb, boff, R, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_full(const u64* ids, u64 n, Plan plan, u64 max_chunks, u64 lo, u64 width,
                              const u64* bitmap, const u32* dir, const u64* boff, u64* X, u64 stride,
                              const u64* Rdev, int sms, cudaStream_t st, const u64* kbase)

@@ -62,6 +62,11 @@ constexpr double kDenseBitopsPerMs = 1.1e12;
 constexpr double kSparseBitopsPerMs = 0.75e12;
 constexpr double kIngestDenseMs[2] = {2.8e-8, 2.5e-8};
 constexpr double kIngestSparseMs[2] = {2.8e-8, 3.4e-8};
+// Windowed ingest (windows.cu): windows of 2^kWinLog rows, used where a
+// sample has kWinMinValues values in a window on average (below, most of a
+// range's work would go to samples with no value in it).
+constexpr int kWinLog = 16;
+constexpr double kWinMinValues = 0.5;
 
 // Row classes from the tiles' bitmaps: class 0 = rows of two or more tiles,
 // class 1 + t = rows of tile t alone (with the two-or-more filter: rows tile
@@ -226,6 +231,25 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     const u64 mt = feed ? feed->mt : sparse_batch_rows(ctx, n, span);
     if (!mt) return JSIM_ERR_UNSUPPORTED;
     ctx->stats.batch_rows = mt;
+    // Windowed ingest where the values are dense enough for windows of
+    // 2^wl rows (the per-value ingest otherwise).
+    const int wl = kWinLog;
+    const double per_window =
+        st.N ? (double)st.N / (double)n / ((double)span + 1.0) * (double)(1ull << wl) : 0.0;
+    const bool windowed = per_window >= kWinMinValues;
+    auto geom = [&](u64 lo, u64 width) {
+        WinGeom g{};
+        g.n = n;
+        g.T = T;
+        g.lo = lo;
+        g.wl = wl;
+        g.nwin = width >> wl;
+        g.nw = width / 64;
+        g.wpc = std::min<u64>(std::max<u64>(g.nwin, 1), std::min<u64>(kMaxWinPerRange, kWinRangeWords >> (wl - 6)));
+        g.G = (g.nwin + g.wpc - 1) / g.wpc;
+        return g;
+    };
+
     // search bounds of a batch at lo: with a feed, the slices of lo's piece
     const u64* pb = st.d_off;
     const u64* pe = nullptr;
@@ -249,21 +273,34 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     // Two slots of batch structures: the next batch is classified while this
     // one's class totals travel to the host and its pack is enqueued, so the
     // device does not wait for the host between batches.  Slot s reads its
-    // totals back into pinned scalars [64 + 32 s, +21) and uploads its class
-    // bases from [128 + 64 s, +2(T + 1)).
+    // totals back into pinned scalars [64 + 32 s, +22) and uploads its class
+    // bases from [128 + 64 s, +2(T + 1)).  Windowed: bsum holds the ranges'
+    // rows per class, cnt the windows', curs the window-start cursors.
     struct Slot {
-        DevBuf B, B2, cls, dir, bsum, boff, Rd, plan_buf;
+        DevBuf B, B2, cls, dir, bsum, boff, Rd, plan_buf, cnt, curs;
         Plan plan{};
+        WinGeom g{};
         cudaEvent_t done = nullptr;  // totals on the host
         ~Slot() { if (done) cudaEventDestroy(done); }
     } slot[2];
+    const u64 nwin_max = mt >> wl;
+    const u64 ranges_max = nwin_max;  // a range holds one window or more
     for (Slot& x : slot) {
-        ALLOC(x.B, T * nw_max * sizeof(u64));
-        if (twice) ALLOC(x.B2, T * nw_max * sizeof(u64));
         ALLOC(x.cls, (T + 1) * nw_max * sizeof(u64));
-        ALLOC(x.dir, (T + 1) * nw_max * sizeof(u32));
-        ALLOC(x.bsum, nb_max * sizeof(u64));
-        ALLOC(x.boff, (nb_max + 1) * sizeof(u64));
+        if (windowed) {
+            ALLOC(x.B, T * nw_max * sizeof(u64));
+            if (twice) ALLOC(x.B2, T * nw_max * sizeof(u64));
+            ALLOC(x.cnt, (T + 1) * nwin_max * sizeof(u32));
+            ALLOC(x.bsum, (T + 1) * ranges_max * sizeof(u64));
+            ALLOC(x.boff, ((T + 1) * ranges_max + 1) * sizeof(u64));
+            ALLOC(x.curs, (nwin_max + 1) * n * sizeof(u64));
+        } else {
+            ALLOC(x.B, T * nw_max * sizeof(u64));
+            if (twice) ALLOC(x.B2, T * nw_max * sizeof(u64));
+            ALLOC(x.dir, (T + 1) * nw_max * sizeof(u32));
+            ALLOC(x.bsum, nb_max * sizeof(u64));
+            ALLOC(x.boff, (nb_max + 1) * sizeof(u64));
+        }
         ALLOC(x.Rd, sizeof(u64));
         ALLOC(x.plan_buf, plan_words(n) * sizeof(u64));
         x.plan = carve_plan(x.plan_buf, n);
@@ -285,6 +322,33 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
         Slot& x = slot[si];
         const u64 nw = width / 64;
         const u64 hi = lo + width;  // 0 on wrap-around: unbounded
+        u64* hs = ctx->h_scalars + 64 + 32 * si;
+        if (windowed) {
+            {
+                StageTimer t(ctx, &ctx->stats.ms_filter);
+                CK(launch_plan(pb, st.d_ids, n, lo, hi, false, x.plan, cs, d_order.as<u32>(), pe));
+                x.g = geom(lo, width);
+                if (x.g.nwin > nwin_max || x.g.G > ranges_max || x.g.nwin * (1ull << wl) != width)
+                    return JSIM_ERR_UNSUPPORTED;  // the slot's buffers are sized for nwin_max windows
+                CK(launch_win_classes(st.d_ids, x.plan, x.g, twice, x.B.as<u64>(), twice ? x.B2.as<u64>() : nullptr,
+                                      x.cls.as<u64>(), x.cnt.as<u32>(), x.bsum.as<u64>(), x.curs.as<u64>(), cs));
+                ctx->stats.launches += 3;
+                ctx->stats.windows += x.g.nwin;
+            }
+            {
+                StageTimer t(ctx, &ctx->stats.ms_scan);
+                CK(launch_scan_top(x.bsum.as<u64>(), (T + 1) * x.g.G, x.boff.as<u64>(), x.Rd.as<u64>(), cs));
+                ctx->stats.launches += 1;
+            }
+            CK(cudaMemcpy2DAsync(hs, sizeof(u64), x.boff.as<u64>(), x.g.G * sizeof(u64), sizeof(u64), T + 1,
+                                 cudaMemcpyDeviceToHost, cs));
+            CK(cudaMemcpyAsync(hs + 17, x.Rd.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
+            CK(cudaMemcpyAsync(hs + 18, x.plan.totals + 2, 2 * sizeof(u64), cudaMemcpyDeviceToHost, cs));
+            CK(cudaMemcpyAsync(hs + 20, x.plan.totals, sizeof(u64), cudaMemcpyDeviceToHost, cs));
+            CK(cudaMemcpyAsync(hs + 21, x.plan.totals + kPlanRowsTotal, sizeof(u64), cudaMemcpyDeviceToHost, cs));
+            CK(cudaEventRecord(x.done, cs));
+            return JSIM_OK;
+        }
         {
             StageTimer t(ctx, &ctx->stats.ms_filter);
             // the plan lists the samples in their order (entry k: the sample
@@ -308,7 +372,6 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
             ctx->stats.launches += 2;
         }
         // every class's first block offset, the total and the plan's next value
-        u64* hs = ctx->h_scalars + 64 + 32 * si;
         const u64 nb = nw / kScanBlockWords;
         CK(cudaMemcpy2DAsync(hs, sizeof(u64), x.boff.as<u64>(), nb * sizeof(u64), sizeof(u64), T + 1,
                              cudaMemcpyDeviceToHost, cs));
@@ -319,12 +382,18 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
         return JSIM_OK;
     };
     // R_c of the batch in slot s, its plan's next value and its value count
+    // (windowed: rounded up per range) and its rows without the rounding
     std::vector<u64> Rc(T + 1, 0);
-    u64 range_values = 0;
+    u64 range_values = 0, range_rows = 0;
     auto read_classify = [&](int si, bool& has_next, u64& next) -> int {
         CK(cudaEventSynchronize(slot[si].done));
         const u64* hs = ctx->h_scalars + 64 + 32 * si;
-        for (u64 c = 0; c <= T; ++c) Rc[c] = (c < T ? hs[c + 1] : hs[17]) - hs[c];
+        range_rows = 0;
+        for (u64 c = 0; c <= T; ++c) {
+            Rc[c] = (c < T ? hs[c + 1] : hs[17]) - hs[c];
+            range_rows += Rc[c];
+        }
+        if (windowed) range_rows = hs[21];
         next = hs[18];
         has_next = hs[19] != 0;
         range_values = hs[20];
@@ -410,6 +479,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
             const double t_sparse = sparse_bitops / kSparseBitopsPerMs + (double)st.N * kIngestSparseMs[twice];
             if (t_sparse > 0.95 * t_dense) {
                 declined = true;
+                ctx->stats.windows = 0;
                 return JSIM_OK;
             }
         }
@@ -545,7 +615,13 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                 }
                 CK(cudaMemcpyAsync(kbase.p, hk, (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
                 CK(cudaMemcpyAsync(Wc.p, hk + T + 1, (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
-                {
+                if (windowed) {
+                    StageTimer t(ctx, &ctx->stats.ms_pack);
+                    CK(launch_win_pack(st.d_ids, x.g, x.cls.as<u64>(), x.cnt.as<u32>(), x.boff.as<u64>(),
+                                       x.curs.as<u64>(), kbase.as<u64>(), W[0] ? XM.as<u64>() : nullptr, stride_m,
+                                       Wmax_s ? XS.as<u64>() : nullptr, stride_s, cs));
+                    ctx->stats.launches += 1;
+                } else {
                     StageTimer t(ctx, &ctx->stats.ms_pack);
                     if (W[0]) {
                         dim3 g(std::max<unsigned>(1, (unsigned)std::min<u64>((W[0] + 255) / 256, 64)),
@@ -569,11 +645,12 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                 totM += W[0];
                 for (u64 t2 = 0; t2 < T; ++t2) totS[t2] += W[1 + t2];
                 u64 ws_sum = 0;
-                for (u64 t2 = 0; t2 < T; ++t2) ws_sum += W[1 + t2];
-                ctx->stats.pack_bytes += 8 * range_values + 8 * (n_pad * W[0] + kTile * ws_sum);
-                const u64 Wd = (R + 63) / 64;  // the words of the dense packing of the batch
+                for (u64 t2 = 0; t2 < T; ++t2)
+                    ws_sum += (windowed ? std::min<u64>(kTile, n - t2 * kTile) : kTile) * W[1 + t2];
+                ctx->stats.pack_bytes += 8 * range_values + 8 * ((windowed ? n : n_pad) * W[0] + ws_sum);
+                const u64 Wd = (range_rows + 63) / 64;  // the words of the dense packing of the batch
                 ctx->stats.batches += 1;
-                ctx->stats.rows_nonzero += R;
+                ctx->stats.rows_nonzero += range_rows;
                 ctx->stats.words += Wd;
                 ctx->stats.bitops_dense += 64.0 * (double)Wd * (double)n * (double)(n + 1) / 2.0;
             }

@@ -94,7 +94,8 @@ class Stats(ctypes.Structure):
                 ("pack_bytes", ctypes.c_uint64),
                 ("h2d_copies", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64),
-                ("h2d_pieces", ctypes.c_uint64)]
+                ("h2d_pieces", ctypes.c_uint64),
+                ("windows", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
