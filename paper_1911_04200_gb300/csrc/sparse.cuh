@@ -232,11 +232,16 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     if (!mt) return JSIM_ERR_UNSUPPORTED;
     ctx->stats.batch_rows = mt;
     // Windowed ingest where the values are dense enough for windows of
-    // 2^wl rows (the per-value ingest otherwise).
+    // 2^wl rows, on device-resident input (the per-value ingest otherwise).
+    // Input fed piece by piece keeps the per-value ingest: the windowed
+    // kernels hold an SM's registers for tens of microseconds per CTA, which
+    // holds back the copy CTAs that feed the link (measured on the default
+    // workload from page-locked host memory: 70 to 75 ms per call windowed,
+    // 67.5 ms per value).
     const int wl = kWinLog;
     const double per_window =
         st.N ? (double)st.N / (double)n / ((double)span + 1.0) * (double)(1ull << wl) : 0.0;
-    const bool windowed = per_window >= kWinMinValues;
+    const bool windowed = per_window >= kWinMinValues && !feed;
     auto geom = [&](u64 lo, u64 width) {
         WinGeom g{};
         g.n = n;

@@ -33,9 +33,9 @@ namespace jsim {
 namespace {
 
 constexpr int kWin1Threads = 256;
-constexpr int kWin1Warps = kWin1Threads / 32;
 constexpr int kSlots1 = 4;        // samples a warp walks at once in pass 1
 constexpr int kClassThreads = 256;
+constexpr u64 kTileRanges = 2;    // consecutive ranges a pass-1 CTA walks
 constexpr int kWin2Threads = 512;
 constexpr int kWin2Warps = kWin2Threads / 32;
 constexpr int kDepth2 = 4;        // 32-value chunks of a sample a warp loads at once in pass 2
@@ -58,116 +58,130 @@ __device__ __forceinline__ void prefetch_values(const u64* ids, u64 p, u64 e)
     if (p + 16 < e) asm volatile("prefetch.global.L2 [%0];" ::"l"(ids + p + 16));
 }
 
-// Pass 1: CTA (range r, tile t) = blockIdx.x (r * T + t) sets the rows of
-// the range that tile t's samples hold (Eq. 5 over the tile; TWICE: also
-// the rows two or more of them hold) in shared memory and stores the
-// bitmaps to B (and B2), tile-major.  Shared memory: the bitmaps, then the
-// tile's cursors and ends.  A warp walks kSlots1 samples at once, 32
-// consecutive values of each per step, and takes the next sample of its
-// share when one leaves the range.
+// Pass 1: CTA (range group rq, tile t) = blockIdx.x (rq * T + t) walks
+// tile t's samples through ranges kTileRanges rq .. kTileRanges rq +
+// kTileRanges - 1 in turn: per range it sets the rows that the tile's
+// samples hold (Eq. 5 over the tile; TWICE: also the rows two or more of
+// them hold) in shared memory and stores the bitmaps to B (and B2),
+// tile-major.  Only the group's first range needs its cursors found by
+// search; the next range starts where the walk stopped.  Shared memory: the
+// bitmaps, then the tile's cursors and ends.  A warp walks kSlots1 samples
+// at once, 32 consecutive values of each per step, and takes the next
+// sample when one leaves the range.
 template <bool TWICE>
-__global__ void __launch_bounds__(kWin1Threads)
+__global__ void __launch_bounds__(kWin1Threads, 4)
 k_win_tiles(const u64* __restrict__ ids, Plan plan, WinGeom g, u64* __restrict__ B, u64* __restrict__ B2,
             u64* __restrict__ curs)
 {
     extern __shared__ __align__(16) unsigned char win_smem[];
-    const u64 r = blockIdx.x / g.T, t = blockIdx.x % g.T;
-    const u64 w0 = r * g.wpc, w1 = min(w0 + g.wpc, g.nwin);
-    const u64 rows_r = (w1 - w0) << g.wl, RW32 = rows_r >> 5, RW64 = rows_r >> 6;
+    const u64 rq = blockIdx.x / g.T, t = blockIdx.x % g.T;
     u32* bm = reinterpret_cast<u32*>(win_smem);
     u32* bm2 = bm + (g.wpc << (g.wl - 5));
     u64* cur = reinterpret_cast<u64*>(bm + (TWICE ? 2 : 1) * (g.wpc << (g.wl - 5)));
     u64* cend = cur + kWinTile;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const u64 k0 = t * kWinTile, m = min(kWinTile, g.n - k0);
-    const u64 rlo = g.lo + (w0 << g.wl);
-
-    {
-        uint4* z = reinterpret_cast<uint4*>(bm);
-        const u64 nz = (TWICE ? 2 : 1) * RW32 / 4;
-        for (u64 i = tid; i < nz; i += kWin1Threads) z[i] = make_uint4(0u, 0u, 0u, 0u);
-    }
     __shared__ u32 s_next;
-    if (tid == 0) s_next = 0;
-    for (u64 kk = tid; kk < m; kk += kWin1Threads) {
-        const u64 b = plan.beg[k0 + kk], e = b + plan.len[k0 + kk];
-        const u64 c = w0 == 0 ? b : lower_bound_u64(ids, b, e, rlo);
-        cur[kk] = c;
-        cend[kk] = e;
-        curs[r * g.n + k0 + kk] = c;
-    }
-    __syncthreads();
-    for (u64 kk = warp + (u64)lane * kWin1Warps; kk < m; kk += 32 * (u64)kWin1Warps)
-        prefetch_values(ids, cur[kk], cend[kk]);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const u64 k0 = t * kWinTile, m = min(kWinTile, g.n - k0);
+    const u64 r_end = min(rq * kTileRanges + kTileRanges, g.G);
 
-    // samples go to warps as they free a slot (sizes vary by two decades)
-    u64 ks[kSlots1], ps[kSlots1], es[kSlots1], prev[kSlots1];
-    bool act[kSlots1], hp[kSlots1];
-    auto take = [&](int s) {
-        u32 e = 0;
-        if (lane == 0) e = atomicAdd(&s_next, 1u);
-        e = __shfl_sync(0xffffffffu, e, 0);
-        act[s] = e < m;
-        ks[s] = e;
-        ps[s] = act[s] ? cur[e] : 0;
-        es[s] = act[s] ? cend[e] : 0;
-        hp[s] = false;  // the value before a range's first one is below it (sorted input)
-        prev[s] = 0;
-    };
-    #pragma unroll
-    for (int s = 0; s < kSlots1; ++s) take(s);
-    for (;;) {
-        bool any = false;
-        #pragma unroll
-        for (int s = 0; s < kSlots1; ++s) any = any || act[s];
-        if (!any) break;
-        u64 x[kSlots1];
-        #pragma unroll
-        for (int s = 0; s < kSlots1; ++s) {
-            const u64 pos = ps[s] + (u64)lane;
-            x[s] = (act[s] && pos < es[s]) ? ids[pos] : 0ull;
+    for (u64 r = rq * kTileRanges; r < r_end; ++r) {
+        const u64 w0 = r * g.wpc, w1 = min(w0 + g.wpc, g.nwin);
+        const u64 rows_r = (w1 - w0) << g.wl, RW64 = rows_r >> 6;
+        const u64 rlo = g.lo + (w0 << g.wl);
+        {
+            uint4* z = reinterpret_cast<uint4*>(bm);
+            const u64 nz = (TWICE ? 2 : 1) * (g.wpc << (g.wl - 5)) / 4;
+            for (u64 i = tid; i < nz; i += kWin1Threads) z[i] = make_uint4(0u, 0u, 0u, 0u);
         }
+        if (tid == 0) s_next = 0;
+        for (u64 kk = tid; kk < m; kk += kWin1Threads) {
+            u64 c;
+            if (r == rq * kTileRanges) {
+                const u64 b = plan.beg[k0 + kk], e = b + plan.len[k0 + kk];
+                c = w0 == 0 ? b : lower_bound_u64(ids, b, e, rlo);
+                cur[kk] = c;
+                cend[kk] = e;
+            } else {
+                c = cur[kk];
+            }
+            curs[r * g.n + k0 + kk] = c;
+        }
+        __syncthreads();
+        for (u64 kk = tid; kk < m; kk += kWin1Threads) prefetch_values(ids, cur[kk], cend[kk]);
+
+        // samples go to warps as they free a slot (sizes vary by two decades)
+        u64 ks[kSlots1], ps[kSlots1], es[kSlots1], prev[kSlots1];
+        bool act[kSlots1], hp[kSlots1];
+        auto take = [&](int s) {
+            u32 e = 0;
+            if (lane == 0) e = atomicAdd(&s_next, 1u);
+            e = __shfl_sync(0xffffffffu, e, 0);
+            act[s] = e < m;
+            ks[s] = e;
+            ps[s] = act[s] ? cur[e] : 0;
+            es[s] = act[s] ? cend[e] : 0;
+            hp[s] = false;  // the value before a range's first one is below it (sorted input)
+            prev[s] = 0;
+        };
         #pragma unroll
-        for (int s = 0; s < kSlots1; ++s) {
-            if (!act[s]) continue;
-            const u64 pos = ps[s] + (u64)lane, v = x[s], d = v - rlo;
-            // the values from the first one at or past the range's end stay for
-            // the next range (a value below it only comes from unsorted input,
-            // and is passed over)
-            const bool stop = pos >= es[s] || (v >= rlo && d >= rows_r);
-            const unsigned bal = __ballot_sync(0xffffffffu, stop);
-            const int run = bal ? __ffs((int)bal) - 1 : 32;
-            if (TWICE) {
-                const u64 pv = __shfl_up_sync(0xffffffffu, v, 1);
-                const u64 lastv = __shfl_sync(0xffffffffu, v, 31);
-                const bool dup = lane ? pv == v : (hp[s] && prev[s] == v);
-                if (lane < run && v >= rlo && !dup) {
-                    const u32 bit = 1u << (d & 31);
-                    const u32 old = atomicOr(bm + (d >> 5), bit);
-                    if (old & bit) atomicOr(bm2 + (d >> 5), bit);
+        for (int s = 0; s < kSlots1; ++s) take(s);
+        for (;;) {
+            bool any = false;
+            #pragma unroll
+            for (int s = 0; s < kSlots1; ++s) any = any || act[s];
+            if (!any) break;
+            u64 x[kSlots1];
+            #pragma unroll
+            for (int s = 0; s < kSlots1; ++s) {
+                const u64 pos = ps[s] + (u64)lane;
+                x[s] = (act[s] && pos < es[s]) ? ids[pos] : 0ull;
+            }
+            #pragma unroll
+            for (int s = 0; s < kSlots1; ++s) {
+                if (!act[s]) continue;
+                const u64 pos = ps[s] + (u64)lane, v = x[s], d = v - rlo;
+                // the values from the first one at or past the range's end stay for
+                // the next range (a value below it only comes from unsorted input,
+                // and is passed over)
+                const bool stop = pos >= es[s] || (v >= rlo && d >= rows_r);
+                const unsigned bal = __ballot_sync(0xffffffffu, stop);
+                const int run = bal ? __ffs((int)bal) - 1 : 32;
+                if (TWICE) {
+                    const u64 pv = __shfl_up_sync(0xffffffffu, v, 1);
+                    const u64 lastv = __shfl_sync(0xffffffffu, v, 31);
+                    const bool dup = lane ? pv == v : (hp[s] && prev[s] == v);
+                    if (lane < run && v >= rlo && !dup) {
+                        const u32 bit = 1u << (d & 31);
+                        const u32 old = atomicOr(bm + (d >> 5), bit);
+                        if (old & bit) atomicOr(bm2 + (d >> 5), bit);
+                    }
+                    hp[s] = true;
+                    prev[s] = lastv;
+                } else if (lane < run && v >= rlo) {
+                    atomicOr(bm + (d >> 5), 1u << (d & 31));
                 }
-                hp[s] = true;
-                prev[s] = lastv;
-            } else if (lane < run && v >= rlo) {
-                atomicOr(bm + (d >> 5), 1u << (d & 31));
-            }
-            ps[s] += (u64)run;
-            if (run < 32) {
-                // the last range's ends close pass 2's segments (every other
-                // range's CTA finds its own first cursors)
-                if (lane == 0 && r + 1 == g.G) curs[(r + 1) * g.n + k0 + ks[s]] = ps[s];
-                take(s);
+                ps[s] += (u64)run;
+                if (run < 32) {
+                    if (lane == 0) {
+                        cur[ks[s]] = ps[s];  // the next range of the group starts here
+                        // the last range's ends close pass 2's segments (every other
+                        // group's CTA finds its own first cursors)
+                        if (r + 1 == g.G) curs[(r + 1) * g.n + k0 + ks[s]] = ps[s];
+                    }
+                    take(s);
+                }
             }
         }
-    }
-    __syncthreads();
-    const u64* b64 = reinterpret_cast<const u64*>(bm);
-    u64* out = B + t * g.nw + (w0 << (g.wl - 6));
-    for (u64 j = tid; j < RW64; j += kWin1Threads) out[j] = b64[j];
-    if (TWICE) {
-        const u64* c64 = reinterpret_cast<const u64*>(bm2);
-        u64* out2 = B2 + t * g.nw + (w0 << (g.wl - 6));
-        for (u64 j = tid; j < RW64; j += kWin1Threads) out2[j] = c64[j];
+        __syncthreads();
+        const u64* b64 = reinterpret_cast<const u64*>(bm);
+        u64* out = B + t * g.nw + (w0 << (g.wl - 6));
+        for (u64 j = tid; j < RW64; j += kWin1Threads) out[j] = b64[j];
+        if (TWICE) {
+            const u64* c64 = reinterpret_cast<const u64*>(bm2);
+            u64* out2 = B2 + t * g.nw + (w0 << (g.wl - 6));
+            for (u64 j = tid; j < RW64; j += kWin1Threads) out2[j] = c64[j];
+        }
+        __syncthreads();  // the bitmaps are cleared and the cursors read for the next range
     }
 }
 
@@ -420,7 +434,7 @@ cudaError_t launch_win_classes(const u64* ids, Plan plan, const WinGeom& g, bool
 {
     if (g.G == 0) return cudaSuccess;
     const size_t smem = win_tiles_smem(g, twice);
-    const unsigned grid = (unsigned)(g.G * g.T);
+    const unsigned grid = (unsigned)((g.G + kTileRanges - 1) / kTileRanges * g.T);
     cudaError_t e;
     if (twice) {
         e = cudaFuncSetAttribute(k_win_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -2,7 +2,8 @@
 path: the device reads the values in value-range pieces (one slice of every
 sample per piece) while the batch loop runs on the pieces already there,
 and the input is validated once it is all in.  Results are bit-identical to the same call
-on device-resident input (itself checked against the oracle elsewhere) and
+on device-resident input (which takes the windowed ingest where the fed call takes the
+per-value one; itself checked against the oracle elsewhere) and
 agree with the oracle on sampled pairs and every size; bad input (a descent
 in a late piece, a value beyond id_bits) is reported before any output is
 written; a collection where the automatic choice declines the block-sparse
@@ -27,12 +28,12 @@ def device_call(off, ids, **kw):
     d_ids = torch.from_numpy(ids.view(np.int64)).cuda()
     with jsim.Context(**kw) as ctx:
         C, s, J = ctx.all_pairs(d_off, d_ids)
-        v = ctx.stats()["variant"]
+        st = ctx.stats()
         torch.cuda.synchronize()
         dt = torch.int64 if kw.get("count_bits") == 64 else torch.int32
         ndt = np.uint64 if kw.get("count_bits") == 64 else np.uint32
         return (C.view(dt).cpu().numpy().view(ndt), s.view(torch.int64).cpu().numpy().view(np.uint64),
-                J.cpu().numpy(), v)
+                J.cpu().numpy(), st)
 
 
 def sampled(off, ids, C, s, J, pairs=256, distance=False):
@@ -67,8 +68,11 @@ def test_fed_input_equals_device_input(gpu, clades, kw):
     assert st["variant"] == "sparse"
     assert st["h2d_pieces"] >= 3, "the values were not fed piece by piece"
     assert st["h2d_bytes"] >= ids.nbytes
-    Cd, sd, Jd, vd = device_call(off, ids, id_bits=32, **kw)
-    assert vd == "sparse"
+    # fed input takes the per-value ingest, device-resident input the
+    # windowed one: the two ingests give the same words
+    assert st["windows"] == 0
+    Cd, sd, Jd, std = device_call(off, ids, id_bits=32, **kw)
+    assert std["variant"] == "sparse" and std["windows"] > 0
     np.testing.assert_array_equal(C, Cd)
     np.testing.assert_array_equal(s, sd)
     np.testing.assert_array_equal(J.view(np.uint64), Jd.view(np.uint64))
@@ -115,8 +119,8 @@ def test_fed_input_auto_declines_to_dense(gpu):
         st = ctx.stats()
     assert st["variant"] != "sparse"
     assert st["h2d_pieces"] >= 3
-    Cd, sd, Jd, vd = device_call(off, ids, **kw)
-    assert vd == st["variant"]
+    Cd, sd, Jd, std = device_call(off, ids, **kw)
+    assert std["variant"] == st["variant"]
     np.testing.assert_array_equal(C, Cd)
     np.testing.assert_array_equal(J.view(np.uint64), Jd.view(np.uint64))
     sampled(off, ids, C, s, J, pairs=64)
