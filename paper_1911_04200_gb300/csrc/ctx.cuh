@@ -140,11 +140,12 @@ struct StageTimer {
     jsim_ctx* ctx;
     cudaEvent_t a = nullptr;
     double* acc;
-    StageTimer(jsim_ctx* c, double* target) : ctx(c), acc(target)
+    cudaStream_t s;  // the stream the stage runs on (the context's by default)
+    StageTimer(jsim_ctx* c, double* target, cudaStream_t on = nullptr) : ctx(c), acc(target), s(on ? on : c->stream)
     {
         if (ctx->opt.profile) {
             a = take_event(ctx);
-            if (a) cudaEventRecord(a, ctx->stream);
+            if (a) cudaEventRecord(a, s);
         }
     }
     void stop()
@@ -152,7 +153,7 @@ struct StageTimer {
         if (a) {
             cudaEvent_t b = take_event(ctx);
             if (b) {
-                cudaEventRecord(b, ctx->stream);
+                cudaEventRecord(b, s);
                 ctx->pending.push_back({a, b, acc});
             }
             a = nullptr;

@@ -285,8 +285,14 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
         DevBuf B, B2, cls, dir, bsum, boff, Rd, plan_buf, cnt, curs;
         Plan plan{};
         WinGeom g{};
-        cudaEvent_t done = nullptr;  // totals on the host
-        ~Slot() { if (done) cudaEventDestroy(done); }
+        cudaEvent_t done = nullptr;    // totals on the host
+        cudaEvent_t packed = nullptr;  // the last pack that read the slot's structures
+        bool pack_pending = false;
+        ~Slot()
+        {
+            if (done) cudaEventDestroy(done);
+            if (packed) cudaEventDestroy(packed);
+        }
     } slot[2];
     const u64 nwin_max = mt >> wl;
     const u64 ranges_max = nwin_max;  // a range holds one window or more
@@ -310,7 +316,37 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
         ALLOC(x.plan_buf, plan_words(n) * sizeof(u64));
         x.plan = carve_plan(x.plan_buf, n);
         CK(cudaEventCreateWithFlags(&x.done, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&x.packed, cudaEventDisableTiming));
     }
+    // Windowed: the batches are classified on a side stream, so the next
+    // batch's classification runs beside this batch's pack (both are bound
+    // by latency and instruction issue, at about half the SMs' issue rate
+    // each); slot s's classification waits for the pack that last read slot
+    // s, and a pack for its slot's classification.  Whatever way the call
+    // returns, the context's stream then waits for the side stream (before
+    // the slots' memory is released on it).
+    cudaStream_t ccs = cs;
+    if (windowed) {
+        int rc = lanes_ensure(ctx, 1);
+        if (rc) return rc;
+        ccs = ctx->lanes[0];
+    }
+    struct Join {
+        cudaStream_t a, b;
+        cudaEvent_t e = nullptr;
+        ~Join()
+        {
+            if (a == b) return;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+                cudaEventRecord(e, b);
+                cudaStreamWaitEvent(a, e, 0);
+                cudaEventDestroy(e);
+            } else {
+                cudaStreamSynchronize(b);
+            }
+            cudaGetLastError();
+        }
+    } join{cs, ccs};
     ALLOC(Wc, (T + 1) * sizeof(u64));
     ALLOC(kbase, (T + 1) * sizeof(u64));
     ALLOC(d_pos, n * sizeof(u32));
@@ -329,29 +365,30 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
         const u64 hi = lo + width;  // 0 on wrap-around: unbounded
         u64* hs = ctx->h_scalars + 64 + 32 * si;
         if (windowed) {
+            x.g = geom(lo, width);
+            if (x.g.nwin > nwin_max || x.g.G > ranges_max || x.g.nwin * (1ull << wl) != width)
+                return JSIM_ERR_UNSUPPORTED;  // the slot's buffers are sized for nwin_max windows
+            if (x.pack_pending) CK(cudaStreamWaitEvent(ccs, x.packed, 0));
             {
-                StageTimer t(ctx, &ctx->stats.ms_filter);
-                CK(launch_plan(pb, st.d_ids, n, lo, hi, false, x.plan, cs, d_order.as<u32>(), pe));
-                x.g = geom(lo, width);
-                if (x.g.nwin > nwin_max || x.g.G > ranges_max || x.g.nwin * (1ull << wl) != width)
-                    return JSIM_ERR_UNSUPPORTED;  // the slot's buffers are sized for nwin_max windows
+                StageTimer t(ctx, &ctx->stats.ms_filter, ccs);
+                CK(launch_plan(pb, st.d_ids, n, lo, hi, false, x.plan, ccs, d_order.as<u32>(), pe));
                 CK(launch_win_classes(st.d_ids, x.plan, x.g, twice, x.B.as<u64>(), twice ? x.B2.as<u64>() : nullptr,
-                                      x.cls.as<u64>(), x.cnt.as<u32>(), x.bsum.as<u64>(), x.curs.as<u64>(), cs));
+                                      x.cls.as<u64>(), x.cnt.as<u32>(), x.bsum.as<u64>(), x.curs.as<u64>(), ccs));
                 ctx->stats.launches += 3;
                 ctx->stats.windows += x.g.nwin;
             }
             {
-                StageTimer t(ctx, &ctx->stats.ms_scan);
-                CK(launch_scan_top(x.bsum.as<u64>(), (T + 1) * x.g.G, x.boff.as<u64>(), x.Rd.as<u64>(), cs));
+                StageTimer t(ctx, &ctx->stats.ms_scan, ccs);
+                CK(launch_scan_top(x.bsum.as<u64>(), (T + 1) * x.g.G, x.boff.as<u64>(), x.Rd.as<u64>(), ccs));
                 ctx->stats.launches += 1;
             }
             CK(cudaMemcpy2DAsync(hs, sizeof(u64), x.boff.as<u64>(), x.g.G * sizeof(u64), sizeof(u64), T + 1,
-                                 cudaMemcpyDeviceToHost, cs));
-            CK(cudaMemcpyAsync(hs + 17, x.Rd.p, sizeof(u64), cudaMemcpyDeviceToHost, cs));
-            CK(cudaMemcpyAsync(hs + 18, x.plan.totals + 2, 2 * sizeof(u64), cudaMemcpyDeviceToHost, cs));
-            CK(cudaMemcpyAsync(hs + 20, x.plan.totals, sizeof(u64), cudaMemcpyDeviceToHost, cs));
-            CK(cudaMemcpyAsync(hs + 21, x.plan.totals + kPlanRowsTotal, sizeof(u64), cudaMemcpyDeviceToHost, cs));
-            CK(cudaEventRecord(x.done, cs));
+                                 cudaMemcpyDeviceToHost, ccs));
+            CK(cudaMemcpyAsync(hs + 17, x.Rd.p, sizeof(u64), cudaMemcpyDeviceToHost, ccs));
+            CK(cudaMemcpyAsync(hs + 18, x.plan.totals + 2, 2 * sizeof(u64), cudaMemcpyDeviceToHost, ccs));
+            CK(cudaMemcpyAsync(hs + 20, x.plan.totals, sizeof(u64), cudaMemcpyDeviceToHost, ccs));
+            CK(cudaMemcpyAsync(hs + 21, x.plan.totals + kPlanRowsTotal, sizeof(u64), cudaMemcpyDeviceToHost, ccs));
+            CK(cudaEventRecord(x.done, ccs));
             return JSIM_OK;
         }
         {
@@ -622,9 +659,12 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                 CK(cudaMemcpyAsync(Wc.p, hk + T + 1, (T + 1) * sizeof(u64), cudaMemcpyHostToDevice, cs));
                 if (windowed) {
                     StageTimer t(ctx, &ctx->stats.ms_pack);
+                    CK(cudaStreamWaitEvent(cs, x.done, 0));
                     CK(launch_win_pack(st.d_ids, x.g, x.cls.as<u64>(), x.cnt.as<u32>(), x.boff.as<u64>(),
                                        x.curs.as<u64>(), kbase.as<u64>(), W[0] ? XM.as<u64>() : nullptr, stride_m,
                                        Wmax_s ? XS.as<u64>() : nullptr, stride_s, cs));
+                    CK(cudaEventRecord(slot[si].packed, cs));
+                    slot[si].pack_pending = true;
                     ctx->stats.launches += 1;
                 } else {
                     StageTimer t(ctx, &ctx->stats.ms_pack);
