@@ -118,6 +118,7 @@ void jsim_destroy(jsim_ctx* ctx)
     if (ctx->d_err) ctx->opt.free(ctx->d_err, 256, (void*)ctx->stream, ctx->opt.alloc_user);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
+    if (ctx->h_sketch) cudaFreeHost(ctx->h_sketch);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);  // released once nothing from it is outstanding

@@ -31,6 +31,9 @@ struct jsim_ctx {
     char cuda_err[256];
     // small pinned host scratch (256 u64) for device <-> host scalars
     unsigned long long* h_scalars;
+    // page-locked scratch for the block-sparse path's sketch similarities (grown on demand)
+    void* h_sketch = nullptr;
+    size_t h_sketch_bytes = 0;
     // device error word of kernels with bounded waits
     unsigned int* d_err;
     // the context's own stream-ordered memory pool (default allocator only)

@@ -136,53 +136,66 @@ unsigned grid_of(u64 items, int sms, unsigned threads)
     return (unsigned)std::max<u64>(1, std::min(g, cap));
 }
 
-// Sample order from sketch counts (n x n, upper triangle and diagonal):
-// J_ij = c / (s_i + s_j - c).  A greedy chain: start at the largest sample;
-// the next sample is the unplaced one with the largest J to any sample
-// already in the current tile of kTile (a new tile starts from its
-// predecessor's similarities); ties go to the smaller index, and a sample
-// sharing nothing with the tile is taken largest first.
-std::vector<u32> sample_order(const std::vector<u64>& Cs, u64 n)
+// Single-precision similarities of the sketch, for ordering the samples:
+// Jf[i][j] = c / (s_i + s_j - c) from the upper-triangle counts (0 on the
+// diagonal and for two empty sketches), and the sketch sizes s_i = C_ii.
+// Sketch counts are far below 2^24, so c and u are exact floats and c / u is
+// one correctly rounded division.
+template <typename CT>
+__global__ void k_sketch_j(const CT* __restrict__ Cs, u64 n, float* __restrict__ Jf, u64* __restrict__ sz)
 {
-    std::vector<float> Jm(n * n, 0.f);
-    for (u64 i = 0; i < n; ++i)
-        for (u64 j = i + 1; j < n; ++j) {
-            const double c = (double)Cs[i * n + j], u = (double)Cs[i * n + i] + (double)Cs[j * n + j] - c;
-            const float v = u > 0 ? (float)(c / u) : 0.f;
-            Jm[i * n + j] = v;
-            Jm[j * n + i] = v;
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < n * n; t += (u64)gridDim.x * blockDim.x) {
+        const u64 i = t / n, j = t - i * n;
+        float v = 0.f;
+        if (i != j) {
+            const u64 a = i < j ? i : j, b = i < j ? j : i;
+            const float c = (float)Cs[a * n + b], u = (float)Cs[i * n + i] + (float)Cs[j * n + j] - c;
+            v = u > 0.f ? __fdiv_rn(c, u) : 0.f;
         }
+        Jf[t] = v;
+        if (i == j) sz[i] = (u64)Cs[t];
+    }
+}
+
+// Sample order from the sketch's similarities Jm (n x n, symmetric) and
+// sizes: a greedy chain.  Start at the largest sample; the next sample is
+// the unplaced one with the largest J to any sample already in the current
+// tile of kTile (a new tile starts from its predecessor's similarities);
+// ties go to the smaller index, and a sample sharing nothing with the tile
+// is taken largest first.  Each step is one pass: the scores take in the
+// last placed sample's similarities and the best unplaced sample is found
+// in the same loop.
+std::vector<u32> sample_order(const float* Jm, const u64* sz, u64 n)
+{
     std::vector<u32> order;
     order.reserve(n);
     std::vector<char> placed(n, 0);
     std::vector<float> score(n, 0.f);
     u64 first = 0;
     for (u64 i = 1; i < n; ++i)
-        if (Cs[i * n + i] > Cs[first * n + first]) first = i;
-    auto place = [&](u64 k, bool fresh) {
-        order.push_back((u32)k);
-        placed[k] = 1;
-        const float* r = &Jm[k * n];
-        if (fresh)
-            for (u64 j = 0; j < n; ++j) score[j] = r[j];
-        else
-            for (u64 j = 0; j < n; ++j) score[j] = std::max(score[j], r[j]);
-    };
-    place(first, true);
+        if (sz[i] > sz[first]) first = i;
+    order.push_back((u32)first);
+    placed[first] = 1;
     for (u64 step = 1; step < n; ++step) {
-        if (step % kTile == 0) {
-            // a new tile: similarities of its predecessor only
-            const float* r = &Jm[(u64)order.back() * n];
-            for (u64 j = 0; j < n; ++j) score[j] = r[j];
-        }
+        // the scores: J to the current tile's samples (a new tile: to its
+        // predecessor only), with the last placed sample taken in now
+        const float* r = Jm + (u64)order.back() * n;
+        const bool fresh = step == 1 || step % kTile == 0;
         u64 best = n;
         float bs = 0.f;
-        for (u64 j = 0; j < n; ++j)
-            if (!placed[j] && score[j] > bs) { bs = score[j]; best = j; }
+        for (u64 j = 0; j < n; ++j) {
+            const float v = fresh ? r[j] : std::max(score[j], r[j]);
+            score[j] = v;
+            if (!placed[j] && v > bs) {
+                bs = v;
+                best = j;
+            }
+        }
         if (best == n)
             for (u64 j = 0; j < n; ++j)
-                if (!placed[j] && (best == n || Cs[j * n + j] > Cs[best * n + best])) best = j;
-        place(best, false);
+                if (!placed[j] && (best == n || sz[j] > sz[best])) best = j;
+        order.push_back((u32)best);
+        placed[best] = 1;
     }
     return order;
 }
@@ -465,17 +478,32 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                 rc = sv->start(ctx, st);
                 if (rc) return rc;
             }
-            std::vector<u64> hc(n * n);
-            if (cb == 8) {
-                CK(cudaMemcpyAsync(hc.data(), Cs.p, n * n * 8, cudaMemcpyDeviceToHost, cs));
-                CK(cudaStreamSynchronize(cs));
-            } else {
-                std::vector<u32> h32(n * n);
-                CK(cudaMemcpyAsync(h32.data(), Cs.p, n * n * 4, cudaMemcpyDeviceToHost, cs));
-                CK(cudaStreamSynchronize(cs));
-                for (u64 k = 0; k < n * n; ++k) hc[k] = h32[k];
+            // the sizes (n u64) and then the similarities (n x n floats) into
+            // page-locked memory kept by the context: the host only runs the
+            // greedy chain
+            const size_t hb = n * sizeof(u64) + n * n * sizeof(float);
+            if (ctx->h_sketch_bytes < hb) {
+                if (ctx->h_sketch) cudaFreeHost(ctx->h_sketch);
+                ctx->h_sketch = nullptr;
+                ctx->h_sketch_bytes = 0;
+                CK(cudaMallocHost(&ctx->h_sketch, hb));
+                ctx->h_sketch_bytes = hb;
             }
-            order = sample_order(hc, n);
+            DevBuf Jf;
+            ALLOC(Jf, hb);
+            const unsigned g = grid_of(n * n, ctx->sms, 256);
+            u64* d_sz = Jf.as<u64>();
+            float* d_jf = (float*)(d_sz + n);
+            if (cb == 8)
+                k_sketch_j<u64><<<g, 256, 0, cs>>>(Cs.as<u64>(), n, d_jf, d_sz);
+            else
+                k_sketch_j<u32><<<g, 256, 0, cs>>>(Cs.as<u32>(), n, d_jf, d_sz);
+            CK(cudaGetLastError());
+            ctx->stats.launches += 1;
+            CK(cudaMemcpyAsync(ctx->h_sketch, Jf.p, hb, cudaMemcpyDeviceToHost, cs));
+            CK(cudaStreamSynchronize(cs));
+            const u64* h_sz = (const u64*)ctx->h_sketch;
+            order = sample_order((const float*)(h_sz + n), h_sz, n);
         }
         for (u64 k = 0; k < n; ++k) pos[order[k]] = (u32)k;
         // per plan entry k (the sample at position k): its tile, class and row
