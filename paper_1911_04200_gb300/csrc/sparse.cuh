@@ -387,7 +387,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                 CK(launch_plan(pb, st.d_ids, n, lo, hi, false, x.plan, ccs, d_order.as<u32>(), pe));
                 CK(launch_win_classes(st.d_ids, x.plan, x.g, twice, x.B.as<u64>(), twice ? x.B2.as<u64>() : nullptr,
                                       x.cls.as<u64>(), x.cnt.as<u32>(), x.bsum.as<u64>(), x.curs.as<u64>(), ccs));
-                ctx->stats.launches += 3;
+                ctx->stats.launches += 4;
                 ctx->stats.windows += x.g.nwin;
             }
             {

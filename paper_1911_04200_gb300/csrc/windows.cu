@@ -10,9 +10,10 @@
 //
 // Pass 1 (k_win_tiles, one CTA per range and tile): the tile's filter
 // bitmap of the range is set in shared memory and stored.  k_win_classify
-// (one CTA per range) classifies the rows - class 0: held by two or more
+// (one CTA per window) classifies the rows - class 0: held by two or more
 // tiles; class 1 + t: by tile t alone (with the two-or-more filter, by two
-// or more of its samples) - and counts every class per window and range.
+// or more of its samples) - and counts every class per window; k_win_agg
+// sums the counts per range.
 //
 // Ranks: a class's rows are numbered in row order, range after range, and
 // each range's count is rounded up to a multiple of 64 - the rows in between
@@ -185,65 +186,66 @@ k_win_tiles(const u64* __restrict__ ids, Plan plan, WinGeom g, u64* __restrict__
     }
 }
 
-// Classes of range r's rows = blockIdx.x from the tiles' bitmaps: class 0
+// Classes of window w's rows = blockIdx.x from the tiles' bitmaps: class 0
 // = rows of two or more tiles, class 1 + t = rows of tile t alone (with the
 // two-or-more filter: rows tile t holds twice or more and no other tile
-// holds); the class words, every window's rows per class, and the range's
-// rows per class rounded up to 64.
-__global__ void __launch_bounds__(kClassThreads)
-k_win_classify(const u64* __restrict__ B, const u64* __restrict__ B2, WinGeom g, Plan plan, u64* __restrict__ cls,
-               u32* __restrict__ cnt, u64* __restrict__ agg)
+// holds); the class words and the window's rows per class.
+__global__ void __launch_bounds__(kClassThreads, 4)
+k_win_classify(const u64* __restrict__ B, const u64* __restrict__ B2, WinGeom g, u64* __restrict__ cls,
+               u32* __restrict__ cnt)
 {
     __shared__ u32 s_cnt[kWinClasses];
     const int tid = threadIdx.x, lane = tid & 31;
-    const u64 r = blockIdx.x, w0 = r * g.wpc, w1 = min(w0 + g.wpc, g.nwin);
-    const u64 W64 = 1ull << (g.wl - 6);
-    u64 acc = 0;  // thread c <= T: the range's rows of class c
-    for (u64 w = w0; w < w1; ++w) {
-        if (tid < kWinClasses) s_cnt[tid] = 0;
-        __syncthreads();
-        u32 c[kWinClasses];
+    const u64 w = blockIdx.x, W64 = 1ull << (g.wl - 6);
+    if (tid < kWinClasses) s_cnt[tid] = 0;
+    __syncthreads();
+    u32 c[kWinClasses];
+    #pragma unroll
+    for (int q = 0; q < kWinClasses; ++q) c[q] = 0;
+    for (u64 j = w * W64 + tid; j < (w + 1) * W64; j += kClassThreads) {
+        u64 ones = 0, twos = 0;
         #pragma unroll
-        for (int q = 0; q < kWinClasses; ++q) c[q] = 0;
-        for (u64 j = w * W64 + tid; j < (w + 1) * W64; j += kClassThreads) {
-            u64 ones = 0, twos = 0;
-            #pragma unroll
-            for (int q = 0; q < kWinClasses - 1; ++q) {
-                if ((u64)q < g.T) {
-                    const u64 v = B[q * g.nw + j];
-                    twos |= ones & v;
-                    ones |= v;
-                }
-            }
-            cls[j] = twos;
-            c[0] += (u32)__popcll(twos);
-            #pragma unroll
-            for (int q = 0; q < kWinClasses - 1; ++q) {
-                if ((u64)q < g.T) {
-                    const u64 v = (B2 ? B2[q * g.nw + j] : B[q * g.nw + j]) & ~twos;
-                    cls[(1 + q) * g.nw + j] = v;
-                    c[1 + q] += (u32)__popcll(v);
-                }
+        for (int q = 0; q < kWinClasses - 1; ++q) {
+            if ((u64)q < g.T) {
+                const u64 v = B[q * g.nw + j];
+                twos |= ones & v;
+                ones |= v;
             }
         }
+        cls[j] = twos;
+        c[0] += (u32)__popcll(twos);
         #pragma unroll
-        for (int q = 0; q < kWinClasses; ++q) {
-            if ((u64)q <= g.T) {
-                const u32 v = warp_sum(c[q]);
-                if (lane == 0 && v) atomicAdd(&s_cnt[q], v);
+        for (int q = 0; q < kWinClasses - 1; ++q) {
+            if ((u64)q < g.T) {
+                const u64 v = (B2 ? B2[q * g.nw + j] : B[q * g.nw + j]) & ~twos;
+                cls[(1 + q) * g.nw + j] = v;
+                c[1 + q] += (u32)__popcll(v);
             }
         }
-        __syncthreads();
-        if ((u64)tid <= g.T) {
-            cnt[tid * g.nwin + w] = s_cnt[tid];
-            acc += s_cnt[tid];
+    }
+    #pragma unroll
+    for (int q = 0; q < kWinClasses; ++q) {
+        if ((u64)q <= g.T) {
+            const u32 v = warp_sum(c[q]);
+            if (lane == 0 && v) atomicAdd(&s_cnt[q], v);
         }
-        __syncthreads();
     }
-    if ((u64)tid <= g.T) {
-        agg[tid * g.G + r] = (acc + 63) / 64 * 64;
-        if (acc) atomicAdd((unsigned long long*)(plan.totals + kPlanRowsTotal), (unsigned long long)acc);
-    }
+    __syncthreads();
+    if ((u64)tid <= g.T) cnt[tid * g.nwin + w] = s_cnt[tid];
+}
+
+// Every range's rows per class, rounded up to 64 (one thread per class and
+// range), and the rows of all classes into plan.totals.
+__global__ void k_win_agg(const u32* __restrict__ cnt, WinGeom g, Plan plan, u64* __restrict__ agg)
+{
+    const u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x;
+    if (i >= (g.T + 1) * g.G) return;
+    const u64 c = i / g.G, r = i - c * g.G;
+    const u64 w0 = r * g.wpc, w1 = min(w0 + g.wpc, g.nwin);
+    u64 s = 0;
+    for (u64 w = w0; w < w1; ++w) s += cnt[c * g.nwin + w];
+    agg[i] = (s + 63) / 64 * 64;
+    if (s) atomicAdd((unsigned long long*)(plan.totals + kPlanRowsTotal), (unsigned long long)s);
 }
 
 // Pass 2 state of one class of a range: the rows' first word of the range
@@ -447,7 +449,10 @@ cudaError_t launch_win_classes(const u64* ids, Plan plan, const WinGeom& g, bool
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_win_classify<<<(unsigned)g.G, kClassThreads, 0, st>>>(B, twice ? B2 : nullptr, g, plan, cls, cnt, agg);
+    k_win_classify<<<(unsigned)g.nwin, kClassThreads, 0, st>>>(B, twice ? B2 : nullptr, g, cls, cnt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_win_agg<<<(unsigned)(((g.T + 1) * g.G + 255) / 256), 256, 0, st>>>(cnt, g, plan, agg);
     return cudaGetLastError();
 }
 
