@@ -936,10 +936,15 @@ def run_jsim(args):
     # matrices filled)
     pk, src = measured_peaks()
     pack_gbs = agg["pack_bytes"] / (agg["ms_pack"] * 1e-3) / 1e9 if agg["ms_pack"] else 0.0
+    # the pack kernel that ran: the windowed one on device-resident input
+    # dense enough for it, else the per-value one of the variant
+    pack_kernel = ("k_win_pack" if last.get("windows") else
+                   "k_pack_classes" if variant == "sparse" else "k_pack_full")
     roof_pack = {"bound": "hbm", "achieved": round(pack_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                  "frac": round(pack_gbs / pk["hbm_gbs"], 4),
-                 "traffic": traffic_from_profiles("pack-" + variant, args.workload),
-                 "kernel": "pack", "peak_source": "%s HBM copy bandwidth" % src,
+                 "traffic": (traffic_from_profiles("pack-" + pack_kernel, args.workload)
+                             if args.filter_min == 1 else None),
+                 "kernel": "pack (%s)" % pack_kernel, "peak_source": "%s HBM copy bandwidth" % src,
                  "unit_bytes": "8 B per value packed + 8 B per word of the packed matrices filled"}
     # the roofline line is the dominant stage's (by time)
     if agg["ms_pack"] > agg["ms_product"]:

@@ -79,23 +79,25 @@ struct WinGeom {
 };
 // Pass 1: B (B2 with the two-or-more filter; T x nw words, tile-major) = the
 // tiles' filter bitmaps, cls ((T + 1) x nw, class-major) = the class
-// bitmaps, cnt ((T + 1) x nwin) = every window's rows per class, agg
+// bitmaps, pre (likewise) = every class word's rank within its window (the
+// class's rows of the window below the word), cnt ((T + 1) x nwin) = every
+// window's rows per class, agg
 // ((T + 1) x G) = every range's rows per class rounded up to 64, curs
 // ((G + 1) x n) = every sample's position at each range start and at the
 // batch end; plan.totals[kPlanRowsTotal] += the rows of all classes (zeroed
 // by the plan).
 size_t win_tiles_smem(const WinGeom& g, bool twice);
 cudaError_t launch_win_classes(const u64* ids, Plan plan, const WinGeom& g, bool twice, u64* B, u64* B2, u64* cls,
-                               u32* cnt, u64* agg, u64* curs, cudaStream_t st);
+                               unsigned short* pre, u32* cnt, u64* agg, u64* curs, cudaStream_t st);
 // Pass 2: with boff the exclusive prefix of agg (class c's range r at
 // boff[c G + r] - boff[c G]), every word of the batch's class-0 part of XM
 // (words [kbase[0], kbase[0] + W_0) of rows 0..n-1; null: no class-0 rows)
 // and of tile t's part of XS (words [kbase[1 + t], ...) of rows 128t..) is
 // stored once, with plain stores.
 size_t win_pack_smem(const WinGeom& g);
-cudaError_t launch_win_pack(const u64* ids, const WinGeom& g, const u64* cls, const u32* cnt, const u64* boff,
-                            const u64* curs, const u64* kbase, u64* XM, u64 stride_m, u64* XS, u64 stride_s,
-                            cudaStream_t st);
+cudaError_t launch_win_pack(const u64* ids, const WinGeom& g, const u64* cls, const unsigned short* pre,
+                            const u32* cnt, const u64* boff, const u64* curs, const u64* kbase, u64* XM, u64 stride_m,
+                            u64* XS, u64 stride_s, cudaStream_t st);
 
 // ---- ingest.cu -------------------------------------------------------------
 // perm (optional): entry i of the plan describes sample perm[i].  ends

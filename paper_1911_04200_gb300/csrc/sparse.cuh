@@ -295,7 +295,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     // bases from [128 + 64 s, +2(T + 1)).  Windowed: bsum holds the ranges'
     // rows per class, cnt the windows', curs the window-start cursors.
     struct Slot {
-        DevBuf B, B2, cls, dir, bsum, boff, Rd, plan_buf, cnt, curs;
+        DevBuf B, B2, cls, dir, bsum, boff, Rd, plan_buf, cnt, curs, pre;
         Plan plan{};
         WinGeom g{};
         cudaEvent_t done = nullptr;    // totals on the host
@@ -315,6 +315,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
             ALLOC(x.B, T * nw_max * sizeof(u64));
             if (twice) ALLOC(x.B2, T * nw_max * sizeof(u64));
             ALLOC(x.cnt, (T + 1) * nwin_max * sizeof(u32));
+            ALLOC(x.pre, (T + 1) * nw_max * sizeof(unsigned short));
             ALLOC(x.bsum, (T + 1) * ranges_max * sizeof(u64));
             ALLOC(x.boff, ((T + 1) * ranges_max + 1) * sizeof(u64));
             ALLOC(x.curs, (nwin_max + 1) * n * sizeof(u64));
@@ -386,7 +387,8 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                 StageTimer t(ctx, &ctx->stats.ms_filter, ccs);
                 CK(launch_plan(pb, st.d_ids, n, lo, hi, false, x.plan, ccs, d_order.as<u32>(), pe));
                 CK(launch_win_classes(st.d_ids, x.plan, x.g, twice, x.B.as<u64>(), twice ? x.B2.as<u64>() : nullptr,
-                                      x.cls.as<u64>(), x.cnt.as<u32>(), x.bsum.as<u64>(), x.curs.as<u64>(), ccs));
+                                      x.cls.as<u64>(), x.pre.as<unsigned short>(), x.cnt.as<u32>(),
+                                      x.bsum.as<u64>(), x.curs.as<u64>(), ccs));
                 ctx->stats.launches += 4;
                 ctx->stats.windows += x.g.nwin;
             }
@@ -688,9 +690,10 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
                 if (windowed) {
                     StageTimer t(ctx, &ctx->stats.ms_pack);
                     CK(cudaStreamWaitEvent(cs, x.done, 0));
-                    CK(launch_win_pack(st.d_ids, x.g, x.cls.as<u64>(), x.cnt.as<u32>(), x.boff.as<u64>(),
-                                       x.curs.as<u64>(), kbase.as<u64>(), W[0] ? XM.as<u64>() : nullptr, stride_m,
-                                       Wmax_s ? XS.as<u64>() : nullptr, stride_s, cs));
+                    CK(launch_win_pack(st.d_ids, x.g, x.cls.as<u64>(), x.pre.as<unsigned short>(), x.cnt.as<u32>(),
+                                       x.boff.as<u64>(), x.curs.as<u64>(), kbase.as<u64>(),
+                                       W[0] ? XM.as<u64>() : nullptr, stride_m, Wmax_s ? XS.as<u64>() : nullptr,
+                                       stride_s, cs));
                     CK(cudaEventRecord(slot[si].packed, cs));
                     slot[si].pack_pending = true;
                     ctx->stats.launches += 1;

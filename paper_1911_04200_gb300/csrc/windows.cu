@@ -36,6 +36,7 @@ namespace {
 constexpr int kWin1Threads = 256;
 constexpr int kSlots1 = 4;        // samples a warp walks at once in pass 1
 constexpr int kClassThreads = 256;
+constexpr int kClassWords = 4;    // words of a window per classify thread (2^16 rows = 256 x 4 words)
 constexpr u64 kTileRanges = 2;    // consecutive ranges a pass-1 CTA walks
 constexpr int kWin2Threads = 512;
 constexpr int kWin2Warps = kWin2Threads / 32;
@@ -189,49 +190,65 @@ k_win_tiles(const u64* __restrict__ ids, Plan plan, WinGeom g, u64* __restrict__
 // Classes of window w's rows = blockIdx.x from the tiles' bitmaps: class 0
 // = rows of two or more tiles, class 1 + t = rows of tile t alone (with the
 // two-or-more filter: rows tile t holds twice or more and no other tile
-// holds); the class words and the window's rows per class.
+// holds); the class words, every word's rank within the window (the class's
+// rows below it, 16 bits: a window has at most 2^16 rows), and the window's
+// rows per class.  Thread i takes the window's words [kClassWords i,
+// kClassWords (i + 1)); the words are formed twice (for the counts, then for
+// the ranks), the second time from tile words still in L1.
 __global__ void __launch_bounds__(kClassThreads, 4)
 k_win_classify(const u64* __restrict__ B, const u64* __restrict__ B2, WinGeom g, u64* __restrict__ cls,
-               u32* __restrict__ cnt)
+               unsigned short* __restrict__ pre, u32* __restrict__ cnt)
 {
-    __shared__ u32 s_cnt[kWinClasses];
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ u64 s_scan[kClassThreads / 32];
+    const int tid = threadIdx.x;
     const u64 w = blockIdx.x, W64 = 1ull << (g.wl - 6);
-    if (tid < kWinClasses) s_cnt[tid] = 0;
-    __syncthreads();
-    u32 c[kWinClasses];
+    const u64 j0 = w * W64 + (u64)tid * kClassWords;
+    const bool mine = (u64)tid * kClassWords < W64;
+    u64 twos[kClassWords];
     #pragma unroll
-    for (int q = 0; q < kWinClasses; ++q) c[q] = 0;
-    for (u64 j = w * W64 + tid; j < (w + 1) * W64; j += kClassThreads) {
-        u64 ones = 0, twos = 0;
-        #pragma unroll
-        for (int q = 0; q < kWinClasses - 1; ++q) {
-            if ((u64)q < g.T) {
-                const u64 v = B[q * g.nw + j];
-                twos |= ones & v;
+    for (int i = 0; i < kClassWords; ++i) {
+        u64 ones = 0, tw = 0;
+        if (mine)
+            for (u64 q = 0; q < g.T; ++q) {
+                const u64 v = B[q * g.nw + j0 + i];
+                tw |= ones & v;
                 ones |= v;
             }
+        twos[i] = tw;
+    }
+    auto word = [&](u64 q, int i) -> u64 {  // class q's word i of this thread
+        if (q == 0) return twos[i];
+        const u64 v = B2 ? B2[(q - 1) * g.nw + j0 + i] : B[(q - 1) * g.nw + j0 + i];
+        return v & ~twos[i];
+    };
+    // counts of this thread's words, three classes to a scan (fields of 21 bits)
+    for (u64 q0 = 0; q0 <= g.T; q0 += 3) {
+        u64 packed = 0;
+        for (u64 f = 0; f < 3 && q0 + f <= g.T; ++f) {
+            u64 sum = 0;
+            if (mine)
+                #pragma unroll
+                for (int i = 0; i < kClassWords; ++i) {
+                    const u64 v = word(q0 + f, i);
+                    cls[(q0 + f) * g.nw + j0 + i] = v;
+                    sum += (u64)__popcll(v);
+                }
+            packed |= sum << (21 * f);
         }
-        cls[j] = twos;
-        c[0] += (u32)__popcll(twos);
-        #pragma unroll
-        for (int q = 0; q < kWinClasses - 1; ++q) {
-            if ((u64)q < g.T) {
-                const u64 v = (B2 ? B2[q * g.nw + j] : B[q * g.nw + j]) & ~twos;
-                cls[(1 + q) * g.nw + j] = v;
-                c[1 + q] += (u32)__popcll(v);
-            }
+        u64 ex;
+        const u64 tot = block_exclusive_scan<kClassThreads>(packed, ex, s_scan);
+        for (u64 f = 0; f < 3 && q0 + f <= g.T; ++f) {
+            const u64 q = q0 + f;
+            u32 run = (u32)((ex >> (21 * f)) & 0x1fffffull);
+            if (mine)
+                #pragma unroll
+                for (int i = 0; i < kClassWords; ++i) {
+                    pre[q * g.nw + j0 + i] = (unsigned short)run;
+                    run += (u32)__popcll(cls[q * g.nw + j0 + i]);
+                }
+            if (tid == 0) cnt[q * g.nwin + w] = (u32)((tot >> (21 * f)) & 0x1fffffull);
         }
     }
-    #pragma unroll
-    for (int q = 0; q < kWinClasses; ++q) {
-        if ((u64)q <= g.T) {
-            const u32 v = warp_sum(c[q]);
-            if (lane == 0 && v) atomicAdd(&s_cnt[q], v);
-        }
-    }
-    __syncthreads();
-    if ((u64)tid <= g.T) cnt[tid * g.nwin + w] = s_cnt[tid];
 }
 
 // Every range's rows per class, rounded up to 64 (one thread per class and
@@ -294,15 +311,15 @@ __device__ __forceinline__ void rc_place(const RangeClass& c, u64* row, u32& blk
 
 // Pass 2: CTA (range r, tile t) = blockIdx.x (r * T + t) packs the tile's
 // samples over the whole range.  Shared memory: the range's class-0 and
-// class-(1 + t) words, their prefix counts within each window, and the
-// staged words of every warp's sample.  A warp packs one sample at a time,
+// class-(1 + t) words, their ranks within each window, and the staged words
+// of every warp's sample.  A warp packs one sample at a time,
 // kDepth2 x 32 consecutive values per step; a sample's ranks run on from
 // window to window, and the range holds whole words, so every word is
 // stored once, by its sample's warp.
 __global__ void __launch_bounds__(kWin2Threads, 2)
-k_win_pack(const u64* __restrict__ ids, WinGeom g, const u64* __restrict__ cls, const u32* __restrict__ cnt,
-           const u64* __restrict__ boff, const u64* __restrict__ curs, const u64* __restrict__ kbase, u64* XM,
-           u64 stride_m, u64* XS, u64 stride_s)
+k_win_pack(const u64* __restrict__ ids, WinGeom g, const u64* __restrict__ cls,
+           const unsigned short* __restrict__ pre, const u32* __restrict__ cnt, const u64* __restrict__ boff,
+           const u64* __restrict__ curs, const u64* __restrict__ kbase, u64* XM, u64 stride_m, u64* XS, u64 stride_s)
 {
     extern __shared__ __align__(16) unsigned char win_smem[];
     const u32 W64 = (u32)(1u << (g.wl - 6));
@@ -324,6 +341,8 @@ k_win_pack(const u64* __restrict__ ids, WinGeom g, const u64* __restrict__ cls, 
     for (u32 j = tid; j < RW; j += kWin2Threads) {
         sW[j] = cls[w0 * W64 + j];
         sW[RW + j] = cls[cl1 * g.nw + w0 * W64 + j];
+        sP[j] = pre[w0 * W64 + j];
+        sP[RW + j] = pre[cl1 * g.nw + w0 * W64 + j];
     }
     if (tid == 0) s_next = 0;
     if (tid < 2) {
@@ -335,24 +354,6 @@ k_win_pack(const u64* __restrict__ ids, WinGeom g, const u64* __restrict__ cls, 
         }
         s_rb[tid] = (boff[c * g.G + r] - boff[c * g.G]) / 64;  // ranges start on whole words
         s_qn[tid] = (s + 63) / 64;
-    }
-    __syncthreads();
-    // prefix counts within each window: one warp per (class, window)
-    for (u32 cw = warp; cw < 2 * nwr; cw += kWin2Warps) {
-        const u64* wd = sW + (u64)(cw / nwr) * RW + (u64)(cw % nwr) * W64;
-        unsigned short* pd = sP + (u64)(cw / nwr) * RW + (u64)(cw % nwr) * W64;
-        u32 carry = 0;
-        for (u32 j = lane; j < W64; j += 32) {
-            const u32 c = (u32)__popcll(wd[j]);
-            u32 x = c;
-            #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const u32 y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            pd[j] = (unsigned short)(carry + x - c);
-            carry += __shfl_sync(0xffffffffu, x, 31);
-        }
     }
     __syncthreads();
 
@@ -432,7 +433,7 @@ size_t win_pack_smem(const WinGeom& g)
 }
 
 cudaError_t launch_win_classes(const u64* ids, Plan plan, const WinGeom& g, bool twice, u64* B, u64* B2, u64* cls,
-                               u32* cnt, u64* agg, u64* curs, cudaStream_t st)
+                               unsigned short* pre, u32* cnt, u64* agg, u64* curs, cudaStream_t st)
 {
     if (g.G == 0) return cudaSuccess;
     const size_t smem = win_tiles_smem(g, twice);
@@ -449,22 +450,22 @@ cudaError_t launch_win_classes(const u64* ids, Plan plan, const WinGeom& g, bool
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_win_classify<<<(unsigned)g.nwin, kClassThreads, 0, st>>>(B, twice ? B2 : nullptr, g, cls, cnt);
+    k_win_classify<<<(unsigned)g.nwin, kClassThreads, 0, st>>>(B, twice ? B2 : nullptr, g, cls, pre, cnt);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_win_agg<<<(unsigned)(((g.T + 1) * g.G + 255) / 256), 256, 0, st>>>(cnt, g, plan, agg);
     return cudaGetLastError();
 }
 
-cudaError_t launch_win_pack(const u64* ids, const WinGeom& g, const u64* cls, const u32* cnt, const u64* boff,
-                            const u64* curs, const u64* kbase, u64* XM, u64 stride_m, u64* XS, u64 stride_s,
-                            cudaStream_t st)
+cudaError_t launch_win_pack(const u64* ids, const WinGeom& g, const u64* cls, const unsigned short* pre,
+                            const u32* cnt, const u64* boff, const u64* curs, const u64* kbase, u64* XM, u64 stride_m,
+                            u64* XS, u64 stride_s, cudaStream_t st)
 {
     if (g.G == 0 || g.T == 0 || (!XM && !XS)) return cudaSuccess;
     const size_t smem = win_pack_smem(g);
     cudaError_t e = cudaFuncSetAttribute(k_win_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_win_pack<<<(unsigned)(g.G * g.T), kWin2Threads, smem, st>>>(ids, g, cls, cnt, boff, curs, kbase, XM,
+    k_win_pack<<<(unsigned)(g.G * g.T), kWin2Threads, smem, st>>>(ids, g, cls, pre, cnt, boff, curs, kbase, XM,
                                                                   stride_m, XS, stride_s);
     return cudaGetLastError();
 }
