@@ -113,6 +113,7 @@ void jsim_destroy(jsim_ctx* ctx)
     jsim_batched_release(ctx);
     jsim_streamed_release(ctx);
     for (cudaStream_t s : ctx->lanes) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    if (ctx->class_stream) { cudaStreamSynchronize(ctx->class_stream); cudaStreamDestroy(ctx->class_stream); }
     for (cudaEvent_t e : ctx->lane_join) cudaEventDestroy(e);
     if (ctx->lane_fork) cudaEventDestroy(ctx->lane_fork);
     if (ctx->d_err) ctx->opt.free(ctx->d_err, 256, (void*)ctx->stream, ctx->opt.alloc_user);

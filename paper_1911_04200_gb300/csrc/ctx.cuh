@@ -34,6 +34,8 @@ struct jsim_ctx {
     // page-locked scratch for the block-sparse path's sketch similarities (grown on demand)
     void* h_sketch = nullptr;
     size_t h_sketch_bytes = 0;
+    // the block-sparse path's classification stream, at the device's highest priority (created on demand)
+    cudaStream_t class_stream = nullptr;
     // device error word of kernels with bounded waits
     unsigned int* d_err;
     // the context's own stream-ordered memory pool (default allocator only)

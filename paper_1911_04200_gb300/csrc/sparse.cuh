@@ -336,14 +336,20 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     // batch's classification runs beside this batch's pack (both are bound
     // by latency and instruction issue, at about half the SMs' issue rate
     // each); slot s's classification waits for the pack that last read slot
-    // s, and a pack for its slot's classification.  Whatever way the call
-    // returns, the context's stream then waits for the side stream (before
-    // the slots' memory is released on it).
+    // s, and a pack for its slot's classification.  The side stream has the
+    // device's highest priority: the pack of a batch waits for the next
+    // classification, so the classification's CTAs go first and the pack
+    // takes the SMs' remaining room.  Whatever way the call returns, the
+    // context's stream then waits for the side stream (before the slots'
+    // memory is released on it).
     cudaStream_t ccs = cs;
     if (windowed) {
-        int rc = lanes_ensure(ctx, 1);
-        if (rc) return rc;
-        ccs = ctx->lanes[0];
+        if (!ctx->class_stream) {
+            int lo_p = 0, hi_p = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&lo_p, &hi_p));
+            CK(cudaStreamCreateWithPriority(&ctx->class_stream, cudaStreamNonBlocking, hi_p));
+        }
+        ccs = ctx->class_stream;
     }
     struct Join {
         cudaStream_t a, b;
