@@ -67,6 +67,7 @@ constexpr double kIngestSparseMs[2] = {2.8e-8, 3.4e-8};
 // range's work would go to samples with no value in it).
 constexpr int kWinLog = 16;
 constexpr double kWinMinValues = 0.5;
+constexpr u64 kWinMaxBatch = 1ull << 30;
 
 // Row classes from the tiles' bitmaps: class 0 = rows of two or more tiles,
 // class 1 + t = rows of tile t alone (with the two-or-more filter: rows tile
@@ -206,16 +207,34 @@ std::vector<u32> sample_order(const float* Jm, const u64* sz, u64 n)
 u64 sparse_matrix_budget(u64 total_bytes) { return std::min<u64>(12ull << 30, total_bytes / 16); }
 
 // Batch width of the block-sparse path for n samples over a value span: a
-// power of two, a whole scan block of every class, all tiles' bitmaps within
-// kTileBitmapBytes (0: the context's batch_rows does not divide into scan
-// blocks).
-u64 sparse_batch_rows(const jsim_ctx* ctx, u64 n, u64 span)
+// power of two and a whole scan block of every class (0: the context's
+// batch_rows does not divide into scan blocks).  Per-value ingest: all
+// tiles' bitmaps within kTileBitmapBytes (they are updated with L2 atomics).
+// Windowed ingest: the span's width up to kWinMaxBatch rows (measured on the
+// default workload: 44.0 / 43.3 / 43.1 / 42.8 ms per call at 2^27 / 2^28 /
+// 2^29 / 2^30 rows - fewer batches, fewer fixed costs), with both slots'
+// batch structures within a sixteenth of the device and a quarter of what is
+// free.
+u64 sparse_batch_rows(const jsim_ctx* ctx, u64 n, u64 span, bool windowed = false)
 {
     const u64 T = (n + kTile - 1) / kTile;
+    const u64 f2 = ctx->opt.filter_min == 2 ? 2 : 1;
     u64 mt = ctx->opt.batch_rows;
     if (mt) return mt % kMinClassRows ? 0 : mt;
+    if (windowed) {
+        mt = kMinClassRows;
+        while (mt < kWinMaxBatch && mt - 1 < span) mt <<= 1;
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); return kMinClassRows; }
+        auto slots_bytes = [&](u64 m) {
+            const u64 nwin = m >> kWinLog;
+            return 2 * (m / 8 * (T * f2 + T + 1) + m / 64 * 2 * (T + 1) + (nwin + 1) * n * 8 + (T + 1) * nwin * 12);
+        };
+        while (mt > kMinClassRows && (slots_bytes(mt) > total_b / 16 || slots_bytes(mt) > free_b / 4)) mt >>= 1;
+        return mt;
+    }
     mt = auto_batch_rows(span + 1 ? span + 1 : ~0ull);
-    while (mt > kMinClassRows && T * (mt / 8) * (ctx->opt.filter_min == 2 ? 2 : 1) > kTileBitmapBytes) mt >>= 1;
+    while (mt > kMinClassRows && T * (mt / 8) * f2 > kTileBitmapBytes) mt >>= 1;
     return std::max(mt, kMinClassRows);
 }
 
@@ -241,9 +260,6 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     const u64 n_pad = round_up(n, kRowPad);
 
     const u64 span = st.N ? st.maxid - st.minid : 0;
-    const u64 mt = feed ? feed->mt : sparse_batch_rows(ctx, n, span);
-    if (!mt) return JSIM_ERR_UNSUPPORTED;
-    ctx->stats.batch_rows = mt;
     // Windowed ingest where the values are dense enough for windows of
     // 2^wl rows, on device-resident input (the per-value ingest otherwise).
     // Input fed piece by piece keeps the per-value ingest: the windowed
@@ -255,6 +271,9 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     const double per_window =
         st.N ? (double)st.N / (double)n / ((double)span + 1.0) * (double)(1ull << wl) : 0.0;
     const bool windowed = per_window >= kWinMinValues && !feed;
+    const u64 mt = feed ? feed->mt : sparse_batch_rows(ctx, n, span, windowed);
+    if (!mt) return JSIM_ERR_UNSUPPORTED;
+    ctx->stats.batch_rows = mt;
     auto geom = [&](u64 lo, u64 width) {
         WinGeom g{};
         g.n = n;
