@@ -37,7 +37,7 @@ constexpr int kWin1Threads = 256;
 constexpr int kSlots1 = 4;        // samples a warp walks at once in pass 1
 constexpr int kClassThreads = 256;
 constexpr int kClassWords = 4;    // words of a window per classify thread (2^16 rows = 256 x 4 words)
-constexpr u64 kTileRanges = 2;    // consecutive ranges a pass-1 CTA walks
+constexpr u64 kTileRanges = 4;    // consecutive ranges a pass-1 CTA walks
 constexpr int kWin2Threads = 512;
 constexpr int kWin2Warps = kWin2Threads / 32;
 constexpr int kDepth2 = 4;        // 32-value chunks of a sample a warp loads at once in pass 2
