@@ -63,23 +63,16 @@ __global__ void __launch_bounds__(kIngestThreads)
 k_validate(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, Plan plan,
            int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, u64 err_stride)
 {
-    __shared__ u64 s_i, s_p0, s_p1, s_c;
+    __shared__ ChunkDesc s_d[2];
     __shared__ u32 s_cnt[kIngestThreads / 32];
     const u64 nch = plan.totals[1];
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const u64 c = next_chunk(plan, kTicketValidate);
-            s_c = c;
-            if (c < nch) {
-                u64 i = chunk_sample(plan.cofs, n, c);
-                u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
-                u64 p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
-                s_i = i; s_p0 = p0; s_p1 = p1;
-            }
-        }
-        __syncthreads();
-        if (s_c >= nch) break;
-        const u64 i = s_i, p0 = s_p0, p1 = s_p1;
+    if (threadIdx.x == 0) fetch_chunk(plan, n, nch, kTicketValidate, s_d[0]);
+    __syncthreads();
+    for (int db = 0;; db ^= 1) {
+        const ChunkDesc d = s_d[db];
+        if (d.c >= nch) break;
+        if (threadIdx.x == 0) fetch_chunk(plan, n, nch, kTicketValidate, s_d[db ^ 1]);
+        const u64 i = d.i, p0 = d.p0, p1 = d.p1;
         const u64 sb = offsets[i], se = offsets[i + 1];
         u32 cnt = 0, flags = 0;
         for (u64 pos = p0 + threadIdx.x; pos < p1; pos += kIngestThreads) {
@@ -122,27 +115,19 @@ __global__ void __launch_bounds__(kIngestThreads)
 k_filter(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, u32* bitmap_all, u32* twice_all,
          const u32* __restrict__ tile_of, u64 tile_words)
 {
-    __shared__ u64 s_p0, s_p1, s_b, s_t, s_c;
+    __shared__ ChunkDesc s_d[2];
     const u64 nch = plan.totals[1];
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const u64 c = next_chunk(plan, kTicketFilter);
-            s_c = c;
-            if (c < nch) {
-                u64 i = chunk_sample(plan.cofs, n, c);
-                u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
-                s_p0 = p0;
-                s_b = plan.beg[i];
-                s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
-                s_t = tile_of ? (u64)tile_of[i] * tile_words : 0ull;
-            }
-        }
-        __syncthreads();
-        if (s_c >= nch) break;
-        const u64 p0 = s_p0, p1 = s_p1, bb = s_b;
+    if (threadIdx.x == 0) fetch_chunk(plan, n, nch, kTicketFilter, s_d[0]);
+    __syncthreads();
+    for (int db = 0;; db ^= 1) {
+        const ChunkDesc d = s_d[db];
+        if (d.c >= nch) break;
+        if (threadIdx.x == 0) fetch_chunk(plan, n, nch, kTicketFilter, s_d[db ^ 1]);
+        const u64 p0 = d.p0, p1 = d.p1, bb = d.b;
         // the sample's own bitmap (one per sample tile when tile_of is given)
-        u32* bitmap = bitmap_all + s_t;
-        u32* twice = twice_all ? twice_all + s_t : nullptr;
+        const u64 toff = tile_of ? (u64)tile_of[d.i] * tile_words : 0ull;
+        u32* bitmap = bitmap_all + toff;
+        u32* twice = twice_all ? twice_all + toff : nullptr;
         // every warp walks whole 32-position groups so shuffles see full warps
         for (u64 base = p0 + (threadIdx.x & ~31u); base < p1; base += kIngestThreads) {
             u64 pos = base + (threadIdx.x & 31);
@@ -451,23 +436,16 @@ __global__ void __launch_bounds__(kIngestThreads)
 k_pack_classes(const u64* __restrict__ ids, u64 n, Plan plan, u64 lo, u64 width, ClassView v, u64* XM,
                u64 stride_m, u64* XS, u64 stride_s)
 {
-    __shared__ u64 s_i, s_p0, s_p1, s_c;
+    __shared__ ChunkDesc s_d[2];
     const u64 nch = plan.totals[1];
     const u64 blk0 = 0;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const u64 c = next_chunk(plan, kTicketPack);
-            s_c = c;
-            if (c < nch) {
-                const u64 i = chunk_sample(plan.cofs, n, c);
-                const u64 p0 = plan.beg[i] + (c - plan.cofs[i]) * kChunk;
-                s_i = i; s_p0 = p0;
-                s_p1 = min(p0 + kChunk, plan.beg[i] + plan.len[i]);
-            }
-        }
-        __syncthreads();
-        if (s_c >= nch) break;
-        const u64 i = s_i, p0 = s_p0, p1 = s_p1;
+    if (threadIdx.x == 0) fetch_chunk(plan, n, nch, kTicketPack, s_d[0]);
+    __syncthreads();
+    for (int db = 0;; db ^= 1) {
+        const ChunkDesc d = s_d[db];
+        if (d.c >= nch) break;
+        if (threadIdx.x == 0) fetch_chunk(plan, n, nch, kTicketPack, s_d[db ^ 1]);
+        const u64 i = d.i, p0 = d.p0, p1 = d.p1;
         const u64 cs = v.cls_of[i];
         const u64 row = v.row_of[i];
         u64* rowm = XM ? XM + row * stride_m + v.kbase[0] : nullptr;

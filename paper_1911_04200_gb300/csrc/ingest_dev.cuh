@@ -69,6 +69,30 @@ __device__ __forceinline__ u64 chunk_sample(const u64* cofs, u64 n, u64 c)
     return lo;
 }
 
+// One chunk of a plan: ticket c (c >= the plan's chunk count: none left),
+// sample i, its values [p0, p1) and the sample's first batch value b.
+struct ChunkDesc {
+    u64 c, i, p0, p1, b;
+};
+
+// Take the next ticket of counter `which` and describe its chunk (one thread).
+// The ticket kernels keep two descriptors in shared memory: thread 0 takes
+// the next chunk's ticket and finds its sample while the CTA works on the
+// current chunk, so the ticket's round trip and the search do not stall it.
+__device__ __forceinline__ void fetch_chunk(const Plan& plan, u64 n, u64 nch, int which, ChunkDesc& d)
+{
+    const u64 c = next_chunk(plan, which);
+    d.c = c;
+    if (c < nch) {
+        const u64 i = chunk_sample(plan.cofs, n, c);
+        const u64 b = plan.beg[i], p0 = b + (c - plan.cofs[i]) * kChunk;
+        d.i = i;
+        d.b = b;
+        d.p0 = p0;
+        d.p1 = min(p0 + kChunk, b + plan.len[i]);
+    }
+}
+
 // Inclusive OR over the lanes that share key q, accumulated toward the
 // segment's first lane (q is non-decreasing across lanes).  Returns true on
 // the lane that must publish the segment's value.
