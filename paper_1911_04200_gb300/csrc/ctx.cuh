@@ -323,16 +323,33 @@ int stage_input(jsim_ctx* ctx, const jsim_sets* s, Staged& st, const std::vector
 
 // Validation of the staged values on stream `vs`: sorted segments, value
 // range, distinct counts per sample (into st.sizes), min and max value.
-int validate_staged(jsim_ctx* ctx, Staged& st, cudaStream_t vs)
+// First the validation's sizes and flags cleared (on vs).
+int validate_init(jsim_ctx* ctx, Staged& st, cudaStream_t vs)
 {
     CK(cudaMemsetAsync(st.sizes.p, 0, st.n * sizeof(u64), vs));
     CK(cudaMemsetAsync(st.flags.p, 0, 2 * sizeof(u64), vs));
     CK(cudaMemsetAsync(st.flags.as<u64>() + 2, 0xff, sizeof(u64), vs));
-    CK(launch_plan(st.d_off, st.d_ids, st.n, 0, 0, true, st.plan, vs));
+    return JSIM_OK;
+}
+
+// Validation of the values [begs[i], ends[i]) of every sample i (on vs;
+// ends null: to the sample's end), adding to the sizes and flags; slices of
+// several calls that tile every sample validate it as one call would (a
+// value is compared with the one before it in its sample, wherever that is).
+int validate_slices(jsim_ctx* ctx, Staged& st, cudaStream_t vs, const u64* begs, const u64* ends)
+{
+    CK(launch_plan(begs, st.d_ids, st.n, 0, 0, true, st.plan, vs, nullptr, ends));
     CK(launch_validate(st.d_off, st.d_ids, st.n, st.plan, st.max_chunks, ctx->opt.id_bits, st.sizes.as<u64>(),
                        st.flags.as<u32>(), st.flags.as<u64>() + 1, st.flags.as<u64>() + 2, ctx->sms, vs));
     ctx->stats.launches += 2;
     return JSIM_OK;
+}
+
+int validate_staged(jsim_ctx* ctx, Staged& st, cudaStream_t vs)
+{
+    int rc = validate_init(ctx, st, vs);
+    if (rc) return rc;
+    return validate_slices(ctx, st, vs, st.d_off, nullptr);
 }
 
 // The validation's verdict (after the context's stream has waited for it):
@@ -376,7 +393,8 @@ struct SideValidation {
         if (validated) cudaEventDestroy(validated);
         cudaGetLastError();
     }
-    int start(jsim_ctx* c, Staged& st, cudaEvent_t after = nullptr)
+    // the side stream, ordered after what the context's stream has enqueued so far
+    int open(jsim_ctx* c)
     {
         ctx = c;
         CK(cudaStreamCreateWithFlags(&vs, cudaStreamNonBlocking));
@@ -384,12 +402,23 @@ struct SideValidation {
         CK(cudaEventCreateWithFlags(&validated, cudaEventDisableTiming));
         CK(cudaEventRecord(ready, ctx->stream));
         CK(cudaStreamWaitEvent(vs, ready, 0));
-        if (after) CK(cudaStreamWaitEvent(vs, after, 0));
-        int rc = validate_staged(ctx, st, vs);
-        if (rc) return rc;
+        return JSIM_OK;
+    }
+    // what the side stream holds so far is the validation
+    int close()
+    {
         CK(cudaEventRecord(validated, vs));
         started = true;
         return JSIM_OK;
+    }
+    int start(jsim_ctx* c, Staged& st, cudaEvent_t after = nullptr)
+    {
+        int rc = open(c);
+        if (rc) return rc;
+        if (after) CK(cudaStreamWaitEvent(vs, after, 0));
+        rc = validate_staged(ctx, st, vs);
+        if (rc) return rc;
+        return close();
     }
     int finish(jsim_ctx* c, Staged& st)
     {

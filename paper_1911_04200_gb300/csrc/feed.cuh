@@ -19,8 +19,9 @@
 // left when it ends.  The ingest kernels take their chunks by ticket, so the
 // CTA slots the copy grid holds delay none of them.
 //
-// The input is validated once, whole, after the last piece has arrived (on a
-// side stream, while the batch loop goes on), and its verdict is read before
+// The input is validated piece by piece as the pieces arrive (on a side
+// stream, while the batch loop goes on; the pieces' slices tile every
+// sample, so every value is checked once), and the verdict is read before
 // any output is written.  Until then the loop relies only on what holds for
 // any input: plans stay inside their slices, the ingest kernels drop values
 // outside the batch, and the batch cursor only moves forward.
@@ -46,7 +47,7 @@ struct InputFeed {
     cudaStream_t xs = nullptr;  // the copy stream
     cudaEvent_t ready = nullptr, t0 = nullptr;
     std::vector<cudaEvent_t> ev;  // piece g on the device
-    SideValidation val;           // of the whole input, once the last piece is in
+    SideValidation val;           // of every piece as it arrives
 
     InputFeed() = default;
     InputFeed(const InputFeed&) = delete;
@@ -120,8 +121,21 @@ struct InputFeed {
             CK(cudaEventRecord(ev[g], xs));
         }
         ctx->stats.launches += 2 * (u64)K;
-        // the whole input validated once it is all in, beside the batch loop
-        return val.start(ctx, st, ev[K - 1]);
+        // every piece validated as it arrives, beside the batch loop: the
+        // pieces' slices tile every sample, so each value is checked once,
+        // against the value before it in its sample (in an earlier piece at a
+        // slice's start), and only the last piece's check is left when the
+        // copy ends
+        int rc = val.open(ctx);
+        if (rc) return rc;
+        rc = validate_init(ctx, st, val.vs);
+        if (rc) return rc;
+        for (int g = 0; g < K; ++g) {
+            CK(cudaStreamWaitEvent(val.vs, ev[g], 0));
+            rc = validate_slices(ctx, st, val.vs, beg(g), end(g));
+            if (rc) return rc;
+        }
+        return val.close();
     }
 
     // the context's stream waits for piece g
