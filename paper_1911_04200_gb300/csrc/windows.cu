@@ -6,14 +6,15 @@
 // A row batch [lo, lo + m) is cut into windows of 2^wl rows and the windows
 // into ranges of up to wpc consecutive windows.  A sample's values are
 // sorted, so a sample's values in a range are one segment, walked by one
-// warp; its start is found by binary search once per range.
+// warp; its start is found by binary search once per group of ranges.
 //
-// Pass 1 (k_win_tiles, one CTA per range and tile): the tile's filter
-// bitmap of the range is set in shared memory and stored.  k_win_classify
-// (one CTA per window) classifies the rows - class 0: held by two or more
-// tiles; class 1 + t: by tile t alone (with the two-or-more filter, by two
-// or more of its samples) - and counts every class per window; k_win_agg
-// sums the counts per range.
+// Pass 1 (k_win_tiles, one CTA per group of kTileRanges ranges and tile):
+// the tile's filter bitmap of each range is set in shared memory and stored.
+// k_win_classify (one CTA per window) classifies the rows - class 0: held by
+// two or more tiles; class 1 + t: by tile t alone (with the two-or-more
+// filter, by two or more of its samples) - and writes every class word's
+// rank within its window and every class's rows per window; k_win_agg sums
+// the counts per range.
 //
 // Ranks: a class's rows are numbered in row order, range after range, and
 // each range's count is rounded up to a multiple of 64 - the rows in between
@@ -22,11 +23,12 @@
 //
 // Pass 2 (k_win_pack, one CTA per range and tile): the tile's samples are
 // packed into the class-0 matrix XM and the tile's matrix XS.  A value's
-// class and rank come from the range's class words and their prefix counts
-// in shared memory; a sample's bits are gathered in shared memory, 32 words
-// at a time, and stored as whole words with plain stores.  Every word of the
-// batch's part of XM and XS is written exactly once, zero words included,
-// so nothing is zeroed beforehand and no global atomics are needed.
+// class and rank come from the range's class words and their window ranks
+// in shared memory; a sample's bits are gathered in shared memory, kStage
+// words at a time, and stored as whole words with plain stores.  Every word
+// of the batch's part of XM and XS is written exactly once, zero words
+// included, so nothing is zeroed beforehand and no global atomics are
+// needed.
 #include "ingest_dev.cuh"
 
 namespace jsim {
@@ -43,15 +45,6 @@ constexpr int kWin2Warps = kWin2Threads / 32;
 constexpr int kDepth2 = 4;        // 32-value chunks of a sample a warp loads at once in pass 2
 constexpr int kStage = 64;        // words gathered at a time per sample and class
 constexpr u64 kWinTile = 128;     // samples per tile
-constexpr int kWinClasses = 17;   // class 0 and up to 16 tiles
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // Bring the 32 values from p on (up to e) toward L2 ahead of their loads.
 __device__ __forceinline__ void prefetch_values(const u64* ids, u64 p, u64 e)
