@@ -76,6 +76,9 @@ struct WinGeom {
     u64 nwin, wpc, G;
     u64 nw;     // words per class bitmap: nwin 2^wl / 64
     int wl;     // log2 of the rows of a window, 12..16
+    // per tile, the order its samples are handed to warps (tile-local
+    // positions, largest sample first: entry 128t + j of the plan's order)
+    const u32* lpt;
 };
 // Pass 1: B (B2 with the two-or-more filter; T x nw words, tile-major) = the
 // tiles' filter bitmaps, cls ((T + 1) x nw, class-major) = the class

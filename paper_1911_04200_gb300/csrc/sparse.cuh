@@ -304,7 +304,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     // kSketchPerSample per sample ----
     std::vector<u32> order(n), pos(n);
     for (u64 i = 0; i < n; ++i) order[i] = (u32)i;
-    DevBuf d_pos, d_order, d_tile, d_cls_of, d_rowk, jobtab, Wc, kbase;
+    DevBuf d_pos, d_order, d_tile, d_cls_of, d_rowk, d_lpt, jobtab, Wc, kbase;
     const u64 nw_max = mt / 64;
     const u64 nb_max = (T + 1) * nw_max / kScanBlockWords;
     // Two slots of batch structures: the next batch is classified while this
@@ -391,6 +391,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
     ALLOC(d_pos, n * sizeof(u32));
     ALLOC(d_order, n * sizeof(u32));
     ALLOC(d_rowk, n * sizeof(u32));
+    ALLOC(d_lpt, n * sizeof(u32));
     ALLOC(d_tile, n * sizeof(u32));
     ALLOC(d_cls_of, n * sizeof(u32));
     ALLOC(jobtab, kMaxTiles * sizeof(TcJobDesc));
@@ -405,6 +406,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
         u64* hs = ctx->h_scalars + 64 + 32 * si;
         if (windowed) {
             x.g = geom(lo, width);
+            x.g.lpt = d_lpt.as<u32>();
             if (x.g.nwin > nwin_max || x.g.G > ranges_max || x.g.nwin * (1ull << wl) != width)
                 return JSIM_ERR_UNSUPPORTED;  // the slot's buffers are sized for nwin_max windows
             if (x.pack_pending) CK(cudaStreamWaitEvent(ccs, x.packed, 0));
@@ -482,6 +484,7 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
         return JSIM_OK;
     };
 
+    std::vector<u64> ssz(n, 0);  // the samples' sketch sizes (by sample)
     if (st.N) {
         u64 ws = 1ull << 16;
         const double want = (double)kSketchPerSample * (double)n;
@@ -531,15 +534,26 @@ int all_pairs_sparse(jsim_ctx* ctx, Staged& st, void* C, uint64_t* sizes, double
             CK(cudaStreamSynchronize(cs));
             const u64* h_sz = (const u64*)ctx->h_sketch;
             order = sample_order((const float*)(h_sz + n), h_sz, n);
+            ssz.assign(h_sz, h_sz + n);
         }
         for (u64 k = 0; k < n; ++k) pos[order[k]] = (u32)k;
-        // per plan entry k (the sample at position k): its tile, class and row
-        std::vector<u32> tile(n), cls_of(n), rowk(n);
+        // per plan entry k (the sample at position k): its tile, class and
+        // row; and per tile the order its samples go to the windowed kernels'
+        // warps: largest sketch first (sizes vary by two decades, and a large
+        // sample taken last would hold its CTA up)
+        std::vector<u32> tile(n), cls_of(n), rowk(n), lpt(n);
         for (u64 k = 0; k < n; ++k) {
             tile[k] = (u32)(k / kTile);
             cls_of[k] = 1 + tile[k];
             rowk[k] = (u32)k;
+            lpt[k] = (u32)(k % kTile);
         }
+        for (u64 k0 = 0; k0 < n; k0 += kTile) {
+            u32* l = lpt.data() + k0;
+            const u64 m = std::min<u64>(kTile, n - k0);
+            std::stable_sort(l, l + m, [&](u32 a, u32 b) { return ssz[order[k0 + a]] > ssz[order[k0 + b]]; });
+        }
+        CK(cudaMemcpyAsync(d_lpt.p, lpt.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
         CK(cudaMemcpyAsync(d_pos.p, pos.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
         CK(cudaMemcpyAsync(d_order.p, order.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));
         CK(cudaMemcpyAsync(d_tile.p, tile.data(), n * sizeof(u32), cudaMemcpyHostToDevice, cs));

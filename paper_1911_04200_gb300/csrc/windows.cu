@@ -109,7 +109,10 @@ k_win_tiles(const u64* __restrict__ ids, Plan plan, WinGeom g, u64* __restrict__
         bool act[kSlots1], hp[kSlots1];
         auto take = [&](int s) {
             u32 e = 0;
-            if (lane == 0) e = atomicAdd(&s_next, 1u);
+            if (lane == 0) {
+                e = atomicAdd(&s_next, 1u);
+                if (e < m) e = g.lpt[k0 + e];  // largest samples first
+            }
             e = __shfl_sync(0xffffffffu, e, 0);
             act[s] = e < m;
             ks[s] = e;
@@ -365,7 +368,10 @@ k_win_pack(const u64* __restrict__ ids, WinGeom g, const u64* __restrict__ cls,
     const int wsh = g.wl - 6;  // words of a window = 1 << wsh
     for (;;) {
         u32 e32 = 0;
-        if (lane == 0) e32 = atomicAdd(&s_next, 1u);
+        if (lane == 0) {
+            e32 = atomicAdd(&s_next, 1u);
+            if (e32 < m) e32 = g.lpt[k0 + e32];  // largest samples first
+        }
         const u64 e = __shfl_sync(0xffffffffu, e32, 0);
         if (e >= m) break;
         const u64 a = curs[r * g.n + k0 + e], b = max(a, curs[(r + 1) * g.n + k0 + e]);
