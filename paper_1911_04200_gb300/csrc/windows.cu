@@ -62,9 +62,10 @@ __device__ __forceinline__ void prefetch_values(const u64* ids, u64 p, u64 e)
 // search; the next range starts where the walk stopped.  Shared memory: the
 // bitmaps, then the tile's cursors and ends.  A warp walks kSlots1 samples
 // at once, 32 consecutive values of each per step, and takes the next
-// sample when one leaves the range.
+// sample when one leaves the range.  Five CTAs an SM with one filter bitmap
+// (47 registers, no spills); the two-or-more filter keeps four.
 template <bool TWICE>
-__global__ void __launch_bounds__(kWin1Threads, 4)
+__global__ void __launch_bounds__(kWin1Threads, TWICE ? 4 : 5)
 k_win_tiles(const u64* __restrict__ ids, Plan plan, WinGeom g, u64* __restrict__ B, u64* __restrict__ B2,
             u64* __restrict__ curs)
 {
