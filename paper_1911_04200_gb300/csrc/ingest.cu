@@ -59,6 +59,8 @@ k_plan(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, u64 
     }
 }
 
+constexpr int kValidateDepth = 4;  // values a thread loads per step
+
 __global__ void __launch_bounds__(kIngestThreads)
 k_validate(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, Plan plan,
            int id_bits, u64* sizes, u32* err, u64* maxid, u64* minid, u64 err_stride)
@@ -75,18 +77,35 @@ k_validate(const u64* __restrict__ offsets, const u64* __restrict__ ids, u64 n, 
         const u64 i = d.i, p0 = d.p0, p1 = d.p1;
         const u64 sb = offsets[i], se = offsets[i + 1];
         u32 cnt = 0, flags = 0;
-        for (u64 pos = p0 + threadIdx.x; pos < p1; pos += kIngestThreads) {
-            u64 x = ids[pos];
-            if (pos > sb) {
-                u64 prev = ids[pos - 1];
-                if (x < prev) flags |= kFlagUnsorted;
-                cnt += (x != prev);
-            } else {
-                cnt += 1;
-                atomicMin(minid, x);
+        // kValidateDepth coalesced loads a thread in flight per step; a
+        // value's predecessor comes from the lane before it (lane 0 loads
+        // its own, ahead, with the values)
+        const int lane = threadIdx.x & 31;
+        for (u64 base = p0; base < p1; base += kValidateDepth * kIngestThreads) {
+            u64 x[kValidateDepth], pv[kValidateDepth];
+            #pragma unroll
+            for (int k = 0; k < kValidateDepth; ++k) {
+                const u64 pos = base + (u64)(k * kIngestThreads) + threadIdx.x;
+                x[k] = pos < p1 ? ids[pos] : 0ull;
+                pv[k] = (lane == 0 && pos < p1 && pos > sb) ? ids[pos - 1] : 0ull;
             }
-            if (id_bits < 64 && (x >> id_bits) != 0) flags |= kFlagIdRange;
-            if (pos + 1 == se) atomicMax(maxid, x);
+            #pragma unroll
+            for (int k = 0; k < kValidateDepth; ++k) {
+                const u64 pos = base + (u64)(k * kIngestThreads) + threadIdx.x;
+                const u64 up = __shfl_up_sync(0xffffffffu, x[k], 1);
+                if (pos >= p1) continue;
+                const u64 v = x[k];
+                if (pos > sb) {
+                    const u64 prev = lane ? up : pv[k];
+                    if (v < prev) flags |= kFlagUnsorted;
+                    cnt += (v != prev);
+                } else {
+                    cnt += 1;
+                    atomicMin(minid, v);
+                }
+                if (id_bits < 64 && (v >> id_bits) != 0) flags |= kFlagIdRange;
+                if (pos + 1 == se) atomicMax(maxid, v);
+            }
         }
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
